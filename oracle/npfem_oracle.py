@@ -1,0 +1,474 @@
+"""Plain CPU FP64 oracle of one npFEM time step for closed triangulated membranes.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import or call this
+module; only tests/, the smoke check and the benchmark's CPU-baseline leg do.
+It shares no code with the CUDA path (the only shared module is the seeded
+input generator, which holds none of the method's arithmetic).
+
+What it computes, and where each piece comes from
+-------------------------------------------------
+* The solid is solved by npFEM, a mass-lumped linear finite-element solver on
+  triangulated membranes, implicit in time (Introduction; Implementation and
+  architecture).  It discretises the elastodynamics equation, Eq. (2).
+* npFEM is derived from ShapeOp / projective dynamics (Bouaziz et al. 2014) and
+  advances bodies with the quasi-Newton projective-dynamics kernel of Liu et
+  al. 2017 (Implementation and architecture, first bullet), iterated towards a
+  converged solution rather than a fixed graphics budget (second bullet).
+* The material is a sum of per-element energies, each with a weight and
+  parameters (Setting up new materials section).
+* Per step the solid solver receives external forces and returns positions and
+  velocities (Implementation and architecture).
+
+The paper prints no formulas for the energies or the iteration; the readings
+used here (strain = distance of the triangle deformation gradient to the
+rotations, cotangent hinge bending with rest-curvature magnitude, quadratic
+global area/volume penalties, Armijo line search with an approximate-Armijo
+fallback, history 5) are listed with their reasons in the project design notes.
+
+Parity pins: every function here is pinned by tests/test_oracle_*.py against
+closed forms, invariants, brute-force Newton minimisation and finite
+differences (no function is "parity unpinned").
+
+Implementation style: plain numpy float64, vectorised over elements only.  A
+dense Cholesky from numpy serves as the library step for the global matrix.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Dict, List, Optional
+
+import numpy as np
+
+# Line-search / history constants (readings; identical on the CUDA side).
+ARMIJO_C1 = 1e-4
+MAX_HALVINGS = 20
+ENERGY_GUARD_EPS = 1e-6        # approximate-Armijo energy guard, relative
+CURVATURE_EPS = 1e-12          # skip pair when s.y <= eps*|s||y|
+HISTORY = 5
+DEGENERATE_DET = 1e-30         # det(F^T F) below this: element contributes nothing
+DEGENERATE_NORM = 1e-30        # |K| below this: projection falls back to K0
+
+STATUS_OK = 0
+STATUS_LINESEARCH_FAIL = 1
+STATUS_DEGENERATE = 2
+STATUS_NONFINITE = 4
+
+
+# ---------------------------------------------------------------- topology
+def hinges_of(tris: np.ndarray, n: int) -> np.ndarray:
+    """Interior edges of a closed oriented mesh as hinges [E, 4] = (i, j, kA, kB).
+
+    (i, j) is the shared edge with i < j; kA is the vertex opposite the edge in
+    the triangle that traverses i -> j, kB the one in the triangle traversing
+    j -> i.  Raises ValueError when the mesh is not a closed 2-manifold.
+    """
+    directed = {}
+    for t in tris:
+        for a, b, c in ((t[0], t[1], t[2]), (t[1], t[2], t[0]), (t[2], t[0], t[1])):
+            key = (int(a), int(b))
+            if key in directed:
+                raise ValueError("edge traversed twice in the same direction")
+            directed[key] = int(c)
+    hinges = []
+    for (a, b), c in directed.items():
+        if a < b:
+            if (b, a) not in directed:
+                raise ValueError("open edge: mesh is not closed")
+            hinges.append((a, b, c, directed[(b, a)]))
+    hinges.sort()
+    return np.array(hinges, dtype=np.int64).reshape(-1, 4)
+
+
+# ---------------------------------------------------------------- rest state
+@dataclasses.dataclass
+class RestState:
+    """Per-cell-type constants computed once from the rest mesh (setup step)."""
+    n: int
+    tris: np.ndarray        # [T, 3]
+    hinges: np.ndarray      # [E, 4]
+    Dm_inv: np.ndarray      # [T, 2, 2] inverse rest edge matrix in the local frame
+    area_rest: np.ndarray   # [T]
+    w_tri: np.ndarray       # [T]   strain weight per triangle = w_strain * rest area
+    c_hinge: np.ndarray     # [E, 4] cotangent hinge stencil
+    kappa0: np.ndarray      # [E]   rest |K|
+    K0: np.ndarray          # [E, 3] rest K (tie-break direction)
+    w_hinge: np.ndarray     # [E]   bending weight per hinge = w_bend * 3/(A_A + A_B)
+    A0: float
+    V0: float
+    mass: np.ndarray        # [n] lumped nodal masses
+    w_area: float
+    w_vol: float
+    dt: float
+
+
+def _cot(a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Cotangent of the angle between row vectors a and b."""
+    return np.einsum("ij,ij->i", a, b) / np.linalg.norm(np.cross(a, b), axis=1)
+
+
+def rest_state(X: np.ndarray, tris: np.ndarray, w_strain: float, w_bend: float,
+               w_area: float, w_vol: float, density: float, dt: float) -> RestState:
+    """Rest-shape constants of a cell type (mass-lumped linear FE, Introduction).
+
+    * Each triangle gets a local orthonormal frame (u along the first edge, w in
+      the plane) and Dm = [e1 e2] expressed in it; F = [x1-x0, x2-x0] Dm^-1.
+    * Each interior edge gets the cotangent hinge stencil c (sums to zero and
+      annihilates flat hinges) and its rest magnitude |K0|.
+    * Lumped masses: the cell mass density*V0 is spread by the area share of
+      each vertex (a third of the incident rest triangle areas).
+    """
+    X = np.asarray(X, dtype=np.float64)
+    tris = np.asarray(tris, dtype=np.int64)
+    n = X.shape[0]
+    x0, x1, x2 = X[tris[:, 0]], X[tris[:, 1]], X[tris[:, 2]]
+    e1, e2 = x1 - x0, x2 - x0
+    cr = np.cross(e1, e2)
+    crn = np.linalg.norm(cr, axis=1)
+    if np.any(crn <= 0):
+        raise ValueError("degenerate rest triangle")
+    area = 0.5 * crn
+    l1 = np.linalg.norm(e1, axis=1)
+    u = e1 / l1[:, None]
+    nrm = cr / crn[:, None]
+    w = np.cross(nrm, u)
+    Dm = np.zeros((tris.shape[0], 2, 2))
+    Dm[:, 0, 0] = l1
+    Dm[:, 0, 1] = np.einsum("ij,ij->i", e2, u)
+    Dm[:, 1, 0] = 0.0
+    Dm[:, 1, 1] = np.einsum("ij,ij->i", e2, w)
+    Dm_inv = np.linalg.inv(Dm)
+
+    H = hinges_of(tris, n)
+    if H.shape[0] * 2 != 3 * tris.shape[0]:
+        raise ValueError("mesh is not a closed manifold")
+    p0, p1, p2, p3 = X[H[:, 0]], X[H[:, 1]], X[H[:, 2]], X[H[:, 3]]
+    cotA0 = _cot(p1 - p0, p2 - p0)
+    cotA1 = _cot(p0 - p1, p2 - p1)
+    cotB0 = _cot(p1 - p0, p3 - p0)
+    cotB1 = _cot(p0 - p1, p3 - p1)
+    c = np.stack([cotA1 + cotB1, cotA0 + cotB0, -(cotA0 + cotA1), -(cotB0 + cotB1)], axis=1)
+    K0 = (c[:, 0, None] * p0 + c[:, 1, None] * p1 + c[:, 2, None] * p2 + c[:, 3, None] * p3)
+    kappa0 = np.linalg.norm(K0, axis=1)
+    areaA = 0.5 * np.linalg.norm(np.cross(p1 - p0, p2 - p0), axis=1)
+    areaB = 0.5 * np.linalg.norm(np.cross(p1 - p0, p3 - p0), axis=1)
+    w_h = w_bend * 3.0 / (areaA + areaB)
+
+    A0 = float(np.sum(area))
+    ctr = X.mean(axis=0)
+    V0 = float(_volume(X - ctr, tris))
+    vert_area = np.zeros(n)
+    for k in range(3):
+        np.add.at(vert_area, tris[:, k], area / 3.0)
+    mass = density * V0 * vert_area / A0
+    return RestState(n, tris, H, Dm_inv, area, w_strain * area, c, kappa0, K0, w_h,
+                     A0, V0, mass, float(w_area), float(w_vol), float(dt))
+
+
+def _volume(x: np.ndarray, tris: np.ndarray) -> float:
+    a, b, c = x[tris[:, 0]], x[tris[:, 1]], x[tris[:, 2]]
+    return np.sum(np.einsum("ij,ij->i", a, np.cross(b, c))) / 6.0
+
+
+# ---------------------------------------------------------------- projections
+def polar_project(F: np.ndarray) -> (np.ndarray, np.ndarray):
+    """Closest rotation-like 3x2 matrix R = F (F^T F)^(-1/2) for a batch of F [T,3,2].
+
+    Uses the closed form of the 2x2 SPD square root:
+    sqrt(C) = (C + sqrt(det C) I) / sqrt(tr C + 2 sqrt(det C)).
+    Returns (R, degenerate_mask); degenerate elements (det C <= 1e-30) get R = F.
+    """
+    C = np.einsum("tki,tkj->tij", F, F)
+    det = C[:, 0, 0] * C[:, 1, 1] - C[:, 0, 1] * C[:, 1, 0]
+    bad = det <= DEGENERATE_DET
+    det_s = np.where(bad, 1.0, det)
+    s = np.sqrt(det_s)
+    tau = np.sqrt(C[:, 0, 0] + C[:, 1, 1] + 2.0 * s)
+    S = (C + s[:, None, None] * np.eye(2)[None]) / tau[:, None, None]
+    detS = S[:, 0, 0] * S[:, 1, 1] - S[:, 0, 1] * S[:, 1, 0]
+    Sinv = np.empty_like(S)
+    Sinv[:, 0, 0] = S[:, 1, 1] / detS
+    Sinv[:, 1, 1] = S[:, 0, 0] / detS
+    Sinv[:, 0, 1] = -S[:, 0, 1] / detS
+    Sinv[:, 1, 0] = -S[:, 1, 0] / detS
+    R = np.einsum("tij,tjk->tik", F, Sinv)
+    R[bad] = F[bad]
+    return R, bad
+
+
+def deformation_gradient(rs: RestState, x: np.ndarray) -> np.ndarray:
+    t = rs.tris
+    E = np.stack([x[t[:, 1]] - x[t[:, 0]], x[t[:, 2]] - x[t[:, 0]]], axis=2)  # [T,3,2]
+    return np.einsum("tij,tjk->tik", E, rs.Dm_inv)
+
+
+def hinge_K(rs: RestState, x: np.ndarray) -> np.ndarray:
+    """K = sum_j c_j x_j, evaluated on edge vectors (sum c_j = 0)."""
+    H, c = rs.hinges, rs.c_hinge
+    base = x[H[:, 0]]
+    return (c[:, 1, None] * (x[H[:, 1]] - base) + c[:, 2, None] * (x[H[:, 2]] - base)
+            + c[:, 3, None] * (x[H[:, 3]] - base))
+
+
+def bending_project(rs: RestState, K: np.ndarray) -> np.ndarray:
+    """Closest point of K on the sphere |p| = |K0|; tie-break p = K0 for |K| ~ 0."""
+    kn = np.linalg.norm(K, axis=1)
+    small = kn < DEGENERATE_NORM
+    p = rs.kappa0[:, None] * K / np.where(small, 1.0, kn)[:, None]
+    p[small] = rs.K0[small]
+    return p
+
+
+# ---------------------------------------------------------------- objective
+@dataclasses.dataclass
+class EnergyParts:
+    inertia: float
+    strain: float
+    bend: float
+    area: float
+    volume: float
+    A: float
+    V: float
+    degenerate: int
+
+    @property
+    def total(self) -> float:
+        return self.inertia + self.strain + self.bend + self.area + self.volume
+
+
+def internal_energy_and_gradient(rs: RestState, x: np.ndarray, w_scale=None):
+    """Elastic energy sum_t E_t + sum_e E_e + E_A + E_V and its gradient [n,3].
+
+    E_t = w_t/2 |F - R(F)|^2,  grad_F = w_t (F - R)   (projection onto rotations)
+    E_e = w_e/2 |K - p(K)|^2,  grad_xj = c_j w_e (K - p)
+    E_A = w_A/2 (A - A0)^2 / A0,  E_V = w_V/2 (V - V0)^2 / V0
+    `w_scale` optionally multiplies (w_strain, w_bend, w_area, w_vol).
+    """
+    ws = np.ones(4) if w_scale is None else np.asarray(w_scale, dtype=np.float64)
+    n = rs.n
+    g = np.zeros((n, 3))
+    t = rs.tris
+    # --- membrane strain, per triangle
+    F = deformation_gradient(rs, x)
+    R, bad = polar_project(F)
+    wt = rs.w_tri * ws[0]
+    Dlt = F - R
+    e_strain = 0.5 * np.sum(wt * np.einsum("tij,tij->t", Dlt, Dlt))
+    P = wt[:, None, None] * Dlt                       # dE/dF  [T,3,2]
+    dE = np.einsum("tij,tkj->tik", P, rs.Dm_inv)      # dE/d[e1 e2] = P Dm^-T  [T,3,2]
+    np.add.at(g, t[:, 1], dE[:, :, 0])
+    np.add.at(g, t[:, 2], dE[:, :, 1])
+    np.add.at(g, t[:, 0], -dE[:, :, 0] - dE[:, :, 1])
+    # --- bending, per hinge
+    K = hinge_K(rs, x)
+    p = bending_project(rs, K)
+    we = rs.w_hinge * ws[1]
+    r = K - p
+    e_bend = 0.5 * np.sum(we * np.einsum("ij,ij->i", r, r))
+    wr = we[:, None] * r
+    for k in range(4):
+        np.add.at(g, rs.hinges[:, k], rs.c_hinge[:, k, None] * wr)
+    # --- global area
+    a, b, c = x[t[:, 0]], x[t[:, 1]], x[t[:, 2]]
+    cr = np.cross(b - a, c - a)
+    crn = np.linalg.norm(cr, axis=1)
+    A = 0.5 * np.sum(crn)
+    nh = cr / np.where(crn > 0, crn, 1.0)[:, None]
+    kA = ws[2] * rs.w_area * (A - rs.A0) / rs.A0
+    e_area = 0.5 * ws[2] * rs.w_area * (A - rs.A0) ** 2 / rs.A0
+    np.add.at(g, t[:, 0], kA * 0.5 * np.cross(nh, c - b))
+    np.add.at(g, t[:, 1], kA * 0.5 * np.cross(nh, a - c))
+    np.add.at(g, t[:, 2], kA * 0.5 * np.cross(nh, b - a))
+    # --- global volume (about the centroid, translation invariant on a closed mesh)
+    ctr = x.mean(axis=0)
+    aa, bb, cc = a - ctr, b - ctr, c - ctr
+    V = np.sum(np.einsum("ij,ij->i", aa, np.cross(bb, cc))) / 6.0
+    kV = ws[3] * rs.w_vol * (V - rs.V0) / rs.V0
+    e_vol = 0.5 * ws[3] * rs.w_vol * (V - rs.V0) ** 2 / rs.V0
+    np.add.at(g, t[:, 0], kV * np.cross(bb, cc) / 6.0)
+    np.add.at(g, t[:, 1], kV * np.cross(cc, aa) / 6.0)
+    np.add.at(g, t[:, 2], kV * np.cross(aa, bb) / 6.0)
+    parts = EnergyParts(0.0, e_strain, e_bend, e_area, e_vol, A, V, int(np.sum(bad)))
+    return parts, g
+
+
+def objective(rs: RestState, x: np.ndarray, y: np.ndarray, w_scale=None):
+    """Implicit-Euler variational objective of one step (Eq. (2) discretised):
+    f(x) = (x-y)^T M (x-y) / (2 dt^2) + E_int(x), and its gradient."""
+    parts, g = internal_energy_and_gradient(rs, x, w_scale)
+    dx = x - y
+    m = rs.mass
+    parts.inertia = float(np.sum(m[:, None] * dx * dx) / (2.0 * rs.dt ** 2))
+    g = g + m[:, None] * dx / rs.dt ** 2
+    return parts, g
+
+
+# ---------------------------------------------------------------- global matrix
+def pd_matrix(rs: RestState, w_scale=None) -> np.ndarray:
+    """Projective-dynamics system matrix (n x n, shared by x, y, z):
+    A = M/dt^2 + sum_t w_t G_t^T G_t + sum_e w_e c_e c_e^T,
+    where G_t maps a triangle's three vertex coordinates to one row of F."""
+    ws = np.ones(4) if w_scale is None else np.asarray(w_scale, dtype=np.float64)
+    n = rs.n
+    A = np.diag(rs.mass / rs.dt ** 2)
+    S = np.array([[-1.0, 1.0, 0.0], [-1.0, 0.0, 1.0]])
+    for ti in range(rs.tris.shape[0]):
+        G = rs.Dm_inv[ti].T @ S                    # [2,3]
+        blk = ws[0] * rs.w_tri[ti] * (G.T @ G)
+        idx = rs.tris[ti]
+        A[np.ix_(idx, idx)] += blk
+    for e in range(rs.hinges.shape[0]):
+        cvec = rs.c_hinge[e]
+        idx = rs.hinges[e]
+        A[np.ix_(idx, idx)] += ws[1] * rs.w_hinge[e] * np.outer(cvec, cvec)
+    return A
+
+
+class GlobalSolver:
+    """H0 = A^-1 applied coordinate-wise through a dense Cholesky factor A = L L^T."""
+
+    def __init__(self, A: np.ndarray):
+        self.A = A
+        self.L = np.linalg.cholesky(A)
+
+    def solve(self, q: np.ndarray) -> np.ndarray:
+        import scipy.linalg as sla
+        z = sla.solve_triangular(self.L, q, lower=True)
+        return sla.solve_triangular(self.L.T, z, lower=False)
+
+
+# ---------------------------------------------------------------- quasi-Newton step
+@dataclasses.dataclass
+class StepResult:
+    x: np.ndarray
+    v: np.ndarray
+    alphas: List[float]
+    energies: List[float]          # f(x_k), k = 0..iters
+    grad_norms: List[float]        # |g_k|, k = 0..iters
+    residual: float
+    status: int
+    trials: int
+
+
+def two_loop(g: np.ndarray, S: List[np.ndarray], Y: List[np.ndarray],
+             solver: GlobalSolver) -> np.ndarray:
+    """L-BFGS two-loop recursion with initial inverse Hessian H0 = A^-1 (Liu et al.
+    2017); returns r = H g (the search direction is -r).  Dots run over all 3n
+    components; S, Y are ordered oldest -> newest."""
+    q = g.copy()
+    m = len(S)
+    rho = [1.0 / np.sum(Y[i] * S[i]) for i in range(m)]
+    a = [0.0] * m
+    for i in range(m - 1, -1, -1):
+        a[i] = rho[i] * np.sum(S[i] * q)
+        q = q - a[i] * Y[i]
+    r = solver.solve(q)
+    for i in range(m):
+        b = rho[i] * np.sum(Y[i] * r)
+        r = r + S[i] * (a[i] - b)
+    return r
+
+
+def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
+         f_ext: np.ndarray, iters: int, w_scale=None) -> StepResult:
+    """One implicit time step of one cell by quasi-Newton projective dynamics.
+
+    y = x_n + dt v_n + dt^2 M^-1 f_ext;  x^(0) = y;  history cleared.
+    Repeat `iters` times: d = -two_loop(g); backtracking line search from alpha = 1
+    (Armijo, or approximate Armijo g(x+ad).d <= (2 c1 - 1) g.d together with an
+    energy guard f(x+ad) <= f(x) + 1e-6 |f(x)|); x <- x + alpha d; keep (s, y) when
+    s.y > 1e-12 |s||y|, at most 5 pairs.
+    v_{n+1} = (x^(iters) - x_n) / dt.  Works relative to the centroid of x_n
+    (the objective is translation invariant), adding it back at the end.
+    """
+    dt = rs.dt
+    ctr = x_n.mean(axis=0)
+    xn = x_n - ctr
+    y = xn + dt * v_n + dt * dt * f_ext / rs.mass[:, None]
+    x = y.copy()
+    parts, g = objective(rs, x, y, w_scale)
+    fx = parts.total
+    g0n = float(np.sqrt(np.sum(g * g)))
+    S: List[np.ndarray] = []
+    Y: List[np.ndarray] = []
+    alphas, energies, gnorms = [], [fx], [g0n]
+    status = STATUS_OK
+    trials = 0
+    for k in range(iters):
+        d = -two_loop(g, S, Y, solver)
+        gd = float(np.sum(g * d))
+        if not gd < 0.0:
+            S.clear()
+            Y.clear()
+            d = -solver.solve(g)
+            gd = float(np.sum(g * d))
+        alpha = 1.0
+        for h in range(MAX_HALVINGS + 1):
+            xt = x + alpha * d
+            pt, gt = objective(rs, xt, y, w_scale)
+            trials += 1
+            ft = pt.total
+            armijo = ft <= fx + ARMIJO_C1 * alpha * gd
+            approx = (float(np.sum(gt * d)) <= (2.0 * ARMIJO_C1 - 1.0) * gd
+                      and ft <= fx + ENERGY_GUARD_EPS * abs(fx))
+            if armijo or approx:
+                break
+            if h == MAX_HALVINGS:
+                status |= STATUS_LINESEARCH_FAIL
+                break
+            alpha *= 0.5
+        s = xt - x
+        yy = gt - g
+        if k < iters - 1:
+            sy = float(np.sum(s * yy))
+            if sy > CURVATURE_EPS * np.sqrt(np.sum(s * s)) * np.sqrt(np.sum(yy * yy)):
+                S.append(s)
+                Y.append(yy)
+                if len(S) > HISTORY:
+                    S.pop(0)
+                    Y.pop(0)
+        x, g, fx = xt, gt, ft
+        if pt.degenerate:
+            status |= STATUS_DEGENERATE
+        alphas.append(alpha)
+        energies.append(fx)
+        gnorms.append(float(np.sqrt(np.sum(g * g))))
+    residual = gnorms[-1] / g0n if g0n > 0 else 0.0
+    x_new = x + ctr
+    v_new = (x - xn) / dt
+    if not (np.all(np.isfinite(x_new)) and np.all(np.isfinite(v_new))):
+        status |= STATUS_NONFINITE
+    return StepResult(x_new, v_new, alphas, energies, gnorms, residual, status, trials)
+
+
+# ---------------------------------------------------------------- batch driver
+class CellType:
+    """Rest state + factored global matrix of one cell type."""
+
+    def __init__(self, verts, tris, material, dt, w_scale=None):
+        w_strain, w_bend, w_area, w_vol, density = material
+        self.rest = rest_state(verts, tris, w_strain, w_bend, w_area, w_vol, density, dt)
+        self.solver = GlobalSolver(pd_matrix(self.rest, w_scale))
+        self.w_scale = w_scale
+
+
+def batch_step(types: List[CellType], type_of_cell, offsets, x, v, f, iters,
+               cells: Optional[List[int]] = None) -> Dict[str, np.ndarray]:
+    """One step for a batch in SoA [3, N_total] layout; returns new x, v (for the
+    selected cells only; other columns are copied through) plus per-cell residuals,
+    statuses and accepted step lengths."""
+    xo, vo = x.copy(), v.copy()
+    ncells = len(type_of_cell)
+    cells = range(ncells) if cells is None else cells
+    res = np.zeros(ncells)
+    st = np.zeros(ncells, dtype=np.int32)
+    alphas = {}
+    for c in cells:
+        s = slice(int(offsets[c]), int(offsets[c + 1]))
+        ct = types[int(type_of_cell[c])]
+        r = step(ct.rest, ct.solver, x[:, s].T, v[:, s].T, f[:, s].T, int(iters[c]), ct.w_scale)
+        xo[:, s] = r.x.T
+        vo[:, s] = r.v.T
+        res[c] = r.residual
+        st[c] = r.status
+        alphas[c] = r.alphas
+    return {"x": xo, "v": vo, "residual": res, "status": st, "alphas": alphas}

@@ -1,0 +1,150 @@
+"""Pins of the oracle's quasi-Newton time step: rest invariance, monotone objective,
+the one-iteration projective-dynamics equivalence, brute-force Newton minimisation
+on tiny meshes, and the history/line-search bookkeeping."""
+import numpy as np
+import pytest
+
+from oracle import npfem_oracle as O
+from paper_2011_04332_b300 import inputs as I
+
+MAT = (1.0, 0.05, 10.0, 10.0, 1.1)
+DT = 0.1
+
+
+def _type(mesh, mat=MAT, dt=DT, w_scale=None):
+    return O.CellType(mesh.verts, mesh.tris, mat, dt, w_scale)
+
+
+def test_rest_stays_at_rest():
+    m = I.rbc_mesh(2)
+    ct = _type(m)
+    x = m.verts @ I.random_rotation(np.random.default_rng(1)).T + np.array([120.0, 40.0, 7.0])
+    r = O.step(ct.rest, ct.solver, x, np.zeros_like(x), np.zeros_like(x), 5)
+    assert np.max(np.abs(r.x - x)) <= 1e-14 * np.max(np.abs(x))
+    assert np.max(np.abs(r.v)) <= 1e-12
+    assert r.status == O.STATUS_OK
+
+
+def test_free_flight_of_rigid_cell():
+    """A rest-shaped cell with uniform velocity and no force translates rigidly."""
+    m = I.rbc_mesh(2)
+    ct = _type(m)
+    v = np.tile(np.array([[0.3, -0.1, 0.2]]), (m.n, 1))
+    r = O.step(ct.rest, ct.solver, m.verts, v, np.zeros_like(v), 3)
+    assert np.allclose(r.x, m.verts + DT * v, rtol=0, atol=1e-13)
+    assert np.allclose(r.v, v, rtol=0, atol=1e-11)
+
+
+def test_uniform_gravity_like_force():
+    """A uniform acceleration a (f = m a) on a rest cell: exact result x + dt^2 a."""
+    m = I.rbc_mesh(2)
+    ct = _type(m)
+    a = np.array([0.0, 0.0, -2.0])
+    f = ct.rest.mass[:, None] * a[None, :]
+    r = O.step(ct.rest, ct.solver, m.verts, np.zeros_like(f), f, 2)
+    assert np.allclose(r.x, m.verts + DT * DT * a, rtol=0, atol=1e-13)
+
+
+def test_objective_decreases_every_iteration():
+    b = I.single_rbc(seed=1000, subdiv=2, iters=8)
+    m = b.types[0].mesh
+    ct = _type(m)
+    x, v, f = b.cell_state(0)
+    f = f * 50.0   # large forces: strongly nonlinear step
+    for s in range(3):
+        r = O.step(ct.rest, ct.solver, x, v, f, 8)
+        e = np.array(r.energies)
+        assert np.all(e[1:] <= e[:-1] + O.ENERGY_GUARD_EPS * np.abs(e[:-1]))
+        assert r.grad_norms[-1] < r.grad_norms[0]
+        x, v = r.x, r.v
+
+
+def test_one_iteration_equals_projective_dynamics_step():
+    """With no area/volume energy and one iteration, quasi-Newton PD reduces to one
+    local/global PD step: x1 = A^-1 (M y/dt^2 + sum_t w_t G_t^T p_t + sum_e w_e c_e p_e)."""
+    m = I.rbc_mesh(2)
+    mat = (1.0, 0.05, 0.0, 0.0, 1.1)
+    ct = _type(m, mat)
+    rs = ct.rest
+    rng = np.random.default_rng(21)
+    x = m.verts
+    v = 0.5 * rng.standard_normal(x.shape)
+    f = 0.05 * rng.standard_normal(x.shape)
+    r = O.step(rs, ct.solver, x, v, f, 1)
+    assert r.alphas == [1.0]
+    # independent assembly of the PD right-hand side at y
+    y = x + DT * v + DT * DT * f / rs.mass[:, None]
+    Fy = O.deformation_gradient(rs, y)
+    P, _ = O.polar_project(Fy)
+    rhs = rs.mass[:, None] * y / DT ** 2
+    S = np.array([[-1.0, 1.0, 0.0], [-1.0, 0.0, 1.0]])
+    for t in range(rs.tris.shape[0]):
+        G = rs.Dm_inv[t].T @ S                         # F_row^T = G [x0 x1 x2]_coord
+        contrib = rs.w_tri[t] * G.T @ P[t].T           # [3 verts, 3 coords]
+        np.add.at(rhs, rs.tris[t], contrib)
+    K = O.hinge_K(rs, y)
+    p = O.bending_project(rs, K)
+    for e in range(rs.hinges.shape[0]):
+        np.add.at(rhs, rs.hinges[e], rs.w_hinge[e] * np.outer(rs.c_hinge[e], p[e]))
+    x1 = np.linalg.solve(O.pd_matrix(rs), rhs)
+    assert np.allclose(r.x, x1, rtol=0, atol=1e-12 * np.max(np.abs(x1)))
+
+
+def _newton_minimise(rs, y, x0, tol=1e-13, max_it=60):
+    """Full Newton with a Hessian from central differences of the analytic gradient,
+    plus backtracking; used only as an independent minimiser."""
+    x = x0.copy()
+    n3 = x.size
+    for it in range(max_it):
+        parts, g = O.objective(rs, x, y)
+        if np.linalg.norm(g) < tol:
+            break
+        h = 1e-7
+        H = np.zeros((n3, n3))
+        for k in range(n3):
+            e = np.zeros(n3)
+            e[k] = h
+            gp = O.objective(rs, x + e.reshape(x.shape), y)[1].ravel()
+            gm = O.objective(rs, x - e.reshape(x.shape), y)[1].ravel()
+            H[:, k] = (gp - gm) / (2 * h)
+        H = 0.5 * (H + H.T)
+        d = -np.linalg.solve(H, g.ravel()).reshape(x.shape)
+        a = 1.0
+        f0 = parts.total
+        while O.objective(rs, x + a * d, y)[0].total > f0 and a > 1e-8:
+            a *= 0.5
+        x = x + a * d
+    return x
+
+
+@pytest.mark.parametrize("mesh_fn,dt", [(I.tetrahedron, 0.5), (I.icosahedron, 0.5)])
+def test_lbfgs_agrees_with_brute_force_newton(mesh_fn, dt):
+    """Many quasi-Newton iterations reach the exact minimiser of the step objective."""
+    m = mesh_fn()
+    mat = (1.0, 0.05, 10.0, 10.0, 1.1)
+    ct = _type(m, mat, dt)
+    rs = ct.rest
+    rng = np.random.default_rng(31)
+    x = m.verts
+    v = 0.2 * rng.standard_normal(x.shape)
+    f = 0.3 * rng.standard_normal(x.shape)
+    r = O.step(rs, ct.solver, x, v, f, 200)
+    ctr = x.mean(axis=0)
+    y = (x - ctr) + dt * v + dt * dt * f / rs.mass[:, None]
+    xs = _newton_minimise(rs, y, y.copy()) + ctr
+    radius = np.max(np.linalg.norm(xs - xs.mean(axis=0), axis=1))
+    assert np.max(np.abs(r.x - xs)) <= 1e-10 * radius
+    assert r.residual < 1e-10
+
+
+def test_history_is_bounded_and_curvature_checked():
+    g = np.random.default_rng(1).standard_normal((10, 3))
+    A = np.diag(np.arange(1, 11, dtype=float))
+    gs = O.GlobalSolver(A)
+    # with no history the two-loop is exactly H0 g = A^-1 g
+    assert np.allclose(O.two_loop(g, [], [], gs), np.linalg.solve(A, g))
+    # secant condition: with one pair (s, y), H y = s
+    s = np.random.default_rng(2).standard_normal((10, 3))
+    y = np.random.default_rng(3).standard_normal((10, 3))
+    y = y + 5 * s                    # make s.y > 0
+    assert np.allclose(O.two_loop(y, [s], [y], gs), s)
