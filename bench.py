@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Throughput of the batched npFEM step on B300 (one JSON line on stdout).
+
+A step is one npfem_step over the whole batch: every cell runs the full quasi-Newton
+solve (prediction, local projections, global FP64 solves, L-BFGS, line search,
+write-back).  Metric: RBC-equivalent cell-steps per second, one RBC-equivalent being
+(n_vertices/642)*(iterations/5).  Default workload: 4096 placed 642-vertex RBCs,
+5 iterations, FP32 form (FP32 local work, FP64 factor/solves/reductions).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload homog4096|hetero10k]
+                  [--precision fp32form|fp64] [--impl ours|reference]
+
+`--impl reference` times the CPU FP64 oracle (the only other implementation of the
+method) on a bounded sample of the same workload.  Under torchrun every rank steps its
+own batch (cells are independent: no collective); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "RBC-equivalent cell-steps/sec on 1 B300 at stated residual"
+UNIT = "RBC-equivalent cell-steps/s"
+
+
+# ------------------------------------------------------------------ workloads
+def make_workload(name: str, rank: int = 0):
+    from paper_2011_04332_b300 import inputs as I
+    if name == "homog4096":
+        b = I.homogeneous_rbc_batch(ncells=4096, seed=1001 + 100 * rank)
+        desc = "homogeneous 4096 RBC (642 vertices, Evans-Fung), 5 iterations, random placement in a 200 um box"
+    elif name == "hetero10k":
+        b = I.heterogeneous_batch(4500, 4500, 1000, seed=1002 + 100 * rank)
+        desc = ("heterogeneous 10^4 cells: 4500 RBC 642v + 4500 RBC 2562v + 1000 PLT 162v, "
+                "3..8 iterations per cell, seeded random order")
+    elif name == "homog1184":
+        b = I.homogeneous_rbc_batch(ncells=1184, seed=1001 + 100 * rank)
+        desc = "homogeneous 1184 RBC (642 vertices; one cell per warp slot), 5 iterations"
+    elif name == "small":
+        b = I.homogeneous_rbc_batch(ncells=64, seed=1001 + 100 * rank)
+        desc = "64 RBC (642 vertices), 5 iterations"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return b, desc
+
+
+# ------------------------------------------------------------------ oracle baseline
+def _oracle_worker(args):
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    from oracle import npfem_oracle as O
+    mesh_v, mesh_t, mat, dt, cells = args
+    ct = O.CellType(mesh_v, mesh_t, mat, dt)
+    t0 = time.perf_counter()
+    for (x, v, f, it) in cells:
+        O.step(ct.rest, ct.solver, x, v, f, int(it))
+    return time.perf_counter() - t0, len(cells)
+
+
+def oracle_baseline(b, sample_cells: int, workers: int):
+    """Time the oracle on the first `sample_cells` cells, one step each, spread over
+    `workers` single-threaded processes (spawn).  Returns (rbc_eq per s, cores, desc)."""
+    import multiprocessing as mp
+    sel = list(range(min(sample_cells, b.ncells)))
+    by_type = {}
+    for c in sel:
+        by_type.setdefault(int(b.type_of_cell[c]), []).append(c)
+    jobs = []
+    for t, cells in by_type.items():
+        ty = b.types[t]
+        chunks = [cells[i::workers] for i in range(workers)]
+        for ch in chunks:
+            if ch:
+                jobs.append((ty.mesh.verts, ty.mesh.tris, ty.material.as_tuple(), b.dt,
+                             [(*b.cell_state(c), b.iters[c]) for c in ch]))
+    ctx = mp.get_context("spawn")
+    env_backup = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env_backup:
+        os.environ[k] = "1"
+    try:
+        t0 = time.perf_counter()
+        with ctx.Pool(workers) as pool:
+            res = pool.map(_oracle_worker, jobs)
+        wall = time.perf_counter() - t0
+    finally:
+        for k, v in env_backup.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    busy = max(r[0] for r in res)  # the slowest worker's stepping time (setup excluded)
+    n = np.array([b.types[int(b.type_of_cell[c])].mesh.n for c in sel], dtype=np.float64)
+    rbc_eq = float(np.sum(n / 642.0 * b.iters[sel] / 5.0))
+    desc = (f"{len(sel)} cells x 1 step of the same workload (first cells in batch order), "
+            f"{workers} single-threaded processes; type setup excluded; wall incl. setup {wall:.1f}s")
+    return rbc_eq / busy, workers, desc
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").strip().splitlines():
+            p = [q.strip() for q in line.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, p[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2011_04332_b300 import build as B
+    from paper_2011_04332_b300 import native
+    B.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    b, desc = make_workload(args.workload, rank)
+    # oracle baseline first (spawned processes, before heavy GPU work), rank 0 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, cores, sdesc = oracle_baseline(b, args.cpu_sample, args.cpu_workers)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc}
+
+    prec = native.FP32FORM if args.precision == "fp32form" else native.FP64
+    tdt = torch.float32 if prec == native.FP32FORM else torch.float64
+    types = [native.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
+    infos = [t.info() for t in types]
+    batch = native.Batch(types, b.type_of_cell, prec)
+    x0 = torch.tensor(b.x, dtype=tdt, device=dev)
+    v0 = torch.tensor(b.v, dtype=tdt, device=dev)
+    f = torch.tensor(b.f, dtype=tdt, device=dev)
+    iters = torch.tensor(b.iters, device=dev)
+    res = torch.zeros(b.ncells, dtype=torch.float64, device=dev)
+    st = torch.zeros(b.ncells, dtype=torch.int32, device=dev)
+    x, v = x0.clone(), v0.clone()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 126 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    # sampled parity against the oracle on the first step (rank 0)
+    err = None
+    if rank == 0 and not args.no_check:
+        from oracle import npfem_oracle as O
+        xs, vs_ = x0.clone(), v0.clone()
+        batch.step(xs, vs_, f, iters=iters, residual=res, status=st)
+        torch.cuda.synchronize()
+        sample = [0, b.ncells // 3, (2 * b.ncells) // 3, b.ncells - 1]
+        ot = {}
+        xin, vin, fin = (t.double().cpu().numpy() for t in (x0, v0, f))
+        xg = xs.double().cpu().numpy()
+        errs = []
+        for c in sample:
+            t = int(b.type_of_cell[c])
+            if t not in ot:
+                ty = b.types[t]
+                ot[t] = O.CellType(ty.mesh.verts, ty.mesh.tris, ty.material.as_tuple(), b.dt)
+            s = b.cell_slice(c)
+            r = O.step(ot[t].rest, ot[t].solver, xin[:, s].T, vin[:, s].T, fin[:, s].T, int(b.iters[c]))
+            rad = np.max(np.linalg.norm(r.x - r.x.mean(axis=0), axis=1))
+            errs.append(float(np.max(np.abs(xg[:, s].T - r.x)) / rad))
+        err = {"cells": sample, "max_rel_position_error": max(errs),
+               "bar": 1e-5 if prec == native.FP32FORM else 1e-10}
+
+    for _ in range(args.warmup):
+        batch.step(x, v, f, iters=iters, residual=res, status=st)
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            batch.step(x, v, f, iters=iters, residual=res, status=st)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    if world > 1:
+        torch.distributed.barrier()
+    ms = [a.elapsed_time(bq) for a, bq in ev]
+    total_ms = float(sum(ms))
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    rbc_eq_per_rank = b.rbc_equivalents()
+    value = rbc_eq_per_rank * world * args.steps / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+    resid = res.cpu().numpy()
+    status = st.cpu().numpy()
+
+    # roofline of the step kernel: FP64 triangular-solve flops (ALU bound, FP64 pipe)
+    nnz = np.array([infos[t]["nnz_factor"] for t in b.type_of_cell], dtype=np.float64)
+    nv = np.array([infos[t]["n_verts"] for t in b.type_of_cell], dtype=np.float64)
+    flops_per_launch = float(np.sum(b.iters * (12.0 * nnz + 3.0 * nv)))
+    fp64_peak, fp32_peak = probe_peaks()
+    achieved = flops_per_launch / (ms_per_step / 1e3) / 1e12
+    roofline = {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak if fp64_peak else None, "traffic": None,
+                "peak_source": "measured live: FP64 FMA probe (8 chains/thread, 4 CTAs/SM)",
+                "algorithmic": "FP64 flops of the triangular solves: iters*(12*nnz(L)+3n) per cell",
+                "kernel_time": "CUDA events around npfem_step (one memset + one kernel per cell type)"}
+
+    # end-to-end through the C ABI with host (pinned) buffers
+    e2e = None
+    if rank == 0 and not args.no_e2e:
+        ssz = 4 if prec == native.FP32FORM else 8
+        hx = torch.empty((3, b.n_total), dtype=tdt, pin_memory=True)
+        hv = torch.empty_like(hx, pin_memory=True)
+        hf = torch.empty_like(hx, pin_memory=True)
+        hx.copy_(x0.cpu())
+        hv.copy_(v0.cpu())
+        hf.copy_(f.cpu())
+        hit = torch.tensor(b.iters, dtype=torch.int32).pin_memory()
+        hres = torch.zeros(b.ncells, dtype=torch.float64).pin_memory()
+        hst = torch.zeros(b.ncells, dtype=torch.int32).pin_memory()
+        nx, nv_, nf, ni, nr, ns = (hx.numpy(), hv.numpy(), hf.numpy(), hit.numpy(), hres.numpy(), hst.numpy())
+        for _ in range(max(1, args.warmup)):
+            batch.step_host(nx, nv_, nf, iters=ni, residual=nr, status=ns, stream=stream.cuda_stream)
+        times = []
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            batch.step_host(nx, nv_, nf, iters=ni, residual=nr, status=ns, stream=stream.cuda_stream)
+            times.append(time.perf_counter() - t0)
+        h2d = 3 * 3 * b.n_total * ssz + 4 * b.ncells
+        d2h = 2 * 3 * b.n_total * ssz + 12 * b.ncells
+        e2e = {"value": rbc_eq_per_rank / statistics.mean(times), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "api": "npfem_step_host (pinned host buffers, copies + step + copies, synchronous)"}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if prec == native.FP32FORM else "f64", "data": "synthetic",
+        "config": {"workload": desc, "cells": b.ncells, "rbc_equivalents_per_step": rbc_eq_per_rank,
+                   "precision": args.precision, "l2": "flushed between steps (256 MB write, untimed)",
+                   "parallelism": "cells sharded across ranks, no collective" if world > 1 else "1 GPU"},
+        "residual": {"median": float(np.median(resid)), "max": float(np.max(resid)),
+                     "definition": "|grad f(x_final)| / |grad f(x_0)| per cell after the step"},
+        "status_nonzero_cells": int(np.count_nonzero(status)),
+        "parity_sample": err,
+        "roofline": roofline,
+        "fp32_peak_tflops": fp32_peak,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": args.steps * len(set(int(t) for t in b.type_of_cell)),
+        "clocks": clk.summary(),
+        "wall_s_timed_region": t_wall,
+    }
+    return out
+
+
+def probe_peaks():
+    import ctypes
+    from paper_2011_04332_b300 import build as B
+    try:
+        lib = ctypes.CDLL(B.build_probe())
+        fn = lib.npfem_probe_fma_peaks
+        fn.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+        a, c = ctypes.c_double(), ctypes.c_double()
+        if fn(ctypes.byref(a), ctypes.byref(c)) == 0:
+            return a.value, c.value
+    except OSError:
+        pass
+    return None, None
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    b, desc = make_workload(args.workload, 0)
+    per_step = []
+    cores = args.cpu_workers
+    sdesc = ""
+    for _ in range(args.warmup + args.steps):
+        v, cores, sdesc = oracle_baseline(b, args.ref_sample, args.cpu_workers)
+        per_step.append(v)
+    vals = per_step[args.warmup:]
+    value = float(statistics.mean(vals))
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "precision": "fp64 (CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="homog4096", choices=["homog4096", "hetero10k", "homog1184", "small"])
+    ap.add_argument("--precision", default="fp32form", choices=["fp32form", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=128)
+    ap.add_argument("--ref-sample", type=int, default=32)
+    ap.add_argument("--cpu-workers", type=int, default=max(1, os.cpu_count() or 1))
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-check", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    out = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

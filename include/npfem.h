@@ -1,0 +1,160 @@
+/*
+ * npfem.h - C ABI of the B300 npFEM batched deformable-body step.
+ *
+ * What the library computes (paper: Palabos-npFEM, arXiv 2011.04332)
+ * ------------------------------------------------------------------
+ * One implicit time step of npFEM - the mass-lumped linear finite-element solver
+ * for triangulated cell membranes (Introduction) - for a batch of independent
+ * red blood cells and platelets.  The step advances every cell from (x_n, v_n)
+ * under per-vertex external forces to (x_{n+1}, v_{n+1}); in the coupled code
+ * these forces come from the immersed-boundary coupling and the positions and
+ * velocities go back to the fluid (Implementation and architecture section).
+ * The step minimises the implicit-Euler objective of Eq. (2)
+ *     f(x) = (x-y)^T M (x-y)/(2 dt^2) + sum_t E_t + sum_e E_e + E_A + E_V,
+ *     y    = x_n + dt v_n + dt^2 M^-1 f_ext,
+ * with the quasi-Newton projective-dynamics iteration the paper adopts from Liu
+ * et al. 2017 (Implementation and architecture, first bullet): L-BFGS with
+ * history 5 whose initial inverse Hessian is the prefactored projective-dynamics
+ * matrix A = M/dt^2 + sum_t w_t G_t^T G_t + sum_e w_e c_e c_e^T (one Cholesky
+ * factor per cell type), plus a backtracking line search.  The elemental
+ * energies (per-triangle strain, per-hinge bending, global area and volume) are
+ * the per-element energies with weights of the material file (Setting up new
+ * materials section).
+ *
+ * Units: um, us, pg (force nN, energy nN*um, weights nN/um).
+ *
+ * Conventions
+ * -----------
+ * - Status codes: 0 = OK, negative = error (see NPFEM_ERR_*).  Errors of
+ *   arguments or setup are returned synchronously; the message is available
+ *   from npfem_last_error_string().  Per-cell numerical outcomes of a step are
+ *   written to the device array status_out as bit flags (NPFEM_CELL_*); device
+ *   code never traps.
+ * - State layout is structure-of-arrays, coordinate-major: x[c*N_total + k] is
+ *   coordinate c (0=x,1=y,2=z) of global vertex k; the vertices of cell i are
+ *   k in [offset_i, offset_{i+1}) in batch order, each cell's vertices in its
+ *   type's mesh order.
+ * - Ownership: the caller owns every state array (device memory for
+ *   npfem_step, host memory for npfem_step_host).  The library owns cell types,
+ *   batches and their device workspace.  Types are immutable after creation and
+ *   may be shared by several batches; a type must outlive its batches.
+ * - Streams: npfem_step and npfem_step_adjoint are asynchronous on the given
+ *   stream (0 = legacy default stream) and perform no host synchronisation, so
+ *   they can be captured into a CUDA graph.  A batch must not be used on two
+ *   streams at the same time (its workspace is shared by its calls).
+ */
+#ifndef NPFEM_H
+#define NPFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int npfem_status;
+
+#define NPFEM_OK 0
+#define NPFEM_ERR_INVALID_ARG (-1)  /* null pointer, bad size or enum */
+#define NPFEM_ERR_BAD_MESH (-2)     /* open / non-manifold mesh or degenerate rest triangle */
+#define NPFEM_ERR_NOT_SPD (-3)      /* global matrix not positive definite (e.g. negative weight) */
+#define NPFEM_ERR_CUDA (-4)         /* a CUDA runtime call failed */
+#define NPFEM_ERR_OOM (-5)          /* device or host allocation failed */
+#define NPFEM_ERR_UNSUPPORTED (-6)  /* size beyond a compiled limit */
+
+/* Per-cell status bits written by a step (device array status_out). */
+#define NPFEM_CELL_OK 0
+#define NPFEM_CELL_LINESEARCH_FAIL 1  /* no acceptable step after 20 halvings (last trial kept) */
+#define NPFEM_CELL_DEGENERATE 2       /* a triangle collapsed (det F^T F <= 1e-30) */
+#define NPFEM_CELL_NONFINITE 4        /* NaN/Inf in the result */
+
+typedef enum { NPFEM_FP64 = 0, NPFEM_FP32FORM = 1 } npfem_precision;
+
+/* Closed, consistently outward-oriented triangle mesh of a cell type at rest
+ * (host memory, read during the call only). */
+typedef struct {
+  int32_t n_verts;
+  int32_t n_tris;
+  const double* rest_xyz; /* [n_verts][3] rest positions, um */
+  const int32_t* tris;    /* [n_tris][3] vertex indices, counter-clockwise seen from outside */
+} npfem_mesh;
+
+/* Per-type material: the weights of the per-element energies. */
+typedef struct {
+  double w_strain; /* nN/um: E_t = w_strain*A_t/2 |F - R(F)|^2 per triangle (A_t rest area) */
+  double w_bend;   /* nN*um: E_e = w_bend*3/(A_A+A_B)/2 |K - |K0| K/|K||^2 per interior edge */
+  double w_area;   /* nN/um: E_A = w_area/2 (A - A0)^2 / A0 */
+  double w_vol;    /* nN/um^2: E_V = w_vol/2 (V - V0)^2 / V0 */
+  double density;  /* pg/um^3: cell mass density*V0, lumped by vertex area share */
+} npfem_material;
+
+typedef struct {
+  int32_t iters;           /* quasi-Newton iterations per cell when iters array is NULL */
+  int32_t alpha_log_len;   /* entries per cell in alpha_log (0 = no log) */
+  double* alpha_log;       /* device [ncells][alpha_log_len] accepted step lengths, or NULL */
+} npfem_solver_opts;
+
+typedef struct npfem_cell_type npfem_cell_type;
+typedef struct npfem_batch npfem_batch;
+
+/* Sizes and factor statistics of a cell type (host-side query). */
+typedef struct {
+  int32_t n_verts, n_tris, n_hinges;
+  int64_t nnz_factor;      /* off-diagonal nonzeros of the unit lower factor */
+  int64_t solve_chunks;    /* 32-entry chunks per triangular solve */
+  double rest_area, rest_volume, total_mass;
+} npfem_type_info;
+
+/* Build a cell type once: rest geometry, lumped masses, the global matrix A and
+ * its FP64 Cholesky factor (fill-reducing ordering, A = P^T L D L^T P), uploaded to
+ * the current CUDA device.  dt in us.  *out is owned by the caller and released
+ * with npfem_destroy_cell_type.  Errors: INVALID_ARG, BAD_MESH, NOT_SPD, CUDA, OOM. */
+npfem_status npfem_create_cell_type(const npfem_mesh* mesh, const npfem_material* mat,
+                                    double dt, npfem_cell_type** out);
+npfem_status npfem_destroy_cell_type(npfem_cell_type* type);
+/* Host-only dry run of npfem_create_cell_type: validates the mesh and material,
+ * builds and factors the global matrix on the host and fills *info, without touching
+ * any GPU.  Same error codes as npfem_create_cell_type (except CUDA/OOM). */
+npfem_status npfem_cell_type_analyze(const npfem_mesh* mesh, const npfem_material* mat, double dt,
+                                     npfem_type_info* info);
+
+npfem_status npfem_cell_type_info(const npfem_cell_type* type, npfem_type_info* info);
+
+/* Group cells into a batch: cell i has type types[type_of_cell[i]] (host arrays,
+ * read during the call).  Computes vertex offsets, per-type work queues and the
+ * launch shape, and allocates the device workspace.  Errors: INVALID_ARG, CUDA, OOM. */
+npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t ntypes,
+                                const int32_t* type_of_cell, int32_t ncells,
+                                npfem_precision prec, npfem_batch** out);
+npfem_status npfem_batch_destroy(npfem_batch* batch);
+/* Total vertex count N_total and the vertex offsets [ncells+1] (host copy). */
+npfem_status npfem_batch_layout(const npfem_batch* batch, int64_t* n_total, int64_t* offsets);
+
+/* One time step for every cell of the batch (device memory, caller-owned).
+ *   x, v  in/out [3][N_total] positions (um) and velocities (um/us): double for
+ *         NPFEM_FP64, float for NPFEM_FP32FORM; overwritten with x_{n+1}, v_{n+1}.
+ *   f_ext in [3][N_total] external forces (nN), same type as x.
+ *   iters in [ncells] int32 per-cell iteration counts (>= 0), or NULL to use opts->iters.
+ *   residual_out out [ncells] |grad f(x_final)| / |grad f(x_0)| (FP64), or NULL.
+ *   status_out   out [ncells] NPFEM_CELL_* bit flags, or NULL.
+ * Asynchronous on `stream` (a cudaStream_t).  Errors: INVALID_ARG, CUDA. */
+npfem_status npfem_step(npfem_batch* batch, void* x, void* v, const void* f_ext,
+                        const int32_t* iters, const npfem_solver_opts* opts,
+                        double* residual_out, int32_t* status_out, void* stream);
+
+/* Same step with HOST arrays (pageable or pinned): copies x, v, f_ext (and iters,
+ * when given) to batch-owned device buffers, runs npfem_step, and copies x, v,
+ * residuals and statuses back; synchronous.  residual_out/status_out are host
+ * arrays or NULL. */
+npfem_status npfem_step_host(npfem_batch* batch, void* x, void* v, const void* f_ext,
+                             const int32_t* iters, const npfem_solver_opts* opts,
+                             double* residual_out, int32_t* status_out, void* stream);
+
+/* Message of the last error returned on the calling thread (empty if none). */
+npfem_status npfem_last_error_string(char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NPFEM_H */

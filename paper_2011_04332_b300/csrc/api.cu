@@ -1,0 +1,438 @@
+// C ABI of the npFEM library: cell types, batches and the batched step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/npfem.h"
+#include "npfem_internal.h"
+#include "step_kernel.cuh"
+
+using namespace npfem;
+
+namespace {
+thread_local std::string g_last_error;
+
+npfem_status fail(npfem_status code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+#define NPFEM_CUDA_TRY(expr)                                                              \
+  do {                                                                                    \
+    cudaError_t e_ = (expr);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? NPFEM_ERR_OOM : NPFEM_ERR_CUDA,       \
+                  std::string(#expr) + ": " + cudaGetErrorString(e_));                    \
+  } while (0)
+
+// Device allocation list owned by a type or batch.
+struct DevAllocs {
+  std::vector<void*> ptrs;
+  ~DevAllocs() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  cudaError_t upload(const std::vector<T>& h, const T** out) {
+    void* d = nullptr;
+    size_t bytes = std::max<size_t>(1, h.size()) * sizeof(T);
+    cudaError_t e = cudaMalloc(&d, bytes);
+    if (e != cudaSuccess) return e;
+    ptrs.push_back(d);
+    if (!h.empty()) e = cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    *out = static_cast<const T*>(d);
+    return e;
+  }
+  cudaError_t alloc(size_t bytes, void** out) {
+    cudaError_t e = cudaMalloc(out, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) ptrs.push_back(*out);
+    return e;
+  }
+};
+
+template <typename D, typename S>
+std::vector<D> convert(const std::vector<S>& s) {
+  return std::vector<D>(s.begin(), s.end());
+}
+}  // namespace
+
+struct npfem_cell_type {
+  HostType host;
+  DevAllocs mem;
+  DevTypeView<double> v64;
+  DevTypeView<float> v32;
+  int device = 0;
+};
+
+struct TypeLaunch {
+  int type_index;
+  int ncells;
+  const int32_t* cell_list;  // device
+  int* counter;              // device
+  char* scratch;
+  size_t slot_bytes;
+  int blocks, warps_per_block;
+  int z_in_smem;
+  size_t smem_bytes;
+};
+
+struct npfem_batch {
+  std::vector<const npfem_cell_type*> types;
+  std::vector<int32_t> type_of_cell;
+  std::vector<int64_t> offsets;
+  int64_t n_total = 0;
+  int ncells = 0;
+  npfem_precision prec = NPFEM_FP64;
+  DevAllocs mem;
+  const int64_t* d_offsets = nullptr;
+  std::vector<TypeLaunch> launches;
+  int* d_counters = nullptr;
+  // host-step staging (allocated on first npfem_step_host)
+  void* d_x = nullptr;
+  void* d_v = nullptr;
+  void* d_f = nullptr;
+  int32_t* d_iters = nullptr;
+  double* d_res = nullptr;
+  int32_t* d_status = nullptr;
+};
+
+template <typename S>
+static void fill_view(npfem_cell_type* t, DevTypeView<S>* v, const S* Dinv, const S* w_tri, const S* c_hinge,
+                      const S* K0, const S* w_hinge, const S* mass, const S* inv_mass, const S* inc_coef,
+                      const int32_t* tris, const int32_t* hinges, const int32_t* inc_ptr, const int32_t* inc_code,
+                      const int32_t* perm, const double* dinv, const int32_t* fcol, const uint16_t* frow,
+                      const double* fval, const int32_t* bcol, const uint16_t* brow, const double* bval) {
+  const HostType& H = t->host;
+  v->n = H.n;
+  v->T = H.T;
+  v->E = H.E;
+  v->nchunks_fwd = (int)H.fwd_col.size();
+  v->nchunks_bwd = (int)H.bwd_col.size();
+  v->tris = tris;
+  v->Dinv = Dinv;
+  v->w_tri = w_tri;
+  v->hinges = hinges;
+  v->c_hinge = c_hinge;
+  v->K0 = K0;
+  v->w_hinge = w_hinge;
+  v->mass = mass;
+  v->inv_mass = inv_mass;
+  v->inc_ptr = inc_ptr;
+  v->inc_code = inc_code;
+  v->inc_coef = inc_coef;
+  v->perm = perm;
+  v->dinv = dinv;
+  v->fwd_col = fcol;
+  v->fwd_row = frow;
+  v->fwd_val = fval;
+  v->bwd_col = bcol;
+  v->bwd_row = brow;
+  v->bwd_val = bval;
+  v->A0 = H.A0;
+  v->V0 = H.V0;
+  v->w_area = H.w_area;
+  v->w_vol = H.w_vol;
+  v->dt = H.dt;
+}
+
+template <typename S>
+static cudaError_t upload_precision(npfem_cell_type* t, DevTypeView<S>* view, const int32_t* tris,
+                                    const int32_t* hinges, const int32_t* inc_ptr, const int32_t* inc_code,
+                                    const int32_t* perm, const double* dinv, const int32_t* fcol,
+                                    const uint16_t* frow, const double* fval, const int32_t* bcol,
+                                    const uint16_t* brow, const double* bval) {
+  const HostType& H = t->host;
+  std::vector<double> inv_mass(H.n);
+  for (int i = 0; i < H.n; ++i) inv_mass[i] = 1.0 / H.mass[i];
+  const S *Dinv, *w_tri, *c_hinge, *K0, *w_hinge, *mass, *im, *coef;
+  cudaError_t e;
+  if ((e = t->mem.upload(convert<S>(H.Dinv), &Dinv)) != cudaSuccess) return e;
+  if ((e = t->mem.upload(convert<S>(H.w_tri), &w_tri)) != cudaSuccess) return e;
+  if ((e = t->mem.upload(convert<S>(H.c_hinge), &c_hinge)) != cudaSuccess) return e;
+  if ((e = t->mem.upload(convert<S>(H.K0), &K0)) != cudaSuccess) return e;
+  if ((e = t->mem.upload(convert<S>(H.w_hinge), &w_hinge)) != cudaSuccess) return e;
+  if ((e = t->mem.upload(convert<S>(H.mass), &mass)) != cudaSuccess) return e;
+  if ((e = t->mem.upload(convert<S>(inv_mass), &im)) != cudaSuccess) return e;
+  if ((e = t->mem.upload(convert<S>(H.inc_coef), &coef)) != cudaSuccess) return e;
+  fill_view<S>(t, view, Dinv, w_tri, c_hinge, K0, w_hinge, mass, im, coef, tris, hinges, inc_ptr, inc_code, perm,
+               dinv, fcol, frow, fval, bcol, brow, bval);
+  return cudaSuccess;
+}
+
+extern "C" {
+
+npfem_status npfem_last_error_string(char* buf, size_t len) {
+  if (!buf || len == 0) return NPFEM_ERR_INVALID_ARG;
+  std::snprintf(buf, len, "%s", g_last_error.c_str());
+  return NPFEM_OK;
+}
+
+npfem_status npfem_create_cell_type(const npfem_mesh* mesh, const npfem_material* mat, double dt,
+                                    npfem_cell_type** out) {
+  if (!mesh || !mat || !out) return fail(NPFEM_ERR_INVALID_ARG, "create_cell_type: null argument");
+  *out = nullptr;
+  auto* t = new (std::nothrow) npfem_cell_type();
+  if (!t) return fail(NPFEM_ERR_OOM, "create_cell_type: host allocation failed");
+  std::string err;
+  int rc = build_host_type(mesh->n_verts, mesh->n_tris, mesh->rest_xyz, mesh->tris, mat->w_strain, mat->w_bend,
+                           mat->w_area, mat->w_vol, mat->density, dt, &t->host, &err);
+  if (rc != NPFEM_OK) {
+    delete t;
+    return fail(rc, err);
+  }
+  cudaError_t e = cudaGetDevice(&t->device);
+  const HostType& H = t->host;
+  const int32_t *tris, *hinges, *inc_ptr, *inc_code, *perm, *fcol, *bcol;
+  const uint16_t *frow, *brow;
+  const double *dinv, *fval, *bval;
+#define UP(vec, ptr)                                      \
+  if (e == cudaSuccess) e = t->mem.upload(vec, &ptr);
+  UP(H.tris, tris);
+  UP(H.hinges, hinges);
+  UP(H.inc_ptr, inc_ptr);
+  UP(H.inc_code, inc_code);
+  UP(H.perm, perm);
+  UP(H.dinv, dinv);
+  UP(H.fwd_col, fcol);
+  UP(H.fwd_row, frow);
+  UP(H.fwd_val, fval);
+  UP(H.bwd_col, bcol);
+  UP(H.bwd_row, brow);
+  UP(H.bwd_val, bval);
+#undef UP
+  if (e == cudaSuccess)
+    e = upload_precision<double>(t, &t->v64, tris, hinges, inc_ptr, inc_code, perm, dinv, fcol, frow, fval, bcol,
+                                 brow, bval);
+  if (e == cudaSuccess)
+    e = upload_precision<float>(t, &t->v32, tris, hinges, inc_ptr, inc_code, perm, dinv, fcol, frow, fval, bcol,
+                                brow, bval);
+  if (e != cudaSuccess) {
+    delete t;
+    return fail(e == cudaErrorMemoryAllocation ? NPFEM_ERR_OOM : NPFEM_ERR_CUDA,
+                std::string("create_cell_type: device upload failed: ") + cudaGetErrorString(e));
+  }
+  *out = t;
+  return NPFEM_OK;
+}
+
+npfem_status npfem_destroy_cell_type(npfem_cell_type* type) {
+  if (!type) return fail(NPFEM_ERR_INVALID_ARG, "destroy_cell_type: null");
+  delete type;
+  return NPFEM_OK;
+}
+
+npfem_status npfem_cell_type_info(const npfem_cell_type* t, npfem_type_info* info) {
+  if (!t || !info) return fail(NPFEM_ERR_INVALID_ARG, "cell_type_info: null argument");
+  const HostType& H = t->host;
+  info->n_verts = H.n;
+  info->n_tris = H.T;
+  info->n_hinges = H.E;
+  info->nnz_factor = H.nnz_factor;
+  info->solve_chunks = (int64_t)H.fwd_col.size();
+  info->rest_area = H.A0;
+  info->rest_volume = H.V0;
+  info->total_mass = H.total_mass;
+  return NPFEM_OK;
+}
+
+npfem_status npfem_cell_type_analyze(const npfem_mesh* mesh, const npfem_material* mat, double dt,
+                                     npfem_type_info* info) {
+  if (!mesh || !mat || !info) return fail(NPFEM_ERR_INVALID_ARG, "cell_type_analyze: null argument");
+  HostType H;
+  std::string err;
+  int rc = build_host_type(mesh->n_verts, mesh->n_tris, mesh->rest_xyz, mesh->tris, mat->w_strain, mat->w_bend,
+                           mat->w_area, mat->w_vol, mat->density, dt, &H, &err);
+  if (rc != NPFEM_OK) return fail(rc, err);
+  info->n_verts = H.n;
+  info->n_tris = H.T;
+  info->n_hinges = H.E;
+  info->nnz_factor = H.nnz_factor;
+  info->solve_chunks = (int64_t)H.fwd_col.size();
+  info->rest_area = H.A0;
+  info->rest_volume = H.V0;
+  info->total_mass = H.total_mass;
+  return NPFEM_OK;
+}
+
+npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t ntypes, const int32_t* type_of_cell,
+                                int32_t ncells, npfem_precision prec, npfem_batch** out) {
+  if (!out || !types || ntypes <= 0 || ncells < 0 || (ncells > 0 && !type_of_cell))
+    return fail(NPFEM_ERR_INVALID_ARG, "batch_create: bad arguments");
+  if (prec != NPFEM_FP64 && prec != NPFEM_FP32FORM) return fail(NPFEM_ERR_INVALID_ARG, "batch_create: bad precision");
+  *out = nullptr;
+  for (int i = 0; i < ntypes; ++i)
+    if (!types[i]) return fail(NPFEM_ERR_INVALID_ARG, "batch_create: null type");
+  for (int c = 0; c < ncells; ++c)
+    if (type_of_cell[c] < 0 || type_of_cell[c] >= ntypes)
+      return fail(NPFEM_ERR_INVALID_ARG, "batch_create: type_of_cell out of range");
+  auto* b = new (std::nothrow) npfem_batch();
+  if (!b) return fail(NPFEM_ERR_OOM, "batch_create: host allocation failed");
+  b->types.assign(types, types + ntypes);
+  b->type_of_cell.assign(type_of_cell, type_of_cell + ncells);
+  b->ncells = ncells;
+  b->prec = prec;
+  b->offsets.assign(ncells + 1, 0);
+  for (int c = 0; c < ncells; ++c) b->offsets[c + 1] = b->offsets[c] + types[type_of_cell[c]]->host.n;
+  b->n_total = b->offsets[ncells];
+  auto cleanup = [&](npfem_status code, const std::string& msg) {
+    delete b;
+    return fail(code, msg);
+  };
+  cudaError_t e = b->mem.upload(b->offsets, &b->d_offsets);
+  if (e != cudaSuccess) return cleanup(NPFEM_ERR_CUDA, std::string("batch_create: ") + cudaGetErrorString(e));
+  void* cnt = nullptr;
+  e = b->mem.alloc(sizeof(int) * ntypes, &cnt);
+  if (e != cudaSuccess) return cleanup(NPFEM_ERR_OOM, std::string("batch_create: ") + cudaGetErrorString(e));
+  b->d_counters = static_cast<int*>(cnt);
+  int dev = 0, sms = 148, smem_optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const size_t ssize = prec == NPFEM_FP64 ? sizeof(double) : sizeof(float);
+  for (int ti = 0; ti < ntypes; ++ti) {
+    std::vector<int32_t> list;
+    for (int c = 0; c < ncells; ++c)
+      if (type_of_cell[c] == ti) list.push_back(c);
+    if (list.empty()) continue;
+    const HostType& H = types[ti]->host;
+    TypeLaunch L{};
+    L.type_index = ti;
+    L.ncells = (int)list.size();
+    L.warps_per_block = 4;
+    const int blocks_per_sm = 2;
+    L.blocks = std::min<int>(sms * blocks_per_sm, (L.ncells + L.warps_per_block - 1) / L.warps_per_block);
+    size_t zbytes = sizeof(double) * 3 * ((size_t)H.n + 1);
+    L.z_in_smem = (zbytes * L.warps_per_block <= 100 * 1024) ? 1 : 0;
+    L.smem_bytes = L.z_in_smem ? zbytes * L.warps_per_block : 0;
+    size_t v = (size_t)3 * H.n;
+    size_t bytes = ssize * ((8 + 2 * kHistory) * v + 9 * (size_t)H.T + 3 * (size_t)H.E);
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (!L.z_in_smem) bytes += zbytes;
+    L.slot_bytes = (bytes + 255) & ~(size_t)255;
+    const int32_t* dl = nullptr;
+    if ((e = b->mem.upload(list, &dl)) != cudaSuccess)
+      return cleanup(NPFEM_ERR_OOM, std::string("batch_create: ") + cudaGetErrorString(e));
+    L.cell_list = dl;
+    void* scr = nullptr;
+    if ((e = b->mem.alloc(L.slot_bytes * (size_t)L.blocks * L.warps_per_block, &scr)) != cudaSuccess)
+      return cleanup(NPFEM_ERR_OOM, std::string("batch_create: workspace: ") + cudaGetErrorString(e));
+    L.scratch = static_cast<char*>(scr);
+    L.counter = b->d_counters + ti;
+    if (L.smem_bytes > 48 * 1024) {
+      if (prec == NPFEM_FP64)
+        e = cudaFuncSetAttribute(npfem_step_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)std::min<size_t>(L.smem_bytes, smem_optin));
+      else
+        e = cudaFuncSetAttribute(npfem_step_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)std::min<size_t>(L.smem_bytes, smem_optin));
+      if (e != cudaSuccess) return cleanup(NPFEM_ERR_CUDA, std::string("batch_create: ") + cudaGetErrorString(e));
+    }
+    b->launches.push_back(L);
+  }
+  *out = b;
+  return NPFEM_OK;
+}
+
+npfem_status npfem_batch_destroy(npfem_batch* batch) {
+  if (!batch) return fail(NPFEM_ERR_INVALID_ARG, "batch_destroy: null");
+  delete batch;
+  return NPFEM_OK;
+}
+
+npfem_status npfem_batch_layout(const npfem_batch* b, int64_t* n_total, int64_t* offsets) {
+  if (!b) return fail(NPFEM_ERR_INVALID_ARG, "batch_layout: null batch");
+  if (n_total) *n_total = b->n_total;
+  if (offsets) std::memcpy(offsets, b->offsets.data(), sizeof(int64_t) * b->offsets.size());
+  return NPFEM_OK;
+}
+
+npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, const int32_t* iters,
+                        const npfem_solver_opts* opts, double* residual_out, int32_t* status_out, void* stream) {
+  if (!b || !opts) return fail(NPFEM_ERR_INVALID_ARG, "step: null batch or opts");
+  if (b->ncells == 0) return NPFEM_OK;
+  if (!x || !v || !f_ext) return fail(NPFEM_ERR_INVALID_ARG, "step: null state array");
+  if (opts->iters < 0) return fail(NPFEM_ERR_INVALID_ARG, "step: negative iteration count");
+  if (opts->alpha_log_len < 0 || (opts->alpha_log_len > 0 && !opts->alpha_log))
+    return fail(NPFEM_ERR_INVALID_ARG, "step: bad alpha log");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size(), st));
+  for (const TypeLaunch& L : b->launches) {
+    const npfem_cell_type* t = b->types[L.type_index];
+    StepParams P;
+    P.ncells_list = L.ncells;
+    P.cell_list = L.cell_list;
+    P.offsets = b->d_offsets;
+    P.n_total = b->n_total;
+    P.iters = iters;
+    P.iters_default = opts->iters;
+    P.residual_out = residual_out;
+    P.status_out = status_out;
+    P.alpha_log = opts->alpha_log;
+    P.alpha_log_len = opts->alpha_log_len;
+    P.queue_counter = L.counter;
+    P.scratch = L.scratch;
+    P.slot_bytes = L.slot_bytes;
+    P.z_in_smem = L.z_in_smem;
+    dim3 grid(L.blocks), block(32 * L.warps_per_block);
+    if (b->prec == NPFEM_FP64)
+      npfem_step_kernel<double><<<grid, block, L.smem_bytes, st>>>(t->v64, P, static_cast<double*>(x),
+                                                                   static_cast<double*>(v),
+                                                                   static_cast<const double*>(f_ext));
+    else
+      npfem_step_kernel<float><<<grid, block, L.smem_bytes, st>>>(t->v32, P, static_cast<float*>(x),
+                                                                  static_cast<float*>(v),
+                                                                  static_cast<const float*>(f_ext));
+    NPFEM_CUDA_TRY(cudaGetLastError());
+  }
+  return NPFEM_OK;
+}
+
+npfem_status npfem_step_host(npfem_batch* b, void* x, void* v, const void* f_ext, const int32_t* iters,
+                             const npfem_solver_opts* opts, double* residual_out, int32_t* status_out,
+                             void* stream) {
+  if (!b || !opts || !x || !v || !f_ext) return fail(NPFEM_ERR_INVALID_ARG, "step_host: null argument");
+  if (b->ncells == 0) return NPFEM_OK;
+  const size_t ssize = b->prec == NPFEM_FP64 ? sizeof(double) : sizeof(float);
+  const size_t bytes = ssize * 3 * (size_t)b->n_total;
+  if (!b->d_x) {
+    void* p;
+    NPFEM_CUDA_TRY(b->mem.alloc(bytes, &p));
+    b->d_x = p;
+    NPFEM_CUDA_TRY(b->mem.alloc(bytes, &p));
+    b->d_v = p;
+    NPFEM_CUDA_TRY(b->mem.alloc(bytes, &p));
+    b->d_f = p;
+    NPFEM_CUDA_TRY(b->mem.alloc(sizeof(int32_t) * b->ncells, &p));
+    b->d_iters = static_cast<int32_t*>(p);
+    NPFEM_CUDA_TRY(b->mem.alloc(sizeof(double) * b->ncells, &p));
+    b->d_res = static_cast<double*>(p);
+    NPFEM_CUDA_TRY(b->mem.alloc(sizeof(int32_t) * b->ncells, &p));
+    b->d_status = static_cast<int32_t*>(p);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_x, x, bytes, cudaMemcpyHostToDevice, st));
+  NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_v, v, bytes, cudaMemcpyHostToDevice, st));
+  NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_f, f_ext, bytes, cudaMemcpyHostToDevice, st));
+  if (iters)
+    NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_iters, iters, sizeof(int32_t) * b->ncells, cudaMemcpyHostToDevice, st));
+  npfem_solver_opts o = *opts;
+  o.alpha_log = nullptr;
+  o.alpha_log_len = 0;
+  npfem_status rc = npfem_step(b, b->d_x, b->d_v, b->d_f, iters ? b->d_iters : nullptr, &o, b->d_res,
+                               b->d_status, stream);
+  if (rc != NPFEM_OK) return rc;
+  NPFEM_CUDA_TRY(cudaMemcpyAsync(x, b->d_x, bytes, cudaMemcpyDeviceToHost, st));
+  NPFEM_CUDA_TRY(cudaMemcpyAsync(v, b->d_v, bytes, cudaMemcpyDeviceToHost, st));
+  if (residual_out)
+    NPFEM_CUDA_TRY(cudaMemcpyAsync(residual_out, b->d_res, sizeof(double) * b->ncells, cudaMemcpyDeviceToHost, st));
+  if (status_out)
+    NPFEM_CUDA_TRY(
+        cudaMemcpyAsync(status_out, b->d_status, sizeof(int32_t) * b->ncells, cudaMemcpyDeviceToHost, st));
+  NPFEM_CUDA_TRY(cudaStreamSynchronize(st));
+  return NPFEM_OK;
+}
+
+}  // extern "C"

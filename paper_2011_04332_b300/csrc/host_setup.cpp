@@ -1,0 +1,414 @@
+// Per-cell-type setup on the host, once per type: topology, rest geometry, lumped
+// masses, the projective-dynamics matrix, a fill-reducing ordering, the FP64
+// Cholesky (LDL^T) factor and the chunked tables the GPU triangular solves read.
+//
+// The global matrix is A = M/dt^2 + sum_t w_t G_t^T G_t + sum_e w_e c_e c_e^T
+// (projective dynamics of Bouaziz et al. 2014, reused as the initial Hessian of the
+// quasi-Newton iteration of Liu et al. 2017; both named in the paper's
+// Implementation and architecture section).  It depends only on the rest mesh,
+// the weights and dt, so it is factored once per cell type.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <map>
+#include <numeric>
+#include <set>
+#include <utility>
+
+#include "npfem_internal.h"
+#include "../../include/npfem.h"
+
+namespace npfem {
+namespace {
+
+struct V3 {
+  double x, y, z;
+};
+inline V3 sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+inline V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+inline double norm(V3 a) { return std::sqrt(dot(a, a)); }
+inline double cotangent(V3 a, V3 b) { return dot(a, b) / norm(cross(a, b)); }
+
+// ---------------------------------------------------------------- orderings
+using Graph = std::vector<std::vector<int>>;
+
+// Geometric nested dissection: split along the longest axis at the median; the
+// separator is the set of left-side vertices with a neighbour on the right side.
+void nested_dissection(const Graph& g, const std::vector<V3>& p, std::vector<int> idx,
+                       std::vector<int>* order, int leaf) {
+  if ((int)idx.size() <= leaf) {
+    order->insert(order->end(), idx.begin(), idx.end());
+    return;
+  }
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int v : idx) {
+    const double c[3] = {p[v].x, p[v].y, p[v].z};
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = std::min(lo[k], c[k]);
+      hi[k] = std::max(hi[k], c[k]);
+    }
+  }
+  int ax = 0;
+  for (int k = 1; k < 3; ++k)
+    if (hi[k] - lo[k] > hi[ax] - lo[ax]) ax = k;
+  auto coord = [&](int v) { return ax == 0 ? p[v].x : (ax == 1 ? p[v].y : p[v].z); };
+  std::vector<int> sorted = idx;
+  std::sort(sorted.begin(), sorted.end(), [&](int a, int b) {
+    double ca = coord(a), cb = coord(b);
+    return ca < cb || (ca == cb && a < b);
+  });
+  size_t half = sorted.size() / 2;
+  std::vector<char> side(p.size(), 2);  // 0 left, 1 right, 2 outside this subproblem
+  for (size_t i = 0; i < sorted.size(); ++i) side[sorted[i]] = i < half ? 0 : 1;
+  std::vector<int> left, right, sep;
+  for (int v : sorted) {
+    if (side[v] == 1) {
+      right.push_back(v);
+      continue;
+    }
+    bool touches = false;
+    for (int u : g[v])
+      if (side[u] == 1) {
+        touches = true;
+        break;
+      }
+    (touches ? sep : left).push_back(v);
+  }
+  if (left.empty() || right.empty()) {  // cannot split further
+    order->insert(order->end(), idx.begin(), idx.end());
+    return;
+  }
+  std::sort(left.begin(), left.end());
+  std::sort(right.begin(), right.end());
+  nested_dissection(g, p, left, order, leaf);
+  nested_dissection(g, p, right, order, leaf);
+  order->insert(order->end(), sep.begin(), sep.end());
+}
+
+// Exact minimum degree on the elimination graph (small n only).
+std::vector<int> minimum_degree(const Graph& g) {
+  int n = (int)g.size();
+  std::vector<std::set<int>> nb(n);
+  for (int v = 0; v < n; ++v)
+    for (int u : g[v])
+      if (u != v) nb[v].insert(u);
+  std::vector<char> alive(n, 1);
+  std::set<std::pair<int, int>> pq;
+  for (int v = 0; v < n; ++v) pq.insert({(int)nb[v].size(), v});
+  std::vector<int> order;
+  order.reserve(n);
+  while (!pq.empty()) {
+    int v = pq.begin()->second;
+    pq.erase(pq.begin());
+    alive[v] = 0;
+    order.push_back(v);
+    std::vector<int> N(nb[v].begin(), nb[v].end());
+    for (int a : N) {
+      pq.erase({(int)nb[a].size(), a});
+      nb[a].erase(v);
+      for (int b : N)
+        if (b != a) nb[a].insert(b);
+      pq.insert({(int)nb[a].size(), a});
+    }
+  }
+  return order;
+}
+
+// Symbolic factorisation of the permuted pattern: column structures (rows > j).
+int64_t symbolic(const Graph& g, const std::vector<int>& order, std::vector<std::vector<int>>* cols) {
+  int n = (int)g.size();
+  std::vector<int> inv(n);
+  for (int i = 0; i < n; ++i) inv[order[i]] = i;
+  std::vector<std::vector<int>> children(n);
+  cols->assign(n, {});
+  int64_t nnz = 0;
+  for (int j = 0; j < n; ++j) {
+    std::set<int> s;
+    for (int u : g[order[j]]) {
+      int r = inv[u];
+      if (r > j) s.insert(r);
+    }
+    for (int c : children[j])
+      for (int r : (*cols)[c])
+        if (r > j) s.insert(r);
+    (*cols)[j].assign(s.begin(), s.end());
+    nnz += (int64_t)s.size();
+    if (!s.empty()) children[*s.begin()].push_back(j);
+  }
+  return nnz;
+}
+
+}  // namespace
+
+int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double w_strain,
+                    double w_bend, double w_area, double w_vol, double density, double dt,
+                    HostType* out, std::string* err) {
+  if (n < 4 || T < 4 || !xyz || !tris || !(dt > 0) || !(density > 0)) {
+    *err = "create_cell_type: need n >= 4, T >= 4, dt > 0, density > 0 and non-null arrays";
+    return NPFEM_ERR_INVALID_ARG;
+  }
+  if (n > 65535) {
+    *err = "create_cell_type: at most 65535 vertices per cell type";
+    return NPFEM_ERR_UNSUPPORTED;
+  }
+  HostType& H = *out;
+  H.n = n;
+  H.T = T;
+  H.dt = dt;
+  H.w_area = w_area;
+  H.w_vol = w_vol;
+  H.tris.assign(tris, tris + 3 * T);
+  std::vector<V3> X(n);
+  for (int i = 0; i < n; ++i) X[i] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
+  for (int k = 0; k < 3 * T; ++k)
+    if (tris[k] < 0 || tris[k] >= n) {
+      *err = "create_cell_type: triangle index out of range";
+      return NPFEM_ERR_BAD_MESH;
+    }
+
+  // ---- topology: each directed edge once, each undirected edge in both directions
+  std::map<std::pair<int, int>, int> directed;  // (a,b) -> opposite vertex
+  for (int t = 0; t < T; ++t) {
+    const int* v = &tris[3 * t];
+    for (int k = 0; k < 3; ++k) {
+      int a = v[k], b = v[(k + 1) % 3], c = v[(k + 2) % 3];
+      if (a == b || b == c || a == c) {
+        *err = "create_cell_type: triangle with repeated vertex";
+        return NPFEM_ERR_BAD_MESH;
+      }
+      if (!directed.emplace(std::make_pair(a, b), c).second) {
+        *err = "create_cell_type: edge traversed twice in one direction (non-manifold or inconsistent orientation)";
+        return NPFEM_ERR_BAD_MESH;
+      }
+    }
+  }
+  for (auto& kv : directed) {
+    int a = kv.first.first, b = kv.first.second;
+    if (a < b) {
+      auto it = directed.find({b, a});
+      if (it == directed.end()) {
+        *err = "create_cell_type: open edge (mesh is not closed)";
+        return NPFEM_ERR_BAD_MESH;
+      }
+      H.hinges.insert(H.hinges.end(), {a, b, kv.second, it->second});
+    }
+  }
+  H.E = (int)H.hinges.size() / 4;
+  if (2 * H.E != 3 * T) {
+    *err = "create_cell_type: mesh is not a closed manifold";
+    return NPFEM_ERR_BAD_MESH;
+  }
+
+  // ---- per-triangle rest frame: Dm = [[|e1|, e2.u], [0, e2.w]], F = [e1 e2] Dm^-1
+  H.Dinv.resize(3 * T);
+  H.w_tri.resize(T);
+  std::vector<double> area(T);
+  std::vector<double> vert_area(n, 0.0);
+  double A0 = 0.0;
+  for (int t = 0; t < T; ++t) {
+    V3 x0 = X[tris[3 * t]], x1 = X[tris[3 * t + 1]], x2 = X[tris[3 * t + 2]];
+    V3 e1 = sub(x1, x0), e2 = sub(x2, x0);
+    V3 cr = cross(e1, e2);
+    double crn = norm(cr);
+    if (!(crn > 0.0)) {
+      *err = "create_cell_type: degenerate rest triangle";
+      return NPFEM_ERR_BAD_MESH;
+    }
+    double l1 = norm(e1);
+    double a01 = dot(e2, e1) / l1;  // e2 . u
+    double a11 = crn / l1;          // e2 . w  (w = n x u)
+    // inverse of [[l1, a01], [0, a11]]
+    H.Dinv[3 * t + 0] = 1.0 / l1;
+    H.Dinv[3 * t + 1] = -a01 / (l1 * a11);
+    H.Dinv[3 * t + 2] = 1.0 / a11;
+    area[t] = 0.5 * crn;
+    H.w_tri[t] = w_strain * area[t];
+    A0 += area[t];
+    for (int k = 0; k < 3; ++k) vert_area[tris[3 * t + k]] += area[t] / 3.0;
+  }
+  H.A0 = A0;
+  V3 ctr{0, 0, 0};
+  for (auto& p : X) ctr = {ctr.x + p.x / n, ctr.y + p.y / n, ctr.z + p.z / n};
+  double V0 = 0.0;
+  for (int t = 0; t < T; ++t) {
+    V3 a = sub(X[tris[3 * t]], ctr), b = sub(X[tris[3 * t + 1]], ctr), c = sub(X[tris[3 * t + 2]], ctr);
+    V0 += dot(a, cross(b, c)) / 6.0;
+  }
+  if (!(V0 > 0.0)) {
+    *err = "create_cell_type: non-positive rest volume (mesh must be oriented outward)";
+    return NPFEM_ERR_BAD_MESH;
+  }
+  H.V0 = V0;
+  H.mass.resize(n);
+  H.total_mass = density * V0;
+  for (int i = 0; i < n; ++i) H.mass[i] = density * V0 * vert_area[i] / A0;
+
+  // ---- hinges: cotangent stencil with rest cotangents, |K0|, weight
+  int E = H.E;
+  H.c_hinge.resize(4 * E);
+  H.K0.resize(4 * E);
+  H.w_hinge.resize(E);
+  for (int e = 0; e < E; ++e) {
+    const int* h = &H.hinges[4 * e];
+    V3 p0 = X[h[0]], p1 = X[h[1]], p2 = X[h[2]], p3 = X[h[3]];
+    double cA0 = cotangent(sub(p1, p0), sub(p2, p0));
+    double cA1 = cotangent(sub(p0, p1), sub(p2, p1));
+    double cB0 = cotangent(sub(p1, p0), sub(p3, p0));
+    double cB1 = cotangent(sub(p0, p1), sub(p3, p1));
+    double c[4] = {cA1 + cB1, cA0 + cB0, -(cA0 + cA1), -(cB0 + cB1)};
+    V3 K{0, 0, 0};
+    const V3 d[3] = {sub(p1, p0), sub(p2, p0), sub(p3, p0)};
+    for (int k = 0; k < 3; ++k) K = {K.x + c[k + 1] * d[k].x, K.y + c[k + 1] * d[k].y, K.z + c[k + 1] * d[k].z};
+    for (int k = 0; k < 4; ++k) H.c_hinge[4 * e + k] = c[k];
+    H.K0[4 * e + 0] = K.x;
+    H.K0[4 * e + 1] = K.y;
+    H.K0[4 * e + 2] = K.z;
+    H.K0[4 * e + 3] = norm(K);
+    double aA = 0.5 * norm(cross(sub(p1, p0), sub(p2, p0)));
+    double aB = 0.5 * norm(cross(sub(p1, p0), sub(p3, p0)));
+    H.w_hinge[e] = w_bend * 3.0 / (aA + aB);
+  }
+
+  // ---- gradient gather lists
+  {
+    std::vector<std::vector<std::pair<int32_t, double>>> inc(n);
+    for (int t = 0; t < T; ++t)
+      for (int k = 0; k < 3; ++k) inc[tris[3 * t + k]].push_back({t * 3 + k, 0.0});
+    for (int e = 0; e < E; ++e)
+      for (int k = 0; k < 4; ++k) inc[H.hinges[4 * e + k]].push_back({-(e * 4 + k) - 1, H.c_hinge[4 * e + k]});
+    H.inc_ptr.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+      H.inc_ptr[i + 1] = H.inc_ptr[i] + (int)inc[i].size();
+      for (auto& pr : inc[i]) {
+        H.inc_code.push_back(pr.first);
+        H.inc_coef.push_back(pr.second);
+      }
+    }
+  }
+
+  // ---- assemble A (sparse, symmetric)
+  std::map<std::pair<int, int>, double> Aij;
+  for (int i = 0; i < n; ++i) Aij[{i, i}] += H.mass[i] / (dt * dt);
+  for (int t = 0; t < T; ++t) {
+    // G = Dm^-T S, S = [[-1,1,0],[-1,0,1]];  Dm^-1 = [[d00, d01], [0, d11]]
+    double d00 = H.Dinv[3 * t], d01 = H.Dinv[3 * t + 1], d11 = H.Dinv[3 * t + 2];
+    double G[2][3] = {{-d00, d00, 0.0}, {-(d01 + d11), d01, d11}};
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double s = G[0][a] * G[0][b] + G[1][a] * G[1][b];
+        Aij[{tris[3 * t + a], tris[3 * t + b]}] += H.w_tri[t] * s;
+      }
+  }
+  for (int e = 0; e < E; ++e)
+    for (int a = 0; a < 4; ++a)
+      for (int b = 0; b < 4; ++b)
+        Aij[{H.hinges[4 * e + a], H.hinges[4 * e + b]}] +=
+            H.w_hinge[e] * H.c_hinge[4 * e + a] * H.c_hinge[4 * e + b];
+  Graph g(n);
+  for (auto& kv : Aij)
+    if (kv.first.first != kv.first.second) g[kv.first.first].push_back(kv.first.second);
+
+  // ---- ordering: best of geometric nested dissection and minimum degree
+  std::vector<int> best;
+  std::vector<std::vector<int>> best_cols;
+  int64_t best_nnz = -1;
+  {
+    std::vector<int> idx(n);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::vector<std::vector<int>> orders;
+    for (int leaf : {16, 32, 64}) {
+      std::vector<int> o;
+      nested_dissection(g, X, idx, &o, leaf);
+      orders.push_back(o);
+    }
+    if (n <= 12000) orders.push_back(minimum_degree(g));
+    for (auto& o : orders) {
+      std::vector<std::vector<int>> cols;
+      int64_t nz = symbolic(g, o, &cols);
+      if (best_nnz < 0 || nz < best_nnz) {
+        best_nnz = nz;
+        best = o;
+        best_cols = std::move(cols);
+      }
+    }
+  }
+  H.perm.assign(best.begin(), best.end());
+  H.nnz_factor = best_nnz;
+  std::vector<int> inv(n);
+  for (int i = 0; i < n; ++i) inv[best[i]] = i;
+
+  // ---- numeric left-looking Cholesky on the symbolic pattern
+  std::vector<std::vector<double>> Lval(n);
+  std::vector<double> Ldiag(n);
+  std::vector<std::vector<std::pair<int, int>>> rowlist(n);  // row r -> (col k, position in col k)
+  for (int j = 0; j < n; ++j)
+    for (size_t q = 0; q < best_cols[j].size(); ++q) rowlist[best_cols[j][q]].push_back({j, (int)q});
+  std::vector<double> work(n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    // scatter A(j:n, j) in permuted numbering
+    int vj = best[j];
+    work[j] = Aij[{vj, vj}];
+    for (int u : g[vj]) {
+      int r = inv[u];
+      if (r > j) work[r] = Aij[{u, vj}];
+    }
+    // subtract sum_k L(j:n,k) L(j,k) over k with L(j,k) != 0
+    for (auto& kq : rowlist[j]) {
+      int k = kq.first;
+      double ljk = Lval[k][kq.second];
+      work[j] -= ljk * ljk;
+      for (size_t q = kq.second + 1; q < best_cols[k].size(); ++q) work[best_cols[k][q]] -= Lval[k][q] * ljk;
+    }
+    double piv = work[j];
+    if (!(piv > 0.0) || !std::isfinite(piv)) {
+      char buf[160];
+      std::snprintf(buf, sizeof buf, "create_cell_type: global matrix not positive definite (pivot %g at %d)", piv, j);
+      *err = buf;
+      return NPFEM_ERR_NOT_SPD;
+    }
+    double d = std::sqrt(piv);
+    Ldiag[j] = d;
+    work[j] = 0.0;
+    Lval[j].resize(best_cols[j].size());
+    for (size_t q = 0; q < best_cols[j].size(); ++q) {
+      int r = best_cols[j][q];
+      Lval[j][q] = work[r] / d;
+      work[r] = 0.0;
+    }
+  }
+
+  // ---- LDL^T form: Lt(i,j) = L(i,j)/L(j,j), D = L(j,j)^2
+  H.dinv.resize(n);
+  for (int j = 0; j < n; ++j) {
+    H.dinv[j] = 1.0 / (Ldiag[j] * Ldiag[j]);
+    for (auto& v : Lval[j]) v /= Ldiag[j];
+  }
+  // forward (column j of Lt, rows > j) and backward (row j of Lt, cols < j) chunks
+  auto push_chunks = [&](int col, const std::vector<std::pair<int, double>>& ent, std::vector<int32_t>& ccol,
+                         std::vector<uint16_t>& crow, std::vector<double>& cval) {
+    for (size_t s = 0; s < ent.size(); s += kChunk) {
+      ccol.push_back(col);
+      for (int l = 0; l < kChunk; ++l) {
+        size_t q = s + l;
+        crow.push_back(q < ent.size() ? (uint16_t)ent[q].first : (uint16_t)n);
+        cval.push_back(q < ent.size() ? ent[q].second : 0.0);
+      }
+    }
+  };
+  for (int j = 0; j < n; ++j) {
+    std::vector<std::pair<int, double>> ent;
+    for (size_t q = 0; q < best_cols[j].size(); ++q) ent.push_back({best_cols[j][q], Lval[j][q]});
+    push_chunks(j, ent, H.fwd_col, H.fwd_row, H.fwd_val);
+  }
+  for (int j = n - 1; j >= 0; --j) {
+    std::vector<std::pair<int, double>> ent;
+    for (auto& kq : rowlist[j]) ent.push_back({kq.first, Lval[kq.first][kq.second]});
+    push_chunks(j, ent, H.bwd_col, H.bwd_row, H.bwd_val);
+  }
+  return NPFEM_OK;
+}
+
+}  // namespace npfem

@@ -1,0 +1,79 @@
+// Internal data structures of the npFEM library (host setup <-> CUDA kernels).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace npfem {
+
+constexpr int kHistory = 5;              // L-BFGS pairs kept (m)
+constexpr int kMaxHalvings = 20;         // line-search backtracking limit
+constexpr double kArmijoC1 = 1e-4;
+constexpr double kEnergyGuardEps = 1e-6; // approximate-Armijo energy guard (relative)
+constexpr double kCurvatureEps = 1e-12;  // keep pair only if s.y > eps |s||y|
+constexpr double kDegenerateDet = 1e-30; // det(F^T F) below this: triangle skipped
+constexpr double kDegenerateNorm = 1e-30;
+constexpr int kChunk = 32;               // entries per triangular-solve chunk (one per lane)
+
+// Host-side result of the per-type setup (all FP64; the device upload makes FP32
+// copies of the element constants for the FP32-form kernels).
+struct HostType {
+  int n = 0, T = 0, E = 0;
+  std::vector<int32_t> tris;     // [T][3]
+  std::vector<double> Dinv;      // [T][3] (d00, d01, d11) of the upper-triangular Dm^-1
+  std::vector<double> w_tri;     // [T]
+  std::vector<int32_t> hinges;   // [E][4] (i, j, kA, kB)
+  std::vector<double> c_hinge;   // [E][4]
+  std::vector<double> K0;        // [E][4] (K0x, K0y, K0z, |K0|)
+  std::vector<double> w_hinge;   // [E]
+  std::vector<double> mass;      // [n]
+  double A0 = 0, V0 = 0, w_area = 0, w_vol = 0, dt = 0, total_mass = 0;
+  // gradient gather: per vertex, corner codes (t*3+slot >= 0) and hinge codes
+  // (-(h*4+k)-1 < 0) with the hinge coefficient
+  std::vector<int32_t> inc_ptr;  // [n+1]
+  std::vector<int32_t> inc_code; // [nnz]
+  std::vector<double> inc_coef;  // [nnz]
+  // global solve: A = P^T Lt D Lt^T P with unit lower Lt; row r of the factor is vertex perm[r]
+  std::vector<int32_t> perm;     // [n]
+  std::vector<double> dinv;      // [n] 1/D
+  int64_t nnz_factor = 0;
+  // column-oriented chunk tables (32 entries each, padding row = n, value 0)
+  std::vector<int32_t> fwd_col, bwd_col;     // [nchunks]
+  std::vector<uint16_t> fwd_row, bwd_row;    // [nchunks*32]
+  std::vector<double> fwd_val, bwd_val;      // [nchunks*32]
+};
+
+// Build the host type.  Returns 0 or a negative NPFEM_ERR_* code with a message.
+int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double w_strain,
+                    double w_bend, double w_area, double w_vol, double density, double dt,
+                    HostType* out, std::string* err);
+
+// ------------------------------------------------------------------ device view
+template <typename S>
+struct DevTypeView {
+  int n, T, E;
+  int nchunks_fwd, nchunks_bwd;
+  const int32_t* tris;      // [T][3]
+  const S* Dinv;            // [T][3]
+  const S* w_tri;           // [T]
+  const int32_t* hinges;    // [E][4]
+  const S* c_hinge;         // [E][4]
+  const S* K0;              // [E][4]
+  const S* w_hinge;         // [E]
+  const S* mass;            // [n]
+  const S* inv_mass;        // [n]
+  const int32_t* inc_ptr;   // [n+1]
+  const int32_t* inc_code;  // [nnz]
+  const S* inc_coef;        // [nnz]
+  const int32_t* perm;      // [n]
+  const double* dinv;       // [n]
+  const int32_t* fwd_col;
+  const uint16_t* fwd_row;
+  const double* fwd_val;
+  const int32_t* bwd_col;
+  const uint16_t* bwd_row;
+  const double* bwd_val;
+  double A0, V0, w_area, w_vol, dt;
+};
+
+}  // namespace npfem

@@ -1,0 +1,568 @@
+// Device code of the npFEM batched step: one warp advances one cell by one time step.
+//
+// Per cell (npFEM solid step, Implementation and architecture section of the paper;
+// quasi-Newton projective dynamics of Liu et al. 2017 named there):
+//   K1  y = x_n + dt v_n + dt^2 M^-1 f_ext, x^(0) = y           (prediction, Eq. (2))
+//   K2  f(x) and grad f(x): per-triangle strain projections, per-hinge bending
+//       projections, global area/volume terms, inertia; gradient gathered per vertex
+//   K3  L-BFGS two-loop recursion, history 5
+//   K4  H0 = A^-1 by the per-type FP64 LDL^T factor: permute, unit-lower forward
+//       solve, diagonal scaling, unit-upper backward solve (3 right-hand sides)
+//   K5  backtracking line search (K2 at every trial point)
+//   K6  history update and FP64 residual / energy reductions
+//   K7  v_{n+1} = (x_{n+1} - x_n)/dt, write back
+//
+// Everything a warp needs for its cell lives in its workspace slot (global memory,
+// L1/L2 resident) except the FP64 solve vector, which sits in shared memory when it
+// fits.  All intra-cell synchronisation is warp-level (__syncwarp, shuffles).
+// Positions are handled as x = anchor + X + U where anchor is the cell's first input
+// vertex, X = x_n - anchor and U is the displacement of the step, so that FP32 work
+// never subtracts two large nearby coordinates.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "npfem_internal.h"
+
+namespace npfem {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+struct StepParams {
+  int ncells_list;             // cells handled by this launch
+  const int32_t* cell_list;    // [ncells_list] cell ids (batch order)
+  const int64_t* offsets;      // [ncells+1] vertex offsets
+  int64_t n_total;
+  const int32_t* iters;        // [ncells] or null
+  int iters_default;
+  double* residual_out;        // [ncells] or null
+  int32_t* status_out;         // [ncells] or null
+  double* alpha_log;           // [ncells][alpha_log_len] or null
+  int alpha_log_len;
+  int* queue_counter;          // work-queue head (zeroed before the launch)
+  char* scratch;               // workspace, slot_bytes per warp
+  size_t slot_bytes;
+  int z_in_smem;               // 1: FP64 solve vector in dynamic shared memory
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+template <typename S>
+__device__ __forceinline__ S warp_sum(S v);
+template <>
+__device__ __forceinline__ float warp_sum<float>(float v) { return warp_sum_f(v); }
+template <>
+__device__ __forceinline__ double warp_sum<double>(double v) { return warp_sum_d(v); }
+
+template <typename S>
+struct V3 {
+  S x, y, z;
+};
+template <typename S>
+__device__ __forceinline__ V3<S> ld3(const S* p, int i) {
+  return {p[3 * i], p[3 * i + 1], p[3 * i + 2]};
+}
+template <typename S>
+__device__ __forceinline__ void st3(S* p, int i, V3<S> v) {
+  p[3 * i] = v.x;
+  p[3 * i + 1] = v.y;
+  p[3 * i + 2] = v.z;
+}
+template <typename S>
+__device__ __forceinline__ V3<S> operator+(V3<S> a, V3<S> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename S>
+__device__ __forceinline__ V3<S> operator-(V3<S> a, V3<S> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename S>
+__device__ __forceinline__ V3<S> operator*(S s, V3<S> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <typename S>
+__device__ __forceinline__ V3<S> cross(V3<S> a, V3<S> b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename S>
+__device__ __forceinline__ S dot(V3<S> a, V3<S> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// Edge vector x_b - x_a from the rest-relative start positions X and displacement U.
+template <typename S>
+__device__ __forceinline__ V3<S> edge(const S* X, const S* U, int a, int b) {
+  return (ld3(X, b) - ld3(X, a)) + (ld3(U, b) - ld3(U, a));
+}
+
+// Per-cell workspace pointers (all arrays [n][3] of S unless noted).
+template <typename S>
+struct CellWs {
+  S *X, *W, *U, *UT, *G, *GT, *D, *Q;
+  S *hs, *hy;      // [m][3n]
+  S *corner;       // [T][3][3] per-corner gradient of the triangle terms
+  S *hbuf;         // [E][3] w_e (K - p)
+  double* z;       // [n+1][3] FP64 solve vector (row n = padding sink)
+};
+
+template <typename S>
+__device__ __forceinline__ size_t slot_bytes_for(int n, int T, int E, bool z_in_smem) {
+  size_t v = (size_t)3 * n;
+  size_t bytes = sizeof(S) * ((8 + 2 * kHistory) * v + 9 * (size_t)T + 3 * (size_t)E);
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (!z_in_smem) bytes += sizeof(double) * 3 * ((size_t)n + 1);
+  return (bytes + 255) & ~(size_t)255;
+}
+
+template <typename S>
+__device__ __forceinline__ CellWs<S> carve(char* base, int n, int T, int E, double* zsmem) {
+  CellWs<S> w;
+  size_t v = (size_t)3 * n;
+  S* p = reinterpret_cast<S*>(base);
+  w.X = p; p += v;
+  w.W = p; p += v;
+  w.U = p; p += v;
+  w.UT = p; p += v;
+  w.G = p; p += v;
+  w.GT = p; p += v;
+  w.D = p; p += v;
+  w.Q = p; p += v;
+  w.hs = p; p += kHistory * v;
+  w.hy = p; p += kHistory * v;
+  w.corner = p; p += 9 * (size_t)T;
+  w.hbuf = p; p += 3 * (size_t)E;
+  if (zsmem) {
+    w.z = zsmem;
+  } else {
+    size_t off = reinterpret_cast<char*>(p) - base;
+    off = (off + 255) & ~(size_t)255;
+    w.z = reinterpret_cast<double*>(base + off);
+  }
+  return w;
+}
+
+// ------------------------------------------------------------------ K2
+struct EvalOut {
+  double energy;
+  bool degenerate;
+};
+
+// f(X+U) and its gradient into Gout.  W = y - x_n.  The strain projection maps the
+// triangle deformation gradient F = [e1 e2] Dm^-1 to R = F (F^T F)^(-1/2) via the
+// closed-form 2x2 SPD square root (C + sqrt(det C) I)/sqrt(tr C + 2 sqrt(det C)).
+template <typename S>
+__device__ EvalOut eval_objective(const DevTypeView<S>& ty, const CellWs<S>& w, const S* U, S* Gout,
+                                  V3<S> cvol, int lane) {
+  const int n = ty.n, T = ty.T, E = ty.E;
+  const S* X = w.X;
+  // pass A: global area and volume (FP64 reductions)
+  double a_sum = 0.0, v_sum = 0.0;
+  for (int t = lane; t < T; t += 32) {
+    int i0 = __ldg(&ty.tris[3 * t]), i1 = __ldg(&ty.tris[3 * t + 1]), i2 = __ldg(&ty.tris[3 * t + 2]);
+    V3<S> e1 = edge(X, U, i0, i1), e2 = edge(X, U, i0, i2);
+    V3<S> N = cross(e1, e2);
+    a_sum += (double)sqrt(dot(N, N));
+    V3<S> q0 = (ld3(X, i0) + ld3(U, i0)) - cvol;
+    v_sum += (double)dot(q0, N);
+  }
+  const double A = 0.5 * warp_sum_d(a_sum);
+  const double V = warp_sum_d(v_sum) / 6.0;
+  const double dA = A - ty.A0, dV = V - ty.V0;
+  const double e_area = 0.5 * ty.w_area * dA * dA / ty.A0;
+  const double e_vol = 0.5 * ty.w_vol * dV * dV / ty.V0;
+  const S kA = (S)(ty.w_area * dA / ty.A0);
+  const S kV = (S)(ty.w_vol * dV / ty.V0);
+  const S half = (S)0.5, sixth = (S)(1.0 / 6.0);
+
+  // pass B: triangles (strain projection + area/volume corner gradients)
+  double e_strain = 0.0;
+  bool degen = false;
+  for (int t = lane; t < T; t += 32) {
+    int i0 = __ldg(&ty.tris[3 * t]), i1 = __ldg(&ty.tris[3 * t + 1]), i2 = __ldg(&ty.tris[3 * t + 2]);
+    V3<S> e1 = edge(X, U, i0, i1), e2 = edge(X, U, i0, i2);
+    const S d00 = __ldg(&ty.Dinv[3 * t]), d01 = __ldg(&ty.Dinv[3 * t + 1]), d11 = __ldg(&ty.Dinv[3 * t + 2]);
+    const S wt = __ldg(&ty.w_tri[t]);
+    V3<S> F0 = d00 * e1;
+    V3<S> F1 = d01 * e1 + d11 * e2;
+    S c00 = dot(F0, F0), c01 = dot(F0, F1), c11 = dot(F1, F1);
+    S det = c00 * c11 - c01 * c01;
+    V3<S> P0{0, 0, 0}, P1{0, 0, 0};
+    if ((double)det > kDegenerateDet) {
+      S s = sqrt(det);
+      S tau = sqrt(c00 + c11 + (S)2 * s);
+      S s00 = (c00 + s) / tau, s01 = c01 / tau, s11 = (c11 + s) / tau;
+      S idet = (S)1 / (s00 * s11 - s01 * s01);
+      // R = F S^-1, S^-1 = [[s11, -s01], [-s01, s00]] / det S
+      V3<S> R0 = idet * (s11 * F0 - s01 * F1);
+      V3<S> R1 = idet * (s00 * F1 - s01 * F0);
+      V3<S> D0 = F0 - R0, D1 = F1 - R1;
+      e_strain += (double)(half * wt * (dot(D0, D0) + dot(D1, D1)));
+      P0 = wt * D0;
+      P1 = wt * D1;
+    } else {
+      degen = true;
+    }
+    // strain: dE/de1 = P0 d00 + P1 d01, dE/de2 = P1 d11
+    V3<S> g1 = d00 * P0 + d01 * P1;
+    V3<S> g2 = d11 * P1;
+    V3<S> g0 = (S)-1 * (g1 + g2);
+    // area: dA_t/dx_k = n/2 x (x_{k+2} - x_{k+1})
+    V3<S> N = cross(e1, e2);
+    S nn = sqrt(dot(N, N));
+    if (nn > (S)0) {
+      V3<S> nh = ((S)1 / nn) * N;
+      g0 = g0 + (kA * half) * cross(nh, e2 - e1);
+      g1 = g1 + (kA * half) * cross(nh, (S)-1 * e2);
+      g2 = g2 + (kA * half) * cross(nh, e1);
+    }
+    // volume: dV_t/dq0 = q1 x q2 / 6 (cyclic), q = x - cvol
+    V3<S> q0 = (ld3(X, i0) + ld3(U, i0)) - cvol;
+    V3<S> q1 = q0 + e1, q2 = q0 + e2;
+    g0 = g0 + (kV * sixth) * cross(q1, q2);
+    g1 = g1 + (kV * sixth) * cross(q2, q0);
+    g2 = g2 + (kV * sixth) * cross(q0, q1);
+    st3(w.corner, 3 * t + 0, g0);
+    st3(w.corner, 3 * t + 1, g1);
+    st3(w.corner, 3 * t + 2, g2);
+  }
+
+  // pass C: hinges (bending projection onto |K| = |K0|)
+  double e_bend = 0.0;
+  for (int h = lane; h < E; h += 32) {
+    int i = __ldg(&ty.hinges[4 * h]), j = __ldg(&ty.hinges[4 * h + 1]);
+    int ka = __ldg(&ty.hinges[4 * h + 2]), kb = __ldg(&ty.hinges[4 * h + 3]);
+    const S c1 = __ldg(&ty.c_hinge[4 * h + 1]), c2 = __ldg(&ty.c_hinge[4 * h + 2]), c3 = __ldg(&ty.c_hinge[4 * h + 3]);
+    V3<S> K = c1 * edge(X, U, i, j) + c2 * edge(X, U, i, ka) + c3 * edge(X, U, i, kb);
+    S kn = sqrt(dot(K, K));
+    V3<S> p;
+    if ((double)kn < kDegenerateNorm) {
+      p = {__ldg(&ty.K0[4 * h]), __ldg(&ty.K0[4 * h + 1]), __ldg(&ty.K0[4 * h + 2])};
+    } else {
+      p = (__ldg(&ty.K0[4 * h + 3]) / kn) * K;
+    }
+    V3<S> r = K - p;
+    const S we = __ldg(&ty.w_hinge[h]);
+    e_bend += (double)(half * we * dot(r, r));
+    st3(w.hbuf, h, we * r);
+  }
+  __syncwarp();
+
+  // pass D: vertices (inertia + gather of element contributions)
+  const S idt2 = (S)(1.0 / (ty.dt * ty.dt));
+  double e_inertia = 0.0;
+  for (int v = lane; v < n; v += 32) {
+    V3<S> du = ld3(U, v) - ld3(w.W, v);
+    const S m = __ldg(&ty.mass[v]);
+    e_inertia += (double)(half * m * idt2 * dot(du, du));
+    V3<S> g = (m * idt2) * du;
+    const int e0 = __ldg(&ty.inc_ptr[v]), e1 = __ldg(&ty.inc_ptr[v + 1]);
+    for (int e = e0; e < e1; ++e) {
+      int code = __ldg(&ty.inc_code[e]);
+      if (code >= 0) {
+        g = g + ld3(w.corner, code);
+      } else {
+        int h = (-code - 1) >> 2;
+        g = g + __ldg(&ty.inc_coef[e]) * ld3(w.hbuf, h);
+      }
+    }
+    st3(Gout, v, g);
+  }
+  double e_el = warp_sum_d(e_strain + e_bend + e_inertia);
+  EvalOut o;
+  o.energy = e_el + e_area + e_vol;
+  o.degenerate = __any_sync(kFull, degen);
+  __syncwarp();
+  return o;
+}
+
+// ------------------------------------------------------------------ vector helpers
+template <typename S>
+__device__ __forceinline__ S vdot(const S* a, const S* b, int len, int lane) {
+  S s = 0;
+  for (int i = lane; i < len; i += 32) s += a[i] * b[i];
+  return warp_sum<S>(s);
+}
+template <typename S>
+__device__ __forceinline__ double vdot64(const S* a, const S* b, int len, int lane) {
+  double s = 0;
+  for (int i = lane; i < len; i += 32) s += (double)a[i] * (double)b[i];
+  return warp_sum_d(s);
+}
+
+// ------------------------------------------------------------------ K4
+// R = A^-1 Q for the three coordinates (Q and R may alias).  FP64 throughout.
+template <typename S>
+__device__ void global_solve(const DevTypeView<S>& ty, double* z, const S* Q, S* R, int lane) {
+  const int n = ty.n;
+  for (int r = lane; r < n; r += 32) {
+    int v = __ldg(&ty.perm[r]);
+    z[3 * r] = (double)Q[3 * v];
+    z[3 * r + 1] = (double)Q[3 * v + 1];
+    z[3 * r + 2] = (double)Q[3 * v + 2];
+  }
+  if (lane < 3) z[3 * n + lane] = 0.0;
+  __syncwarp();
+  // forward: unit lower Lt, column-oriented, one chunk of 32 entries per step
+  {
+    const int nc = ty.nchunks_fwd;
+    int ch = 0;
+    int j_cur = nc > 0 ? __ldg(&ty.fwd_col[0]) : 0;
+    int row_cur = nc > 0 ? __ldg(&ty.fwd_row[lane]) : n;
+    double val_cur = nc > 0 ? __ldg(&ty.fwd_val[lane]) : 0.0;
+    for (; ch < nc; ++ch) {
+      int j_nx = 0, row_nx = n;
+      double val_nx = 0.0;
+      if (ch + 1 < nc) {
+        j_nx = __ldg(&ty.fwd_col[ch + 1]);
+        row_nx = __ldg(&ty.fwd_row[(size_t)(ch + 1) * kChunk + lane]);
+        val_nx = __ldg(&ty.fwd_val[(size_t)(ch + 1) * kChunk + lane]);
+      }
+      const double x0 = z[3 * j_cur], x1 = z[3 * j_cur + 1], x2 = z[3 * j_cur + 2];
+      double* zr = z + 3 * row_cur;
+      double a0 = zr[0], a1 = zr[1], a2 = zr[2];
+      a0 = fma(-val_cur, x0, a0);
+      a1 = fma(-val_cur, x1, a1);
+      a2 = fma(-val_cur, x2, a2);
+      zr[0] = a0;
+      zr[1] = a1;
+      zr[2] = a2;
+      __syncwarp();
+      j_cur = j_nx;
+      row_cur = row_nx;
+      val_cur = val_nx;
+    }
+  }
+  for (int r = lane; r < n; r += 32) {
+    double d = __ldg(&ty.dinv[r]);
+    z[3 * r] *= d;
+    z[3 * r + 1] *= d;
+    z[3 * r + 2] *= d;
+  }
+  __syncwarp();
+  // backward: unit upper Lt^T, columns in descending order
+  {
+    const int nc = ty.nchunks_bwd;
+    int j_cur = nc > 0 ? __ldg(&ty.bwd_col[0]) : 0;
+    int row_cur = nc > 0 ? __ldg(&ty.bwd_row[lane]) : n;
+    double val_cur = nc > 0 ? __ldg(&ty.bwd_val[lane]) : 0.0;
+    for (int ch = 0; ch < nc; ++ch) {
+      int j_nx = 0, row_nx = n;
+      double val_nx = 0.0;
+      if (ch + 1 < nc) {
+        j_nx = __ldg(&ty.bwd_col[ch + 1]);
+        row_nx = __ldg(&ty.bwd_row[(size_t)(ch + 1) * kChunk + lane]);
+        val_nx = __ldg(&ty.bwd_val[(size_t)(ch + 1) * kChunk + lane]);
+      }
+      const double x0 = z[3 * j_cur], x1 = z[3 * j_cur + 1], x2 = z[3 * j_cur + 2];
+      double* zr = z + 3 * row_cur;
+      double a0 = zr[0], a1 = zr[1], a2 = zr[2];
+      a0 = fma(-val_cur, x0, a0);
+      a1 = fma(-val_cur, x1, a1);
+      a2 = fma(-val_cur, x2, a2);
+      zr[0] = a0;
+      zr[1] = a1;
+      zr[2] = a2;
+      __syncwarp();
+      j_cur = j_nx;
+      row_cur = row_nx;
+      val_cur = val_nx;
+    }
+  }
+  for (int r = lane; r < n; r += 32) {
+    int v = __ldg(&ty.perm[r]);
+    R[3 * v] = (S)z[3 * r];
+    R[3 * v + 1] = (S)z[3 * r + 1];
+    R[3 * v + 2] = (S)z[3 * r + 2];
+  }
+  __syncwarp();
+}
+
+// ------------------------------------------------------------------ one cell
+template <typename S>
+__device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, const CellWs<S>& w, int cell,
+                             S* x, S* v, const S* f, int lane) {
+  const int n = ty.n;
+  const int len = 3 * n;
+  const int64_t off = P.offsets[cell];
+  const int64_t Nt = P.n_total;
+  const int iters = P.iters ? P.iters[cell] : P.iters_default;
+  const double dt = ty.dt;
+  const S sdt = (S)dt, sdt2 = (S)(dt * dt);
+
+  // K1: anchor, X = x_n - anchor, W = y - x_n, U = W
+  const S ax = x[off], ay = x[Nt + off], az = x[2 * Nt + off];
+  double cx = 0, cy = 0, cz = 0;
+  for (int k = lane; k < n; k += 32) {
+    S px = x[off + k] - ax, py = x[Nt + off + k] - ay, pz = x[2 * Nt + off + k] - az;
+    w.X[3 * k] = px;
+    w.X[3 * k + 1] = py;
+    w.X[3 * k + 2] = pz;
+    cx += (double)px;
+    cy += (double)py;
+    cz += (double)pz;
+    const S im = __ldg(&ty.inv_mass[k]);
+    S wx = sdt * v[off + k] + sdt2 * f[off + k] * im;
+    S wy = sdt * v[Nt + off + k] + sdt2 * f[Nt + off + k] * im;
+    S wz = sdt * v[2 * Nt + off + k] + sdt2 * f[2 * Nt + off + k] * im;
+    w.W[3 * k] = wx;
+    w.W[3 * k + 1] = wy;
+    w.W[3 * k + 2] = wz;
+    w.U[3 * k] = wx;
+    w.U[3 * k + 1] = wy;
+    w.U[3 * k + 2] = wz;
+  }
+  V3<S> cvol{(S)(warp_sum_d(cx) / n), (S)(warp_sum_d(cy) / n), (S)(warp_sum_d(cz) / n)};
+  __syncwarp();
+
+  S* U = w.U;
+  S* UT = w.UT;
+  S* G = w.G;
+  S* GT = w.GT;
+  EvalOut ev = eval_objective<S>(ty, w, U, G, cvol, lane);
+  double fx = ev.energy;
+  bool degen = ev.degenerate;
+  const double g0n = sqrt(vdot64<S>(G, G, len, lane));
+  int status = 0;
+  int hcount = 0, hhead = 0;
+  S rho[kHistory], aco[kHistory];
+#pragma unroll
+  for (int i = 0; i < kHistory; ++i) rho[i] = aco[i] = 0;
+
+  for (int k = 0; k < iters; ++k) {
+    // K3 first loop: Q = G; newest -> oldest
+    for (int i = lane; i < len; i += 32) w.Q[i] = G[i];
+    __syncwarp();
+    for (int q = 0; q < hcount; ++q) {
+      int i = (hhead - 1 - q + kHistory) % kHistory;
+      const S* si = w.hs + (size_t)i * len;
+      const S* yi = w.hy + (size_t)i * len;
+      S a = rho[i] * vdot<S>(si, w.Q, len, lane);
+      aco[i] = a;
+      for (int e = lane; e < len; e += 32) w.Q[e] -= a * yi[e];
+      __syncwarp();
+    }
+    // K4: r = H0 q
+    global_solve<S>(ty, w.z, w.Q, w.Q, lane);
+    // K3 second loop: oldest -> newest
+    for (int q = hcount - 1; q >= 0; --q) {
+      int i = (hhead - 1 - q + kHistory) % kHistory;
+      const S* si = w.hs + (size_t)i * len;
+      const S* yi = w.hy + (size_t)i * len;
+      S b = rho[i] * vdot<S>(yi, w.Q, len, lane);
+      S c = aco[i] - b;
+      for (int e = lane; e < len; e += 32) w.Q[e] += c * si[e];
+      __syncwarp();
+    }
+    for (int e = lane; e < len; e += 32) w.D[e] = -w.Q[e];
+    __syncwarp();
+    double gd = vdot64<S>(G, w.D, len, lane);
+    if (!(gd < 0.0)) {  // not a descent direction: drop history, plain PD step
+      hcount = 0;
+      hhead = 0;
+      global_solve<S>(ty, w.z, G, w.Q, lane);
+      for (int e = lane; e < len; e += 32) w.D[e] = -w.Q[e];
+      __syncwarp();
+      gd = vdot64<S>(G, w.D, len, lane);
+    }
+    // K5: backtracking line search
+    double alpha = 1.0, ft = 0.0;
+    for (int h = 0; h <= kMaxHalvings; ++h) {
+      const S sa = (S)alpha;
+      for (int e = lane; e < len; e += 32) UT[e] = U[e] + sa * w.D[e];
+      __syncwarp();
+      EvalOut et = eval_objective<S>(ty, w, UT, GT, cvol, lane);
+      ft = et.energy;
+      degen = degen || et.degenerate;
+      double gtd = vdot64<S>(GT, w.D, len, lane);
+      bool armijo = ft <= fx + kArmijoC1 * alpha * gd;
+      bool approx = (gtd <= (2.0 * kArmijoC1 - 1.0) * gd) && (ft <= fx + kEnergyGuardEps * fabs(fx));
+      if (armijo || approx) break;
+      if (h == kMaxHalvings) {
+        status |= 1;
+        break;
+      }
+      alpha *= 0.5;
+    }
+    // K6: history pair (s, y) = (UT - U, GT - G) into the ring slot hhead
+    if (k < iters - 1) {
+      S* si = w.hs + (size_t)hhead * len;
+      S* yi = w.hy + (size_t)hhead * len;
+      double sy = 0, ss = 0, yy = 0;
+      for (int e = lane; e < len; e += 32) {
+        S s = UT[e] - U[e];
+        S y = GT[e] - G[e];
+        si[e] = s;
+        yi[e] = y;
+        sy += (double)s * (double)y;
+        ss += (double)s * (double)s;
+        yy += (double)y * (double)y;
+      }
+      sy = warp_sum_d(sy);
+      ss = warp_sum_d(ss);
+      yy = warp_sum_d(yy);
+      if (sy > kCurvatureEps * sqrt(ss) * sqrt(yy)) {
+        rho[hhead] = (S)(1.0 / sy);
+        hhead = (hhead + 1) % kHistory;
+        hcount = hcount < kHistory ? hcount + 1 : kHistory;
+      }
+      __syncwarp();
+    }
+    if (P.alpha_log && k < P.alpha_log_len && lane == 0) P.alpha_log[(size_t)cell * P.alpha_log_len + k] = alpha;
+    // accept
+    S* t1 = U;
+    U = UT;
+    UT = t1;
+    S* t2 = G;
+    G = GT;
+    GT = t2;
+    fx = ft;
+  }
+
+  // K7: residual, write x_{n+1} = anchor + X + U and v_{n+1} = U / dt
+  const double gn = sqrt(vdot64<S>(G, G, len, lane));
+  const S idt = (S)(1.0 / dt);
+  bool bad = false;
+  for (int k = lane; k < n; k += 32) {
+    double nx = (double)ax + ((double)w.X[3 * k] + (double)U[3 * k]);
+    double ny = (double)ay + ((double)w.X[3 * k + 1] + (double)U[3 * k + 1]);
+    double nz = (double)az + ((double)w.X[3 * k + 2] + (double)U[3 * k + 2]);
+    S vx = U[3 * k] * idt, vy = U[3 * k + 1] * idt, vz = U[3 * k + 2] * idt;
+    x[off + k] = (S)nx;
+    x[Nt + off + k] = (S)ny;
+    x[2 * Nt + off + k] = (S)nz;
+    v[off + k] = vx;
+    v[Nt + off + k] = vy;
+    v[2 * Nt + off + k] = vz;
+    bad = bad || !isfinite(nx) || !isfinite(ny) || !isfinite(nz) || !isfinite((double)vx) ||
+          !isfinite((double)vy) || !isfinite((double)vz);
+  }
+  bad = __any_sync(kFull, bad);
+  if (lane == 0) {
+    if (degen) status |= 2;
+    if (bad) status |= 4;
+    if (P.status_out) P.status_out[cell] = status;
+    if (P.residual_out) P.residual_out[cell] = g0n > 0.0 ? gn / g0n : 0.0;
+  }
+  __syncwarp();
+}
+
+// Persistent kernel: each warp owns one workspace slot and pops cells from the queue.
+template <typename S>
+__global__ void __launch_bounds__(128) npfem_step_kernel(DevTypeView<S> ty, StepParams P, S* x, S* v,
+                                                          const S* f) {
+  extern __shared__ double smem_z[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
+  double* zs = P.z_in_smem ? smem_z + (size_t)wib * 3 * (ty.n + 1) : nullptr;
+  CellWs<S> w = carve<S>(P.scratch + (size_t)slot * P.slot_bytes, ty.n, ty.T, ty.E, zs);
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(P.queue_counter, 1);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= P.ncells_list) break;
+    process_cell<S>(ty, P, w, P.cell_list[item], x, v, f, lane);
+  }
+}
+
+}  // namespace npfem

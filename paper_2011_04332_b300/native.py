@@ -1,0 +1,188 @@
+"""Thin ctypes binding of the C ABI in include/npfem.h (argument marshalling only).
+
+Every step of the hot path runs in libnpfem.so; this module only converts Python
+objects (numpy meshes, torch device tensors) into plain pointers and sizes.  It
+raises if the shared library is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libnpfem.so")
+
+FP64 = 0
+FP32FORM = 1
+
+CELL_LINESEARCH_FAIL = 1
+CELL_DEGENERATE = 2
+CELL_NONFINITE = 4
+
+ERRORS = {-1: "INVALID_ARG", -2: "BAD_MESH", -3: "NOT_SPD", -4: "CUDA", -5: "OOM", -6: "UNSUPPORTED"}
+
+
+class NpfemError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"npfem error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class _Mesh(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("n_tris", C.c_int32),
+                ("rest_xyz", C.POINTER(C.c_double)), ("tris", C.POINTER(C.c_int32))]
+
+
+class _Material(C.Structure):
+    _fields_ = [("w_strain", C.c_double), ("w_bend", C.c_double), ("w_area", C.c_double),
+                ("w_vol", C.c_double), ("density", C.c_double)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("alpha_log_len", C.c_int32), ("alpha_log", C.c_void_p)]
+
+
+class _TypeInfo(C.Structure):
+    _fields_ = [("n_verts", C.c_int32), ("n_tris", C.c_int32), ("n_hinges", C.c_int32),
+                ("nnz_factor", C.c_int64), ("solve_chunks", C.c_int64),
+                ("rest_area", C.c_double), ("rest_volume", C.c_double), ("total_mass", C.c_double)]
+
+
+_lib = None
+
+
+def load_library() -> C.CDLL:
+    """Load libnpfem.so (built in-tree by paper_2011_04332_b300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libnpfem.so not built at {LIB_PATH}: run paper_2011_04332_b300/build.py")
+    lib = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    sig = {
+        "npfem_create_cell_type": [C.POINTER(_Mesh), C.POINTER(_Material), C.c_double, C.POINTER(vp)],
+        "npfem_destroy_cell_type": [vp],
+        "npfem_cell_type_info": [vp, C.POINTER(_TypeInfo)],
+        "npfem_cell_type_analyze": [C.POINTER(_Mesh), C.POINTER(_Material), C.c_double, C.POINTER(_TypeInfo)],
+        "npfem_batch_create": [C.POINTER(vp), C.c_int32, C.POINTER(C.c_int32), C.c_int32, C.c_int,
+                               C.POINTER(vp)],
+        "npfem_batch_destroy": [vp],
+        "npfem_batch_layout": [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
+        "npfem_step": [vp, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp],
+        "npfem_step_host": [vp, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp],
+        "npfem_last_error_string": [C.c_char_p, C.c_size_t],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        buf = C.create_string_buffer(512)
+        _lib.npfem_last_error_string(buf, 512)
+        raise NpfemError(rc, buf.value.decode())
+
+
+def _ptr(t) -> Optional[int]:
+    """Device/host pointer of a torch tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous()
+    return t.data_ptr()
+
+
+def analyze_cell_type(verts: np.ndarray, tris: np.ndarray, material: Sequence[float], dt: float) -> dict:
+    """npfem_cell_type_analyze: host-only validation + factorisation statistics (no GPU)."""
+    lib = load_library()
+    xyz = np.ascontiguousarray(verts, dtype=np.float64)
+    tr = np.ascontiguousarray(tris, dtype=np.int32)
+    m = _Mesh(xyz.shape[0], tr.shape[0], xyz.ctypes.data_as(C.POINTER(C.c_double)),
+              tr.ctypes.data_as(C.POINTER(C.c_int32)))
+    mat = _Material(*[float(a) for a in material])
+    inf = _TypeInfo()
+    _check(lib.npfem_cell_type_analyze(C.byref(m), C.byref(mat), float(dt), C.byref(inf)))
+    return {k: getattr(inf, k) for k, _ in _TypeInfo._fields_}
+
+
+class CellType:
+    """A prefactored cell type: npfem_create_cell_type(mesh, material, dt)."""
+
+    def __init__(self, verts: np.ndarray, tris: np.ndarray, material: Sequence[float], dt: float):
+        lib = load_library()
+        self._xyz = np.ascontiguousarray(verts, dtype=np.float64)
+        self._tris = np.ascontiguousarray(tris, dtype=np.int32)
+        m = _Mesh(self._xyz.shape[0], self._tris.shape[0],
+                  self._xyz.ctypes.data_as(C.POINTER(C.c_double)),
+                  self._tris.ctypes.data_as(C.POINTER(C.c_int32)))
+        mat = _Material(*[float(a) for a in material])
+        h = C.c_void_p()
+        _check(lib.npfem_create_cell_type(C.byref(m), C.byref(mat), float(dt), C.byref(h)))
+        self.handle = h
+        self.dt = float(dt)
+
+    def info(self) -> dict:
+        inf = _TypeInfo()
+        _check(_lib.npfem_cell_type_info(self.handle, C.byref(inf)))
+        return {k: getattr(inf, k) for k, _ in _TypeInfo._fields_}
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.npfem_destroy_cell_type(self.handle)
+            self.handle = None
+
+
+class Batch:
+    """npfem_batch_create(types, type_of_cell, precision)."""
+
+    def __init__(self, types: Sequence[CellType], type_of_cell, precision: int = FP64):
+        lib = load_library()
+        self.types = list(types)
+        arr = (C.c_void_p * len(self.types))(*[t.handle.value for t in self.types])
+        toc = np.ascontiguousarray(type_of_cell, dtype=np.int32)
+        h = C.c_void_p()
+        _check(lib.npfem_batch_create(arr, len(self.types), toc.ctypes.data_as(C.POINTER(C.c_int32)),
+                                      int(toc.shape[0]), int(precision), C.byref(h)))
+        self.handle = h
+        self.ncells = int(toc.shape[0])
+        self.precision = precision
+        nt = C.c_int64()
+        offs = np.zeros(self.ncells + 1, dtype=np.int64)
+        _check(lib.npfem_batch_layout(h, C.byref(nt), offs.ctypes.data_as(C.POINTER(C.c_int64))))
+        self.n_total = int(nt.value)
+        self.offsets = offs
+
+    def step(self, x, v, f, iters=None, iters_default: int = 5, residual=None, status=None,
+             alpha_log=None, stream=None):
+        """npfem_step on device tensors (torch); asynchronous on `stream` (torch stream or int)."""
+        opts = _Opts(int(iters_default), 0 if alpha_log is None else int(alpha_log.shape[-1]),
+                     _ptr(alpha_log))
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        elif not isinstance(stream, int):
+            stream = stream.cuda_stream
+        _check(_lib.npfem_step(self.handle, _ptr(x), _ptr(v), _ptr(f), _ptr(iters), C.byref(opts),
+                               _ptr(residual), _ptr(status), C.c_void_p(stream)))
+
+    def step_host(self, x: np.ndarray, v: np.ndarray, f: np.ndarray, iters=None, iters_default: int = 5,
+                  residual=None, status=None, stream: int = 0):
+        """npfem_step_host on host arrays (copies in, steps, copies out; synchronous)."""
+        opts = _Opts(int(iters_default), 0, None)
+        _check(_lib.npfem_step_host(self.handle, _ptr(x), _ptr(v), _ptr(f), _ptr(iters), C.byref(opts),
+                                    _ptr(residual), _ptr(status), C.c_void_p(stream)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.npfem_batch_destroy(self.handle)
+            self.handle = None

@@ -1,0 +1,106 @@
+"""CPU checks of the C ABI: the library builds and loads, exports every function the
+header declares, and the host-side type setup validates meshes and materials."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2011_04332_b300 import build, inputs as I, native
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+           if f.endswith(".h")]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return native.load_library()
+
+
+def declared_functions():
+    names = set()
+    for h in HEADERS:
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"^\s*npfem_status\s+(npfem_\w+)\s*\(", src, flags=re.M))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("npfem_create_cell_type", "npfem_destroy_cell_type", "npfem_batch_create",
+                     "npfem_step", "npfem_step_host", "npfem_last_error_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    cdll = ctypes.CDLL(native.LIB_PATH)
+    for name in declared_functions():
+        assert hasattr(cdll, name), f"{name} declared in include/ but not exported"
+
+
+def test_analyze_reports_factor_statistics(lib):
+    m = I.rbc_mesh(3)
+    info = native.analyze_cell_type(m.verts, m.tris, I.RBC_MATERIAL.as_tuple(), I.DT_DEFAULT)
+    assert info["n_verts"] == 642 and info["n_tris"] == 1280 and info["n_hinges"] == 1920
+    # a fill-reducing ordering keeps the factor far below the dense n(n-1)/2
+    assert 0 < info["nnz_factor"] < 0.2 * 642 * 641 / 2
+    assert info["total_mass"] == pytest.approx(1.1 * info["rest_volume"], rel=1e-12)
+
+
+def test_analyze_matches_oracle_rest_quantities(lib):
+    from oracle import npfem_oracle as O
+    for m in (I.tetrahedron(), I.icosahedron(), I.platelet_mesh(1), I.rbc_mesh(2)):
+        info = native.analyze_cell_type(m.verts, m.tris, I.RBC_MATERIAL.as_tuple(), 0.1)
+        rs = O.rest_state(m.verts, m.tris, *I.RBC_MATERIAL.as_tuple(), 0.1)
+        assert info["rest_area"] == pytest.approx(rs.A0, rel=1e-13)
+        assert info["rest_volume"] == pytest.approx(rs.V0, rel=1e-13)
+        assert info["n_hinges"] == rs.hinges.shape[0]
+
+
+def _expect(code, fn):
+    with pytest.raises(native.NpfemError) as ei:
+        fn()
+    assert ei.value.code == code, str(ei.value)
+
+
+def test_bad_meshes_are_rejected(lib):
+    m = I.icosahedron()
+    mat = I.RBC_MATERIAL.as_tuple()
+    # open mesh: drop a triangle
+    _expect(-2, lambda: native.analyze_cell_type(m.verts, m.tris[:-1], mat, 0.1))
+    # inconsistent orientation: flip one triangle
+    t = m.tris.copy()
+    t[0] = t[0][[0, 2, 1]]
+    _expect(-2, lambda: native.analyze_cell_type(m.verts, t, mat, 0.1))
+    # index out of range
+    t = m.tris.copy()
+    t[3, 1] = 99
+    _expect(-2, lambda: native.analyze_cell_type(m.verts, t, mat, 0.1))
+    # degenerate rest triangle (two coincident vertices)
+    v = m.verts.copy()
+    v[m.tris[0, 1]] = v[m.tris[0, 0]]
+    _expect(-2, lambda: native.analyze_cell_type(v, m.tris, mat, 0.1))
+    # inward orientation: negative volume
+    _expect(-2, lambda: native.analyze_cell_type(m.verts, m.tris[:, [0, 2, 1]], mat, 0.1))
+
+
+def test_invalid_arguments_are_rejected(lib):
+    m = I.icosahedron()
+    _expect(-1, lambda: native.analyze_cell_type(m.verts, m.tris, I.RBC_MATERIAL.as_tuple(), -1.0))
+    _expect(-1, lambda: native.analyze_cell_type(m.verts, m.tris, (1, .05, 10, 10, 0.0), 0.1))
+
+
+def test_non_spd_material_is_rejected(lib):
+    m = I.rbc_mesh(2)
+    _expect(-3, lambda: native.analyze_cell_type(m.verts, m.tris, (-50.0, 0.05, 10, 10, 1.1), 10.0))
+
+
+def test_last_error_string_is_set(lib):
+    try:
+        native.analyze_cell_type(I.icosahedron().verts, I.icosahedron().tris[:-1], (1, 1, 1, 1, 1), 0.1)
+    except native.NpfemError as e:
+        assert "open edge" in str(e) or "closed" in str(e)

@@ -1,0 +1,224 @@
+"""GPU parity: the CUDA step (through the C ABI) against the FP64 CPU oracle, one step
+from identical inputs, element by element on vertex positions and velocities.
+
+Bars (error per cell = max_j |x_j - x_j^ref|_inf / max_j |x_j^ref - centroid^ref|):
+  FP64 form        <= 1e-10
+  FP32 form        <= 1e-5   (FP32 local work, FP64 factor/solves/reductions)
+The accepted line-search step lengths are integers in disguise (a count of halvings)
+and are compared exactly in the FP64 form.
+"""
+import numpy as np
+import pytest
+
+from oracle import npfem_oracle as O
+from paper_2011_04332_b300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_BAR = 1e-10
+FP32_BAR = 1e-5
+
+
+def _native():
+    from paper_2011_04332_b300 import native
+    return native
+
+
+class Runner:
+    """Builds library types/batch for a BatchInputs and steps it on the GPU."""
+
+    def __init__(self, b: I.BatchInputs, precision: int):
+        nat = _native()
+        self.b = b
+        self.prec = precision
+        self.types = [nat.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
+        self.batch = nat.Batch(self.types, b.type_of_cell, precision)
+        assert self.batch.n_total == b.n_total
+        assert np.array_equal(self.batch.offsets, b.offsets)
+        self.dtype = torch.float64 if precision == nat.FP64 else torch.float32
+
+    def step(self, x, v, f, iters=None, alpha_len=8, iters_default=5):
+        dev = torch.device("cuda:0")
+        X = torch.tensor(x, dtype=self.dtype, device=dev).contiguous()
+        Vt = torch.tensor(v, dtype=self.dtype, device=dev).contiguous()
+        F = torch.tensor(f, dtype=self.dtype, device=dev).contiguous()
+        it = None if iters is None else torch.tensor(np.asarray(iters, np.int32), device=dev)
+        nc = self.b.ncells
+        res = torch.full((max(nc, 1),), -1.0, dtype=torch.float64, device=dev)
+        st = torch.full((max(nc, 1),), -1, dtype=torch.int32, device=dev)
+        al = torch.zeros((max(nc, 1), alpha_len), dtype=torch.float64, device=dev)
+        self.batch.step(X, Vt, F, iters=it, iters_default=iters_default, residual=res, status=st, alpha_log=al)
+        torch.cuda.synchronize()
+        return (X.double().cpu().numpy(), Vt.double().cpu().numpy(), res.cpu().numpy()[:nc],
+                st.cpu().numpy()[:nc], al.cpu().numpy()[:nc])
+
+
+def oracle_types(b: I.BatchInputs):
+    return [O.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
+
+
+def cell_errors(b, x, xref, radius_from=None):
+    """Per-cell max-norm error divided by the cell radius (of `radius_from`, default xref)."""
+    errs = []
+    rf = xref if radius_from is None else radius_from
+    for c in range(b.ncells):
+        s = b.cell_slice(c)
+        xr = rf[:, s]
+        rad = np.max(np.linalg.norm(xr - xr.mean(axis=1, keepdims=True), axis=0))
+        errs.append(np.max(np.abs(x[:, s] - xref[:, s])) / rad)
+    return np.array(errs)
+
+
+def compare(b, precision, cells=None, steps=1, iters=None, check_alpha=True, bar=None):
+    nat = _native()
+    r = Runner(b, precision)
+    ots = oracle_types(b)
+    x, v, f = b.x.copy(), b.v.copy(), b.f.copy()
+    if precision == nat.FP32FORM:
+        x, v, f = (a.astype(np.float32).astype(np.float64) for a in (x, v, f))
+    iters = b.iters if iters is None else iters
+    bar = bar if bar is not None else (FP64_BAR if precision == nat.FP64 else FP32_BAR)
+    worst = 0.0
+    for s in range(steps):
+        xg, vg, res, st, al = r.step(x, v, f, iters=iters)
+        ref = O.batch_step(ots, b.type_of_cell, b.offsets, x, v, f, iters, cells=cells)
+        sel = list(range(b.ncells)) if cells is None else list(cells)
+        e = cell_errors(b, xg, ref["x"])[sel]
+        ev = cell_errors(b, vg * b.dt, ref["v"] * b.dt, radius_from=ref["x"])[sel]
+        worst = max(worst, float(e.max()), float(ev.max()))
+        assert e.max() <= bar, f"step {s}: position error {e.max():.3e} > {bar}"
+        assert ev.max() <= bar, f"step {s}: velocity*dt error {ev.max():.3e} > {bar}"
+        for c in sel:
+            assert st[c] == ref["status"][c]
+            if check_alpha and precision == nat.FP64:
+                n_it = int(iters[c])
+                assert np.array_equal(al[c, :min(n_it, al.shape[1])], np.array(ref["alphas"][c][:al.shape[1]]))
+            if precision == nat.FP64:
+                assert res[c] == pytest.approx(ref["residual"][c], rel=1e-4, abs=1e-8)
+        # next step from the oracle's state so that both sides see identical inputs
+        x, v = ref["x"], ref["v"]
+        if precision == nat.FP32FORM:
+            x, v = (a.astype(np.float32).astype(np.float64) for a in (x, v))
+    return worst
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_single_rbc_parity(prec):
+    """Single 642-vertex Evans-Fung RBC, axial 10 pN stretch + 0.1 pN noise, 5 iterations,
+    three consecutive steps (each from the oracle's previous state)."""
+    nat = _native()
+    b = I.single_rbc()
+    compare(b, nat.FP64 if prec == "fp64" else nat.FP32FORM, steps=3)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_small_mixed_batch_parity(prec):
+    """Three small types (42-vertex RBC, 42-vertex platelet, 162-vertex RBC), ragged
+    per-cell iteration counts, non-zero initial velocities."""
+    nat = _native()
+    b = I.small_mixed_batch()
+    compare(b, nat.FP64 if prec == "fp64" else nat.FP32FORM, steps=2)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_homogeneous_batch_parity(prec):
+    """48 placed 642-vertex RBCs (random rotation, translation in a 200 um box,
+    Gaussian + linear-shear forces): more cells than warps per block, ragged tail."""
+    nat = _native()
+    b = I.homogeneous_rbc_batch(ncells=48, seed=1001, velocity_sigma=0.02)
+    compare(b, nat.FP64 if prec == "fp64" else nat.FP32FORM)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_batch_sampled_cells(prec):
+    """The 4096-cell homogeneous workload in the benchmark's launch configuration;
+    16 sampled cells are checked against the oracle."""
+    nat = _native()
+    b = I.homogeneous_rbc_batch(ncells=4096, seed=1001)
+    cells = sorted(np.random.default_rng(5).choice(4096, size=16, replace=False).tolist())
+    compare(b, nat.FP64 if prec == "fp64" else nat.FP32FORM, cells=cells)
+
+
+def test_heterogeneous_types_and_iterations():
+    nat = _native()
+    b = I.heterogeneous_batch(n_rbc3=6, n_rbc4=3, n_plt=5, seed=1002)
+    compare(b, nat.FP64)
+    compare(b, nat.FP32FORM)
+
+
+def test_zero_iterations_returns_prediction():
+    nat = _native()
+    b = I.small_mixed_batch()
+    iters = np.zeros(b.ncells, np.int32)
+    r = Runner(b, nat.FP64)
+    xg, vg, res, st, _ = r.step(b.x, b.v, b.f, iters=iters)
+    mass = [O.rest_state(t.mesh.verts, t.mesh.tris, *t.material.as_tuple(), b.dt).mass for t in b.types]
+    for c in range(b.ncells):
+        s = b.cell_slice(c)
+        m = mass[b.type_of_cell[c]]
+        y = b.x[:, s] + b.dt * b.v[:, s] + b.dt ** 2 * b.f[:, s] / m[None, :]
+        assert np.allclose(xg[:, s], y, rtol=0, atol=1e-12)
+        assert res[c] == 1.0 or np.isclose(res[c], 1.0)
+
+
+def test_rest_state_stays_at_rest():
+    nat = _native()
+    b = I.homogeneous_rbc_batch(ncells=8, seed=3)
+    for prec in (nat.FP64, nat.FP32FORM):
+        r = Runner(b, prec)
+        x = b.x if prec == nat.FP64 else b.x.astype(np.float32).astype(np.float64)
+        xg, vg, res, st, _ = r.step(x, np.zeros_like(x), np.zeros_like(x))
+        tol = 1e-12 if prec == nat.FP64 else 2e-5
+        assert np.max(np.abs(xg - x)) <= tol * 200
+        assert np.all(st == 0)
+
+
+def test_nonfinite_force_sets_status_only_for_that_cell():
+    nat = _native()
+    b = I.homogeneous_rbc_batch(ncells=6, seed=4)
+    f = b.f.copy()
+    s = b.cell_slice(2)
+    f[0, s.start + 5] = np.nan
+    r = Runner(b, nat.FP64)
+    xg, vg, res, st, _ = r.step(b.x, b.v, f)
+    assert st[2] & nat.CELL_NONFINITE
+    assert all(st[c] == 0 for c in range(6) if c != 2)
+    assert np.all(np.isfinite(xg[:, b.cell_slice(0)]))
+
+
+def test_host_buffer_step_matches_device_step():
+    nat = _native()
+    b = I.homogeneous_rbc_batch(ncells=10, seed=6)
+    r = Runner(b, nat.FP64)
+    xg, vg, res, st, _ = r.step(b.x, b.v, b.f, iters=b.iters)
+    xh, vh, fh = b.x.copy(), b.v.copy(), b.f.copy()
+    rh = np.zeros(b.ncells)
+    sh = np.zeros(b.ncells, np.int32)
+    r.batch.step_host(xh, vh, fh, iters=np.ascontiguousarray(b.iters), residual=rh, status=sh)
+    assert np.array_equal(xh, xg) and np.array_equal(vh, vg)
+    assert np.array_equal(rh, res) and np.array_equal(sh, st)
+
+
+def test_empty_batch_is_a_no_op():
+    nat = _native()
+    t = nat.CellType(I.icosahedron().verts, I.icosahedron().tris, I.RBC_MATERIAL.as_tuple(), 0.1)
+    bt = nat.Batch([t], np.zeros(0, np.int32), nat.FP64)
+    x = torch.zeros(3, 0, dtype=torch.float64, device="cuda")
+    bt.step(x, x.clone(), x.clone())
+    torch.cuda.synchronize()
+
+
+def test_rollout_tracks_oracle():
+    """20 steps of the single RBC on both sides from the same start (informational bar)."""
+    nat = _native()
+    b = I.single_rbc()
+    r = Runner(b, nat.FP64)
+    ots = oracle_types(b)
+    x, v = b.x.copy(), b.v.copy()
+    xo, vo = b.x.copy(), b.v.copy()
+    for s in range(20):
+        x, v, *_ = r.step(x, v, b.f, iters=b.iters)
+        ref = O.batch_step(ots, b.type_of_cell, b.offsets, xo, vo, b.f, b.iters)
+        xo, vo = ref["x"], ref["v"]
+    assert cell_errors(b, x, xo).max() < 1e-8
