@@ -302,10 +302,10 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
     L.type_index = ti;
     L.ncells = (int)list.size();
     L.warps_per_block = 4;
-    const int blocks_per_sm = 2;
-    L.blocks = std::min<int>(sms * blocks_per_sm, (L.ncells + L.warps_per_block - 1) / L.warps_per_block);
     size_t zbytes = sizeof(double) * 3 * ((size_t)H.n + 1);
-    L.z_in_smem = (zbytes * L.warps_per_block <= 100 * 1024) ? 1 : 0;
+    L.z_in_smem = (zbytes * L.warps_per_block <= 72 * 1024) ? 1 : 0;
+    const int blocks_per_sm = 3;
+    L.blocks = std::min<int>(sms * blocks_per_sm, (L.ncells + L.warps_per_block - 1) / L.warps_per_block);
     L.smem_bytes = L.z_in_smem ? zbytes * L.warps_per_block : 0;
     size_t v = (size_t)3 * H.n;
     size_t bytes = ssize * ((8 + 2 * kHistory) * v + 9 * (size_t)H.T + 3 * (size_t)H.E);

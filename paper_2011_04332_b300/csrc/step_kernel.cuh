@@ -62,6 +62,38 @@ __device__ __forceinline__ float warp_sum<float>(float v) { return warp_sum_f(v)
 template <>
 __device__ __forceinline__ double warp_sum<double>(double v) { return warp_sum_d(v); }
 
+// Per-lane accumulator for sums that are reduced in FP64 across the warp.  For FP32
+// terms it keeps an unevaluated (hi, lo) pair updated with error-free transformations
+// (TwoSum; TwoProd through fmaf), so a lane's partial sum carries ~48 significant bits
+// on the FP32 pipe; the lane totals are then combined in FP64.  For FP64 terms it is a
+// plain double.
+template <typename S>
+struct Acc;
+template <>
+struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double total() const { return warp_sum_d(s); }
+};
+template <>
+struct Acc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float t = hi + x;
+    float bb = t - hi;
+    lo += (hi - (t - bb)) + (x - bb);
+    hi = t;
+  }
+  __device__ __forceinline__ void add_prod(float a, float b) {
+    float p = a * b;
+    float e = fmaf(a, b, -p);
+    add(p);
+    lo += e;
+  }
+  __device__ __forceinline__ double total() const { return warp_sum_d((double)hi + (double)lo); }
+};
+
 template <typename S>
 struct V3 {
   S x, y, z;
@@ -156,17 +188,17 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const CellWs<S>& w, 
   const int n = ty.n, T = ty.T, E = ty.E;
   const S* X = w.X;
   // pass A: global area and volume (FP64 reductions)
-  double a_sum = 0.0, v_sum = 0.0;
+  Acc<S> a_sum, v_sum;
   for (int t = lane; t < T; t += 32) {
     int i0 = __ldg(&ty.tris[3 * t]), i1 = __ldg(&ty.tris[3 * t + 1]), i2 = __ldg(&ty.tris[3 * t + 2]);
     V3<S> e1 = edge(X, U, i0, i1), e2 = edge(X, U, i0, i2);
     V3<S> N = cross(e1, e2);
-    a_sum += (double)sqrt(dot(N, N));
+    a_sum.add(sqrt(dot(N, N)));
     V3<S> q0 = (ld3(X, i0) + ld3(U, i0)) - cvol;
-    v_sum += (double)dot(q0, N);
+    v_sum.add(dot(q0, N));
   }
-  const double A = 0.5 * warp_sum_d(a_sum);
-  const double V = warp_sum_d(v_sum) / 6.0;
+  const double A = 0.5 * a_sum.total();
+  const double V = v_sum.total() / 6.0;
   const double dA = A - ty.A0, dV = V - ty.V0;
   const double e_area = 0.5 * ty.w_area * dA * dA / ty.A0;
   const double e_vol = 0.5 * ty.w_vol * dV * dV / ty.V0;
@@ -175,7 +207,7 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const CellWs<S>& w, 
   const S half = (S)0.5, sixth = (S)(1.0 / 6.0);
 
   // pass B: triangles (strain projection + area/volume corner gradients)
-  double e_strain = 0.0;
+  Acc<S> e_el;
   bool degen = false;
   for (int t = lane; t < T; t += 32) {
     int i0 = __ldg(&ty.tris[3 * t]), i1 = __ldg(&ty.tris[3 * t + 1]), i2 = __ldg(&ty.tris[3 * t + 2]);
@@ -196,7 +228,7 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const CellWs<S>& w, 
       V3<S> R0 = idet * (s11 * F0 - s01 * F1);
       V3<S> R1 = idet * (s00 * F1 - s01 * F0);
       V3<S> D0 = F0 - R0, D1 = F1 - R1;
-      e_strain += (double)(half * wt * (dot(D0, D0) + dot(D1, D1)));
+      e_el.add(half * wt * (dot(D0, D0) + dot(D1, D1)));
       P0 = wt * D0;
       P1 = wt * D1;
     } else {
@@ -227,7 +259,6 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const CellWs<S>& w, 
   }
 
   // pass C: hinges (bending projection onto |K| = |K0|)
-  double e_bend = 0.0;
   for (int h = lane; h < E; h += 32) {
     int i = __ldg(&ty.hinges[4 * h]), j = __ldg(&ty.hinges[4 * h + 1]);
     int ka = __ldg(&ty.hinges[4 * h + 2]), kb = __ldg(&ty.hinges[4 * h + 3]);
@@ -242,18 +273,17 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const CellWs<S>& w, 
     }
     V3<S> r = K - p;
     const S we = __ldg(&ty.w_hinge[h]);
-    e_bend += (double)(half * we * dot(r, r));
+    e_el.add(half * we * dot(r, r));
     st3(w.hbuf, h, we * r);
   }
   __syncwarp();
 
   // pass D: vertices (inertia + gather of element contributions)
   const S idt2 = (S)(1.0 / (ty.dt * ty.dt));
-  double e_inertia = 0.0;
   for (int v = lane; v < n; v += 32) {
     V3<S> du = ld3(U, v) - ld3(w.W, v);
     const S m = __ldg(&ty.mass[v]);
-    e_inertia += (double)(half * m * idt2 * dot(du, du));
+    e_el.add(half * m * idt2 * dot(du, du));
     V3<S> g = (m * idt2) * du;
     const int e0 = __ldg(&ty.inc_ptr[v]), e1 = __ldg(&ty.inc_ptr[v + 1]);
     for (int e = e0; e < e1; ++e) {
@@ -267,9 +297,8 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const CellWs<S>& w, 
     }
     st3(Gout, v, g);
   }
-  double e_el = warp_sum_d(e_strain + e_bend + e_inertia);
   EvalOut o;
-  o.energy = e_el + e_area + e_vol;
+  o.energy = e_el.total() + e_area + e_vol;
   o.degenerate = __any_sync(kFull, degen);
   __syncwarp();
   return o;
@@ -284,13 +313,69 @@ __device__ __forceinline__ S vdot(const S* a, const S* b, int len, int lane) {
 }
 template <typename S>
 __device__ __forceinline__ double vdot64(const S* a, const S* b, int len, int lane) {
-  double s = 0;
-  for (int i = lane; i < len; i += 32) s += (double)a[i] * (double)b[i];
-  return warp_sum_d(s);
+  Acc<S> s;
+  for (int i = lane; i < len; i += 32) s.add_prod(a[i], b[i]);
+  return s.total();
 }
 
 // ------------------------------------------------------------------ K4
-// R = A^-1 Q for the three coordinates (Q and R may alias).  FP64 throughout.
+// One sweep of column-oriented updates z[row] -= l * z[col] over 32-entry chunks, the
+// chunk tables prefetched kPrefetch chunks ahead in registers (the tables stream from
+// L2).  Consecutive chunks of one column touch distinct rows and never write z[col],
+// so the warp only synchronises where the column changes.
+constexpr int kPrefetch = 8;
+
+__device__ __forceinline__ void chunk_sweep(int nc, const int32_t* __restrict__ col,
+                                            const uint16_t* __restrict__ row, const double* __restrict__ val,
+                                            double* z, int n, int lane) {
+  int jb[kPrefetch], rb[kPrefetch];
+  double vb[kPrefetch];
+#pragma unroll
+  for (int k = 0; k < kPrefetch; ++k) {
+    if (k < nc) {
+      jb[k] = __ldg(col + k);
+      rb[k] = __ldg(row + (size_t)k * kChunk + lane);
+      vb[k] = __ldg(val + (size_t)k * kChunk + lane);
+    } else {
+      jb[k] = -1;
+      rb[k] = n;
+      vb[k] = 0.0;
+    }
+  }
+  for (int base = 0; base < nc; base += kPrefetch) {
+#pragma unroll
+    for (int k = 0; k < kPrefetch; ++k) {
+      const int ch = base + k;
+      if (ch < nc) {
+        const int j = jb[k], r = rb[k];
+        const double l = vb[k];
+        const int nx = ch + kPrefetch;
+        if (nx < nc) {
+          jb[k] = __ldg(col + nx);
+          rb[k] = __ldg(row + (size_t)nx * kChunk + lane);
+          vb[k] = __ldg(val + (size_t)nx * kChunk + lane);
+        } else {
+          jb[k] = -1;
+        }
+        const double x0 = z[3 * j], x1 = z[3 * j + 1], x2 = z[3 * j + 2];
+        double* zr = z + 3 * r;
+        const double a0 = fma(-l, x0, zr[0]);
+        const double a1 = fma(-l, x1, zr[1]);
+        const double a2 = fma(-l, x2, zr[2]);
+        zr[0] = a0;
+        zr[1] = a1;
+        zr[2] = a2;
+        // next chunk's column (ring slot k+1; slot k already holds chunk ch+kPrefetch)
+        const int jn = jb[(k + 1) % kPrefetch];
+        if (jn != j) __syncwarp();
+      }
+    }
+  }
+  __syncwarp();
+}
+
+// R = A^-1 Q for the three coordinates (Q and R may alias).  FP64 throughout:
+// permute, unit-lower forward sweep, D^-1 scaling, unit-upper backward sweep.
 template <typename S>
 __device__ void global_solve(const DevTypeView<S>& ty, double* z, const S* Q, S* R, int lane) {
   const int n = ty.n;
@@ -302,36 +387,7 @@ __device__ void global_solve(const DevTypeView<S>& ty, double* z, const S* Q, S*
   }
   if (lane < 3) z[3 * n + lane] = 0.0;
   __syncwarp();
-  // forward: unit lower Lt, column-oriented, one chunk of 32 entries per step
-  {
-    const int nc = ty.nchunks_fwd;
-    int ch = 0;
-    int j_cur = nc > 0 ? __ldg(&ty.fwd_col[0]) : 0;
-    int row_cur = nc > 0 ? __ldg(&ty.fwd_row[lane]) : n;
-    double val_cur = nc > 0 ? __ldg(&ty.fwd_val[lane]) : 0.0;
-    for (; ch < nc; ++ch) {
-      int j_nx = 0, row_nx = n;
-      double val_nx = 0.0;
-      if (ch + 1 < nc) {
-        j_nx = __ldg(&ty.fwd_col[ch + 1]);
-        row_nx = __ldg(&ty.fwd_row[(size_t)(ch + 1) * kChunk + lane]);
-        val_nx = __ldg(&ty.fwd_val[(size_t)(ch + 1) * kChunk + lane]);
-      }
-      const double x0 = z[3 * j_cur], x1 = z[3 * j_cur + 1], x2 = z[3 * j_cur + 2];
-      double* zr = z + 3 * row_cur;
-      double a0 = zr[0], a1 = zr[1], a2 = zr[2];
-      a0 = fma(-val_cur, x0, a0);
-      a1 = fma(-val_cur, x1, a1);
-      a2 = fma(-val_cur, x2, a2);
-      zr[0] = a0;
-      zr[1] = a1;
-      zr[2] = a2;
-      __syncwarp();
-      j_cur = j_nx;
-      row_cur = row_nx;
-      val_cur = val_nx;
-    }
-  }
+  chunk_sweep(ty.nchunks_fwd, ty.fwd_col, ty.fwd_row, ty.fwd_val, z, n, lane);
   for (int r = lane; r < n; r += 32) {
     double d = __ldg(&ty.dinv[r]);
     z[3 * r] *= d;
@@ -339,35 +395,7 @@ __device__ void global_solve(const DevTypeView<S>& ty, double* z, const S* Q, S*
     z[3 * r + 2] *= d;
   }
   __syncwarp();
-  // backward: unit upper Lt^T, columns in descending order
-  {
-    const int nc = ty.nchunks_bwd;
-    int j_cur = nc > 0 ? __ldg(&ty.bwd_col[0]) : 0;
-    int row_cur = nc > 0 ? __ldg(&ty.bwd_row[lane]) : n;
-    double val_cur = nc > 0 ? __ldg(&ty.bwd_val[lane]) : 0.0;
-    for (int ch = 0; ch < nc; ++ch) {
-      int j_nx = 0, row_nx = n;
-      double val_nx = 0.0;
-      if (ch + 1 < nc) {
-        j_nx = __ldg(&ty.bwd_col[ch + 1]);
-        row_nx = __ldg(&ty.bwd_row[(size_t)(ch + 1) * kChunk + lane]);
-        val_nx = __ldg(&ty.bwd_val[(size_t)(ch + 1) * kChunk + lane]);
-      }
-      const double x0 = z[3 * j_cur], x1 = z[3 * j_cur + 1], x2 = z[3 * j_cur + 2];
-      double* zr = z + 3 * row_cur;
-      double a0 = zr[0], a1 = zr[1], a2 = zr[2];
-      a0 = fma(-val_cur, x0, a0);
-      a1 = fma(-val_cur, x1, a1);
-      a2 = fma(-val_cur, x2, a2);
-      zr[0] = a0;
-      zr[1] = a1;
-      zr[2] = a2;
-      __syncwarp();
-      j_cur = j_nx;
-      row_cur = row_nx;
-      val_cur = val_nx;
-    }
-  }
+  chunk_sweep(ty.nchunks_bwd, ty.bwd_col, ty.bwd_row, ty.bwd_val, z, n, lane);
   for (int r = lane; r < n; r += 32) {
     int v = __ldg(&ty.perm[r]);
     R[3 * v] = (S)z[3 * r];
@@ -391,15 +419,15 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
 
   // K1: anchor, X = x_n - anchor, W = y - x_n, U = W
   const S ax = x[off], ay = x[Nt + off], az = x[2 * Nt + off];
-  double cx = 0, cy = 0, cz = 0;
+  Acc<S> cx, cy, cz;
   for (int k = lane; k < n; k += 32) {
     S px = x[off + k] - ax, py = x[Nt + off + k] - ay, pz = x[2 * Nt + off + k] - az;
     w.X[3 * k] = px;
     w.X[3 * k + 1] = py;
     w.X[3 * k + 2] = pz;
-    cx += (double)px;
-    cy += (double)py;
-    cz += (double)pz;
+    cx.add(px);
+    cy.add(py);
+    cz.add(pz);
     const S im = __ldg(&ty.inv_mass[k]);
     S wx = sdt * v[off + k] + sdt2 * f[off + k] * im;
     S wy = sdt * v[Nt + off + k] + sdt2 * f[Nt + off + k] * im;
@@ -411,7 +439,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
     w.U[3 * k + 1] = wy;
     w.U[3 * k + 2] = wz;
   }
-  V3<S> cvol{(S)(warp_sum_d(cx) / n), (S)(warp_sum_d(cy) / n), (S)(warp_sum_d(cz) / n)};
+  V3<S> cvol{(S)(cx.total() / n), (S)(cy.total() / n), (S)(cz.total() / n)};
   __syncwarp();
 
   S* U = w.U;
@@ -487,19 +515,17 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
     if (k < iters - 1) {
       S* si = w.hs + (size_t)hhead * len;
       S* yi = w.hy + (size_t)hhead * len;
-      double sy = 0, ss = 0, yy = 0;
+      Acc<S> asy, ass, ayy;
       for (int e = lane; e < len; e += 32) {
         S s = UT[e] - U[e];
         S y = GT[e] - G[e];
         si[e] = s;
         yi[e] = y;
-        sy += (double)s * (double)y;
-        ss += (double)s * (double)s;
-        yy += (double)y * (double)y;
+        asy.add_prod(s, y);
+        ass.add_prod(s, s);
+        ayy.add_prod(y, y);
       }
-      sy = warp_sum_d(sy);
-      ss = warp_sum_d(ss);
-      yy = warp_sum_d(yy);
+      const double sy = asy.total(), ss = ass.total(), yy = ayy.total();
       if (sy > kCurvatureEps * sqrt(ss) * sqrt(yy)) {
         rho[hhead] = (S)(1.0 / sy);
         hhead = (hhead + 1) % kHistory;
