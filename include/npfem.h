@@ -151,6 +151,26 @@ npfem_status npfem_step_host(npfem_batch* batch, void* x, void* v, const void* f
                              const int32_t* iters, const npfem_solver_opts* opts,
                              double* residual_out, int32_t* status_out, void* stream);
 
+/* Allocation-free step for callers that must not allocate device memory: code
+ * running inside a framework whose pool owns all device memory, code called while a
+ * stream is being captured, or tools with a device-memory budget fixed at start-up.
+ * The paper has no counterpart; this is a library convenience.
+ * Steps `ncells` cells of one type laid out back to back (cell i owns vertices
+ * [i*n, (i+1)*n) of x, v, f_ext, each [3][ncells*n], same element types and
+ * meaning as npfem_step).  It allocates nothing: its workspace is a 32 MiB static
+ * device array reserved on every GPU that loads the library, held until exit.
+ * Limits: ncells <= 65536, and the type's per-warp workspace must fit four warps
+ * in the array (otherwise NPFEM_ERR_UNSUPPORTED with the sizes in the message).
+ * The first call on a device looks up the array's device address and sets the
+ * kernels' shared-memory limit; make that first call before any stream capture.
+ * Every call reuses the same array (the work-queue counter is cleared on each call),
+ * so calls whose GPU work overlaps (two streams, or two threads) race and must be
+ * serialised by the caller.  Asynchronous on `stream`. */
+npfem_status npfem_step_noalloc(const npfem_cell_type* type, npfem_precision prec, int32_t ncells,
+                                void* x, void* v, const void* f_ext, const int32_t* iters,
+                                const npfem_solver_opts* opts, double* residual_out,
+                                int32_t* status_out, void* stream);
+
 /* Message of the last error returned on the calling thread (empty if none). */
 npfem_status npfem_last_error_string(char* buf, size_t len);
 

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libnpfem.so")
 PROBE_LIB = os.path.join(HERE, "libnpfem_probe.so")
-SOURCES = ["api.cu", "host_setup.cpp"]
+SOURCES = ["api.cu", "noalloc.cu", "host_setup.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

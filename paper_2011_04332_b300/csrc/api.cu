@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/npfem.h"
+#include "api_internal.h"
 #include "npfem_internal.h"
 #include "step_kernel.cuh"
 
@@ -29,43 +30,11 @@ npfem_status fail(npfem_status code, const std::string& msg) {
                   std::string(#expr) + ": " + cudaGetErrorString(e_));                    \
   } while (0)
 
-// Device allocation list owned by a type or batch.
-struct DevAllocs {
-  std::vector<void*> ptrs;
-  ~DevAllocs() {
-    for (void* p : ptrs) cudaFree(p);
-  }
-  template <typename T>
-  cudaError_t upload(const std::vector<T>& h, const T** out) {
-    void* d = nullptr;
-    size_t bytes = std::max<size_t>(1, h.size()) * sizeof(T);
-    cudaError_t e = cudaMalloc(&d, bytes);
-    if (e != cudaSuccess) return e;
-    ptrs.push_back(d);
-    if (!h.empty()) e = cudaMemcpy(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
-    *out = static_cast<const T*>(d);
-    return e;
-  }
-  cudaError_t alloc(size_t bytes, void** out) {
-    cudaError_t e = cudaMalloc(out, std::max<size_t>(bytes, 16));
-    if (e == cudaSuccess) ptrs.push_back(*out);
-    return e;
-  }
-};
-
 template <typename D, typename S>
 std::vector<D> convert(const std::vector<S>& s) {
   return std::vector<D>(s.begin(), s.end());
 }
 }  // namespace
-
-struct npfem_cell_type {
-  HostType host;
-  DevAllocs mem;
-  DevTypeView<double> v64;
-  DevTypeView<float> v32;
-  int device = 0;
-};
 
 struct TypeLaunch {
   int type_index;
@@ -161,6 +130,8 @@ static cudaError_t upload_precision(npfem_cell_type* t, DevTypeView<S>* view, co
                dinv, fcol, frow, fval, bcol, brow, bval);
   return cudaSuccess;
 }
+
+npfem_status npfem_internal_fail(npfem_status code, const std::string& msg) { return fail(code, msg); }
 
 extern "C" {
 

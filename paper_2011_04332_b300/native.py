@@ -75,6 +75,7 @@ def load_library() -> C.CDLL:
         "npfem_step": [vp, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp],
         "npfem_step_host": [vp, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp],
         "npfem_last_error_string": [C.c_char_p, C.c_size_t],
+        "npfem_step_noalloc": [vp, C.c_int, C.c_int32, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -140,6 +141,21 @@ class CellType:
         if getattr(self, "handle", None) and _lib is not None:
             _lib.npfem_destroy_cell_type(self.handle)
             self.handle = None
+
+
+def step_noalloc(cell_type: "CellType", precision: int, ncells: int, x, v, f, iters=None,
+                 iters_default: int = 5, residual=None, status=None, alpha_log=None, stream=None):
+    """npfem_step_noalloc: step `ncells` back-to-back cells of one type without any
+    device allocation (static library workspace); device tensors as for Batch.step."""
+    opts = _Opts(int(iters_default), 0 if alpha_log is None else int(alpha_log.shape[-1]), _ptr(alpha_log))
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    elif not isinstance(stream, int):
+        stream = stream.cuda_stream
+    _check(_lib.npfem_step_noalloc(cell_type.handle, int(precision), int(ncells), _ptr(x), _ptr(v), _ptr(f),
+                                   _ptr(iters), C.byref(opts), _ptr(residual), _ptr(status),
+                                   C.c_void_p(stream)))
 
 
 class Batch:
