@@ -143,6 +143,13 @@ npfem_status npfem_step(npfem_batch* batch, void* x, void* v, const void* f_ext,
                         const int32_t* iters, const npfem_solver_opts* opts,
                         double* residual_out, int32_t* status_out, void* stream);
 
+/* Per-phase telemetry of the batch's steps since creation or the last reset: SM
+ * clock cycles summed over all warps, in the order prediction, objective evaluation,
+ * two-loop recursion, global FP64 solve, history update, write-back, and (contained
+ * in the objective) the area/volume pass and the gradient gather.  Synchronises the
+ * device.  cycles: host array of 8; reset != 0 zeroes the counters after reading. */
+npfem_status npfem_batch_phase_cycles(npfem_batch* batch, uint64_t* cycles, int32_t reset);
+
 /* Same step with HOST arrays (pageable or pinned): copies x, v, f_ext (and iters,
  * when given) to batch-owned device buffers, runs npfem_step, and copies x, v,
  * residuals and statuses back; synchronous.  residual_out/status_out are host

@@ -59,6 +59,7 @@ struct npfem_batch {
   const int64_t* d_offsets = nullptr;
   std::vector<TypeLaunch> launches;
   int* d_counters = nullptr;
+  unsigned long long* d_phase = nullptr;  // [kPhases] per-phase cycle counters
   // host-step staging (allocated on first npfem_step_host)
   void* d_x = nullptr;
   void* d_v = nullptr;
@@ -72,14 +73,14 @@ template <typename S>
 static void fill_view(npfem_cell_type* t, DevTypeView<S>* v, const S* Dinv, const S* w_tri, const S* c_hinge,
                       const S* K0, const S* w_hinge, const S* mass, const S* inv_mass, const S* inc_coef,
                       const int32_t* tris, const int32_t* hinges, const int32_t* inc_ptr, const int32_t* inc_code,
-                      const int32_t* perm, const double* dinv, const int32_t* fcol, const uint16_t* frow,
-                      const double* fval, const int32_t* bcol, const uint16_t* brow, const double* bval) {
+                      const int32_t* perm, const double* dinv, const int32_t* fcol, const uint32_t* frow,
+                      const double* fval, const int32_t* bcol, const uint32_t* brow, const double* bval) {
   const HostType& H = t->host;
   v->n = H.n;
   v->T = H.T;
   v->E = H.E;
-  v->nchunks_fwd = (int)H.fwd_col.size();
-  v->nchunks_bwd = (int)H.bwd_col.size();
+  v->nchunks_fwd = (int)H.fwd_meta.size();
+  v->nchunks_bwd = (int)H.bwd_meta.size();
   v->tris = tris;
   v->Dinv = Dinv;
   v->w_tri = w_tri;
@@ -94,11 +95,11 @@ static void fill_view(npfem_cell_type* t, DevTypeView<S>* v, const S* Dinv, cons
   v->inc_coef = inc_coef;
   v->perm = perm;
   v->dinv = dinv;
-  v->fwd_col = fcol;
-  v->fwd_row = frow;
+  v->fwd_meta = fcol;
+  v->fwd_rc = frow;
   v->fwd_val = fval;
-  v->bwd_col = bcol;
-  v->bwd_row = brow;
+  v->bwd_meta = bcol;
+  v->bwd_rc = brow;
   v->bwd_val = bval;
   v->A0 = H.A0;
   v->V0 = H.V0;
@@ -111,8 +112,8 @@ template <typename S>
 static cudaError_t upload_precision(npfem_cell_type* t, DevTypeView<S>* view, const int32_t* tris,
                                     const int32_t* hinges, const int32_t* inc_ptr, const int32_t* inc_code,
                                     const int32_t* perm, const double* dinv, const int32_t* fcol,
-                                    const uint16_t* frow, const double* fval, const int32_t* bcol,
-                                    const uint16_t* brow, const double* bval) {
+                                    const uint32_t* frow, const double* fval, const int32_t* bcol,
+                                    const uint32_t* brow, const double* bval) {
   const HostType& H = t->host;
   std::vector<double> inv_mass(H.n);
   for (int i = 0; i < H.n; ++i) inv_mass[i] = 1.0 / H.mass[i];
@@ -157,7 +158,7 @@ npfem_status npfem_create_cell_type(const npfem_mesh* mesh, const npfem_material
   cudaError_t e = cudaGetDevice(&t->device);
   const HostType& H = t->host;
   const int32_t *tris, *hinges, *inc_ptr, *inc_code, *perm, *fcol, *bcol;
-  const uint16_t *frow, *brow;
+  const uint32_t *frow, *brow;
   const double *dinv, *fval, *bval;
 #define UP(vec, ptr)                                      \
   if (e == cudaSuccess) e = t->mem.upload(vec, &ptr);
@@ -167,11 +168,11 @@ npfem_status npfem_create_cell_type(const npfem_mesh* mesh, const npfem_material
   UP(H.inc_code, inc_code);
   UP(H.perm, perm);
   UP(H.dinv, dinv);
-  UP(H.fwd_col, fcol);
-  UP(H.fwd_row, frow);
+  UP(H.fwd_meta, fcol);
+  UP(H.fwd_rc, frow);
   UP(H.fwd_val, fval);
-  UP(H.bwd_col, bcol);
-  UP(H.bwd_row, brow);
+  UP(H.bwd_meta, bcol);
+  UP(H.bwd_rc, brow);
   UP(H.bwd_val, bval);
 #undef UP
   if (e == cudaSuccess)
@@ -202,7 +203,7 @@ npfem_status npfem_cell_type_info(const npfem_cell_type* t, npfem_type_info* inf
   info->n_tris = H.T;
   info->n_hinges = H.E;
   info->nnz_factor = H.nnz_factor;
-  info->solve_chunks = (int64_t)H.fwd_col.size();
+  info->solve_chunks = (int64_t)H.fwd_meta.size();
   info->rest_area = H.A0;
   info->rest_volume = H.V0;
   info->total_mass = H.total_mass;
@@ -221,7 +222,7 @@ npfem_status npfem_cell_type_analyze(const npfem_mesh* mesh, const npfem_materia
   info->n_tris = H.T;
   info->n_hinges = H.E;
   info->nnz_factor = H.nnz_factor;
-  info->solve_chunks = (int64_t)H.fwd_col.size();
+  info->solve_chunks = (int64_t)H.fwd_meta.size();
   info->rest_area = H.A0;
   info->rest_volume = H.V0;
   info->total_mass = H.total_mass;
@@ -258,6 +259,12 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
   e = b->mem.alloc(sizeof(int) * ntypes, &cnt);
   if (e != cudaSuccess) return cleanup(NPFEM_ERR_OOM, std::string("batch_create: ") + cudaGetErrorString(e));
   b->d_counters = static_cast<int*>(cnt);
+  void* ph = nullptr;
+  e = b->mem.alloc(sizeof(unsigned long long) * kPhases, &ph);
+  if (e != cudaSuccess) return cleanup(NPFEM_ERR_OOM, std::string("batch_create: ") + cudaGetErrorString(e));
+  b->d_phase = static_cast<unsigned long long*>(ph);
+  e = cudaMemset(ph, 0, sizeof(unsigned long long) * kPhases);
+  if (e != cudaSuccess) return cleanup(NPFEM_ERR_CUDA, std::string("batch_create: ") + cudaGetErrorString(e));
   int dev = 0, sms = 148, smem_optin = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -347,6 +354,7 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
     P.scratch = L.scratch;
     P.slot_bytes = L.slot_bytes;
     P.z_in_smem = L.z_in_smem;
+    P.phase_cycles = b->d_phase;
     dim3 grid(L.blocks), block(32 * L.warps_per_block);
     if (b->prec == NPFEM_FP64)
       npfem_step_kernel<double><<<grid, block, L.smem_bytes, st>>>(t->v64, P, static_cast<double*>(x),
@@ -358,6 +366,16 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
                                                                   static_cast<const float*>(f_ext));
     NPFEM_CUDA_TRY(cudaGetLastError());
   }
+  return NPFEM_OK;
+}
+
+npfem_status npfem_batch_phase_cycles(npfem_batch* b, uint64_t* cycles, int32_t reset) {
+  if (!b || !cycles) return fail(NPFEM_ERR_INVALID_ARG, "batch_phase_cycles: null argument");
+  NPFEM_CUDA_TRY(cudaDeviceSynchronize());
+  unsigned long long h[kPhases];
+  NPFEM_CUDA_TRY(cudaMemcpy(h, b->d_phase, sizeof(h), cudaMemcpyDeviceToHost));
+  for (int k = 0; k < kPhases; ++k) cycles[k] = h[k];
+  if (reset) NPFEM_CUDA_TRY(cudaMemset(b->d_phase, 0, sizeof(h)));
   return NPFEM_OK;
 }
 

@@ -141,6 +141,107 @@ int64_t symbolic(const Graph& g, const std::vector<int>& order, std::vector<std:
   return nnz;
 }
 
+// One update of a triangular sweep: z[t] -= v * z[s], valid once every update that
+// targets s has been applied.  Indices satisfy t > s.
+struct SweepOp {
+  int t, s;
+  double v;
+};
+
+// Pack the updates of one sweep into chunks of kChunk (one update per lane): each
+// chunk's sources are final before it starts, its targets are distinct, and at most
+// kBankCap targets share a shared-memory bank class (t mod 16; a row of three doubles
+// starts at bank 6t mod 32).  Greedy list scheduling, sources with the longest
+// remaining dependency chain first.  `relabel` maps r -> n-1-r when emitting indices.
+void pack_sweep(int n, const std::vector<SweepOp>& ops, bool relabel, std::vector<int32_t>* meta,
+                std::vector<uint32_t>* rc, std::vector<double>* val) {
+  constexpr int kBankCap = 3;
+  std::vector<std::vector<int>> by_src(n);
+  std::vector<int> remaining(n, 0);
+  for (int k = 0; k < (int)ops.size(); ++k) {
+    by_src[ops[k].s].push_back(k);
+    remaining[ops[k].t]++;
+  }
+  std::vector<int> dist(n, 0);
+  for (int s = n - 1; s >= 0; --s) {
+    int d = 0;
+    for (int k : by_src[s]) d = std::max(d, 1 + dist[ops[k].t]);
+    dist[s] = d;
+  }
+  std::set<std::pair<int, int>> ready;  // (-dist, source) with pending updates
+  std::vector<size_t> next(n, 0);       // next pending update of each source
+  for (int s = 0; s < n; ++s)
+    if (remaining[s] == 0 && !by_src[s].empty()) ready.insert({-dist[s], s});
+  auto emit_index = [&](int r) { return relabel ? n - 1 - r : r; };
+  std::vector<char> dirty(n + 1, 0), in_chunk(n + 1, 0);
+  std::vector<int> dirty_list;
+  size_t done = 0;
+  while (done < ops.size()) {
+    std::vector<int> chunk;
+    int cls[16] = {0};
+    std::vector<std::pair<int, int>> revisit;
+    while (!ready.empty() && (int)chunk.size() < kChunk) {
+      auto it = ready.begin();
+      auto key = *it;
+      ready.erase(it);
+      int s = key.second;
+      std::vector<int>& lst = by_src[s];
+      std::vector<int> keep;
+      for (size_t q = next[s]; q < lst.size(); ++q) {
+        int k = lst[q];
+        int t = ops[k].t;
+        if ((int)chunk.size() < kChunk && !in_chunk[t] && cls[emit_index(t) & 15] < kBankCap) {
+          chunk.push_back(k);
+          in_chunk[t] = 1;
+          cls[emit_index(t) & 15]++;
+        } else {
+          keep.push_back(k);
+        }
+      }
+      if (!keep.empty()) {
+        lst.assign(keep.begin(), keep.end());
+        next[s] = 0;
+        revisit.push_back(key);
+      } else {
+        next[s] = lst.size();
+      }
+    }
+    for (auto& key : revisit) ready.insert(key);
+    // hazard with rows written since the last synchronisation
+    bool hazard = false;
+    for (int k : chunk)
+      if (dirty[ops[k].t] || dirty[ops[k].s]) hazard = true;
+    if (hazard) {
+      for (int r : dirty_list) dirty[r] = 0;
+      dirty_list.clear();
+    }
+    meta->push_back(hazard ? 1 : 0);
+    for (int l = 0; l < kChunk; ++l) {
+      if (l < (int)chunk.size()) {
+        const SweepOp& op = ops[chunk[l]];
+        rc->push_back((uint32_t)emit_index(op.t) | ((uint32_t)emit_index(op.s) << 16));
+        val->push_back(op.v);
+      } else {
+        rc->push_back((uint32_t)n | ((uint32_t)n << 16));
+        val->push_back(0.0);
+      }
+    }
+    for (int k : chunk) {
+      int t = ops[k].t;
+      in_chunk[t] = 0;
+      if (!dirty[t]) {
+        dirty[t] = 1;
+        dirty_list.push_back(t);
+      }
+    }
+    done += chunk.size();
+    for (int k : chunk) {
+      int t = ops[k].t;
+      if (--remaining[t] == 0 && !by_src[t].empty()) ready.insert({-dist[t], t});
+    }
+  }
+}
+
 }  // namespace
 
 int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double w_strain,
@@ -386,28 +487,18 @@ int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double
     H.dinv[j] = 1.0 / (Ldiag[j] * Ldiag[j]);
     for (auto& v : Lval[j]) v /= Ldiag[j];
   }
-  // forward (column j of Lt, rows > j) and backward (row j of Lt, cols < j) chunks
-  auto push_chunks = [&](int col, const std::vector<std::pair<int, double>>& ent, std::vector<int32_t>& ccol,
-                         std::vector<uint16_t>& crow, std::vector<double>& cval) {
-    for (size_t s = 0; s < ent.size(); s += kChunk) {
-      ccol.push_back(col);
-      for (int l = 0; l < kChunk; ++l) {
-        size_t q = s + l;
-        crow.push_back(q < ent.size() ? (uint16_t)ent[q].first : (uint16_t)n);
-        cval.push_back(q < ent.size() ? ent[q].second : 0.0);
-      }
+  // forward sweep (Lt y = z): z[i] -= Lt(i,j) z[j] for i > j; backward sweep
+  // (Lt^T w = y): z[j] -= Lt(i,j) z[i], relabelled r -> n-1-r so that in both sweeps a
+  // target index exceeds its source index
+  std::vector<SweepOp> fwd, bwd;
+  for (int j = 0; j < n; ++j)
+    for (size_t q = 0; q < best_cols[j].size(); ++q) {
+      int i = best_cols[j][q];
+      fwd.push_back({i, j, Lval[j][q]});
+      bwd.push_back({n - 1 - j, n - 1 - i, Lval[j][q]});
     }
-  };
-  for (int j = 0; j < n; ++j) {
-    std::vector<std::pair<int, double>> ent;
-    for (size_t q = 0; q < best_cols[j].size(); ++q) ent.push_back({best_cols[j][q], Lval[j][q]});
-    push_chunks(j, ent, H.fwd_col, H.fwd_row, H.fwd_val);
-  }
-  for (int j = n - 1; j >= 0; --j) {
-    std::vector<std::pair<int, double>> ent;
-    for (auto& kq : rowlist[j]) ent.push_back({kq.first, Lval[kq.first][kq.second]});
-    push_chunks(j, ent, H.bwd_col, H.bwd_row, H.bwd_val);
-  }
+  pack_sweep(n, fwd, false, &H.fwd_meta, &H.fwd_rc, &H.fwd_val);
+  pack_sweep(n, bwd, true, &H.bwd_meta, &H.bwd_rc, &H.bwd_val);
   return NPFEM_OK;
 }
 

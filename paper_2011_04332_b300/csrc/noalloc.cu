@@ -25,6 +25,7 @@ namespace {
 constexpr size_t kStaticBytes = size_t(32) << 20;
 constexpr int kStaticMaxCells = 65536;
 constexpr size_t kCounterOff = 0;
+constexpr size_t kPhaseOff = 64;  // per-phase cycle counters (telemetry, not read back here)
 constexpr size_t kOffsetsOff = 256;
 constexpr size_t kCellsOff = kOffsetsOff + sizeof(int64_t) * (kStaticMaxCells + 1);
 constexpr size_t kSlotsOff = (kCellsOff + sizeof(int32_t) * kStaticMaxCells + 255) & ~size_t(255);
@@ -136,6 +137,7 @@ extern "C" npfem_status npfem_step_noalloc(const npfem_cell_type* type, npfem_pr
   P.alpha_log = opts->alpha_log;
   P.alpha_log_len = opts->alpha_log_len;
   P.queue_counter = counter;
+  P.phase_cycles = reinterpret_cast<unsigned long long*>(base + kPhaseOff);
   P.scratch = reinterpret_cast<char*>(base + kSlotsOff);
   P.slot_bytes = slot;
   P.z_in_smem = z_in_smem;

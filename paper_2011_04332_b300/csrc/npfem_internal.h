@@ -37,9 +37,11 @@ struct HostType {
   std::vector<int32_t> perm;     // [n]
   std::vector<double> dinv;      // [n] 1/D
   int64_t nnz_factor = 0;
-  // column-oriented chunk tables (32 entries each, padding row = n, value 0)
-  std::vector<int32_t> fwd_col, bwd_col;     // [nchunks]
-  std::vector<uint16_t> fwd_row, bwd_row;    // [nchunks*32]
+  // Triangular sweeps as chunks of 32 updates z[row] -= val * z[col], one per lane
+  // (padding: row = col = n, val = 0).  meta bit 0: synchronise the warp before the
+  // chunk (it reads or writes a row written since the last synchronisation).
+  std::vector<int32_t> fwd_meta, bwd_meta;   // [nchunks]
+  std::vector<uint32_t> fwd_rc, bwd_rc;      // [nchunks*32] row | col << 16
   std::vector<double> fwd_val, bwd_val;      // [nchunks*32]
 };
 
@@ -67,11 +69,11 @@ struct DevTypeView {
   const S* inc_coef;        // [nnz]
   const int32_t* perm;      // [n]
   const double* dinv;       // [n]
-  const int32_t* fwd_col;
-  const uint16_t* fwd_row;
+  const int32_t* fwd_meta;
+  const uint32_t* fwd_rc;
   const double* fwd_val;
-  const int32_t* bwd_col;
-  const uint16_t* bwd_row;
+  const int32_t* bwd_meta;
+  const uint32_t* bwd_rc;
   const double* bwd_val;
   double A0, V0, w_area, w_vol, dt;
 };

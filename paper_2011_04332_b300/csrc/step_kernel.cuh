@@ -43,7 +43,16 @@ struct StepParams {
   char* scratch;               // workspace, slot_bytes per warp
   size_t slot_bytes;
   int z_in_smem;               // 1: FP64 solve vector in dynamic shared memory
+  unsigned long long* phase_cycles;  // [kPhases] per-phase SM cycles summed over warps
 };
+
+// Per-phase cycle telemetry: each warp adds the SM clock cycles it spent in a phase
+// to a batch-owned counter (one relaxed 64-bit atomic by lane 0 per phase instance).
+enum Phase { kPhPredict = 0, kPhObjective, kPhTwoLoop, kPhSolve, kPhHistory, kPhWrite, kPhAreaVolume, kPhGather,
+             kPhases = 8 };
+#define NPFEM_PHASE_BEGIN(var) const long long var = clock64();
+#define NPFEM_PHASE_END(var, ph, P, lane) \
+  if ((lane) == 0) atomicAdd(&(P).phase_cycles[ph], (unsigned long long)(clock64() - (var)));
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -183,10 +192,11 @@ struct EvalOut {
 // triangle deformation gradient F = [e1 e2] Dm^-1 to R = F (F^T F)^(-1/2) via the
 // closed-form 2x2 SPD square root (C + sqrt(det C) I)/sqrt(tr C + 2 sqrt(det C)).
 template <typename S>
-__device__ EvalOut eval_objective(const DevTypeView<S>& ty, const CellWs<S>& w, const S* U, S* Gout,
-                                  V3<S> cvol, int lane) {
+__device__ EvalOut eval_objective(const DevTypeView<S>& ty, const StepParams& P, const CellWs<S>& w, const S* U,
+                                  S* Gout, V3<S> cvol, int lane) {
   const int n = ty.n, T = ty.T, E = ty.E;
   const S* X = w.X;
+  NPFEM_PHASE_BEGIN(t_area)
   // pass A: global area and volume (FP64 reductions)
   Acc<S> a_sum, v_sum;
   for (int t = lane; t < T; t += 32) {
@@ -206,6 +216,7 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const CellWs<S>& w, 
   const S kV = (S)(ty.w_vol * dV / ty.V0);
   const S half = (S)0.5, sixth = (S)(1.0 / 6.0);
 
+  NPFEM_PHASE_END(t_area, kPhAreaVolume, P, lane)
   // pass B: triangles (strain projection + area/volume corner gradients)
   Acc<S> e_el;
   bool degen = false;
@@ -278,6 +289,7 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const CellWs<S>& w, 
   }
   __syncwarp();
 
+  NPFEM_PHASE_BEGIN(t_gather)
   // pass D: vertices (inertia + gather of element contributions)
   const S idt2 = (S)(1.0 / (ty.dt * ty.dt));
   for (int v = lane; v < n; v += 32) {
@@ -297,6 +309,7 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const CellWs<S>& w, 
     }
     st3(Gout, v, g);
   }
+  NPFEM_PHASE_END(t_gather, kPhGather, P, lane)
   EvalOut o;
   o.energy = e_el.total() + e_area + e_vol;
   o.degenerate = __any_sync(kFull, degen);
@@ -319,26 +332,39 @@ __device__ __forceinline__ double vdot64(const S* a, const S* b, int len, int la
 }
 
 // ------------------------------------------------------------------ K4
-// One sweep of column-oriented updates z[row] -= l * z[col] over 32-entry chunks, the
-// chunk tables prefetched kPrefetch chunks ahead in registers (the tables stream from
-// L2).  Consecutive chunks of one column touch distinct rows and never write z[col],
-// so the warp only synchronises where the column changes.
+// One triangular sweep: chunks of 32 updates z[row] -= val * z[col], one per lane,
+// packed on the host so that every source is final before its chunk and targets are
+// distinct; the warp synchronises only before chunks flagged as hazardous.  The chunk
+// tables stream from L2 and are prefetched kPrefetch chunks ahead in registers.  When
+// the solve vector is in shared memory it is addressed through the shared window.
 constexpr int kPrefetch = 8;
 
-__device__ __forceinline__ void chunk_sweep(int nc, const int32_t* __restrict__ col,
-                                            const uint16_t* __restrict__ row, const double* __restrict__ val,
+__device__ __forceinline__ double lds_f64(uint32_t a) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void sts_f64(uint32_t a, double v) {
+  asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+
+template <bool kShared>
+__device__ __forceinline__ void chunk_sweep(int nc, const int32_t* __restrict__ meta,
+                                            const uint32_t* __restrict__ rc, const double* __restrict__ val,
                                             double* z, int n, int lane) {
-  int jb[kPrefetch], rb[kPrefetch];
+  const uint32_t zs = kShared ? (uint32_t)__cvta_generic_to_shared(z) : 0u;
+  int mb[kPrefetch];
+  uint32_t eb[kPrefetch];
   double vb[kPrefetch];
 #pragma unroll
   for (int k = 0; k < kPrefetch; ++k) {
     if (k < nc) {
-      jb[k] = __ldg(col + k);
-      rb[k] = __ldg(row + (size_t)k * kChunk + lane);
+      mb[k] = __ldg(meta + k);
+      eb[k] = __ldg(rc + (size_t)k * kChunk + lane);
       vb[k] = __ldg(val + (size_t)k * kChunk + lane);
     } else {
-      jb[k] = -1;
-      rb[k] = n;
+      mb[k] = 0;
+      eb[k] = (uint32_t)n | ((uint32_t)n << 16);
       vb[k] = 0.0;
     }
   }
@@ -347,27 +373,36 @@ __device__ __forceinline__ void chunk_sweep(int nc, const int32_t* __restrict__ 
     for (int k = 0; k < kPrefetch; ++k) {
       const int ch = base + k;
       if (ch < nc) {
-        const int j = jb[k], r = rb[k];
+        const int m = mb[k];
+        const uint32_t e = eb[k];
         const double l = vb[k];
         const int nx = ch + kPrefetch;
         if (nx < nc) {
-          jb[k] = __ldg(col + nx);
-          rb[k] = __ldg(row + (size_t)nx * kChunk + lane);
+          mb[k] = __ldg(meta + nx);
+          eb[k] = __ldg(rc + (size_t)nx * kChunk + lane);
           vb[k] = __ldg(val + (size_t)nx * kChunk + lane);
-        } else {
-          jb[k] = -1;
         }
-        const double x0 = z[3 * j], x1 = z[3 * j + 1], x2 = z[3 * j + 2];
-        double* zr = z + 3 * r;
-        const double a0 = fma(-l, x0, zr[0]);
-        const double a1 = fma(-l, x1, zr[1]);
-        const double a2 = fma(-l, x2, zr[2]);
-        zr[0] = a0;
-        zr[1] = a1;
-        zr[2] = a2;
-        // next chunk's column (ring slot k+1; slot k already holds chunk ch+kPrefetch)
-        const int jn = jb[(k + 1) % kPrefetch];
-        if (jn != j) __syncwarp();
+        if (m & 1) __syncwarp();
+        const int r = (int)(e & 0xffffu), j = (int)(e >> 16);
+        if (kShared) {
+          const uint32_t aj = zs + 24u * (uint32_t)j, ar = zs + 24u * (uint32_t)r;
+          const double x0 = lds_f64(aj), x1 = lds_f64(aj + 8), x2 = lds_f64(aj + 16);
+          const double a0 = fma(-l, x0, lds_f64(ar));
+          const double a1 = fma(-l, x1, lds_f64(ar + 8));
+          const double a2 = fma(-l, x2, lds_f64(ar + 16));
+          sts_f64(ar, a0);
+          sts_f64(ar + 8, a1);
+          sts_f64(ar + 16, a2);
+        } else {
+          const double x0 = z[3 * j], x1 = z[3 * j + 1], x2 = z[3 * j + 2];
+          double* zr = z + 3 * r;
+          const double a0 = fma(-l, x0, zr[0]);
+          const double a1 = fma(-l, x1, zr[1]);
+          const double a2 = fma(-l, x2, zr[2]);
+          zr[0] = a0;
+          zr[1] = a1;
+          zr[2] = a2;
+        }
       }
     }
   }
@@ -377,7 +412,7 @@ __device__ __forceinline__ void chunk_sweep(int nc, const int32_t* __restrict__ 
 // R = A^-1 Q for the three coordinates (Q and R may alias).  FP64 throughout:
 // permute, unit-lower forward sweep, D^-1 scaling, unit-upper backward sweep.
 template <typename S>
-__device__ void global_solve(const DevTypeView<S>& ty, double* z, const S* Q, S* R, int lane) {
+__device__ void global_solve(const DevTypeView<S>& ty, double* z, bool z_shared, const S* Q, S* R, int lane) {
   const int n = ty.n;
   for (int r = lane; r < n; r += 32) {
     int v = __ldg(&ty.perm[r]);
@@ -387,7 +422,10 @@ __device__ void global_solve(const DevTypeView<S>& ty, double* z, const S* Q, S*
   }
   if (lane < 3) z[3 * n + lane] = 0.0;
   __syncwarp();
-  chunk_sweep(ty.nchunks_fwd, ty.fwd_col, ty.fwd_row, ty.fwd_val, z, n, lane);
+  if (z_shared)
+    chunk_sweep<true>(ty.nchunks_fwd, ty.fwd_meta, ty.fwd_rc, ty.fwd_val, z, n, lane);
+  else
+    chunk_sweep<false>(ty.nchunks_fwd, ty.fwd_meta, ty.fwd_rc, ty.fwd_val, z, n, lane);
   for (int r = lane; r < n; r += 32) {
     double d = __ldg(&ty.dinv[r]);
     z[3 * r] *= d;
@@ -395,7 +433,10 @@ __device__ void global_solve(const DevTypeView<S>& ty, double* z, const S* Q, S*
     z[3 * r + 2] *= d;
   }
   __syncwarp();
-  chunk_sweep(ty.nchunks_bwd, ty.bwd_col, ty.bwd_row, ty.bwd_val, z, n, lane);
+  if (z_shared)
+    chunk_sweep<true>(ty.nchunks_bwd, ty.bwd_meta, ty.bwd_rc, ty.bwd_val, z, n, lane);
+  else
+    chunk_sweep<false>(ty.nchunks_bwd, ty.bwd_meta, ty.bwd_rc, ty.bwd_val, z, n, lane);
   for (int r = lane; r < n; r += 32) {
     int v = __ldg(&ty.perm[r]);
     R[3 * v] = (S)z[3 * r];
@@ -417,6 +458,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
   const double dt = ty.dt;
   const S sdt = (S)dt, sdt2 = (S)(dt * dt);
 
+  NPFEM_PHASE_BEGIN(t_predict)
   // K1: anchor, X = x_n - anchor, W = y - x_n, U = W
   const S ax = x[off], ay = x[Nt + off], az = x[2 * Nt + off];
   Acc<S> cx, cy, cz;
@@ -446,7 +488,10 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
   S* UT = w.UT;
   S* G = w.G;
   S* GT = w.GT;
-  EvalOut ev = eval_objective<S>(ty, w, U, G, cvol, lane);
+  NPFEM_PHASE_END(t_predict, kPhPredict, P, lane)
+  NPFEM_PHASE_BEGIN(t_obj0)
+  EvalOut ev = eval_objective<S>(ty, P, w, U, G, cvol, lane);
+  NPFEM_PHASE_END(t_obj0, kPhObjective, P, lane)
   double fx = ev.energy;
   bool degen = ev.degenerate;
   const double g0n = sqrt(vdot64<S>(G, G, len, lane));
@@ -457,6 +502,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
   for (int i = 0; i < kHistory; ++i) rho[i] = aco[i] = 0;
 
   for (int k = 0; k < iters; ++k) {
+    NPFEM_PHASE_BEGIN(t_loop1)
     // K3 first loop: Q = G; newest -> oldest
     for (int i = lane; i < len; i += 32) w.Q[i] = G[i];
     __syncwarp();
@@ -470,7 +516,11 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
       __syncwarp();
     }
     // K4: r = H0 q
-    global_solve<S>(ty, w.z, w.Q, w.Q, lane);
+    NPFEM_PHASE_END(t_loop1, kPhTwoLoop, P, lane)
+    NPFEM_PHASE_BEGIN(t_solve)
+    global_solve<S>(ty, w.z, P.z_in_smem != 0, w.Q, w.Q, lane);
+    NPFEM_PHASE_END(t_solve, kPhSolve, P, lane)
+    NPFEM_PHASE_BEGIN(t_loop2)
     // K3 second loop: oldest -> newest
     for (int q = hcount - 1; q >= 0; --q) {
       int i = (hhead - 1 - q + kHistory) % kHistory;
@@ -484,10 +534,11 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
     for (int e = lane; e < len; e += 32) w.D[e] = -w.Q[e];
     __syncwarp();
     double gd = vdot64<S>(G, w.D, len, lane);
+    NPFEM_PHASE_END(t_loop2, kPhTwoLoop, P, lane)
     if (!(gd < 0.0)) {  // not a descent direction: drop history, plain PD step
       hcount = 0;
       hhead = 0;
-      global_solve<S>(ty, w.z, G, w.Q, lane);
+      global_solve<S>(ty, w.z, P.z_in_smem != 0, G, w.Q, lane);
       for (int e = lane; e < len; e += 32) w.D[e] = -w.Q[e];
       __syncwarp();
       gd = vdot64<S>(G, w.D, len, lane);
@@ -498,7 +549,9 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
       const S sa = (S)alpha;
       for (int e = lane; e < len; e += 32) UT[e] = U[e] + sa * w.D[e];
       __syncwarp();
-      EvalOut et = eval_objective<S>(ty, w, UT, GT, cvol, lane);
+      NPFEM_PHASE_BEGIN(t_obj)
+      EvalOut et = eval_objective<S>(ty, P, w, UT, GT, cvol, lane);
+      NPFEM_PHASE_END(t_obj, kPhObjective, P, lane)
       ft = et.energy;
       degen = degen || et.degenerate;
       double gtd = vdot64<S>(GT, w.D, len, lane);
@@ -511,6 +564,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
       }
       alpha *= 0.5;
     }
+    NPFEM_PHASE_BEGIN(t_hist)
     // K6: history pair (s, y) = (UT - U, GT - G) into the ring slot hhead
     if (k < iters - 1) {
       S* si = w.hs + (size_t)hhead * len;
@@ -533,6 +587,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
       }
       __syncwarp();
     }
+    NPFEM_PHASE_END(t_hist, kPhHistory, P, lane)
     if (P.alpha_log && k < P.alpha_log_len && lane == 0) P.alpha_log[(size_t)cell * P.alpha_log_len + k] = alpha;
     // accept
     S* t1 = U;
@@ -544,6 +599,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
     fx = ft;
   }
 
+  NPFEM_PHASE_BEGIN(t_write)
   // K7: residual, write x_{n+1} = anchor + X + U and v_{n+1} = U / dt
   const double gn = sqrt(vdot64<S>(G, G, len, lane));
   const S idt = (S)(1.0 / dt);
@@ -563,6 +619,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
           !isfinite((double)vy) || !isfinite((double)vz);
   }
   bad = __any_sync(kFull, bad);
+  NPFEM_PHASE_END(t_write, kPhWrite, P, lane)
   if (lane == 0) {
     if (degen) status |= 2;
     if (bad) status |= 4;

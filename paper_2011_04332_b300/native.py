@@ -75,6 +75,7 @@ def load_library() -> C.CDLL:
         "npfem_step": [vp, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp],
         "npfem_step_host": [vp, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp],
         "npfem_last_error_string": [C.c_char_p, C.c_size_t],
+        "npfem_batch_phase_cycles": [vp, C.POINTER(C.c_uint64), C.c_int32],
         "npfem_step_noalloc": [vp, C.c_int, C.c_int32, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp],
     }
     for name, args in sig.items():
@@ -190,6 +191,14 @@ class Batch:
             stream = stream.cuda_stream
         _check(_lib.npfem_step(self.handle, _ptr(x), _ptr(v), _ptr(f), _ptr(iters), C.byref(opts),
                                _ptr(residual), _ptr(status), C.c_void_p(stream)))
+
+    PHASES = ("predict", "objective", "two_loop", "solve", "history", "write", "area_volume", "gather")
+
+    def phase_cycles(self, reset: bool = False) -> dict:
+        """npfem_batch_phase_cycles: SM cycles per phase summed over warps (synchronises)."""
+        out = (C.c_uint64 * 8)()
+        _check(_lib.npfem_batch_phase_cycles(self.handle, out, int(reset)))
+        return {k: int(out[i]) for i, k in enumerate(self.PHASES)}
 
     def step_host(self, x: np.ndarray, v: np.ndarray, f: np.ndarray, iters=None, iters_default: int = 5,
                   residual=None, status=None, stream: int = 0):

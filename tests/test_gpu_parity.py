@@ -222,3 +222,16 @@ def test_rollout_tracks_oracle():
         ref = O.batch_step(ots, b.type_of_cell, b.offsets, xo, vo, b.f, b.iters)
         xo, vo = ref["x"], ref["v"]
     assert cell_errors(b, x, xo).max() < 1e-8
+
+
+def test_phase_cycle_telemetry():
+    """Per-phase cycle counters accumulate over steps and reset on request."""
+    nat = _native()
+    b = I.homogeneous_rbc_batch(ncells=8, seed=11)
+    r = Runner(b, nat.FP32FORM)
+    r.batch.phase_cycles(reset=True)
+    r.step(b.x, b.v, b.f)
+    c = r.batch.phase_cycles(reset=True)
+    assert c["solve"] > 0 and c["objective"] > 0 and c["two_loop"] > 0 and c["write"] > 0
+    assert c["gather"] < c["objective"] and c["area_volume"] < c["objective"]
+    assert all(v == 0 for v in r.batch.phase_cycles().values())
