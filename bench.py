@@ -43,9 +43,9 @@ def make_workload(name: str, rank: int = 0):
         b = I.heterogeneous_batch(4500, 4500, 1000, seed=1002 + 100 * rank)
         desc = ("heterogeneous 10^4 cells: 4500 RBC 642v + 4500 RBC 2562v + 1000 PLT 162v, "
                 "3..8 iterations per cell, seeded random order")
-    elif name == "homog1184":
-        b = I.homogeneous_rbc_batch(ncells=1184, seed=1001 + 100 * rank)
-        desc = "homogeneous 1184 RBC (642 vertices; one cell per warp slot), 5 iterations"
+    elif name == "homog1776":
+        b = I.homogeneous_rbc_batch(ncells=1776, seed=1001 + 100 * rank)
+        desc = "homogeneous 1776 RBC (642 vertices; one cell per warp slot of 148 SMs x 12 warps), 5 iterations"
     elif name == "small":
         b = I.homogeneous_rbc_batch(ncells=64, seed=1001 + 100 * rank)
         desc = "64 RBC (642 vertices), 5 iterations"
@@ -280,6 +280,10 @@ def run_ours(args, rank, world, local_rank):
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "api": "npfem_step_host (pinned host buffers, copies + step + copies, synchronous)"}
 
+    adjoint = None
+    if rank == 0 and not args.no_adjoint:
+        adjoint = measure_adjoint(dev)
+
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -295,11 +299,47 @@ def run_ours(args, rank, world, local_rank):
         "fp32_peak_tflops": fp32_peak,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "adjoint": adjoint,
         "gpu_launches": args.steps * len(set(int(t) for t in b.type_of_cell)),
         "clocks": clk.summary(),
         "wall_s_timed_region": t_wall,
     }
     return out
+
+
+def measure_adjoint(dev, nsteps: int = 40, ckpt_every: int = 20, ncells: int = 256):
+    """Adjoint throughput on the calibration workload: ncells placed 642-vertex RBCs,
+    FP64, loss = squared distance of axial/transverse diameters to seeded targets after
+    an nsteps rollout with checkpoints every ckpt_every steps (forward + backward)."""
+    import torch
+    from paper_2011_04332_b300 import autograd as AG
+    from paper_2011_04332_b300 import inputs as I
+    b = I.homogeneous_rbc_batch(ncells=ncells, seed=1003)
+    targets = torch.tensor(np.random.default_rng(1003).uniform(6, 12, size=(ncells, 2)), device=dev)
+    cal = AG.Calibration(b.types[0].mesh, b.types[0].material.as_tuple(), b.dt, ncells)
+    x0 = torch.tensor(b.x, device=dev)
+    v0 = torch.tensor(b.v, device=dev)
+    f = torch.tensor(b.f, device=dev, requires_grad=True)
+    iters = torch.tensor(b.iters, device=dev)
+    loss, w = cal.loss(x0, v0, f, targets, iters, 2, 1)       # warm-up (allocates the workspace)
+    loss.backward()
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    f.grad = None
+    e[0].record()
+    loss, w = cal.loss(x0, v0, f, targets, iters, nsteps, ckpt_every)
+    e[1].record()
+    loss.backward()
+    e[2].record()
+    torch.cuda.synchronize()
+    t_fwd, t_bwd = e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2])
+    return {"workload": f"calibration: {ncells} RBC (642 vertices) FP64, {nsteps}-step rollout, "
+                        f"checkpoints every {ckpt_every} steps, diameter loss",
+            "adjoint_cell_steps_per_s": ncells * nsteps / (t_bwd / 1e3),
+            "ms_per_adjoint_step": t_bwd / nsteps,
+            "ms_per_forward_step": t_fwd / nsteps,
+            "backward_includes": "segment recomputation (one extra forward step per step) + adjoint steps",
+            "loss": float(loss.detach()), "grad_w": [float(g) for g in w.grad[0].tolist()]}
 
 
 def probe_peaks():
@@ -342,7 +382,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="homog4096", choices=["homog4096", "hetero10k", "homog1184", "small"])
+    ap.add_argument("--workload", default="homog4096", choices=["homog4096", "hetero10k", "homog1776", "small"])
     ap.add_argument("--precision", default="fp32form", choices=["fp32form", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=128)
@@ -351,6 +391,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

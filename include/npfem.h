@@ -143,6 +143,26 @@ npfem_status npfem_step(npfem_batch* batch, void* x, void* v, const void* f_ext,
                         const int32_t* iters, const npfem_solver_opts* opts,
                         double* residual_out, int32_t* status_out, void* stream);
 
+/* Reverse mode of one step (FP64 batches only): given dL/dx_{n+1} and dL/dv_{n+1},
+ * returns dL/dx_n, dL/dv_n, dL/df_ext and, per cell, dL/d(w_strain, w_bend, w_area,
+ * w_vol) of its type's material.  The derivative is that of the unrolled
+ * quasi-Newton iteration of npfem_step (Liu et al. 2017, the iteration named in the
+ * paper's Implementation and architecture section) with its accepted line-search
+ * step lengths held fixed; the forward step is recomputed from (x, v, f_ext).
+ *   x, v, f_ext   in  [3][N_total] double: the state the step started from.
+ *   iters         in  [ncells] int32 or NULL (opts->iters); at most 16 per cell.
+ *   gx_next       in  [3][N_total] dL/dx_{n+1};  gv_next in [3][N_total] or NULL (zero).
+ *   gx, gv, gf    out [3][N_total] (overwritten).
+ *   gw            out [ncells][4] (overwritten).
+ *   status_out    out [ncells] or NULL: 0, or 8 when a cell's iteration count exceeds 16.
+ * The first call on a batch allocates its adjoint workspace (about 2 MB per warp
+ * slot for a 642-vertex type).  Asynchronous on `stream`.
+ * Errors: INVALID_ARG (null pointer, FP32-form batch), CUDA, OOM. */
+npfem_status npfem_step_adjoint(npfem_batch* batch, const void* x, const void* v, const void* f_ext,
+                                const int32_t* iters, const npfem_solver_opts* opts,
+                                const double* gx_next, const double* gv_next, double* gx, double* gv,
+                                double* gf, double* gw, int32_t* status_out, void* stream);
+
 /* Per-phase telemetry of the batch's steps since creation or the last reset: SM
  * clock cycles summed over all warps, in the order prediction, objective evaluation,
  * two-loop recursion, global FP64 solve, history update, write-back, and (contained

@@ -31,6 +31,11 @@ differences (no function is "parity unpinned").
 
 Implementation style: plain numpy float64, vectorised over elements only.  A
 dense Cholesky from numpy serves as the library step for the global matrix.
+Every function also accepts complex inputs with an infinitesimal imaginary part
+(complex-step differentiation): norms are written as sqrt(sum(x*x)), decisions use
+real parts, and the global solve propagates an imaginary perturbation of A or of
+the right-hand side exactly to first order.  This gives the oracle its own
+forward-mode derivative, used to check the CUDA adjoint.
 """
 from __future__ import annotations
 
@@ -164,6 +169,11 @@ def rest_state(X: np.ndarray, tris: np.ndarray, w_strain: float, w_bend: float,
                      A0, V0, mass, float(w_area), float(w_vol), float(dt))
 
 
+def _norm_rows(a: np.ndarray) -> np.ndarray:
+    """Row norms sqrt(sum a^2), analytic for complex-step inputs."""
+    return np.sqrt(np.sum(a * a, axis=1))
+
+
 def _volume(x: np.ndarray, tris: np.ndarray) -> float:
     a, b, c = x[tris[:, 0]], x[tris[:, 1]], x[tris[:, 2]]
     return np.sum(np.einsum("ij,ij->i", a, np.cross(b, c))) / 6.0
@@ -179,7 +189,7 @@ def polar_project(F: np.ndarray) -> (np.ndarray, np.ndarray):
     """
     C = np.einsum("tki,tkj->tij", F, F)
     det = C[:, 0, 0] * C[:, 1, 1] - C[:, 0, 1] * C[:, 1, 0]
-    bad = det <= DEGENERATE_DET
+    bad = np.real(det) <= DEGENERATE_DET
     det_s = np.where(bad, 1.0, det)
     s = np.sqrt(det_s)
     tau = np.sqrt(C[:, 0, 0] + C[:, 1, 1] + 2.0 * s)
@@ -211,8 +221,8 @@ def hinge_K(rs: RestState, x: np.ndarray) -> np.ndarray:
 
 def bending_project(rs: RestState, K: np.ndarray) -> np.ndarray:
     """Closest point of K on the sphere |p| = |K0|; tie-break p = K0 for |K| ~ 0."""
-    kn = np.linalg.norm(K, axis=1)
-    small = kn < DEGENERATE_NORM
+    kn = _norm_rows(K)
+    small = np.real(kn) < DEGENERATE_NORM
     p = rs.kappa0[:, None] * K / np.where(small, 1.0, kn)[:, None]
     p[small] = rs.K0[small]
     return p
@@ -243,9 +253,9 @@ def internal_energy_and_gradient(rs: RestState, x: np.ndarray, w_scale=None):
     E_A = w_A/2 (A - A0)^2 / A0,  E_V = w_V/2 (V - V0)^2 / V0
     `w_scale` optionally multiplies (w_strain, w_bend, w_area, w_vol).
     """
-    ws = np.ones(4) if w_scale is None else np.asarray(w_scale, dtype=np.float64)
+    ws = np.ones(4) if w_scale is None else np.asarray(w_scale)
     n = rs.n
-    g = np.zeros((n, 3))
+    g = np.zeros((n, 3), dtype=np.result_type(x, ws))
     t = rs.tris
     # --- membrane strain, per triangle
     F = deformation_gradient(rs, x)
@@ -270,9 +280,9 @@ def internal_energy_and_gradient(rs: RestState, x: np.ndarray, w_scale=None):
     # --- global area
     a, b, c = x[t[:, 0]], x[t[:, 1]], x[t[:, 2]]
     cr = np.cross(b - a, c - a)
-    crn = np.linalg.norm(cr, axis=1)
+    crn = _norm_rows(cr)
     A = 0.5 * np.sum(crn)
-    nh = cr / np.where(crn > 0, crn, 1.0)[:, None]
+    nh = cr / np.where(np.real(crn) > 0, crn, 1.0)[:, None]
     kA = ws[2] * rs.w_area * (A - rs.A0) / rs.A0
     e_area = 0.5 * ws[2] * rs.w_area * (A - rs.A0) ** 2 / rs.A0
     np.add.at(g, t[:, 0], kA * 0.5 * np.cross(nh, c - b))
@@ -297,7 +307,7 @@ def objective(rs: RestState, x: np.ndarray, y: np.ndarray, w_scale=None):
     parts, g = internal_energy_and_gradient(rs, x, w_scale)
     dx = x - y
     m = rs.mass
-    parts.inertia = float(np.sum(m[:, None] * dx * dx) / (2.0 * rs.dt ** 2))
+    parts.inertia = np.sum(m[:, None] * dx * dx) / (2.0 * rs.dt ** 2)
     g = g + m[:, None] * dx / rs.dt ** 2
     return parts, g
 
@@ -307,9 +317,9 @@ def pd_matrix(rs: RestState, w_scale=None) -> np.ndarray:
     """Projective-dynamics system matrix (n x n, shared by x, y, z):
     A = M/dt^2 + sum_t w_t G_t^T G_t + sum_e w_e c_e c_e^T,
     where G_t maps a triangle's three vertex coordinates to one row of F."""
-    ws = np.ones(4) if w_scale is None else np.asarray(w_scale, dtype=np.float64)
+    ws = np.ones(4) if w_scale is None else np.asarray(w_scale)
     n = rs.n
-    A = np.diag(rs.mass / rs.dt ** 2)
+    A = np.diag(rs.mass / rs.dt ** 2).astype(np.result_type(ws, np.float64))
     S = np.array([[-1.0, 1.0, 0.0], [-1.0, 0.0, 1.0]])
     for ti in range(rs.tris.shape[0]):
         G = rs.Dm_inv[ti].T @ S                    # [2,3]
@@ -324,16 +334,30 @@ def pd_matrix(rs: RestState, w_scale=None) -> np.ndarray:
 
 
 class GlobalSolver:
-    """H0 = A^-1 applied coordinate-wise through a dense Cholesky factor A = L L^T."""
+    """H0 = A^-1 applied coordinate-wise through a dense Cholesky factor A = L L^T.
+
+    For a complex-step matrix A = Ar + i Ai (Ai infinitesimal) and right-hand side
+    q = qr + i qi, the solution is zr = Ar^-1 qr, zi = Ar^-1 (qi - Ai zr), exact to
+    first order in the imaginary parts."""
 
     def __init__(self, A: np.ndarray):
         self.A = A
-        self.L = np.linalg.cholesky(A)
+        self.Ai = np.imag(A) if np.iscomplexobj(A) else None
+        self.L = np.linalg.cholesky(np.real(A))
 
-    def solve(self, q: np.ndarray) -> np.ndarray:
+    def _real_solve(self, q):
         import scipy.linalg as sla
         z = sla.solve_triangular(self.L, q, lower=True)
         return sla.solve_triangular(self.L.T, z, lower=False)
+
+    def solve(self, q: np.ndarray) -> np.ndarray:
+        if not np.iscomplexobj(q) and self.Ai is None:
+            return self._real_solve(q)
+        zr = self._real_solve(np.real(q))
+        qi = np.imag(q) if np.iscomplexobj(q) else np.zeros_like(zr)
+        if self.Ai is not None:
+            qi = qi - self.Ai @ zr
+        return zr + 1j * self._real_solve(qi)
 
 
 # ---------------------------------------------------------------- quasi-Newton step
@@ -381,13 +405,13 @@ def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
     (the objective is translation invariant), adding it back at the end.
     """
     dt = rs.dt
-    ctr = x_n.mean(axis=0)
+    ctr = np.real(x_n).mean(axis=0)
     xn = x_n - ctr
     y = xn + dt * v_n + dt * dt * f_ext / rs.mass[:, None]
     x = y.copy()
     parts, g = objective(rs, x, y, w_scale)
     fx = parts.total
-    g0n = float(np.sqrt(np.sum(g * g)))
+    g0n = float(np.sqrt(np.sum(np.real(g) ** 2)))
     S: List[np.ndarray] = []
     Y: List[np.ndarray] = []
     alphas, energies, gnorms = [], [fx], [g0n]
@@ -395,21 +419,21 @@ def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
     trials = 0
     for k in range(iters):
         d = -two_loop(g, S, Y, solver)
-        gd = float(np.sum(g * d))
-        if not gd < 0.0:
+        gd = np.sum(g * d)
+        if not np.real(gd) < 0.0:
             S.clear()
             Y.clear()
             d = -solver.solve(g)
-            gd = float(np.sum(g * d))
+            gd = np.sum(g * d)
         alpha = 1.0
         for h in range(MAX_HALVINGS + 1):
             xt = x + alpha * d
             pt, gt = objective(rs, xt, y, w_scale)
             trials += 1
             ft = pt.total
-            armijo = ft <= fx + ARMIJO_C1 * alpha * gd
-            approx = (float(np.sum(gt * d)) <= (2.0 * ARMIJO_C1 - 1.0) * gd
-                      and ft <= fx + ENERGY_GUARD_EPS * abs(fx))
+            armijo = np.real(ft) <= np.real(fx + ARMIJO_C1 * alpha * gd)
+            approx = (np.real(np.sum(gt * d)) <= np.real((2.0 * ARMIJO_C1 - 1.0) * gd)
+                      and np.real(ft) <= np.real(fx) + ENERGY_GUARD_EPS * abs(np.real(fx)))
             if armijo or approx:
                 break
             if h == MAX_HALVINGS:
@@ -419,8 +443,8 @@ def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
         s = xt - x
         yy = gt - g
         if k < iters - 1:
-            sy = float(np.sum(s * yy))
-            if sy > CURVATURE_EPS * np.sqrt(np.sum(s * s)) * np.sqrt(np.sum(yy * yy)):
+            sy = np.real(np.sum(s * yy))
+            if sy > CURVATURE_EPS * np.sqrt(np.sum(np.real(s) ** 2)) * np.sqrt(np.sum(np.real(yy) ** 2)):
                 S.append(s)
                 Y.append(yy)
                 if len(S) > HISTORY:
@@ -430,13 +454,14 @@ def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
         if pt.degenerate:
             status |= STATUS_DEGENERATE
         alphas.append(alpha)
-        energies.append(fx)
-        gnorms.append(float(np.sqrt(np.sum(g * g))))
+        energies.append(float(np.real(fx)))
+        gnorms.append(float(np.sqrt(np.sum(np.real(g) ** 2))))
     residual = gnorms[-1] / g0n if g0n > 0 else 0.0
     x_new = x + ctr
     v_new = (x - xn) / dt
-    if not (np.all(np.isfinite(x_new)) and np.all(np.isfinite(v_new))):
+    if not (np.all(np.isfinite(np.real(x_new))) and np.all(np.isfinite(np.real(v_new)))):
         status |= STATUS_NONFINITE
+    energies[0] = float(np.real(energies[0]))
     return StepResult(x_new, v_new, alphas, energies, gnorms, residual, status, trials)
 
 

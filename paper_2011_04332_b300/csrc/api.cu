@@ -11,6 +11,7 @@
 #include "api_internal.h"
 #include "npfem_internal.h"
 #include "step_kernel.cuh"
+#include "adjoint.cuh"
 
 using namespace npfem;
 
@@ -60,6 +61,8 @@ struct npfem_batch {
   std::vector<TypeLaunch> launches;
   int* d_counters = nullptr;
   unsigned long long* d_phase = nullptr;  // [kPhases] per-phase cycle counters
+  std::vector<char*> adj_scratch;         // per launch: adjoint workspace (first adjoint call)
+  std::vector<size_t> adj_slot;
   // host-step staging (allocated on first npfem_step_host)
   void* d_x = nullptr;
   void* d_v = nullptr;
@@ -117,7 +120,7 @@ static cudaError_t upload_precision(npfem_cell_type* t, DevTypeView<S>* view, co
   const HostType& H = t->host;
   std::vector<double> inv_mass(H.n);
   for (int i = 0; i < H.n; ++i) inv_mass[i] = 1.0 / H.mass[i];
-  const S *Dinv, *w_tri, *c_hinge, *K0, *w_hinge, *mass, *im, *coef;
+  const S *Dinv, *w_tri, *c_hinge, *K0, *w_hinge, *mass, *im, *coef, *tarea, *hunit;
   cudaError_t e;
   if ((e = t->mem.upload(convert<S>(H.Dinv), &Dinv)) != cudaSuccess) return e;
   if ((e = t->mem.upload(convert<S>(H.w_tri), &w_tri)) != cudaSuccess) return e;
@@ -127,6 +130,10 @@ static cudaError_t upload_precision(npfem_cell_type* t, DevTypeView<S>* view, co
   if ((e = t->mem.upload(convert<S>(H.mass), &mass)) != cudaSuccess) return e;
   if ((e = t->mem.upload(convert<S>(inv_mass), &im)) != cudaSuccess) return e;
   if ((e = t->mem.upload(convert<S>(H.inc_coef), &coef)) != cudaSuccess) return e;
+  if ((e = t->mem.upload(convert<S>(H.area), &tarea)) != cudaSuccess) return e;
+  if ((e = t->mem.upload(convert<S>(H.hinge_unit), &hunit)) != cudaSuccess) return e;
+  view->tri_area = tarea;
+  view->hinge_unit = hunit;
   fill_view<S>(t, view, Dinv, w_tri, c_hinge, K0, w_hinge, mass, im, coef, tris, hinges, inc_ptr, inc_code, perm,
                dinv, fcol, frow, fval, bcol, brow, bval);
   return cudaSuccess;
@@ -300,9 +307,13 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
     L.scratch = static_cast<char*>(scr);
     L.counter = b->d_counters + ti;
     if (L.smem_bytes > 48 * 1024) {
-      if (prec == NPFEM_FP64)
+      if (prec == NPFEM_FP64) {
         e = cudaFuncSetAttribute(npfem_step_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)std::min<size_t>(L.smem_bytes, smem_optin));
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(npfem_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)std::min<size_t>(L.smem_bytes, smem_optin));
+      }
       else
         e = cudaFuncSetAttribute(npfem_step_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)std::min<size_t>(L.smem_bytes, smem_optin));
@@ -364,6 +375,72 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
       npfem_step_kernel<float><<<grid, block, L.smem_bytes, st>>>(t->v32, P, static_cast<float*>(x),
                                                                   static_cast<float*>(v),
                                                                   static_cast<const float*>(f_ext));
+    NPFEM_CUDA_TRY(cudaGetLastError());
+  }
+  return NPFEM_OK;
+}
+
+npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, const void* f_ext,
+                                const int32_t* iters, const npfem_solver_opts* opts, const double* gx_next,
+                                const double* gv_next, double* gx, double* gv, double* gf, double* gw,
+                                int32_t* status_out, void* stream) {
+  if (!b || !opts) return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: null batch or opts");
+  if (b->prec != NPFEM_FP64) return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: needs an FP64 batch");
+  if (b->ncells == 0) return NPFEM_OK;
+  if (!x || !v || !f_ext || !gx_next || !gx || !gv || !gf || !gw)
+    return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: null array");
+  if (opts->iters < 0 || opts->iters > kMaxAdjIters)
+    return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: iteration count must be in [0, 16]");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (b->adj_scratch.empty()) {
+    for (const TypeLaunch& L : b->launches) {
+      const HostType& H = b->types[L.type_index]->host;
+      size_t v3 = (size_t)3 * H.n;
+      size_t nvec = 3 * (size_t)(kMaxAdjIters + 1) + 4 * (size_t)kMaxAdjIters + 2 * (size_t)(kHistory + 1) + 6;
+      size_t bytes = ((sizeof(double) * (nvec * v3 + 3 * kMaxAdjIters) + sizeof(int) * kMaxAdjIters) + 255) &
+                     ~(size_t)255;
+      void* p = nullptr;
+      NPFEM_CUDA_TRY(b->mem.alloc(bytes * (size_t)L.blocks * L.warps_per_block, &p));
+      b->adj_scratch.push_back(static_cast<char*>(p));
+      b->adj_slot.push_back(bytes);
+    }
+  }
+  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size(), st));
+  for (size_t li = 0; li < b->launches.size(); ++li) {
+    const TypeLaunch& L = b->launches[li];
+    const npfem_cell_type* t = b->types[L.type_index];
+    StepParams P;
+    P.ncells_list = L.ncells;
+    P.cell_list = L.cell_list;
+    P.offsets = b->d_offsets;
+    P.n_total = b->n_total;
+    P.iters = iters;
+    P.iters_default = opts->iters;
+    P.residual_out = nullptr;
+    P.status_out = status_out;
+    P.alpha_log = nullptr;
+    P.alpha_log_len = 0;
+    P.queue_counter = L.counter;
+    P.scratch = L.scratch;
+    P.slot_bytes = L.slot_bytes;
+    P.z_in_smem = L.z_in_smem;
+    P.phase_cycles = b->d_phase;
+    AdjParams A;
+    A.gx_next = gx_next;
+    A.gv_next = gv_next;
+    A.gx = gx;
+    A.gv = gv;
+    A.gf = gf;
+    A.gw = gw;
+    A.scratch = b->adj_scratch[li];
+    A.slot_bytes = b->adj_slot[li];
+    const HostType& H = t->host;
+    A.w_mat[0] = 0;
+    A.w_mat[1] = 0;
+    A.w_mat[2] = H.w_area;
+    A.w_mat[3] = H.w_vol;
+    npfem_adjoint_kernel<<<L.blocks, 32 * L.warps_per_block, L.smem_bytes, st>>>(
+        t->v64, P, A, static_cast<const double*>(x), static_cast<const double*>(v), static_cast<const double*>(f_ext));
     NPFEM_CUDA_TRY(cudaGetLastError());
   }
   return NPFEM_OK;

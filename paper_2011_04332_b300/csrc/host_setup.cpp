@@ -331,6 +331,7 @@ int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double
     for (int k = 0; k < 3; ++k) vert_area[tris[3 * t + k]] += area[t] / 3.0;
   }
   H.A0 = A0;
+  H.area = area;
   V3 ctr{0, 0, 0};
   for (auto& p : X) ctr = {ctr.x + p.x / n, ctr.y + p.y / n, ctr.z + p.z / n};
   double V0 = 0.0;
@@ -352,6 +353,7 @@ int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double
   H.c_hinge.resize(4 * E);
   H.K0.resize(4 * E);
   H.w_hinge.resize(E);
+  H.hinge_unit.resize(E);
   for (int e = 0; e < E; ++e) {
     const int* h = &H.hinges[4 * e];
     V3 p0 = X[h[0]], p1 = X[h[1]], p2 = X[h[2]], p3 = X[h[3]];
@@ -370,7 +372,8 @@ int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double
     H.K0[4 * e + 3] = norm(K);
     double aA = 0.5 * norm(cross(sub(p1, p0), sub(p2, p0)));
     double aB = 0.5 * norm(cross(sub(p1, p0), sub(p3, p0)));
-    H.w_hinge[e] = w_bend * 3.0 / (aA + aB);
+    H.hinge_unit[e] = 3.0 / (aA + aB);
+    H.w_hinge[e] = w_bend * H.hinge_unit[e];
   }
 
   // ---- gradient gather lists

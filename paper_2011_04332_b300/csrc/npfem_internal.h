@@ -22,10 +22,12 @@ struct HostType {
   std::vector<int32_t> tris;     // [T][3]
   std::vector<double> Dinv;      // [T][3] (d00, d01, d11) of the upper-triangular Dm^-1
   std::vector<double> w_tri;     // [T]
+  std::vector<double> area;      // [T] rest areas
   std::vector<int32_t> hinges;   // [E][4] (i, j, kA, kB)
   std::vector<double> c_hinge;   // [E][4]
   std::vector<double> K0;        // [E][4] (K0x, K0y, K0z, |K0|)
   std::vector<double> w_hinge;   // [E]
+  std::vector<double> hinge_unit;  // [E] 3/(A_A+A_B): w_hinge per unit bending weight
   std::vector<double> mass;      // [n]
   double A0 = 0, V0 = 0, w_area = 0, w_vol = 0, dt = 0, total_mass = 0;
   // gradient gather: per vertex, corner codes (t*3+slot >= 0) and hinge codes
@@ -62,6 +64,8 @@ struct DevTypeView {
   const S* c_hinge;         // [E][4]
   const S* K0;              // [E][4]
   const S* w_hinge;         // [E]
+  const S* tri_area;        // [T] rest areas (w_tri per unit strain weight)
+  const S* hinge_unit;      // [E] w_hinge per unit bending weight
   const S* mass;            // [n]
   const S* inv_mass;        // [n]
   const int32_t* inc_ptr;   // [n+1]

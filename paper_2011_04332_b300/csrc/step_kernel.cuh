@@ -447,9 +447,26 @@ __device__ void global_solve(const DevTypeView<S>& ty, double* z, bool z_shared,
 }
 
 // ------------------------------------------------------------------ one cell
+// Forward record kept for the adjoint (tape mode): iterates and gradients of every
+// accepted quasi-Newton iteration, step lengths, and per-iteration flags.
+struct TapeRec {
+  double* U;      // [maxk+1][3n] displacement iterates U_k (x_k = x_n + U_k)
+  double* G;      // [maxk+1][3n] gradients g_k
+  double* alpha;  // [maxk] accepted step lengths
+  int* flags;     // [maxk] bit 0: history cleared before the direction; bit 1: pair (s_k, y_k) kept
+};
+constexpr int kTapeReset = 1, kTapeKept = 2;
+
 template <typename S>
+__device__ __forceinline__ void copy_vec(S* dst, const S* src, int len, int lane) {
+  for (int i = lane; i < len; i += 32) dst[i] = src[i];
+}
+
+// One cell, one step.  kTape = true (FP64 only) records the forward pass into `tape`
+// for the adjoint and writes no output state.
+template <typename S, bool kTape = false>
 __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, const CellWs<S>& w, int cell,
-                             S* x, S* v, const S* f, int lane) {
+                             S* x, S* v, const S* f, int lane, const TapeRec* tape = nullptr) {
   const int n = ty.n;
   const int len = 3 * n;
   const int64_t off = P.offsets[cell];
@@ -494,6 +511,10 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
   NPFEM_PHASE_END(t_obj0, kPhObjective, P, lane)
   double fx = ev.energy;
   bool degen = ev.degenerate;
+  if (kTape) {
+    copy_vec<double>(tape->U, (const double*)U, len, lane);
+    copy_vec<double>(tape->G, (const double*)G, len, lane);
+  }
   const double g0n = sqrt(vdot64<S>(G, G, len, lane));
   int status = 0;
   int hcount = 0, hhead = 0;
@@ -535,9 +556,11 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
     __syncwarp();
     double gd = vdot64<S>(G, w.D, len, lane);
     NPFEM_PHASE_END(t_loop2, kPhTwoLoop, P, lane)
+    if (kTape && lane == 0) tape->flags[k] = 0;
     if (!(gd < 0.0)) {  // not a descent direction: drop history, plain PD step
       hcount = 0;
       hhead = 0;
+      if (kTape && lane == 0) tape->flags[k] |= kTapeReset;
       global_solve<S>(ty, w.z, P.z_in_smem != 0, G, w.Q, lane);
       for (int e = lane; e < len; e += 32) w.D[e] = -w.Q[e];
       __syncwarp();
@@ -581,6 +604,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
       }
       const double sy = asy.total(), ss = ass.total(), yy = ayy.total();
       if (sy > kCurvatureEps * sqrt(ss) * sqrt(yy)) {
+        if (kTape && lane == 0) tape->flags[k] |= kTapeKept;
         rho[hhead] = (S)(1.0 / sy);
         hhead = (hhead + 1) % kHistory;
         hcount = hcount < kHistory ? hcount + 1 : kHistory;
@@ -597,9 +621,19 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
     G = GT;
     GT = t2;
     fx = ft;
+    if (kTape) {
+      copy_vec<double>(tape->U + (size_t)(k + 1) * len, (const double*)U, len, lane);
+      copy_vec<double>(tape->G + (size_t)(k + 1) * len, (const double*)G, len, lane);
+      if (lane == 0) tape->alpha[k] = alpha;
+      __syncwarp();
+    }
   }
 
   NPFEM_PHASE_BEGIN(t_write)
+  if (kTape) {
+    __syncwarp();
+    return;
+  }
   // K7: residual, write x_{n+1} = anchor + X + U and v_{n+1} = U / dt
   const double gn = sqrt(vdot64<S>(G, G, len, lane));
   const S idt = (S)(1.0 / dt);

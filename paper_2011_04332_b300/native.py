@@ -75,6 +75,7 @@ def load_library() -> C.CDLL:
         "npfem_step": [vp, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp],
         "npfem_step_host": [vp, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp],
         "npfem_last_error_string": [C.c_char_p, C.c_size_t],
+        "npfem_step_adjoint": [vp, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp, vp, vp, vp, vp, vp],
         "npfem_batch_phase_cycles": [vp, C.POINTER(C.c_uint64), C.c_int32],
         "npfem_step_noalloc": [vp, C.c_int, C.c_int32, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp],
     }
@@ -191,6 +192,19 @@ class Batch:
             stream = stream.cuda_stream
         _check(_lib.npfem_step(self.handle, _ptr(x), _ptr(v), _ptr(f), _ptr(iters), C.byref(opts),
                                _ptr(residual), _ptr(status), C.c_void_p(stream)))
+
+    def step_adjoint(self, x, v, f, gx_next, gv_next, gx, gv, gf, gw, iters=None, iters_default: int = 5,
+                     status=None, stream=None):
+        """npfem_step_adjoint on device tensors (FP64 batches): reverse mode of one step."""
+        opts = _Opts(int(iters_default), 0, None)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        elif not isinstance(stream, int):
+            stream = stream.cuda_stream
+        _check(_lib.npfem_step_adjoint(self.handle, _ptr(x), _ptr(v), _ptr(f), _ptr(iters), C.byref(opts),
+                                       _ptr(gx_next), _ptr(gv_next), _ptr(gx), _ptr(gv), _ptr(gf), _ptr(gw),
+                                       _ptr(status), C.c_void_p(stream)))
 
     PHASES = ("predict", "objective", "two_loop", "solve", "history", "write", "area_volume", "gather")
 

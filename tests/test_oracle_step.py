@@ -148,3 +148,33 @@ def test_history_is_bounded_and_curvature_checked():
     y = np.random.default_rng(3).standard_normal((10, 3))
     y = y + 5 * s                    # make s.y > 0
     assert np.allclose(O.two_loop(y, [s], [y], gs), s)
+
+
+def test_complex_step_derivative_matches_central_differences():
+    """The oracle's forward-mode derivative (complex step through the whole step,
+    forces and weight scales) agrees with central differences of the real step."""
+    m = I.rbc_mesh(1)
+    b = I.single_rbc(subdiv=1)
+    ct = _type(m)
+    x, v, f = b.cell_state(0)
+    f = 30 * f
+    rng = np.random.default_rng(0)
+    df = rng.standard_normal(f.shape) * 1e-3
+    h = 1e-30
+    rc = O.step(ct.rest, ct.solver, x.astype(complex), v.astype(complex), f + 1j * h * df, 5)
+    cs = np.imag(rc.x) / h
+    e = 1e-4
+    fd = (O.step(ct.rest, ct.solver, x, v, f + e * df, 5).x - O.step(ct.rest, ct.solver, x, v, f - e * df, 5).x) / (2 * e)
+    assert np.max(np.abs(cs - fd)) <= 1e-6 * np.max(np.abs(cs))
+    for q in range(4):
+        ws = np.ones(4, complex)
+        ws[q] += 1j * h
+        ctc = _type(m, w_scale=ws)
+        csw = np.imag(O.step(ctc.rest, ctc.solver, x.astype(complex), v.astype(complex), f.astype(complex), 5, ws).x) / h
+        e = 1e-5
+        wp, wm = np.ones(4), np.ones(4)
+        wp[q] += e
+        wm[q] -= e
+        cp, cm = _type(m, w_scale=wp), _type(m, w_scale=wm)
+        fdw = (O.step(cp.rest, cp.solver, x, v, f, 5, wp).x - O.step(cm.rest, cm.solver, x, v, f, 5, wm).x) / (2 * e)
+        assert np.max(np.abs(csw - fdw)) <= 2e-5 * np.max(np.abs(csw)), q
