@@ -247,8 +247,10 @@ def run_ours(args, rank, world, local_rank):
     flops_per_launch = float(np.sum(b.iters * (12.0 * nnz + 3.0 * nv)))
     fp64_peak, fp32_peak = probe_peaks()
     achieved = flops_per_launch / (ms_per_step / 1e3) / 1e12
+    traffic, traffic_how = measured_traffic(args.workload, args.precision)
     roofline = {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak if fp64_peak else None, "traffic": None,
+                "frac": achieved / fp64_peak if fp64_peak else None, "traffic": traffic,
+                "traffic_note": traffic_how,
                 "peak_source": "measured live: FP64 FMA probe (8 chains/thread, 4 CTAs/SM)",
                 "algorithmic": "FP64 flops of the triangular solves: iters*(12*nnz(L)+3n) per cell",
                 "kernel_time": "CUDA events around npfem_step (one memset + one kernel per cell type)"}
@@ -340,6 +342,34 @@ def measure_adjoint(dev, nsteps: int = 40, ckpt_every: int = 20, ncells: int = 2
             "ms_per_forward_step": t_fwd / nsteps,
             "backward_includes": "segment recomputation (one extra forward step per step) + adjoint steps",
             "loss": float(loss.detach()), "grad_w": [float(g) for g in w.grad[0].tolist()]}
+
+
+def kernel_source_hash() -> str:
+    """SHA-256 over the CUDA/C++ sources of the library (detects a changed kernel)."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2011_04332_b300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".cpp", ".h")):
+            h.update(name.encode())
+            h.update(open(os.path.join(d, name), "rb").read())
+    return h.hexdigest()
+
+
+def measured_traffic(workload: str, precision: str):
+    """DRAM bytes per launch of the step kernel from profiles/traffic.json, only if it was
+    captured for the current kernel sources and this workload/precision; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(p))
+    except (OSError, ValueError):
+        return None, "no traffic record"
+    if rec.get("kernel_src_sha256") != kernel_source_hash():
+        return None, "kernel changed since the ncu capture"
+    ent = rec.get("entries", {}).get(f"{workload}/{precision}")
+    if not ent:
+        return None, "no capture for this workload"
+    return ent["dram_bytes_per_launch"], ent["how"]
 
 
 def probe_peaks():
