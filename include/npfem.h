@@ -68,6 +68,8 @@ typedef int npfem_status;
 #define NPFEM_CELL_LINESEARCH_FAIL 1  /* no acceptable step after 20 halvings (last trial kept) */
 #define NPFEM_CELL_DEGENERATE 2       /* a triangle collapsed (det F^T F <= 1e-30) */
 #define NPFEM_CELL_NONFINITE 4        /* NaN/Inf in the result */
+#define NPFEM_CELL_ITER_LIMIT 8       /* iteration count above the supported bound (adjoint: 16;
+                                         split step: opts->max_iters); the cell stopped there */
 
 typedef enum { NPFEM_FP64 = 0, NPFEM_FP32FORM = 1 } npfem_precision;
 
@@ -93,6 +95,8 @@ typedef struct {
   int32_t iters;           /* quasi-Newton iterations per cell when iters array is NULL */
   int32_t alpha_log_len;   /* entries per cell in alpha_log (0 = no log) */
   double* alpha_log;       /* device [ncells][alpha_log_len] accepted step lengths, or NULL */
+  int32_t max_iters;       /* upper bound of the per-cell counts of an iters array (split mode
+                              launches that many iterations; 0 = unknown: fused mode) */
 } npfem_solver_opts;
 
 typedef struct npfem_cell_type npfem_cell_type;
@@ -162,6 +166,35 @@ npfem_status npfem_step_adjoint(npfem_batch* batch, const void* x, const void* v
                                 const int32_t* iters, const npfem_solver_opts* opts,
                                 const double* gx_next, const double* gv_next, double* gx, double* gv,
                                 double* gf, double* gw, int32_t* status_out, void* stream);
+
+/* Launch shape of the cells of one type (the autotuner's knobs): warps per CTA
+ * (1..4; one warp advances one cell), CTAs per SM (1..16), whether each warp's FP64
+ * solve vector lives in shared memory (1) or in the workspace (0), and whether the
+ * three coordinates share each triangular sweep (solve_per_coord = 0, vector of
+ * 24*(n+1) bytes) or are swept one after another (1, vector of 8*(n+1) bytes).
+ * Results do not depend on the shape.  Reallocates that type's workspace; synchronises
+ * the device.  Default: 4 warps, 3 CTAs/SM, shared memory when four interleaved
+ * vectors fit in 72 KB.  Errors: INVALID_ARG, UNSUPPORTED (vectors exceed shared
+ * memory), OOM.  npfem_batch_get_launch fills shape[5] = {warps per CTA, CTAs per SM,
+ * solve in shared memory, per-coordinate solve, grid size}. */
+npfem_status npfem_batch_set_launch(npfem_batch* batch, int32_t type_index, int32_t warps_per_block,
+                                    int32_t blocks_per_sm, int32_t solve_in_shared, int32_t solve_per_coord);
+npfem_status npfem_batch_get_launch(const npfem_batch* batch, int32_t type_index, int32_t* shape);
+
+/* Execution mode of npfem_step for a batch.  mode 1 (default, "split"): per cell type
+ * one kernel for the prediction and first evaluation, then per iteration one kernel for
+ * the FP64 global solves and one for the rest of the iteration (all asynchronous on the
+ * stream; needs the iteration bound: opts->iters without an iters array, else
+ * opts->max_iters in 1..32; a cell whose count exceeds it stops there and gets status
+ * bit 8).  mode 0 ("fused"): one persistent kernel per cell type (any iteration count;
+ * also used by split-mode batches when the bound is unknown).  Results are identical.
+ * npfem_batch_set_split_launch sets, per type, shape[6] = {warps per CTA, CTAs per SM of
+ * the iteration kernels; warps per CTA, CTAs per SM, solve vector in shared memory,
+ * per-coordinate solve of the solve kernel}; npfem_batch_get_split_launch returns those
+ * six values plus the mode in shape[6]. */
+npfem_status npfem_batch_set_mode(npfem_batch* batch, int32_t mode);
+npfem_status npfem_batch_set_split_launch(npfem_batch* batch, int32_t type_index, const int32_t* shape);
+npfem_status npfem_batch_get_split_launch(const npfem_batch* batch, int32_t type_index, int32_t* shape);
 
 /* Per-phase telemetry of the batch's steps since creation or the last reset: SM
  * clock cycles summed over all warps, in the order prediction, objective evaluation,

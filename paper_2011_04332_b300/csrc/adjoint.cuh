@@ -356,7 +356,7 @@ __device__ void reverse_cell(const DevTypeView<double>& ty, const StepParams& P,
       __syncwarp();
       abar[t] = 0.0;
     }
-    global_solve<double>(ty, w.z, P.z_in_smem != 0, aw.Qs + (size_t)h * len, aw.Rs, lane);
+    global_solve<double>(ty, w.z, P.z_in_smem != 0, aw.Qs + (size_t)h * len, aw.Rs, lane, P.solve_per_coord != 0);
     for (int u = 0; u < h; ++u) {
       const int t = h - 1 - u, i = plist[t];
       const double* si = aw.sP + (size_t)i * len;
@@ -390,7 +390,7 @@ __device__ void reverse_cell(const DevTypeView<double>& ty, const StepParams& P,
       __syncwarp();
     }
     // r_0 = A^-1 q_h: dL/dq_h = A^-1 dL/dr_0; dL/dw via dA/dw
-    global_solve<double>(ty, w.z, P.z_in_smem != 0, aw.RB, aw.QB, lane);
+    global_solve<double>(ty, w.z, P.z_in_smem != 0, aw.RB, aw.QB, lane, P.solve_per_coord != 0);
     {
       double fs, fb;
       matrix_weight_forms(ty, aw.QB, aw.Rs, &fs, &fb, lane);
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(128) npfem_adjoint_kernel(DevTypeView<double> 
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  double* zs = P.z_in_smem ? smem_z + (size_t)wib * 3 * (ty.n + 1) : nullptr;
+  double* zs = P.z_in_smem ? smem_z + (size_t)wib * (P.solve_per_coord ? 1 : 3) * (ty.n + 1) : nullptr;
   CellWs<double> w = carve<double>(P.scratch + (size_t)slot * P.slot_bytes, ty.n, ty.T, ty.E, zs);
   AdjWs aw = carve_adj(A.scratch + (size_t)slot * A.slot_bytes, ty.n);
   for (;;) {

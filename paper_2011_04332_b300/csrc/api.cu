@@ -12,6 +12,7 @@
 #include "npfem_internal.h"
 #include "step_kernel.cuh"
 #include "adjoint.cuh"
+#include "split_kernels.cuh"
 
 using namespace npfem;
 
@@ -42,11 +43,18 @@ struct TypeLaunch {
   int ncells;
   const int32_t* cell_list;  // device
   int* counter;              // device
-  char* scratch;
+  char* scratch;             // owned: slot_bytes per warp slot
   size_t slot_bytes;
-  int blocks, warps_per_block;
+  int blocks, warps_per_block, blocks_per_sm;
   int z_in_smem;
+  int solve_per_coord;
   size_t smem_bytes;
+  char* adj_scratch;         // owned: adjoint workspace (first adjoint call)
+  size_t adj_slot;
+  // split mode: per-cell workspace and the shapes of k_begin/k_iter and k_solve
+  char* cell_scratch;        // owned: cell_slot bytes per cell (first split step)
+  size_t cell_slot;
+  int it_wpb, it_bps, sv_wpb, sv_bps, sv_smem, sv_percoord;
 };
 
 struct npfem_batch {
@@ -61,8 +69,23 @@ struct npfem_batch {
   std::vector<TypeLaunch> launches;
   int* d_counters = nullptr;
   unsigned long long* d_phase = nullptr;  // [kPhases] per-phase cycle counters
-  std::vector<char*> adj_scratch;         // per launch: adjoint workspace (first adjoint call)
-  std::vector<size_t> adj_slot;
+  int sms = 148, smem_optin = 0;
+  int mode = 1;  // 0: fused persistent kernel, 1: split kernels (k_begin, k_solve, k_iter)
+  // split mode with several cell types: one internal stream per type, forked from and
+  // joined back into the caller's stream with events (also under stream capture)
+  std::vector<cudaStream_t> type_streams;
+  std::vector<cudaEvent_t> type_events;
+  cudaEvent_t fork_event = nullptr;
+  ~npfem_batch() {
+    for (cudaStream_t s : type_streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : type_events) cudaEventDestroy(e);
+    if (fork_event) cudaEventDestroy(fork_event);
+    for (TypeLaunch& L : launches) {
+      if (L.scratch) cudaFree(L.scratch);
+      if (L.adj_scratch) cudaFree(L.adj_scratch);
+      if (L.cell_scratch) cudaFree(L.cell_scratch);
+    }
+  }
   // host-step staging (allocated on first npfem_step_host)
   void* d_x = nullptr;
   void* d_v = nullptr;
@@ -140,6 +163,169 @@ static cudaError_t upload_precision(npfem_cell_type* t, DevTypeView<S>* view, co
 }
 
 npfem_status npfem_internal_fail(npfem_status code, const std::string& msg) { return fail(code, msg); }
+
+// Launch shape of one cell type: warps per CTA (1..4), CTAs per SM, and whether each
+// warp's FP64 solve vector lives in shared memory.  (Re)allocates the per-warp workspace.
+static npfem_status configure_launch(npfem_batch* b, TypeLaunch& L, int wpb, int bps, int zsmem, int per_coord) {
+  const HostType& H = b->types[L.type_index]->host;
+  if (wpb < 1 || wpb > 4 || bps < 1 || bps > 16) return fail(NPFEM_ERR_INVALID_ARG, "launch: warps/CTA in 1..4, CTAs/SM in 1..16");
+  const size_t ssize = b->prec == NPFEM_FP64 ? sizeof(double) : sizeof(float);
+  const size_t zbytes = sizeof(double) * (per_coord ? 1 : 3) * ((size_t)H.n + 1);
+  const size_t smem = zsmem ? zbytes * wpb : 0;
+  if (smem > (size_t)b->smem_optin) return fail(NPFEM_ERR_UNSUPPORTED, "launch: solve vectors exceed shared memory");
+  size_t v = (size_t)3 * H.n;
+  size_t bytes = ssize * ((8 + 2 * kHistory) * v + 9 * (size_t)H.T + 3 * (size_t)H.E);
+  bytes = (bytes + 255) & ~(size_t)255;
+  if (!zsmem) bytes += zbytes;
+  bytes = (bytes + 255) & ~(size_t)255;
+  const int blocks = std::max(1, std::min<int>(b->sms * bps, (L.ncells + wpb - 1) / wpb));
+  void* scr = nullptr;
+  cudaError_t e = cudaMalloc(&scr, std::max<size_t>(16, bytes * (size_t)blocks * wpb));
+  if (e != cudaSuccess) return fail(NPFEM_ERR_OOM, std::string("launch: workspace: ") + cudaGetErrorString(e));
+  if (L.scratch) cudaFree(L.scratch);
+  if (L.adj_scratch) cudaFree(L.adj_scratch);
+  L.scratch = static_cast<char*>(scr);
+  L.adj_scratch = nullptr;
+  L.adj_slot = 0;
+  L.slot_bytes = bytes;
+  L.blocks = blocks;
+  L.warps_per_block = wpb;
+  L.blocks_per_sm = bps;
+  L.z_in_smem = zsmem ? 1 : 0;
+  L.solve_per_coord = per_coord ? 1 : 0;
+  L.smem_bytes = smem;
+  return NPFEM_OK;
+}
+
+// Default split-mode shapes by size class, from autotuning on B300 (homogeneous 642-vertex
+// batch and the mixed 162/642/2562-vertex batch, FP32 form).
+static void default_split_shape(TypeLaunch& L, int n) {
+  if (n <= 256) {         // platelet-sized: 16 iteration warps/SM; 14 solve warps/SM, interleaved in smem
+    L.it_wpb = 4, L.it_bps = 4;
+    L.sv_wpb = 2, L.sv_bps = 7, L.sv_smem = 1, L.sv_percoord = 0;
+  } else if (n <= 1024) {  // 642-vertex RBC: 14 iteration warps/SM; 32 solve warps/SM, per coordinate in smem
+    L.it_wpb = 2, L.it_bps = 7;
+    L.sv_wpb = 2, L.sv_bps = 16, L.sv_smem = 1, L.sv_percoord = 1;
+  } else {                 // 2562-vertex RBC: 16 warps/SM for both, solve vector in the workspace
+    L.it_wpb = 2, L.it_bps = 8;
+    L.sv_wpb = 2, L.sv_bps = 8, L.sv_smem = 0, L.sv_percoord = 0;
+  }
+  const size_t zb = sizeof(double) * (L.sv_percoord ? 1 : 3) * ((size_t)n + 1);
+  if (L.sv_smem && (size_t)L.sv_bps * L.sv_wpb * zb > 220 * 1024) L.sv_smem = 0;
+}
+
+static npfem_status ensure_cell_scratch(npfem_batch* b, TypeLaunch& L) {
+  if (L.cell_scratch) return NPFEM_OK;
+  const HostType& H = b->types[L.type_index]->host;
+  const size_t ssize = b->prec == NPFEM_FP64 ? sizeof(double) : sizeof(float);
+  size_t v = (size_t)3 * H.n;
+  size_t bytes = ssize * ((8 + 2 * kHistory) * v + 9 * (size_t)H.T + 3 * (size_t)H.E);
+  bytes = (bytes + 255) & ~(size_t)255;
+  bytes += sizeof(double) * 3 * ((size_t)H.n + 1);
+  bytes = kStateBytes + ((bytes + 255) & ~(size_t)255);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes * (size_t)L.ncells);
+  if (e != cudaSuccess) return fail(NPFEM_ERR_OOM, std::string("split step: workspace: ") + cudaGetErrorString(e));
+  L.cell_scratch = static_cast<char*>(p);
+  L.cell_slot = bytes;
+  return NPFEM_OK;
+}
+
+template <typename S>
+static npfem_status launch_split(npfem_batch* b, const npfem_cell_type* t, const TypeLaunch& L, StepParams P, int kind,
+                                 int it, int max_iters, S* x, S* v, const S* f, const DevTypeView<S>& view,
+                                 cudaStream_t st) {
+  P.scratch = L.cell_scratch;
+  P.slot_bytes = L.cell_slot;
+  if (kind == 0) {
+    P.queue_counter = L.counter;
+    int grid = std::max(1, std::min<int>(b->sms * L.it_bps, (L.ncells + L.it_wpb - 1) / L.it_wpb));
+    npfem_k_begin<S><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, max_iters, x, v, f);
+  } else if (kind == 1) {
+    P.queue_counter = L.counter + 1 + 2 * it;
+    P.z_in_smem = L.sv_smem;
+    P.solve_per_coord = L.sv_percoord;
+    const HostType& H = t->host;
+    size_t smem = L.sv_smem ? sizeof(double) * (L.sv_percoord ? 1 : 3) * ((size_t)H.n + 1) * L.sv_wpb : 0;
+    int grid = std::max(1, std::min<int>(b->sms * L.sv_bps, (L.ncells + L.sv_wpb - 1) / L.sv_wpb));
+    npfem_k_solve<S><<<grid, 32 * L.sv_wpb, smem, st>>>(view, P);
+  } else {
+    P.queue_counter = L.counter + 2 + 2 * it;
+    int grid = std::max(1, std::min<int>(b->sms * L.it_bps, (L.ncells + L.it_wpb - 1) / L.it_wpb));
+    npfem_k_iter<S><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, x, v);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(NPFEM_ERR_CUDA, std::string("split step launch: ") + cudaGetErrorString(e));
+  return NPFEM_OK;
+}
+
+static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_ext, const int32_t* iters,
+                               const npfem_solver_opts* opts, int max_iters, double* residual_out,
+                               int32_t* status_out, cudaStream_t st) {
+  for (TypeLaunch& L : b->launches) {
+    npfem_status rc = ensure_cell_scratch(b, L);
+    if (rc != NPFEM_OK) return rc;
+  }
+  const size_t nl = b->launches.size();
+  const bool fork = nl > 1;
+  if (fork && b->type_streams.size() < nl) {
+    if (!b->fork_event) NPFEM_CUDA_TRY(cudaEventCreateWithFlags(&b->fork_event, cudaEventDisableTiming));
+    while (b->type_streams.size() < nl) {
+      cudaStream_t s2;
+      cudaEvent_t e2;
+      NPFEM_CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+      NPFEM_CUDA_TRY(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+      b->type_streams.push_back(s2);
+      b->type_events.push_back(e2);
+    }
+  }
+  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kSplitCounters, st));
+  if (fork) {
+    NPFEM_CUDA_TRY(cudaEventRecord(b->fork_event, st));
+    for (size_t li = 0; li < nl; ++li) NPFEM_CUDA_TRY(cudaStreamWaitEvent(b->type_streams[li], b->fork_event, 0));
+  }
+  for (size_t li = 0; li < nl; ++li) {
+    const TypeLaunch& L = b->launches[li];
+    const npfem_cell_type* t = b->types[L.type_index];
+    cudaStream_t ts = fork ? b->type_streams[li] : st;
+    StepParams P{};
+    P.ncells_list = L.ncells;
+    P.cell_list = L.cell_list;
+    P.offsets = b->d_offsets;
+    P.n_total = b->n_total;
+    P.iters = iters;
+    P.iters_default = opts->iters;
+    P.residual_out = residual_out;
+    P.status_out = status_out;
+    P.alpha_log = opts->alpha_log;
+    P.alpha_log_len = opts->alpha_log_len;
+    P.phase_cycles = b->d_phase;
+    for (int kind = 0, it = 0; kind == 0 || it < max_iters;) {
+      npfem_status rc;
+      if (b->prec == NPFEM_FP64)
+        rc = launch_split<double>(b, t, L, P, kind, it, max_iters, static_cast<double*>(x), static_cast<double*>(v),
+                                  static_cast<const double*>(f_ext), t->v64, ts);
+      else
+        rc = launch_split<float>(b, t, L, P, kind, it, max_iters, static_cast<float*>(x), static_cast<float*>(v),
+                                 static_cast<const float*>(f_ext), t->v32, ts);
+      if (rc != NPFEM_OK) return rc;
+      if (kind == 0) {
+        kind = 1;
+      } else if (kind == 1) {
+        kind = 2;
+      } else {
+        kind = 1;
+        ++it;
+      }
+    }
+  }
+  if (fork)
+    for (size_t li = 0; li < nl; ++li) {
+      NPFEM_CUDA_TRY(cudaEventRecord(b->type_events[li], b->type_streams[li]));
+      NPFEM_CUDA_TRY(cudaStreamWaitEvent(st, b->type_events[li], 0));
+    }
+  return NPFEM_OK;
+}
 
 extern "C" {
 
@@ -263,7 +449,7 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
   cudaError_t e = b->mem.upload(b->offsets, &b->d_offsets);
   if (e != cudaSuccess) return cleanup(NPFEM_ERR_CUDA, std::string("batch_create: ") + cudaGetErrorString(e));
   void* cnt = nullptr;
-  e = b->mem.alloc(sizeof(int) * ntypes, &cnt);
+  e = b->mem.alloc(sizeof(int) * ntypes * kSplitCounters, &cnt);
   if (e != cudaSuccess) return cleanup(NPFEM_ERR_OOM, std::string("batch_create: ") + cudaGetErrorString(e));
   b->d_counters = static_cast<int*>(cnt);
   void* ph = nullptr;
@@ -276,6 +462,18 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  b->sms = sms;
+  b->smem_optin = smem_optin;
+  e = cudaFuncSetAttribute(npfem_step_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(npfem_step_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(npfem_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(npfem_k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(npfem_k_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  if (e != cudaSuccess) return cleanup(NPFEM_ERR_CUDA, std::string("batch_create: ") + cudaGetErrorString(e));
   const size_t ssize = prec == NPFEM_FP64 ? sizeof(double) : sizeof(float);
   for (int ti = 0; ti < ntypes; ++ti) {
     std::vector<int32_t> list;
@@ -286,38 +484,26 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
     TypeLaunch L{};
     L.type_index = ti;
     L.ncells = (int)list.size();
-    L.warps_per_block = 4;
-    size_t zbytes = sizeof(double) * 3 * ((size_t)H.n + 1);
-    L.z_in_smem = (zbytes * L.warps_per_block <= 72 * 1024) ? 1 : 0;
-    const int blocks_per_sm = 3;
-    L.blocks = std::min<int>(sms * blocks_per_sm, (L.ncells + L.warps_per_block - 1) / L.warps_per_block);
-    L.smem_bytes = L.z_in_smem ? zbytes * L.warps_per_block : 0;
-    size_t v = (size_t)3 * H.n;
-    size_t bytes = ssize * ((8 + 2 * kHistory) * v + 9 * (size_t)H.T + 3 * (size_t)H.E);
-    bytes = (bytes + 255) & ~(size_t)255;
-    if (!L.z_in_smem) bytes += zbytes;
-    L.slot_bytes = (bytes + 255) & ~(size_t)255;
     const int32_t* dl = nullptr;
     if ((e = b->mem.upload(list, &dl)) != cudaSuccess)
       return cleanup(NPFEM_ERR_OOM, std::string("batch_create: ") + cudaGetErrorString(e));
     L.cell_list = dl;
-    void* scr = nullptr;
-    if ((e = b->mem.alloc(L.slot_bytes * (size_t)L.blocks * L.warps_per_block, &scr)) != cudaSuccess)
-      return cleanup(NPFEM_ERR_OOM, std::string("batch_create: workspace: ") + cudaGetErrorString(e));
-    L.scratch = static_cast<char*>(scr);
-    L.counter = b->d_counters + ti;
-    if (L.smem_bytes > 48 * 1024) {
-      if (prec == NPFEM_FP64) {
-        e = cudaFuncSetAttribute(npfem_step_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)std::min<size_t>(L.smem_bytes, smem_optin));
-        if (e == cudaSuccess)
-          e = cudaFuncSetAttribute(npfem_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)std::min<size_t>(L.smem_bytes, smem_optin));
+    L.counter = b->d_counters + ti * kSplitCounters;
+    // default shape: 4 warps per CTA and 3 CTAs per SM, solve vectors in shared memory
+    // when four of them fit in 72 KB (n <= 767), else in the workspace
+    const size_t zbytes = sizeof(double) * 3 * ((size_t)H.n + 1);
+    const int zs = zbytes * 4 <= 72 * 1024 ? 1 : 0;
+    default_split_shape(L, H.n);
+    npfem_status rc = configure_launch(b, L, 4, 3, zs, 0);
+    if (rc != NPFEM_OK) {
+      for (TypeLaunch& P : b->launches) {
+        if (P.scratch) cudaFree(P.scratch);
+        P.scratch = nullptr;
       }
-      else
-        e = cudaFuncSetAttribute(npfem_step_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)std::min<size_t>(L.smem_bytes, smem_optin));
-      if (e != cudaSuccess) return cleanup(NPFEM_ERR_CUDA, std::string("batch_create: ") + cudaGetErrorString(e));
+      if (L.scratch) cudaFree(L.scratch);
+      std::string msg = g_last_error;
+      delete b;
+      return fail(rc, msg);
     }
     b->launches.push_back(L);
   }
@@ -347,7 +533,11 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
   if (opts->alpha_log_len < 0 || (opts->alpha_log_len > 0 && !opts->alpha_log))
     return fail(NPFEM_ERR_INVALID_ARG, "step: bad alpha log");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size(), st));
+  if (b->mode == 1 && (iters == nullptr || opts->max_iters > 0)) {
+    const int max_iters = iters ? opts->max_iters : opts->iters;
+    if (max_iters <= kSplitMaxIters) return step_split(b, x, v, f_ext, iters, opts, max_iters, residual_out, status_out, st);
+  }
+  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kSplitCounters, st));
   for (const TypeLaunch& L : b->launches) {
     const npfem_cell_type* t = b->types[L.type_index];
     StepParams P;
@@ -365,6 +555,7 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
     P.scratch = L.scratch;
     P.slot_bytes = L.slot_bytes;
     P.z_in_smem = L.z_in_smem;
+    P.solve_per_coord = L.solve_per_coord;
     P.phase_cycles = b->d_phase;
     dim3 grid(L.blocks), block(32 * L.warps_per_block);
     if (b->prec == NPFEM_FP64)
@@ -392,20 +583,19 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
   if (opts->iters < 0 || opts->iters > kMaxAdjIters)
     return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: iteration count must be in [0, 16]");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (b->adj_scratch.empty()) {
-    for (const TypeLaunch& L : b->launches) {
-      const HostType& H = b->types[L.type_index]->host;
-      size_t v3 = (size_t)3 * H.n;
-      size_t nvec = 3 * (size_t)(kMaxAdjIters + 1) + 4 * (size_t)kMaxAdjIters + 2 * (size_t)(kHistory + 1) + 6;
-      size_t bytes = ((sizeof(double) * (nvec * v3 + 3 * kMaxAdjIters) + sizeof(int) * kMaxAdjIters) + 255) &
-                     ~(size_t)255;
-      void* p = nullptr;
-      NPFEM_CUDA_TRY(b->mem.alloc(bytes * (size_t)L.blocks * L.warps_per_block, &p));
-      b->adj_scratch.push_back(static_cast<char*>(p));
-      b->adj_slot.push_back(bytes);
-    }
+  for (TypeLaunch& L : b->launches) {
+    if (L.adj_scratch) continue;
+    const HostType& H = b->types[L.type_index]->host;
+    size_t v3 = (size_t)3 * H.n;
+    size_t nvec = 3 * (size_t)(kMaxAdjIters + 1) + 4 * (size_t)kMaxAdjIters + 2 * (size_t)(kHistory + 1) + 6;
+    size_t bytes = ((sizeof(double) * (nvec * v3 + 3 * kMaxAdjIters) + sizeof(int) * kMaxAdjIters) + 255) &
+                   ~(size_t)255;
+    void* p = nullptr;
+    NPFEM_CUDA_TRY(cudaMalloc(&p, bytes * (size_t)L.blocks * L.warps_per_block));
+    L.adj_scratch = static_cast<char*>(p);
+    L.adj_slot = bytes;
   }
-  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size(), st));
+  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kSplitCounters, st));
   for (size_t li = 0; li < b->launches.size(); ++li) {
     const TypeLaunch& L = b->launches[li];
     const npfem_cell_type* t = b->types[L.type_index];
@@ -424,6 +614,7 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     P.scratch = L.scratch;
     P.slot_bytes = L.slot_bytes;
     P.z_in_smem = L.z_in_smem;
+    P.solve_per_coord = L.solve_per_coord;
     P.phase_cycles = b->d_phase;
     AdjParams A;
     A.gx_next = gx_next;
@@ -432,8 +623,8 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     A.gv = gv;
     A.gf = gf;
     A.gw = gw;
-    A.scratch = b->adj_scratch[li];
-    A.slot_bytes = b->adj_slot[li];
+    A.scratch = L.adj_scratch;
+    A.slot_bytes = L.adj_slot;
     const HostType& H = t->host;
     A.w_mat[0] = 0;
     A.w_mat[1] = 0;
@@ -444,6 +635,74 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     NPFEM_CUDA_TRY(cudaGetLastError());
   }
   return NPFEM_OK;
+}
+
+npfem_status npfem_batch_set_launch(npfem_batch* b, int32_t type_index, int32_t warps_per_block,
+                                    int32_t blocks_per_sm, int32_t solve_in_shared, int32_t solve_per_coord) {
+  if (!b) return fail(NPFEM_ERR_INVALID_ARG, "batch_set_launch: null batch");
+  NPFEM_CUDA_TRY(cudaDeviceSynchronize());
+  for (TypeLaunch& L : b->launches)
+    if (L.type_index == type_index)
+      return configure_launch(b, L, warps_per_block, blocks_per_sm, solve_in_shared, solve_per_coord);
+  return fail(NPFEM_ERR_INVALID_ARG, "batch_set_launch: no cells of that type in the batch");
+}
+
+npfem_status npfem_batch_get_launch(const npfem_batch* b, int32_t type_index, int32_t* shape) {
+  if (!b || !shape) return fail(NPFEM_ERR_INVALID_ARG, "batch_get_launch: null argument");
+  for (const TypeLaunch& L : b->launches)
+    if (L.type_index == type_index) {
+      shape[0] = L.warps_per_block;
+      shape[1] = L.blocks_per_sm;
+      shape[2] = L.z_in_smem;
+      shape[3] = L.solve_per_coord;
+      shape[4] = L.blocks;
+      return NPFEM_OK;
+    }
+  return fail(NPFEM_ERR_INVALID_ARG, "batch_get_launch: no cells of that type in the batch");
+}
+
+npfem_status npfem_batch_set_mode(npfem_batch* b, int32_t mode) {
+  if (!b || (mode != 0 && mode != 1)) return fail(NPFEM_ERR_INVALID_ARG, "batch_set_mode: mode must be 0 or 1");
+  b->mode = mode;
+  return NPFEM_OK;
+}
+
+npfem_status npfem_batch_set_split_launch(npfem_batch* b, int32_t type_index, const int32_t* shape) {
+  if (!b || !shape) return fail(NPFEM_ERR_INVALID_ARG, "batch_set_split_launch: null argument");
+  for (TypeLaunch& L : b->launches)
+    if (L.type_index == type_index) {
+      const HostType& H = b->types[L.type_index]->host;
+      if (shape[0] < 1 || shape[0] > 4 || shape[1] < 1 || shape[1] > 16 || shape[2] < 1 || shape[2] > 4 ||
+          shape[3] < 1 || shape[3] > 16)
+        return fail(NPFEM_ERR_INVALID_ARG, "batch_set_split_launch: warps/CTA in 1..4, CTAs/SM in 1..16");
+      size_t smem = shape[4] ? sizeof(double) * (shape[5] ? 1 : 3) * ((size_t)H.n + 1) * shape[2] : 0;
+      if (smem > (size_t)b->smem_optin)
+        return fail(NPFEM_ERR_UNSUPPORTED, "batch_set_split_launch: solve vectors exceed shared memory");
+      L.it_wpb = shape[0];
+      L.it_bps = shape[1];
+      L.sv_wpb = shape[2];
+      L.sv_bps = shape[3];
+      L.sv_smem = shape[4] ? 1 : 0;
+      L.sv_percoord = shape[5] ? 1 : 0;
+      return NPFEM_OK;
+    }
+  return fail(NPFEM_ERR_INVALID_ARG, "batch_set_split_launch: no cells of that type in the batch");
+}
+
+npfem_status npfem_batch_get_split_launch(const npfem_batch* b, int32_t type_index, int32_t* shape) {
+  if (!b || !shape) return fail(NPFEM_ERR_INVALID_ARG, "batch_get_split_launch: null argument");
+  for (const TypeLaunch& L : b->launches)
+    if (L.type_index == type_index) {
+      shape[0] = L.it_wpb;
+      shape[1] = L.it_bps;
+      shape[2] = L.sv_wpb;
+      shape[3] = L.sv_bps;
+      shape[4] = L.sv_smem;
+      shape[5] = L.sv_percoord;
+      shape[6] = b->mode;
+      return NPFEM_OK;
+    }
+  return fail(NPFEM_ERR_INVALID_ARG, "batch_get_split_launch: no cells of that type in the batch");
 }
 
 npfem_status npfem_batch_phase_cycles(npfem_batch* b, uint64_t* cycles, int32_t reset) {

@@ -1,0 +1,331 @@
+// The batched step as a sequence of kernels (split mode): the same per-cell arithmetic as
+// process_cell, cut at the global solves so that the FP64 triangular sweeps run in a kernel
+// of their own.
+//
+//   k_begin   K1 prediction, first objective evaluation, first half of the two-loop (Q = g)
+//   k_solve   Q <- A^-1 Q, FP64 LDL^T sweeps with the solve vector in shared memory
+//   k_iter    second half of the two-loop, line search, history update, then either the
+//             first half of the next iteration's two-loop or the K7 write-back
+//
+// One step launches k_begin once and (k_solve, k_iter) max_iters times per cell type.
+// Between kernels each cell's state lives in its own workspace slot (a CellState header
+// followed by the CellWs vectors and a workspace copy of the solve vector, used only by
+// the rare non-descent reset inside k_iter).  A warp advances one cell per queue item;
+// cells whose iteration budget is exhausted are skipped.
+#pragma once
+#include "step_kernel.cuh"
+
+namespace npfem {
+
+constexpr int kSplitMaxIters = 32;
+constexpr int kSplitCounters = 2 + 2 * kSplitMaxIters;  // queue counters per cell type and step
+constexpr size_t kStateBytes = 256;
+
+template <typename S>
+struct CellState {
+  double fx, g0n;
+  int k, iters, hcount, hhead, status, degen, cur;  // cur: 1 when UT/GT hold the current iterate
+  S rho[kHistory], aco[kHistory];
+  S cvol[3];
+};
+static_assert(sizeof(CellState<double>) <= kStateBytes, "cell state header too large");
+
+struct SplitCtx {
+  char* base;
+  int cell;
+};
+
+template <typename S>
+__device__ __forceinline__ CellWs<S> split_ws(char* base, const DevTypeView<S>& ty) {
+  return carve<S>(base + kStateBytes, ty.n, ty.T, ty.E, nullptr);
+}
+
+// First half of the two-loop recursion: Q = g, newest -> oldest pairs.
+template <typename S>
+__device__ __forceinline__ void two_loop_first(const CellWs<S>& w, CellState<S>* st, const S* G, int len,
+                                               int lane) {
+  for (int i = lane; i < len; i += 32) w.Q[i] = G[i];
+  __syncwarp();
+  for (int q = 0; q < st->hcount; ++q) {
+    int i = (st->hhead - 1 - q + kHistory) % kHistory;
+    const S* si = w.hs + (size_t)i * len;
+    const S* yi = w.hy + (size_t)i * len;
+    S a = st->rho[i] * vdot<S>(si, w.Q, len, lane);
+    if (lane == 0) st->aco[i] = a;
+    for (int e = lane; e < len; e += 32) w.Q[e] -= a * yi[e];
+    __syncwarp();
+  }
+}
+
+// K7: residual, x_{n+1} = anchor + X + U, v_{n+1} = U / dt, status.
+template <typename S>
+__device__ void split_finalize(const DevTypeView<S>& ty, const StepParams& P, const CellWs<S>& w, CellState<S>* st,
+                               const S* U, const S* G, int cell, S* x, S* v, int lane) {
+  const int n = ty.n, len = 3 * n;
+  const int64_t off = P.offsets[cell], Nt = P.n_total;
+  NPFEM_PHASE_BEGIN(t_write)
+  const S ax = x[off], ay = x[Nt + off], az = x[2 * Nt + off];
+  const double gn = sqrt(vdot64<S>(G, G, len, lane));
+  const S idt = (S)(1.0 / ty.dt);
+  bool bad = false;
+  __syncwarp();
+  for (int k = lane; k < n; k += 32) {
+    double nx = (double)ax + ((double)w.X[3 * k] + (double)U[3 * k]);
+    double ny = (double)ay + ((double)w.X[3 * k + 1] + (double)U[3 * k + 1]);
+    double nz = (double)az + ((double)w.X[3 * k + 2] + (double)U[3 * k + 2]);
+    S vx = U[3 * k] * idt, vy = U[3 * k + 1] * idt, vz = U[3 * k + 2] * idt;
+    bad = bad || !isfinite(nx) || !isfinite(ny) || !isfinite(nz) || !isfinite((double)vx) ||
+          !isfinite((double)vy) || !isfinite((double)vz);
+    if (k != 0) {
+      x[off + k] = (S)nx;
+      x[Nt + off + k] = (S)ny;
+      x[2 * Nt + off + k] = (S)nz;
+    }
+    v[off + k] = vx;
+    v[Nt + off + k] = vy;
+    v[2 * Nt + off + k] = vz;
+  }
+  // vertex 0 is the anchor: every lane read it above, so it is written last
+  __syncwarp();
+  if (lane == 0) {
+    double nx = (double)ax + ((double)w.X[0] + (double)U[0]);
+    double ny = (double)ay + ((double)w.X[1] + (double)U[1]);
+    double nz = (double)az + ((double)w.X[2] + (double)U[2]);
+    x[off] = (S)nx;
+    x[Nt + off] = (S)ny;
+    x[2 * Nt + off] = (S)nz;
+  }
+  bad = __any_sync(kFull, bad);
+  NPFEM_PHASE_END(t_write, kPhWrite, P, lane)
+  if (lane == 0) {
+    int status = st->status;
+    if (st->degen) status |= 2;
+    if (bad) status |= 4;
+    if (P.status_out) P.status_out[cell] = status;
+    if (P.residual_out) P.residual_out[cell] = st->g0n > 0.0 ? gn / st->g0n : 0.0;
+    st->k = st->iters;
+  }
+  __syncwarp();
+}
+
+template <typename S>
+__global__ void __launch_bounds__(128) npfem_k_begin(DevTypeView<S> ty, StepParams P, int max_iters, S* x,
+                                                     S* v, const S* f) {
+  const int lane = threadIdx.x & 31;
+  const int n = ty.n, len = 3 * n;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(P.queue_counter, 1);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= P.ncells_list) break;
+    const int cell = P.cell_list[item];
+    char* base = P.scratch + (size_t)item * P.slot_bytes;
+    CellState<S>* st = reinterpret_cast<CellState<S>*>(base);
+    CellWs<S> w = split_ws<S>(base, ty);
+    const int64_t off = P.offsets[cell], Nt = P.n_total;
+    int iters = P.iters ? P.iters[cell] : P.iters_default;
+    int status = 0;
+    if (iters > max_iters) {
+      iters = max_iters;
+      status |= 8;
+    }
+    if (iters < 0) iters = 0;
+    const double dt = ty.dt;
+    const S sdt = (S)dt, sdt2 = (S)(dt * dt);
+    NPFEM_PHASE_BEGIN(t_predict)
+    const S ax = x[off], ay = x[Nt + off], az = x[2 * Nt + off];
+    Acc<S> cx, cy, cz;
+    for (int k = lane; k < n; k += 32) {
+      S px = x[off + k] - ax, py = x[Nt + off + k] - ay, pz = x[2 * Nt + off + k] - az;
+      w.X[3 * k] = px;
+      w.X[3 * k + 1] = py;
+      w.X[3 * k + 2] = pz;
+      cx.add(px);
+      cy.add(py);
+      cz.add(pz);
+      const S im = __ldg(&ty.inv_mass[k]);
+      S wx = sdt * v[off + k] + sdt2 * f[off + k] * im;
+      S wy = sdt * v[Nt + off + k] + sdt2 * f[Nt + off + k] * im;
+      S wz = sdt * v[2 * Nt + off + k] + sdt2 * f[2 * Nt + off + k] * im;
+      w.W[3 * k] = wx;
+      w.W[3 * k + 1] = wy;
+      w.W[3 * k + 2] = wz;
+      w.U[3 * k] = wx;
+      w.U[3 * k + 1] = wy;
+      w.U[3 * k + 2] = wz;
+    }
+    V3<S> cvol{(S)(cx.total() / n), (S)(cy.total() / n), (S)(cz.total() / n)};
+    __syncwarp();
+    NPFEM_PHASE_END(t_predict, kPhPredict, P, lane)
+    NPFEM_PHASE_BEGIN(t_obj0)
+    EvalOut ev = eval_objective<S>(ty, P, w, w.U, w.G, cvol, lane);
+    NPFEM_PHASE_END(t_obj0, kPhObjective, P, lane)
+    const double g0n = sqrt(vdot64<S>(w.G, w.G, len, lane));
+    if (lane == 0) {
+      st->fx = ev.energy;
+      st->g0n = g0n;
+      st->k = 0;
+      st->iters = iters;
+      st->hcount = 0;
+      st->hhead = 0;
+      st->status = status;
+      st->degen = ev.degenerate ? 1 : 0;
+      st->cur = 0;
+      for (int i = 0; i < kHistory; ++i) st->rho[i] = st->aco[i] = (S)0;
+      st->cvol[0] = cvol.x;
+      st->cvol[1] = cvol.y;
+      st->cvol[2] = cvol.z;
+    }
+    __syncwarp();
+    if (iters == 0) {
+      split_finalize<S>(ty, P, w, st, w.U, w.G, cell, x, v, lane);
+      continue;
+    }
+    NPFEM_PHASE_BEGIN(t_loop1)
+    two_loop_first<S>(w, st, w.G, len, lane);
+    NPFEM_PHASE_END(t_loop1, kPhTwoLoop, P, lane)
+  }
+}
+
+// Q <- A^-1 Q for every cell still iterating.  The solve vector lives in shared memory
+// when P.z_in_smem (interleaved [n+1][3] or per coordinate [n+1]), else in the workspace.
+template <typename S>
+__global__ void __launch_bounds__(128) npfem_k_solve(DevTypeView<S> ty, StepParams P) {
+  extern __shared__ double smem_z[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int zc = P.solve_per_coord ? 1 : 3;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(P.queue_counter, 1);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= P.ncells_list) break;
+    char* base = P.scratch + (size_t)item * P.slot_bytes;
+    const CellState<S>* st = reinterpret_cast<const CellState<S>*>(base);
+    if (st->k >= st->iters) continue;
+    CellWs<S> w = split_ws<S>(base, ty);
+    double* z = P.z_in_smem ? smem_z + (size_t)wib * zc * (ty.n + 1) : w.z;
+    NPFEM_PHASE_BEGIN(t_solve)
+    global_solve<S>(ty, z, P.z_in_smem != 0, w.Q, w.Q, lane, P.solve_per_coord != 0);
+    NPFEM_PHASE_END(t_solve, kPhSolve, P, lane)
+  }
+}
+
+template <typename S>
+__global__ void __launch_bounds__(128) npfem_k_iter(DevTypeView<S> ty, StepParams P, S* x, S* v) {
+  const int lane = threadIdx.x & 31;
+  const int n = ty.n, len = 3 * n;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(P.queue_counter, 1);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= P.ncells_list) break;
+    const int cell = P.cell_list[item];
+    char* base = P.scratch + (size_t)item * P.slot_bytes;
+    CellState<S>* st = reinterpret_cast<CellState<S>*>(base);
+    const int k = st->k, iters = st->iters;
+    if (k >= iters) continue;
+    CellWs<S> w = split_ws<S>(base, ty);
+    S* U = st->cur ? w.UT : w.U;
+    S* UT = st->cur ? w.U : w.UT;
+    S* G = st->cur ? w.GT : w.G;
+    S* GT = st->cur ? w.G : w.GT;
+    const V3<S> cvol{st->cvol[0], st->cvol[1], st->cvol[2]};
+    const double fx = st->fx;
+    int hcount = st->hcount, hhead = st->hhead;
+    NPFEM_PHASE_BEGIN(t_loop2)
+    for (int q = hcount - 1; q >= 0; --q) {
+      int i = (hhead - 1 - q + kHistory) % kHistory;
+      const S* si = w.hs + (size_t)i * len;
+      const S* yi = w.hy + (size_t)i * len;
+      S b = st->rho[i] * vdot<S>(yi, w.Q, len, lane);
+      S c = st->aco[i] - b;
+      for (int e = lane; e < len; e += 32) w.Q[e] += c * si[e];
+      __syncwarp();
+    }
+    for (int e = lane; e < len; e += 32) w.D[e] = -w.Q[e];
+    __syncwarp();
+    double gd = vdot64<S>(G, w.D, len, lane);
+    NPFEM_PHASE_END(t_loop2, kPhTwoLoop, P, lane)
+    if (!(gd < 0.0)) {  // not a descent direction: drop history, plain PD step
+      hcount = 0;
+      hhead = 0;
+      global_solve<S>(ty, w.z, false, G, w.Q, lane, false);
+      for (int e = lane; e < len; e += 32) w.D[e] = -w.Q[e];
+      __syncwarp();
+      gd = vdot64<S>(G, w.D, len, lane);
+    }
+    double alpha = 1.0, ft = 0.0;
+    bool degen = false;
+    int status = 0;
+    for (int h = 0; h <= kMaxHalvings; ++h) {
+      const S sa = (S)alpha;
+      for (int e = lane; e < len; e += 32) UT[e] = U[e] + sa * w.D[e];
+      __syncwarp();
+      NPFEM_PHASE_BEGIN(t_obj)
+      EvalOut et = eval_objective<S>(ty, P, w, UT, GT, cvol, lane);
+      NPFEM_PHASE_END(t_obj, kPhObjective, P, lane)
+      ft = et.energy;
+      degen = degen || et.degenerate;
+      double gtd = vdot64<S>(GT, w.D, len, lane);
+      bool armijo = ft <= fx + kArmijoC1 * alpha * gd;
+      bool approx = (gtd <= (2.0 * kArmijoC1 - 1.0) * gd) && (ft <= fx + kEnergyGuardEps * fabs(fx));
+      if (armijo || approx) break;
+      if (h == kMaxHalvings) {
+        status |= 1;
+        break;
+      }
+      alpha *= 0.5;
+    }
+    NPFEM_PHASE_BEGIN(t_hist)
+    S new_rho = (S)0;
+    bool keep = false;
+    if (k < iters - 1) {
+      S* si = w.hs + (size_t)hhead * len;
+      S* yi = w.hy + (size_t)hhead * len;
+      Acc<S> asy, ass, ayy;
+      for (int e = lane; e < len; e += 32) {
+        S s = UT[e] - U[e];
+        S y = GT[e] - G[e];
+        si[e] = s;
+        yi[e] = y;
+        asy.add_prod(s, y);
+        ass.add_prod(s, s);
+        ayy.add_prod(y, y);
+      }
+      const double sy = asy.total(), ss = ass.total(), yy = ayy.total();
+      if (sy > kCurvatureEps * sqrt(ss) * sqrt(yy)) {
+        keep = true;
+        new_rho = (S)(1.0 / sy);
+      }
+      __syncwarp();
+    }
+    NPFEM_PHASE_END(t_hist, kPhHistory, P, lane)
+    if (P.alpha_log && k < P.alpha_log_len && lane == 0) P.alpha_log[(size_t)cell * P.alpha_log_len + k] = alpha;
+    if (lane == 0) {
+      if (keep) {
+        st->rho[hhead] = new_rho;
+        hhead = (hhead + 1) % kHistory;
+        hcount = hcount < kHistory ? hcount + 1 : kHistory;
+      }
+      st->hcount = hcount;
+      st->hhead = hhead;
+      st->fx = ft;
+      st->cur ^= 1;
+      st->k = k + 1;
+      st->status |= status;
+      if (degen) st->degen = 1;
+    }
+    __syncwarp();
+    // the accepted trial (UT, GT) is the new current iterate
+    if (k + 1 < iters) {
+      NPFEM_PHASE_BEGIN(t_loop1)
+      two_loop_first<S>(w, st, GT, len, lane);
+      NPFEM_PHASE_END(t_loop1, kPhTwoLoop, P, lane)
+    } else {
+      split_finalize<S>(ty, P, w, st, UT, GT, cell, x, v, lane);
+    }
+  }
+}
+
+}  // namespace npfem

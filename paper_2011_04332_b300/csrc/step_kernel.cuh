@@ -43,6 +43,7 @@ struct StepParams {
   char* scratch;               // workspace, slot_bytes per warp
   size_t slot_bytes;
   int z_in_smem;               // 1: FP64 solve vector in dynamic shared memory
+  int solve_per_coord;         // 1: sweep x, y, z one after another with a one-coordinate vector
   unsigned long long* phase_cycles;  // [kPhases] per-phase SM cycles summed over warps
 };
 
@@ -348,7 +349,7 @@ __device__ __forceinline__ void sts_f64(uint32_t a, double v) {
   asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
 }
 
-template <bool kShared>
+template <bool kShared, int kComp>
 __device__ __forceinline__ void chunk_sweep(int nc, const int32_t* __restrict__ meta,
                                             const uint32_t* __restrict__ rc, const double* __restrict__ val,
                                             double* z, int n, int lane) {
@@ -385,23 +386,24 @@ __device__ __forceinline__ void chunk_sweep(int nc, const int32_t* __restrict__ 
         if (m & 1) __syncwarp();
         const int r = (int)(e & 0xffffu), j = (int)(e >> 16);
         if (kShared) {
-          const uint32_t aj = zs + 24u * (uint32_t)j, ar = zs + 24u * (uint32_t)r;
-          const double x0 = lds_f64(aj), x1 = lds_f64(aj + 8), x2 = lds_f64(aj + 16);
-          const double a0 = fma(-l, x0, lds_f64(ar));
-          const double a1 = fma(-l, x1, lds_f64(ar + 8));
-          const double a2 = fma(-l, x2, lds_f64(ar + 16));
-          sts_f64(ar, a0);
-          sts_f64(ar + 8, a1);
-          sts_f64(ar + 16, a2);
+          const uint32_t aj = zs + 8u * kComp * (uint32_t)j, ar = zs + 8u * kComp * (uint32_t)r;
+          double xj[kComp], zr[kComp];
+#pragma unroll
+          for (int c = 0; c < kComp; ++c) xj[c] = lds_f64(aj + 8 * c);
+#pragma unroll
+          for (int c = 0; c < kComp; ++c) zr[c] = fma(-l, xj[c], lds_f64(ar + 8 * c));
+#pragma unroll
+          for (int c = 0; c < kComp; ++c) sts_f64(ar + 8 * c, zr[c]);
         } else {
-          const double x0 = z[3 * j], x1 = z[3 * j + 1], x2 = z[3 * j + 2];
-          double* zr = z + 3 * r;
-          const double a0 = fma(-l, x0, zr[0]);
-          const double a1 = fma(-l, x1, zr[1]);
-          const double a2 = fma(-l, x2, zr[2]);
-          zr[0] = a0;
-          zr[1] = a1;
-          zr[2] = a2;
+          double xj[kComp];
+#pragma unroll
+          for (int c = 0; c < kComp; ++c) xj[c] = z[kComp * j + c];
+          double* zr = z + kComp * r;
+          double a[kComp];
+#pragma unroll
+          for (int c = 0; c < kComp; ++c) a[c] = fma(-l, xj[c], zr[c]);
+#pragma unroll
+          for (int c = 0; c < kComp; ++c) zr[c] = a[c];
         }
       }
     }
@@ -410,40 +412,58 @@ __device__ __forceinline__ void chunk_sweep(int nc, const int32_t* __restrict__ 
 }
 
 // R = A^-1 Q for the three coordinates (Q and R may alias).  FP64 throughout:
-// permute, unit-lower forward sweep, D^-1 scaling, unit-upper backward sweep.
+// permute, unit-lower forward sweep, D^-1 scaling, unit-upper backward sweep.  Either
+// the three coordinates share each sweep (z is [n+1][3]) or, per_coord, they are swept
+// one after another through a one-coordinate vector (z is [n+1]).
+template <bool kShared, int kComp, typename View>
+__device__ void solve_components(const View& ty, double* z, int n, int lane) {
+  chunk_sweep<kShared, kComp>(ty.nchunks_fwd, ty.fwd_meta, ty.fwd_rc, ty.fwd_val, z, n, lane);
+  for (int r = lane; r < n; r += 32) {
+    const double d = __ldg(&ty.dinv[r]);
+#pragma unroll
+    for (int c = 0; c < kComp; ++c) z[kComp * r + c] *= d;
+  }
+  __syncwarp();
+  chunk_sweep<kShared, kComp>(ty.nchunks_bwd, ty.bwd_meta, ty.bwd_rc, ty.bwd_val, z, n, lane);
+}
+
 template <typename S>
-__device__ void global_solve(const DevTypeView<S>& ty, double* z, bool z_shared, const S* Q, S* R, int lane) {
+__device__ void global_solve(const DevTypeView<S>& ty, double* z, bool z_shared, const S* Q, S* R, int lane,
+                             bool per_coord = false) {
   const int n = ty.n;
-  for (int r = lane; r < n; r += 32) {
-    int v = __ldg(&ty.perm[r]);
-    z[3 * r] = (double)Q[3 * v];
-    z[3 * r + 1] = (double)Q[3 * v + 1];
-    z[3 * r + 2] = (double)Q[3 * v + 2];
+  if (!per_coord) {
+    for (int r = lane; r < n; r += 32) {
+      int v = __ldg(&ty.perm[r]);
+      z[3 * r] = (double)Q[3 * v];
+      z[3 * r + 1] = (double)Q[3 * v + 1];
+      z[3 * r + 2] = (double)Q[3 * v + 2];
+    }
+    if (lane < 3) z[3 * n + lane] = 0.0;
+    __syncwarp();
+    if (z_shared)
+      solve_components<true, 3>(ty, z, n, lane);
+    else
+      solve_components<false, 3>(ty, z, n, lane);
+    for (int r = lane; r < n; r += 32) {
+      int v = __ldg(&ty.perm[r]);
+      R[3 * v] = (S)z[3 * r];
+      R[3 * v + 1] = (S)z[3 * r + 1];
+      R[3 * v + 2] = (S)z[3 * r + 2];
+    }
+    __syncwarp();
+    return;
   }
-  if (lane < 3) z[3 * n + lane] = 0.0;
-  __syncwarp();
-  if (z_shared)
-    chunk_sweep<true>(ty.nchunks_fwd, ty.fwd_meta, ty.fwd_rc, ty.fwd_val, z, n, lane);
-  else
-    chunk_sweep<false>(ty.nchunks_fwd, ty.fwd_meta, ty.fwd_rc, ty.fwd_val, z, n, lane);
-  for (int r = lane; r < n; r += 32) {
-    double d = __ldg(&ty.dinv[r]);
-    z[3 * r] *= d;
-    z[3 * r + 1] *= d;
-    z[3 * r + 2] *= d;
+  for (int c = 0; c < 3; ++c) {
+    for (int r = lane; r < n; r += 32) z[r] = (double)Q[3 * __ldg(&ty.perm[r]) + c];
+    if (lane == 0) z[n] = 0.0;
+    __syncwarp();
+    if (z_shared)
+      solve_components<true, 1>(ty, z, n, lane);
+    else
+      solve_components<false, 1>(ty, z, n, lane);
+    for (int r = lane; r < n; r += 32) R[3 * __ldg(&ty.perm[r]) + c] = (S)z[r];
+    __syncwarp();
   }
-  __syncwarp();
-  if (z_shared)
-    chunk_sweep<true>(ty.nchunks_bwd, ty.bwd_meta, ty.bwd_rc, ty.bwd_val, z, n, lane);
-  else
-    chunk_sweep<false>(ty.nchunks_bwd, ty.bwd_meta, ty.bwd_rc, ty.bwd_val, z, n, lane);
-  for (int r = lane; r < n; r += 32) {
-    int v = __ldg(&ty.perm[r]);
-    R[3 * v] = (S)z[3 * r];
-    R[3 * v + 1] = (S)z[3 * r + 1];
-    R[3 * v + 2] = (S)z[3 * r + 2];
-  }
-  __syncwarp();
 }
 
 // ------------------------------------------------------------------ one cell
@@ -539,7 +559,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
     // K4: r = H0 q
     NPFEM_PHASE_END(t_loop1, kPhTwoLoop, P, lane)
     NPFEM_PHASE_BEGIN(t_solve)
-    global_solve<S>(ty, w.z, P.z_in_smem != 0, w.Q, w.Q, lane);
+    global_solve<S>(ty, w.z, P.z_in_smem != 0, w.Q, w.Q, lane, P.solve_per_coord != 0);
     NPFEM_PHASE_END(t_solve, kPhSolve, P, lane)
     NPFEM_PHASE_BEGIN(t_loop2)
     // K3 second loop: oldest -> newest
@@ -561,7 +581,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
       hcount = 0;
       hhead = 0;
       if (kTape && lane == 0) tape->flags[k] |= kTapeReset;
-      global_solve<S>(ty, w.z, P.z_in_smem != 0, G, w.Q, lane);
+      global_solve<S>(ty, w.z, P.z_in_smem != 0, G, w.Q, lane, P.solve_per_coord != 0);
       for (int e = lane; e < len; e += 32) w.D[e] = -w.Q[e];
       __syncwarp();
       gd = vdot64<S>(G, w.D, len, lane);
@@ -671,7 +691,8 @@ __global__ void __launch_bounds__(128) npfem_step_kernel(DevTypeView<S> ty, Step
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
   const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  double* zs = P.z_in_smem ? smem_z + (size_t)wib * 3 * (ty.n + 1) : nullptr;
+  const int zc = P.solve_per_coord ? 1 : 3;
+  double* zs = P.z_in_smem ? smem_z + (size_t)wib * zc * (ty.n + 1) : nullptr;
   CellWs<S> w = carve<S>(P.scratch + (size_t)slot * P.slot_bytes, ty.n, ty.T, ty.E, zs);
   for (;;) {
     int item = 0;

@@ -42,7 +42,8 @@ class _Material(C.Structure):
 
 
 class _Opts(C.Structure):
-    _fields_ = [("iters", C.c_int32), ("alpha_log_len", C.c_int32), ("alpha_log", C.c_void_p)]
+    _fields_ = [("iters", C.c_int32), ("alpha_log_len", C.c_int32), ("alpha_log", C.c_void_p),
+                ("max_iters", C.c_int32)]
 
 
 class _TypeInfo(C.Structure):
@@ -77,6 +78,11 @@ def load_library() -> C.CDLL:
         "npfem_last_error_string": [C.c_char_p, C.c_size_t],
         "npfem_step_adjoint": [vp, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp, vp, vp, vp, vp, vp],
         "npfem_batch_phase_cycles": [vp, C.POINTER(C.c_uint64), C.c_int32],
+        "npfem_batch_set_mode": [vp, C.c_int32],
+        "npfem_batch_set_split_launch": [vp, C.c_int32, C.POINTER(C.c_int32)],
+        "npfem_batch_get_split_launch": [vp, C.c_int32, C.POINTER(C.c_int32)],
+        "npfem_batch_set_launch": [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
+        "npfem_batch_get_launch": [vp, C.c_int32, C.POINTER(C.c_int32)],
         "npfem_step_noalloc": [vp, C.c_int, C.c_int32, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp],
     }
     for name, args in sig.items():
@@ -173,6 +179,7 @@ class Batch:
                                       int(toc.shape[0]), int(precision), C.byref(h)))
         self.handle = h
         self.ncells = int(toc.shape[0])
+        self.type_of_cell = toc
         self.precision = precision
         nt = C.c_int64()
         offs = np.zeros(self.ncells + 1, dtype=np.int64)
@@ -181,10 +188,13 @@ class Batch:
         self.offsets = offs
 
     def step(self, x, v, f, iters=None, iters_default: int = 5, residual=None, status=None,
-             alpha_log=None, stream=None):
-        """npfem_step on device tensors (torch); asynchronous on `stream` (torch stream or int)."""
+             alpha_log=None, stream=None, max_iters: int = 0):
+        """npfem_step on device tensors (torch); asynchronous on `stream` (torch stream or int).
+        With an iters tensor, pass max_iters (>= every count) to use the split kernels."""
+        if iters is not None and max_iters == 0:
+            max_iters = self._iter_bound(iters)
         opts = _Opts(int(iters_default), 0 if alpha_log is None else int(alpha_log.shape[-1]),
-                     _ptr(alpha_log))
+                     _ptr(alpha_log), int(max_iters))
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -196,7 +206,7 @@ class Batch:
     def step_adjoint(self, x, v, f, gx_next, gv_next, gx, gv, gf, gw, iters=None, iters_default: int = 5,
                      status=None, stream=None):
         """npfem_step_adjoint on device tensors (FP64 batches): reverse mode of one step."""
-        opts = _Opts(int(iters_default), 0, None)
+        opts = _Opts(int(iters_default), 0, None, 0)
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -206,6 +216,18 @@ class Batch:
                                        _ptr(gx_next), _ptr(gv_next), _ptr(gx), _ptr(gv), _ptr(gf), _ptr(gw),
                                        _ptr(status), C.c_void_p(stream)))
 
+    def set_launch(self, type_index: int, warps_per_block: int, blocks_per_sm: int, solve_in_shared: bool,
+                   solve_per_coord: bool = False):
+        """npfem_batch_set_launch: launch shape of one cell type (reallocates its workspace)."""
+        _check(_lib.npfem_batch_set_launch(self.handle, int(type_index), int(warps_per_block),
+                                           int(blocks_per_sm), int(bool(solve_in_shared)), int(bool(solve_per_coord))))
+
+    def get_launch(self, type_index: int) -> dict:
+        out = (C.c_int32 * 5)()
+        _check(_lib.npfem_batch_get_launch(self.handle, int(type_index), out))
+        return {"warps_per_block": out[0], "blocks_per_sm": out[1], "solve_in_shared": bool(out[2]),
+                "solve_per_coord": bool(out[3]), "grid": out[4]}
+
     PHASES = ("predict", "objective", "two_loop", "solve", "history", "write", "area_volume", "gather")
 
     def phase_cycles(self, reset: bool = False) -> dict:
@@ -214,10 +236,32 @@ class Batch:
         _check(_lib.npfem_batch_phase_cycles(self.handle, out, int(reset)))
         return {k: int(out[i]) for i, k in enumerate(self.PHASES)}
 
+    def _iter_bound(self, iters) -> int:
+        """Cached maximum of an iteration-count tensor (read once per tensor)."""
+        key = (iters.data_ptr(), int(iters.numel()))
+        if getattr(self, "_bound_key", None) != key:
+            self._bound_key, self._bound = key, int(iters.max().item()) if iters.numel() else 0
+        return self._bound
+
+    def set_mode(self, split: bool):
+        """npfem_batch_set_mode: split kernels (True, default) or one fused kernel (False)."""
+        _check(_lib.npfem_batch_set_mode(self.handle, 1 if split else 0))
+
+    def set_split_launch(self, type_index: int, shape):
+        """npfem_batch_set_split_launch: (iter warps/CTA, iter CTAs/SM, solve warps/CTA,
+        solve CTAs/SM, solve vector in shared memory, per-coordinate solve)."""
+        arr = (C.c_int32 * 6)(*[int(s) for s in shape])
+        _check(_lib.npfem_batch_set_split_launch(self.handle, int(type_index), arr))
+
+    def get_split_launch(self, type_index: int):
+        out = (C.c_int32 * 7)()
+        _check(_lib.npfem_batch_get_split_launch(self.handle, int(type_index), out))
+        return tuple(int(v) for v in out[:6]), bool(out[6])
+
     def step_host(self, x: np.ndarray, v: np.ndarray, f: np.ndarray, iters=None, iters_default: int = 5,
                   residual=None, status=None, stream: int = 0):
         """npfem_step_host on host arrays (copies in, steps, copies out; synchronous)."""
-        opts = _Opts(int(iters_default), 0, None)
+        opts = _Opts(int(iters_default), 0, None, int(np.max(iters)) if iters is not None and len(iters) else 0)
         _check(_lib.npfem_step_host(self.handle, _ptr(x), _ptr(v), _ptr(f), _ptr(iters), C.byref(opts),
                                     _ptr(residual), _ptr(status), C.c_void_p(stream)))
 

@@ -1,0 +1,132 @@
+"""Launch-shape autotuner for a batch: picks warps per CTA, CTAs per SM and the
+placement of the FP64 solve vector (shared memory or workspace) per cell type by
+timing real steps of the caller's batch on copies of its state."""
+from __future__ import annotations
+
+from typing import Dict, List, Optional, Tuple
+
+import torch
+
+from . import native
+
+Shape = Tuple[int, int, int, int]   # (warps per CTA, CTAs per SM, solve in shared memory, per-coordinate)
+
+
+def candidate_shapes(n_verts: int, smem_per_sm: int = 228 * 1024, smem_per_cta: int = 227 * 1024) -> List[Shape]:
+    """Feasible shapes for an n-vertex type: solve vectors (24(n+1) B interleaved or
+    8(n+1) B per coordinate) in shared memory only when the CTA's vectors fit a CTA and
+    the SM holds all its CTAs; at least three warps per SM."""
+    out = []
+    for wpb in (1, 2, 3, 4):
+        for bps in (1, 2, 3, 4):
+            if wpb * bps < 3:
+                continue
+            out.append((wpb, bps, 0, 0))
+            for pc, zb in ((0, 24 * (n_verts + 1)), (1, 8 * (n_verts + 1))):
+                if wpb * zb <= smem_per_cta and bps * wpb * zb <= smem_per_sm:
+                    out.append((wpb, bps, 1, pc))
+    return out
+
+
+def _time_step(batch: native.Batch, x, v, f, iters, reps: int) -> float:
+    xs, vs = x.clone(), v.clone()
+    batch.step(xs, vs, f, iters=iters)          # warm-up (first touch of the workspace)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    for _ in range(reps):
+        xs.copy_(x)
+        vs.copy_(v)
+        e0.record()
+        batch.step(xs, vs, f, iters=iters)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    return best
+
+
+def autotune(batch: native.Batch, x, v, f, iters=None, type_sizes: Optional[Dict[int, int]] = None,
+             reps: int = 1, rounds: int = 1) -> Dict[int, dict]:
+    """Coordinate search over the types present in the batch (one type's shape varies,
+    the others stay at their current best).  Returns {type: {"shape", "ms"}}."""
+    types = sorted({int(t) for t in batch.type_of_cell})
+    sizes = type_sizes or {t: batch.types[t].info()["n_verts"] for t in types}
+    best_ms = _time_step(batch, x, v, f, iters, reps)
+    result = {t: {"shape": tuple(int(batch.get_launch(t)[k]) for k in ("warps_per_block", "blocks_per_sm",
+                                                                        "solve_in_shared", "solve_per_coord")),
+                  "ms": best_ms} for t in types}
+    for _ in range(rounds):
+        for t in types:
+            cur = result[t]["shape"]
+            for shape in candidate_shapes(sizes[t]):
+                if shape == cur:
+                    continue
+                try:
+                    batch.set_launch(t, *shape)
+                except native.NpfemError:
+                    continue
+                ms = _time_step(batch, x, v, f, iters, reps)
+                if ms < best_ms:
+                    best_ms, cur = ms, shape
+            batch.set_launch(t, *cur)
+            result[t] = {"shape": tuple(int(s) for s in cur), "ms": best_ms}
+    return result
+
+
+SplitShape = Tuple[int, int, int, int, int, int]
+
+
+def split_solve_candidates(n_verts: int, smem_per_sm: int = 228 * 1024, smem_per_cta: int = 227 * 1024):
+    """(warps per CTA, CTAs per SM, in shared memory, per coordinate) for the solve kernel:
+    8 to 32 warps per SM, solve vectors in shared memory when the SM holds them."""
+    out = []
+    for wpb in (2, 4):
+        for bps in range(1, 17):
+            wps = wpb * bps
+            if wps < 8 or wps > 32:
+                continue
+            out.append((wpb, bps, 0, 0))
+            for pc, zb in ((0, 24 * (n_verts + 1)), (1, 8 * (n_verts + 1))):
+                if wpb * zb <= smem_per_cta and bps * wpb * zb <= smem_per_sm:
+                    out.append((wpb, bps, 1, pc))
+    return out
+
+
+def split_iter_candidates():
+    """(warps per CTA, CTAs per SM) for the iteration kernels: 8 to 16 warps per SM."""
+    return [(wpb, bps) for wpb in (2, 4) for bps in range(1, 9) if 8 <= wpb * bps <= 16]
+
+
+def autotune_split(batch: native.Batch, x, v, f, iters=None, reps: int = 1, solve_only: bool = False) -> Dict[int, dict]:
+    """Coordinate search of the split-mode shapes per cell type: first the solve kernel's
+    shape, then the iteration kernels' shape, timing whole steps."""
+    batch.set_mode(True)
+    types = sorted({int(t) for t in batch.type_of_cell})
+    best_ms = _time_step(batch, x, v, f, iters, reps)
+    out = {}
+    for t in types:
+        n = batch.types[t].info()["n_verts"]
+        cur = list(batch.get_split_launch(t)[0])
+        for cand in split_solve_candidates(n):
+            shape = cur[:2] + list(cand)
+            if shape == cur:
+                continue
+            try:
+                batch.set_split_launch(t, shape)
+            except native.NpfemError:
+                continue
+            ms = _time_step(batch, x, v, f, iters, reps)
+            if ms < best_ms:
+                best_ms, cur = ms, shape
+        batch.set_split_launch(t, cur)
+        if not solve_only:
+            for cand in split_iter_candidates():
+                shape = list(cand) + cur[2:]
+                if shape == cur:
+                    continue
+                batch.set_split_launch(t, shape)
+                ms = _time_step(batch, x, v, f, iters, reps)
+                if ms < best_ms:
+                    best_ms, cur = ms, shape
+            batch.set_split_launch(t, cur)
+        out[t] = {"split_shape": tuple(cur), "ms": best_ms}
+    return out

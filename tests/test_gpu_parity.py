@@ -235,3 +235,82 @@ def test_phase_cycle_telemetry():
     assert c["solve"] > 0 and c["objective"] > 0 and c["two_loop"] > 0 and c["write"] > 0
     assert c["gather"] < c["objective"] and c["area_volume"] < c["objective"]
     assert all(v == 0 for v in r.batch.phase_cycles().values())
+
+
+def test_launch_shapes_give_identical_results():
+    """A cell's arithmetic does not depend on the launch shape: every feasible shape
+    (warps per CTA, CTAs per SM, solve vector in shared memory or workspace) gives
+    bit-identical states; the autotuner keeps one of them."""
+    nat = _native()
+    from paper_2011_04332_b300 import tuning
+    b = I.heterogeneous_batch(n_rbc3=9, n_rbc4=2, n_plt=7, seed=1002)
+    r = Runner(b, nat.FP32FORM)
+    x0, v0, *_ = r.step(b.x, b.v, b.f, iters=b.iters)
+    for t in range(len(b.types)):
+        n = b.types[t].mesh.n
+        shapes = tuning.candidate_shapes(n)
+        for shape in shapes[:5] + [sh for sh in shapes if sh[3] == 1][:3] + [(3, 1, 1, 0)]:
+            r.batch.set_launch(t, *shape)
+            assert r.batch.get_launch(t)["warps_per_block"] == shape[0]
+            x1, v1, *_ = r.step(b.x, b.v, b.f, iters=b.iters)
+            assert np.array_equal(x1, x0) and np.array_equal(v1, v0), (t, shape)
+    dev = torch.device("cuda:0")
+    T = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    res = tuning.autotune(r.batch, T(b.x), T(b.v), T(b.f), iters=torch.tensor(b.iters, device=dev))
+    assert set(res) == {0, 1, 2}
+    x2, v2, *_ = r.step(b.x, b.v, b.f, iters=b.iters)
+    assert np.array_equal(x2, x0)
+
+
+def test_cuda_graph_replay_equals_direct_steps():
+    """npfem_step is capturable: a captured step replayed twice gives the same state as
+    two direct calls."""
+    nat = _native()
+    b = I.small_mixed_batch(seed=21)
+    r = Runner(b, nat.FP32FORM)
+    dev = torch.device("cuda:0")
+    T = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    it = torch.tensor(b.iters, device=dev)
+    xa, va, f = T(b.x), T(b.v), T(b.f)
+    for _ in range(2):
+        r.batch.step(xa, va, f, iters=it)
+    xb, vb = T(b.x), T(b.v)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            r.batch.step(xb, vb, f, iters=it)
+    torch.cuda.current_stream().wait_stream(s)
+    xb.copy_(T(b.x))
+    vb.copy_(T(b.v))
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(xa, xb) and torch.equal(va, vb)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_split_and_fused_modes_are_identical(prec):
+    """The split kernels (k_begin, k_solve, k_iter) and the fused persistent kernel run the
+    same arithmetic: identical states, statuses, residuals and step lengths, with ragged
+    per-cell iteration counts including zero and non-default launch shapes."""
+    nat = _native()
+    b = I.heterogeneous_batch(n_rbc3=7, n_rbc4=3, n_plt=6, seed=1005)
+    it = b.iters.copy()
+    it[0] = 0
+    it[3] = 1
+    p = nat.FP64 if prec == "fp64" else nat.FP32FORM
+    r = Runner(b, p)
+    r.batch.set_mode(False)
+    fused = r.step(b.x, b.v, b.f, iters=it)
+    r.batch.set_mode(True)
+    assert r.batch.get_split_launch(0)[1] is True
+    split = r.step(b.x, b.v, b.f, iters=it)
+    for a, c in zip(fused, split):
+        assert np.array_equal(a, c)
+    r.batch.set_split_launch(1, (2, 3, 3, 1, 1, 0))
+    r.batch.set_split_launch(2, (4, 2, 2, 2, 0, 1))
+    split2 = r.step(b.x, b.v, b.f, iters=it)
+    for a, c in zip(fused, split2):
+        assert np.array_equal(a, c)
