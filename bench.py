@@ -235,6 +235,7 @@ def run_ours(args, rank, world, local_rank):
         tuned = tuning.autotune_split(batch, x0, v0, f, iters=iters)
         tuned = {"seconds": round(time.perf_counter() - t0, 1),
                  "shapes": {str(t): list(r["split_shape"]) for t, r in tuned.items()}}
+    batch.set_kernel_timing(True)       # CUDA events around every launch (also inside the graph)
     for _ in range(args.warmup):
         batch.step(x, v, f, iters=iters, residual=res, status=st)
     torch.cuda.synchronize()
@@ -262,6 +263,8 @@ def run_ours(args, rank, world, local_rank):
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    present = sorted({int(t) for t in b.type_of_cell})
+    ktime = {t: {k: [0.0, 0] for k in native.Batch.KERNELS} for t in present}
     with ClockSampler(local_rank) as clk:
         t_wall0 = time.perf_counter()
         for k in range(args.steps):
@@ -269,6 +272,11 @@ def run_ours(args, rank, world, local_rank):
             ev[k][0].record(stream)
             one_step()
             ev[k][1].record(stream)
+            # per-kernel durations of this step (events on the kernels' own streams)
+            for t in present:
+                for name, (kms, kn) in batch.kernel_times(t).items():
+                    ktime[t][name][0] += kms
+                    ktime[t][name][1] += kn
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
     if world > 1:
@@ -281,20 +289,38 @@ def run_ours(args, rank, world, local_rank):
     resid = res.cpu().numpy()
     status = st.cpu().numpy()
 
-    # roofline of the step kernel: FP64 triangular-solve flops (ALU bound, FP64 pipe)
+    # roofline of the dominant kernel, npfem_k_solve (the FP64 triangular solves; ALU
+    # bound on the FP64 pipe): its algorithmic flops over its own launch durations
     nnz = np.array([infos[t]["nnz_factor"] for t in b.type_of_cell], dtype=np.float64)
     nv = np.array([infos[t]["n_verts"] for t in b.type_of_cell], dtype=np.float64)
-    flops_per_launch = float(np.sum(b.iters * (12.0 * nnz + 3.0 * nv)))
+    solve_flops = b.iters * (12.0 * nnz + 3.0 * nv)          # per cell and step
+    flops_per_step = float(np.sum(solve_flops))
     fp64_peak, fp32_peak = probe_peaks()
-    achieved = flops_per_launch / (ms_per_step / 1e3) / 1e12
+    kernels = {}
+    for t in present:
+        kt = ktime[t]
+        step_ms = {name: kt[name][0] / args.steps for name in kt}
+        ft = float(np.sum(solve_flops[b.type_of_cell == t]))
+        launches = kt["k_solve"][1] / args.steps
+        kernels[str(t)] = {"ms_per_step": step_ms, "launches_per_step": {n: kt[n][1] / args.steps for n in kt},
+                           "k_solve_flops_per_launch": ft / launches if launches else None,
+                           "k_solve_tflops": ft / (step_ms["k_solve"] / 1e3) / 1e12 if step_ms["k_solve"] else None}
+    solve_ms_total = sum(ktime[t]["k_solve"][0] for t in present) / args.steps
+    solve_launches = sum(ktime[t]["k_solve"][1] for t in present) / args.steps
+    kern_ms_total = sum(ktime[t][n][0] for t in present for n in native.Batch.KERNELS) / args.steps
+    achieved = flops_per_step / (solve_ms_total / 1e3) / 1e12 if solve_ms_total > 0 else None
     traffic, traffic_how = measured_traffic(args.workload, args.precision)
-    roofline = {"bound": "alu", "pipe": "fp64", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak if fp64_peak else None, "traffic": traffic,
+    roofline = {"bound": "alu", "pipe": "fp64", "kernel": "npfem_k_solve", "achieved": achieved, "peak": fp64_peak,
+                "unit": "TFLOP/s", "frac": achieved / fp64_peak if fp64_peak and achieved else None, "traffic": traffic,
                 "traffic_note": traffic_how,
                 "peak_source": "measured live: FP64 FMA probe (8 chains/thread, 4 CTAs/SM)",
-                "algorithmic": "FP64 flops of the triangular solves: iters*(12*nnz(L)+3n) per cell",
-                "kernel_time": "CUDA events around one step (one CUDA graph: memset + split kernels); the FP64 "
-                               "solves run in npfem_k_solve, which dominates the step"}
+                "algorithmic": "FP64 flops of the triangular solves: iters*(12*nnz(L)+3n) per cell and step, "
+                               f"{flops_per_step / max(solve_launches, 1):.4g} per launch on average",
+                "kernel_time": "CUDA events around each npfem_k_solve launch on its own stream, recorded by "
+                               "the timed graph replays (average launch %.4f ms, %.1f launches per step)"
+                               % (solve_ms_total / max(solve_launches, 1), solve_launches),
+                "kernel_share_of_step": solve_ms_total / kern_ms_total if kern_ms_total else None,
+                "step_frac": flops_per_step / (ms_per_step / 1e3) / 1e12 / fp64_peak if fp64_peak else None}
 
     # end-to-end through the C ABI with host (pinned) buffers
     e2e = None
@@ -347,6 +373,7 @@ def run_ours(args, rank, world, local_rank):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "adjoint": adjoint,
+        "kernels": kernels,
         "gpu_launches": args.steps * len(set(int(t) for t in b.type_of_cell)) * (1 + 2 * int(np.max(b.iters))),
         "clocks": clk.summary(),
         "wall_s_timed_region": t_wall,

@@ -203,6 +203,18 @@ npfem_status npfem_batch_get_split_launch(const npfem_batch* batch, int32_t type
  * device.  cycles: host array of 8; reset != 0 zeroes the counters after reading. */
 npfem_status npfem_batch_phase_cycles(npfem_batch* batch, uint64_t* cycles, int32_t reset);
 
+/* Per-kernel timing of split-mode steps with CUDA events recorded on the stream each
+ * kernel is launched on (a per-type internal stream when the batch holds several
+ * types).  enable != 0 creates the events (once) and makes every later split-mode step
+ * record a start/end pair around each of its launches; under stream capture the pairs
+ * become event-record nodes that each graph replay re-records.  npfem_batch_kernel_times
+ * waits for the last recorded step of cell type type_index and returns, in host arrays
+ * of 3, the summed durations in ms and launch counts of {k_begin, k_solve, k_iter}.
+ * Errors: NPFEM_ERR_INVALID_ARG when timing was never enabled or the type has no cells;
+ * NPFEM_ERR_CUDA when an event cannot be read. */
+npfem_status npfem_batch_set_kernel_timing(npfem_batch* batch, int32_t enable);
+npfem_status npfem_batch_kernel_times(npfem_batch* batch, int32_t type_index, double* ms, int32_t* launches);
+
 /* Same step with HOST arrays (pageable or pinned): copies x, v, f_ext (and iters,
  * when given) to batch-owned device buffers, runs npfem_step, and copies x, v,
  * residuals and statuses back; synchronous.  residual_out/status_out are host

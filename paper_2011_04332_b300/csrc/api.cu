@@ -76,7 +76,14 @@ struct npfem_batch {
   std::vector<cudaStream_t> type_streams;
   std::vector<cudaEvent_t> type_events;
   cudaEvent_t fork_event = nullptr;
+  // optional per-launch kernel timing in split mode: a (start, end) event pair around
+  // every launch, per cell-type launch and launch slot (0: k_begin, 1 + 2i: k_solve of
+  // iteration i, 2 + 2i: k_iter of iteration i), re-recorded by every step
+  bool ktiming = false;
+  std::vector<cudaEvent_t> kev;      // [launches.size()][kTimingSlots][2]
+  std::vector<int> k_last_slots;     // slots recorded by the last step, per type launch
   ~npfem_batch() {
+    for (cudaEvent_t e : kev) cudaEventDestroy(e);
     for (cudaStream_t s : type_streams) cudaStreamDestroy(s);
     for (cudaEvent_t e : type_events) cudaEventDestroy(e);
     if (fork_event) cudaEventDestroy(fork_event);
@@ -259,6 +266,18 @@ static npfem_status launch_split(npfem_batch* b, const npfem_cell_type* t, const
   return NPFEM_OK;
 }
 
+static constexpr int kTimingSlots = 1 + 2 * kSplitMaxIters;
+
+// Records one timing event on stream s; under stream capture it becomes an external
+// event-record node of the graph, so graph replays re-record it.
+static cudaError_t record_timing_event(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaError_t err = cudaStreamIsCapturing(s, &cs);
+  if (err != cudaSuccess) return err;
+  return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal)
+                                             : cudaEventRecord(e, s);
+}
+
 static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_ext, const int32_t* iters,
                                const npfem_solver_opts* opts, int max_iters, double* residual_out,
                                int32_t* status_out, cudaStream_t st) {
@@ -300,8 +319,11 @@ static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_e
     P.alpha_log = opts->alpha_log;
     P.alpha_log_len = opts->alpha_log_len;
     P.phase_cycles = b->d_phase;
-    for (int kind = 0, it = 0; kind == 0 || it < max_iters;) {
+    int slot = 0;
+    for (int kind = 0, it = 0; kind == 0 || it < max_iters; ++slot) {
       npfem_status rc;
+      cudaEvent_t* ke = b->ktiming ? &b->kev[(li * kTimingSlots + slot) * 2] : nullptr;
+      if (ke) NPFEM_CUDA_TRY(record_timing_event(ke[0], ts));
       if (b->prec == NPFEM_FP64)
         rc = launch_split<double>(b, t, L, P, kind, it, max_iters, static_cast<double*>(x), static_cast<double*>(v),
                                   static_cast<const double*>(f_ext), t->v64, ts);
@@ -309,6 +331,7 @@ static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_e
         rc = launch_split<float>(b, t, L, P, kind, it, max_iters, static_cast<float*>(x), static_cast<float*>(v),
                                  static_cast<const float*>(f_ext), t->v32, ts);
       if (rc != NPFEM_OK) return rc;
+      if (ke) NPFEM_CUDA_TRY(record_timing_event(ke[1], ts));
       if (kind == 0) {
         kind = 1;
       } else if (kind == 1) {
@@ -318,6 +341,7 @@ static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_e
         ++it;
       }
     }
+    if (b->ktiming) b->k_last_slots[li] = slot;
   }
   if (fork)
     for (size_t li = 0; li < nl; ++li) {
@@ -713,6 +737,37 @@ npfem_status npfem_batch_phase_cycles(npfem_batch* b, uint64_t* cycles, int32_t 
   for (int k = 0; k < kPhases; ++k) cycles[k] = h[k];
   if (reset) NPFEM_CUDA_TRY(cudaMemset(b->d_phase, 0, sizeof(h)));
   return NPFEM_OK;
+}
+
+npfem_status npfem_batch_set_kernel_timing(npfem_batch* b, int32_t enable) {
+  if (!b) return fail(NPFEM_ERR_INVALID_ARG, "batch_set_kernel_timing: null batch");
+  if (enable && b->kev.empty() && !b->launches.empty()) {
+    b->kev.resize(b->launches.size() * kTimingSlots * 2, nullptr);
+    for (cudaEvent_t& e : b->kev) NPFEM_CUDA_TRY(cudaEventCreate(&e));
+    b->k_last_slots.assign(b->launches.size(), 0);
+  }
+  b->ktiming = enable != 0 && !b->launches.empty();
+  return NPFEM_OK;
+}
+
+npfem_status npfem_batch_kernel_times(npfem_batch* b, int32_t type_index, double* ms, int32_t* launches) {
+  if (!b || !ms || !launches) return fail(NPFEM_ERR_INVALID_ARG, "batch_kernel_times: null argument");
+  for (int k = 0; k < 3; ++k) ms[k] = 0.0, launches[k] = 0;
+  if (b->kev.empty()) return fail(NPFEM_ERR_INVALID_ARG, "batch_kernel_times: kernel timing was never enabled");
+  for (size_t li = 0; li < b->launches.size(); ++li) {
+    if (b->launches[li].type_index != type_index) continue;
+    for (int slot = 0; slot < b->k_last_slots[li]; ++slot) {
+      cudaEvent_t* ke = &b->kev[(li * kTimingSlots + slot) * 2];
+      NPFEM_CUDA_TRY(cudaEventSynchronize(ke[1]));
+      float t = 0.f;
+      NPFEM_CUDA_TRY(cudaEventElapsedTime(&t, ke[0], ke[1]));
+      const int kind = slot == 0 ? 0 : 2 - (slot & 1);
+      ms[kind] += t;
+      launches[kind] += 1;
+    }
+    return NPFEM_OK;
+  }
+  return fail(NPFEM_ERR_INVALID_ARG, "batch_kernel_times: no cells of that type in the batch");
 }
 
 npfem_status npfem_step_host(npfem_batch* b, void* x, void* v, const void* f_ext, const int32_t* iters,

@@ -78,6 +78,8 @@ def load_library() -> C.CDLL:
         "npfem_last_error_string": [C.c_char_p, C.c_size_t],
         "npfem_step_adjoint": [vp, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp, vp, vp, vp, vp, vp],
         "npfem_batch_phase_cycles": [vp, C.POINTER(C.c_uint64), C.c_int32],
+        "npfem_batch_set_kernel_timing": [vp, C.c_int32],
+        "npfem_batch_kernel_times": [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int32)],
         "npfem_batch_set_mode": [vp, C.c_int32],
         "npfem_batch_set_split_launch": [vp, C.c_int32, C.POINTER(C.c_int32)],
         "npfem_batch_get_split_launch": [vp, C.c_int32, C.POINTER(C.c_int32)],
@@ -235,6 +237,18 @@ class Batch:
         out = (C.c_uint64 * 8)()
         _check(_lib.npfem_batch_phase_cycles(self.handle, out, int(reset)))
         return {k: int(out[i]) for i, k in enumerate(self.PHASES)}
+
+    KERNELS = ("k_begin", "k_solve", "k_iter")
+
+    def set_kernel_timing(self, enable: bool = True) -> None:
+        """npfem_batch_set_kernel_timing: CUDA events around every split-mode launch."""
+        _check(_lib.npfem_batch_set_kernel_timing(self.handle, int(enable)))
+
+    def kernel_times(self, type_index: int) -> dict:
+        """npfem_batch_kernel_times: {kernel: (summed ms, launches)} of the last timed step."""
+        ms, n = (C.c_double * 3)(), (C.c_int32 * 3)()
+        _check(_lib.npfem_batch_kernel_times(self.handle, int(type_index), ms, n))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(self.KERNELS)}
 
     def _iter_bound(self, iters) -> int:
         """Cached maximum of an iteration-count tensor (read once per tensor)."""

@@ -290,6 +290,52 @@ def test_cuda_graph_replay_equals_direct_steps():
     assert torch.equal(xa, xb) and torch.equal(va, vb)
 
 
+def test_kernel_timing_eager_and_in_graph():
+    """Per-kernel CUDA-event timing of split-mode steps: one k_begin and, per iteration up
+    to the batch's largest count, one k_solve and one k_iter per cell type, with positive
+    durations, both for direct steps and for replays of a captured step; the timed step
+    is unchanged by the events."""
+    nat = _native()
+    b = I.small_mixed_batch(seed=23)
+    r = Runner(b, nat.FP32FORM)
+    dev = torch.device("cuda:0")
+    T = lambda a: torch.tensor(a, dtype=torch.float32, device=dev)
+    it = torch.tensor(b.iters, device=dev)
+    kmax = int(b.iters.max())
+    present = sorted({int(t) for t in b.type_of_cell})
+    xa, va, f = T(b.x), T(b.v), T(b.f)
+    r.batch.step(xa, va, f, iters=it)
+    with pytest.raises(nat.NpfemError):
+        r.batch.kernel_times(present[0])
+    r.batch.set_kernel_timing(True)
+    xb, vb = T(b.x), T(b.v)
+    r.batch.step(xb, vb, f, iters=it)
+    torch.cuda.synchronize()
+    assert torch.equal(xa, xb) and torch.equal(va, vb)
+    for t in present:
+        kt = r.batch.kernel_times(t)
+        assert [kt[k][1] for k in nat.Batch.KERNELS] == [1, kmax, kmax]
+        assert all(kt[k][0] > 0 for k in nat.Batch.KERNELS)
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    xc, vc = T(b.x), T(b.v)
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            r.batch.step(xc, vc, f, iters=it)
+    torch.cuda.current_stream().wait_stream(s)
+    xc.copy_(T(b.x))
+    vc.copy_(T(b.v))
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(xa, xc) and torch.equal(va, vc)
+    for t in present:
+        kt = r.batch.kernel_times(t)
+        assert [kt[k][1] for k in nat.Batch.KERNELS] == [1, kmax, kmax]
+        assert all(kt[k][0] > 0 for k in nat.Batch.KERNELS)
+    r.batch.set_kernel_timing(False)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_split_and_fused_modes_are_identical(prec):
     """The split kernels (k_begin, k_solve, k_iter) and the fused persistent kernel run the
