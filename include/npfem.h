@@ -187,11 +187,16 @@ npfem_status npfem_batch_get_launch(const npfem_batch* batch, int32_t type_index
  * stream; needs the iteration bound: opts->iters without an iters array, else
  * opts->max_iters in 1..32; a cell whose count exceeds it stops there and gets status
  * bit 8).  mode 0 ("fused"): one persistent kernel per cell type (any iteration count;
- * also used by split-mode batches when the bound is unknown).  Results are identical.
- * npfem_batch_set_split_launch sets, per type, shape[6] = {warps per CTA, CTAs per SM of
- * the iteration kernels; warps per CTA, CTAs per SM, solve vector in shared memory,
- * per-coordinate solve of the solve kernel}; npfem_batch_get_split_launch returns those
- * six values plus the mode in shape[6]. */
+ * also used by split-mode batches when the bound is unknown).  The two modes agree to
+ * rounding (their kernels are compiled separately and the compiler may contract
+ * multiply-adds differently); split launch shapes never change split-mode results.
+ * npfem_batch_set_split_launch sets, per type, shape[7] = {warps per CTA (1..4), CTAs per
+ * SM (1..16) of the iteration kernels; warps per CTA (1..4), CTAs per SM (1..16), solve
+ * vectors in shared memory, per-coordinate solve, cells per warp (1..4) of the solve
+ * kernel: a warp sweeps that many cells of the type together through the shared factor};
+ * NPFEM_ERR_INVALID_ARG outside those ranges, NPFEM_ERR_UNSUPPORTED when a CTA's solve
+ * vectors exceed shared memory.  npfem_batch_get_split_launch returns those seven values
+ * plus the mode in shape[7] (host array of 8). */
 npfem_status npfem_batch_set_mode(npfem_batch* batch, int32_t mode);
 npfem_status npfem_batch_set_split_launch(npfem_batch* batch, int32_t type_index, const int32_t* shape);
 npfem_status npfem_batch_get_split_launch(const npfem_batch* batch, int32_t type_index, int32_t* shape);

@@ -54,7 +54,8 @@ struct TypeLaunch {
   // split mode: per-cell workspace and the shapes of k_begin/k_iter and k_solve
   char* cell_scratch;        // owned: cell_slot bytes per cell (first split step)
   size_t cell_slot;
-  int it_wpb, it_bps, sv_wpb, sv_bps, sv_smem, sv_percoord;
+  int it_wpb, it_bps, sv_wpb, sv_bps, sv_smem, sv_percoord, sv_cells;
+  int* active = nullptr;  // split mode: [2][ncells] lists of iterating cells (inside cell_scratch)
 };
 
 struct npfem_batch {
@@ -204,6 +205,32 @@ static npfem_status configure_launch(npfem_batch* b, TypeLaunch& L, int wpb, int
   return NPFEM_OK;
 }
 
+// The solve kernel instantiated for a cell count and vector placement.
+template <typename S>
+static void (*solve_kernel(int cells, int place))(DevTypeView<S>, StepParams) {
+  static void (*const table[4][3])(DevTypeView<S>, StepParams) = {
+      {npfem_k_solve<S, 1, kZWorkspace>, npfem_k_solve<S, 1, kZShared>, npfem_k_solve<S, 1, kZSharedPerCoord>},
+      {npfem_k_solve<S, 2, kZWorkspace>, npfem_k_solve<S, 2, kZShared>, npfem_k_solve<S, 2, kZSharedPerCoord>},
+      {npfem_k_solve<S, 3, kZWorkspace>, npfem_k_solve<S, 3, kZShared>, npfem_k_solve<S, 3, kZSharedPerCoord>},
+      {npfem_k_solve<S, 4, kZWorkspace>, npfem_k_solve<S, 4, kZShared>, npfem_k_solve<S, 4, kZSharedPerCoord>}};
+  return table[cells - 1][place];
+}
+
+template <typename S>
+static cudaError_t set_solve_smem_attr(int bytes) {
+  cudaError_t e = cudaSuccess;
+  for (int c = 1; c <= 4 && e == cudaSuccess; ++c)
+    for (int pl = 1; pl <= 2 && e == cudaSuccess; ++pl)
+      e = cudaFuncSetAttribute(solve_kernel<S>(c, pl), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  return e;
+}
+
+// Dynamic shared memory of a solve-kernel CTA: per warp, `cells` solve vectors of
+// [n+1][3] doubles (or [n+1] per coordinate).
+static size_t split_solve_smem(int n, int wpb, int per_coord, int cells) {
+  return sizeof(double) * (per_coord ? 1 : 3) * ((size_t)n + 1) * (size_t)wpb * (size_t)cells;
+}
+
 // Default split-mode shapes by size class, from autotuning on B300 (homogeneous 642-vertex
 // batch and the mixed 162/642/2562-vertex batch, FP32 form).
 static void default_split_shape(TypeLaunch& L, int n) {
@@ -217,8 +244,9 @@ static void default_split_shape(TypeLaunch& L, int n) {
     L.it_wpb = 2, L.it_bps = 8;
     L.sv_wpb = 2, L.sv_bps = 8, L.sv_smem = 0, L.sv_percoord = 0;
   }
-  const size_t zb = sizeof(double) * (L.sv_percoord ? 1 : 3) * ((size_t)n + 1);
-  if (L.sv_smem && (size_t)L.sv_bps * L.sv_wpb * zb > 220 * 1024) L.sv_smem = 0;
+  L.sv_cells = 1;
+  if (L.sv_smem && (size_t)L.sv_bps * split_solve_smem(n, L.sv_wpb, L.sv_percoord, L.sv_cells) > 220 * 1024)
+    L.sv_smem = 0;
 }
 
 static npfem_status ensure_cell_scratch(npfem_batch* b, TypeLaunch& L) {
@@ -231,10 +259,12 @@ static npfem_status ensure_cell_scratch(npfem_batch* b, TypeLaunch& L) {
   bytes += sizeof(double) * 3 * ((size_t)H.n + 1);
   bytes = kStateBytes + ((bytes + 255) & ~(size_t)255);
   void* p = nullptr;
-  cudaError_t e = cudaMalloc(&p, bytes * (size_t)L.ncells);
+  // per-cell slots, then two lists of cell slots (the cells iterating at even / odd iterations)
+  cudaError_t e = cudaMalloc(&p, bytes * (size_t)L.ncells + 2 * sizeof(int) * (size_t)L.ncells);
   if (e != cudaSuccess) return fail(NPFEM_ERR_OOM, std::string("split step: workspace: ") + cudaGetErrorString(e));
   L.cell_scratch = static_cast<char*>(p);
   L.cell_slot = bytes;
+  L.active = reinterpret_cast<int*>(L.cell_scratch + bytes * (size_t)L.ncells);
   return NPFEM_OK;
 }
 
@@ -244,20 +274,30 @@ static npfem_status launch_split(npfem_batch* b, const npfem_cell_type* t, const
                                  cudaStream_t st) {
   P.scratch = L.cell_scratch;
   P.slot_bytes = L.cell_slot;
+  int* act_count = L.counter + kActiveCountOff;
   if (kind == 0) {
     P.queue_counter = L.counter;
+    P.act_out = L.active;
+    P.act_count_out = act_count;
     int grid = std::max(1, std::min<int>(b->sms * L.it_bps, (L.ncells + L.it_wpb - 1) / L.it_wpb));
     npfem_k_begin<S><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, max_iters, x, v, f);
   } else if (kind == 1) {
     P.queue_counter = L.counter + 1 + 2 * it;
+    P.act_in = L.active + (size_t)(it & 1) * L.ncells;
+    P.act_count_in = act_count + it;
     P.z_in_smem = L.sv_smem;
     P.solve_per_coord = L.sv_percoord;
+    P.solve_cells = std::max(1, std::min(4, L.sv_cells));
     const HostType& H = t->host;
-    size_t smem = L.sv_smem ? sizeof(double) * (L.sv_percoord ? 1 : 3) * ((size_t)H.n + 1) * L.sv_wpb : 0;
-    int grid = std::max(1, std::min<int>(b->sms * L.sv_bps, (L.ncells + L.sv_wpb - 1) / L.sv_wpb));
-    npfem_k_solve<S><<<grid, 32 * L.sv_wpb, smem, st>>>(view, P);
+    size_t smem = L.sv_smem ? split_solve_smem(H.n, L.sv_wpb, L.sv_percoord, P.solve_cells) : 0;
+    const int per_cta = L.sv_wpb * P.solve_cells;
+    int grid = std::max(1, std::min<int>(b->sms * L.sv_bps, (L.ncells + per_cta - 1) / per_cta));
+    const int place = !L.sv_smem ? kZWorkspace : (L.sv_percoord ? kZSharedPerCoord : kZShared);
+    solve_kernel<S>(P.solve_cells, place)<<<grid, 32 * L.sv_wpb, smem, st>>>(view, P);
   } else {
     P.queue_counter = L.counter + 2 + 2 * it;
+    P.act_out = L.active + (size_t)((it + 1) & 1) * L.ncells;
+    P.act_count_out = act_count + it + 1;
     int grid = std::max(1, std::min<int>(b->sms * L.it_bps, (L.ncells + L.it_wpb - 1) / L.it_wpb));
     npfem_k_iter<S><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, x, v);
   }
@@ -494,9 +534,9 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(npfem_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(npfem_k_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+    e = set_solve_smem_attr<double>(smem_optin);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(npfem_k_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+    e = set_solve_smem_attr<float>(smem_optin);
   if (e != cudaSuccess) return cleanup(NPFEM_ERR_CUDA, std::string("batch_create: ") + cudaGetErrorString(e));
   const size_t ssize = prec == NPFEM_FP64 ? sizeof(double) : sizeof(float);
   for (int ti = 0; ti < ntypes; ++ti) {
@@ -697,9 +737,10 @@ npfem_status npfem_batch_set_split_launch(npfem_batch* b, int32_t type_index, co
     if (L.type_index == type_index) {
       const HostType& H = b->types[L.type_index]->host;
       if (shape[0] < 1 || shape[0] > 4 || shape[1] < 1 || shape[1] > 16 || shape[2] < 1 || shape[2] > 4 ||
-          shape[3] < 1 || shape[3] > 16)
-        return fail(NPFEM_ERR_INVALID_ARG, "batch_set_split_launch: warps/CTA in 1..4, CTAs/SM in 1..16");
-      size_t smem = shape[4] ? sizeof(double) * (shape[5] ? 1 : 3) * ((size_t)H.n + 1) * shape[2] : 0;
+          shape[3] < 1 || shape[3] > 16 || shape[6] < 1 || shape[6] > 4)
+        return fail(NPFEM_ERR_INVALID_ARG,
+                    "batch_set_split_launch: warps/CTA in 1..4, CTAs/SM in 1..16, cells per solve warp in 1..4");
+      size_t smem = shape[4] ? split_solve_smem(H.n, shape[2], shape[5], shape[6]) : 0;
       if (smem > (size_t)b->smem_optin)
         return fail(NPFEM_ERR_UNSUPPORTED, "batch_set_split_launch: solve vectors exceed shared memory");
       L.it_wpb = shape[0];
@@ -708,6 +749,7 @@ npfem_status npfem_batch_set_split_launch(npfem_batch* b, int32_t type_index, co
       L.sv_bps = shape[3];
       L.sv_smem = shape[4] ? 1 : 0;
       L.sv_percoord = shape[5] ? 1 : 0;
+      L.sv_cells = shape[6];
       return NPFEM_OK;
     }
   return fail(NPFEM_ERR_INVALID_ARG, "batch_set_split_launch: no cells of that type in the batch");
@@ -723,7 +765,8 @@ npfem_status npfem_batch_get_split_launch(const npfem_batch* b, int32_t type_ind
       shape[3] = L.sv_bps;
       shape[4] = L.sv_smem;
       shape[5] = L.sv_percoord;
-      shape[6] = b->mode;
+      shape[6] = L.sv_cells;
+      shape[7] = b->mode;
       return NPFEM_OK;
     }
   return fail(NPFEM_ERR_INVALID_ARG, "batch_get_split_launch: no cells of that type in the batch");

@@ -142,6 +142,7 @@ extern "C" npfem_status npfem_step_noalloc(const npfem_cell_type* type, npfem_pr
   P.slot_bytes = slot;
   P.z_in_smem = z_in_smem;
   P.solve_per_coord = 0;
+  P.solve_cells = 1;
   const size_t smem = z_in_smem ? zbytes * kWarpsPerBlock : 0;
   if (prec == NPFEM_FP64)
     npfem_step_kernel<double><<<blocks, 32 * kWarpsPerBlock, smem, st>>>(

@@ -18,7 +18,11 @@
 namespace npfem {
 
 constexpr int kSplitMaxIters = 32;
-constexpr int kSplitCounters = 2 + 2 * kSplitMaxIters;  // queue counters per cell type and step
+// Device counters per cell type and step: [0] k_begin queue, [1 + 2i] / [2 + 2i] queues of
+// k_solve / k_iter of iteration i, [kActiveCountOff + i] length of the list of cells
+// that still iterate at iteration i (appended by k_begin for i = 0, by k_iter(i - 1)).
+constexpr int kActiveCountOff = 2 + 2 * kSplitMaxIters;
+constexpr int kSplitCounters = kActiveCountOff + kSplitMaxIters + 1;
 constexpr size_t kStateBytes = 256;
 
 template <typename S>
@@ -181,32 +185,62 @@ __global__ void __launch_bounds__(128) npfem_k_begin(DevTypeView<S> ty, StepPara
       split_finalize<S>(ty, P, w, st, w.U, w.G, cell, x, v, lane);
       continue;
     }
+    if (lane == 0) P.act_out[atomicAdd(P.act_count_out, 1)] = item;
     NPFEM_PHASE_BEGIN(t_loop1)
     two_loop_first<S>(w, st, w.G, len, lane);
     NPFEM_PHASE_END(t_loop1, kPhTwoLoop, P, lane)
   }
 }
 
-// Q <- A^-1 Q for every cell still iterating.  The solve vector lives in shared memory
-// when P.z_in_smem (interleaved [n+1][3] or per coordinate [n+1]), else in the workspace.
-template <typename S>
+// Vector placement of the solve kernel: kZWorkspace (each cell's [n+1][3] vector in its
+// workspace), kZShared ([n+1][3] per cell in shared memory) or kZSharedPerCoord ([n+1]
+// per cell in shared memory, the three coordinates swept one after another).
+constexpr int kZWorkspace = 0, kZShared = 1, kZSharedPerCoord = 2;
+
+template <typename S, int kCells, int kPlace>
+__device__ __forceinline__ void solve_group(const DevTypeView<S>& ty, const StepParams& P, char* const* base,
+                                            double* zsm, int lane) {
+  constexpr int zc = kPlace == kZSharedPerCoord ? 1 : 3;
+  double* z[kCells];
+  S* q[kCells];
+#pragma unroll
+  for (int c = 0; c < kCells; ++c) {
+    CellWs<S> w = split_ws<S>(base[c], ty);
+    z[c] = kPlace == kZWorkspace ? w.z : zsm + (size_t)c * zc * (ty.n + 1);
+    q[c] = w.Q;
+  }
+  global_solve_n<S, kCells, true>(ty, z, kPlace != kZWorkspace, q, q, lane, kPlace == kZSharedPerCoord);
+}
+
+// Q <- A^-1 Q for every cell still iterating (the compacted list of iteration i).  A
+// warp claims kCells list entries at a time and sweeps them together, so each factor
+// entry it loads serves 3 x kCells right-hand sides; a short last group goes cell by
+// cell.  One instantiation per cell count and vector placement keeps a single sweep
+// variant (and its register allocation) per kernel.
+template <typename S, int kCells, int kPlace>
 __global__ void __launch_bounds__(128) npfem_k_solve(DevTypeView<S> ty, StepParams P) {
   extern __shared__ double smem_z[];
+  constexpr int zc = kPlace == kZSharedPerCoord ? 1 : 3;
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const int zc = P.solve_per_coord ? 1 : 3;
+  double* zsm = smem_z + (size_t)wib * kCells * zc * (ty.n + 1);
+  const int total = *P.act_count_in;
   for (;;) {
     int item = 0;
-    if (lane == 0) item = atomicAdd(P.queue_counter, 1);
+    if (lane == 0) item = atomicAdd(P.queue_counter, kCells);
     item = __shfl_sync(kFull, item, 0);
-    if (item >= P.ncells_list) break;
-    char* base = P.scratch + (size_t)item * P.slot_bytes;
-    const CellState<S>* st = reinterpret_cast<const CellState<S>*>(base);
-    if (st->k >= st->iters) continue;
-    CellWs<S> w = split_ws<S>(base, ty);
-    double* z = P.z_in_smem ? smem_z + (size_t)wib * zc * (ty.n + 1) : w.z;
+    if (item >= total) break;
+    char* base[kCells];
+    const int cnt = total - item < kCells ? total - item : kCells;
+#pragma unroll
+    for (int c = 0; c < kCells; ++c)
+      base[c] = P.scratch + (size_t)P.act_in[c < cnt ? item + c : item] * P.slot_bytes;
     NPFEM_PHASE_BEGIN(t_solve)
-    global_solve<S>(ty, z, P.z_in_smem != 0, w.Q, w.Q, lane, P.solve_per_coord != 0);
+    if (cnt == kCells) {
+      solve_group<S, kCells, kPlace>(ty, P, base, zsm, lane);
+    } else {
+      for (int c = 0; c < cnt; ++c) solve_group<S, 1, kPlace>(ty, P, base + c, zsm, lane);
+    }
     NPFEM_PHASE_END(t_solve, kPhSolve, P, lane)
   }
 }
@@ -319,6 +353,7 @@ __global__ void __launch_bounds__(128) npfem_k_iter(DevTypeView<S> ty, StepParam
     __syncwarp();
     // the accepted trial (UT, GT) is the new current iterate
     if (k + 1 < iters) {
+      if (lane == 0) P.act_out[atomicAdd(P.act_count_out, 1)] = item;
       NPFEM_PHASE_BEGIN(t_loop1)
       two_loop_first<S>(w, st, GT, len, lane);
       NPFEM_PHASE_END(t_loop1, kPhTwoLoop, P, lane)

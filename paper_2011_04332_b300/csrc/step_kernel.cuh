@@ -44,6 +44,11 @@ struct StepParams {
   size_t slot_bytes;
   int z_in_smem;               // 1: FP64 solve vector in dynamic shared memory
   int solve_per_coord;         // 1: sweep x, y, z one after another with a one-coordinate vector
+  int solve_cells;             // split mode: cells a warp of the solve kernel sweeps together (1..4)
+  const int* act_in;           // split mode: list of cells iterating at this iteration (k_solve)
+  const int* act_count_in;     //   and its length
+  int* act_out;                // split mode: list of cells iterating at the next iteration
+  int* act_count_out;          //   (appended by k_begin / k_iter) and its length
   unsigned long long* phase_cycles;  // [kPhases] per-phase SM cycles summed over warps
 };
 
@@ -349,11 +354,19 @@ __device__ __forceinline__ void sts_f64(uint32_t a, double v) {
   asm volatile("st.shared.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
 }
 
-template <bool kShared, int kComp>
-__device__ __forceinline__ void chunk_sweep(int nc, const int32_t* __restrict__ meta,
-                                            const uint32_t* __restrict__ rc, const double* __restrict__ val,
-                                            double* z, int n, int lane) {
-  const uint32_t zs = kShared ? (uint32_t)__cvta_generic_to_shared(z) : 0u;
+// One triangular sweep (Eqs. (7)-(8): the prefactored global step) over the packed
+// 32-entry chunks of L, applied to kCells solve vectors at once: cells of one type
+// share L, so every entry (r, j, l) loaded from the factor stream updates
+// z_c[r] -= l * z_c[j] for all kCells cells and kComp coordinates.  Each z_c is its
+// own array ([n+1][kComp]: row n is the pad row of inactive lanes), so every shared
+// memory access keeps the bank pattern the chunk packing was scheduled for.
+template <bool kShared, int kComp, int kCells>
+__device__ __forceinline__ void chunk_sweep_n(int nc, const int32_t* __restrict__ meta,
+                                              const uint32_t* __restrict__ rc, const double* __restrict__ val,
+                                              double* const* z, int n, int lane) {
+  uint32_t zs[kCells];
+#pragma unroll
+  for (int c = 0; c < kCells; ++c) zs[c] = kShared ? (uint32_t)__cvta_generic_to_shared(z[c]) : 0u;
   int mb[kPrefetch];
   uint32_t eb[kPrefetch];
   double vb[kPrefetch];
@@ -385,25 +398,34 @@ __device__ __forceinline__ void chunk_sweep(int nc, const int32_t* __restrict__ 
         }
         if (m & 1) __syncwarp();
         const int r = (int)(e & 0xffffu), j = (int)(e >> 16);
+        double xj[kCells][kComp], zr[kCells][kComp];
         if (kShared) {
-          const uint32_t aj = zs + 8u * kComp * (uint32_t)j, ar = zs + 8u * kComp * (uint32_t)r;
-          double xj[kComp], zr[kComp];
+          const uint32_t oj = 8u * kComp * (uint32_t)j, orr = 8u * kComp * (uint32_t)r;
 #pragma unroll
-          for (int c = 0; c < kComp; ++c) xj[c] = lds_f64(aj + 8 * c);
+          for (int c = 0; c < kCells; ++c)
 #pragma unroll
-          for (int c = 0; c < kComp; ++c) zr[c] = fma(-l, xj[c], lds_f64(ar + 8 * c));
+            for (int d = 0; d < kComp; ++d) xj[c][d] = lds_f64(zs[c] + oj + 8 * d);
 #pragma unroll
-          for (int c = 0; c < kComp; ++c) sts_f64(ar + 8 * c, zr[c]);
+          for (int c = 0; c < kCells; ++c)
+#pragma unroll
+            for (int d = 0; d < kComp; ++d) zr[c][d] = fma(-l, xj[c][d], lds_f64(zs[c] + orr + 8 * d));
+#pragma unroll
+          for (int c = 0; c < kCells; ++c)
+#pragma unroll
+            for (int d = 0; d < kComp; ++d) sts_f64(zs[c] + orr + 8 * d, zr[c][d]);
         } else {
-          double xj[kComp];
 #pragma unroll
-          for (int c = 0; c < kComp; ++c) xj[c] = z[kComp * j + c];
-          double* zr = z + kComp * r;
-          double a[kComp];
+          for (int c = 0; c < kCells; ++c)
 #pragma unroll
-          for (int c = 0; c < kComp; ++c) a[c] = fma(-l, xj[c], zr[c]);
+            for (int d = 0; d < kComp; ++d) xj[c][d] = z[c][kComp * j + d];
 #pragma unroll
-          for (int c = 0; c < kComp; ++c) zr[c] = a[c];
+          for (int c = 0; c < kCells; ++c)
+#pragma unroll
+            for (int d = 0; d < kComp; ++d) zr[c][d] = fma(-l, xj[c][d], z[c][kComp * r + d]);
+#pragma unroll
+          for (int c = 0; c < kCells; ++c)
+#pragma unroll
+            for (int d = 0; d < kComp; ++d) z[c][kComp * r + d] = zr[c][d];
         }
       }
     }
@@ -411,59 +433,151 @@ __device__ __forceinline__ void chunk_sweep(int nc, const int32_t* __restrict__ 
   __syncwarp();
 }
 
-// R = A^-1 Q for the three coordinates (Q and R may alias).  FP64 throughout:
-// permute, unit-lower forward sweep, D^-1 scaling, unit-upper backward sweep.  Either
-// the three coordinates share each sweep (z is [n+1][3]) or, per_coord, they are swept
-// one after another through a one-coordinate vector (z is [n+1]).
-template <bool kShared, int kComp, typename View>
-__device__ void solve_components(const View& ty, double* z, int n, int lane) {
-  chunk_sweep<kShared, kComp>(ty.nchunks_fwd, ty.fwd_meta, ty.fwd_rc, ty.fwd_val, z, n, lane);
-  for (int r = lane; r < n; r += 32) {
-    const double d = __ldg(&ty.dinv[r]);
+// R = A^-1 Q for kCells cells of one type and kComp coordinates per vector: permute,
+// unit-lower forward sweep, D^-1 scaling, unit-upper backward sweep, all in FP64.
+template <bool kShared, int kComp, int kCells, bool kBlocked, typename View>
+__device__ void solve_components_n(const View& ty, double* const* z, int n, int lane) {
+  chunk_sweep_n<kShared, kComp, kCells>(ty.nchunks_fwd, ty.fwd_meta, ty.fwd_rc, ty.fwd_val, z, n, lane);
+  constexpr int B = kBlocked ? 4 : 1;
+#pragma unroll 1
+  for (int r0 = 0; r0 < n; r0 += 32 * B) {
+    double d[B];
 #pragma unroll
-    for (int c = 0; c < kComp; ++c) z[kComp * r + c] *= d;
+    for (int u = 0; u < B; ++u) {
+      const int r = r0 + 32 * u + lane;
+      d[u] = r < n ? __ldg(&ty.dinv[r]) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int r = r0 + 32 * u + lane;
+      if (r < n)
+#pragma unroll
+        for (int c = 0; c < kCells; ++c)
+#pragma unroll
+          for (int q = 0; q < kComp; ++q) z[c][kComp * r + q] *= d[u];
+    }
   }
   __syncwarp();
-  chunk_sweep<kShared, kComp>(ty.nchunks_bwd, ty.bwd_meta, ty.bwd_rc, ty.bwd_val, z, n, lane);
+  chunk_sweep_n<kShared, kComp, kCells>(ty.nchunks_bwd, ty.bwd_meta, ty.bwd_rc, ty.bwd_val, z, n, lane);
+}
+
+// Rows per lane per block of the permuted gather / scatter and of the D^-1 scaling
+// (kBlocked): every load of a block is issued before any of its stores, so a lane has
+// several independent global loads in flight instead of one round trip per row (the
+// compiler cannot move the loads past stores to possibly aliasing vectors).  The price
+// is registers, so only the solve kernel of the split mode takes it.
+template <int kCells, bool kBlocked>
+struct GatherBlock {
+  static constexpr int value = !kBlocked ? 1 : (kCells >= 3 ? 1 : (kCells == 2 ? 2 : 4));
+};
+
+// z[c][kComp r + q] = Q[c][3 perm[r] + q0 + q] for the rows of the type (q0 = 0 and
+// kComp = 3, or one coordinate q0 with kComp = 1); pad row n = 0.
+template <typename S, int kCells, int kComp, bool kBlocked>
+__device__ __forceinline__ void gather_rhs(const DevTypeView<S>& ty, double* const* z, const S* const* Q, int q0,
+                                           int lane) {
+  constexpr int B = GatherBlock<kCells, kBlocked>::value;
+  const int n = ty.n;
+#pragma unroll 1
+  for (int r0 = 0; r0 < n; r0 += 32 * B) {
+    int v[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int r = r0 + 32 * u + lane;
+      v[u] = r < n ? __ldg(&ty.perm[r]) : -1;
+    }
+    S q[B][kCells][kComp];
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (v[u] >= 0)
+#pragma unroll
+        for (int c = 0; c < kCells; ++c)
+#pragma unroll
+          for (int d = 0; d < kComp; ++d) q[u][c][d] = Q[c][3 * v[u] + q0 + d];
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (v[u] >= 0) {
+        const int r = r0 + 32 * u + lane;
+#pragma unroll
+        for (int c = 0; c < kCells; ++c)
+#pragma unroll
+          for (int d = 0; d < kComp; ++d) z[c][kComp * r + d] = (double)q[u][c][d];
+      }
+  }
+  if (lane < kComp)
+#pragma unroll
+    for (int c = 0; c < kCells; ++c) z[c][kComp * n + lane] = 0.0;
+}
+
+// R[c][3 perm[r] + q0 + q] = z[c][kComp r + q], rounded to S.
+template <typename S, int kCells, int kComp, bool kBlocked>
+__device__ __forceinline__ void scatter_result(const DevTypeView<S>& ty, double* const* z, S* const* R, int q0,
+                                               int lane) {
+  constexpr int B = GatherBlock<kCells, kBlocked>::value;
+  const int n = ty.n;
+#pragma unroll 1
+  for (int r0 = 0; r0 < n; r0 += 32 * B) {
+    int v[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int r = r0 + 32 * u + lane;
+      v[u] = r < n ? __ldg(&ty.perm[r]) : -1;
+    }
+    S o[B][kCells][kComp];
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (v[u] >= 0) {
+        const int r = r0 + 32 * u + lane;
+#pragma unroll
+        for (int c = 0; c < kCells; ++c)
+#pragma unroll
+          for (int d = 0; d < kComp; ++d) o[u][c][d] = (S)z[c][kComp * r + d];
+      }
+#pragma unroll
+    for (int u = 0; u < B; ++u)
+      if (v[u] >= 0)
+#pragma unroll
+        for (int c = 0; c < kCells; ++c)
+#pragma unroll
+          for (int d = 0; d < kComp; ++d) R[c][3 * v[u] + q0 + d] = o[u][c][d];
+  }
+}
+
+// Global solve of kCells cells of one type (Q[c] -> R[c] = A^-1 Q[c], Q and R may
+// alias), the three coordinates interleaved in z[c] ([n+1][3]) or, per_coord with the
+// vectors in shared memory, swept one after another through one-coordinate vectors
+// ([n+1]); both orders do the same FP64 operations per coordinate.
+template <typename S, int kCells, bool kBlocked = false>
+__device__ void global_solve_n(const DevTypeView<S>& ty, double* const* z, bool z_shared, const S* const* Q,
+                               S* const* R, int lane, bool per_coord) {
+  const int n = ty.n;
+  if (!per_coord || !z_shared) {
+    gather_rhs<S, kCells, 3, kBlocked>(ty, z, Q, 0, lane);
+    __syncwarp();
+    if (z_shared)
+      solve_components_n<true, 3, kCells, kBlocked>(ty, z, n, lane);
+    else
+      solve_components_n<false, 3, kCells, kBlocked>(ty, z, n, lane);
+    scatter_result<S, kCells, 3, kBlocked>(ty, z, R, 0, lane);
+    __syncwarp();
+    return;
+  }
+  for (int q = 0; q < 3; ++q) {
+    gather_rhs<S, kCells, 1, kBlocked>(ty, z, Q, q, lane);
+    __syncwarp();
+    solve_components_n<true, 1, kCells, kBlocked>(ty, z, n, lane);
+    scatter_result<S, kCells, 1, kBlocked>(ty, z, R, q, lane);
+    __syncwarp();
+  }
 }
 
 template <typename S>
 __device__ void global_solve(const DevTypeView<S>& ty, double* z, bool z_shared, const S* Q, S* R, int lane,
                              bool per_coord = false) {
-  const int n = ty.n;
-  if (!per_coord) {
-    for (int r = lane; r < n; r += 32) {
-      int v = __ldg(&ty.perm[r]);
-      z[3 * r] = (double)Q[3 * v];
-      z[3 * r + 1] = (double)Q[3 * v + 1];
-      z[3 * r + 2] = (double)Q[3 * v + 2];
-    }
-    if (lane < 3) z[3 * n + lane] = 0.0;
-    __syncwarp();
-    if (z_shared)
-      solve_components<true, 3>(ty, z, n, lane);
-    else
-      solve_components<false, 3>(ty, z, n, lane);
-    for (int r = lane; r < n; r += 32) {
-      int v = __ldg(&ty.perm[r]);
-      R[3 * v] = (S)z[3 * r];
-      R[3 * v + 1] = (S)z[3 * r + 1];
-      R[3 * v + 2] = (S)z[3 * r + 2];
-    }
-    __syncwarp();
-    return;
-  }
-  for (int c = 0; c < 3; ++c) {
-    for (int r = lane; r < n; r += 32) z[r] = (double)Q[3 * __ldg(&ty.perm[r]) + c];
-    if (lane == 0) z[n] = 0.0;
-    __syncwarp();
-    if (z_shared)
-      solve_components<true, 1>(ty, z, n, lane);
-    else
-      solve_components<false, 1>(ty, z, n, lane);
-    for (int r = lane; r < n; r += 32) R[3 * __ldg(&ty.perm[r]) + c] = (S)z[r];
-    __syncwarp();
-  }
+  double* zz[1] = {z};
+  const S* qq[1] = {Q};
+  S* rr[1] = {R};
+  global_solve_n<S, 1>(ty, zz, z_shared, qq, rr, lane, per_coord);
 }
 
 // ------------------------------------------------------------------ one cell

@@ -263,14 +263,16 @@ class Batch:
 
     def set_split_launch(self, type_index: int, shape):
         """npfem_batch_set_split_launch: (iter warps/CTA, iter CTAs/SM, solve warps/CTA,
-        solve CTAs/SM, solve vector in shared memory, per-coordinate solve)."""
-        arr = (C.c_int32 * 6)(*[int(s) for s in shape])
+        solve CTAs/SM, solve vectors in shared memory, per-coordinate solve, cells per
+        solve warp); a 6-tuple keeps one cell per solve warp."""
+        shape = list(shape) + [1] * (7 - len(shape))
+        arr = (C.c_int32 * 7)(*[int(s) for s in shape])
         _check(_lib.npfem_batch_set_split_launch(self.handle, int(type_index), arr))
 
     def get_split_launch(self, type_index: int):
-        out = (C.c_int32 * 7)()
+        out = (C.c_int32 * 8)()
         _check(_lib.npfem_batch_get_split_launch(self.handle, int(type_index), out))
-        return tuple(int(v) for v in out[:6]), bool(out[6])
+        return tuple(int(v) for v in out[:7]), bool(out[7])
 
     def step_host(self, x: np.ndarray, v: np.ndarray, f: np.ndarray, iters=None, iters_default: int = 5,
                   residual=None, status=None, stream: int = 0):

@@ -28,9 +28,10 @@ def candidate_shapes(n_verts: int, smem_per_sm: int = 228 * 1024, smem_per_cta: 
     return out
 
 
-def _time_step(batch: native.Batch, x, v, f, iters, reps: int) -> float:
+def _time_step(batch: native.Batch, x, v, f, iters, reps: int, warm: bool = True) -> float:
     xs, vs = x.clone(), v.clone()
-    batch.step(xs, vs, f, iters=iters)          # warm-up (first touch of the workspace)
+    if warm:
+        batch.step(xs, vs, f, iters=iters)      # warm-up (first touch of the workspace)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     best = float("inf")
     for _ in range(reps):
@@ -72,22 +73,34 @@ def autotune(batch: native.Batch, x, v, f, iters=None, type_sizes: Optional[Dict
     return result
 
 
-SplitShape = Tuple[int, int, int, int, int, int]
+SplitShape = Tuple[int, int, int, int, int, int, int]
+
+# Largest resident warps per SM of the solve kernel for 1..4 cells per warp (register
+# use of the four instantiations on sm_103a: 64, 80, 96, 126 registers per thread).
+SOLVE_MAX_WARPS = {1: 32, 2: 24, 3: 20, 4: 16}
 
 
 def split_solve_candidates(n_verts: int, smem_per_sm: int = 228 * 1024, smem_per_cta: int = 227 * 1024):
-    """(warps per CTA, CTAs per SM, in shared memory, per coordinate) for the solve kernel:
-    8 to 32 warps per SM, solve vectors in shared memory when the SM holds them."""
+    """(warps per CTA, CTAs per SM, in shared memory, per coordinate, cells per warp) for
+    the solve kernel.  Shared-memory placements take the largest CTA count the SM holds
+    (and one less); workspace placements 8 to 32 warps per SM.  At least 4 warps per SM
+    (one per scheduler) and 8 cells in flight per SM."""
     out = []
-    for wpb in (2, 4):
-        for bps in range(1, 17):
-            wps = wpb * bps
-            if wps < 8 or wps > 32:
-                continue
-            out.append((wpb, bps, 0, 0))
+    for cells in (1, 2, 3, 4):
+        wmax = SOLVE_MAX_WARPS[cells]
+        for wpb in (1, 2, 4):
             for pc, zb in ((0, 24 * (n_verts + 1)), (1, 8 * (n_verts + 1))):
-                if wpb * zb <= smem_per_cta and bps * wpb * zb <= smem_per_sm:
-                    out.append((wpb, bps, 1, pc))
+                cta = wpb * cells * zb
+                if cta > smem_per_cta:
+                    continue
+                top = min(16, smem_per_sm // (cta + 1024), wmax // wpb)
+                for bps in sorted({top, top - 1}):
+                    if bps >= 1 and 4 <= wpb * bps and wpb * bps * cells >= 8:
+                        out.append((wpb, bps, 1, pc, cells))
+            if cells != 3:
+                for wps in (8, 16, 24, 32):
+                    if wps <= wmax and wps % wpb == 0 and wps // wpb <= 16:
+                        out.append((wpb, wps // wpb, 0, 0, cells))
     return out
 
 
@@ -114,7 +127,7 @@ def autotune_split(batch: native.Batch, x, v, f, iters=None, reps: int = 1, solv
                 batch.set_split_launch(t, shape)
             except native.NpfemError:
                 continue
-            ms = _time_step(batch, x, v, f, iters, reps)
+            ms = _time_step(batch, x, v, f, iters, reps, warm=False)
             if ms < best_ms:
                 best_ms, cur = ms, shape
         batch.set_split_launch(t, cur)
@@ -124,7 +137,7 @@ def autotune_split(batch: native.Batch, x, v, f, iters=None, reps: int = 1, solv
                 if shape == cur:
                     continue
                 batch.set_split_launch(t, shape)
-                ms = _time_step(batch, x, v, f, iters, reps)
+                ms = _time_step(batch, x, v, f, iters, reps, warm=False)
                 if ms < best_ms:
                     best_ms, cur = ms, shape
             batch.set_split_launch(t, cur)

@@ -336,11 +336,29 @@ def test_kernel_timing_eager_and_in_graph():
     r.batch.set_kernel_timing(False)
 
 
+def _assert_modes_agree(fused, split, prec, b):
+    """The fused and the split kernels are compiled separately, and the compiler may
+    contract multiply-adds differently in them, so their results agree to rounding of a
+    few iterations: 1e-12 (FP64) or 1e-6 (FP32 form) of the cell radius plus four ulps
+    of the stored coordinates; statuses exactly."""
+    xf, vf, rf, sf, af = fused
+    xs, vs, rs, ss, as_ = split
+    assert np.array_equal(sf, ss)
+    rel, dt_ = (1e-12, np.float64) if prec == "fp64" else (1e-6, np.float32)
+    for c in range(b.ncells):
+        s = b.cell_slice(c)
+        rad = np.max(np.linalg.norm(xf[:, s] - xf[:, s].mean(axis=1, keepdims=True), axis=0))
+        ulp = float(np.spacing(dt_(np.max(np.abs(xf[:, s])))))
+        assert np.max(np.abs(xf[:, s] - xs[:, s])) <= rel * rad + 4 * ulp
+        assert np.max(np.abs(vf[:, s] - vs[:, s])) * b.dt <= rel * rad + 4 * ulp
+    assert np.allclose(rf, rs, rtol=1e-3 if prec != "fp64" else 1e-8, atol=1e-7 if prec != "fp64" else 1e-12)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_split_and_fused_modes_are_identical(prec):
+def test_split_and_fused_modes_agree(prec):
     """The split kernels (k_begin, k_solve, k_iter) and the fused persistent kernel run the
-    same arithmetic: identical states, statuses, residuals and step lengths, with ragged
-    per-cell iteration counts including zero and non-default launch shapes."""
+    same arithmetic, with ragged per-cell iteration counts including zero; split launch
+    shapes do not change the split results at all."""
     nat = _native()
     b = I.heterogeneous_batch(n_rbc3=7, n_rbc4=3, n_plt=6, seed=1005)
     it = b.iters.copy()
@@ -353,10 +371,41 @@ def test_split_and_fused_modes_are_identical(prec):
     r.batch.set_mode(True)
     assert r.batch.get_split_launch(0)[1] is True
     split = r.step(b.x, b.v, b.f, iters=it)
-    for a, c in zip(fused, split):
-        assert np.array_equal(a, c)
+    _assert_modes_agree(fused, split, prec, b)
     r.batch.set_split_launch(1, (2, 3, 3, 1, 1, 0))
     r.batch.set_split_launch(2, (4, 2, 2, 2, 0, 1))
     split2 = r.step(b.x, b.v, b.f, iters=it)
-    for a, c in zip(fused, split2):
+    for a, c in zip(split, split2):
         assert np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("cells", [2, 3, 4])
+def test_multi_cell_solve_is_identical(prec, cells):
+    """Several cells per solve warp (shared factor, 3 x cells right-hand sides per entry)
+    in every vector placement gives the one-cell split results bit for bit (and the fused
+    kernel's, as above), with ragged iteration counts (short last groups, cells dropping
+    out of the active lists)."""
+    nat = _native()
+    b = I.heterogeneous_batch(n_rbc3=9, n_rbc4=3, n_plt=11, seed=1006)
+    it = b.iters.copy()
+    it[0] = 0
+    it[5] = 1
+    p = nat.FP64 if prec == "fp64" else nat.FP32FORM
+    r = Runner(b, p)
+    r.batch.set_mode(False)
+    fused = r.step(b.x, b.v, b.f, iters=it)
+    r.batch.set_mode(True)
+    one = r.step(b.x, b.v, b.f, iters=it)
+    _assert_modes_agree(fused, one, prec, b)
+    for placement in [(1, 0), (1, 1), (0, 0)]:
+        for t, wpb in ((0, 1), (1, 2), (2, 1)):
+            shape = (2, 4, wpb, 2, placement[0], placement[1], cells)
+            try:
+                r.batch.set_split_launch(t, shape)
+            except nat.NpfemError:          # vectors of 2562-vertex cells exceed shared memory
+                r.batch.set_split_launch(t, (2, 4, wpb, 2, 0, 0, cells))
+            assert r.batch.get_split_launch(t)[0][6] == cells
+        split = r.step(b.x, b.v, b.f, iters=it)
+        for a, c in zip(one, split):
+            assert np.array_equal(a, c)
