@@ -189,11 +189,16 @@ npfem_status npfem_batch_get_launch(const npfem_batch* batch, int32_t type_index
  * bit 8).  mode 0 ("fused"): one persistent kernel per cell type (any iteration count;
  * also used by split-mode batches when the bound is unknown).  The two modes agree to
  * rounding (their kernels are compiled separately and the compiler may contract
- * multiply-adds differently); split launch shapes never change split-mode results.
+ * multiply-adds differently).  Split launch shapes do not change split-mode results,
+ * except that placement 2 applies the factor updates in another (equally exact) order:
+ * its results agree with the others to FP64 rounding.
  * npfem_batch_set_split_launch sets, per type, shape[7] = {warps per CTA (1..4), CTAs per
- * SM (1..16) of the iteration kernels; warps per CTA (1..4), CTAs per SM (1..16), solve
- * vectors in shared memory, per-coordinate solve, cells per warp (1..4) of the solve
- * kernel: a warp sweeps that many cells of the type together through the shared factor};
+ * SM (1..16) of the iteration kernels; warps per CTA (1..4), CTAs per SM (1..16),
+ * placement of the FP64 solve vectors (0: each cell's workspace, 1: shared memory, one
+ * per warp, 2: shared memory, one per CTA whose 2 or 4 warps sweep the cell together
+ * through a level packing of the factor), per-coordinate solve, cells per warp (1..4)
+ * of the solve kernel: a warp sweeps that many cells of the type together through the
+ * shared factor};
  * NPFEM_ERR_INVALID_ARG outside those ranges, NPFEM_ERR_UNSUPPORTED when a CTA's solve
  * vectors exceed shared memory.  npfem_batch_get_split_launch returns those seven values
  * plus the mode in shape[7] (host array of 8). */

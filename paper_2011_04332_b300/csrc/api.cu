@@ -216,37 +216,58 @@ static void (*solve_kernel(int cells, int place))(DevTypeView<S>, StepParams) {
   return table[cells - 1][place];
 }
 
+// Lets a kernel use up to `optin` bytes of shared memory per block in total (its static
+// shared memory included).
+template <typename F>
+static cudaError_t allow_dynamic_smem(F* kernel, int optin) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - (int)a.sharedSizeBytes);
+}
+
 template <typename S>
 static cudaError_t set_solve_smem_attr(int bytes) {
   cudaError_t e = cudaSuccess;
   for (int c = 1; c <= 4 && e == cudaSuccess; ++c)
-    for (int pl = 1; pl <= 2 && e == cudaSuccess; ++pl)
-      e = cudaFuncSetAttribute(solve_kernel<S>(c, pl), cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    for (int pl = 1; pl <= 2 && e == cudaSuccess; ++pl) e = allow_dynamic_smem(solve_kernel<S>(c, pl), bytes);
+  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[0]>, bytes);
+  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[1]>, bytes);
   return e;
 }
 
 // Dynamic shared memory of a solve-kernel CTA: per warp, `cells` solve vectors of
-// [n+1][3] doubles (or [n+1] per coordinate).
-static size_t split_solve_smem(int n, int wpb, int per_coord, int cells) {
+// [n+1][3] doubles (or [n+1] per coordinate); placement 2 (the CTA's warps sweep one
+// cell together): one vector of [n+1][3] doubles.
+static size_t split_solve_smem(int n, int wpb, int per_coord, int cells, int placement = 1) {
+  if (placement == 2) return sizeof(double) * 3 * ((size_t)n + 1);
   return sizeof(double) * (per_coord ? 1 : 3) * ((size_t)n + 1) * (size_t)wpb * (size_t)cells;
 }
 
 // Default split-mode shapes by size class, from autotuning on B300 (homogeneous 642-vertex
-// batch and the mixed 162/642/2562-vertex batch, FP32 form).
+// batch and the mixed 162/642/2562-vertex batch).
 static void default_split_shape(TypeLaunch& L, int n) {
-  if (n <= 256) {         // platelet-sized: 16 iteration warps/SM; 14 solve warps/SM, interleaved in smem
-    L.it_wpb = 4, L.it_bps = 4;
-    L.sv_wpb = 2, L.sv_bps = 7, L.sv_smem = 1, L.sv_percoord = 0;
-  } else if (n <= 1024) {  // 642-vertex RBC: 14 iteration warps/SM; 32 solve warps/SM, per coordinate in smem
-    L.it_wpb = 2, L.it_bps = 7;
-    L.sv_wpb = 2, L.sv_bps = 16, L.sv_smem = 1, L.sv_percoord = 1;
-  } else {                 // 2562-vertex RBC: 16 warps/SM for both, solve vector in the workspace
-    L.it_wpb = 2, L.it_bps = 8;
-    L.sv_wpb = 2, L.sv_bps = 8, L.sv_smem = 0, L.sv_percoord = 0;
-  }
+  L.sv_percoord = 0;
   L.sv_cells = 1;
-  if (L.sv_smem && (size_t)L.sv_bps * split_solve_smem(n, L.sv_wpb, L.sv_percoord, L.sv_cells) > 220 * 1024)
+  if (n <= 256) {         // platelet-sized: 16 iteration warps/SM; 14 solve warps/SM, one vector per warp
+    L.it_wpb = 4, L.it_bps = 4;
+    L.sv_wpb = 2, L.sv_bps = 7, L.sv_smem = 1;
+  } else if (n <= 1024) {  // 642-vertex RBC: 14 iteration warps/SM; CTAs of 2 warps per cell, 10 per SM
+    L.it_wpb = 2, L.it_bps = 7;
+    L.sv_wpb = 2, L.sv_bps = 10, L.sv_smem = 2;
+  } else {                 // 2562-vertex RBC: 16 iteration warps/SM; CTAs of 4 warps per cell, 3 per SM
+    L.it_wpb = 2, L.it_bps = 8;
+    L.sv_wpb = 4, L.sv_bps = 3, L.sv_smem = 2;
+  }
+  // fewer CTAs per SM where the SM cannot hold that many shared vectors; workspace
+  // vectors where it cannot hold one
+  const size_t cta = split_solve_smem(n, L.sv_wpb, L.sv_percoord, L.sv_cells, L.sv_smem) + 1024;
+  while (L.sv_smem && L.sv_bps > 1 && cta * (size_t)L.sv_bps > 228 * 1024) --L.sv_bps;
+  if (L.sv_smem && cta > 227 * 1024) {
     L.sv_smem = 0;
+    L.sv_wpb = 2, L.sv_bps = 8;
+  }
 }
 
 static npfem_status ensure_cell_scratch(npfem_batch* b, TypeLaunch& L) {
@@ -285,15 +306,24 @@ static npfem_status launch_split(npfem_batch* b, const npfem_cell_type* t, const
     P.queue_counter = L.counter + 1 + 2 * it;
     P.act_in = L.active + (size_t)(it & 1) * L.ncells;
     P.act_count_in = act_count + it;
-    P.z_in_smem = L.sv_smem;
+    P.z_in_smem = L.sv_smem == 1;
     P.solve_per_coord = L.sv_percoord;
     P.solve_cells = std::max(1, std::min(4, L.sv_cells));
     const HostType& H = t->host;
-    size_t smem = L.sv_smem ? split_solve_smem(H.n, L.sv_wpb, L.sv_percoord, P.solve_cells) : 0;
-    const int per_cta = L.sv_wpb * P.solve_cells;
-    int grid = std::max(1, std::min<int>(b->sms * L.sv_bps, (L.ncells + per_cta - 1) / per_cta));
-    const int place = !L.sv_smem ? kZWorkspace : (L.sv_percoord ? kZSharedPerCoord : kZShared);
-    solve_kernel<S>(P.solve_cells, place)<<<grid, 32 * L.sv_wpb, smem, st>>>(view, P);
+    if (L.sv_smem == 2) {  // CTA-cooperative: one cell per CTA of sv_wpb warps
+      const size_t smem = split_solve_smem(H.n, L.sv_wpb, 0, 1, 2);
+      const int grid = std::max(1, std::min<int>(b->sms * L.sv_bps, L.ncells));
+      if (L.sv_wpb == kCtaWarps[0])
+        npfem_k_solve_cta<S, kCtaWarps[0]><<<grid, 32 * kCtaWarps[0], smem, st>>>(view, P);
+      else
+        npfem_k_solve_cta<S, kCtaWarps[1]><<<grid, 32 * kCtaWarps[1], smem, st>>>(view, P);
+    } else {
+      size_t smem = L.sv_smem ? split_solve_smem(H.n, L.sv_wpb, L.sv_percoord, P.solve_cells) : 0;
+      const int per_cta = L.sv_wpb * P.solve_cells;
+      int grid = std::max(1, std::min<int>(b->sms * L.sv_bps, (L.ncells + per_cta - 1) / per_cta));
+      const int place = !L.sv_smem ? kZWorkspace : (L.sv_percoord ? kZSharedPerCoord : kZShared);
+      solve_kernel<S>(P.solve_cells, place)<<<grid, 32 * L.sv_wpb, smem, st>>>(view, P);
+    }
   } else {
     P.queue_counter = L.counter + 2 + 2 * it;
     P.act_out = L.active + (size_t)((it + 1) & 1) * L.ncells;
@@ -432,12 +462,38 @@ npfem_status npfem_create_cell_type(const npfem_mesh* mesh, const npfem_material
   UP(H.bwd_rc, brow);
   UP(H.bwd_val, bval);
 #undef UP
+  const int32_t *cfm[kCtaPacks], *cbm[kCtaPacks];
+  const uint32_t *cfr[kCtaPacks], *cbr[kCtaPacks];
+  const double *cfv[kCtaPacks], *cbv[kCtaPacks];
+  for (int i = 0; i < kCtaPacks; ++i) {
+    const HostType::LevelPack& P = H.cta[i];
+    if (e == cudaSuccess) e = t->mem.upload(P.fwd_meta, &cfm[i]);
+    if (e == cudaSuccess) e = t->mem.upload(P.fwd_rc, &cfr[i]);
+    if (e == cudaSuccess) e = t->mem.upload(P.fwd_val, &cfv[i]);
+    if (e == cudaSuccess) e = t->mem.upload(P.bwd_meta, &cbm[i]);
+    if (e == cudaSuccess) e = t->mem.upload(P.bwd_rc, &cbr[i]);
+    if (e == cudaSuccess) e = t->mem.upload(P.bwd_val, &cbv[i]);
+  }
   if (e == cudaSuccess)
     e = upload_precision<double>(t, &t->v64, tris, hinges, inc_ptr, inc_code, perm, dinv, fcol, frow, fval, bcol,
                                  brow, bval);
   if (e == cudaSuccess)
     e = upload_precision<float>(t, &t->v32, tris, hinges, inc_ptr, inc_code, perm, dinv, fcol, frow, fval, bcol,
                                 brow, bval);
+  if (e == cudaSuccess) {
+    for (int i = 0; i < kCtaPacks; ++i) {
+      const HostType::LevelPack& P = H.cta[i];
+      const int nf = (int)P.fwd_meta.size() / P.W, nb = (int)P.bwd_meta.size() / P.W;
+      t->v64.cta_nlev_fwd[i] = t->v32.cta_nlev_fwd[i] = nf;
+      t->v64.cta_nlev_bwd[i] = t->v32.cta_nlev_bwd[i] = nb;
+      t->v64.cta_fwd_meta[i] = t->v32.cta_fwd_meta[i] = cfm[i];
+      t->v64.cta_fwd_rc[i] = t->v32.cta_fwd_rc[i] = cfr[i];
+      t->v64.cta_fwd_val[i] = t->v32.cta_fwd_val[i] = cfv[i];
+      t->v64.cta_bwd_meta[i] = t->v32.cta_bwd_meta[i] = cbm[i];
+      t->v64.cta_bwd_rc[i] = t->v32.cta_bwd_rc[i] = cbr[i];
+      t->v64.cta_bwd_val[i] = t->v32.cta_bwd_val[i] = cbv[i];
+    }
+  }
   if (e != cudaSuccess) {
     delete t;
     return fail(e == cudaErrorMemoryAllocation ? NPFEM_ERR_OOM : NPFEM_ERR_CUDA,
@@ -737,17 +793,23 @@ npfem_status npfem_batch_set_split_launch(npfem_batch* b, int32_t type_index, co
     if (L.type_index == type_index) {
       const HostType& H = b->types[L.type_index]->host;
       if (shape[0] < 1 || shape[0] > 4 || shape[1] < 1 || shape[1] > 16 || shape[2] < 1 || shape[2] > 4 ||
-          shape[3] < 1 || shape[3] > 16 || shape[6] < 1 || shape[6] > 4)
+          shape[3] < 1 || shape[3] > 16 || shape[6] < 1 || shape[6] > 4 || shape[4] < 0 || shape[4] > 2)
         return fail(NPFEM_ERR_INVALID_ARG,
-                    "batch_set_split_launch: warps/CTA in 1..4, CTAs/SM in 1..16, cells per solve warp in 1..4");
-      size_t smem = shape[4] ? split_solve_smem(H.n, shape[2], shape[5], shape[6]) : 0;
+                    "batch_set_split_launch: warps/CTA in 1..4, CTAs/SM in 1..16, cells per solve warp in 1..4, "
+                    "placement in 0..2");
+      if (shape[4] == 2 && ((shape[2] != kCtaWarps[0] && shape[2] != kCtaWarps[1]) || shape[5] != 0 || shape[6] != 1))
+        return fail(NPFEM_ERR_INVALID_ARG,
+                    "batch_set_split_launch: a CTA-cooperative solve takes 2 or 4 warps per CTA, one cell, "
+                    "interleaved coordinates");
+      size_t smem = shape[4] ? split_solve_smem(H.n, shape[2], shape[5], shape[6], shape[4]) : 0;
+      if (shape[4] == 2) smem += 16;  // the CTA kernel's static shared memory (rounded up)
       if (smem > (size_t)b->smem_optin)
         return fail(NPFEM_ERR_UNSUPPORTED, "batch_set_split_launch: solve vectors exceed shared memory");
       L.it_wpb = shape[0];
       L.it_bps = shape[1];
       L.sv_wpb = shape[2];
       L.sv_bps = shape[3];
-      L.sv_smem = shape[4] ? 1 : 0;
+      L.sv_smem = shape[4];
       L.sv_percoord = shape[5] ? 1 : 0;
       L.sv_cells = shape[6];
       return NPFEM_OK;

@@ -8,6 +8,7 @@
 // Implementation and architecture section).  It depends only on the rest mesh,
 // the weights and dt, so it is factored once per cell type.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <map>
@@ -141,21 +142,20 @@ int64_t symbolic(const Graph& g, const std::vector<int>& order, std::vector<std:
   return nnz;
 }
 
-// One update of a triangular sweep: z[t] -= v * z[s], valid once every update that
-// targets s has been applied.  Indices satisfy t > s.
-struct SweepOp {
-  int t, s;
-  double v;
-};
+}  // namespace
 
-// Pack the updates of one sweep into chunks of kChunk (one update per lane): each
-// chunk's sources are final before it starts, its targets are distinct, and at most
-// kBankCap targets share a shared-memory bank class (t mod 16; a row of three doubles
-// starts at bank 6t mod 32).  Greedy list scheduling, sources with the longest
-// remaining dependency chain first.  `relabel` maps r -> n-1-r when emitting indices.
-void pack_sweep(int n, const std::vector<SweepOp>& ops, bool relabel, std::vector<int32_t>* meta,
+// Pack the updates of one sweep into levels of W sub-chunks of kChunk updates (one per
+// lane; W = 1: one warp's chunks): every level's sources are final before it starts,
+// its targets are distinct, and in each sub-chunk at most kBankCap targets share a
+// shared-memory bank class (t mod 16; a row of three doubles starts at bank 6t mod 32).
+// Greedy list scheduling, sources with the longest remaining dependency chain first;
+// sub-chunks fill in order.  A level that reads or writes a row written since the last
+// synchronisation gets bit 0 (synchronise first), so the levels between two
+// synchronisations commute.  `relabel` maps r -> n-1-r when emitting indices.
+void pack_sweep(int n, const std::vector<SweepOp>& ops, bool relabel, int W, std::vector<int32_t>* meta,
                 std::vector<uint32_t>* rc, std::vector<double>* val) {
   constexpr int kBankCap = 3;
+  const int width = W * kChunk;
   std::vector<std::vector<int>> by_src(n);
   std::vector<int> remaining(n, 0);
   for (int k = 0; k < (int)ops.size(); ++k) {
@@ -173,14 +173,16 @@ void pack_sweep(int n, const std::vector<SweepOp>& ops, bool relabel, std::vecto
   for (int s = 0; s < n; ++s)
     if (remaining[s] == 0 && !by_src[s].empty()) ready.insert({-dist[s], s});
   auto emit_index = [&](int r) { return relabel ? n - 1 - r : r; };
-  std::vector<char> dirty(n + 1, 0), in_chunk(n + 1, 0);
+  std::vector<char> dirty(n + 1, 0), in_level(n + 1, 0);
   std::vector<int> dirty_list;
   size_t done = 0;
   while (done < ops.size()) {
-    std::vector<int> chunk;
-    int cls[16] = {0};
+    std::vector<std::vector<int>> sub(W);
+    std::vector<std::array<int, 16>> cls(W);
+    for (auto& c : cls) c.fill(0);
+    int count = 0;
     std::vector<std::pair<int, int>> revisit;
-    while (!ready.empty() && (int)chunk.size() < kChunk) {
+    while (!ready.empty() && count < width) {
       auto it = ready.begin();
       auto key = *it;
       ready.erase(it);
@@ -190,10 +192,14 @@ void pack_sweep(int n, const std::vector<SweepOp>& ops, bool relabel, std::vecto
       for (size_t q = next[s]; q < lst.size(); ++q) {
         int k = lst[q];
         int t = ops[k].t;
-        if ((int)chunk.size() < kChunk && !in_chunk[t] && cls[emit_index(t) & 15] < kBankCap) {
-          chunk.push_back(k);
-          in_chunk[t] = 1;
-          cls[emit_index(t) & 15]++;
+        const int b = emit_index(t) & 15;
+        int w = 0;
+        while (w < W && ((int)sub[w].size() >= kChunk || cls[w][b] >= kBankCap)) ++w;
+        if (count < width && !in_level[t] && w < W) {
+          sub[w].push_back(k);
+          in_level[t] = 1;
+          cls[w][b]++;
+          ++count;
         } else {
           keep.push_back(k);
         }
@@ -209,40 +215,43 @@ void pack_sweep(int n, const std::vector<SweepOp>& ops, bool relabel, std::vecto
     for (auto& key : revisit) ready.insert(key);
     // hazard with rows written since the last synchronisation
     bool hazard = false;
-    for (int k : chunk)
-      if (dirty[ops[k].t] || dirty[ops[k].s]) hazard = true;
+    for (auto& sc : sub)
+      for (int k : sc)
+        if (dirty[ops[k].t] || dirty[ops[k].s]) hazard = true;
     if (hazard) {
       for (int r : dirty_list) dirty[r] = 0;
       dirty_list.clear();
     }
-    meta->push_back(hazard ? 1 : 0);
-    for (int l = 0; l < kChunk; ++l) {
-      if (l < (int)chunk.size()) {
-        const SweepOp& op = ops[chunk[l]];
-        rc->push_back((uint32_t)emit_index(op.t) | ((uint32_t)emit_index(op.s) << 16));
-        val->push_back(op.v);
-      } else {
-        rc->push_back((uint32_t)n | ((uint32_t)n << 16));
-        val->push_back(0.0);
+    for (int w = 0; w < W; ++w) {
+      meta->push_back((hazard ? 1 : 0) | (sub[w].empty() && W > 1 ? 2 : 0));
+      for (int l = 0; l < kChunk; ++l) {
+        if (l < (int)sub[w].size()) {
+          const SweepOp& op = ops[sub[w][l]];
+          rc->push_back((uint32_t)emit_index(op.t) | ((uint32_t)emit_index(op.s) << 16));
+          val->push_back(op.v);
+        } else {
+          rc->push_back((uint32_t)n | ((uint32_t)n << 16));
+          val->push_back(0.0);
+        }
       }
     }
-    for (int k : chunk) {
-      int t = ops[k].t;
-      in_chunk[t] = 0;
-      if (!dirty[t]) {
-        dirty[t] = 1;
-        dirty_list.push_back(t);
+    for (auto& sc : sub)
+      for (int k : sc) {
+        int t = ops[k].t;
+        in_level[t] = 0;
+        if (!dirty[t]) {
+          dirty[t] = 1;
+          dirty_list.push_back(t);
+        }
       }
-    }
-    done += chunk.size();
-    for (int k : chunk) {
-      int t = ops[k].t;
-      if (--remaining[t] == 0 && !by_src[t].empty()) ready.insert({-dist[t], t});
-    }
+    done += count;
+    for (auto& sc : sub)
+      for (int k : sc) {
+        int t = ops[k].t;
+        if (--remaining[t] == 0 && !by_src[t].empty()) ready.insert({-dist[t], t});
+      }
   }
 }
-
-}  // namespace
 
 int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double w_strain,
                     double w_bend, double w_area, double w_vol, double density, double dt,
@@ -500,8 +509,14 @@ int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double
       fwd.push_back({i, j, Lval[j][q]});
       bwd.push_back({n - 1 - j, n - 1 - i, Lval[j][q]});
     }
-  pack_sweep(n, fwd, false, &H.fwd_meta, &H.fwd_rc, &H.fwd_val);
-  pack_sweep(n, bwd, true, &H.bwd_meta, &H.bwd_rc, &H.bwd_val);
+  pack_sweep(n, fwd, false, 1, &H.fwd_meta, &H.fwd_rc, &H.fwd_val);
+  pack_sweep(n, bwd, true, 1, &H.bwd_meta, &H.bwd_rc, &H.bwd_val);
+  for (int i = 0; i < kCtaPacks; ++i) {
+    HostType::LevelPack& P = H.cta[i];
+    P.W = kCtaWarps[i];
+    pack_sweep(n, fwd, false, P.W, &P.fwd_meta, &P.fwd_rc, &P.fwd_val);
+    pack_sweep(n, bwd, true, P.W, &P.bwd_meta, &P.bwd_rc, &P.bwd_val);
+  }
   return NPFEM_OK;
 }
 

@@ -14,6 +14,8 @@ constexpr double kCurvatureEps = 1e-12;  // keep pair only if s.y > eps |s||y|
 constexpr double kDegenerateDet = 1e-30; // det(F^T F) below this: triangle skipped
 constexpr double kDegenerateNorm = 1e-30;
 constexpr int kChunk = 32;               // entries per triangular-solve chunk (one per lane)
+constexpr int kCtaPacks = 2;             // level packings for CTA-cooperative sweeps
+constexpr int kCtaWarps[kCtaPacks] = {2, 4};
 
 // Host-side result of the per-type setup (all FP64; the device upload makes FP32
 // copies of the element constants for the FP32-form kernels).
@@ -45,7 +47,31 @@ struct HostType {
   std::vector<int32_t> fwd_meta, bwd_meta;   // [nchunks]
   std::vector<uint32_t> fwd_rc, bwd_rc;      // [nchunks*32] row | col << 16
   std::vector<double> fwd_val, bwd_val;      // [nchunks*32]
+  // The same sweeps packed for a CTA of W warps that sweeps one cell together: levels
+  // of W sub-chunks of 32 updates (sub-chunk w of level L at [L*W + w]); the targets of
+  // a level are distinct.  meta[L*W + w] bit 0: barrier of the CTA before level L (it
+  // reads or writes a row written since the last barrier; equal for all w); bit 1:
+  // sub-chunk w of level L is empty.
+  struct LevelPack {
+    int W = 0;
+    std::vector<int32_t> fwd_meta, bwd_meta;   // [nlevels*W]
+    std::vector<uint32_t> fwd_rc, bwd_rc;      // [nlevels*W*32]
+    std::vector<double> fwd_val, bwd_val;      // [nlevels*W*32]
+  };
+  LevelPack cta[kCtaPacks];                    // W = kCtaWarps[i]
 };
+
+// One update of a triangular sweep: z[t] -= v * z[s], valid once every update that
+// targets s has been applied.  Indices satisfy t > s (in the sweep's own order).
+struct SweepOp {
+  int t, s;
+  double v;
+};
+
+// Pack the updates of one sweep into levels of W x 32 updates (relabel maps r -> n-1-r
+// when emitting indices); see HostType for the layout.
+void pack_sweep(int n, const std::vector<SweepOp>& ops, bool relabel, int W, std::vector<int32_t>* meta,
+                std::vector<uint32_t>* rc, std::vector<double>* val);
 
 // Build the host type.  Returns 0 or a negative NPFEM_ERR_* code with a message.
 int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double w_strain,
@@ -57,6 +83,7 @@ template <typename S>
 struct DevTypeView {
   int n, T, E;
   int nchunks_fwd, nchunks_bwd;
+  int cta_nlev_fwd[kCtaPacks], cta_nlev_bwd[kCtaPacks];   // levels of the CTA packings
   const int32_t* tris;      // [T][3]
   const S* Dinv;            // [T][3]
   const S* w_tri;           // [T]
@@ -79,6 +106,12 @@ struct DevTypeView {
   const int32_t* bwd_meta;
   const uint32_t* bwd_rc;
   const double* bwd_val;
+  const int32_t* cta_fwd_meta[kCtaPacks];
+  const uint32_t* cta_fwd_rc[kCtaPacks];
+  const double* cta_fwd_val[kCtaPacks];
+  const int32_t* cta_bwd_meta[kCtaPacks];
+  const uint32_t* cta_bwd_rc[kCtaPacks];
+  const double* cta_bwd_val[kCtaPacks];
   double A0, V0, w_area, w_vol, dt;
 };
 

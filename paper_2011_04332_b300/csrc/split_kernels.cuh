@@ -245,6 +245,113 @@ __global__ void __launch_bounds__(128) npfem_k_solve(DevTypeView<S> ty, StepPara
   }
 }
 
+// One sweep of a CTA of W warps over a level packing (Eqs. (7)-(8), as in chunk_sweep_n
+// but cooperative): warp w applies sub-chunk w of every level to the shared vector
+// zs ([n+1][3] doubles in shared memory), with a barrier of the CTA before every level
+// that touches a row written since the last barrier; the levels in between commute.
+template <int W>
+__device__ __forceinline__ void cta_sweep(int nlev, const int32_t* __restrict__ meta, const uint32_t* __restrict__ rc,
+                                          const double* __restrict__ val, uint32_t zs, int n, int warp, int lane) {
+  int mb[kPrefetch];
+  uint32_t eb[kPrefetch];
+  double vb[kPrefetch];
+#pragma unroll
+  for (int k = 0; k < kPrefetch; ++k) {
+    if (k < nlev) {
+      const size_t sc = (size_t)k * W + warp;
+      mb[k] = __ldg(meta + sc);
+      eb[k] = __ldg(rc + sc * kChunk + lane);
+      vb[k] = __ldg(val + sc * kChunk + lane);
+    } else {
+      mb[k] = 2;
+      eb[k] = (uint32_t)n | ((uint32_t)n << 16);
+      vb[k] = 0.0;
+    }
+  }
+  for (int base = 0; base < nlev; base += kPrefetch) {
+#pragma unroll
+    for (int k = 0; k < kPrefetch; ++k) {
+      const int lv = base + k;
+      if (lv < nlev) {
+        const int m = mb[k];
+        const uint32_t e = eb[k];
+        const double l = vb[k];
+        const int nx = lv + kPrefetch;
+        if (nx < nlev) {
+          const size_t sc = (size_t)nx * W + warp;
+          mb[k] = __ldg(meta + sc);
+          eb[k] = __ldg(rc + sc * kChunk + lane);
+          vb[k] = __ldg(val + sc * kChunk + lane);
+        }
+        if (m & 1) __syncthreads();
+        if (!(m & 2)) {
+          const int r = (int)(e & 0xffffu), j = (int)(e >> 16);
+          const uint32_t aj = zs + 24u * (uint32_t)j, ar = zs + 24u * (uint32_t)r;
+          const double x0 = lds_f64(aj), x1 = lds_f64(aj + 8), x2 = lds_f64(aj + 16);
+          const double z0 = fma(-l, x0, lds_f64(ar)), z1 = fma(-l, x1, lds_f64(ar + 8)),
+                       z2 = fma(-l, x2, lds_f64(ar + 16));
+          sts_f64(ar, z0);
+          sts_f64(ar + 8, z1);
+          sts_f64(ar + 16, z2);
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Q <- A^-1 Q for every cell still iterating, one cell per CTA of W warps at a time:
+// for cells whose FP64 solve vector ([n+1][3], 24(n+1) bytes) is too large to keep
+// one per warp in shared memory.  The CTA's warps share the vector and sweep the
+// W-warp level packing of the factor together.
+template <typename S, int W>
+__global__ void __launch_bounds__(128) npfem_k_solve_cta(DevTypeView<S> ty, StepParams P) {
+  static_assert(W == kCtaWarps[0] || W == kCtaWarps[1], "no level packing for this CTA width");
+  constexpr int pk = W == kCtaWarps[0] ? 0 : 1;
+  extern __shared__ double smem_z[];
+  __shared__ int s_item;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = ty.n;
+  const int total = *P.act_count_in;
+  const uint32_t zs = (uint32_t)__cvta_generic_to_shared(smem_z);
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(P.queue_counter, 1);
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= total) break;
+    char* base = P.scratch + (size_t)P.act_in[item] * P.slot_bytes;
+    CellWs<S> w = split_ws<S>(base, ty);
+    NPFEM_PHASE_BEGIN(t_solve)
+    for (int r = tid; r < n; r += 32 * W) {
+      const int v = __ldg(&ty.perm[r]);
+      const S q0 = w.Q[3 * v], q1 = w.Q[3 * v + 1], q2 = w.Q[3 * v + 2];
+      smem_z[3 * r] = (double)q0;
+      smem_z[3 * r + 1] = (double)q1;
+      smem_z[3 * r + 2] = (double)q2;
+    }
+    if (tid < 3) smem_z[3 * n + tid] = 0.0;
+    __syncthreads();
+    cta_sweep<W>(ty.cta_nlev_fwd[pk], ty.cta_fwd_meta[pk], ty.cta_fwd_rc[pk], ty.cta_fwd_val[pk], zs, n, warp, lane);
+    for (int r = tid; r < n; r += 32 * W) {
+      const double d = __ldg(&ty.dinv[r]);
+      smem_z[3 * r] *= d;
+      smem_z[3 * r + 1] *= d;
+      smem_z[3 * r + 2] *= d;
+    }
+    __syncthreads();
+    cta_sweep<W>(ty.cta_nlev_bwd[pk], ty.cta_bwd_meta[pk], ty.cta_bwd_rc[pk], ty.cta_bwd_val[pk], zs, n, warp, lane);
+    for (int r = tid; r < n; r += 32 * W) {
+      const int v = __ldg(&ty.perm[r]);
+      w.Q[3 * v] = (S)smem_z[3 * r];
+      w.Q[3 * v + 1] = (S)smem_z[3 * r + 1];
+      w.Q[3 * v + 2] = (S)smem_z[3 * r + 2];
+    }
+    NPFEM_PHASE_END(t_solve, kPhSolve, P, warp == 0 ? lane : 1)
+    __syncthreads();
+  }
+}
+
 template <typename S>
 __global__ void __launch_bounds__(128) npfem_k_iter(DevTypeView<S> ty, StepParams P, S* x, S* v) {
   const int lane = threadIdx.x & 31;

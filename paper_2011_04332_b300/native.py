@@ -263,8 +263,9 @@ class Batch:
 
     def set_split_launch(self, type_index: int, shape):
         """npfem_batch_set_split_launch: (iter warps/CTA, iter CTAs/SM, solve warps/CTA,
-        solve CTAs/SM, solve vectors in shared memory, per-coordinate solve, cells per
-        solve warp); a 6-tuple keeps one cell per solve warp."""
+        solve CTAs/SM, solve-vector placement (0 workspace, 1 shared memory per warp,
+        2 shared memory per CTA whose 2 or 4 warps sweep one cell together),
+        per-coordinate solve, cells per solve warp); a 6-tuple keeps one cell per warp."""
         shape = list(shape) + [1] * (7 - len(shape))
         arr = (C.c_int32 * 7)(*[int(s) for s in shape])
         _check(_lib.npfem_batch_set_split_launch(self.handle, int(type_index), arr))

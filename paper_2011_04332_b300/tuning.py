@@ -76,16 +76,27 @@ def autotune(batch: native.Batch, x, v, f, iters=None, type_sizes: Optional[Dict
 SplitShape = Tuple[int, int, int, int, int, int, int]
 
 # Largest resident warps per SM of the solve kernel for 1..4 cells per warp (register
-# use of the four instantiations on sm_103a: 64, 80, 96, 126 registers per thread).
+# use of the four instantiations on sm_103a: 64, 80, 96, 126 registers per thread), and
+# of the CTA-cooperative solve kernel (96 registers).
 SOLVE_MAX_WARPS = {1: 32, 2: 24, 3: 20, 4: 16}
+CTA_MAX_WARPS = 20
 
 
 def split_solve_candidates(n_verts: int, smem_per_sm: int = 228 * 1024, smem_per_cta: int = 227 * 1024):
-    """(warps per CTA, CTAs per SM, in shared memory, per coordinate, cells per warp) for
-    the solve kernel.  Shared-memory placements take the largest CTA count the SM holds
-    (and one less); workspace placements 8 to 32 warps per SM.  At least 4 warps per SM
-    (one per scheduler) and 8 cells in flight per SM."""
+    """(warps per CTA, CTAs per SM, placement, per coordinate, cells per warp) for the
+    solve kernel; placement 0: vectors in the workspace, 1: in shared memory per warp,
+    2: one vector per CTA whose 2 or 4 warps sweep the cell together.  Shared-memory
+    placements take the largest CTA count the SM holds (and one less); workspace
+    placements 8 to 32 warps per SM.  At least 4 warps per SM (one per scheduler) and,
+    per warp, 8 cells in flight per SM."""
     out = []
+    zb = 24 * (n_verts + 1)
+    if zb <= smem_per_cta:
+        for wpb in (2, 4):
+            top = min(16, smem_per_sm // (zb + 1024), CTA_MAX_WARPS // wpb)
+            for bps in sorted({top, top - 1}):
+                if bps >= 1 and wpb * bps >= 4:
+                    out.append((wpb, bps, 2, 0, 1))
     for cells in (1, 2, 3, 4):
         wmax = SOLVE_MAX_WARPS[cells]
         for wpb in (1, 2, 4):

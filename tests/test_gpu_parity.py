@@ -70,9 +70,11 @@ def cell_errors(b, x, xref, radius_from=None):
     return np.array(errs)
 
 
-def compare(b, precision, cells=None, steps=1, iters=None, check_alpha=True, bar=None):
+def compare(b, precision, cells=None, steps=1, iters=None, check_alpha=True, bar=None, shapes=None):
     nat = _native()
     r = Runner(b, precision)
+    for t, shape in (shapes or {}).items():
+        r.batch.set_split_launch(t, shape)
     ots = oracle_types(b)
     x, v, f = b.x.copy(), b.v.copy(), b.f.copy()
     if precision == nat.FP32FORM:
@@ -409,3 +411,35 @@ def test_multi_cell_solve_is_identical(prec, cells):
         split = r.step(b.x, b.v, b.f, iters=it)
         for a, c in zip(one, split):
             assert np.array_equal(a, c)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("warps", [2, 4])
+def test_cta_cooperative_solve(prec, warps):
+    """Placement 2: the 2 or 4 warps of a CTA sweep one cell's shared solve vector
+    through the level packing of the factor, for every type of a mixed batch (162, 642
+    and 2562 vertices, 3..8 iterations): parity with the oracle at the usual bars over
+    two steps, and agreement with the one-warp solve to rounding (the level packing
+    applies the same updates in another order)."""
+    nat = _native()
+    b = I.heterogeneous_batch(n_rbc3=6, n_rbc4=4, n_plt=5, seed=1007)
+    p = nat.FP64 if prec == "fp64" else nat.FP32FORM
+    shapes = {t: (2, 4, warps, 2, 2, 0, 1) for t in range(len(b.types))}
+    compare(b, p, steps=2, shapes=shapes)
+    r = Runner(b, p)
+    one = r.step(b.x, b.v, b.f, iters=b.iters)
+    for t, shape in shapes.items():
+        r.batch.set_split_launch(t, shape)
+        assert r.batch.get_split_launch(t)[0] == shape
+    cta = r.step(b.x, b.v, b.f, iters=b.iters)
+    _assert_modes_agree(one, cta, prec, b)
+
+
+def test_cta_cooperative_shape_validation():
+    """Placement 2 takes 2 or 4 warps per CTA, one cell, interleaved coordinates."""
+    nat = _native()
+    b = I.heterogeneous_batch(n_rbc3=2, n_rbc4=1, n_plt=1, seed=1008)
+    r = Runner(b, nat.FP64)
+    for bad in [(2, 4, 3, 2, 2, 0, 1), (2, 4, 2, 2, 2, 1, 1), (2, 4, 4, 2, 2, 0, 2), (2, 4, 2, 2, 3, 0, 1)]:
+        with pytest.raises(nat.NpfemError):
+            r.batch.set_split_launch(0, bad)
