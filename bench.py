@@ -46,6 +46,9 @@ def make_workload(name: str, rank: int = 0):
     elif name == "homog1776":
         b = I.homogeneous_rbc_batch(ncells=1776, seed=1001 + 100 * rank)
         desc = "homogeneous 1776 RBC (642 vertices; one cell per warp slot of 148 SMs x 12 warps), 5 iterations"
+    elif name == "homog2562":
+        b = I.homogeneous_rbc_batch(ncells=1184, seed=1001 + 100 * rank, subdiv=4)
+        desc = "homogeneous 1184 RBC (2562 vertices, Evans-Fung), 5 iterations"
     elif name == "small":
         b = I.homogeneous_rbc_batch(ncells=64, seed=1001 + 100 * rank)
         desc = "64 RBC (642 vertices), 5 iterations"
@@ -484,7 +487,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="homog4096", choices=["homog4096", "hetero10k", "homog1776", "small"])
+    ap.add_argument("--workload", default="homog4096", choices=["homog4096", "hetero10k", "homog1776", "homog2562", "small"])
     ap.add_argument("--precision", default="fp32form", choices=["fp32form", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=128)

@@ -247,19 +247,18 @@ static size_t split_solve_smem(int n, int wpb, int per_coord, int cells, int pla
 
 // Default split-mode shapes by size class, from autotuning on B300 (homogeneous 642-vertex
 // batch and the mixed 162/642/2562-vertex batch).
-static void default_split_shape(TypeLaunch& L, int n) {
+static void default_split_shape(TypeLaunch& L, int n, npfem_precision prec) {
   L.sv_percoord = 0;
   L.sv_cells = 1;
-  if (n <= 256) {         // platelet-sized: 16 iteration warps/SM; 14 solve warps/SM, one vector per warp
-    L.it_wpb = 4, L.it_bps = 4;
+  if (n <= 256) {         // platelet-sized: 14 solve warps/SM, one vector per warp
     L.sv_wpb = 2, L.sv_bps = 7, L.sv_smem = 1;
-  } else if (n <= 1024) {  // 642-vertex RBC: 14 iteration warps/SM; CTAs of 2 warps per cell, 10 per SM
-    L.it_wpb = 2, L.it_bps = 7;
+  } else if (n <= 1024) {  // 642-vertex RBC: CTAs of 2 warps per cell, 10 per SM
     L.sv_wpb = 2, L.sv_bps = 10, L.sv_smem = 2;
-  } else {                 // 2562-vertex RBC: 16 iteration warps/SM; CTAs of 4 warps per cell, 3 per SM
-    L.it_wpb = 2, L.it_bps = 8;
+  } else {                 // 2562-vertex RBC: CTAs of 4 warps per cell, 3 per SM
     L.sv_wpb = 4, L.sv_bps = 3, L.sv_smem = 2;
   }
+  // iteration kernels: 32 warps per SM in the FP32 form (64 registers), 16 in FP64
+  L.it_wpb = 2, L.it_bps = prec == NPFEM_FP64 ? 8 : 16;
   // fewer CTAs per SM where the SM cannot hold that many shared vectors; workspace
   // vectors where it cannot hold one
   const size_t cta = split_solve_smem(n, L.sv_wpb, L.sv_percoord, L.sv_cells, L.sv_smem) + 1024;
@@ -613,7 +612,7 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
     // when four of them fit in 72 KB (n <= 767), else in the workspace
     const size_t zbytes = sizeof(double) * 3 * ((size_t)H.n + 1);
     const int zs = zbytes * 4 <= 72 * 1024 ? 1 : 0;
-    default_split_shape(L, H.n);
+    default_split_shape(L, H.n, prec);
     npfem_status rc = configure_launch(b, L, 4, 3, zs, 0);
     if (rc != NPFEM_OK) {
       for (TypeLaunch& P : b->launches) {

@@ -18,6 +18,20 @@
 namespace npfem {
 
 constexpr int kSplitMaxIters = 32;
+// Resident 128-thread CTAs per SM that k_begin and k_iter are compiled for (a budget of
+// 65536 / (128 x min_blocks) registers per thread).  The FP32 form is bound by the
+// latency of its gathers, not by arithmetic: 64 registers let 32 warps per SM hold one
+// cell each (4096 cells in one wave instead of two at 16 warps).  The FP64 objective
+// is bound by the FP64 pipe from 12 warps per SM on: 128 registers, 16 warps.
+template <typename S>
+struct IterOccupancy {
+  static constexpr int min_blocks = 4;
+};
+template <>
+struct IterOccupancy<float> {
+  static constexpr int min_blocks = 8;
+};
+
 // Device counters per cell type and step: [0] k_begin queue, [1 + 2i] / [2 + 2i] queues of
 // k_solve / k_iter of iteration i, [kActiveCountOff + i] length of the list of cells
 // that still iterate at iteration i (appended by k_begin for i = 0, by k_iter(i - 1)).
@@ -113,7 +127,7 @@ __device__ void split_finalize(const DevTypeView<S>& ty, const StepParams& P, co
 }
 
 template <typename S>
-__global__ void __launch_bounds__(128) npfem_k_begin(DevTypeView<S> ty, StepParams P, int max_iters, S* x,
+__global__ void __launch_bounds__(128, IterOccupancy<S>::min_blocks) npfem_k_begin(DevTypeView<S> ty, StepParams P, int max_iters, S* x,
                                                      S* v, const S* f) {
   const int lane = threadIdx.x & 31;
   const int n = ty.n, len = 3 * n;
@@ -353,7 +367,7 @@ __global__ void __launch_bounds__(128) npfem_k_solve_cta(DevTypeView<S> ty, Step
 }
 
 template <typename S>
-__global__ void __launch_bounds__(128) npfem_k_iter(DevTypeView<S> ty, StepParams P, S* x, S* v) {
+__global__ void __launch_bounds__(128, IterOccupancy<S>::min_blocks) npfem_k_iter(DevTypeView<S> ty, StepParams P, S* x, S* v) {
   const int lane = threadIdx.x & 31;
   const int n = ty.n, len = 3 * n;
   for (;;) {

@@ -116,8 +116,9 @@ def split_solve_candidates(n_verts: int, smem_per_sm: int = 228 * 1024, smem_per
 
 
 def split_iter_candidates():
-    """(warps per CTA, CTAs per SM) for the iteration kernels: 8 to 16 warps per SM."""
-    return [(wpb, bps) for wpb in (2, 4) for bps in range(1, 9) if 8 <= wpb * bps <= 16]
+    """(warps per CTA, CTAs per SM) for the iteration kernels: 8 to 32 warps per SM (the
+    FP32 form's iteration kernels hold 32 warps per SM, the FP64 ones 16)."""
+    return [(wpb, bps) for wpb in (2, 4) for bps in range(1, 17) if 8 <= wpb * bps <= 32 and (wpb * bps) % 4 == 0]
 
 
 def autotune_split(batch: native.Batch, x, v, f, iters=None, reps: int = 1, solve_only: bool = False) -> Dict[int, dict]:

@@ -374,10 +374,15 @@ def test_split_and_fused_modes_agree(prec):
     assert r.batch.get_split_launch(0)[1] is True
     split = r.step(b.x, b.v, b.f, iters=it)
     _assert_modes_agree(fused, split, prec, b)
-    r.batch.set_split_launch(1, (2, 3, 3, 1, 1, 0))
-    r.batch.set_split_launch(2, (4, 2, 2, 2, 0, 1))
+    # one-warp solves (placements 0 and 1) in two different shapes: identical results
+    for t, shape in enumerate([(2, 8, 2, 7, 1, 0), (2, 8, 2, 8, 0, 0), (4, 4, 2, 7, 1, 0)]):
+        r.batch.set_split_launch(t, shape)
+    split1 = r.step(b.x, b.v, b.f, iters=it)
+    _assert_modes_agree(fused, split1, prec, b)
+    for t, shape in enumerate([(4, 3, 1, 14, 1, 1), (2, 3, 3, 1, 0, 0), (4, 2, 2, 2, 0, 1)]):
+        r.batch.set_split_launch(t, shape)
     split2 = r.step(b.x, b.v, b.f, iters=it)
-    for a, c in zip(split, split2):
+    for a, c in zip(split1, split2):
         assert np.array_equal(a, c)
 
 
@@ -398,6 +403,8 @@ def test_multi_cell_solve_is_identical(prec, cells):
     r.batch.set_mode(False)
     fused = r.step(b.x, b.v, b.f, iters=it)
     r.batch.set_mode(True)
+    for t in range(len(b.types)):            # one cell per warp, vectors in shared memory
+        r.batch.set_split_launch(t, (2, 4, 1, 2, 1, 0, 1))
     one = r.step(b.x, b.v, b.f, iters=it)
     _assert_modes_agree(fused, one, prec, b)
     for placement in [(1, 0), (1, 1), (0, 0)]:
@@ -427,6 +434,8 @@ def test_cta_cooperative_solve(prec, warps):
     shapes = {t: (2, 4, warps, 2, 2, 0, 1) for t in range(len(b.types))}
     compare(b, p, steps=2, shapes=shapes)
     r = Runner(b, p)
+    for t in range(len(b.types)):            # one cell per warp, vectors in shared memory
+        r.batch.set_split_launch(t, (2, 4, 1, 2, 1, 0, 1))
     one = r.step(b.x, b.v, b.f, iters=b.iters)
     for t, shape in shapes.items():
         r.batch.set_split_launch(t, shape)
