@@ -46,6 +46,10 @@ def make_workload(name: str, rank: int = 0):
     elif name == "homog1776":
         b = I.homogeneous_rbc_batch(ncells=1776, seed=1001 + 100 * rank)
         desc = "homogeneous 1776 RBC (642 vertices; one cell per warp slot of 148 SMs x 12 warps), 5 iterations"
+    elif name == "stress20k":
+        b = I.stress_mix_batch(ncells=20000, seed=1005 + 100 * rank)
+        desc = ("serving-shaped mix: 20000 cells (70 % RBC 642v, 10 % RBC 2562v, 20 % PLT 162v), "
+                "5 iterations, force field re-drawn every 10 steps")
     elif name == "homog2562":
         b = I.homogeneous_rbc_batch(ncells=1184, seed=1001 + 100 * rank, subdiv=4)
         desc = "homogeneous 1184 RBC (2562 vertices, Evans-Fung), 5 iterations"
@@ -199,6 +203,12 @@ def run_ours(args, rank, world, local_rank):
     x0 = torch.tensor(b.x, dtype=tdt, device=dev)
     v0 = torch.tensor(b.v, dtype=tdt, device=dev)
     f = torch.tensor(b.f, dtype=tdt, device=dev)
+    fpool = None
+    if args.workload == "stress20k":
+        # coupling-force updates: the step's force buffer takes a re-drawn field every 10 steps
+        from paper_2011_04332_b300 import inputs as I
+        fpool = [f.clone()] + [torch.tensor(I.redrawn_forces(b, b.x, 1005 + 100 * rank, k), dtype=tdt, device=dev)
+                               for k in (1, 2)]
     iters = torch.tensor(b.iters, device=dev)
     res = torch.zeros(b.ncells, dtype=torch.float64, device=dev)
     st = torch.zeros(b.ncells, dtype=torch.int32, device=dev)
@@ -273,6 +283,8 @@ def run_ours(args, rank, world, local_rank):
         for k in range(args.steps):
             flush.zero_()
             ev[k][0].record(stream)
+            if fpool is not None and k % 10 == 0:
+                f.copy_(fpool[(k // 10) % len(fpool)])
             one_step()
             ev[k][1].record(stream)
             # per-kernel durations of this step (events on the kernels' own streams)
@@ -487,7 +499,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="homog4096", choices=["homog4096", "hetero10k", "homog1776", "homog2562", "small"])
+    ap.add_argument("--workload", default="homog4096", choices=["homog4096", "hetero10k", "stress20k", "homog1776", "homog2562", "small"])
     ap.add_argument("--precision", default="fp32form", choices=["fp32form", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=128)

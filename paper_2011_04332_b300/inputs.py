@@ -306,6 +306,26 @@ def heterogeneous_batch(n_rbc3: int = 4500, n_rbc4: int = 4500, n_plt: int = 100
     return placed_cells(types, toc, seed + 7, iters)
 
 
+def stress_mix_batch(ncells: int = 20000, seed: int = 1005, iters: int = 5) -> BatchInputs:
+    """Serving-shaped mix: 70 % 642-vertex RBCs, 10 % 2562-vertex RBCs and 20 % 162-vertex
+    platelets in a seeded random order, `iters` iterations per cell."""
+    n3 = int(round(0.7 * ncells))
+    n4 = int(round(0.1 * ncells))
+    return heterogeneous_batch(n3, n4, ncells - n3 - n4, seed=seed, iters_range=(iters, iters))
+
+
+def redrawn_forces(b: BatchInputs, x: np.ndarray, seed: int, segment: int) -> np.ndarray:
+    """A new seeded force field for the cells of `b` at positions x ([3][N_total]): the
+    Gaussian + linear-shear recipe of the batch generators, drawn from the sub-streams of
+    SeedSequence((seed, segment)); stands in for an updated coupling force."""
+    children = np.random.SeedSequence((seed, segment)).spawn(b.ncells)
+    f = np.empty_like(x)
+    for c in range(b.ncells):
+        s = b.cell_slice(c)
+        f[:, s] = shear_noise_forces(x[:, s].T, np.random.default_rng(children[c])).T
+    return f
+
+
 def small_mixed_batch(seed: int = 7, iters=(2, 4, 5)) -> BatchInputs:
     """A few cells of tiny and small types for quick parity runs."""
     types = [CellTypeSpec(rbc_mesh(1), RBC_MATERIAL),

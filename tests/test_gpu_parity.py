@@ -142,6 +142,18 @@ def test_full_size_batch_sampled_cells(prec):
     compare(b, nat.FP64 if prec == "fp64" else nat.FP32FORM, cells=cells)
 
 
+def test_stress_mix_sampled_cells():
+    """The 20000-cell serving-shaped mix (70 % 642-vertex RBC, 10 % 2562-vertex RBC, 20 %
+    platelets) in the FP32 form with the default launch shapes: 32 sampled cells against the
+    oracle, for the first step and for a step under a re-drawn force field."""
+    nat = _native()
+    b = I.stress_mix_batch()
+    cells = sorted(np.random.default_rng(11).choice(b.ncells, size=32, replace=False).tolist())
+    compare(b, nat.FP32FORM, cells=cells)
+    b.f = I.redrawn_forces(b, b.x, 1005, 1)
+    compare(b, nat.FP32FORM, cells=cells)
+
+
 def test_heterogeneous_types_and_iterations():
     nat = _native()
     b = I.heterogeneous_batch(n_rbc3=6, n_rbc4=3, n_plt=5, seed=1002)
