@@ -241,13 +241,17 @@ def run_ours(args, rank, world, local_rank):
                "bar": 1e-5 if prec == native.FP32FORM else 1e-10}
 
     tuned = None
+    if args.no_tune and args.groups > 0:
+        for t in sorted({int(q) for q in b.type_of_cell}):
+            batch.set_groups(t, args.groups)
     if not args.no_tune:
         # launch-shape autotuning on copies of the state (outside the timed region)
         from paper_2011_04332_b300 import tuning
         t0 = time.perf_counter()
         tuned = tuning.autotune_split(batch, x0, v0, f, iters=iters)
         tuned = {"seconds": round(time.perf_counter() - t0, 1),
-                 "shapes": {str(t): list(r["split_shape"]) for t, r in tuned.items()}}
+                 "shapes": {str(t): list(r["split_shape"]) for t, r in tuned.items()},
+                 "groups": {str(t): r["groups"] for t, r in tuned.items()}}
     batch.set_kernel_timing(True)       # CUDA events around every launch (also inside the graph)
     for _ in range(args.warmup):
         batch.step(x, v, f, iters=iters, residual=res, status=st)
@@ -377,6 +381,7 @@ def run_ours(args, rank, world, local_rank):
                    "launch": "one CUDA graph per step" if graph is not None else "direct npfem_step call",
                    "mode": "split kernels (k_begin, then k_solve + k_iter per iteration and cell type)",
                    "split_shapes": {str(t): list(batch.get_split_launch(t)[0]) for t in sorted(set(int(q) for q in b.type_of_cell))},
+                   "groups": {str(t): batch.get_groups(t) for t in sorted(set(int(q) for q in b.type_of_cell))},
                    "autotune": tuned,
                    "parallelism": "cells sharded across ranks, no collective" if world > 1 else "1 GPU"},
         "residual": {"median": float(np.median(resid)), "max": float(np.max(resid)),
@@ -389,7 +394,8 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "adjoint": adjoint,
         "kernels": kernels,
-        "gpu_launches": args.steps * len(set(int(t) for t in b.type_of_cell)) * (1 + 2 * int(np.max(b.iters))),
+        "gpu_launches": args.steps * sum(min(batch.get_groups(t), int(np.sum(b.type_of_cell == t)))
+                                         for t in set(int(q) for q in b.type_of_cell)) * (1 + 2 * int(np.max(b.iters))),
         "clocks": clk.summary(),
         "wall_s_timed_region": t_wall,
     }
@@ -511,6 +517,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--groups", type=int, default=0,
+                    help="with --no-tune: phase-offset chains per cell type (0: library default)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

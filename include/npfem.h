@@ -193,16 +193,25 @@ npfem_status npfem_batch_get_launch(const npfem_batch* batch, int32_t type_index
  * except that placement 2 applies the factor updates in another (equally exact) order:
  * its results agree with the others to FP64 rounding.
  * npfem_batch_set_split_launch sets, per type, shape[7] = {warps per CTA (1..4), CTAs per
- * SM (1..16) of the iteration kernels; warps per CTA (1..4), CTAs per SM (1..16),
- * placement of the FP64 solve vectors (0: each cell's workspace, 1: shared memory, one
- * per warp, 2: shared memory, one per CTA whose 2 or 4 warps sweep the cell together
- * through a level packing of the factor), per-coordinate solve, cells per warp (1..4)
+ * SM (1..16) of the iteration kernels; warps per CTA (1..4; placement 2: 2, 4, 6 or 8),
+ * CTAs per SM (1..16), placement of the FP64 solve vectors (0: each cell's workspace,
+ * 1: shared memory, one per warp, 2: shared memory, one per CTA whose warps sweep the
+ * cell together through a level packing of the factor), per-coordinate solve, cells per warp (1..4)
  * of the solve kernel: a warp sweeps that many cells of the type together through the
  * shared factor};
  * NPFEM_ERR_INVALID_ARG outside those ranges, NPFEM_ERR_UNSUPPORTED when a CTA's solve
  * vectors exceed shared memory.  npfem_batch_get_split_launch returns those seven values
  * plus the mode in shape[7] (host array of 8). */
 npfem_status npfem_batch_set_mode(npfem_batch* batch, int32_t mode);
+
+/* Split mode: cut the cells of type type_index into `groups` (1..4) contiguous groups,
+ * each with its own chain of kernels on its own stream.  The groups take turns on the
+ * FP64 solve (group g's solve of iteration i after group g-1's, group 0's of iteration
+ * i+1 after the last group's of iteration i), so one group's iteration kernel overlaps
+ * another group's solve.  Results do not depend on the grouping.
+ * NPFEM_ERR_INVALID_ARG for groups outside 1..4 or a type without cells in the batch. */
+npfem_status npfem_batch_set_groups(npfem_batch* batch, int32_t type_index, int32_t groups);
+npfem_status npfem_batch_get_groups(const npfem_batch* batch, int32_t type_index, int32_t* groups);
 npfem_status npfem_batch_set_split_launch(npfem_batch* batch, int32_t type_index, const int32_t* shape);
 npfem_status npfem_batch_get_split_launch(const npfem_batch* batch, int32_t type_index, int32_t* shape);
 

@@ -56,6 +56,7 @@ struct TypeLaunch {
   size_t cell_slot;
   int it_wpb, it_bps, sv_wpb, sv_bps, sv_smem, sv_percoord, sv_cells;
   int* active = nullptr;  // split mode: [2][ncells] lists of iterating cells (inside cell_scratch)
+  int groups = 1;         // split mode: cells split into this many groups with phase-offset chains
 };
 
 struct npfem_batch {
@@ -77,14 +78,19 @@ struct npfem_batch {
   std::vector<cudaStream_t> type_streams;
   std::vector<cudaEvent_t> type_events;
   cudaEvent_t fork_event = nullptr;
+  // split mode with several groups of one type: one event per group and iteration,
+  // recorded after the group's solve; the next group's solve waits on it
+  std::vector<cudaEvent_t> solve_events;  // [launches.size() * kMaxGroups][kSplitMaxIters]
   // optional per-launch kernel timing in split mode: a (start, end) event pair around
-  // every launch, per cell-type launch and launch slot (0: k_begin, 1 + 2i: k_solve of
-  // iteration i, 2 + 2i: k_iter of iteration i), re-recorded by every step
+  // every launch, per chain (type launch x group) and launch slot (0: k_begin, 1 + 2i:
+  // k_solve of iteration i, 2 + 2i: k_iter of iteration i), re-recorded by every step
   bool ktiming = false;
-  std::vector<cudaEvent_t> kev;      // [launches.size()][kTimingSlots][2]
-  std::vector<int> k_last_slots;     // slots recorded by the last step, per type launch
+  std::vector<cudaEvent_t> kev;      // [launches.size() * kMaxGroups][kTimingSlots][2]
+  std::vector<int> k_last_slots;     // slots recorded by the last step, per chain
+  std::vector<int> k_last_chains;    // cell type of each chain of the last split step
   ~npfem_batch() {
     for (cudaEvent_t e : kev) cudaEventDestroy(e);
+    for (cudaEvent_t e : solve_events) cudaEventDestroy(e);
     for (cudaStream_t s : type_streams) cudaStreamDestroy(s);
     for (cudaEvent_t e : type_events) cudaEventDestroy(e);
     if (fork_event) cudaEventDestroy(fork_event);
@@ -234,6 +240,8 @@ static cudaError_t set_solve_smem_attr(int bytes) {
     for (int pl = 1; pl <= 2 && e == cudaSuccess; ++pl) e = allow_dynamic_smem(solve_kernel<S>(c, pl), bytes);
   if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[0]>, bytes);
   if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[1]>, bytes);
+  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[2]>, bytes);
+  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[3]>, bytes);
   return e;
 }
 
@@ -254,8 +262,8 @@ static void default_split_shape(TypeLaunch& L, int n, npfem_precision prec) {
     L.sv_wpb = 2, L.sv_bps = 7, L.sv_smem = 1;
   } else if (n <= 1024) {  // 642-vertex RBC: CTAs of 2 warps per cell, 10 per SM
     L.sv_wpb = 2, L.sv_bps = 10, L.sv_smem = 2;
-  } else {                 // 2562-vertex RBC: CTAs of 4 warps per cell, 3 per SM
-    L.sv_wpb = 4, L.sv_bps = 3, L.sv_smem = 2;
+  } else {                 // 2562-vertex RBC: CTAs of 6 warps per cell, 3 per SM
+    L.sv_wpb = 6, L.sv_bps = 3, L.sv_smem = 2;
   }
   // iteration kernels: 32 warps per SM in the FP32 form (64 registers), 16 in FP64
   L.it_wpb = 2, L.it_bps = prec == NPFEM_FP64 ? 8 : 16;
@@ -288,22 +296,32 @@ static npfem_status ensure_cell_scratch(npfem_batch* b, TypeLaunch& L) {
   return NPFEM_OK;
 }
 
+// One group of a type's cells: list items [g0, g0 + gn) with its own counter block.
+struct GroupRange {
+  int g0, gn;
+  int* counter;
+};
+
 template <typename S>
-static npfem_status launch_split(npfem_batch* b, const npfem_cell_type* t, const TypeLaunch& L, StepParams P, int kind,
-                                 int it, int max_iters, S* x, S* v, const S* f, const DevTypeView<S>& view,
-                                 cudaStream_t st) {
-  P.scratch = L.cell_scratch;
+static npfem_status launch_split(npfem_batch* b, const npfem_cell_type* t, const TypeLaunch& L, const GroupRange& G,
+                                 StepParams P, int kind, int it, int max_iters, S* x, S* v, const S* f,
+                                 const DevTypeView<S>& view, cudaStream_t st) {
+  P.ncells_list = G.gn;
+  P.cell_list = L.cell_list + G.g0;
+  P.scratch = L.cell_scratch + (size_t)G.g0 * L.cell_slot;
   P.slot_bytes = L.cell_slot;
-  int* act_count = L.counter + kActiveCountOff;
+  int* act_count = G.counter + kActiveCountOff;
+  int* act0 = L.active + G.g0;                // list of even iterations (item indices of the group)
+  int* act1 = L.active + L.ncells + G.g0;     // list of odd iterations
   if (kind == 0) {
-    P.queue_counter = L.counter;
-    P.act_out = L.active;
+    P.queue_counter = G.counter;
+    P.act_out = act0;
     P.act_count_out = act_count;
-    int grid = std::max(1, std::min<int>(b->sms * L.it_bps, (L.ncells + L.it_wpb - 1) / L.it_wpb));
+    int grid = std::max(1, std::min<int>(b->sms * L.it_bps, (G.gn + L.it_wpb - 1) / L.it_wpb));
     npfem_k_begin<S><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, max_iters, x, v, f);
   } else if (kind == 1) {
-    P.queue_counter = L.counter + 1 + 2 * it;
-    P.act_in = L.active + (size_t)(it & 1) * L.ncells;
+    P.queue_counter = G.counter + 1 + 2 * it;
+    P.act_in = (it & 1) ? act1 : act0;
     P.act_count_in = act_count + it;
     P.z_in_smem = L.sv_smem == 1;
     P.solve_per_coord = L.sv_percoord;
@@ -311,23 +329,25 @@ static npfem_status launch_split(npfem_batch* b, const npfem_cell_type* t, const
     const HostType& H = t->host;
     if (L.sv_smem == 2) {  // CTA-cooperative: one cell per CTA of sv_wpb warps
       const size_t smem = split_solve_smem(H.n, L.sv_wpb, 0, 1, 2);
-      const int grid = std::max(1, std::min<int>(b->sms * L.sv_bps, L.ncells));
-      if (L.sv_wpb == kCtaWarps[0])
-        npfem_k_solve_cta<S, kCtaWarps[0]><<<grid, 32 * kCtaWarps[0], smem, st>>>(view, P);
-      else
-        npfem_k_solve_cta<S, kCtaWarps[1]><<<grid, 32 * kCtaWarps[1], smem, st>>>(view, P);
+      const int grid = std::max(1, std::min<int>(b->sms * L.sv_bps, G.gn));
+      switch (L.sv_wpb) {
+        case kCtaWarps[0]: npfem_k_solve_cta<S, kCtaWarps[0]><<<grid, 32 * kCtaWarps[0], smem, st>>>(view, P); break;
+        case kCtaWarps[1]: npfem_k_solve_cta<S, kCtaWarps[1]><<<grid, 32 * kCtaWarps[1], smem, st>>>(view, P); break;
+        case kCtaWarps[2]: npfem_k_solve_cta<S, kCtaWarps[2]><<<grid, 32 * kCtaWarps[2], smem, st>>>(view, P); break;
+        default: npfem_k_solve_cta<S, kCtaWarps[3]><<<grid, 32 * kCtaWarps[3], smem, st>>>(view, P); break;
+      }
     } else {
       size_t smem = L.sv_smem ? split_solve_smem(H.n, L.sv_wpb, L.sv_percoord, P.solve_cells) : 0;
       const int per_cta = L.sv_wpb * P.solve_cells;
-      int grid = std::max(1, std::min<int>(b->sms * L.sv_bps, (L.ncells + per_cta - 1) / per_cta));
+      int grid = std::max(1, std::min<int>(b->sms * L.sv_bps, (G.gn + per_cta - 1) / per_cta));
       const int place = !L.sv_smem ? kZWorkspace : (L.sv_percoord ? kZSharedPerCoord : kZShared);
       solve_kernel<S>(P.solve_cells, place)<<<grid, 32 * L.sv_wpb, smem, st>>>(view, P);
     }
   } else {
-    P.queue_counter = L.counter + 2 + 2 * it;
-    P.act_out = L.active + (size_t)((it + 1) & 1) * L.ncells;
+    P.queue_counter = G.counter + 2 + 2 * it;
+    P.act_out = (it & 1) ? act0 : act1;
     P.act_count_out = act_count + it + 1;
-    int grid = std::max(1, std::min<int>(b->sms * L.it_bps, (L.ncells + L.it_wpb - 1) / L.it_wpb));
+    int grid = std::max(1, std::min<int>(b->sms * L.it_bps, (G.gn + L.it_wpb - 1) / L.it_wpb));
     npfem_k_iter<S><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, x, v);
   }
   cudaError_t e = cudaGetLastError();
@@ -347,75 +367,145 @@ static cudaError_t record_timing_event(cudaEvent_t e, cudaStream_t s) {
                                              : cudaEventRecord(e, s);
 }
 
+// Split-mode step.  Each (type, group) is a chain of kernels -- k_begin, then per
+// iteration k_solve and k_iter -- on its own stream when there is more than one chain.
+// The groups of one type take turns on the FP64 solve: group g's solve of iteration i
+// waits for group g-1's, and group 0's solve of iteration i+1 for the last group's of
+// iteration i, so one group's iteration kernel runs beside another group's solve.
 static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_ext, const int32_t* iters,
                                const npfem_solver_opts* opts, int max_iters, double* residual_out,
                                int32_t* status_out, cudaStream_t st) {
-  for (TypeLaunch& L : b->launches) {
+  struct Chain {
+    size_t li;
+    int g;
+    GroupRange G;
+  };
+  std::vector<Chain> chains;
+  for (size_t li = 0; li < b->launches.size(); ++li) {
+    TypeLaunch& L = b->launches[li];
     npfem_status rc = ensure_cell_scratch(b, L);
     if (rc != NPFEM_OK) return rc;
-  }
-  const size_t nl = b->launches.size();
-  const bool fork = nl > 1;
-  if (fork && b->type_streams.size() < nl) {
-    if (!b->fork_event) NPFEM_CUDA_TRY(cudaEventCreateWithFlags(&b->fork_event, cudaEventDisableTiming));
-    while (b->type_streams.size() < nl) {
-      cudaStream_t s2;
-      cudaEvent_t e2;
-      NPFEM_CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
-      NPFEM_CUDA_TRY(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
-      b->type_streams.push_back(s2);
-      b->type_events.push_back(e2);
+    const int ng = std::max(1, std::min(L.groups, L.ncells));
+    for (int g = 0; g < ng; ++g) {
+      const int g0 = (int)((int64_t)L.ncells * g / ng), g1 = (int)((int64_t)L.ncells * (g + 1) / ng);
+      chains.push_back({li, g, {g0, g1 - g0, L.counter + (size_t)g * kSplitCounters}});
     }
   }
-  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kSplitCounters, st));
+  const size_t nc = chains.size();
+  const bool fork = nc > 1;
   if (fork) {
-    NPFEM_CUDA_TRY(cudaEventRecord(b->fork_event, st));
-    for (size_t li = 0; li < nl; ++li) NPFEM_CUDA_TRY(cudaStreamWaitEvent(b->type_streams[li], b->fork_event, 0));
-  }
-  for (size_t li = 0; li < nl; ++li) {
-    const TypeLaunch& L = b->launches[li];
-    const npfem_cell_type* t = b->types[L.type_index];
-    cudaStream_t ts = fork ? b->type_streams[li] : st;
-    StepParams P{};
-    P.ncells_list = L.ncells;
-    P.cell_list = L.cell_list;
-    P.offsets = b->d_offsets;
-    P.n_total = b->n_total;
-    P.iters = iters;
-    P.iters_default = opts->iters;
-    P.residual_out = residual_out;
-    P.status_out = status_out;
-    P.alpha_log = opts->alpha_log;
-    P.alpha_log_len = opts->alpha_log_len;
-    P.phase_cycles = b->d_phase;
-    int slot = 0;
-    for (int kind = 0, it = 0; kind == 0 || it < max_iters; ++slot) {
-      npfem_status rc;
-      cudaEvent_t* ke = b->ktiming ? &b->kev[(li * kTimingSlots + slot) * 2] : nullptr;
-      if (ke) NPFEM_CUDA_TRY(record_timing_event(ke[0], ts));
-      if (b->prec == NPFEM_FP64)
-        rc = launch_split<double>(b, t, L, P, kind, it, max_iters, static_cast<double*>(x), static_cast<double*>(v),
-                                  static_cast<const double*>(f_ext), t->v64, ts);
-      else
-        rc = launch_split<float>(b, t, L, P, kind, it, max_iters, static_cast<float*>(x), static_cast<float*>(v),
-                                 static_cast<const float*>(f_ext), t->v32, ts);
-      if (rc != NPFEM_OK) return rc;
-      if (ke) NPFEM_CUDA_TRY(record_timing_event(ke[1], ts));
-      if (kind == 0) {
-        kind = 1;
-      } else if (kind == 1) {
-        kind = 2;
+    // Stream priorities: the chains of the type with the most work per step (cells x
+    // vertices) run at the highest priority, so the others fill its gaps instead of
+    // delaying it.  Streams are (re)created outside stream capture only.
+    size_t heavy = 0;
+    double most = -1.0;
+    for (size_t li = 0; li < b->launches.size(); ++li) {
+      const double w = (double)b->launches[li].ncells * b->types[b->launches[li].type_index]->host.n;
+      if (w > most) most = w, heavy = li;
+    }
+    int least = 0, greatest = 0;
+    NPFEM_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    NPFEM_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (!b->fork_event) NPFEM_CUDA_TRY(cudaEventCreateWithFlags(&b->fork_event, cudaEventDisableTiming));
+    for (size_t c = 0; c < nc; ++c) {
+      const int want = chains[c].li == heavy ? greatest : least;
+      if (c < b->type_streams.size()) {
+        int have = 0;
+        NPFEM_CUDA_TRY(cudaStreamGetPriority(b->type_streams[c], &have));
+        if (have == want || cs != cudaStreamCaptureStatusNone) continue;
+        NPFEM_CUDA_TRY(cudaStreamSynchronize(b->type_streams[c]));
+        NPFEM_CUDA_TRY(cudaStreamDestroy(b->type_streams[c]));
+        NPFEM_CUDA_TRY(cudaStreamCreateWithPriority(&b->type_streams[c], cudaStreamNonBlocking, want));
       } else {
-        kind = 1;
-        ++it;
+        if (cs != cudaStreamCaptureStatusNone)
+          return fail(NPFEM_ERR_INVALID_ARG,
+                      "split step: first step of this batch configuration under stream capture; run it once uncaptured");
+        cudaStream_t s2;
+        cudaEvent_t e2;
+        NPFEM_CUDA_TRY(cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, want));
+        NPFEM_CUDA_TRY(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+        b->type_streams.push_back(s2);
+        b->type_events.push_back(e2);
       }
     }
-    if (b->ktiming) b->k_last_slots[li] = slot;
   }
+  bool any_groups = false;
+  for (const TypeLaunch& L : b->launches) any_groups = any_groups || L.groups > 1;
+  if (any_groups && b->solve_events.size() < nc * kSplitMaxIters) {
+    const size_t old = b->solve_events.size();
+    b->solve_events.resize(nc * kSplitMaxIters, nullptr);
+    for (size_t i = old; i < b->solve_events.size(); ++i)
+      NPFEM_CUDA_TRY(cudaEventCreateWithFlags(&b->solve_events[i], cudaEventDisableTiming));
+  }
+  if (b->ktiming && b->k_last_slots.size() < nc) {
+    return fail(NPFEM_ERR_INVALID_ARG, "split step: kernel timing was enabled for fewer chains; enable it again");
+  }
+  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kMaxGroups * kSplitCounters, st));
+  if (fork) {
+    NPFEM_CUDA_TRY(cudaEventRecord(b->fork_event, st));
+    for (size_t c = 0; c < nc; ++c) NPFEM_CUDA_TRY(cudaStreamWaitEvent(b->type_streams[c], b->fork_event, 0));
+  }
+  StepParams P{};
+  P.offsets = b->d_offsets;
+  P.n_total = b->n_total;
+  P.iters = iters;
+  P.iters_default = opts->iters;
+  P.residual_out = residual_out;
+  P.status_out = status_out;
+  P.alpha_log = opts->alpha_log;
+  P.alpha_log_len = opts->alpha_log_len;
+  P.phase_cycles = b->d_phase;
+  auto launch = [&](size_t c, int kind, int it, int slot) -> npfem_status {
+    const Chain& C = chains[c];
+    const TypeLaunch& L = b->launches[C.li];
+    const npfem_cell_type* t = b->types[L.type_index];
+    cudaStream_t cs = fork ? b->type_streams[c] : st;
+    cudaEvent_t* ke = b->ktiming ? &b->kev[(c * kTimingSlots + slot) * 2] : nullptr;
+    if (ke) NPFEM_CUDA_TRY(record_timing_event(ke[0], cs));
+    npfem_status rc;
+    if (b->prec == NPFEM_FP64)
+      rc = launch_split<double>(b, t, L, C.G, P, kind, it, max_iters, static_cast<double*>(x),
+                                static_cast<double*>(v), static_cast<const double*>(f_ext), t->v64, cs);
+    else
+      rc = launch_split<float>(b, t, L, C.G, P, kind, it, max_iters, static_cast<float*>(x), static_cast<float*>(v),
+                               static_cast<const float*>(f_ext), t->v32, cs);
+    if (rc != NPFEM_OK) return rc;
+    if (ke) NPFEM_CUDA_TRY(record_timing_event(ke[1], cs));
+    return NPFEM_OK;
+  };
+  for (size_t c = 0; c < nc; ++c) {
+    npfem_status rc = launch(c, 0, 0, 0);
+    if (rc != NPFEM_OK) return rc;
+  }
+  for (int it = 0; it < max_iters; ++it) {
+    for (size_t c = 0; c < nc; ++c) {
+      const Chain& C = chains[c];
+      const TypeLaunch& L = b->launches[C.li];
+      cudaStream_t cs = fork ? b->type_streams[c] : st;
+      const int ng = std::max(1, std::min(L.groups, L.ncells));
+      if (ng > 1) {  // the solve ring of this type's groups
+        if (C.g > 0) {
+          NPFEM_CUDA_TRY(cudaStreamWaitEvent(cs, b->solve_events[(c - 1) * kSplitMaxIters + it], 0));
+        } else if (it > 0) {
+          NPFEM_CUDA_TRY(cudaStreamWaitEvent(cs, b->solve_events[(c + ng - 1) * kSplitMaxIters + it - 1], 0));
+        }
+      }
+      npfem_status rc = launch(c, 1, it, 1 + 2 * it);
+      if (rc != NPFEM_OK) return rc;
+      if (ng > 1) NPFEM_CUDA_TRY(cudaEventRecord(b->solve_events[c * kSplitMaxIters + it], cs));
+      rc = launch(c, 2, it, 2 + 2 * it);
+      if (rc != NPFEM_OK) return rc;
+    }
+  }
+  if (b->ktiming)
+    for (size_t c = 0; c < nc; ++c) b->k_last_slots[c] = 1 + 2 * max_iters;
+  b->k_last_chains.assign(nc, 0);
+  for (size_t c = 0; c < nc; ++c) b->k_last_chains[c] = b->launches[chains[c].li].type_index;
   if (fork)
-    for (size_t li = 0; li < nl; ++li) {
-      NPFEM_CUDA_TRY(cudaEventRecord(b->type_events[li], b->type_streams[li]));
-      NPFEM_CUDA_TRY(cudaStreamWaitEvent(st, b->type_events[li], 0));
+    for (size_t c = 0; c < nc; ++c) {
+      NPFEM_CUDA_TRY(cudaEventRecord(b->type_events[c], b->type_streams[c]));
+      NPFEM_CUDA_TRY(cudaStreamWaitEvent(st, b->type_events[c], 0));
     }
   return NPFEM_OK;
 }
@@ -568,7 +658,7 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
   cudaError_t e = b->mem.upload(b->offsets, &b->d_offsets);
   if (e != cudaSuccess) return cleanup(NPFEM_ERR_CUDA, std::string("batch_create: ") + cudaGetErrorString(e));
   void* cnt = nullptr;
-  e = b->mem.alloc(sizeof(int) * ntypes * kSplitCounters, &cnt);
+  e = b->mem.alloc(sizeof(int) * ntypes * kMaxGroups * kSplitCounters, &cnt);
   if (e != cudaSuccess) return cleanup(NPFEM_ERR_OOM, std::string("batch_create: ") + cudaGetErrorString(e));
   b->d_counters = static_cast<int*>(cnt);
   void* ph = nullptr;
@@ -607,7 +697,7 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
     if ((e = b->mem.upload(list, &dl)) != cudaSuccess)
       return cleanup(NPFEM_ERR_OOM, std::string("batch_create: ") + cudaGetErrorString(e));
     L.cell_list = dl;
-    L.counter = b->d_counters + ti * kSplitCounters;
+    L.counter = b->d_counters + (size_t)ti * kMaxGroups * kSplitCounters;  // group 0's block
     // default shape: 4 warps per CTA and 3 CTAs per SM, solve vectors in shared memory
     // when four of them fit in 72 KB (n <= 767), else in the workspace
     const size_t zbytes = sizeof(double) * 3 * ((size_t)H.n + 1);
@@ -656,7 +746,7 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
     const int max_iters = iters ? opts->max_iters : opts->iters;
     if (max_iters <= kSplitMaxIters) return step_split(b, x, v, f_ext, iters, opts, max_iters, residual_out, status_out, st);
   }
-  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kSplitCounters, st));
+  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kMaxGroups * kSplitCounters, st));
   for (const TypeLaunch& L : b->launches) {
     const npfem_cell_type* t = b->types[L.type_index];
     StepParams P;
@@ -714,7 +804,7 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     L.adj_scratch = static_cast<char*>(p);
     L.adj_slot = bytes;
   }
-  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kSplitCounters, st));
+  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kMaxGroups * kSplitCounters, st));
   for (size_t li = 0; li < b->launches.size(); ++li) {
     const TypeLaunch& L = b->launches[li];
     const npfem_cell_type* t = b->types[L.type_index];
@@ -791,14 +881,17 @@ npfem_status npfem_batch_set_split_launch(npfem_batch* b, int32_t type_index, co
   for (TypeLaunch& L : b->launches)
     if (L.type_index == type_index) {
       const HostType& H = b->types[L.type_index]->host;
-      if (shape[0] < 1 || shape[0] > 4 || shape[1] < 1 || shape[1] > 16 || shape[2] < 1 || shape[2] > 4 ||
-          shape[3] < 1 || shape[3] > 16 || shape[6] < 1 || shape[6] > 4 || shape[4] < 0 || shape[4] > 2)
+      const bool cta_width = shape[2] == kCtaWarps[0] || shape[2] == kCtaWarps[1] || shape[2] == kCtaWarps[2] ||
+                             shape[2] == kCtaWarps[3];
+      if (shape[0] < 1 || shape[0] > 4 || shape[1] < 1 || shape[1] > 16 || shape[2] < 1 ||
+          shape[2] > (shape[4] == 2 ? 8 : 4) || shape[3] < 1 || shape[3] > 16 || shape[6] < 1 || shape[6] > 4 ||
+          shape[4] < 0 || shape[4] > 2)
         return fail(NPFEM_ERR_INVALID_ARG,
-                    "batch_set_split_launch: warps/CTA in 1..4, CTAs/SM in 1..16, cells per solve warp in 1..4, "
-                    "placement in 0..2");
-      if (shape[4] == 2 && ((shape[2] != kCtaWarps[0] && shape[2] != kCtaWarps[1]) || shape[5] != 0 || shape[6] != 1))
+                    "batch_set_split_launch: warps/CTA in 1..4 (solve placement 2: 2, 4, 6 or 8), CTAs/SM in 1..16, "
+                    "cells per solve warp in 1..4, placement in 0..2");
+      if (shape[4] == 2 && (!cta_width || shape[5] != 0 || shape[6] != 1))
         return fail(NPFEM_ERR_INVALID_ARG,
-                    "batch_set_split_launch: a CTA-cooperative solve takes 2 or 4 warps per CTA, one cell, "
+                    "batch_set_split_launch: a CTA-cooperative solve takes 2, 4, 6 or 8 warps per CTA, one cell, "
                     "interleaved coordinates");
       size_t smem = shape[4] ? split_solve_smem(H.n, shape[2], shape[5], shape[6], shape[4]) : 0;
       if (shape[4] == 2) smem += 16;  // the CTA kernel's static shared memory (rounded up)
@@ -845,10 +938,12 @@ npfem_status npfem_batch_phase_cycles(npfem_batch* b, uint64_t* cycles, int32_t 
 
 npfem_status npfem_batch_set_kernel_timing(npfem_batch* b, int32_t enable) {
   if (!b) return fail(NPFEM_ERR_INVALID_ARG, "batch_set_kernel_timing: null batch");
-  if (enable && b->kev.empty() && !b->launches.empty()) {
-    b->kev.resize(b->launches.size() * kTimingSlots * 2, nullptr);
-    for (cudaEvent_t& e : b->kev) NPFEM_CUDA_TRY(cudaEventCreate(&e));
-    b->k_last_slots.assign(b->launches.size(), 0);
+  const size_t chains = b->launches.size() * kMaxGroups;
+  if (enable && b->kev.size() < chains * kTimingSlots * 2) {
+    const size_t old = b->kev.size();
+    b->kev.resize(chains * kTimingSlots * 2, nullptr);
+    for (size_t i = old; i < b->kev.size(); ++i) NPFEM_CUDA_TRY(cudaEventCreate(&b->kev[i]));
+    b->k_last_slots.assign(chains, 0);
   }
   b->ktiming = enable != 0 && !b->launches.empty();
   return NPFEM_OK;
@@ -858,10 +953,13 @@ npfem_status npfem_batch_kernel_times(npfem_batch* b, int32_t type_index, double
   if (!b || !ms || !launches) return fail(NPFEM_ERR_INVALID_ARG, "batch_kernel_times: null argument");
   for (int k = 0; k < 3; ++k) ms[k] = 0.0, launches[k] = 0;
   if (b->kev.empty()) return fail(NPFEM_ERR_INVALID_ARG, "batch_kernel_times: kernel timing was never enabled");
-  for (size_t li = 0; li < b->launches.size(); ++li) {
-    if (b->launches[li].type_index != type_index) continue;
-    for (int slot = 0; slot < b->k_last_slots[li]; ++slot) {
-      cudaEvent_t* ke = &b->kev[(li * kTimingSlots + slot) * 2];
+  bool found = false;
+  for (const TypeLaunch& L : b->launches) found = found || L.type_index == type_index;
+  if (!found) return fail(NPFEM_ERR_INVALID_ARG, "batch_kernel_times: no cells of that type in the batch");
+  for (size_t c = 0; c < b->k_last_chains.size() && c < b->k_last_slots.size(); ++c) {
+    if (b->k_last_chains[c] != type_index) continue;
+    for (int slot = 0; slot < b->k_last_slots[c]; ++slot) {
+      cudaEvent_t* ke = &b->kev[(c * kTimingSlots + slot) * 2];
       NPFEM_CUDA_TRY(cudaEventSynchronize(ke[1]));
       float t = 0.f;
       NPFEM_CUDA_TRY(cudaEventElapsedTime(&t, ke[0], ke[1]));
@@ -869,9 +967,29 @@ npfem_status npfem_batch_kernel_times(npfem_batch* b, int32_t type_index, double
       ms[kind] += t;
       launches[kind] += 1;
     }
-    return NPFEM_OK;
   }
-  return fail(NPFEM_ERR_INVALID_ARG, "batch_kernel_times: no cells of that type in the batch");
+  return NPFEM_OK;
+}
+
+npfem_status npfem_batch_set_groups(npfem_batch* b, int32_t type_index, int32_t groups) {
+  if (!b || groups < 1 || groups > kMaxGroups)
+    return fail(NPFEM_ERR_INVALID_ARG, "batch_set_groups: groups in 1..4");
+  for (TypeLaunch& L : b->launches)
+    if (L.type_index == type_index) {
+      L.groups = groups;
+      return NPFEM_OK;
+    }
+  return fail(NPFEM_ERR_INVALID_ARG, "batch_set_groups: no cells of that type in the batch");
+}
+
+npfem_status npfem_batch_get_groups(const npfem_batch* b, int32_t type_index, int32_t* groups) {
+  if (!b || !groups) return fail(NPFEM_ERR_INVALID_ARG, "batch_get_groups: null argument");
+  for (const TypeLaunch& L : b->launches)
+    if (L.type_index == type_index) {
+      *groups = L.groups;
+      return NPFEM_OK;
+    }
+  return fail(NPFEM_ERR_INVALID_ARG, "batch_get_groups: no cells of that type in the batch");
 }
 
 npfem_status npfem_step_host(npfem_batch* b, void* x, void* v, const void* f_ext, const int32_t* iters,

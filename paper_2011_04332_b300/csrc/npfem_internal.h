@@ -14,8 +14,8 @@ constexpr double kCurvatureEps = 1e-12;  // keep pair only if s.y > eps |s||y|
 constexpr double kDegenerateDet = 1e-30; // det(F^T F) below this: triangle skipped
 constexpr double kDegenerateNorm = 1e-30;
 constexpr int kChunk = 32;               // entries per triangular-solve chunk (one per lane)
-constexpr int kCtaPacks = 2;             // level packings for CTA-cooperative sweeps
-constexpr int kCtaWarps[kCtaPacks] = {2, 4};
+constexpr int kCtaPacks = 4;             // level packings for CTA-cooperative sweeps
+constexpr int kCtaWarps[kCtaPacks] = {2, 4, 6, 8};
 
 // Host-side result of the per-type setup (all FP64; the device upload makes FP32
 // copies of the element constants for the FP32-form kernels).

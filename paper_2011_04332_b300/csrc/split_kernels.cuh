@@ -37,6 +37,8 @@ struct IterOccupancy<float> {
 // that still iterate at iteration i (appended by k_begin for i = 0, by k_iter(i - 1)).
 constexpr int kActiveCountOff = 2 + 2 * kSplitMaxIters;
 constexpr int kSplitCounters = kActiveCountOff + kSplitMaxIters + 1;
+// A type's cells can be split into up to kMaxGroups groups, each with its own counters.
+constexpr int kMaxGroups = 4;
 constexpr size_t kStateBytes = 256;
 
 template <typename S>
@@ -318,10 +320,16 @@ __device__ __forceinline__ void cta_sweep(int nlev, const int32_t* __restrict__ 
 // for cells whose FP64 solve vector ([n+1][3], 24(n+1) bytes) is too large to keep
 // one per warp in shared memory.  The CTA's warps share the vector and sweep the
 // W-warp level packing of the factor together.
+// Index of the level packing for a CTA of W warps.
+template <int W>
+struct CtaPack {
+  static constexpr int value = W == kCtaWarps[0] ? 0 : W == kCtaWarps[1] ? 1 : W == kCtaWarps[2] ? 2 : 3;
+  static_assert(W == kCtaWarps[value], "no level packing for this CTA width");
+};
+
 template <typename S, int W>
-__global__ void __launch_bounds__(128) npfem_k_solve_cta(DevTypeView<S> ty, StepParams P) {
-  static_assert(W == kCtaWarps[0] || W == kCtaWarps[1], "no level packing for this CTA width");
-  constexpr int pk = W == kCtaWarps[0] ? 0 : 1;
+__global__ void __launch_bounds__(32 * W) npfem_k_solve_cta(DevTypeView<S> ty, StepParams P) {
+  constexpr int pk = CtaPack<W>::value;
   extern __shared__ double smem_z[];
   __shared__ int s_item;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;

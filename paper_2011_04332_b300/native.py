@@ -79,6 +79,8 @@ def load_library() -> C.CDLL:
         "npfem_step_adjoint": [vp, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp, vp, vp, vp, vp, vp],
         "npfem_batch_phase_cycles": [vp, C.POINTER(C.c_uint64), C.c_int32],
         "npfem_batch_set_kernel_timing": [vp, C.c_int32],
+        "npfem_batch_set_groups": [vp, C.c_int32, C.c_int32],
+        "npfem_batch_get_groups": [vp, C.c_int32, C.POINTER(C.c_int32)],
         "npfem_batch_kernel_times": [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int32)],
         "npfem_batch_set_mode": [vp, C.c_int32],
         "npfem_batch_set_split_launch": [vp, C.c_int32, C.POINTER(C.c_int32)],
@@ -239,6 +241,15 @@ class Batch:
         return {k: int(out[i]) for i, k in enumerate(self.PHASES)}
 
     KERNELS = ("k_begin", "k_solve", "k_iter")
+
+    def set_groups(self, type_index: int, groups: int) -> None:
+        """npfem_batch_set_groups: split mode, cells of the type in `groups` phase-offset chains."""
+        _check(_lib.npfem_batch_set_groups(self.handle, int(type_index), int(groups)))
+
+    def get_groups(self, type_index: int) -> int:
+        out = C.c_int32()
+        _check(_lib.npfem_batch_get_groups(self.handle, int(type_index), C.byref(out)))
+        return int(out.value)
 
     def set_kernel_timing(self, enable: bool = True) -> None:
         """npfem_batch_set_kernel_timing: CUDA events around every split-mode launch."""

@@ -433,7 +433,7 @@ def test_multi_cell_solve_is_identical(prec, cells):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("warps", [2, 4])
+@pytest.mark.parametrize("warps", [2, 4, 6, 8])
 def test_cta_cooperative_solve(prec, warps):
     """Placement 2: the 2 or 4 warps of a CTA sweep one cell's shared solve vector
     through the level packing of the factor, for every type of a mixed batch (162, 642
@@ -461,6 +461,48 @@ def test_cta_cooperative_shape_validation():
     nat = _native()
     b = I.heterogeneous_batch(n_rbc3=2, n_rbc4=1, n_plt=1, seed=1008)
     r = Runner(b, nat.FP64)
-    for bad in [(2, 4, 3, 2, 2, 0, 1), (2, 4, 2, 2, 2, 1, 1), (2, 4, 4, 2, 2, 0, 2), (2, 4, 2, 2, 3, 0, 1)]:
+    for bad in [(2, 4, 3, 2, 2, 0, 1), (2, 4, 2, 2, 2, 1, 1), (2, 4, 4, 2, 2, 0, 2), (2, 4, 2, 2, 3, 0, 1), (2, 4, 5, 2, 2, 0, 1), (2, 4, 6, 2, 1, 0, 1)]:
         with pytest.raises(nat.NpfemError):
             r.batch.set_split_launch(0, bad)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_groups_leave_results_unchanged(prec):
+    """Cells of a type split into 2..4 phase-offset chains (their solves take turns, their
+    iteration kernels overlap the other groups' solves) give the one-group results bit
+    for bit, directly and replayed from a captured CUDA graph; groups outside 1..4 are
+    rejected."""
+    nat = _native()
+    b = I.heterogeneous_batch(n_rbc3=9, n_rbc4=3, n_plt=7, seed=1009)
+    p = nat.FP64 if prec == "fp64" else nat.FP32FORM
+    r = Runner(b, p)
+    ref = r.step(b.x, b.v, b.f, iters=b.iters)
+    for groups in (2, 3, 4):
+        for t in range(len(b.types)):
+            r.batch.set_groups(t, groups)
+            assert r.batch.get_groups(t) == groups
+        out = r.step(b.x, b.v, b.f, iters=b.iters)
+        for a, c in zip(ref, out):
+            assert np.array_equal(a, c)
+    dev = torch.device("cuda:0")
+    dt_ = torch.float64 if prec == "fp64" else torch.float32
+    T = lambda a: torch.tensor(a, dtype=dt_, device=dev)
+    it = torch.tensor(b.iters, device=dev)
+    xg, vg, f = T(b.x), T(b.v), T(b.f)
+    r.batch.step(xg, vg, f, iters=it)        # warm-up (reads the iteration bound once)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            r.batch.step(xg, vg, f, iters=it)
+    torch.cuda.current_stream().wait_stream(s)
+    xg.copy_(T(b.x))
+    vg.copy_(T(b.v))
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(xg.double().cpu().numpy(), ref[0]) and np.array_equal(vg.double().cpu().numpy(), ref[1])
+    for bad in (0, 5):
+        with pytest.raises(nat.NpfemError):
+            r.batch.set_groups(0, bad)
