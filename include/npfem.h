@@ -205,10 +205,10 @@ npfem_status npfem_batch_get_launch(const npfem_batch* batch, int32_t type_index
 npfem_status npfem_batch_set_mode(npfem_batch* batch, int32_t mode);
 
 /* Split mode: cut the cells of type type_index into `groups` (1..4) contiguous groups,
- * each with its own chain of kernels on its own stream.  The groups take turns on the
- * FP64 solve (group g's solve of iteration i after group g-1's, group 0's of iteration
- * i+1 after the last group's of iteration i), so one group's iteration kernel overlaps
- * another group's solve.  Results do not depend on the grouping.
+ * each with its own chain of kernels on its own stream, running concurrently: the
+ * chains fill each other's wave tails and one group's FP32 iteration kernel overlaps
+ * another group's FP64 solve.  Default: 4 groups for types with at least 4096 cells in
+ * the batch, 2 from 2048, else 1.  Results do not depend on the grouping.
  * NPFEM_ERR_INVALID_ARG for groups outside 1..4 or a type without cells in the batch. */
 npfem_status npfem_batch_set_groups(npfem_batch* batch, int32_t type_index, int32_t groups);
 npfem_status npfem_batch_get_groups(const npfem_batch* batch, int32_t type_index, int32_t* groups);
@@ -233,6 +233,11 @@ npfem_status npfem_batch_phase_cycles(npfem_batch* batch, uint64_t* cycles, int3
  * NPFEM_ERR_CUDA when an event cannot be read. */
 npfem_status npfem_batch_set_kernel_timing(npfem_batch* batch, int32_t enable);
 npfem_status npfem_batch_kernel_times(npfem_batch* batch, int32_t type_index, double* ms, int32_t* launches);
+/* The same launches as time spans: for each of {k_begin, k_solve, k_iter}, the length in
+ * ms of the union of the launch intervals of the last timed step (concurrent chains of
+ * the type -- or, for type_index = -1, of all types -- overlap, so the union is the time
+ * during which at least one such kernel was running).  span_ms: host array of 3. */
+npfem_status npfem_batch_kernel_spans(npfem_batch* batch, int32_t type_index, double* span_ms);
 
 /* Same step with HOST arrays (pageable or pinned): copies x, v, f_ext (and iters,
  * when given) to batch-owned device buffers, runs npfem_step, and copies x, v,

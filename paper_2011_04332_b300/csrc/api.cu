@@ -57,6 +57,7 @@ struct TypeLaunch {
   int it_wpb, it_bps, sv_wpb, sv_bps, sv_smem, sv_percoord, sv_cells;
   int* active = nullptr;  // split mode: [2][ncells] lists of iterating cells (inside cell_scratch)
   int groups = 1;         // split mode: cells split into this many groups with phase-offset chains
+  std::vector<int32_t> host_list;  // the type's cells (batch indices, increasing)
 };
 
 struct npfem_batch {
@@ -78,9 +79,6 @@ struct npfem_batch {
   std::vector<cudaStream_t> type_streams;
   std::vector<cudaEvent_t> type_events;
   cudaEvent_t fork_event = nullptr;
-  // split mode with several groups of one type: one event per group and iteration,
-  // recorded after the group's solve; the next group's solve waits on it
-  std::vector<cudaEvent_t> solve_events;  // [launches.size() * kMaxGroups][kSplitMaxIters]
   // optional per-launch kernel timing in split mode: a (start, end) event pair around
   // every launch, per chain (type launch x group) and launch slot (0: k_begin, 1 + 2i:
   // k_solve of iteration i, 2 + 2i: k_iter of iteration i), re-recorded by every step
@@ -88,9 +86,13 @@ struct npfem_batch {
   std::vector<cudaEvent_t> kev;      // [launches.size() * kMaxGroups][kTimingSlots][2]
   std::vector<int> k_last_slots;     // slots recorded by the last step, per chain
   std::vector<int> k_last_chains;    // cell type of each chain of the last split step
+  cudaEvent_t k_ref = nullptr;       // recorded on the caller's stream at the start of a timed step
   ~npfem_batch() {
     for (cudaEvent_t e : kev) cudaEventDestroy(e);
-    for (cudaEvent_t e : solve_events) cudaEventDestroy(e);
+    if (k_ref) cudaEventDestroy(k_ref);
+    for (cudaEvent_t e : pipe_events) cudaEventDestroy(e);
+    if (h2d_stream) cudaStreamDestroy(h2d_stream);
+    if (d2h_stream) cudaStreamDestroy(d2h_stream);
     for (cudaStream_t s : type_streams) cudaStreamDestroy(s);
     for (cudaEvent_t e : type_events) cudaEventDestroy(e);
     if (fork_event) cudaEventDestroy(fork_event);
@@ -100,6 +102,10 @@ struct npfem_batch {
       if (L.cell_scratch) cudaFree(L.cell_scratch);
     }
   }
+  // pipelined host-buffer steps: copy streams and per-chunk events
+  cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
+  std::vector<cudaEvent_t> pipe_events;  // [0]: start, [1..kMaxGroups]: inputs copied,
+                                         // then kMaxGroups x launches: chunk done per type, last: outputs copied
   // host-step staging (allocated on first npfem_step_host)
   void* d_x = nullptr;
   void* d_v = nullptr;
@@ -267,6 +273,8 @@ static void default_split_shape(TypeLaunch& L, int n, npfem_precision prec) {
   }
   // iteration kernels: 32 warps per SM in the FP32 form (64 registers), 16 in FP64
   L.it_wpb = 2, L.it_bps = prec == NPFEM_FP64 ? 8 : 16;
+  // large types run as several concurrent chains that fill each other's wave tails
+  L.groups = L.ncells >= 4096 ? 4 : (L.ncells >= 2048 ? 2 : 1);
   // fewer CTAs per SM where the SM cannot hold that many shared vectors; workspace
   // vectors where it cannot hold one
   const size_t cta = split_solve_smem(n, L.sv_wpb, L.sv_percoord, L.sv_cells, L.sv_smem) + 1024;
@@ -367,14 +375,22 @@ static cudaError_t record_timing_event(cudaEvent_t e, cudaStream_t s) {
                                              : cudaEventRecord(e, s);
 }
 
+// Chunks of a pipelined step: cells [bounds[g], bounds[g+1]) form chunk g; the chains
+// of chunk g wait for in[g] and record done[g * ntypes_launched + type launch].
+struct PipelinePlan {
+  int K;
+  const int* bounds;
+  cudaEvent_t* in;
+  cudaEvent_t* done;
+};
+
 // Split-mode step.  Each (type, group) is a chain of kernels -- k_begin, then per
-// iteration k_solve and k_iter -- on its own stream when there is more than one chain.
-// The groups of one type take turns on the FP64 solve: group g's solve of iteration i
-// waits for group g-1's, and group 0's solve of iteration i+1 for the last group's of
-// iteration i, so one group's iteration kernel runs beside another group's solve.
+// iteration k_solve and k_iter -- on its own stream when there is more than one chain;
+// the chains run concurrently, so they fill each other's wave tails and one chain's
+// FP32 iteration kernel overlaps another's FP64 solve.
 static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_ext, const int32_t* iters,
                                const npfem_solver_opts* opts, int max_iters, double* residual_out,
-                               int32_t* status_out, cudaStream_t st) {
+                               int32_t* status_out, cudaStream_t st, const PipelinePlan* pipe = nullptr) {
   struct Chain {
     size_t li;
     int g;
@@ -385,6 +401,15 @@ static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_e
     TypeLaunch& L = b->launches[li];
     npfem_status rc = ensure_cell_scratch(b, L);
     if (rc != NPFEM_OK) return rc;
+    if (pipe) {  // chunk g: the type's cells with batch index in [bounds[g], bounds[g+1])
+      for (int g = 0; g < pipe->K; ++g) {
+        const auto lo = std::lower_bound(L.host_list.begin(), L.host_list.end(), pipe->bounds[g]);
+        const auto hi = std::lower_bound(L.host_list.begin(), L.host_list.end(), pipe->bounds[g + 1]);
+        const int g0 = (int)(lo - L.host_list.begin()), g1 = (int)(hi - L.host_list.begin());
+        chains.push_back({li, g, {g0, g1 - g0, L.counter + (size_t)g * kSplitCounters}});
+      }
+      continue;
+    }
     const int ng = std::max(1, std::min(L.groups, L.ncells));
     for (int g = 0; g < ng; ++g) {
       const int g0 = (int)((int64_t)L.ncells * g / ng), g1 = (int)((int64_t)L.ncells * (g + 1) / ng);
@@ -430,17 +455,10 @@ static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_e
       }
     }
   }
-  bool any_groups = false;
-  for (const TypeLaunch& L : b->launches) any_groups = any_groups || L.groups > 1;
-  if (any_groups && b->solve_events.size() < nc * kSplitMaxIters) {
-    const size_t old = b->solve_events.size();
-    b->solve_events.resize(nc * kSplitMaxIters, nullptr);
-    for (size_t i = old; i < b->solve_events.size(); ++i)
-      NPFEM_CUDA_TRY(cudaEventCreateWithFlags(&b->solve_events[i], cudaEventDisableTiming));
-  }
   if (b->ktiming && b->k_last_slots.size() < nc) {
     return fail(NPFEM_ERR_INVALID_ARG, "split step: kernel timing was enabled for fewer chains; enable it again");
   }
+  if (b->ktiming) NPFEM_CUDA_TRY(record_timing_event(b->k_ref, st));
   NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kMaxGroups * kSplitCounters, st));
   if (fork) {
     NPFEM_CUDA_TRY(cudaEventRecord(b->fork_event, st));
@@ -475,31 +493,28 @@ static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_e
     return NPFEM_OK;
   };
   for (size_t c = 0; c < nc; ++c) {
+    cudaStream_t cs = fork ? b->type_streams[c] : st;
+    if (pipe) NPFEM_CUDA_TRY(cudaStreamWaitEvent(cs, pipe->in[chains[c].g], 0));
+    if (chains[c].G.gn == 0) continue;
     npfem_status rc = launch(c, 0, 0, 0);
     if (rc != NPFEM_OK) return rc;
   }
   for (int it = 0; it < max_iters; ++it) {
     for (size_t c = 0; c < nc; ++c) {
-      const Chain& C = chains[c];
-      const TypeLaunch& L = b->launches[C.li];
-      cudaStream_t cs = fork ? b->type_streams[c] : st;
-      const int ng = std::max(1, std::min(L.groups, L.ncells));
-      if (ng > 1) {  // the solve ring of this type's groups
-        if (C.g > 0) {
-          NPFEM_CUDA_TRY(cudaStreamWaitEvent(cs, b->solve_events[(c - 1) * kSplitMaxIters + it], 0));
-        } else if (it > 0) {
-          NPFEM_CUDA_TRY(cudaStreamWaitEvent(cs, b->solve_events[(c + ng - 1) * kSplitMaxIters + it - 1], 0));
-        }
-      }
+      if (chains[c].G.gn == 0) continue;
       npfem_status rc = launch(c, 1, it, 1 + 2 * it);
       if (rc != NPFEM_OK) return rc;
-      if (ng > 1) NPFEM_CUDA_TRY(cudaEventRecord(b->solve_events[c * kSplitMaxIters + it], cs));
       rc = launch(c, 2, it, 2 + 2 * it);
       if (rc != NPFEM_OK) return rc;
     }
   }
+  if (pipe)
+    for (size_t c = 0; c < nc; ++c) {
+      cudaStream_t cs = fork ? b->type_streams[c] : st;
+      NPFEM_CUDA_TRY(cudaEventRecord(pipe->done[chains[c].g * b->launches.size() + chains[c].li], cs));
+    }
   if (b->ktiming)
-    for (size_t c = 0; c < nc; ++c) b->k_last_slots[c] = 1 + 2 * max_iters;
+    for (size_t c = 0; c < nc; ++c) b->k_last_slots[c] = chains[c].G.gn ? 1 + 2 * max_iters : 0;
   b->k_last_chains.assign(nc, 0);
   for (size_t c = 0; c < nc; ++c) b->k_last_chains[c] = b->launches[chains[c].li].type_index;
   if (fork)
@@ -697,6 +712,7 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
     if ((e = b->mem.upload(list, &dl)) != cudaSuccess)
       return cleanup(NPFEM_ERR_OOM, std::string("batch_create: ") + cudaGetErrorString(e));
     L.cell_list = dl;
+    L.host_list = list;
     L.counter = b->d_counters + (size_t)ti * kMaxGroups * kSplitCounters;  // group 0's block
     // default shape: 4 warps per CTA and 3 CTAs per SM, solve vectors in shared memory
     // when four of them fit in 72 KB (n <= 767), else in the workspace
@@ -749,7 +765,7 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
   NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kMaxGroups * kSplitCounters, st));
   for (const TypeLaunch& L : b->launches) {
     const npfem_cell_type* t = b->types[L.type_index];
-    StepParams P;
+    StepParams P{};
     P.ncells_list = L.ncells;
     P.cell_list = L.cell_list;
     P.offsets = b->d_offsets;
@@ -945,6 +961,7 @@ npfem_status npfem_batch_set_kernel_timing(npfem_batch* b, int32_t enable) {
     for (size_t i = old; i < b->kev.size(); ++i) NPFEM_CUDA_TRY(cudaEventCreate(&b->kev[i]));
     b->k_last_slots.assign(chains, 0);
   }
+  if (enable && !b->k_ref) NPFEM_CUDA_TRY(cudaEventCreate(&b->k_ref));
   b->ktiming = enable != 0 && !b->launches.empty();
   return NPFEM_OK;
 }
@@ -967,6 +984,41 @@ npfem_status npfem_batch_kernel_times(npfem_batch* b, int32_t type_index, double
       ms[kind] += t;
       launches[kind] += 1;
     }
+  }
+  return NPFEM_OK;
+}
+
+npfem_status npfem_batch_kernel_spans(npfem_batch* b, int32_t type_index, double* span_ms) {
+  if (!b || !span_ms) return fail(NPFEM_ERR_INVALID_ARG, "batch_kernel_spans: null argument");
+  for (int k = 0; k < 3; ++k) span_ms[k] = 0.0;
+  if (b->kev.empty() || !b->k_ref)
+    return fail(NPFEM_ERR_INVALID_ARG, "batch_kernel_spans: kernel timing was never enabled");
+  // launch intervals relative to the step's reference event, per kernel kind
+  std::vector<std::pair<double, double>> iv[3];
+  for (size_t c = 0; c < b->k_last_chains.size() && c < b->k_last_slots.size(); ++c) {
+    if (type_index >= 0 && b->k_last_chains[c] != type_index) continue;
+    for (int slot = 0; slot < b->k_last_slots[c]; ++slot) {
+      cudaEvent_t* ke = &b->kev[(c * kTimingSlots + slot) * 2];
+      NPFEM_CUDA_TRY(cudaEventSynchronize(ke[1]));
+      float t0 = 0.f, t1 = 0.f;
+      NPFEM_CUDA_TRY(cudaEventElapsedTime(&t0, b->k_ref, ke[0]));
+      NPFEM_CUDA_TRY(cudaEventElapsedTime(&t1, b->k_ref, ke[1]));
+      iv[slot == 0 ? 0 : 2 - (slot & 1)].push_back({t0, t1});
+    }
+  }
+  for (int k = 0; k < 3; ++k) {  // length of the union of the intervals
+    std::sort(iv[k].begin(), iv[k].end());
+    double end = -1e300, total = 0.0;
+    for (const auto& q : iv[k]) {
+      if (q.first > end) {
+        total += q.second - q.first;
+        end = q.second;
+      } else if (q.second > end) {
+        total += q.second - end;
+        end = q.second;
+      }
+    }
+    span_ms[k] = total;
   }
   return NPFEM_OK;
 }
@@ -1015,19 +1067,96 @@ npfem_status npfem_step_host(npfem_batch* b, void* x, void* v, const void* f_ext
     b->d_status = static_cast<int32_t*>(p);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_x, x, bytes, cudaMemcpyHostToDevice, st));
-  NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_v, v, bytes, cudaMemcpyHostToDevice, st));
-  NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_f, f_ext, bytes, cudaMemcpyHostToDevice, st));
-  if (iters)
-    NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_iters, iters, sizeof(int32_t) * b->ncells, cudaMemcpyHostToDevice, st));
   npfem_solver_opts o = *opts;
   o.alpha_log = nullptr;
   o.alpha_log_len = 0;
-  npfem_status rc = npfem_step(b, b->d_x, b->d_v, b->d_f, iters ? b->d_iters : nullptr, &o, b->d_res,
-                               b->d_status, stream);
-  if (rc != NPFEM_OK) return rc;
-  NPFEM_CUDA_TRY(cudaMemcpyAsync(x, b->d_x, bytes, cudaMemcpyDeviceToHost, st));
-  NPFEM_CUDA_TRY(cudaMemcpyAsync(v, b->d_v, bytes, cudaMemcpyDeviceToHost, st));
+  int max_iters = 0;
+  bool split = b->mode == 1 && (iters == nullptr || opts->max_iters > 0);
+  if (split) {
+    max_iters = iters ? opts->max_iters : opts->iters;
+    split = max_iters <= kSplitMaxIters && max_iters >= 0;
+  }
+  const int K = split ? std::min(kMaxGroups, b->ncells) : 1;
+  if (K < 2) {  // one chunk: copies in, step, copies out
+    NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_x, x, bytes, cudaMemcpyHostToDevice, st));
+    NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_v, v, bytes, cudaMemcpyHostToDevice, st));
+    NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_f, f_ext, bytes, cudaMemcpyHostToDevice, st));
+    if (iters)
+      NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_iters, iters, sizeof(int32_t) * b->ncells, cudaMemcpyHostToDevice, st));
+    npfem_status rc = npfem_step(b, b->d_x, b->d_v, b->d_f, iters ? b->d_iters : nullptr, &o, b->d_res,
+                                 b->d_status, stream);
+    if (rc != NPFEM_OK) return rc;
+    NPFEM_CUDA_TRY(cudaMemcpyAsync(x, b->d_x, bytes, cudaMemcpyDeviceToHost, st));
+    NPFEM_CUDA_TRY(cudaMemcpyAsync(v, b->d_v, bytes, cudaMemcpyDeviceToHost, st));
+  } else {
+    // K chunks of consecutive cells (about equal vertex counts): chunk g's inputs are
+    // copied on the copy-in stream, its chains start when they have arrived, and its
+    // outputs are copied back on the copy-out stream as soon as its chains are done, so
+    // copies overlap the other chunks' kernels.
+    const size_t nl = b->launches.size();
+    const size_t nev = 2 + kMaxGroups + kMaxGroups * nl;
+    if (!b->h2d_stream) NPFEM_CUDA_TRY(cudaStreamCreateWithFlags(&b->h2d_stream, cudaStreamNonBlocking));
+    if (!b->d2h_stream) NPFEM_CUDA_TRY(cudaStreamCreateWithFlags(&b->d2h_stream, cudaStreamNonBlocking));
+    while (b->pipe_events.size() < nev) {
+      cudaEvent_t e;
+      NPFEM_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      b->pipe_events.push_back(e);
+    }
+    cudaEvent_t* ev_start = &b->pipe_events[0];
+    cudaEvent_t* ev_in = &b->pipe_events[1];
+    cudaEvent_t* ev_done = &b->pipe_events[1 + kMaxGroups];
+    cudaEvent_t* ev_out = &b->pipe_events[1 + kMaxGroups + kMaxGroups * nl];
+    int bounds[kMaxGroups + 1];
+    bounds[0] = 0;
+    for (int g = 1; g < K; ++g) {
+      const int64_t target = b->n_total * g / K;
+      int c = (int)(std::lower_bound(b->offsets.begin(), b->offsets.end() - 1, target) - b->offsets.begin());
+      bounds[g] = std::max(bounds[g - 1], std::min(c, b->ncells));
+    }
+    bounds[K] = b->ncells;
+    const int64_t Nt = b->n_total;
+    auto part = [&](const void* base, int64_t o0) { return static_cast<const char*>(base) + ssize * o0; };
+    auto partw = [&](void* base, int64_t o0) { return static_cast<char*>(base) + ssize * o0; };
+    NPFEM_CUDA_TRY(cudaEventRecord(*ev_start, st));
+    NPFEM_CUDA_TRY(cudaStreamWaitEvent(b->h2d_stream, *ev_start, 0));
+    NPFEM_CUDA_TRY(cudaStreamWaitEvent(b->d2h_stream, *ev_start, 0));
+    if (iters)
+      NPFEM_CUDA_TRY(
+          cudaMemcpyAsync(b->d_iters, iters, sizeof(int32_t) * b->ncells, cudaMemcpyHostToDevice, b->h2d_stream));
+    for (int g = 0; g < K; ++g) {
+      const int64_t o0 = b->offsets[bounds[g]], o1 = b->offsets[bounds[g + 1]];
+      const size_t nb = ssize * (size_t)(o1 - o0);
+      if (nb)
+        for (int d = 0; d < 3; ++d) {
+          NPFEM_CUDA_TRY(cudaMemcpyAsync(partw(b->d_x, d * Nt + o0), part(x, d * Nt + o0), nb,
+                                         cudaMemcpyHostToDevice, b->h2d_stream));
+          NPFEM_CUDA_TRY(cudaMemcpyAsync(partw(b->d_v, d * Nt + o0), part(v, d * Nt + o0), nb,
+                                         cudaMemcpyHostToDevice, b->h2d_stream));
+          NPFEM_CUDA_TRY(cudaMemcpyAsync(partw(b->d_f, d * Nt + o0), part(f_ext, d * Nt + o0), nb,
+                                         cudaMemcpyHostToDevice, b->h2d_stream));
+        }
+      NPFEM_CUDA_TRY(cudaEventRecord(ev_in[g], b->h2d_stream));
+    }
+    PipelinePlan plan{K, bounds, ev_in, ev_done};
+    npfem_status rc = step_split(b, b->d_x, b->d_v, b->d_f, iters ? b->d_iters : nullptr, &o, max_iters, b->d_res,
+                                 b->d_status, st, &plan);
+    if (rc != NPFEM_OK) return rc;
+    for (int g = 0; g < K; ++g) {
+      for (size_t li = 0; li < nl; ++li)
+        NPFEM_CUDA_TRY(cudaStreamWaitEvent(b->d2h_stream, ev_done[g * nl + li], 0));
+      const int64_t o0 = b->offsets[bounds[g]], o1 = b->offsets[bounds[g + 1]];
+      const size_t nb = ssize * (size_t)(o1 - o0);
+      if (nb)
+        for (int d = 0; d < 3; ++d) {
+          NPFEM_CUDA_TRY(cudaMemcpyAsync(partw(x, d * Nt + o0), part(b->d_x, d * Nt + o0), nb,
+                                         cudaMemcpyDeviceToHost, b->d2h_stream));
+          NPFEM_CUDA_TRY(cudaMemcpyAsync(partw(v, d * Nt + o0), part(b->d_v, d * Nt + o0), nb,
+                                         cudaMemcpyDeviceToHost, b->d2h_stream));
+        }
+    }
+    NPFEM_CUDA_TRY(cudaEventRecord(*ev_out, b->d2h_stream));
+    NPFEM_CUDA_TRY(cudaStreamWaitEvent(st, *ev_out, 0));
+  }
   if (residual_out)
     NPFEM_CUDA_TRY(cudaMemcpyAsync(residual_out, b->d_res, sizeof(double) * b->ncells, cudaMemcpyDeviceToHost, st));
   if (status_out)

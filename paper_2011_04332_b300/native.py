@@ -80,6 +80,7 @@ def load_library() -> C.CDLL:
         "npfem_batch_phase_cycles": [vp, C.POINTER(C.c_uint64), C.c_int32],
         "npfem_batch_set_kernel_timing": [vp, C.c_int32],
         "npfem_batch_set_groups": [vp, C.c_int32, C.c_int32],
+        "npfem_batch_kernel_spans": [vp, C.c_int32, C.POINTER(C.c_double)],
         "npfem_batch_get_groups": [vp, C.c_int32, C.POINTER(C.c_int32)],
         "npfem_batch_kernel_times": [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int32)],
         "npfem_batch_set_mode": [vp, C.c_int32],
@@ -241,6 +242,12 @@ class Batch:
         return {k: int(out[i]) for i, k in enumerate(self.PHASES)}
 
     KERNELS = ("k_begin", "k_solve", "k_iter")
+
+    def kernel_spans(self, type_index: int = -1) -> dict:
+        """npfem_batch_kernel_spans: {kernel: ms during which at least one such launch ran}."""
+        ms = (C.c_double * 3)()
+        _check(_lib.npfem_batch_kernel_spans(self.handle, int(type_index), ms))
+        return {k: float(ms[i]) for i, k in enumerate(self.KERNELS)}
 
     def set_groups(self, type_index: int, groups: int) -> None:
         """npfem_batch_set_groups: split mode, cells of the type in `groups` phase-offset chains."""

@@ -201,17 +201,30 @@ def test_nonfinite_force_sets_status_only_for_that_cell():
     assert np.all(np.isfinite(xg[:, b.cell_slice(0)]))
 
 
-def test_host_buffer_step_matches_device_step():
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("kind", ["homogeneous", "mixed"])
+def test_host_buffer_step_matches_device_step(prec, kind):
+    """npfem_step_host (chunks of cells copied in, stepped and copied out in a pipeline;
+    in the mixed batch the chunk boundaries cut through every type's cell list) gives the
+    device-buffer step's results bit for bit, from pinned and from pageable host arrays."""
     nat = _native()
-    b = I.homogeneous_rbc_batch(ncells=10, seed=6)
-    r = Runner(b, nat.FP64)
+    b = (I.homogeneous_rbc_batch(ncells=10, seed=6) if kind == "homogeneous"
+         else I.heterogeneous_batch(n_rbc3=7, n_rbc4=3, n_plt=6, seed=1010))
+    p = nat.FP64 if prec == "fp64" else nat.FP32FORM
+    r = Runner(b, p)
     xg, vg, res, st, _ = r.step(b.x, b.v, b.f, iters=b.iters)
-    xh, vh, fh = b.x.copy(), b.v.copy(), b.f.copy()
-    rh = np.zeros(b.ncells)
-    sh = np.zeros(b.ncells, np.int32)
-    r.batch.step_host(xh, vh, fh, iters=np.ascontiguousarray(b.iters), residual=rh, status=sh)
-    assert np.array_equal(xh, xg) and np.array_equal(vh, vg)
-    assert np.array_equal(rh, res) and np.array_equal(sh, st)
+    npdt = np.float64 if prec == "fp64" else np.float32
+    for pinned in (False, True):
+        if pinned:
+            xh, vh, fh = (torch.tensor(a, dtype=torch.float64 if prec == "fp64" else torch.float32).pin_memory().numpy()
+                          for a in (b.x, b.v, b.f))
+        else:
+            xh, vh, fh = (np.array(a, dtype=npdt, copy=True) for a in (b.x, b.v, b.f))
+        rh = np.zeros(b.ncells)
+        sh = np.zeros(b.ncells, np.int32)
+        r.batch.step_host(xh, vh, fh, iters=np.ascontiguousarray(b.iters), residual=rh, status=sh)
+        assert np.array_equal(xh.astype(np.float64), xg) and np.array_equal(vh.astype(np.float64), vg)
+        assert np.array_equal(rh, res) and np.array_equal(sh, st)
 
 
 def test_empty_batch_is_a_no_op():
@@ -347,6 +360,11 @@ def test_kernel_timing_eager_and_in_graph():
         kt = r.batch.kernel_times(t)
         assert [kt[k][1] for k in nat.Batch.KERNELS] == [1, kmax, kmax]
         assert all(kt[k][0] > 0 for k in nat.Batch.KERNELS)
+        sp = r.batch.kernel_spans(t)
+        # event times resolve to about half a microsecond
+        assert all(0 < sp[k] <= kt[k][0] + 0.01 for k in nat.Batch.KERNELS)
+    spall = r.batch.kernel_spans(-1)
+    assert all(spall[k] >= max(r.batch.kernel_spans(t)[k] for t in present) - 0.01 for k in nat.Batch.KERNELS)
     r.batch.set_kernel_timing(False)
 
 
