@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <map>
 #include <numeric>
@@ -87,6 +88,83 @@ void nested_dissection(const Graph& g, const std::vector<V3>& p, std::vector<int
   nested_dissection(g, p, left, order, leaf);
   nested_dissection(g, p, right, order, leaf);
   order->insert(order->end(), sep.begin(), sep.end());
+}
+
+// Nested dissection with a searched separator: at every level, try cut planes of several
+// directions (given unit vectors) at several quantile positions, take the vertices on one
+// side that touch the other side as the separator (either side), and keep the smallest
+// separator.  Subproblems of at most `leaf` vertices are ordered as they stand.
+void searched_dissection(const Graph& g, const std::vector<V3>& p, const std::vector<V3>& dirs,
+                         std::vector<int> idx, std::vector<int>* order, int leaf) {
+  if ((int)idx.size() <= leaf) {
+    order->insert(order->end(), idx.begin(), idx.end());
+    return;
+  }
+  static const double kFractions[] = {0.4, 0.45, 0.5, 0.55, 0.6};
+  std::vector<char> side(p.size(), 2);  // 0 lower, 1 upper, 2 outside this subproblem
+  std::vector<int> best_lo, best_hi, best_sep;
+  size_t best = SIZE_MAX;
+  std::vector<int> sorted;
+  for (const V3& d : dirs) {
+    sorted = idx;
+    std::sort(sorted.begin(), sorted.end(), [&](int a, int b) {
+      const double ca = dot(p[a], d), cb = dot(p[b], d);
+      return ca < cb || (ca == cb && a < b);
+    });
+    for (double fr : kFractions) {
+      const size_t cut = (size_t)(fr * (double)sorted.size());
+      for (size_t i = 0; i < sorted.size(); ++i) side[sorted[i]] = i < cut ? 0 : 1;
+      for (char sep_side = 0; sep_side < 2; ++sep_side) {
+        std::vector<int> lo, hi, sep;
+        for (int v : sorted) {
+          bool on_sep = false;
+          if (side[v] == sep_side)
+            for (int u : g[v])
+              if (side[u] == 1 - sep_side) {
+                on_sep = true;
+                break;
+              }
+          (on_sep ? sep : (side[v] == 0 ? lo : hi)).push_back(v);
+        }
+        if (!lo.empty() && !hi.empty() && sep.size() < best) {
+          best = sep.size();
+          best_lo.swap(lo);
+          best_hi.swap(hi);
+          best_sep.swap(sep);
+        }
+      }
+    }
+    for (int v : idx) side[v] = 2;
+  }
+  if (best == SIZE_MAX) {  // cannot split further
+    order->insert(order->end(), idx.begin(), idx.end());
+    return;
+  }
+  std::sort(best_lo.begin(), best_lo.end());
+  std::sort(best_hi.begin(), best_hi.end());
+  searched_dissection(g, p, dirs, best_lo, order, leaf);
+  searched_dissection(g, p, dirs, best_hi, order, leaf);
+  order->insert(order->end(), best_sep.begin(), best_sep.end());
+}
+
+// Cut directions for searched_dissection: the three axes, the ten face and space
+// diagonals of a cube (up to sign), and 30 points of a Fibonacci lattice on the upper
+// hemisphere (deterministic).
+std::vector<V3> cut_directions() {
+  std::vector<V3> d = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, -1, 0}, {1, 0, 1}, {1, 0, -1}, {0, 1, 1},
+                       {0, 1, -1}, {1, 1, 1}, {1, 1, -1}, {1, -1, 1}, {-1, 1, 1}};
+  const double golden = 3.14159265358979323846 * (3.0 - std::sqrt(5.0));
+  const int m = 30;
+  for (int k = 0; k < m; ++k) {
+    const double z = 1.0 - (k + 0.5) / m;  // (0, 1): upper hemisphere
+    const double r = std::sqrt(1.0 - z * z);
+    d.push_back({r * std::cos(golden * k), r * std::sin(golden * k), z});
+  }
+  for (V3& v : d) {
+    const double l = norm(v);
+    v = {v.x / l, v.y / l, v.z / l};
+  }
+  return d;
 }
 
 // Exact minimum degree on the elimination graph (small n only).
@@ -424,7 +502,8 @@ int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double
   for (auto& kv : Aij)
     if (kv.first.first != kv.first.second) g[kv.first.first].push_back(kv.first.second);
 
-  // ---- ordering: best of geometric nested dissection and minimum degree
+  // ---- ordering: least fill among geometric nested dissections (longest axis at the
+  // median; searched cut planes) and minimum degree
   std::vector<int> best;
   std::vector<std::vector<int>> best_cols;
   int64_t best_nnz = -1;
@@ -437,7 +516,13 @@ int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double
       nested_dissection(g, X, idx, &o, leaf);
       orders.push_back(o);
     }
-    if (n <= 12000) orders.push_back(minimum_degree(g));
+    const std::vector<V3> dirs = cut_directions();
+    for (int leaf : {4, 8}) {
+      std::vector<int> o;
+      searched_dissection(g, X, dirs, idx, &o, leaf);
+      orders.push_back(o);
+    }
+    if (n <= 1500) orders.push_back(minimum_degree(g));  // exact, quadratic-ish: small meshes only
     for (auto& o : orders) {
       std::vector<std::vector<int>> cols;
       int64_t nz = symbolic(g, o, &cols);
