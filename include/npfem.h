@@ -240,9 +240,11 @@ npfem_status npfem_batch_kernel_times(npfem_batch* batch, int32_t type_index, do
 npfem_status npfem_batch_kernel_spans(npfem_batch* batch, int32_t type_index, double* span_ms);
 
 /* Same step with HOST arrays (pageable or pinned): copies x, v, f_ext (and iters,
- * when given) to batch-owned device buffers, runs npfem_step, and copies x, v,
+ * when given) to batch-owned device buffers, runs the step, and copies x, v,
  * residuals and statuses back; synchronous.  residual_out/status_out are host
- * arrays or NULL. */
+ * arrays or NULL.  In split mode the batch is cut into chunks of consecutive cells whose
+ * copies in and out overlap the other chunks' kernels (pinned host memory lets the
+ * copies run asynchronously); results equal those of npfem_step. */
 npfem_status npfem_step_host(npfem_batch* batch, void* x, void* v, const void* f_ext,
                              const int32_t* iters, const npfem_solver_opts* opts,
                              double* residual_out, int32_t* status_out, void* stream);

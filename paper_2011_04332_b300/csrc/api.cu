@@ -83,7 +83,7 @@ struct npfem_batch {
   // every launch, per chain (type launch x group) and launch slot (0: k_begin, 1 + 2i:
   // k_solve of iteration i, 2 + 2i: k_iter of iteration i), re-recorded by every step
   bool ktiming = false;
-  std::vector<cudaEvent_t> kev;      // [launches.size() * kMaxGroups][kTimingSlots][2]
+  std::vector<cudaEvent_t> kev;      // [launches.size() * kMaxChains][kTimingSlots][2]
   std::vector<int> k_last_slots;     // slots recorded by the last step, per chain
   std::vector<int> k_last_chains;    // cell type of each chain of the last split step
   cudaEvent_t k_ref = nullptr;       // recorded on the caller's stream at the start of a timed step
@@ -104,8 +104,8 @@ struct npfem_batch {
   }
   // pipelined host-buffer steps: copy streams and per-chunk events
   cudaStream_t h2d_stream = nullptr, d2h_stream = nullptr;
-  std::vector<cudaEvent_t> pipe_events;  // [0]: start, [1..kMaxGroups]: inputs copied,
-                                         // then kMaxGroups x launches: chunk done per type, last: outputs copied
+  std::vector<cudaEvent_t> pipe_events;  // [0]: start, [1..kMaxChains]: inputs copied,
+                                         // then kMaxChains x launches: chunk done per type, last: outputs copied
   // host-step staging (allocated on first npfem_step_host)
   void* d_x = nullptr;
   void* d_v = nullptr;
@@ -459,7 +459,7 @@ static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_e
     return fail(NPFEM_ERR_INVALID_ARG, "split step: kernel timing was enabled for fewer chains; enable it again");
   }
   if (b->ktiming) NPFEM_CUDA_TRY(record_timing_event(b->k_ref, st));
-  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kMaxGroups * kSplitCounters, st));
+  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kMaxChains * kSplitCounters, st));
   if (fork) {
     NPFEM_CUDA_TRY(cudaEventRecord(b->fork_event, st));
     for (size_t c = 0; c < nc; ++c) NPFEM_CUDA_TRY(cudaStreamWaitEvent(b->type_streams[c], b->fork_event, 0));
@@ -673,7 +673,7 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
   cudaError_t e = b->mem.upload(b->offsets, &b->d_offsets);
   if (e != cudaSuccess) return cleanup(NPFEM_ERR_CUDA, std::string("batch_create: ") + cudaGetErrorString(e));
   void* cnt = nullptr;
-  e = b->mem.alloc(sizeof(int) * ntypes * kMaxGroups * kSplitCounters, &cnt);
+  e = b->mem.alloc(sizeof(int) * ntypes * kMaxChains * kSplitCounters, &cnt);
   if (e != cudaSuccess) return cleanup(NPFEM_ERR_OOM, std::string("batch_create: ") + cudaGetErrorString(e));
   b->d_counters = static_cast<int*>(cnt);
   void* ph = nullptr;
@@ -713,7 +713,7 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
       return cleanup(NPFEM_ERR_OOM, std::string("batch_create: ") + cudaGetErrorString(e));
     L.cell_list = dl;
     L.host_list = list;
-    L.counter = b->d_counters + (size_t)ti * kMaxGroups * kSplitCounters;  // group 0's block
+    L.counter = b->d_counters + (size_t)ti * kMaxChains * kSplitCounters;  // chain 0's block
     // default shape: 4 warps per CTA and 3 CTAs per SM, solve vectors in shared memory
     // when four of them fit in 72 KB (n <= 767), else in the workspace
     const size_t zbytes = sizeof(double) * 3 * ((size_t)H.n + 1);
@@ -762,7 +762,7 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
     const int max_iters = iters ? opts->max_iters : opts->iters;
     if (max_iters <= kSplitMaxIters) return step_split(b, x, v, f_ext, iters, opts, max_iters, residual_out, status_out, st);
   }
-  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kMaxGroups * kSplitCounters, st));
+  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kMaxChains * kSplitCounters, st));
   for (const TypeLaunch& L : b->launches) {
     const npfem_cell_type* t = b->types[L.type_index];
     StepParams P{};
@@ -820,7 +820,7 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     L.adj_scratch = static_cast<char*>(p);
     L.adj_slot = bytes;
   }
-  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kMaxGroups * kSplitCounters, st));
+  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kMaxChains * kSplitCounters, st));
   for (size_t li = 0; li < b->launches.size(); ++li) {
     const TypeLaunch& L = b->launches[li];
     const npfem_cell_type* t = b->types[L.type_index];
@@ -954,7 +954,7 @@ npfem_status npfem_batch_phase_cycles(npfem_batch* b, uint64_t* cycles, int32_t 
 
 npfem_status npfem_batch_set_kernel_timing(npfem_batch* b, int32_t enable) {
   if (!b) return fail(NPFEM_ERR_INVALID_ARG, "batch_set_kernel_timing: null batch");
-  const size_t chains = b->launches.size() * kMaxGroups;
+  const size_t chains = b->launches.size() * kMaxChains;
   if (enable && b->kev.size() < chains * kTimingSlots * 2) {
     const size_t old = b->kev.size();
     b->kev.resize(chains * kTimingSlots * 2, nullptr);
@@ -1076,7 +1076,9 @@ npfem_status npfem_step_host(npfem_batch* b, void* x, void* v, const void* f_ext
     max_iters = iters ? opts->max_iters : opts->iters;
     split = max_iters <= kSplitMaxIters && max_iters >= 0;
   }
-  const int K = split ? std::min(kMaxGroups, b->ncells) : 1;
+  // chunks: up to 12 chains in all (8 chunks for one cell type, 4 for three)
+  const int per_type = std::max(2, 12 / std::max(1, (int)b->launches.size()));
+  const int K = split ? std::min(std::min(kMaxChains, per_type), b->ncells) : 1;
   if (K < 2) {  // one chunk: copies in, step, copies out
     NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_x, x, bytes, cudaMemcpyHostToDevice, st));
     NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_v, v, bytes, cudaMemcpyHostToDevice, st));
@@ -1094,7 +1096,7 @@ npfem_status npfem_step_host(npfem_batch* b, void* x, void* v, const void* f_ext
     // outputs are copied back on the copy-out stream as soon as its chains are done, so
     // copies overlap the other chunks' kernels.
     const size_t nl = b->launches.size();
-    const size_t nev = 2 + kMaxGroups + kMaxGroups * nl;
+    const size_t nev = 2 + kMaxChains + kMaxChains * nl;
     if (!b->h2d_stream) NPFEM_CUDA_TRY(cudaStreamCreateWithFlags(&b->h2d_stream, cudaStreamNonBlocking));
     if (!b->d2h_stream) NPFEM_CUDA_TRY(cudaStreamCreateWithFlags(&b->d2h_stream, cudaStreamNonBlocking));
     while (b->pipe_events.size() < nev) {
@@ -1104,9 +1106,9 @@ npfem_status npfem_step_host(npfem_batch* b, void* x, void* v, const void* f_ext
     }
     cudaEvent_t* ev_start = &b->pipe_events[0];
     cudaEvent_t* ev_in = &b->pipe_events[1];
-    cudaEvent_t* ev_done = &b->pipe_events[1 + kMaxGroups];
-    cudaEvent_t* ev_out = &b->pipe_events[1 + kMaxGroups + kMaxGroups * nl];
-    int bounds[kMaxGroups + 1];
+    cudaEvent_t* ev_done = &b->pipe_events[1 + kMaxChains];
+    cudaEvent_t* ev_out = &b->pipe_events[1 + kMaxChains + kMaxChains * nl];
+    int bounds[kMaxChains + 1];
     bounds[0] = 0;
     for (int g = 1; g < K; ++g) {
       const int64_t target = b->n_total * g / K;

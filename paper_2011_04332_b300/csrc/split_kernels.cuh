@@ -37,8 +37,11 @@ struct IterOccupancy<float> {
 // that still iterate at iteration i (appended by k_begin for i = 0, by k_iter(i - 1)).
 constexpr int kActiveCountOff = 2 + 2 * kSplitMaxIters;
 constexpr int kSplitCounters = kActiveCountOff + kSplitMaxIters + 1;
-// A type's cells can be split into up to kMaxGroups groups, each with its own counters.
+// A type's cells run as up to kMaxChains chains of kernels, each with its own counter
+// block: up to kMaxGroups concurrent groups of a device-buffer step, up to kMaxChains
+// chunks of a pipelined host-buffer step.
 constexpr int kMaxGroups = 4;
+constexpr int kMaxChains = 8;
 constexpr size_t kStateBytes = 256;
 
 template <typename S>
