@@ -393,16 +393,19 @@ def two_loop(g: np.ndarray, S: List[np.ndarray], Y: List[np.ndarray],
 
 
 def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
-         f_ext: np.ndarray, iters: int, w_scale=None) -> StepResult:
+         f_ext: np.ndarray, iters: int, w_scale=None, tol: float = 0.0) -> StepResult:
     """One implicit time step of one cell by quasi-Newton projective dynamics.
 
     y = x_n + dt v_n + dt^2 M^-1 f_ext;  x^(0) = y;  history cleared.
     Repeat `iters` times: d = -two_loop(g); backtracking line search from alpha = 1
     (Armijo, or approximate Armijo g(x+ad).d <= (2 c1 - 1) g.d together with an
     energy guard f(x+ad) <= f(x) + 1e-6 |f(x)|); x <- x + alpha d; keep (s, y) when
-    s.y > 1e-12 |s||y|, at most 5 pairs.
-    v_{n+1} = (x^(iters) - x_n) / dt.  Works relative to the centroid of x_n
-    (the objective is translation invariant), adding it back at the end.
+    s.y > 1e-12 |s||y|, at most 5 pairs.  With tol > 0 (converged-residual mode, the
+    iteration run towards a converged solution: Implementation and architecture
+    section), stop after the first iteration whose gradient satisfies
+    |g| < tol |g^(0)| (a cell with g^(0) = 0 runs all `iters`).
+    v_{n+1} = (x^(k) - x_n) / dt for the last iterate k.  Works relative to the
+    centroid of x_n (the objective is translation invariant), adding it back at the end.
     """
     dt = rs.dt
     ctr = np.real(x_n).mean(axis=0)
@@ -456,6 +459,8 @@ def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
         alphas.append(alpha)
         energies.append(float(np.real(fx)))
         gnorms.append(float(np.sqrt(np.sum(np.real(g) ** 2))))
+        if tol > 0 and gnorms[-1] < tol * g0n:
+            break
     residual = gnorms[-1] / g0n if g0n > 0 else 0.0
     x_new = x + ctr
     v_new = (x - xn) / dt
@@ -477,23 +482,26 @@ class CellType:
 
 
 def batch_step(types: List[CellType], type_of_cell, offsets, x, v, f, iters,
-               cells: Optional[List[int]] = None) -> Dict[str, np.ndarray]:
+               cells: Optional[List[int]] = None, tol: float = 0.0) -> Dict[str, np.ndarray]:
     """One step for a batch in SoA [3, N_total] layout; returns new x, v (for the
     selected cells only; other columns are copied through) plus per-cell residuals,
-    statuses and accepted step lengths."""
+    statuses, accepted step lengths and iterations done (tol: as in `step`)."""
     xo, vo = x.copy(), v.copy()
     ncells = len(type_of_cell)
     cells = range(ncells) if cells is None else cells
     res = np.zeros(ncells)
     st = np.zeros(ncells, dtype=np.int32)
     alphas = {}
+    done = np.zeros(ncells, dtype=np.int32)
     for c in cells:
         s = slice(int(offsets[c]), int(offsets[c + 1]))
         ct = types[int(type_of_cell[c])]
-        r = step(ct.rest, ct.solver, x[:, s].T, v[:, s].T, f[:, s].T, int(iters[c]), ct.w_scale)
+        r = step(ct.rest, ct.solver, x[:, s].T, v[:, s].T, f[:, s].T, int(iters[c]), ct.w_scale, tol)
         xo[:, s] = r.x.T
         vo[:, s] = r.v.T
         res[c] = r.residual
         st[c] = r.status
         alphas[c] = r.alphas
-    return {"x": xo, "v": vo, "residual": res, "status": st, "alphas": alphas}
+        done[c] = len(r.alphas)
+    return {"x": xo, "v": vo, "residual": res, "status": st, "alphas": alphas,
+            "iters_done": done}

@@ -178,3 +178,45 @@ def test_complex_step_derivative_matches_central_differences():
         cp, cm = _type(m, w_scale=wp), _type(m, w_scale=wm)
         fdw = (O.step(cp.rest, cp.solver, x, v, f, 5, wp).x - O.step(cm.rest, cm.solver, x, v, f, 5, wm).x) / (2 * e)
         assert np.max(np.abs(csw - fdw)) <= 2e-5 * np.max(np.abs(csw)), q
+
+
+def test_converged_residual_mode_stops_at_first_iterate_below_tol():
+    """Converged-residual mode: the step ends after the first iteration whose
+    gradient norm falls below tol |g0|; that run equals a fixed-budget run of the
+    same length, every shorter run is still above tol, and the stopped iterate
+    lies within the tolerance's reach of the exact minimiser (brute-force Newton)."""
+    m = I.icosahedron()
+    dt = 0.5
+    ct = _type(m, MAT, dt)
+    rs = ct.rest
+    rng = np.random.default_rng(31)
+    x = m.verts
+    v = 0.2 * rng.standard_normal(x.shape)
+    f = 0.3 * rng.standard_normal(x.shape)
+    ctr = x.mean(axis=0)
+    y = (x - ctr) + dt * v + dt * dt * f / rs.mass[:, None]
+    xs = _newton_minimise(rs, y, y.copy()) + ctr
+    radius = np.max(np.linalg.norm(xs - xs.mean(axis=0), axis=1))
+    prev = 0
+    for tol in (1e-2, 1e-4, 1e-6, 1e-9):
+        r = O.step(rs, ct.solver, x, v, f, 200, tol=tol)
+        k = len(r.alphas)
+        assert r.residual < tol and k < 200 and k >= prev
+        assert all(gn >= tol * r.grad_norms[0] for gn in r.grad_norms[:-1])
+        fixed = O.step(rs, ct.solver, x, v, f, k)
+        assert np.array_equal(fixed.x, r.x) and np.array_equal(fixed.v, r.v)
+        if k > 1:
+            assert O.step(rs, ct.solver, x, v, f, k - 1).residual >= tol
+        prev = k
+    assert np.max(np.abs(r.x - xs)) <= 1e-7 * radius
+
+
+def test_converged_residual_mode_zero_gradient_runs_budget():
+    """A cell already at the minimiser (|g0| = 0) never meets |g| < tol |g0| and so
+    runs its whole budget; its state is unchanged."""
+    m = I.rbc_mesh(1)
+    ct = _type(m)
+    r = O.step(ct.rest, ct.solver, m.verts, np.zeros_like(m.verts), np.zeros_like(m.verts),
+               4, tol=1e-3)
+    assert len(r.alphas) == 4
+    assert np.max(np.abs(r.x - m.verts)) <= 1e-14 * np.max(np.abs(m.verts))
