@@ -61,19 +61,41 @@ def make_workload(name: str, rank: int = 0):
     return b, desc
 
 
+def residual_mode(b, desc: str, tol: float, budget: int):
+    """Converged-residual mode (tol > 0): every cell's count becomes the budget and the
+    step ends per cell at |g|/|g0| < tol."""
+    if tol > 0:
+        b.iters = np.full(b.ncells, budget, dtype=np.int32)
+        desc += (f"; converged-residual mode in place of the fixed counts: each cell stops at |g|/|g0| < {tol:g} "
+                 f"(budget {budget} iterations)")
+    return b, desc
+
+
 # ------------------------------------------------------------------ oracle baseline
 def _oracle_worker(args):
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     from oracle import npfem_oracle as O
-    mesh_v, mesh_t, mat, dt, cells = args
+    mesh_v, mesh_t, mat, dt, cells, tol = args
     ct = O.CellType(mesh_v, mesh_t, mat, dt)
     t0 = time.perf_counter()
     for (x, v, f, it) in cells:
-        O.step(ct.rest, ct.solver, x, v, f, int(it))
+        O.step(ct.rest, ct.solver, x, v, f, int(it), tol=tol)
     return time.perf_counter() - t0, len(cells)
 
 
-def oracle_baseline(b, sample_cells: int, workers: int):
+def step_units(b, sel=None, tol: float = 0.0) -> float:
+    """RBC-equivalent cell-steps of one step over the cells `sel` (default all): a cell
+    of n vertices counts n/642; with fixed counts it is also weighted by iterations/5
+    (five iterations of a 642-vertex RBC = 1), in the converged-residual mode (tol > 0)
+    every cell-step is delivered at the stated residual and counts n/642."""
+    sel = np.arange(b.ncells) if sel is None else np.asarray(sel)
+    n = np.array([b.types[int(b.type_of_cell[c])].mesh.n for c in sel], dtype=np.float64)
+    if tol > 0:
+        return float(np.sum(n / 642.0))
+    return float(np.sum(n / 642.0 * b.iters[sel] / 5.0))
+
+
+def oracle_baseline(b, sample_cells: int, workers: int, tol: float = 0.0):
     """Time the oracle on the first `sample_cells` cells, one step each, spread over
     `workers` single-threaded processes (spawn).  Returns (rbc_eq per s, cores, desc)."""
     import multiprocessing as mp
@@ -88,7 +110,7 @@ def oracle_baseline(b, sample_cells: int, workers: int):
         for ch in chunks:
             if ch:
                 jobs.append((ty.mesh.verts, ty.mesh.tris, ty.material.as_tuple(), b.dt,
-                             [(*b.cell_state(c), b.iters[c]) for c in ch]))
+                             [(*b.cell_state(c), b.iters[c]) for c in ch], tol))
     ctx = mp.get_context("spawn")
     env_backup = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
     for k in env_backup:
@@ -105,8 +127,7 @@ def oracle_baseline(b, sample_cells: int, workers: int):
             else:
                 os.environ[k] = v
     busy = max(r[0] for r in res)  # the slowest worker's stepping time (setup excluded)
-    n = np.array([b.types[int(b.type_of_cell[c])].mesh.n for c in sel], dtype=np.float64)
-    rbc_eq = float(np.sum(n / 642.0 * b.iters[sel] / 5.0))
+    rbc_eq = step_units(b, sel, tol)
     desc = (f"{len(sel)} cells x 1 step of the same workload (first cells in batch order), "
             f"{workers} single-threaded processes; type setup excluded; wall incl. setup {wall:.1f}s")
     return rbc_eq / busy, workers, desc
@@ -189,10 +210,12 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     b, desc = make_workload(args.workload, rank)
+    b, desc = residual_mode(b, desc, args.tol, args.budget)
+    tol = args.tol
     # oracle baseline first (spawned processes, before heavy GPU work), rank 0 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, cores, sdesc = oracle_baseline(b, args.cpu_sample, args.cpu_workers)
+        v, cores, sdesc = oracle_baseline(b, args.cpu_sample, args.cpu_workers, tol)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc}
 
     prec = native.FP32FORM if args.precision == "fp32form" else native.FP64
@@ -212,6 +235,8 @@ def run_ours(args, rank, world, local_rank):
     iters = torch.tensor(b.iters, device=dev)
     res = torch.zeros(b.ncells, dtype=torch.float64, device=dev)
     st = torch.zeros(b.ncells, dtype=torch.int32, device=dev)
+    done = torch.zeros(b.ncells, dtype=torch.int32, device=dev) if tol > 0 else None
+    done_sum = torch.zeros(b.ncells, dtype=torch.int64, device=dev) if tol > 0 else None
     x, v = x0.clone(), v0.clone()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 126 MB L2
     stream = torch.cuda.current_stream(dev)
@@ -221,24 +246,28 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_check:
         from oracle import npfem_oracle as O
         xs, vs_ = x0.clone(), v0.clone()
-        batch.step(xs, vs_, f, iters=iters, residual=res, status=st)
+        batch.step(xs, vs_, f, iters=iters, residual=res, status=st, tol=tol, iters_done=done)
         torch.cuda.synchronize()
+        done_gpu = done.cpu().numpy() if done is not None else b.iters
         sample = [0, b.ncells // 3, (2 * b.ncells) // 3, b.ncells - 1]
         ot = {}
         xin, vin, fin = (t.double().cpu().numpy() for t in (x0, v0, f))
         xg = xs.double().cpu().numpy()
-        errs = []
+        errs, counts = [], []
         for c in sample:
             t = int(b.type_of_cell[c])
             if t not in ot:
                 ty = b.types[t]
                 ot[t] = O.CellType(ty.mesh.verts, ty.mesh.tris, ty.material.as_tuple(), b.dt)
             s = b.cell_slice(c)
-            r = O.step(ot[t].rest, ot[t].solver, xin[:, s].T, vin[:, s].T, fin[:, s].T, int(b.iters[c]))
+            r = O.step(ot[t].rest, ot[t].solver, xin[:, s].T, vin[:, s].T, fin[:, s].T, int(b.iters[c]), tol=tol)
             rad = np.max(np.linalg.norm(r.x - r.x.mean(axis=0), axis=1))
             errs.append(float(np.max(np.abs(xg[:, s].T - r.x)) / rad))
+            counts.append((int(done_gpu[c]), len(r.alphas)))
         err = {"cells": sample, "max_rel_position_error": max(errs),
                "bar": 1e-5 if prec == native.FP32FORM else 1e-10}
+        if tol > 0:
+            err["iterations_gpu_oracle"] = counts
 
     tuned = None
     if args.no_tune and args.groups > 0:
@@ -248,13 +277,13 @@ def run_ours(args, rank, world, local_rank):
         # launch-shape autotuning on copies of the state (outside the timed region)
         from paper_2011_04332_b300 import tuning
         t0 = time.perf_counter()
-        tuned = tuning.autotune_split(batch, x0, v0, f, iters=iters)
+        tuned = tuning.autotune_split(batch, x0, v0, f, iters=iters, tol=tol)
         tuned = {"seconds": round(time.perf_counter() - t0, 1),
                  "shapes": {str(t): list(r["split_shape"]) for t, r in tuned.items()},
                  "groups": {str(t): r["groups"] for t, r in tuned.items()}}
     batch.set_kernel_timing(True)       # CUDA events around every launch (also inside the graph)
     for _ in range(args.warmup):
-        batch.step(x, v, f, iters=iters, residual=res, status=st)
+        batch.step(x, v, f, iters=iters, residual=res, status=st, tol=tol, iters_done=done)
     torch.cuda.synchronize()
     graph = None
     if not args.no_graph:
@@ -264,7 +293,7 @@ def run_ours(args, rank, world, local_rank):
         side.wait_stream(stream)
         with torch.cuda.stream(side):
             with torch.cuda.graph(graph, stream=side):
-                batch.step(x, v, f, iters=iters, residual=res, status=st)
+                batch.step(x, v, f, iters=iters, residual=res, status=st, tol=tol, iters_done=done)
         stream.wait_stream(side)
         torch.cuda.synchronize()
         graph.replay()          # the capture does not execute; replay once as warm-up
@@ -274,7 +303,7 @@ def run_ours(args, rank, world, local_rank):
         if graph is not None:
             graph.replay()
         else:
-            batch.step(x, v, f, iters=iters, residual=res, status=st)
+            batch.step(x, v, f, iters=iters, residual=res, status=st, tol=tol, iters_done=done)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if world > 1:
@@ -292,6 +321,8 @@ def run_ours(args, rank, world, local_rank):
                 f.copy_(fpool[(k // 10) % len(fpool)])
             one_step()
             ev[k][1].record(stream)
+            if done_sum is not None:
+                done_sum += done     # iterations each cell ran (after the end event: untimed)
             # per-kernel durations of this step (events on the kernels' own streams)
             for t in present:
                 for name, (kms, kn) in batch.kernel_times(t).items():
@@ -305,7 +336,7 @@ def run_ours(args, rank, world, local_rank):
         torch.distributed.barrier()
     ms = [a.elapsed_time(bq) for a, bq in ev]
     total_ms = max_over_ranks(float(sum(ms)), world, dev)
-    rbc_eq_per_rank = b.rbc_equivalents()
+    rbc_eq_per_rank = step_units(b, None, tol)
     value = whole_job_rate(rbc_eq_per_rank, world, args.steps, total_ms)
     ms_per_step = total_ms / args.steps
     resid = res.cpu().numpy()
@@ -316,7 +347,9 @@ def run_ours(args, rank, world, local_rank):
     # union of their intervals: the chains of a step run concurrently)
     nnz = np.array([infos[t]["nnz_factor"] for t in b.type_of_cell], dtype=np.float64)
     nv = np.array([infos[t]["n_verts"] for t in b.type_of_cell], dtype=np.float64)
-    solve_flops = b.iters * (12.0 * nnz + 3.0 * nv)          # per cell and step
+    # iterations per cell and step: the fixed counts, or the mean of those run under tol
+    its = b.iters.astype(np.float64) if done_sum is None else done_sum.cpu().numpy() / args.steps
+    solve_flops = its * (12.0 * nnz + 3.0 * nv)          # per cell and step
     flops_per_step = float(np.sum(solve_flops))
     fp64_peak, fp32_peak = probe_peaks()
     kernels = {}
@@ -333,7 +366,7 @@ def run_ours(args, rank, world, local_rank):
     solve_span = kspan["k_solve"] / args.steps
     achieved = flops_per_step / (solve_span / 1e3) / 1e12 if solve_span > 0 else None
     traffic_cell, traffic_how = measured_traffic(args.workload, args.precision)
-    cell_solves = float(np.sum(b.iters))
+    cell_solves = float(np.sum(its))
     traffic = traffic_cell * cell_solves / solve_launches if traffic_cell and solve_launches else None
     roofline = {"bound": "alu", "pipe": "fp64", "kernel": "npfem_k_solve", "achieved": achieved, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": achieved / fp64_peak if fp64_peak and achieved else None, "traffic": traffic,
@@ -361,16 +394,20 @@ def run_ours(args, rank, world, local_rank):
         hit = torch.tensor(b.iters, dtype=torch.int32).pin_memory()
         hres = torch.zeros(b.ncells, dtype=torch.float64).pin_memory()
         hst = torch.zeros(b.ncells, dtype=torch.int32).pin_memory()
+        hdn = torch.zeros(b.ncells, dtype=torch.int32).pin_memory() if tol > 0 else None
         nx, nv_, nf, ni, nr, ns = (hx.numpy(), hv.numpy(), hf.numpy(), hit.numpy(), hres.numpy(), hst.numpy())
+        nd = hdn.numpy() if hdn is not None else None
         for _ in range(max(1, args.warmup)):
-            batch.step_host(nx, nv_, nf, iters=ni, residual=nr, status=ns, stream=stream.cuda_stream)
+            batch.step_host(nx, nv_, nf, iters=ni, residual=nr, status=ns, stream=stream.cuda_stream,
+                            tol=tol, iters_done=nd)
         times = []
         for _ in range(args.steps):
             t0 = time.perf_counter()
-            batch.step_host(nx, nv_, nf, iters=ni, residual=nr, status=ns, stream=stream.cuda_stream)
+            batch.step_host(nx, nv_, nf, iters=ni, residual=nr, status=ns, stream=stream.cuda_stream,
+                            tol=tol, iters_done=nd)
             times.append(time.perf_counter() - t0)
         h2d = 3 * 3 * b.n_total * ssz + 4 * b.ncells
-        d2h = 2 * 3 * b.n_total * ssz + 12 * b.ncells
+        d2h = 2 * 3 * b.n_total * ssz + 12 * b.ncells + (4 * b.ncells if nd is not None else 0)
         e2e = {"value": rbc_eq_per_rank / statistics.mean(times), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "api": "npfem_step_host (pinned host buffers, copies + step + copies, synchronous)"}
@@ -393,6 +430,11 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": "cells sharded across ranks, no collective" if world > 1 else "1 GPU"},
         "residual": {"median": float(np.median(resid)), "max": float(np.max(resid)),
                      "definition": "|grad f(x_final)| / |grad f(x_0)| per cell after the step"},
+        "residual_mode": ({"tol": tol, "budget": args.budget, "mean_iterations": float(np.mean(its)),
+                           "cells_at_budget_last_step": int(np.sum(done.cpu().numpy() >= args.budget)),
+                           "unit_rule": "each cell-step at the stated residual counts n/642"}
+                          if tol > 0 else {"fixed_iterations": True,
+                                           "unit_rule": "each cell-step counts (n/642)*(iterations/5)"}),
         "status_nonzero_cells": int(np.count_nonzero(status)),
         "parity_sample": err,
         "roofline": roofline,
@@ -496,11 +538,12 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     b, desc = make_workload(args.workload, 0)
+    b, desc = residual_mode(b, desc, args.tol, args.budget)
     per_step = []
     cores = args.cpu_workers
     sdesc = ""
     for _ in range(args.warmup + args.steps):
-        v, cores, sdesc = oracle_baseline(b, args.ref_sample, args.cpu_workers)
+        v, cores, sdesc = oracle_baseline(b, args.ref_sample, args.cpu_workers, args.tol)
         per_step.append(v)
     vals = per_step[args.warmup:]
     value = float(statistics.mean(vals))
@@ -529,6 +572,9 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--tol", type=float, default=0.0,
+                    help="converged-residual mode: per-cell stop at |g|/|g0| < tol (0: fixed iteration counts)")
+    ap.add_argument("--budget", type=int, default=16, help="with --tol: iteration budget per cell")
     ap.add_argument("--groups", type=int, default=0,
                     help="with --no-tune: phase-offset chains per cell type (0: library default)")
     args = ap.parse_args()

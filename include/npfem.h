@@ -97,6 +97,13 @@ typedef struct {
   double* alpha_log;       /* device [ncells][alpha_log_len] accepted step lengths, or NULL */
   int32_t max_iters;       /* upper bound of the per-cell counts of an iters array (split mode
                               launches that many iterations; 0 = unknown: fused mode) */
+  double tol;              /* converged-residual mode (the solver run towards a converged
+                              solution, Implementation and architecture section): > 0 ends a
+                              cell's step after the first iteration whose gradient norm is below
+                              tol * |grad f(x_0)|, compared in FP64; the iteration count is then
+                              a budget.  0 = fixed counts.  Must be finite and >= 0. */
+  int32_t* iters_done;     /* out [ncells] iterations each cell ran, or NULL: device memory for
+                              npfem_step / npfem_step_noalloc, host memory for npfem_step_host */
 } npfem_solver_opts;
 
 typedef struct npfem_cell_type npfem_cell_type;
@@ -142,7 +149,12 @@ npfem_status npfem_batch_layout(const npfem_batch* batch, int64_t* n_total, int6
  *   iters in [ncells] int32 per-cell iteration counts (>= 0), or NULL to use opts->iters.
  *   residual_out out [ncells] |grad f(x_final)| / |grad f(x_0)| (FP64), or NULL.
  *   status_out   out [ncells] NPFEM_CELL_* bit flags, or NULL.
- * Asynchronous on `stream` (a cudaStream_t).  Errors: INVALID_ARG, CUDA. */
+ * With opts->tol > 0 a cell that meets the tolerance stops early and its remaining
+ * iterations are skipped (split mode keeps launching up to the budget over the
+ * shrinking list of cells still iterating).  The result of a cell that stops after k
+ * iterations equals that of a fixed-count step of k iterations.
+ * Asynchronous on `stream` (a cudaStream_t).  Errors: INVALID_ARG (also a negative or
+ * non-finite tol), CUDA. */
 npfem_status npfem_step(npfem_batch* batch, void* x, void* v, const void* f_ext,
                         const int32_t* iters, const npfem_solver_opts* opts,
                         double* residual_out, int32_t* status_out, void* stream);
@@ -161,7 +173,9 @@ npfem_status npfem_step(npfem_batch* batch, void* x, void* v, const void* f_ext,
  *   status_out    out [ncells] or NULL: 0, or 8 when a cell's iteration count exceeds 16.
  * The first call on a batch allocates its adjoint workspace (about 2 MB per warp
  * slot for a 642-vertex type).  Asynchronous on `stream`.
- * Errors: INVALID_ARG (null pointer, FP32-form batch), CUDA, OOM. */
+ * opts->tol must be 0 (the adjoint differentiates fixed iteration counts); opts->iters_done
+ * is ignored.
+ * Errors: INVALID_ARG (null pointer, FP32-form batch, tol != 0), CUDA, OOM. */
 npfem_status npfem_step_adjoint(npfem_batch* batch, const void* x, const void* v, const void* f_ext,
                                 const int32_t* iters, const npfem_solver_opts* opts,
                                 const double* gx_next, const double* gv_next, double* gx, double* gv,
@@ -241,8 +255,8 @@ npfem_status npfem_batch_kernel_spans(npfem_batch* batch, int32_t type_index, do
 
 /* Same step with HOST arrays (pageable or pinned): copies x, v, f_ext (and iters,
  * when given) to batch-owned device buffers, runs the step, and copies x, v,
- * residuals and statuses back; synchronous.  residual_out/status_out are host
- * arrays or NULL.  In split mode the batch is cut into chunks of consecutive cells whose
+ * residuals, statuses (and opts->iters_done) back; synchronous.  residual_out,
+ * status_out and opts->iters_done are host arrays or NULL.  In split mode the batch is cut into chunks of consecutive cells whose
  * copies in and out overlap the other chunks' kernels (pinned host memory lets the
  * copies run asynchronously); results equal those of npfem_step. */
 npfem_status npfem_step_host(npfem_batch* batch, void* x, void* v, const void* f_ext,

@@ -485,13 +485,14 @@ def batch_step(types: List[CellType], type_of_cell, offsets, x, v, f, iters,
                cells: Optional[List[int]] = None, tol: float = 0.0) -> Dict[str, np.ndarray]:
     """One step for a batch in SoA [3, N_total] layout; returns new x, v (for the
     selected cells only; other columns are copied through) plus per-cell residuals,
-    statuses, accepted step lengths and iterations done (tol: as in `step`)."""
+    statuses, accepted step lengths, gradient norms and iterations done (tol: as in
+    `step`)."""
     xo, vo = x.copy(), v.copy()
     ncells = len(type_of_cell)
     cells = range(ncells) if cells is None else cells
     res = np.zeros(ncells)
     st = np.zeros(ncells, dtype=np.int32)
-    alphas = {}
+    alphas, gnorms = {}, {}
     done = np.zeros(ncells, dtype=np.int32)
     for c in cells:
         s = slice(int(offsets[c]), int(offsets[c + 1]))
@@ -502,6 +503,7 @@ def batch_step(types: List[CellType], type_of_cell, offsets, x, v, f, iters,
         res[c] = r.residual
         st[c] = r.status
         alphas[c] = r.alphas
+        gnorms[c] = r.grad_norms
         done[c] = len(r.alphas)
     return {"x": xo, "v": vo, "residual": res, "status": st, "alphas": alphas,
-            "iters_done": done}
+            "grad_norms": gnorms, "iters_done": done}

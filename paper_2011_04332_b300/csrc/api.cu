@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -113,6 +114,7 @@ struct npfem_batch {
   int32_t* d_iters = nullptr;
   double* d_res = nullptr;
   int32_t* d_status = nullptr;
+  int32_t* d_done = nullptr;
 };
 
 template <typename S>
@@ -471,6 +473,8 @@ static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_e
   P.iters_default = opts->iters;
   P.residual_out = residual_out;
   P.status_out = status_out;
+  P.tol = opts->tol;
+  P.iters_done = opts->iters_done;
   P.alpha_log = opts->alpha_log;
   P.alpha_log_len = opts->alpha_log_len;
   P.phase_cycles = b->d_phase;
@@ -757,6 +761,8 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
   if (opts->iters < 0) return fail(NPFEM_ERR_INVALID_ARG, "step: negative iteration count");
   if (opts->alpha_log_len < 0 || (opts->alpha_log_len > 0 && !opts->alpha_log))
     return fail(NPFEM_ERR_INVALID_ARG, "step: bad alpha log");
+  if (!(opts->tol >= 0.0) || std::isinf(opts->tol))
+    return fail(NPFEM_ERR_INVALID_ARG, "step: tol must be finite and >= 0");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (b->mode == 1 && (iters == nullptr || opts->max_iters > 0)) {
     const int max_iters = iters ? opts->max_iters : opts->iters;
@@ -774,6 +780,8 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
     P.iters_default = opts->iters;
     P.residual_out = residual_out;
     P.status_out = status_out;
+    P.tol = opts->tol;
+    P.iters_done = opts->iters_done;
     P.alpha_log = opts->alpha_log;
     P.alpha_log_len = opts->alpha_log_len;
     P.queue_counter = L.counter;
@@ -807,6 +815,8 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: null array");
   if (opts->iters < 0 || opts->iters > kMaxAdjIters)
     return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: iteration count must be in [0, 16]");
+  if (opts->tol != 0.0)
+    return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: tol must be 0 (fixed iteration counts)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   for (TypeLaunch& L : b->launches) {
     if (L.adj_scratch) continue;
@@ -824,7 +834,7 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
   for (size_t li = 0; li < b->launches.size(); ++li) {
     const TypeLaunch& L = b->launches[li];
     const npfem_cell_type* t = b->types[L.type_index];
-    StepParams P;
+    StepParams P{};
     P.ncells_list = L.ncells;
     P.cell_list = L.cell_list;
     P.offsets = b->d_offsets;
@@ -1049,6 +1059,8 @@ npfem_status npfem_step_host(npfem_batch* b, void* x, void* v, const void* f_ext
                              void* stream) {
   if (!b || !opts || !x || !v || !f_ext) return fail(NPFEM_ERR_INVALID_ARG, "step_host: null argument");
   if (b->ncells == 0) return NPFEM_OK;
+  if (!(opts->tol >= 0.0) || std::isinf(opts->tol))
+    return fail(NPFEM_ERR_INVALID_ARG, "step_host: tol must be finite and >= 0");
   const size_t ssize = b->prec == NPFEM_FP64 ? sizeof(double) : sizeof(float);
   const size_t bytes = ssize * 3 * (size_t)b->n_total;
   if (!b->d_x) {
@@ -1065,11 +1077,14 @@ npfem_status npfem_step_host(npfem_batch* b, void* x, void* v, const void* f_ext
     b->d_res = static_cast<double*>(p);
     NPFEM_CUDA_TRY(b->mem.alloc(sizeof(int32_t) * b->ncells, &p));
     b->d_status = static_cast<int32_t*>(p);
+    NPFEM_CUDA_TRY(b->mem.alloc(sizeof(int32_t) * b->ncells, &p));
+    b->d_done = static_cast<int32_t*>(p);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   npfem_solver_opts o = *opts;
   o.alpha_log = nullptr;
   o.alpha_log_len = 0;
+  o.iters_done = opts->iters_done ? b->d_done : nullptr;
   int max_iters = 0;
   bool split = b->mode == 1 && (iters == nullptr || opts->max_iters > 0);
   if (split) {
@@ -1164,6 +1179,9 @@ npfem_status npfem_step_host(npfem_batch* b, void* x, void* v, const void* f_ext
   if (status_out)
     NPFEM_CUDA_TRY(
         cudaMemcpyAsync(status_out, b->d_status, sizeof(int32_t) * b->ncells, cudaMemcpyDeviceToHost, st));
+  if (opts->iters_done)
+    NPFEM_CUDA_TRY(cudaMemcpyAsync(opts->iters_done, b->d_done, sizeof(int32_t) * b->ncells,
+                                   cudaMemcpyDeviceToHost, st));
   NPFEM_CUDA_TRY(cudaStreamSynchronize(st));
   return NPFEM_OK;
 }

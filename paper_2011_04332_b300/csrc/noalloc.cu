@@ -10,6 +10,7 @@
 // the process exits).
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -85,6 +86,8 @@ extern "C" npfem_status npfem_step_noalloc(const npfem_cell_type* type, npfem_pr
     return npfem_internal_fail(NPFEM_ERR_INVALID_ARG, "step_noalloc: bad precision");
   if (ncells < 0 || opts->iters < 0 || opts->alpha_log_len < 0 || (opts->alpha_log_len > 0 && !opts->alpha_log))
     return npfem_internal_fail(NPFEM_ERR_INVALID_ARG, "step_noalloc: negative size or bad alpha log");
+  if (!(opts->tol >= 0.0) || std::isinf(opts->tol))
+    return npfem_internal_fail(NPFEM_ERR_INVALID_ARG, "step_noalloc: tol must be finite and >= 0");
   if (ncells > kStaticMaxCells)
     return npfem_internal_fail(NPFEM_ERR_UNSUPPORTED,
                                "step_noalloc: " + std::to_string(ncells) + " cells exceed the static limit of " +
@@ -125,7 +128,7 @@ extern "C" npfem_status npfem_step_noalloc(const npfem_cell_type* type, npfem_pr
   e = cudaMemsetAsync(counter, 0, sizeof(int), st);
   if (e != cudaSuccess) return npfem_internal_fail(NPFEM_ERR_CUDA, std::string("step_noalloc: ") + cudaGetErrorString(e));
   fill_contiguous_layout<<<(ncells + 256) / 256, 256, 0, st>>>(offsets, cells, ncells, H.n);
-  StepParams P;
+  StepParams P{};
   P.ncells_list = ncells;
   P.cell_list = cells;
   P.offsets = offsets;
@@ -134,6 +137,8 @@ extern "C" npfem_status npfem_step_noalloc(const npfem_cell_type* type, npfem_pr
   P.iters_default = opts->iters;
   P.residual_out = residual_out;
   P.status_out = status_out;
+  P.tol = opts->tol;
+  P.iters_done = opts->iters_done;
   P.alpha_log = opts->alpha_log;
   P.alpha_log_len = opts->alpha_log_len;
   P.queue_counter = counter;

@@ -83,7 +83,7 @@ __device__ __forceinline__ void two_loop_first(const CellWs<S>& w, CellState<S>*
 // K7: residual, x_{n+1} = anchor + X + U, v_{n+1} = U / dt, status.
 template <typename S>
 __device__ void split_finalize(const DevTypeView<S>& ty, const StepParams& P, const CellWs<S>& w, CellState<S>* st,
-                               const S* U, const S* G, int cell, S* x, S* v, int lane) {
+                               const S* U, const S* G, int cell, int done, S* x, S* v, int lane) {
   const int n = ty.n, len = 3 * n;
   const int64_t off = P.offsets[cell], Nt = P.n_total;
   NPFEM_PHASE_BEGIN(t_write)
@@ -126,6 +126,7 @@ __device__ void split_finalize(const DevTypeView<S>& ty, const StepParams& P, co
     if (bad) status |= 4;
     if (P.status_out) P.status_out[cell] = status;
     if (P.residual_out) P.residual_out[cell] = st->g0n > 0.0 ? gn / st->g0n : 0.0;
+    if (P.iters_done) P.iters_done[cell] = done;
     st->k = st->iters;
   }
   __syncwarp();
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(128, IterOccupancy<S>::min_blocks) npfem_k_beg
     }
     __syncwarp();
     if (iters == 0) {
-      split_finalize<S>(ty, P, w, st, w.U, w.G, cell, x, v, lane);
+      split_finalize<S>(ty, P, w, st, w.U, w.G, cell, 0, x, v, lane);
       continue;
     }
     if (lane == 0) P.act_out[atomicAdd(P.act_count_out, 1)] = item;
@@ -443,10 +444,12 @@ __global__ void __launch_bounds__(128, IterOccupancy<S>::min_blocks) npfem_k_ite
       }
       alpha *= 0.5;
     }
+    // converged-residual mode: the accepted trial ends the step when |g| < tol |g0|
+    const bool stop = P.tol > 0.0 && sqrt(vdot64<S>(GT, GT, len, lane)) < P.tol * st->g0n;
     NPFEM_PHASE_BEGIN(t_hist)
     S new_rho = (S)0;
     bool keep = false;
-    if (k < iters - 1) {
+    if (k < iters - 1 && !stop) {
       S* si = w.hs + (size_t)hhead * len;
       S* yi = w.hy + (size_t)hhead * len;
       Acc<S> asy, ass, ayy;
@@ -484,13 +487,13 @@ __global__ void __launch_bounds__(128, IterOccupancy<S>::min_blocks) npfem_k_ite
     }
     __syncwarp();
     // the accepted trial (UT, GT) is the new current iterate
-    if (k + 1 < iters) {
+    if (k + 1 < iters && !stop) {
       if (lane == 0) P.act_out[atomicAdd(P.act_count_out, 1)] = item;
       NPFEM_PHASE_BEGIN(t_loop1)
       two_loop_first<S>(w, st, GT, len, lane);
       NPFEM_PHASE_END(t_loop1, kPhTwoLoop, P, lane)
     } else {
-      split_finalize<S>(ty, P, w, st, UT, GT, cell, x, v, lane);
+      split_finalize<S>(ty, P, w, st, UT, GT, cell, k + 1, x, v, lane);
     }
   }
 }

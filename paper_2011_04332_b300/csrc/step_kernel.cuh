@@ -37,6 +37,8 @@ struct StepParams {
   int iters_default;
   double* residual_out;        // [ncells] or null
   int32_t* status_out;         // [ncells] or null
+  double tol;                  // > 0: stop a cell once |g| < tol |g0| (converged-residual mode)
+  int32_t* iters_done;         // [ncells] iterations run, or null
   double* alpha_log;           // [ncells][alpha_log_len] or null
   int alpha_log_len;
   int* queue_counter;          // work-queue head (zeroed before the launch)
@@ -656,6 +658,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
 #pragma unroll
   for (int i = 0; i < kHistory; ++i) rho[i] = aco[i] = 0;
 
+  int done = iters;
   for (int k = 0; k < iters; ++k) {
     NPFEM_PHASE_BEGIN(t_loop1)
     // K3 first loop: Q = G; newest -> oldest
@@ -721,9 +724,11 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
       }
       alpha *= 0.5;
     }
+    // converged-residual mode: the accepted trial ends the step when |g| < tol |g0|
+    const bool stop = P.tol > 0.0 && sqrt(vdot64<S>(GT, GT, len, lane)) < P.tol * g0n;
     NPFEM_PHASE_BEGIN(t_hist)
     // K6: history pair (s, y) = (UT - U, GT - G) into the ring slot hhead
-    if (k < iters - 1) {
+    if (k < iters - 1 && !stop) {
       S* si = w.hs + (size_t)hhead * len;
       S* yi = w.hy + (size_t)hhead * len;
       Acc<S> asy, ass, ayy;
@@ -761,6 +766,10 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
       if (lane == 0) tape->alpha[k] = alpha;
       __syncwarp();
     }
+    if (stop) {
+      done = k + 1;
+      break;
+    }
   }
 
   NPFEM_PHASE_BEGIN(t_write)
@@ -793,6 +802,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
     if (bad) status |= 4;
     if (P.status_out) P.status_out[cell] = status;
     if (P.residual_out) P.residual_out[cell] = g0n > 0.0 ? gn / g0n : 0.0;
+    if (P.iters_done) P.iters_done[cell] = done;
   }
   __syncwarp();
 }

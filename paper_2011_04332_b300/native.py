@@ -43,7 +43,7 @@ class _Material(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("iters", C.c_int32), ("alpha_log_len", C.c_int32), ("alpha_log", C.c_void_p),
-                ("max_iters", C.c_int32)]
+                ("max_iters", C.c_int32), ("tol", C.c_double), ("iters_done", C.c_void_p)]
 
 
 class _TypeInfo(C.Structure):
@@ -157,10 +157,12 @@ class CellType:
 
 
 def step_noalloc(cell_type: "CellType", precision: int, ncells: int, x, v, f, iters=None,
-                 iters_default: int = 5, residual=None, status=None, alpha_log=None, stream=None):
+                 iters_default: int = 5, residual=None, status=None, alpha_log=None, stream=None,
+                 tol: float = 0.0, iters_done=None):
     """npfem_step_noalloc: step `ncells` back-to-back cells of one type without any
     device allocation (static library workspace); device tensors as for Batch.step."""
-    opts = _Opts(int(iters_default), 0 if alpha_log is None else int(alpha_log.shape[-1]), _ptr(alpha_log))
+    opts = _Opts(int(iters_default), 0 if alpha_log is None else int(alpha_log.shape[-1]), _ptr(alpha_log),
+                 0, float(tol), _ptr(iters_done))
     if stream is None:
         import torch
         stream = torch.cuda.current_stream().cuda_stream
@@ -193,13 +195,15 @@ class Batch:
         self.offsets = offs
 
     def step(self, x, v, f, iters=None, iters_default: int = 5, residual=None, status=None,
-             alpha_log=None, stream=None, max_iters: int = 0):
+             alpha_log=None, stream=None, max_iters: int = 0, tol: float = 0.0, iters_done=None):
         """npfem_step on device tensors (torch); asynchronous on `stream` (torch stream or int).
-        With an iters tensor, pass max_iters (>= every count) to use the split kernels."""
+        With an iters tensor, pass max_iters (>= every count) to use the split kernels.
+        tol > 0: converged-residual mode (iteration counts become budgets); iters_done: an
+        int32 device tensor [ncells] that receives the iterations each cell ran."""
         if iters is not None and max_iters == 0:
             max_iters = self._iter_bound(iters)
         opts = _Opts(int(iters_default), 0 if alpha_log is None else int(alpha_log.shape[-1]),
-                     _ptr(alpha_log), int(max_iters))
+                     _ptr(alpha_log), int(max_iters), float(tol), _ptr(iters_done))
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -209,9 +213,10 @@ class Batch:
                                _ptr(residual), _ptr(status), C.c_void_p(stream)))
 
     def step_adjoint(self, x, v, f, gx_next, gv_next, gx, gv, gf, gw, iters=None, iters_default: int = 5,
-                     status=None, stream=None):
-        """npfem_step_adjoint on device tensors (FP64 batches): reverse mode of one step."""
-        opts = _Opts(int(iters_default), 0, None, 0)
+                     status=None, stream=None, tol: float = 0.0):
+        """npfem_step_adjoint on device tensors (FP64 batches): reverse mode of one step
+        (fixed iteration counts: the library rejects tol != 0)."""
+        opts = _Opts(int(iters_default), 0, None, 0, float(tol), None)
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -294,9 +299,11 @@ class Batch:
         return tuple(int(v) for v in out[:7]), bool(out[7])
 
     def step_host(self, x: np.ndarray, v: np.ndarray, f: np.ndarray, iters=None, iters_default: int = 5,
-                  residual=None, status=None, stream: int = 0):
-        """npfem_step_host on host arrays (copies in, steps, copies out; synchronous)."""
-        opts = _Opts(int(iters_default), 0, None, int(np.max(iters)) if iters is not None and len(iters) else 0)
+                  residual=None, status=None, stream: int = 0, tol: float = 0.0, iters_done=None):
+        """npfem_step_host on host arrays (copies in, steps, copies out; synchronous);
+        iters_done: a host int32 array [ncells] or None."""
+        opts = _Opts(int(iters_default), 0, None, int(np.max(iters)) if iters is not None and len(iters) else 0,
+                     float(tol), _ptr(iters_done))
         _check(_lib.npfem_step_host(self.handle, _ptr(x), _ptr(v), _ptr(f), _ptr(iters), C.byref(opts),
                                     _ptr(residual), _ptr(status), C.c_void_p(stream)))
 

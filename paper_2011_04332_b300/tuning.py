@@ -39,10 +39,10 @@ def _flush_l2(device) -> None:
     buf.zero_()
 
 
-def _time_step(batch: native.Batch, x, v, f, iters, reps: int, warm: bool = True) -> float:
+def _time_step(batch: native.Batch, x, v, f, iters, reps: int, warm: bool = True, tol: float = 0.0) -> float:
     xs, vs = x.clone(), v.clone()
     if warm:
-        batch.step(xs, vs, f, iters=iters)      # warm-up (first touch of the workspace)
+        batch.step(xs, vs, f, iters=iters, tol=tol)      # warm-up (first touch of the workspace)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     best = float("inf")
     for _ in range(reps):
@@ -50,7 +50,7 @@ def _time_step(batch: native.Batch, x, v, f, iters, reps: int, warm: bool = True
         vs.copy_(v)
         _flush_l2(x.device)
         e0.record()
-        batch.step(xs, vs, f, iters=iters)
+        batch.step(xs, vs, f, iters=iters, tol=tol)
         e1.record()
         torch.cuda.synchronize()
         best = min(best, e0.elapsed_time(e1))
@@ -135,7 +135,8 @@ def split_iter_candidates():
     return [(wpb, bps) for wpb in (2, 4) for bps in range(1, 17) if 8 <= wpb * bps <= 32 and (wpb * bps) % 4 == 0]
 
 
-def autotune_split(batch: native.Batch, x, v, f, iters=None, reps: int = 2, solve_only: bool = False) -> Dict[int, dict]:
+def autotune_split(batch: native.Batch, x, v, f, iters=None, reps: int = 2, solve_only: bool = False,
+                   tol: float = 0.0) -> Dict[int, dict]:
     """Coordinate search of the split-mode shapes per cell type (first the solve kernel's
     shape, then the iteration kernels'), then one group count for all types, timing
     whole steps (best of `reps`; the group counts and the final comparison best of 3).
@@ -143,8 +144,8 @@ def autotune_split(batch: native.Batch, x, v, f, iters=None, reps: int = 2, solv
     batch.set_mode(True)
     types = sorted({int(t) for t in batch.type_of_cell})
     start = {t: (list(batch.get_split_launch(t)[0]), batch.get_groups(t)) for t in types}
-    _time_step(batch, x, v, f, iters, 1)                     # first touch of the workspace
-    start_ms = _time_step(batch, x, v, f, iters, 3, warm=False)
+    _time_step(batch, x, v, f, iters, 1, tol=tol)                     # first touch of the workspace
+    start_ms = _time_step(batch, x, v, f, iters, 3, warm=False, tol=tol)
     best_ms = start_ms
     out = {}
     for t in types:
@@ -158,7 +159,7 @@ def autotune_split(batch: native.Batch, x, v, f, iters=None, reps: int = 2, solv
                 batch.set_split_launch(t, shape)
             except native.NpfemError:
                 continue
-            ms = _time_step(batch, x, v, f, iters, reps, warm=False)
+            ms = _time_step(batch, x, v, f, iters, reps, warm=False, tol=tol)
             if ms < best_ms:
                 best_ms, cur = ms, shape
         batch.set_split_launch(t, cur)
@@ -168,7 +169,7 @@ def autotune_split(batch: native.Batch, x, v, f, iters=None, reps: int = 2, solv
                 if shape == cur:
                     continue
                 batch.set_split_launch(t, shape)
-                ms = _time_step(batch, x, v, f, iters, reps, warm=False)
+                ms = _time_step(batch, x, v, f, iters, reps, warm=False, tol=tol)
                 if ms < best_ms:
                     best_ms, cur = ms, shape
             batch.set_split_launch(t, cur)
@@ -178,7 +179,7 @@ def autotune_split(batch: native.Batch, x, v, f, iters=None, reps: int = 2, solv
     for g in (1, 2, 3, 4):
         for t in types:
             batch.set_groups(t, g)
-        ms = _time_step(batch, x, v, f, iters, 3, warm=False)
+        ms = _time_step(batch, x, v, f, iters, 3, warm=False, tol=tol)
         if best_ms is None or ms < best_ms:
             best_g, best_ms = g, ms
     for t in types:

@@ -104,3 +104,31 @@ def test_last_error_string_is_set(lib):
         native.analyze_cell_type(I.icosahedron().verts, I.icosahedron().tris[:-1], (1, 1, 1, 1, 1), 0.1)
     except native.NpfemError as e:
         assert "open edge" in str(e) or "closed" in str(e)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The binding's ctypes structures have the size and field offsets a C compiler
+    gives the header's structs (catches a field added on one side only)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"npfem_mesh": native._Mesh, "npfem_material": native._Material,
+               "npfem_solver_opts": native._Opts, "npfem_type_info": native._TypeInfo}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "npfem.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {(a, b): int(c) for a, b, c in (l.split() for l in out if l)}
+    for cname, py in structs.items():
+        assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

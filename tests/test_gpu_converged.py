@@ -1,0 +1,212 @@
+"""GPU parity of the converged-residual mode (iteration counts as budgets, a cell stops
+after the first iteration with |g| < tol |g0|) against the oracle's same rule.
+
+Where the FP64 gradient-norm ratio of some iterate lies within a hair of tol, the two
+sides may legitimately stop one iteration apart (their norms differ in the last bits);
+such cells are "ambiguous": their count may differ by one, and each side's result must
+still be valid (residual below tol when it stopped early).  Every other cell must stop
+at the oracle's count and match it within the fixed-count bars.
+"""
+import numpy as np
+import pytest
+
+from oracle import npfem_oracle as O
+from paper_2011_04332_b300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FP64_BAR = 1e-10
+FP32_BAR = 1e-5
+# relative closeness of |g_k|/|g_0| to tol below which the stopping decision may differ
+FP64_MARGIN = 1e-8
+FP32_MARGIN = 5e-2
+
+
+def _native():
+    from paper_2011_04332_b300 import native
+    return native
+
+
+def _setup(b, prec):
+    nat = _native()
+    types = [nat.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
+    batch = nat.Batch(types, b.type_of_cell, prec)
+    return types, batch
+
+
+def _inputs(b, prec):
+    nat = _native()
+    x, v, f = b.x.copy(), b.v.copy(), b.f.copy()
+    if prec == nat.FP32FORM:
+        x, v, f = (a.astype(np.float32).astype(np.float64) for a in (x, v, f))
+    return x, v, f
+
+
+def _gpu_step(batch, prec, x, v, f, iters, tol, alpha_len=32):
+    nat = _native()
+    dev = torch.device("cuda:0")
+    dt = torch.float64 if prec == nat.FP64 else torch.float32
+    X = torch.tensor(x, dtype=dt, device=dev)
+    V = torch.tensor(v, dtype=dt, device=dev)
+    F = torch.tensor(f, dtype=dt, device=dev)
+    nc = batch.ncells
+    it = torch.tensor(np.asarray(iters, np.int32), device=dev)
+    res = torch.full((nc,), -1.0, dtype=torch.float64, device=dev)
+    st = torch.full((nc,), -1, dtype=torch.int32, device=dev)
+    dn = torch.full((nc,), -1, dtype=torch.int32, device=dev)
+    al = torch.zeros((nc, alpha_len), dtype=torch.float64, device=dev)
+    batch.step(X, V, F, iters=it, residual=res, status=st, alpha_log=al, tol=tol, iters_done=dn)
+    torch.cuda.synchronize()
+    return {"x": X.double().cpu().numpy(), "v": V.double().cpu().numpy(), "residual": res.cpu().numpy(),
+            "status": st.cpu().numpy(), "iters_done": dn.cpu().numpy(), "alpha": al.cpu().numpy()}
+
+
+def _radius(xr):
+    return np.max(np.linalg.norm(xr - xr.mean(axis=1, keepdims=True), axis=0))
+
+
+def _ambiguous(gnorms, tol, margin):
+    g = np.asarray(gnorms)
+    if g[0] == 0:
+        return False
+    return bool(np.any(np.abs(g[1:] / g[0] / tol - 1.0) < margin))
+
+
+def _check_against_oracle(b, prec, got, ref, iters, tol, cells):
+    nat = _native()
+    bar = FP64_BAR if prec == nat.FP64 else FP32_BAR
+    margin = FP64_MARGIN if prec == nat.FP64 else FP32_MARGIN
+    matched = 0
+    for c in cells:
+        k_gpu, k_ref = int(got["iters_done"][c]), int(ref["iters_done"][c])
+        assert 0 <= k_gpu <= int(iters[c])
+        if k_gpu < int(iters[c]):
+            assert got["residual"][c] < tol, (c, got["residual"][c])
+        if k_gpu != k_ref:
+            assert _ambiguous(ref["grad_norms"][c], tol, margin), (c, k_gpu, k_ref, ref["grad_norms"][c])
+            assert abs(k_gpu - k_ref) == 1
+            continue
+        matched += 1
+        s = b.cell_slice(c)
+        rad = _radius(ref["x"][:, s])
+        assert np.max(np.abs(got["x"][:, s] - ref["x"][:, s])) / rad <= bar, c
+        assert np.max(np.abs(got["v"][:, s] - ref["v"][:, s])) * b.dt / rad <= bar, c
+        assert got["status"][c] == ref["status"][c]
+        if prec == nat.FP64:
+            n = min(k_gpu, got["alpha"].shape[1])
+            assert np.array_equal(got["alpha"][c, :n], np.array(ref["alphas"][c][:n]))
+            assert got["residual"][c] == pytest.approx(ref["residual"][c], rel=1e-4, abs=1e-8)
+    return matched
+
+
+CASES = {
+    # three small types (42-vertex RBC and platelet, 162-vertex RBC): stops at 2..16
+    "mixed": lambda: I.small_mixed_batch(),
+    # 24 placed 642-vertex RBCs, Gaussian + shear forces: stops at 5..13
+    "homog": lambda: I.homogeneous_rbc_batch(ncells=24, seed=1001, velocity_sigma=0.02),
+}
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+@pytest.mark.parametrize("mode", ["split", "fused"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("tol", [1e-2, 1e-3])
+def test_converged_residual_parity(case, mode, prec, tol):
+    """Iteration counts, states, statuses, step lengths and residuals against the oracle
+    run with the same budget (16) and tolerance."""
+    nat = _native()
+    p = nat.FP64 if prec == "fp64" else nat.FP32FORM
+    b = CASES[case]()
+    _, batch = _setup(b, p)
+    batch.set_mode(mode == "split")
+    x, v, f = _inputs(b, p)
+    iters = np.full(b.ncells, 16, np.int32)
+    got = _gpu_step(batch, p, x, v, f, iters, tol)
+    ots = [O.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
+    ref = O.batch_step(ots, b.type_of_cell, b.offsets, x, v, f, iters, tol=tol)
+    matched = _check_against_oracle(b, p, got, ref, iters, tol, range(b.ncells))
+    assert matched >= (b.ncells if p == nat.FP64 else (3 * b.ncells) // 4)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_converged_equals_fixed_count_full_size(prec):
+    """The 4096-cell homogeneous workload, split mode in its default launch
+    configuration: a converged-residual step equals, bit for bit, the fixed-count step
+    with each cell's count set to the iterations it ran; 8 sampled cells match the
+    oracle's converged-residual step."""
+    nat = _native()
+    p = nat.FP64 if prec == "fp64" else nat.FP32FORM
+    b = I.homogeneous_rbc_batch(ncells=4096, seed=1001)
+    _, batch = _setup(b, p)
+    x, v, f = _inputs(b, p)
+    budget = np.full(b.ncells, 16, np.int32)
+    tol = 1e-3
+    got = _gpu_step(batch, p, x, v, f, budget, tol, alpha_len=16)
+    done = got["iters_done"]
+    assert np.all((done >= 1) & (done <= 16))
+    assert np.all(got["residual"][done < 16] < tol)
+    fixed = _gpu_step(batch, p, x, v, f, done, 0.0, alpha_len=16)
+    for k in ("x", "v", "residual", "status", "alpha"):
+        assert np.array_equal(got[k], fixed[k]), k
+    assert np.array_equal(fixed["iters_done"], done)
+    sample = [int(c) for c in np.random.default_rng(7).choice(b.ncells, 8, replace=False)]
+    ots = [O.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
+    ref = O.batch_step(ots, b.type_of_cell, b.offsets, x, v, f, budget, cells=sample, tol=tol)
+    matched = _check_against_oracle(b, p, got, ref, budget, tol, sample)
+    assert matched >= (len(sample) if p == nat.FP64 else 6)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_converged_host_buffers_match_device_step(prec):
+    """npfem_step_host (chunked pipeline) in the converged-residual mode returns the
+    device step's states, residuals and iteration counts."""
+    nat = _native()
+    p = nat.FP64 if prec == "fp64" else nat.FP32FORM
+    b = I.small_mixed_batch()
+    _, batch = _setup(b, p)
+    x, v, f = _inputs(b, p)
+    budget = np.full(b.ncells, 16, np.int32)
+    got = _gpu_step(batch, p, x, v, f, budget, 1e-3)
+    npdt = np.float64 if p == nat.FP64 else np.float32
+    hx, hv, hf = (np.array(a, dtype=npdt, copy=True) for a in (x, v, f))
+    res = np.zeros(b.ncells)
+    st = np.zeros(b.ncells, np.int32)
+    dn = np.full(b.ncells, -1, np.int32)
+    batch.step_host(hx, hv, hf, iters=budget, residual=res, status=st, tol=1e-3, iters_done=dn)
+    assert np.array_equal(dn, got["iters_done"])
+    assert np.array_equal(hx.astype(np.float64), got["x"])
+    assert np.array_equal(hv.astype(np.float64), got["v"])
+    assert np.array_equal(res, got["residual"])
+    assert np.array_equal(st, got["status"])
+
+
+def test_converged_zero_gradient_cell_runs_budget():
+    """A cell at rest with no force has |g0| = 0 and runs its whole budget unchanged."""
+    nat = _native()
+    b = I.single_rbc()
+    _, batch = _setup(b, nat.FP64)
+    x = b.types[0].mesh.verts.T.copy()
+    z = np.zeros_like(x)
+    got = _gpu_step(batch, nat.FP64, x, z, z, np.array([6], np.int32), 1e-3)
+    assert got["iters_done"][0] == 6
+    assert np.max(np.abs(got["x"] - x)) <= 1e-14 * np.max(np.abs(x))
+
+
+def test_converged_invalid_tolerance_rejected():
+    """Negative, NaN and infinite tolerances are argument errors; the adjoint, which
+    differentiates fixed counts, rejects any tol != 0."""
+    nat = _native()
+    b = I.single_rbc()
+    _, batch = _setup(b, nat.FP64)
+    dev = torch.device("cuda:0")
+    X = torch.tensor(b.x, device=dev)
+    V = torch.tensor(b.v, device=dev)
+    F = torch.tensor(b.f, device=dev)
+    for bad in (-1e-3, float("nan"), float("inf")):
+        with pytest.raises(_native().NpfemError, match="tol"):
+            batch.step(X, V, F, iters_default=4, tol=bad)
+    g = [torch.zeros_like(X) for _ in range(5)]
+    gw = torch.zeros((1, 4), dtype=torch.float64, device=dev)
+    with pytest.raises(_native().NpfemError, match="tol"):
+        batch.step_adjoint(X, V, F, g[0], g[1], g[2], g[3], g[4], gw, iters_default=4, tol=1e-3)
