@@ -1,11 +1,18 @@
 """GPU parity of the converged-residual mode (iteration counts as budgets, a cell stops
 after the first iteration with |g| < tol |g0|) against the oracle's same rule.
 
-Where the FP64 gradient-norm ratio of some iterate lies within a hair of tol, the two
-sides may legitimately stop one iteration apart (their norms differ in the last bits);
-such cells are "ambiguous": their count may differ by one, and each side's result must
-still be valid (residual below tol when it stopped early).  Every other cell must stop
-at the oracle's count and match it within the fixed-count bars.
+FP64 form: where the gradient-norm ratio of some iterate lies within a hair of tol, the
+two sides may legitimately stop one iteration apart (their norms differ in the last
+bits); such cells are "ambiguous": their count may differ by one, and each side's result
+must still be valid (residual below tol when it stopped early).  Every other cell must
+stop at the oracle's count and match it within the fixed-count bars.
+
+FP32 form: the kernel evaluates the gradient in FP32, whose norm carries a noise floor
+that is not small against tol |g0| at tol = 1e-3, so the count is a decision taken in
+the kernel's precision.  Given the count the state is unique: each cell must match the
+oracle's fixed-count step of the same count within the FP32 bar, and the decision must
+be valid in FP64 terms within a factor of two (the oracle's ratio at the stopping
+iterate below 2 tol, every earlier ratio above tol / 2).
 """
 import numpy as np
 import pytest
@@ -18,9 +25,8 @@ pytestmark = pytest.mark.gpu
 
 FP64_BAR = 1e-10
 FP32_BAR = 1e-5
-# relative closeness of |g_k|/|g_0| to tol below which the stopping decision may differ
+# relative closeness of |g_k|/|g_0| to tol below which the FP64 stopping decision may differ
 FP64_MARGIN = 1e-8
-FP32_MARGIN = 5e-2
 
 
 def _native():
@@ -73,10 +79,30 @@ def _ambiguous(gnorms, tol, margin):
     return bool(np.any(np.abs(g[1:] / g[0] / tol - 1.0) < margin))
 
 
-def _check_against_oracle(b, prec, got, ref, iters, tol, cells):
-    nat = _native()
-    bar = FP64_BAR if prec == nat.FP64 else FP32_BAR
-    margin = FP64_MARGIN if prec == nat.FP64 else FP32_MARGIN
+def _check_fp32_against_oracle(b, got, ots, x, v, f, budget, tol, cells):
+    """FP32 form: state vs the oracle's fixed-count step at the GPU's count; the stop
+    decision valid against the oracle's FP64 ratios within a factor of two."""
+    done = got["iters_done"]
+    ref = O.batch_step(ots, b.type_of_cell, b.offsets, x, v, f, done, cells=list(cells))
+    for c in cells:
+        k = int(done[c])
+        assert 0 <= k <= int(budget[c])
+        g = np.asarray(ref["grad_norms"][c])
+        r = g / g[0] if g[0] > 0 else g
+        if k < int(budget[c]):
+            assert got["residual"][c] < tol, (c, got["residual"][c])
+            assert r[k] < 2 * tol, (c, k, r)
+        assert np.all(r[1:k] > tol / 2), (c, k, r)
+        s = b.cell_slice(c)
+        rad = _radius(ref["x"][:, s])
+        assert np.max(np.abs(got["x"][:, s] - ref["x"][:, s])) / rad <= FP32_BAR, c
+        assert np.max(np.abs(got["v"][:, s] - ref["v"][:, s])) * b.dt / rad <= FP32_BAR, c
+        assert got["status"][c] == ref["status"][c]
+
+
+def _check_fp64_against_oracle(b, got, ref, iters, tol, cells):
+    """FP64 form: the oracle's count (up to ambiguous cells), state, status, step lengths
+    and residual.  Returns the number of cells whose counts agree."""
     matched = 0
     for c in cells:
         k_gpu, k_ref = int(got["iters_done"][c]), int(ref["iters_done"][c])
@@ -84,19 +110,18 @@ def _check_against_oracle(b, prec, got, ref, iters, tol, cells):
         if k_gpu < int(iters[c]):
             assert got["residual"][c] < tol, (c, got["residual"][c])
         if k_gpu != k_ref:
-            assert _ambiguous(ref["grad_norms"][c], tol, margin), (c, k_gpu, k_ref, ref["grad_norms"][c])
+            assert _ambiguous(ref["grad_norms"][c], tol, FP64_MARGIN), (c, k_gpu, k_ref, ref["grad_norms"][c])
             assert abs(k_gpu - k_ref) == 1
             continue
         matched += 1
         s = b.cell_slice(c)
         rad = _radius(ref["x"][:, s])
-        assert np.max(np.abs(got["x"][:, s] - ref["x"][:, s])) / rad <= bar, c
-        assert np.max(np.abs(got["v"][:, s] - ref["v"][:, s])) * b.dt / rad <= bar, c
+        assert np.max(np.abs(got["x"][:, s] - ref["x"][:, s])) / rad <= FP64_BAR, c
+        assert np.max(np.abs(got["v"][:, s] - ref["v"][:, s])) * b.dt / rad <= FP64_BAR, c
         assert got["status"][c] == ref["status"][c]
-        if prec == nat.FP64:
-            n = min(k_gpu, got["alpha"].shape[1])
-            assert np.array_equal(got["alpha"][c, :n], np.array(ref["alphas"][c][:n]))
-            assert got["residual"][c] == pytest.approx(ref["residual"][c], rel=1e-4, abs=1e-8)
+        n = min(k_gpu, got["alpha"].shape[1])
+        assert np.array_equal(got["alpha"][c, :n], np.array(ref["alphas"][c][:n]))
+        assert got["residual"][c] == pytest.approx(ref["residual"][c], rel=1e-4, abs=1e-8)
     return matched
 
 
@@ -124,9 +149,11 @@ def test_converged_residual_parity(case, mode, prec, tol):
     iters = np.full(b.ncells, 16, np.int32)
     got = _gpu_step(batch, p, x, v, f, iters, tol)
     ots = [O.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
-    ref = O.batch_step(ots, b.type_of_cell, b.offsets, x, v, f, iters, tol=tol)
-    matched = _check_against_oracle(b, p, got, ref, iters, tol, range(b.ncells))
-    assert matched >= (b.ncells if p == nat.FP64 else (3 * b.ncells) // 4)
+    if p == nat.FP64:
+        ref = O.batch_step(ots, b.type_of_cell, b.offsets, x, v, f, iters, tol=tol)
+        _check_fp64_against_oracle(b, got, ref, iters, tol, range(b.ncells))
+    else:
+        _check_fp32_against_oracle(b, got, ots, x, v, f, iters, tol, range(b.ncells))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -152,9 +179,11 @@ def test_converged_equals_fixed_count_full_size(prec):
     assert np.array_equal(fixed["iters_done"], done)
     sample = [int(c) for c in np.random.default_rng(7).choice(b.ncells, 8, replace=False)]
     ots = [O.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
-    ref = O.batch_step(ots, b.type_of_cell, b.offsets, x, v, f, budget, cells=sample, tol=tol)
-    matched = _check_against_oracle(b, p, got, ref, budget, tol, sample)
-    assert matched >= (len(sample) if p == nat.FP64 else 6)
+    if p == nat.FP64:
+        ref = O.batch_step(ots, b.type_of_cell, b.offsets, x, v, f, budget, cells=sample, tol=tol)
+        _check_fp64_against_oracle(b, got, ref, budget, tol, sample)
+    else:
+        _check_fp32_against_oracle(b, got, ots, x, v, f, budget, tol, sample)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
