@@ -10,8 +10,13 @@
 // One step launches k_begin once and (k_solve, k_iter) max_iters times per cell type.
 // Between kernels each cell's state lives in its own workspace slot (a CellState header
 // followed by the CellWs vectors and a workspace copy of the solve vector, used only by
-// the rare non-descent reset inside k_iter).  A warp advances one cell per queue item;
-// cells whose iteration budget is exhausted are skipped.
+// the rare non-descent reset inside k_iter).  k_iter and the CTA-cooperative solve walk
+// the group's cells in batch order and skip those whose step has ended (budget used, or
+// tolerance met in the converged-residual mode): measured faster than taking them from
+// the compacted list of the cells still iterating, whose order is that in which the
+// previous kernel finished them.  The one-warp solve, which packs several cells per
+// warp, takes its cells from that list (written by k_begin for iteration 0 and by
+// k_iter(i - 1) for iteration i).
 #pragma once
 #include "step_kernel.cuh"
 
@@ -320,7 +325,8 @@ __device__ __forceinline__ void cta_sweep(int nlev, const int32_t* __restrict__ 
   __syncthreads();
 }
 
-// Q <- A^-1 Q for every cell still iterating, one cell per CTA of W warps at a time:
+// Q <- A^-1 Q for every cell still iterating (cells in batch order, ended ones
+// skipped), one cell per CTA of W warps at a time:
 // for cells whose FP64 solve vector ([n+1][3], 24(n+1) bytes) is too large to keep
 // one per warp in shared memory.  The CTA's warps share the vector and sweep the
 // W-warp level packing of the factor together.
@@ -338,15 +344,18 @@ __global__ void __launch_bounds__(32 * W) npfem_k_solve_cta(DevTypeView<S> ty, S
   __shared__ int s_item;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = ty.n;
-  const int total = *P.act_count_in;
   const uint32_t zs = (uint32_t)__cvta_generic_to_shared(smem_z);
   for (;;) {
     if (tid == 0) s_item = atomicAdd(P.queue_counter, 1);
     __syncthreads();
     const int item = s_item;
     __syncthreads();
-    if (item >= total) break;
-    char* base = P.scratch + (size_t)P.act_in[item] * P.slot_bytes;
+    if (item >= P.ncells_list) break;
+    char* base = P.scratch + (size_t)item * P.slot_bytes;
+    {
+      const CellState<S>* cs = reinterpret_cast<const CellState<S>*>(base);
+      if (cs->k >= cs->iters) continue;  // same header for the whole CTA: a uniform branch
+    }
     CellWs<S> w = split_ws<S>(base, ty);
     NPFEM_PHASE_BEGIN(t_solve)
     for (int r = tid; r < n; r += 32 * W) {

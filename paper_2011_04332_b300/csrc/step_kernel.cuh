@@ -47,7 +47,7 @@ struct StepParams {
   int z_in_smem;               // 1: FP64 solve vector in dynamic shared memory
   int solve_per_coord;         // 1: sweep x, y, z one after another with a one-coordinate vector
   int solve_cells;             // split mode: cells a warp of the solve kernel sweeps together (1..4)
-  const int* act_in;           // split mode: list of cells iterating at this iteration (k_solve)
+  const int* act_in;           // split mode: list of cells iterating at this iteration (one-warp k_solve)
   const int* act_count_in;     //   and its length
   int* act_out;                // split mode: list of cells iterating at the next iteration
   int* act_count_out;          //   (appended by k_begin / k_iter) and its length
