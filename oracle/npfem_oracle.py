@@ -18,6 +18,11 @@ What it computes, and where each piece comes from
   parameters (Setting up new materials section).
 * Per step the solid solver receives external forces and returns positions and
   velocities (Implementation and architecture).
+* Collisions (optional): contact detection at the start of a step and a penalty
+  per contact in the step objective; the paper names collision detection and
+  collision forces (Performance figure, "Other"), a collision weight (Collision at
+  an obstacle section) and a fluid-free cell-packing application (Cell Packing
+  section), without formulas: the reading is stated at `detect_contacts`.
 
 The paper prints no formulas for the energies or the iteration; the readings
 used here (strain = distance of the triangle deformation gradient to the
@@ -239,10 +244,11 @@ class EnergyParts:
     A: float
     V: float
     degenerate: int
+    contact: float = 0.0
 
     @property
     def total(self) -> float:
-        return self.inertia + self.strain + self.bend + self.area + self.volume
+        return self.inertia + self.strain + self.bend + self.area + self.volume + self.contact
 
 
 def internal_energy_and_gradient(rs: RestState, x: np.ndarray, w_scale=None):
@@ -301,15 +307,131 @@ def internal_energy_and_gradient(rs: RestState, x: np.ndarray, w_scale=None):
     return parts, g
 
 
-def objective(rs: RestState, x: np.ndarray, y: np.ndarray, w_scale=None):
+def objective(rs: RestState, x: np.ndarray, y: np.ndarray, w_scale=None, contact=None):
     """Implicit-Euler variational objective of one step (Eq. (2) discretised):
-    f(x) = (x-y)^T M (x-y) / (2 dt^2) + E_int(x), and its gradient."""
+    f(x) = (x-y)^T M (x-y) / (2 dt^2) + E_int(x) [+ E_contact(x)], and its gradient.
+    contact: (idx, nrm, crel, delta, weight) as in contact_energy_and_gradient."""
     parts, g = internal_energy_and_gradient(rs, x, w_scale)
     dx = x - y
     m = rs.mass
     parts.inertia = np.sum(m[:, None] * dx * dx) / (2.0 * rs.dt ** 2)
     g = g + m[:, None] * dx / rs.dt ** 2
+    if contact is not None:
+        ec, gc = contact_energy_and_gradient(x, *contact)
+        parts.contact = ec
+        g = g + gc
     return parts, g
+
+
+# ---------------------------------------------------------------- contacts
+# Collision reading (the paper names collision detection, collision forces and a
+# collision weight, and a fluid-free cell-packing application in which npFEM resolves
+# the overlaps of randomly placed cells: Performance figure, Cell Packing and
+# Collision at an obstacle sections; it gives no formula).  At the start of a step,
+# every vertex i of cell a is matched with the nearest vertex j of each other cell b
+# within a search radius; the two nearest such cells are kept.  Each kept match is a
+# plane through x_j with normal n_j, the unit area-weighted outward vertex normal of
+# b at j, both from the step's input state and fixed during the step.  The step
+# objective gains, per kept match, the one-sided quadratic penalty
+#     E = (w/2) max(0, delta - (n_j . x_i - n_j . x_j))^2,
+# delta a contact thickness, w the collision weight: a ShapeOp-style energy outside
+# the prefactored matrix (like the area and volume terms), so cells stay independent
+# within a step.
+CONTACT_SLOTS = 2
+
+
+def vertex_normals(x: np.ndarray, tris: np.ndarray) -> np.ndarray:
+    """Unit area-weighted outward vertex normals [n,3]: the sum over incident
+    triangles, in triangle order, of (x1 - x0) x (x2 - x0), normalised."""
+    N = np.cross(x[tris[:, 1]] - x[tris[:, 0]], x[tris[:, 2]] - x[tris[:, 0]])
+    acc = np.zeros_like(x)
+    np.add.at(acc, tris.reshape(-1), np.repeat(N, 3, axis=0))
+    return acc / _norm_rows(acc)[:, None]
+
+
+def _sq_dist(x: np.ndarray, i: int) -> np.ndarray:
+    """|x_i - x_j|^2 for every column j of x [3,N], evaluated as (dx*dx + dy*dy) + dz*dz."""
+    dx = x[0, i] - x[0]
+    dy = x[1, i] - x[1]
+    dz = x[2, i] - x[2]
+    return (dx * dx + dy * dy) + dz * dz
+
+
+def vertex_contacts(x: np.ndarray, offsets, cell_of_vertex: np.ndarray, i: int, radius: float):
+    """The matches of global vertex i: a list of (d2, b, j), nearest cell first, at
+    most CONTACT_SLOTS.  Per other cell b the vertex j of b nearest to x_i (equal
+    distances: the smaller j); cells with that distance below `radius` compete, and
+    equal distances go to the smaller b."""
+    a = int(cell_of_vertex[i])
+    d2 = _sq_dist(x, i)
+    r2 = radius * radius
+    found = []
+    for b in np.unique(cell_of_vertex[d2 < r2]):
+        b = int(b)
+        if b == a:
+            continue
+        s = slice(int(offsets[b]), int(offsets[b + 1]))
+        k = int(np.argmin(d2[s]))           # first occurrence: the smaller j on ties
+        found.append((float(d2[s][k]), b, int(offsets[b]) + k))
+    found.sort(key=lambda t: (t[0], t[1]))
+    return found[:CONTACT_SLOTS]
+
+
+def detect_contacts(types: List["CellType"], type_of_cell, offsets, x: np.ndarray, radius: float,
+                    vertices=None) -> Dict[str, np.ndarray]:
+    """Contacts of the step's input state x [3,N] (brute force over all vertices):
+    per vertex the count (0..2), the matched vertex j and cell b per slot, and the
+    plane of each slot: unit normal n_j [3] and offset c = n_j . x_j (absolute
+    coordinates).  Unused slots hold j = b = -1 and zeros.  `vertices` restricts the
+    search to those global vertices (the others report no contact)."""
+    N = x.shape[1]
+    ncells = len(type_of_cell)
+    cell_of_vertex = np.repeat(np.arange(ncells), np.diff(np.asarray(offsets)))
+    cnt = np.zeros(N, dtype=np.int32)
+    jj = np.full((N, CONTACT_SLOTS), -1, dtype=np.int64)
+    bb = np.full((N, CONTACT_SLOTS), -1, dtype=np.int64)
+    nrm = np.zeros((N, CONTACT_SLOTS, 3))
+    cc = np.zeros((N, CONTACT_SLOTS))
+    normals = {}
+    for i in (range(N) if vertices is None else vertices):
+        for k, (_, b, j) in enumerate(vertex_contacts(x, offsets, cell_of_vertex, i, radius)):
+            if b not in normals:
+                s = slice(int(offsets[b]), int(offsets[b + 1]))
+                normals[b] = vertex_normals(x[:, s].T, types[int(type_of_cell[b])].rest.tris)
+            nj = normals[b][j - int(offsets[b])]
+            cnt[i] = k + 1
+            jj[i, k], bb[i, k] = j, b
+            nrm[i, k] = nj
+            cc[i, k] = float(np.sum(nj * x[:, j]))
+    return {"count": cnt, "vertex": jj, "cell": bb, "normal": nrm, "offset": cc}
+
+
+def cell_contacts(contacts: Dict[str, np.ndarray], o0: int, o1: int):
+    """The matches of the vertices [o0, o1) as flat arrays (local vertex index,
+    normal [m,3], absolute plane offset [m]), in vertex order then slot order."""
+    idx, nrm, off = [], [], []
+    for i in range(o0, o1):
+        for k in range(int(contacts["count"][i])):
+            idx.append(i - o0)
+            nrm.append(contacts["normal"][i, k])
+            off.append(contacts["offset"][i, k])
+    return (np.array(idx, dtype=np.int64), np.array(nrm).reshape(-1, 3), np.array(off))
+
+
+def contact_energy_and_gradient(x: np.ndarray, idx: np.ndarray, nrm: np.ndarray, crel: np.ndarray,
+                                delta: float, weight: float):
+    """E = sum_k (w/2) max(0, delta - (n_k . x_idx[k] - crel_k))^2 and its gradient
+    [n,3] (-w max(0, .) n_k on vertex idx[k]); crel is the plane offset in the
+    coordinates of x."""
+    g = np.zeros_like(x)
+    if len(idx) == 0:
+        return 0.0, g
+    gap = np.sum(nrm * x[idx], axis=1) - crel
+    pen = delta - gap
+    pen = np.where(np.real(pen) > 0.0, pen, 0.0)
+    E = 0.5 * weight * np.sum(pen * pen)
+    np.add.at(g, idx, -weight * pen[:, None] * nrm)
+    return E, g
 
 
 # ---------------------------------------------------------------- global matrix
@@ -393,7 +515,7 @@ def two_loop(g: np.ndarray, S: List[np.ndarray], Y: List[np.ndarray],
 
 
 def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
-         f_ext: np.ndarray, iters: int, w_scale=None, tol: float = 0.0) -> StepResult:
+         f_ext: np.ndarray, iters: int, w_scale=None, tol: float = 0.0, contact=None) -> StepResult:
     """One implicit time step of one cell by quasi-Newton projective dynamics.
 
     y = x_n + dt v_n + dt^2 M^-1 f_ext;  x^(0) = y;  history cleared.
@@ -406,13 +528,18 @@ def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
     |g| < tol |g^(0)| (a cell with g^(0) = 0 runs all `iters`).
     v_{n+1} = (x^(k) - x_n) / dt for the last iterate k.  Works relative to the
     centroid of x_n (the objective is translation invariant), adding it back at the end.
+    contact: (idx, nrm, c, delta, weight) with absolute plane offsets c (see
+    detect_contacts / cell_contacts): the contact penalty joins the objective.
     """
     dt = rs.dt
     ctr = np.real(x_n).mean(axis=0)
     xn = x_n - ctr
     y = xn + dt * v_n + dt * dt * f_ext / rs.mass[:, None]
     x = y.copy()
-    parts, g = objective(rs, x, y, w_scale)
+    if contact is not None:
+        idx, nrm, c_abs, delta, weight = contact
+        contact = (idx, nrm, c_abs - nrm @ ctr, delta, weight)
+    parts, g = objective(rs, x, y, w_scale, contact)
     fx = parts.total
     g0n = float(np.sqrt(np.sum(np.real(g) ** 2)))
     S: List[np.ndarray] = []
@@ -431,7 +558,7 @@ def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
         alpha = 1.0
         for h in range(MAX_HALVINGS + 1):
             xt = x + alpha * d
-            pt, gt = objective(rs, xt, y, w_scale)
+            pt, gt = objective(rs, xt, y, w_scale, contact)
             trials += 1
             ft = pt.total
             armijo = np.real(ft) <= np.real(fx + ARMIJO_C1 * alpha * gd)
@@ -482,12 +609,19 @@ class CellType:
 
 
 def batch_step(types: List[CellType], type_of_cell, offsets, x, v, f, iters,
-               cells: Optional[List[int]] = None, tol: float = 0.0) -> Dict[str, np.ndarray]:
+               cells: Optional[List[int]] = None, tol: float = 0.0,
+               collisions: Optional[tuple] = None) -> Dict[str, np.ndarray]:
     """One step for a batch in SoA [3, N_total] layout; returns new x, v (for the
     selected cells only; other columns are copied through) plus per-cell residuals,
     statuses, accepted step lengths, gradient norms and iterations done (tol: as in
-    `step`)."""
+    `step`).  collisions = (radius, delta, weight): contacts detected on x (for the
+    selected cells' vertices) join each cell's objective; they are returned too."""
     xo, vo = x.copy(), v.copy()
+    contacts = None
+    if collisions is not None:
+        radius, delta, weight = collisions
+        sel = None if cells is None else [i for c in cells for i in range(int(offsets[c]), int(offsets[c + 1]))]
+        contacts = detect_contacts(types, type_of_cell, offsets, x, radius, vertices=sel)
     ncells = len(type_of_cell)
     cells = range(ncells) if cells is None else cells
     res = np.zeros(ncells)
@@ -497,7 +631,10 @@ def batch_step(types: List[CellType], type_of_cell, offsets, x, v, f, iters,
     for c in cells:
         s = slice(int(offsets[c]), int(offsets[c + 1]))
         ct = types[int(type_of_cell[c])]
-        r = step(ct.rest, ct.solver, x[:, s].T, v[:, s].T, f[:, s].T, int(iters[c]), ct.w_scale, tol)
+        con = None
+        if contacts is not None:
+            con = (*cell_contacts(contacts, s.start, s.stop), delta, weight)
+        r = step(ct.rest, ct.solver, x[:, s].T, v[:, s].T, f[:, s].T, int(iters[c]), ct.w_scale, tol, con)
         xo[:, s] = r.x.T
         vo[:, s] = r.v.T
         res[c] = r.residual
@@ -506,4 +643,4 @@ def batch_step(types: List[CellType], type_of_cell, offsets, x, v, f, iters,
         gnorms[c] = r.grad_norms
         done[c] = len(r.alphas)
     return {"x": xo, "v": vo, "residual": res, "status": st, "alphas": alphas,
-            "grad_norms": gnorms, "iters_done": done}
+            "grad_norms": gnorms, "iters_done": done, "contacts": contacts}

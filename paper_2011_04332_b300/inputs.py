@@ -335,3 +335,35 @@ def small_mixed_batch(seed: int = 7, iters=(2, 4, 5)) -> BatchInputs:
     rng = np.random.default_rng(seed)
     it = rng.integers(iters[0], iters[-1] + 1, size=len(toc)).astype(np.int32)
     return placed_cells(types, toc, seed, it, velocity_sigma=0.01)
+
+
+# nominal rest volumes used only to size packing boxes (um^3): Evans-Fung RBC, platelet
+RBC_NOMINAL_VOLUME = 94.1
+PLT_NOMINAL_VOLUME = 6.79
+
+
+def packing_batch(n_rbc: int, n_plt: int = 0, hematocrit: float = 0.35, seed: int = 1006,
+                  rbc_subdiv: int = 3, plt_subdiv: int = 2, iters: int = 5) -> BatchInputs:
+    """Cell-packing workload: cells at their rest shape with seeded random positions
+    (uniform in a cube) and orientations, no velocity and no force.  The cube's side
+    is set by the target volume fraction of the cells (nominal volumes), so randomly
+    placed cells overlap; cell order: RBCs, then platelets."""
+    types = [CellTypeSpec(rbc_mesh(rbc_subdiv), RBC_MATERIAL)]
+    toc = [0] * n_rbc
+    vol = n_rbc * RBC_NOMINAL_VOLUME
+    if n_plt:
+        types.append(CellTypeSpec(platelet_mesh(plt_subdiv), PLT_MATERIAL))
+        toc += [1] * n_plt
+        vol += n_plt * PLT_NOMINAL_VOLUME
+    side = (vol / hematocrit) ** (1.0 / 3.0)
+    ss = np.random.SeedSequence(seed)
+    children = ss.spawn(len(toc))
+    xs, vs, fs = [], [], []
+    for c, t in enumerate(toc):
+        rng = np.random.default_rng(children[c])
+        mesh = types[t].mesh
+        x = mesh.verts @ random_rotation(rng).T + rng.uniform(0.0, side, size=3)[None, :]
+        xs.append(x)
+        vs.append(np.zeros_like(x))
+        fs.append(np.zeros_like(x))
+    return _assemble(types, toc, xs, vs, fs, np.full(len(toc), iters, dtype=np.int32), DT_DEFAULT, seed)
