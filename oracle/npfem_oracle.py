@@ -357,22 +357,33 @@ def _sq_dist(x: np.ndarray, i: int) -> np.ndarray:
     return (dx * dx + dy * dy) + dz * dz
 
 
-def vertex_contacts(x: np.ndarray, offsets, cell_of_vertex: np.ndarray, i: int, radius: float):
+def vertex_contacts(x: np.ndarray, offsets, cell_of_vertex: np.ndarray, i: int, radius: float,
+                    index=None):
     """The matches of global vertex i: a list of (d2, b, j), nearest cell first, at
     most CONTACT_SLOTS.  Per other cell b the vertex j of b nearest to x_i (equal
     distances: the smaller j); cells with that distance below `radius` compete, and
     equal distances go to the smaller b."""
     a = int(cell_of_vertex[i])
-    d2 = _sq_dist(x, i)
+    # |x_i - x_j| < radius needs |dx| < radius: only those columns can match (and they
+    # hold every vertex of a cell that is at least as near as that cell's match).  With
+    # `index` = (argsort of x[0], sorted x[0]) the columns come from a window 1 % wider.
+    if index is None:
+        cand = np.nonzero(np.abs(x[0] - x[0, i]) < radius)[0]
+    else:
+        order, xs = index
+        lo = np.searchsorted(xs, x[0, i] - 1.01 * radius, side="left")
+        hi = np.searchsorted(xs, x[0, i] + 1.01 * radius, side="right")
+        cand = np.sort(order[lo:hi])
+    d2 = _sq_dist(x[:, cand], int(np.searchsorted(cand, i))) if len(cand) else np.zeros(0)
     r2 = radius * radius
     found = []
-    for b in np.unique(cell_of_vertex[d2 < r2]):
+    for b in np.unique(cell_of_vertex[cand[d2 < r2]]):
         b = int(b)
         if b == a:
             continue
-        s = slice(int(offsets[b]), int(offsets[b + 1]))
-        k = int(np.argmin(d2[s]))           # first occurrence: the smaller j on ties
-        found.append((float(d2[s][k]), b, int(offsets[b]) + k))
+        inb = np.nonzero(cell_of_vertex[cand] == b)[0]    # b's candidates, increasing j
+        k = int(np.argmin(d2[inb]))                      # first occurrence: the smaller j on ties
+        found.append((float(d2[inb][k]), b, int(cand[inb[k]])))
     found.sort(key=lambda t: (t[0], t[1]))
     return found[:CONTACT_SLOTS]
 
@@ -393,8 +404,10 @@ def detect_contacts(types: List["CellType"], type_of_cell, offsets, x: np.ndarra
     nrm = np.zeros((N, CONTACT_SLOTS, 3))
     cc = np.zeros((N, CONTACT_SLOTS))
     normals = {}
+    order = np.argsort(x[0], kind="stable")
+    index = (order, x[0][order])
     for i in (range(N) if vertices is None else vertices):
-        for k, (_, b, j) in enumerate(vertex_contacts(x, offsets, cell_of_vertex, i, radius)):
+        for k, (_, b, j) in enumerate(vertex_contacts(x, offsets, cell_of_vertex, i, radius, index)):
             if b not in normals:
                 s = slice(int(offsets[b]), int(offsets[b + 1]))
                 normals[b] = vertex_normals(x[:, s].T, types[int(type_of_cell[b])].rest.tris)
