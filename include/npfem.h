@@ -253,6 +253,47 @@ npfem_status npfem_batch_kernel_times(npfem_batch* batch, int32_t type_index, do
  * during which at least one such kernel was running).  span_ms: host array of 3. */
 npfem_status npfem_batch_kernel_spans(npfem_batch* batch, int32_t type_index, double* span_ms);
 
+/* Collisions.  The paper names collision detection and collision forces among the
+ * coupled code's work (Performance figure, "Other"), a collision weight (Collision at
+ * an obstacle section), and a fluid-free cell-packing application in which npFEM with
+ * collisions resolves the overlaps of cells placed at random (Cell Packing section); it
+ * gives no formula.  The reading implemented here: at the start of every step, each
+ * vertex i of cell a is matched with the nearest vertex j of each other cell b closer
+ * than `radius` (equal distances: the smaller j), and the two nearest such cells are
+ * kept (equal distances: the smaller b).  Each match is a plane through x_j with normal
+ * n_j, b's unit area-weighted outward vertex normal, both from the step's input state
+ * and fixed during the step; the step objective gains, per match,
+ * (weight/2) max(0, delta - (n_j . x_i - n_j . x_j))^2.  Distances are compared in FP64
+ * (squared, evaluated as (dx*dx + dy*dy) + dz*dz).  Cells stay independent within a
+ * step, so the step keeps its data-parallel structure. */
+typedef struct {
+  double radius; /* um: match search radius (also the detection grid's cell edge) */
+  double delta;  /* um: contact thickness, >= 0 */
+  double weight; /* nN/um: collision weight, >= 0 */
+} npfem_collision_params;
+
+/* Enable collisions for every later npfem_step / npfem_step_host of the batch (params
+ * != NULL) or disable them (NULL).  The first enable allocates the detection buffers
+ * (about 170 bytes per vertex plus a hash table of 16 bytes per slot, the next power of
+ * two >= N_total slots, at least 4096) and uploads the vertex-to-cell map (synchronous).
+ * While enabled, each step first runs the detection kernels on its stream (captured
+ * into graphs like the rest of the step); npfem_step_host then copies all inputs before
+ * the step instead of overlapping chunks; npfem_step_adjoint returns INVALID_ARG
+ * (contacts are not differentiated).  Errors: INVALID_ARG (null batch; radius not
+ * finite and > 0; delta or weight negative or not finite), UNSUPPORTED (2^30 vertices or
+ * more), CUDA / OOM. */
+npfem_status npfem_batch_set_collisions(npfem_batch* batch, const npfem_collision_params* params);
+
+/* The contacts found by the last step (device arrays, caller-owned, each NULL to skip),
+ * asynchronous on `stream`:
+ *   count  [N_total] int32 matches per vertex (0..2);
+ *   vertex [N_total][2] int32 global index of the matched vertex j, nearest first, -1 unused;
+ *   plane  [N_total][2][4] double: n_j, then n_j . (x_j - x_anchor), x_anchor the first
+ *          vertex of the cell of vertex i (the vertex matched) at the step's input (zeros unused).
+ * Errors: INVALID_ARG (null batch, collisions never enabled), CUDA. */
+npfem_status npfem_batch_contacts(npfem_batch* batch, int32_t* count, int32_t* vertex, double* plane,
+                                  void* stream);
+
 /* Same step with HOST arrays (pageable or pinned): copies x, v, f_ext (and iters,
  * when given) to batch-owned device buffers, runs the step, and copies x, v,
  * residuals, statuses (and opts->iters_done) back; synchronous.  residual_out,

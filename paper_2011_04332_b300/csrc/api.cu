@@ -14,6 +14,7 @@
 #include "step_kernel.cuh"
 #include "adjoint.cuh"
 #include "split_kernels.cuh"
+#include "contact_kernels.cuh"
 
 using namespace npfem;
 
@@ -115,6 +116,12 @@ struct npfem_batch {
   double* d_res = nullptr;
   int32_t* d_status = nullptr;
   int32_t* d_done = nullptr;
+  // collisions (npfem_batch_set_collisions): parameters and detection buffers
+  bool coll = false;
+  bool coll_alloc = false;
+  npfem_collision_params coll_p{};
+  int64_t coll_T = 0;     // hash-table size (power of two, multiple of the scan block)
+  ContactParams cp{};
 };
 
 template <typename S>
@@ -365,6 +372,55 @@ static npfem_status launch_split(npfem_batch* b, const npfem_cell_type* t, const
   return NPFEM_OK;
 }
 
+// Contact detection on the step's input positions (collisions enabled): normals, spatial
+// hash, scan, scatter, query; all on stream st, before any step kernel.
+template <typename S>
+static npfem_status detect_contacts_t(npfem_batch* b, const S* x, cudaStream_t st) {
+  ContactParams C = b->cp;
+  const int64_t N = b->n_total, T = b->coll_T;
+  C.n_total = N;
+  C.h = b->coll_p.radius;
+  C.h_inv = 1.0 / b->coll_p.radius;
+  C.r2 = b->coll_p.radius * b->coll_p.radius;
+  C.mask = (uint32_t)(T - 1);
+  NPFEM_CUDA_TRY(cudaMemsetAsync(C.count, 0, sizeof(int32_t) * T, st));
+  for (const TypeLaunch& L : b->launches) {
+    const npfem_cell_type* t = b->types[L.type_index];
+    const int grid = std::max(1, std::min(b->sms * 8, (L.ncells + 3) / 4));
+    if constexpr (sizeof(S) == 8)
+      npfem_k_normals<double><<<grid, 128, 0, st>>>(t->v64, L.cell_list, L.ncells, b->d_offsets, N, x, C.nrm);
+    else
+      npfem_k_normals<float><<<grid, 128, 0, st>>>(t->v32, L.cell_list, L.ncells, b->d_offsets, N, x, C.nrm);
+  }
+  const int vgrid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->sms * 16, (N + 255) / 256));
+  npfem_k_hash<S><<<vgrid, 256, 0, st>>>(C, x);
+  const int nblk = (int)(T / kScanBlock);
+  npfem_k_scan_blocks<<<nblk, kScanThreads, 0, st>>>(C.count, C.start, C.bsum);
+  npfem_k_scan_carry<<<1, kScanThreads, 0, st>>>(C.bsum, nblk);
+  const int tgrid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->sms * 16, (T + 255) / 256));
+  npfem_k_scan_add<<<tgrid, 256, 0, st>>>(C, T);
+  npfem_k_scatter<S><<<vgrid, 256, 0, st>>>(C, x);
+  const int qgrid = (int)std::max<int64_t>(1, (N + 127) / 128);
+  npfem_k_query<S><<<qgrid, 128, 0, st>>>(C, x);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(NPFEM_ERR_CUDA, std::string("contact detection: ") + cudaGetErrorString(e));
+  return NPFEM_OK;
+}
+
+static npfem_status detect_contacts(npfem_batch* b, const void* x, cudaStream_t st) {
+  if (b->prec == NPFEM_FP64) return detect_contacts_t<double>(b, static_cast<const double*>(x), st);
+  return detect_contacts_t<float>(b, static_cast<const float*>(x), st);
+}
+
+// The step kernels' view of the contacts of the current step (null when collisions are off).
+static void set_contact_params(const npfem_batch* b, StepParams& P) {
+  if (!b->coll) return;
+  P.contact_count = b->cp.ccount;
+  P.contact_plane = b->cp.cplane;
+  P.contact_delta = b->coll_p.delta;
+  P.contact_weight = b->coll_p.weight;
+}
+
 static constexpr int kTimingSlots = 1 + 2 * kSplitMaxIters;
 
 // Records one timing event on stream s; under stream capture it becomes an external
@@ -478,6 +534,7 @@ static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_e
   P.alpha_log = opts->alpha_log;
   P.alpha_log_len = opts->alpha_log_len;
   P.phase_cycles = b->d_phase;
+  set_contact_params(b, P);
   auto launch = [&](size_t c, int kind, int it, int slot) -> npfem_status {
     const Chain& C = chains[c];
     const TypeLaunch& L = b->launches[C.li];
@@ -764,6 +821,10 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
   if (!(opts->tol >= 0.0) || std::isinf(opts->tol))
     return fail(NPFEM_ERR_INVALID_ARG, "step: tol must be finite and >= 0");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (b->coll) {
+    npfem_status rc = detect_contacts(b, x, st);
+    if (rc != NPFEM_OK) return rc;
+  }
   if (b->mode == 1 && (iters == nullptr || opts->max_iters > 0)) {
     const int max_iters = iters ? opts->max_iters : opts->iters;
     if (max_iters <= kSplitMaxIters) return step_split(b, x, v, f_ext, iters, opts, max_iters, residual_out, status_out, st);
@@ -790,6 +851,7 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
     P.z_in_smem = L.z_in_smem;
     P.solve_per_coord = L.solve_per_coord;
     P.phase_cycles = b->d_phase;
+    set_contact_params(b, P);
     dim3 grid(L.blocks), block(32 * L.warps_per_block);
     if (b->prec == NPFEM_FP64)
       npfem_step_kernel<double><<<grid, block, L.smem_bytes, st>>>(t->v64, P, static_cast<double*>(x),
@@ -817,6 +879,8 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: iteration count must be in [0, 16]");
   if (opts->tol != 0.0)
     return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: tol must be 0 (fixed iteration counts)");
+  if (b->coll)
+    return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: collisions are enabled (contacts are not differentiated)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   for (TypeLaunch& L : b->launches) {
     if (L.adj_scratch) continue;
@@ -1093,7 +1157,8 @@ npfem_status npfem_step_host(npfem_batch* b, void* x, void* v, const void* f_ext
   }
   // chunks: up to 12 chains in all (8 chunks for one cell type, 4 for three)
   const int per_type = std::max(2, 12 / std::max(1, (int)b->launches.size()));
-  const int K = split ? std::min(std::min(kMaxChains, per_type), b->ncells) : 1;
+  // contact detection needs every cell's input on the device: one chunk with collisions
+  const int K = split && !b->coll ? std::min(std::min(kMaxChains, per_type), b->ncells) : 1;
   if (K < 2) {  // one chunk: copies in, step, copies out
     NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_x, x, bytes, cudaMemcpyHostToDevice, st));
     NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_v, v, bytes, cudaMemcpyHostToDevice, st));
@@ -1183,6 +1248,79 @@ npfem_status npfem_step_host(npfem_batch* b, void* x, void* v, const void* f_ext
     NPFEM_CUDA_TRY(cudaMemcpyAsync(opts->iters_done, b->d_done, sizeof(int32_t) * b->ncells,
                                    cudaMemcpyDeviceToHost, st));
   NPFEM_CUDA_TRY(cudaStreamSynchronize(st));
+  return NPFEM_OK;
+}
+
+npfem_status npfem_batch_set_collisions(npfem_batch* b, const npfem_collision_params* p) {
+  if (!b) return fail(NPFEM_ERR_INVALID_ARG, "batch_set_collisions: null batch");
+  if (!p) {
+    b->coll = false;
+    return NPFEM_OK;
+  }
+  if (!(p->radius > 0.0) || std::isinf(p->radius) || !(p->delta >= 0.0) || std::isinf(p->delta) ||
+      !(p->weight >= 0.0) || std::isinf(p->weight))
+    return fail(NPFEM_ERR_INVALID_ARG, "batch_set_collisions: need finite radius > 0, delta >= 0, weight >= 0");
+  if (b->n_total >= ((int64_t)1 << 30))
+    return fail(NPFEM_ERR_UNSUPPORTED, "batch_set_collisions: more than 2^30 vertices");
+  if (!b->coll_alloc && b->n_total > 0) {
+    const int64_t N = b->n_total;
+    int64_t T = kScanBlock;
+    while (T < N) T <<= 1;
+    ContactParams& C = b->cp;
+    void* q = nullptr;
+    auto take = [&](size_t bytes, void** out) -> cudaError_t { return b->mem.alloc(bytes, out); };
+    NPFEM_CUDA_TRY(take(sizeof(int32_t) * N, &q));
+    C.vcell = static_cast<const int32_t*>(q);
+    int32_t* vcell = static_cast<int32_t*>(q);
+    NPFEM_CUDA_TRY(take(sizeof(int32_t) * N, &q));
+    C.key = static_cast<int32_t*>(q);
+    NPFEM_CUDA_TRY(take(sizeof(int32_t) * T, &q));
+    C.count = static_cast<int32_t*>(q);
+    NPFEM_CUDA_TRY(take(sizeof(int32_t) * (T + 1), &q));
+    C.start = static_cast<int32_t*>(q);
+    NPFEM_CUDA_TRY(take(sizeof(int32_t) * T, &q));
+    C.cursor = static_cast<int32_t*>(q);
+    NPFEM_CUDA_TRY(take(sizeof(int32_t) * (T / kScanBlock), &q));
+    C.bsum = static_cast<int32_t*>(q);
+    NPFEM_CUDA_TRY(take(sizeof(int32_t) * N, &q));
+    C.sorted = static_cast<int32_t*>(q);
+    NPFEM_CUDA_TRY(take(sizeof(float4) * N, &q));
+    C.sortpos = static_cast<float4*>(q);
+    NPFEM_CUDA_TRY(take(sizeof(double) * 3 * N, &q));
+    C.nrm = static_cast<double*>(q);
+    NPFEM_CUDA_TRY(take(sizeof(int32_t) * N, &q));
+    C.ccount = static_cast<int32_t*>(q);
+    NPFEM_CUDA_TRY(take(sizeof(int32_t) * kContactSlots * N, &q));
+    C.cvertex = static_cast<int32_t*>(q);
+    NPFEM_CUDA_TRY(take(sizeof(double) * 4 * kContactSlots * N, &q));
+    C.cplane = static_cast<double*>(q);
+    C.offsets = b->d_offsets;
+    std::vector<int32_t> hv((size_t)N);
+    for (int c = 0; c < b->ncells; ++c)
+      for (int64_t i = b->offsets[c]; i < b->offsets[c + 1]; ++i) hv[(size_t)i] = c;
+    NPFEM_CUDA_TRY(cudaMemcpy(vcell, hv.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice));
+    b->coll_T = T;
+    b->coll_alloc = true;
+  }
+  b->coll_p = *p;
+  b->coll = true;
+  return NPFEM_OK;
+}
+
+npfem_status npfem_batch_contacts(npfem_batch* b, int32_t* count, int32_t* vertex, double* plane, void* stream) {
+  if (!b) return fail(NPFEM_ERR_INVALID_ARG, "batch_contacts: null batch");
+  if (b->n_total == 0) return NPFEM_OK;
+  if (!b->coll_alloc) return fail(NPFEM_ERR_INVALID_ARG, "batch_contacts: collisions were never enabled");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t N = b->n_total;
+  if (count)
+    NPFEM_CUDA_TRY(cudaMemcpyAsync(count, b->cp.ccount, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st));
+  if (vertex)
+    NPFEM_CUDA_TRY(cudaMemcpyAsync(vertex, b->cp.cvertex, sizeof(int32_t) * kContactSlots * N,
+                                   cudaMemcpyDeviceToDevice, st));
+  if (plane)
+    NPFEM_CUDA_TRY(cudaMemcpyAsync(plane, b->cp.cplane, sizeof(double) * 4 * kContactSlots * N,
+                                   cudaMemcpyDeviceToDevice, st));
   return NPFEM_OK;
 }
 

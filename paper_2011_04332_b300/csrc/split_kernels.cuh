@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(128, IterOccupancy<S>::min_blocks) npfem_k_beg
     __syncwarp();
     NPFEM_PHASE_END(t_predict, kPhPredict, P, lane)
     NPFEM_PHASE_BEGIN(t_obj0)
-    EvalOut ev = eval_objective<S>(ty, P, w, w.U, w.G, cvol, lane);
+    EvalOut ev = eval_objective<S>(ty, P, w, w.U, w.G, cvol, cell, lane);
     NPFEM_PHASE_END(t_obj0, kPhObjective, P, lane)
     const double g0n = sqrt(vdot64<S>(w.G, w.G, len, lane));
     if (lane == 0) {
@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(128, IterOccupancy<S>::min_blocks) npfem_k_ite
       for (int e = lane; e < len; e += 32) UT[e] = U[e] + sa * w.D[e];
       __syncwarp();
       NPFEM_PHASE_BEGIN(t_obj)
-      EvalOut et = eval_objective<S>(ty, P, w, UT, GT, cvol, lane);
+      EvalOut et = eval_objective<S>(ty, P, w, UT, GT, cvol, cell, lane);
       NPFEM_PHASE_END(t_obj, kPhObjective, P, lane)
       ft = et.energy;
       degen = degen || et.degenerate;

@@ -39,6 +39,9 @@ struct StepParams {
   int32_t* status_out;         // [ncells] or null
   double tol;                  // > 0: stop a cell once |g| < tol |g0| (converged-residual mode)
   int32_t* iters_done;         // [ncells] iterations run, or null
+  const int32_t* contact_count;  // [N_total] contact planes per vertex (0..2), or null: no collisions
+  const double* contact_plane;   // [N_total][2][4] unit normal, offset relative to the cell's anchor
+  double contact_delta, contact_weight;  // penalty (w/2) max(0, delta - gap)^2 per plane
   double* alpha_log;           // [ncells][alpha_log_len] or null
   int alpha_log_len;
   int* queue_counter;          // work-queue head (zeroed before the launch)
@@ -201,7 +204,7 @@ struct EvalOut {
 // closed-form 2x2 SPD square root (C + sqrt(det C) I)/sqrt(tr C + 2 sqrt(det C)).
 template <typename S>
 __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const StepParams& P, const CellWs<S>& w, const S* U,
-                                  S* Gout, V3<S> cvol, int lane) {
+                                  S* Gout, V3<S> cvol, int cell, int lane) {
   const int n = ty.n, T = ty.T, E = ty.E;
   const S* X = w.X;
   NPFEM_PHASE_BEGIN(t_area)
@@ -320,6 +323,33 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const StepParams& P,
   NPFEM_PHASE_END(t_gather, kPhGather, P, lane)
   EvalOut o;
   o.energy = e_el.total() + e_area + e_vol;
+  if (P.contact_count) {
+    // pass E: contact planes (fixed for the step), (w/2) max(0, delta - gap)^2 each, on
+    // the vertices that have any; a pass of its own keeps pass D's registers unchanged
+    __syncwarp();
+    const int64_t off = P.offsets[cell];
+    double e_ct = 0.0;
+    for (int v = lane; v < n; v += 32) {
+      const int nc = P.contact_count[off + v];
+      if (nc == 0) continue;
+      V3<S> g = ld3(Gout, v);
+      const V3<S> p = ld3(X, v) + ld3(U, v);
+      for (int m = 0; m < nc; ++m) {
+        const double* pl = P.contact_plane + 8 * (off + v) + 4 * m;
+        const double gap = pl[0] * (double)p.x + pl[1] * (double)p.y + pl[2] * (double)p.z - pl[3];
+        const double pen = P.contact_delta - gap;
+        if (pen > 0.0) {
+          e_ct += 0.5 * P.contact_weight * pen * pen;
+          const double fw = -P.contact_weight * pen;
+          g.x += (S)(fw * pl[0]);
+          g.y += (S)(fw * pl[1]);
+          g.z += (S)(fw * pl[2]);
+        }
+      }
+      st3(Gout, v, g);
+    }
+    o.energy += warp_sum_d(e_ct);
+  }
   o.degenerate = __any_sync(kFull, degen);
   __syncwarp();
   return o;
@@ -643,7 +673,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
   S* GT = w.GT;
   NPFEM_PHASE_END(t_predict, kPhPredict, P, lane)
   NPFEM_PHASE_BEGIN(t_obj0)
-  EvalOut ev = eval_objective<S>(ty, P, w, U, G, cvol, lane);
+  EvalOut ev = eval_objective<S>(ty, P, w, U, G, cvol, cell, lane);
   NPFEM_PHASE_END(t_obj0, kPhObjective, P, lane)
   double fx = ev.energy;
   bool degen = ev.degenerate;
@@ -710,7 +740,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
       for (int e = lane; e < len; e += 32) UT[e] = U[e] + sa * w.D[e];
       __syncwarp();
       NPFEM_PHASE_BEGIN(t_obj)
-      EvalOut et = eval_objective<S>(ty, P, w, UT, GT, cvol, lane);
+      EvalOut et = eval_objective<S>(ty, P, w, UT, GT, cvol, cell, lane);
       NPFEM_PHASE_END(t_obj, kPhObjective, P, lane)
       ft = et.energy;
       degen = degen || et.degenerate;

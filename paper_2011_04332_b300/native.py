@@ -46,6 +46,10 @@ class _Opts(C.Structure):
                 ("max_iters", C.c_int32), ("tol", C.c_double), ("iters_done", C.c_void_p)]
 
 
+class _CollisionParams(C.Structure):
+    _fields_ = [("radius", C.c_double), ("delta", C.c_double), ("weight", C.c_double)]
+
+
 class _TypeInfo(C.Structure):
     _fields_ = [("n_verts", C.c_int32), ("n_tris", C.c_int32), ("n_hinges", C.c_int32),
                 ("nnz_factor", C.c_int64), ("solve_chunks", C.c_int64),
@@ -89,6 +93,8 @@ def load_library() -> C.CDLL:
         "npfem_batch_set_launch": [vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32],
         "npfem_batch_get_launch": [vp, C.c_int32, C.POINTER(C.c_int32)],
         "npfem_step_noalloc": [vp, C.c_int, C.c_int32, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp],
+        "npfem_batch_set_collisions": [vp, C.POINTER(_CollisionParams)],
+        "npfem_batch_contacts": [vp, vp, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -193,6 +199,7 @@ class Batch:
         _check(lib.npfem_batch_layout(h, C.byref(nt), offs.ctypes.data_as(C.POINTER(C.c_int64))))
         self.n_total = int(nt.value)
         self.offsets = offs
+        self.collisions_on = False
 
     def step(self, x, v, f, iters=None, iters_default: int = 5, residual=None, status=None,
              alpha_log=None, stream=None, max_iters: int = 0, tol: float = 0.0, iters_done=None):
@@ -297,6 +304,27 @@ class Batch:
         out = (C.c_int32 * 8)()
         _check(_lib.npfem_batch_get_split_launch(self.handle, int(type_index), out))
         return tuple(int(v) for v in out[:7]), bool(out[7])
+
+    def set_collisions(self, radius: Optional[float] = None, delta: float = 0.0, weight: float = 0.0) -> None:
+        """npfem_batch_set_collisions: contacts (search radius, thickness delta, weight w)
+        detected at the start of every later step; radius=None disables them."""
+        if radius is None:
+            _check(_lib.npfem_batch_set_collisions(self.handle, None))
+            self.collisions_on = False
+        else:
+            p = _CollisionParams(float(radius), float(delta), float(weight))
+            _check(_lib.npfem_batch_set_collisions(self.handle, C.byref(p)))
+            self.collisions_on = True
+
+    def contacts(self, count=None, vertex=None, plane=None, stream=None) -> None:
+        """npfem_batch_contacts: the last step's contacts into device tensors
+        (int32 [N], int32 [N, 2], float64 [N, 2, 4]; each may be None)."""
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        elif not isinstance(stream, int):
+            stream = stream.cuda_stream
+        _check(_lib.npfem_batch_contacts(self.handle, _ptr(count), _ptr(vertex), _ptr(plane), C.c_void_p(stream)))
 
     def step_host(self, x: np.ndarray, v: np.ndarray, f: np.ndarray, iters=None, iters_default: int = 5,
                   residual=None, status=None, stream: int = 0, tol: float = 0.0, iters_done=None):
