@@ -34,6 +34,10 @@ UNIT = "RBC-equivalent cell-steps/s"
 
 
 # ------------------------------------------------------------------ workloads
+# collision parameters (search radius um, contact thickness um, weight nN/um) per workload
+COLLISIONS = {"pack4096": (0.5, 0.05, 60.0)}
+
+
 def make_workload(name: str, rank: int = 0):
     from paper_2011_04332_b300 import inputs as I
     if name == "homog4096":
@@ -53,6 +57,12 @@ def make_workload(name: str, rank: int = 0):
     elif name == "homog2562":
         b = I.homogeneous_rbc_batch(ncells=1184, seed=1001 + 100 * rank, subdiv=4)
         desc = "homogeneous 1184 RBC (2562 vertices, Evans-Fung), 5 iterations"
+    elif name == "pack4096":
+        b = I.packing_batch(4096, 0, hematocrit=0.35, seed=1006 + 100 * rank)
+        r, d, w = COLLISIONS[name]
+        desc = ("cell packing: 4096 RBC (642 vertices) at rest with random positions and orientations in a "
+                f"cube at 35 % volume fraction (overlapping), 5 iterations, collisions radius {r} um, "
+                f"delta {d} um, weight {w} nN/um, contact detection inside every step")
     elif name == "small":
         b = I.homogeneous_rbc_batch(ncells=64, seed=1001 + 100 * rank)
         desc = "64 RBC (642 vertices), 5 iterations"
@@ -78,8 +88,8 @@ def _oracle_worker(args):
     mesh_v, mesh_t, mat, dt, cells, tol = args
     ct = O.CellType(mesh_v, mesh_t, mat, dt)
     t0 = time.perf_counter()
-    for (x, v, f, it) in cells:
-        O.step(ct.rest, ct.solver, x, v, f, int(it), tol=tol)
+    for (x, v, f, it, con) in cells:
+        O.step(ct.rest, ct.solver, x, v, f, int(it), tol=tol, contact=con)
     return time.perf_counter() - t0, len(cells)
 
 
@@ -95,11 +105,23 @@ def step_units(b, sel=None, tol: float = 0.0) -> float:
     return float(np.sum(n / 642.0 * b.iters[sel] / 5.0))
 
 
-def oracle_baseline(b, sample_cells: int, workers: int, tol: float = 0.0):
+def oracle_baseline(b, sample_cells: int, workers: int, tol: float = 0.0, collisions=None):
     """Time the oracle on the first `sample_cells` cells, one step each, spread over
     `workers` single-threaded processes (spawn).  Returns (rbc_eq per s, cores, desc)."""
     import multiprocessing as mp
     sel = list(range(min(sample_cells, b.ncells)))
+    contacts, t_detect = {}, 0.0
+    if collisions is not None:
+        # the sampled cells' contact detection (over the whole batch) is part of their step
+        from oracle import npfem_oracle as O
+        radius, delta, weight = collisions
+        ots = [O.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
+        verts = [i for c in sel for i in range(int(b.offsets[c]), int(b.offsets[c + 1]))]
+        t0 = time.perf_counter()
+        con = O.detect_contacts(ots, b.type_of_cell, b.offsets, b.x, radius, vertices=verts)
+        for c in sel:
+            contacts[c] = (*O.cell_contacts(con, int(b.offsets[c]), int(b.offsets[c + 1])), delta, weight)
+        t_detect = time.perf_counter() - t0
     by_type = {}
     for c in sel:
         by_type.setdefault(int(b.type_of_cell[c]), []).append(c)
@@ -110,7 +132,7 @@ def oracle_baseline(b, sample_cells: int, workers: int, tol: float = 0.0):
         for ch in chunks:
             if ch:
                 jobs.append((ty.mesh.verts, ty.mesh.tris, ty.material.as_tuple(), b.dt,
-                             [(*b.cell_state(c), b.iters[c]) for c in ch], tol))
+                             [(*b.cell_state(c), b.iters[c], contacts.get(c)) for c in ch], tol))
     ctx = mp.get_context("spawn")
     env_backup = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
     for k in env_backup:
@@ -130,6 +152,9 @@ def oracle_baseline(b, sample_cells: int, workers: int, tol: float = 0.0):
     rbc_eq = step_units(b, sel, tol)
     desc = (f"{len(sel)} cells x 1 step of the same workload (first cells in batch order), "
             f"{workers} single-threaded processes; type setup excluded; wall incl. setup {wall:.1f}s")
+    if collisions is not None:
+        busy += t_detect
+        desc += f"; contact detection of the sampled cells (one process) {t_detect:.2f}s included"
     return rbc_eq / busy, workers, desc
 
 
@@ -215,7 +240,9 @@ def run_ours(args, rank, world, local_rank):
     # oracle baseline first (spawned processes, before heavy GPU work), rank 0 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        v, cores, sdesc = oracle_baseline(b, args.cpu_sample, args.cpu_workers, tol)
+        # with collisions the oracle's brute-force detection dominates: a smaller sample
+        nsample = args.cpu_sample if args.workload not in COLLISIONS else min(args.cpu_sample, 16)
+        v, cores, sdesc = oracle_baseline(b, nsample, args.cpu_workers, tol, COLLISIONS.get(args.workload))
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc}
 
     prec = native.FP32FORM if args.precision == "fp32form" else native.FP64
@@ -223,6 +250,9 @@ def run_ours(args, rank, world, local_rank):
     types = [native.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
     infos = [t.info() for t in types]
     batch = native.Batch(types, b.type_of_cell, prec)
+    coll = COLLISIONS.get(args.workload)
+    if coll is not None:
+        batch.set_collisions(*coll)
     x0 = torch.tensor(b.x, dtype=tdt, device=dev)
     v0 = torch.tensor(b.v, dtype=tdt, device=dev)
     f = torch.tensor(b.f, dtype=tdt, device=dev)
@@ -252,6 +282,11 @@ def run_ours(args, rank, world, local_rank):
         sample = [0, b.ncells // 3, (2 * b.ncells) // 3, b.ncells - 1]
         ot = {}
         xin, vin, fin = (t.double().cpu().numpy() for t in (x0, v0, f))
+        scon = None
+        if coll is not None:
+            allt = [O.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
+            scon = O.detect_contacts(allt, b.type_of_cell, b.offsets, xin, coll[0],
+                                     vertices=[i for c in sample for i in range(int(b.offsets[c]), int(b.offsets[c + 1]))])
         xg = xs.double().cpu().numpy()
         errs, counts = [], []
         for c in sample:
@@ -260,7 +295,9 @@ def run_ours(args, rank, world, local_rank):
                 ty = b.types[t]
                 ot[t] = O.CellType(ty.mesh.verts, ty.mesh.tris, ty.material.as_tuple(), b.dt)
             s = b.cell_slice(c)
-            r = O.step(ot[t].rest, ot[t].solver, xin[:, s].T, vin[:, s].T, fin[:, s].T, int(b.iters[c]), tol=tol)
+            con = None if scon is None else (*O.cell_contacts(scon, s.start, s.stop), coll[1], coll[2])
+            r = O.step(ot[t].rest, ot[t].solver, xin[:, s].T, vin[:, s].T, fin[:, s].T, int(b.iters[c]), tol=tol,
+                       contact=con)
             rad = np.max(np.linalg.norm(r.x - r.x.mean(axis=0), axis=1))
             errs.append(float(np.max(np.abs(xg[:, s].T - r.x)) / rad))
             counts.append((int(done_gpu[c]), len(r.alphas)))
@@ -312,6 +349,7 @@ def run_ours(args, rank, world, local_rank):
     present = sorted({int(t) for t in b.type_of_cell})
     ktime = {t: {k: [0.0, 0] for k in native.Batch.KERNELS} for t in present}
     kspan = {k: 0.0 for k in native.Batch.KERNELS}      # union of concurrent launches, all types
+    detect_ms = 0.0                                      # contact detection (collisions on)
     with ClockSampler(local_rank) as clk:
         t_wall0 = time.perf_counter()
         for k in range(args.steps):
@@ -330,6 +368,8 @@ def run_ours(args, rank, world, local_rank):
                     ktime[t][name][1] += kn
             for name, sms in batch.kernel_spans(-1).items():
                 kspan[name] += sms
+            if coll is not None:
+                detect_ms += batch.contact_time()
         torch.cuda.synchronize()
         t_wall = time.perf_counter() - t_wall0
     if world > 1:
@@ -427,6 +467,10 @@ def run_ours(args, rank, world, local_rank):
                    "split_shapes": {str(t): list(batch.get_split_launch(t)[0]) for t in sorted(set(int(q) for q in b.type_of_cell))},
                    "groups": {str(t): batch.get_groups(t) for t in sorted(set(int(q) for q in b.type_of_cell))},
                    "autotune": tuned,
+                   "collisions": ({"radius_um": coll[0], "delta_um": coll[1], "weight_nN_per_um": coll[2],
+                                   "detection": "normals, spatial hash, scan, scatter, query kernels inside the step",
+                                   "detection_ms_per_step": detect_ms / args.steps}
+                                  if coll is not None else None),
                    "parallelism": "cells sharded across ranks, no collective" if world > 1 else "1 GPU"},
         "residual": {"median": float(np.median(resid)), "max": float(np.max(resid)),
                      "definition": "|grad f(x_final)| / |grad f(x_0)| per cell after the step"},
@@ -443,8 +487,9 @@ def run_ours(args, rank, world, local_rank):
         "e2e": e2e,
         "adjoint": adjoint,
         "kernels": kernels,
-        "gpu_launches": args.steps * sum(min(batch.get_groups(t), int(np.sum(b.type_of_cell == t)))
-                                         for t in set(int(q) for q in b.type_of_cell)) * (1 + 2 * int(np.max(b.iters))),
+        "gpu_launches": args.steps * (sum(min(batch.get_groups(t), int(np.sum(b.type_of_cell == t)))
+                                          for t in set(int(q) for q in b.type_of_cell)) * (1 + 2 * int(np.max(b.iters)))
+                                      + (len(set(int(q) for q in b.type_of_cell)) + 6 if coll is not None else 0)),
         "clocks": clk.summary(),
         "wall_s_timed_region": t_wall,
     }
@@ -543,7 +588,8 @@ def run_reference(args, rank, world):
     cores = args.cpu_workers
     sdesc = ""
     for _ in range(args.warmup + args.steps):
-        v, cores, sdesc = oracle_baseline(b, args.ref_sample, args.cpu_workers, args.tol)
+        nsample = args.ref_sample if args.workload not in COLLISIONS else min(args.ref_sample, 4)
+        v, cores, sdesc = oracle_baseline(b, nsample, args.cpu_workers, args.tol, COLLISIONS.get(args.workload))
         per_step.append(v)
     vals = per_step[args.warmup:]
     value = float(statistics.mean(vals))
@@ -560,7 +606,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="homog4096", choices=["homog4096", "hetero10k", "stress20k", "homog1776", "homog2562", "small"])
+    ap.add_argument("--workload", default="homog4096", choices=["homog4096", "hetero10k", "stress20k", "homog1776", "homog2562",
+                                                            "pack4096", "small"])
     ap.add_argument("--precision", default="fp32form", choices=["fp32form", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=128)

@@ -294,6 +294,13 @@ npfem_status npfem_batch_set_collisions(npfem_batch* batch, const npfem_collisio
 npfem_status npfem_batch_contacts(npfem_batch* batch, int32_t* count, int32_t* vertex, double* plane,
                                   void* stream);
 
+/* With kernel timing on (npfem_batch_set_kernel_timing) and collisions on, every step
+ * records a CUDA event pair around its detection kernels on the step's stream (event
+ * records under stream capture, re-recorded by each replay).  This waits for the last
+ * step's pair and returns the time between them in ms.  Errors: INVALID_ARG (null
+ * argument; the last step ran without timing or without collisions), CUDA. */
+npfem_status npfem_batch_contact_time(npfem_batch* batch, double* ms);
+
 /* Same step with HOST arrays (pageable or pinned): copies x, v, f_ext (and iters,
  * when given) to batch-owned device buffers, runs the step, and copies x, v,
  * residuals, statuses (and opts->iters_done) back; synchronous.  residual_out,

@@ -98,6 +98,8 @@ struct npfem_batch {
     for (cudaStream_t s : type_streams) cudaStreamDestroy(s);
     for (cudaEvent_t e : type_events) cudaEventDestroy(e);
     if (fork_event) cudaEventDestroy(fork_event);
+    for (cudaEvent_t e : det_ev)
+      if (e) cudaEventDestroy(e);
     for (TypeLaunch& L : launches) {
       if (L.scratch) cudaFree(L.scratch);
       if (L.adj_scratch) cudaFree(L.adj_scratch);
@@ -122,6 +124,8 @@ struct npfem_batch {
   npfem_collision_params coll_p{};
   int64_t coll_T = 0;     // hash-table size (power of two, multiple of the scan block)
   ContactParams cp{};
+  cudaEvent_t det_ev[2] = {nullptr, nullptr};  // around the detection kernels (kernel timing on)
+  bool det_timed = false;                      // the last step recorded det_ev
 };
 
 template <typename S>
@@ -821,9 +825,14 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
   if (!(opts->tol >= 0.0) || std::isinf(opts->tol))
     return fail(NPFEM_ERR_INVALID_ARG, "step: tol must be finite and >= 0");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  b->det_timed = false;
   if (b->coll) {
+    const bool timed = b->ktiming && b->det_ev[0] && b->det_ev[1];
+    if (timed) NPFEM_CUDA_TRY(record_timing_event(b->det_ev[0], st));
     npfem_status rc = detect_contacts(b, x, st);
     if (rc != NPFEM_OK) return rc;
+    if (timed) NPFEM_CUDA_TRY(record_timing_event(b->det_ev[1], st));
+    b->det_timed = timed;
   }
   if (b->mode == 1 && (iters == nullptr || opts->max_iters > 0)) {
     const int max_iters = iters ? opts->max_iters : opts->iters;
@@ -1036,7 +1045,22 @@ npfem_status npfem_batch_set_kernel_timing(npfem_batch* b, int32_t enable) {
     b->k_last_slots.assign(chains, 0);
   }
   if (enable && !b->k_ref) NPFEM_CUDA_TRY(cudaEventCreate(&b->k_ref));
+  if (enable)
+    for (cudaEvent_t& e : b->det_ev)
+      if (!e) NPFEM_CUDA_TRY(cudaEventCreate(&e));
   b->ktiming = enable != 0 && !b->launches.empty();
+  return NPFEM_OK;
+}
+
+npfem_status npfem_batch_contact_time(npfem_batch* b, double* ms) {
+  if (!b || !ms) return fail(NPFEM_ERR_INVALID_ARG, "batch_contact_time: null argument");
+  *ms = 0.0;
+  if (!b->det_timed)
+    return fail(NPFEM_ERR_INVALID_ARG, "batch_contact_time: the last step was not timed with collisions on");
+  NPFEM_CUDA_TRY(cudaEventSynchronize(b->det_ev[1]));
+  float t = 0.f;
+  NPFEM_CUDA_TRY(cudaEventElapsedTime(&t, b->det_ev[0], b->det_ev[1]));
+  *ms = t;
   return NPFEM_OK;
 }
 

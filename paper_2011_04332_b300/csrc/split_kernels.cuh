@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(128, IterOccupancy<S>::min_blocks) npfem_k_beg
       st->hcount = 0;
       st->hhead = 0;
       st->status = status;
-      st->degen = ev.degenerate ? 1 : 0;
+      st->degen = 0;  // the flag reports accepted iterates only
       st->cur = 0;
       for (int i = 0; i < kHistory; ++i) st->rho[i] = st->aco[i] = (S)0;
       st->cvol[0] = cvol.x;
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(128, IterOccupancy<S>::min_blocks) npfem_k_ite
       EvalOut et = eval_objective<S>(ty, P, w, UT, GT, cvol, cell, lane);
       NPFEM_PHASE_END(t_obj, kPhObjective, P, lane)
       ft = et.energy;
-      degen = degen || et.degenerate;
+      degen = et.degenerate;  // the trial that ends the search is the accepted one
       double gtd = vdot64<S>(GT, w.D, len, lane);
       bool armijo = ft <= fx + kArmijoC1 * alpha * gd;
       bool approx = (gtd <= (2.0 * kArmijoC1 - 1.0) * gd) && (ft <= fx + kEnergyGuardEps * fabs(fx));

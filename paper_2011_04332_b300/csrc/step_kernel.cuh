@@ -676,7 +676,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
   EvalOut ev = eval_objective<S>(ty, P, w, U, G, cvol, cell, lane);
   NPFEM_PHASE_END(t_obj0, kPhObjective, P, lane)
   double fx = ev.energy;
-  bool degen = ev.degenerate;
+  bool degen = false;  // set by accepted iterates only
   if (kTape) {
     copy_vec<double>(tape->U, (const double*)U, len, lane);
     copy_vec<double>(tape->G, (const double*)G, len, lane);
@@ -735,6 +735,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
     }
     // K5: backtracking line search
     double alpha = 1.0, ft = 0.0;
+    bool trial_degen = false;
     for (int h = 0; h <= kMaxHalvings; ++h) {
       const S sa = (S)alpha;
       for (int e = lane; e < len; e += 32) UT[e] = U[e] + sa * w.D[e];
@@ -743,7 +744,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
       EvalOut et = eval_objective<S>(ty, P, w, UT, GT, cvol, cell, lane);
       NPFEM_PHASE_END(t_obj, kPhObjective, P, lane)
       ft = et.energy;
-      degen = degen || et.degenerate;
+      trial_degen = et.degenerate;
       double gtd = vdot64<S>(GT, w.D, len, lane);
       bool armijo = ft <= fx + kArmijoC1 * alpha * gd;
       bool approx = (gtd <= (2.0 * kArmijoC1 - 1.0) * gd) && (ft <= fx + kEnergyGuardEps * fabs(fx));
@@ -754,6 +755,7 @@ __device__ void process_cell(const DevTypeView<S>& ty, const StepParams& P, cons
       }
       alpha *= 0.5;
     }
+    degen = degen || trial_degen;  // the trial that ends the search is the accepted one
     // converged-residual mode: the accepted trial ends the step when |g| < tol |g0|
     const bool stop = P.tol > 0.0 && sqrt(vdot64<S>(GT, GT, len, lane)) < P.tol * g0n;
     NPFEM_PHASE_BEGIN(t_hist)

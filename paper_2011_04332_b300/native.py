@@ -95,6 +95,7 @@ def load_library() -> C.CDLL:
         "npfem_step_noalloc": [vp, C.c_int, C.c_int32, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp],
         "npfem_batch_set_collisions": [vp, C.POINTER(_CollisionParams)],
         "npfem_batch_contacts": [vp, vp, vp, vp, vp],
+        "npfem_batch_contact_time": [vp, C.POINTER(C.c_double)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -325,6 +326,12 @@ class Batch:
         elif not isinstance(stream, int):
             stream = stream.cuda_stream
         _check(_lib.npfem_batch_contacts(self.handle, _ptr(count), _ptr(vertex), _ptr(plane), C.c_void_p(stream)))
+
+    def contact_time(self) -> float:
+        """npfem_batch_contact_time: ms of the last timed step's contact detection."""
+        ms = C.c_double()
+        _check(_lib.npfem_batch_contact_time(self.handle, C.byref(ms)))
+        return float(ms.value)
 
     def step_host(self, x: np.ndarray, v: np.ndarray, f: np.ndarray, iters=None, iters_default: int = 5,
                   residual=None, status=None, stream: int = 0, tol: float = 0.0, iters_done=None):
