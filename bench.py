@@ -533,7 +533,8 @@ def measure_adjoint(dev, nsteps: int = 40, ckpt_every: int = 20, ncells: int = 2
 
 # Sources that define what the step kernels execute: the device code and the host
 # packer that lays out the factor they stream (launch plumbing is excluded).
-KERNEL_SOURCES = ("npfem_internal.h", "step_kernel.cuh", "split_kernels.cuh", "adjoint.cuh", "host_setup.cpp")
+KERNEL_SOURCES = ("npfem_internal.h", "step_kernel.cuh", "split_kernels.cuh", "adjoint.cuh", "host_setup.cpp",
+                  "contact_kernels.cuh")
 
 
 def kernel_source_hash() -> str:
