@@ -388,13 +388,15 @@ static npfem_status detect_contacts_t(npfem_batch* b, const S* x, cudaStream_t s
   C.r2 = b->coll_p.radius * b->coll_p.radius;
   C.mask = (uint32_t)(T - 1);
   NPFEM_CUDA_TRY(cudaMemsetAsync(C.count, 0, sizeof(int32_t) * T, st));
+  NPFEM_CUDA_TRY(cudaMemsetAsync(C.maxabs, 0, sizeof(int32_t), st));
   for (const TypeLaunch& L : b->launches) {
     const npfem_cell_type* t = b->types[L.type_index];
-    const int grid = std::max(1, std::min(b->sms * 8, (L.ncells + 3) / 4));
+    const int grid = std::max(1, std::min(b->sms * 16, L.ncells));
+    const size_t smem = sizeof(double) * 3 * (size_t)t->host.T;
     if constexpr (sizeof(S) == 8)
-      npfem_k_normals<double><<<grid, 128, 0, st>>>(t->v64, L.cell_list, L.ncells, b->d_offsets, N, x, C.nrm);
+      npfem_k_normals<double><<<grid, 128, smem, st>>>(t->v64, L.cell_list, L.ncells, b->d_offsets, N, x, C.nrm);
     else
-      npfem_k_normals<float><<<grid, 128, 0, st>>>(t->v32, L.cell_list, L.ncells, b->d_offsets, N, x, C.nrm);
+      npfem_k_normals<float><<<grid, 128, smem, st>>>(t->v32, L.cell_list, L.ncells, b->d_offsets, N, x, C.nrm);
   }
   const int vgrid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)b->sms * 16, (N + 255) / 256));
   npfem_k_hash<S><<<vgrid, 256, 0, st>>>(C, x);
@@ -1286,6 +1288,16 @@ npfem_status npfem_batch_set_collisions(npfem_batch* b, const npfem_collision_pa
     return fail(NPFEM_ERR_INVALID_ARG, "batch_set_collisions: need finite radius > 0, delta >= 0, weight >= 0");
   if (b->n_total >= ((int64_t)1 << 30))
     return fail(NPFEM_ERR_UNSUPPORTED, "batch_set_collisions: more than 2^30 vertices");
+  size_t nsmem = 0;  // the normals kernel keeps a cell's triangle normals in shared memory
+  for (const npfem_cell_type* t : b->types) nsmem = std::max(nsmem, sizeof(double) * 3 * (size_t)t->host.T);
+  if (nsmem > (size_t)b->smem_optin)
+    return fail(NPFEM_ERR_UNSUPPORTED, "batch_set_collisions: a cell type has too many triangles for the "
+                                       "normals kernel's shared memory (" + std::to_string(nsmem) + " bytes)");
+  // the attribute is per kernel, shared by every batch: the device maximum serves them all
+  NPFEM_CUDA_TRY(cudaFuncSetAttribute(npfem_k_normals<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      b->smem_optin));
+  NPFEM_CUDA_TRY(cudaFuncSetAttribute(npfem_k_normals<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      b->smem_optin));
   if (!b->coll_alloc && b->n_total > 0) {
     const int64_t N = b->n_total;
     int64_t T = kScanBlock;
@@ -1310,6 +1322,8 @@ npfem_status npfem_batch_set_collisions(npfem_batch* b, const npfem_collision_pa
     C.sorted = static_cast<int32_t*>(q);
     NPFEM_CUDA_TRY(take(sizeof(float4) * N, &q));
     C.sortpos = static_cast<float4*>(q);
+    NPFEM_CUDA_TRY(take(256, &q));
+    C.maxabs = static_cast<int32_t*>(q);
     NPFEM_CUDA_TRY(take(sizeof(double) * 3 * N, &q));
     C.nrm = static_cast<double*>(q);
     NPFEM_CUDA_TRY(take(sizeof(int32_t) * N, &q));

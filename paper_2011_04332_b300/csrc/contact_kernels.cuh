@@ -12,12 +12,14 @@
 //   k_normals  per cell: n_i = normalise(sum over incident triangles (x1-x0) x (x2-x0))
 //   k_hash     per vertex: grid cell (edge = radius) -> bucket of a power-of-two hash table
 //   k_scan_*   exclusive prefix sum of the bucket counts (block scan, carry scan, add)
-//   k_scatter  vertices into bucket order, with their position relative to their grid
-//              cell (float) and their cell index
-//   k_query    per vertex: the 27 neighbouring grid cells; a float pre-filter on the
-//              cell-relative positions, then the exact FP64 squared distance, evaluated
-//              as (dx*dx + dy*dy) + dz*dz without contraction so that every decision is
-//              the one an FP64 evaluation in that order takes
+//   k_scatter  vertices into bucket order, with their position (float) and cell index
+//   k_query    per vertex: the 27 neighbouring grid cells; squared distances in float,
+//              with a bound m on their difference from the FP64 value (from the largest
+//              coordinate magnitude, gathered by k_hash); a decision (inside the radius,
+//              nearer than another candidate) is taken in float when the float values
+//              are more than m apart, and otherwise from the exact FP64 squared distance,
+//              evaluated as (dx*dx + dy*dy) + dz*dz without contraction -- so every
+//              decision is the one an FP64 evaluation in that order takes
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -43,7 +45,8 @@ struct ContactParams {
   int32_t* cursor;           // [T] scatter cursors
   int32_t* bsum;             // [T / kScanBlock] block sums
   int32_t* sorted;           // [N] vertex ids in bucket order
-  float4* sortpos;           // [N] cell-relative position + cell id, bucket order
+  float4* sortpos;           // [N] position (float) + cell id, bucket order
+  int32_t* maxabs;           // [1] largest |coordinate| of the step's input (float bits)
   double* nrm;               // [N][3] unit vertex normals
   int32_t* ccount;           // [N] matches per vertex (0..2)
   int32_t* cvertex;          // [N][2] matched vertex (-1: unused)
@@ -56,33 +59,38 @@ __device__ __forceinline__ uint32_t grid_hash(int ix, int iy, int iz, uint32_t m
   return (((uint32_t)ix * 73856093u) ^ ((uint32_t)iy * 19349663u) ^ ((uint32_t)iz * 83492791u)) & mask;
 }
 
-// Unit area-weighted vertex normals of the cells of one type (one warp per cell).  The
-// incidence list of a vertex holds its triangle corners in triangle order, so the sum
-// runs over the incident triangles in that order.
+// Unit area-weighted vertex normals of the cells of one type, one CTA per cell: the
+// triangles' cross products (x1-x0) x (x2-x0) once into shared memory ([T][3] FP64),
+// then per vertex their sum over its incident triangles, in triangle order (the order of
+// the corner codes in the gradient gather's incidence list), normalised.
 template <typename S>
 __global__ void __launch_bounds__(128) npfem_k_normals(DevTypeView<S> ty, const int32_t* cells, int ncells,
                                                        const int64_t* offsets, int64_t Nt, const S* x, double* nrm) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int c = warp; c < ncells; c += nwarps) {
+  extern __shared__ double tri_n[];
+  for (int c = blockIdx.x; c < ncells; c += gridDim.x) {
     const int64_t off = offsets[cells[c]];
-    for (int v = lane; v < ty.n; v += 32) {
+    for (int t = threadIdx.x; t < ty.T; t += blockDim.x) {
+      const int64_t i0 = off + __ldg(&ty.tris[3 * t]), i1 = off + __ldg(&ty.tris[3 * t + 1]),
+                    i2 = off + __ldg(&ty.tris[3 * t + 2]);
+      const double ax = (double)x[i1] - (double)x[i0], ay = (double)x[Nt + i1] - (double)x[Nt + i0],
+                   az = (double)x[2 * Nt + i1] - (double)x[2 * Nt + i0];
+      const double bx = (double)x[i2] - (double)x[i0], by = (double)x[Nt + i2] - (double)x[Nt + i0],
+                   bz = (double)x[2 * Nt + i2] - (double)x[2 * Nt + i0];
+      tri_n[3 * t] = ay * bz - az * by;
+      tri_n[3 * t + 1] = az * bx - ax * bz;
+      tri_n[3 * t + 2] = ax * by - ay * bx;
+    }
+    __syncthreads();
+    for (int v = threadIdx.x; v < ty.n; v += blockDim.x) {
       double sx = 0.0, sy = 0.0, sz = 0.0;
       const int e0 = __ldg(&ty.inc_ptr[v]), e1 = __ldg(&ty.inc_ptr[v + 1]);
       for (int e = e0; e < e1; ++e) {
         const int code = __ldg(&ty.inc_code[e]);
         if (code < 0) continue;
         const int t = code / 3;
-        const int64_t i0 = off + __ldg(&ty.tris[3 * t]), i1 = off + __ldg(&ty.tris[3 * t + 1]),
-                      i2 = off + __ldg(&ty.tris[3 * t + 2]);
-        const double ax = (double)x[i1] - (double)x[i0], ay = (double)x[Nt + i1] - (double)x[Nt + i0],
-                     az = (double)x[2 * Nt + i1] - (double)x[2 * Nt + i0];
-        const double bx = (double)x[i2] - (double)x[i0], by = (double)x[Nt + i2] - (double)x[Nt + i0],
-                     bz = (double)x[2 * Nt + i2] - (double)x[2 * Nt + i0];
-        sx += ay * bz - az * by;
-        sy += az * bx - ax * bz;
-        sz += ax * by - ay * bx;
+        sx += tri_n[3 * t];
+        sy += tri_n[3 * t + 1];
+        sz += tri_n[3 * t + 2];
       }
       const double inv = 1.0 / sqrt(sx * sx + sy * sy + sz * sz);
       double* o = nrm + 3 * (off + v);
@@ -90,19 +98,25 @@ __global__ void __launch_bounds__(128) npfem_k_normals(DevTypeView<S> ty, const 
       o[1] = sy * inv;
       o[2] = sz * inv;
     }
+    __syncthreads();
   }
 }
 
 template <typename S>
 __global__ void npfem_k_hash(ContactParams C, const S* x) {
   const int64_t Nt = C.n_total;
+  float amax = 0.f;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Nt; i += (int64_t)gridDim.x * blockDim.x) {
     const int ix = grid_coord((double)x[i], C.h_inv), iy = grid_coord((double)x[Nt + i], C.h_inv),
               iz = grid_coord((double)x[2 * Nt + i], C.h_inv);
     const uint32_t k = grid_hash(ix, iy, iz, C.mask);
     C.key[i] = (int32_t)k;
     atomicAdd(&C.count[k], 1);
+    amax = fmaxf(amax, fmaxf(fabsf((float)x[i]), fmaxf(fabsf((float)x[Nt + i]), fabsf((float)x[2 * Nt + i]))));
   }
+  // non-negative floats order like their bit patterns: one integer maximum per warp
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(C.maxabs, __float_as_int(amax));
 }
 
 // Exclusive scan within blocks of kScanBlock entries; block totals to bsum.
@@ -209,36 +223,51 @@ template <typename S>
 __global__ void npfem_k_scatter(ContactParams C, const S* x) {
   const int64_t Nt = C.n_total;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Nt; i += (int64_t)gridDim.x * blockDim.x) {
-    const double px = (double)x[i], py = (double)x[Nt + i], pz = (double)x[2 * Nt + i];
-    const int ix = grid_coord(px, C.h_inv), iy = grid_coord(py, C.h_inv), iz = grid_coord(pz, C.h_inv);
     const int pos = atomicAdd(&C.cursor[C.key[i]], 1);
     C.sorted[pos] = (int32_t)i;
-    C.sortpos[pos] = make_float4((float)(px - ix * C.h), (float)(py - iy * C.h), (float)(pz - iz * C.h),
-                                 __int_as_float(C.vcell[i]));
+    C.sortpos[pos] = make_float4((float)x[i], (float)x[Nt + i], (float)x[2 * Nt + i], __int_as_float(C.vcell[i]));
   }
 }
 
 struct Match {
-  double d2;
-  int b, j;
+  float d2f;  // float squared distance
+  int b, j;   // cell, vertex (j < 0: empty slot)
 };
 
-// (d2, b) order across cells; within one cell the nearer vertex, then the smaller index.
-__device__ __forceinline__ bool match_before(double d2, int b, const Match& m) {
-  return d2 < m.d2 || (d2 == m.d2 && b < m.b);
+// Exact FP64 squared distance from (px, py, pz) to vertex j, rounded operation by operation.
+template <typename S>
+__device__ __forceinline__ double exact_d2(const S* x, int64_t Nt, double px, double py, double pz, int j) {
+  const double dx = px - (double)x[j], dy = py - (double)x[Nt + j], dz = pz - (double)x[2 * Nt + j];
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
-__device__ __forceinline__ void offer(Match* s, double d2, int b, int j) {
+// Is candidate (df, j) before slot s in the order (d2, key)?  key is the vertex index
+// within one cell and the cell index across cells.  Float decides when the float values
+// are more than m apart (they are then ordered like the FP64 values); otherwise both
+// exact FP64 distances are compared.
+template <typename S>
+__device__ __forceinline__ bool before(float df, int j, int key, const Match& s, int skey, float m, const S* x,
+                                       int64_t Nt, double px, double py, double pz) {
+  if (s.j < 0) return true;
+  if (df < s.d2f - m) return true;
+  if (df > s.d2f + m) return false;
+  const double dj = exact_d2(x, Nt, px, py, pz, j), ds = exact_d2(x, Nt, px, py, pz, s.j);
+  return dj < ds || (dj == ds && key < skey);
+}
+
+template <typename S>
+__device__ __forceinline__ void offer(Match* s, float df, int b, int j, float m, const S* x, int64_t Nt, double px,
+                                      double py, double pz) {
   if (b == s[0].b || b == s[1].b) {
-    const int k = b == s[0].b ? 0 : 1;
-    if (d2 < s[k].d2 || (d2 == s[k].d2 && j < s[k].j)) {
-      s[k].d2 = d2;
-      s[k].j = j;
+    Match& t = b == s[0].b ? s[0] : s[1];
+    if (before(df, j, j, t, t.j, m, x, Nt, px, py, pz)) {
+      t.d2f = df;
+      t.j = j;
     }
-  } else if (match_before(d2, b, s[1])) {
-    s[1] = Match{d2, b, j};
+  } else if (before(df, j, b, s[1], s[1].b, m, x, Nt, px, py, pz)) {
+    s[1] = Match{df, b, j};
   }
-  if (match_before(s[1].d2, s[1].b, s[0])) {
+  if (s[1].j >= 0 && before(s[1].d2f, s[1].j, s[1].b, s[0], s[0].b, m, x, Nt, px, py, pz)) {
     const Match t = s[0];
     s[0] = s[1];
     s[1] = t;
@@ -248,16 +277,20 @@ __device__ __forceinline__ void offer(Match* s, double d2, int b, int j) {
 template <typename S>
 __global__ void __launch_bounds__(128) npfem_k_query(ContactParams C, const S* x) {
   const int64_t Nt = C.n_total;
-  // float pre-filter: cell-relative positions carry at most a few 2^-24 h of error, so
-  // a margin of 1e-4 r^2 never rejects a vertex that is inside the radius
-  const float r2f = (float)(C.r2 * (1.0 + 1e-4));
-  const float hf = (float)C.h;
+  // bound on |float d2 - FP64 d2| for candidates within ~r: each coordinate is rounded to
+  // float (error <= u M, u = 2^-24, M the largest magnitude), the difference and the
+  // squares and sums add a few u r^2; a factor two of slack on top
+  const double u = 1.0 / 16777216.0;
+  const double r = sqrt(C.r2);
+  const double M = (double)__int_as_float(*C.maxabs);
+  const float m = (float)(2.0 * (16.0 * u * r * (M + r) + 8.0 * u * C.r2));
+  const float r2f = (float)C.r2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Nt; i += (int64_t)gridDim.x * blockDim.x) {
     const int a = C.vcell[i];
     const double px = (double)x[i], py = (double)x[Nt + i], pz = (double)x[2 * Nt + i];
     const int ix = grid_coord(px, C.h_inv), iy = grid_coord(py, C.h_inv), iz = grid_coord(pz, C.h_inv);
-    const float rx = (float)(px - ix * C.h), ry = (float)(py - iy * C.h), rz = (float)(pz - iz * C.h);
-    Match s[kContactSlots] = {{1e300, 0x7fffffff, -1}, {1e300, 0x7fffffff, -1}};
+    const float xf = (float)x[i], yf = (float)x[Nt + i], zf = (float)x[2 * Nt + i];
+    Match s[kContactSlots] = {{0.f, 0x7fffffff, -1}, {0.f, 0x7fffffff, -1}};
     for (int oz = -1; oz <= 1; ++oz)
       for (int oy = -1; oy <= 1; ++oy)
         for (int ox = -1; ox <= 1; ++ox) {
@@ -267,34 +300,32 @@ __global__ void __launch_bounds__(128) npfem_k_query(ContactParams C, const S* x
             const float4 sp = C.sortpos[q];
             const int b = __float_as_int(sp.w);
             if (b == a) continue;
-            const float fx = (sp.x + (float)ox * hf) - rx, fy = (sp.y + (float)oy * hf) - ry,
-                        fz = (sp.z + (float)oz * hf) - rz;
-            if (fx * fx + fy * fy + fz * fz > r2f) continue;
+            const float fx = sp.x - xf, fy = sp.y - yf, fz = sp.z - zf;
+            const float df = fx * fx + fy * fy + fz * fz;
+            if (df > r2f + m) continue;
             const int j = C.sorted[q];
-            const double dx = px - (double)x[j], dy = py - (double)x[Nt + j], dz = pz - (double)x[2 * Nt + j];
-            const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-            if (!(d2 < C.r2)) continue;
-            offer(s, d2, b, j);
+            if (df >= r2f - m && !(exact_d2(x, Nt, px, py, pz, j) < C.r2)) continue;
+            offer(s, df, b, j, m, x, Nt, px, py, pz);
           }
         }
     const int64_t anc = C.offsets[a];
     const double axx = (double)x[anc], ayy = (double)x[Nt + anc], azz = (double)x[2 * Nt + anc];
     int cnt = 0;
 #pragma unroll
-    for (int m = 0; m < kContactSlots; ++m) {
-      double* pl = C.cplane + 8 * i + 4 * m;
-      if (s[m].j >= 0) {
-        const int j = s[m].j;
+    for (int mm = 0; mm < kContactSlots; ++mm) {
+      double* pl = C.cplane + 8 * i + 4 * mm;
+      if (s[mm].j >= 0) {
+        const int j = s[mm].j;
         const double nx = C.nrm[3 * j], ny = C.nrm[3 * j + 1], nz = C.nrm[3 * j + 2];
         pl[0] = nx;
         pl[1] = ny;
         pl[2] = nz;
         pl[3] = nx * ((double)x[j] - axx) + ny * ((double)x[Nt + j] - ayy) + nz * ((double)x[2 * Nt + j] - azz);
-        C.cvertex[2 * i + m] = j;
-        cnt = m + 1;
+        C.cvertex[2 * i + mm] = j;
+        cnt = mm + 1;
       } else {
         pl[0] = pl[1] = pl[2] = pl[3] = 0.0;
-        C.cvertex[2 * i + m] = -1;
+        C.cvertex[2 * i + mm] = -1;
       }
     }
     C.ccount[i] = cnt;

@@ -148,6 +148,23 @@ def test_contacts_and_step_parity(mode, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_contacts_with_large_cells(prec):
+    """3 RBCs of 2562 vertices (5120 triangles: the normals kernel keeps 123 KB of
+    triangle normals in shared memory) and 3 platelets of 162 vertices, overlapping at
+    35 % volume fraction: contacts and step against the oracle."""
+    nat = _native()
+    p = nat.FP64 if prec == "fp64" else nat.FP32FORM
+    b = I.packing_batch(3, 3, hematocrit=0.35, seed=21, rbc_subdiv=4, plt_subdiv=2, iters=3)
+    _, batch = _setup(b, p)
+    ots = [O.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
+    x, v, f = _inputs(b, p)
+    got = _step(batch, p, x, v, f, b.iters)
+    ref = O.batch_step(ots, b.type_of_cell, b.offsets, x, v, f, b.iters, collisions=(RADIUS, DELTA, WEIGHT))
+    assert _check_contacts(b, got, ref["contacts"], x) > 100
+    _check_state(b, p, got, ref, range(b.ncells), ots)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_contact_free_collisions_equal_plain_step(prec):
     """Collisions on but no vertex within the radius of another cell: the step is bit
     for bit the step without collisions (an empty contact pass adds exact zeros)."""
