@@ -18,6 +18,10 @@ What it computes, and where each piece comes from
   parameters (Setting up new materials section).
 * Per step the solid solver receives external forces and returns positions and
   velocities (Implementation and architecture).
+* Viscoelastic damping (optional): the bodies' viscous behaviour is set by two
+  parameters, Calpha and Cbeta (Setting up new materials section), read here as
+  Rayleigh damping C = Calpha M + Cbeta L (L the elastic part of the PD matrix) in
+  implicit Euler: a dissipation term in the objective and C/dt in the matrix.
 * Collisions (optional): contact detection at the start of a step and a penalty
   per contact in the step objective; the paper names collision detection and
   collision forces (Performance figure, "Other"), a collision weight (Collision at
@@ -109,6 +113,8 @@ class RestState:
     w_area: float
     w_vol: float
     dt: float
+    c_alpha: float = 0.0    # Rayleigh damping: C = c_alpha M + c_beta L (1/us, us)
+    c_beta: float = 0.0
 
 
 def _cot(a: np.ndarray, b: np.ndarray) -> np.ndarray:
@@ -117,7 +123,8 @@ def _cot(a: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 
 def rest_state(X: np.ndarray, tris: np.ndarray, w_strain: float, w_bend: float,
-               w_area: float, w_vol: float, density: float, dt: float) -> RestState:
+               w_area: float, w_vol: float, density: float, dt: float,
+               c_alpha: float = 0.0, c_beta: float = 0.0) -> RestState:
     """Rest-shape constants of a cell type (mass-lumped linear FE, Introduction).
 
     * Each triangle gets a local orthonormal frame (u along the first edge, w in
@@ -171,7 +178,7 @@ def rest_state(X: np.ndarray, tris: np.ndarray, w_strain: float, w_bend: float,
         np.add.at(vert_area, tris[:, k], area / 3.0)
     mass = density * V0 * vert_area / A0
     return RestState(n, tris, H, Dm_inv, area, w_strain * area, c, kappa0, K0, w_h,
-                     A0, V0, mass, float(w_area), float(w_vol), float(dt))
+                     A0, V0, mass, float(w_area), float(w_vol), float(dt), float(c_alpha), float(c_beta))
 
 
 def _norm_rows(a: np.ndarray) -> np.ndarray:
@@ -245,10 +252,11 @@ class EnergyParts:
     V: float
     degenerate: int
     contact: float = 0.0
+    damping: float = 0.0
 
     @property
     def total(self) -> float:
-        return self.inertia + self.strain + self.bend + self.area + self.volume + self.contact
+        return self.inertia + self.strain + self.bend + self.area + self.volume + self.contact + self.damping
 
 
 def internal_energy_and_gradient(rs: RestState, x: np.ndarray, w_scale=None):
@@ -307,15 +315,24 @@ def internal_energy_and_gradient(rs: RestState, x: np.ndarray, w_scale=None):
     return parts, g
 
 
-def objective(rs: RestState, x: np.ndarray, y: np.ndarray, w_scale=None, contact=None):
+def objective(rs: RestState, x: np.ndarray, y: np.ndarray, w_scale=None, contact=None, damp=None):
     """Implicit-Euler variational objective of one step (Eq. (2) discretised):
-    f(x) = (x-y)^T M (x-y) / (2 dt^2) + E_int(x) [+ E_contact(x)], and its gradient.
-    contact: (idx, nrm, crel, delta, weight) as in contact_energy_and_gradient."""
+    f(x) = (x-y)^T M (x-y) / (2 dt^2) + E_int(x) [+ E_contact(x)] [+ E_damp(x)], and its
+    gradient.  contact: (idx, nrm, crel, delta, weight) as in contact_energy_and_gradient.
+    damp: (x_n, C) with the step's start x_n and C = damping_matrix: the dissipation term
+    E_damp = (x - x_n)^T C (x - x_n) / (2 dt) per coordinate joins; the stationarity
+    condition is then implicit Euler for M a + C v + grad E = f."""
     parts, g = internal_energy_and_gradient(rs, x, w_scale)
     dx = x - y
     m = rs.mass
     parts.inertia = np.sum(m[:, None] * dx * dx) / (2.0 * rs.dt ** 2)
     g = g + m[:, None] * dx / rs.dt ** 2
+    if damp is not None:
+        x_n, C = damp
+        u = x - x_n
+        Cu = C @ u
+        parts.damping = np.sum(u * Cu) / (2.0 * rs.dt)
+        g = g + Cu / rs.dt
     if contact is not None:
         ec, gc = contact_energy_and_gradient(x, *contact)
         parts.contact = ec
@@ -448,13 +465,13 @@ def contact_energy_and_gradient(x: np.ndarray, idx: np.ndarray, nrm: np.ndarray,
 
 
 # ---------------------------------------------------------------- global matrix
-def pd_matrix(rs: RestState, w_scale=None) -> np.ndarray:
-    """Projective-dynamics system matrix (n x n, shared by x, y, z):
-    A = M/dt^2 + sum_t w_t G_t^T G_t + sum_e w_e c_e c_e^T,
-    where G_t maps a triangle's three vertex coordinates to one row of F."""
+def elastic_matrix(rs: RestState, w_scale=None) -> np.ndarray:
+    """The elastic part of the projective-dynamics matrix (n x n, shared by x, y, z):
+    L = sum_t w_t G_t^T G_t + sum_e w_e c_e c_e^T, where G_t maps a triangle's three
+    vertex coordinates to one row of F."""
     ws = np.ones(4) if w_scale is None else np.asarray(w_scale)
     n = rs.n
-    A = np.diag(rs.mass / rs.dt ** 2).astype(np.result_type(ws, np.float64))
+    A = np.zeros((n, n), dtype=np.result_type(ws, np.float64))
     S = np.array([[-1.0, 1.0, 0.0], [-1.0, 0.0, 1.0]])
     for ti in range(rs.tris.shape[0]):
         G = rs.Dm_inv[ti].T @ S                    # [2,3]
@@ -466,6 +483,21 @@ def pd_matrix(rs: RestState, w_scale=None) -> np.ndarray:
         idx = rs.hinges[e]
         A[np.ix_(idx, idx)] += ws[1] * rs.w_hinge[e] * np.outer(cvec, cvec)
     return A
+
+
+def damping_matrix(rs: RestState, w_scale=None) -> np.ndarray:
+    """Rayleigh damping C = c_alpha M + c_beta L (damping reading: viscous behaviour of
+    the bodies set by Calpha and Cbeta, Setting up new materials section)."""
+    return rs.c_alpha * np.diag(rs.mass) + rs.c_beta * elastic_matrix(rs, w_scale)
+
+
+def pd_matrix(rs: RestState, w_scale=None) -> np.ndarray:
+    """Projective-dynamics system matrix (n x n, shared by x, y, z):
+    A = M/dt^2 + L, plus C/dt with Rayleigh damping, i.e.
+    A = (1/dt^2 + c_alpha/dt) M + (1 + c_beta/dt) L  (L: elastic_matrix)."""
+    dt = rs.dt
+    L = elastic_matrix(rs, w_scale)
+    return np.diag(rs.mass * (1.0 / dt ** 2 + rs.c_alpha / dt)) + (1.0 + rs.c_beta / dt) * L
 
 
 class GlobalSolver:
@@ -543,6 +575,9 @@ def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
     centroid of x_n (the objective is translation invariant), adding it back at the end.
     contact: (idx, nrm, c, delta, weight) with absolute plane offsets c (see
     detect_contacts / cell_contacts): the contact penalty joins the objective.
+    With Rayleigh damping in the rest state (c_alpha, c_beta), the dissipation term of
+    `objective` joins with x_n the step's start, and the solver's matrix (pd_matrix)
+    carries C/dt.
     """
     dt = rs.dt
     ctr = np.real(x_n).mean(axis=0)
@@ -552,7 +587,8 @@ def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
     if contact is not None:
         idx, nrm, c_abs, delta, weight = contact
         contact = (idx, nrm, c_abs - nrm @ ctr, delta, weight)
-    parts, g = objective(rs, x, y, w_scale, contact)
+    damp = (xn, damping_matrix(rs, w_scale)) if (rs.c_alpha != 0.0 or rs.c_beta != 0.0) else None
+    parts, g = objective(rs, x, y, w_scale, contact, damp)
     fx = parts.total
     g0n = float(np.sqrt(np.sum(np.real(g) ** 2)))
     S: List[np.ndarray] = []
@@ -571,7 +607,7 @@ def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
         alpha = 1.0
         for h in range(MAX_HALVINGS + 1):
             xt = x + alpha * d
-            pt, gt = objective(rs, xt, y, w_scale, contact)
+            pt, gt = objective(rs, xt, y, w_scale, contact, damp)
             trials += 1
             ft = pt.total
             armijo = np.real(ft) <= np.real(fx + ARMIJO_C1 * alpha * gd)
@@ -615,8 +651,10 @@ class CellType:
     """Rest state + factored global matrix of one cell type."""
 
     def __init__(self, verts, tris, material, dt, w_scale=None):
-        w_strain, w_bend, w_area, w_vol, density = material
-        self.rest = rest_state(verts, tris, w_strain, w_bend, w_area, w_vol, density, dt)
+        """material: (w_strain, w_bend, w_area, w_vol, density[, c_alpha, c_beta])."""
+        w_strain, w_bend, w_area, w_vol, density = material[:5]
+        c_alpha, c_beta = (tuple(material[5:7]) + (0.0, 0.0))[:2]
+        self.rest = rest_state(verts, tris, w_strain, w_bend, w_area, w_vol, density, dt, c_alpha, c_beta)
         self.solver = GlobalSolver(pd_matrix(self.rest, w_scale))
         self.w_scale = w_scale
 
