@@ -89,6 +89,15 @@ typedef struct {
   double w_area;   /* nN/um: E_A = w_area/2 (A - A0)^2 / A0 */
   double w_vol;    /* nN/um^2: E_V = w_vol/2 (V - V0)^2 / V0 */
   double density;  /* pg/um^3: cell mass density*V0, lumped by vertex area share */
+  /* Viscoelastic (Rayleigh) damping, C = c_alpha M + c_beta L with M the lumped mass
+   * matrix and L = A - M/dt^2 the elastic part of the projective-dynamics matrix.  The
+   * paper sets the bodies' viscous behaviour with two parameters, Calpha and Cbeta
+   * (Setting up new materials section), without a formula; here the implicit step
+   * minimises f(x) + (x - x_n)^T C (x - x_n) / (2 dt) per coordinate, i.e. implicit Euler
+   * for M a + C v + grad E = f, and the prefactored matrix becomes
+   * (1/dt^2 + c_alpha/dt) M + (1 + c_beta/dt) L.  Both 0: no damping. */
+  double c_alpha;  /* 1/us, >= 0 */
+  double c_beta;   /* us, >= 0 */
 } npfem_material;
 
 typedef struct {

@@ -165,6 +165,8 @@ static void fill_view(npfem_cell_type* t, DevTypeView<S>* v, const S* Dinv, cons
   v->w_area = H.w_area;
   v->w_vol = H.w_vol;
   v->dt = H.dt;
+  v->damp_m = H.c_alpha / H.dt;
+  v->damp_l = H.c_beta / H.dt;
 }
 
 template <typename S>
@@ -608,7 +610,7 @@ npfem_status npfem_create_cell_type(const npfem_mesh* mesh, const npfem_material
   if (!t) return fail(NPFEM_ERR_OOM, "create_cell_type: host allocation failed");
   std::string err;
   int rc = build_host_type(mesh->n_verts, mesh->n_tris, mesh->rest_xyz, mesh->tris, mat->w_strain, mat->w_bend,
-                           mat->w_area, mat->w_vol, mat->density, dt, &t->host, &err);
+                           mat->w_area, mat->w_vol, mat->density, dt, mat->c_alpha, mat->c_beta, &t->host, &err);
   if (rc != NPFEM_OK) {
     delete t;
     return fail(rc, err);
@@ -700,7 +702,7 @@ npfem_status npfem_cell_type_analyze(const npfem_mesh* mesh, const npfem_materia
   HostType H;
   std::string err;
   int rc = build_host_type(mesh->n_verts, mesh->n_tris, mesh->rest_xyz, mesh->tris, mat->w_strain, mat->w_bend,
-                           mat->w_area, mat->w_vol, mat->density, dt, &H, &err);
+                           mat->w_area, mat->w_vol, mat->density, dt, mat->c_alpha, mat->c_beta, &H, &err);
   if (rc != NPFEM_OK) return fail(rc, err);
   info->n_verts = H.n;
   info->n_tris = H.T;
@@ -892,6 +894,9 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: tol must be 0 (fixed iteration counts)");
   if (b->coll)
     return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: collisions are enabled (contacts are not differentiated)");
+  for (const npfem_cell_type* t : b->types)
+    if (t->host.c_alpha != 0.0 || t->host.c_beta != 0.0)
+      return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: a cell type has damping (damping is not differentiated)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   for (TypeLaunch& L : b->launches) {
     if (L.adj_scratch) continue;

@@ -5,7 +5,8 @@
 // The global matrix is A = M/dt^2 + sum_t w_t G_t^T G_t + sum_e w_e c_e c_e^T
 // (projective dynamics of Bouaziz et al. 2014, reused as the initial Hessian of the
 // quasi-Newton iteration of Liu et al. 2017; both named in the paper's
-// Implementation and architecture section).  It depends only on the rest mesh,
+// Implementation and architecture section); with Rayleigh damping C = c_alpha M +
+// c_beta L (L the sum over elements) it is (1/dt^2 + c_alpha/dt) M + (1 + c_beta/dt) L.  It depends only on the rest mesh,
 // the weights and dt, so it is factored once per cell type.
 #include <algorithm>
 #include <array>
@@ -333,9 +334,13 @@ void pack_sweep(int n, const std::vector<SweepOp>& ops, bool relabel, int W, std
 
 int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double w_strain,
                     double w_bend, double w_area, double w_vol, double density, double dt,
-                    HostType* out, std::string* err) {
+                    double c_alpha, double c_beta, HostType* out, std::string* err) {
   if (n < 4 || T < 4 || !xyz || !tris || !(dt > 0) || !(density > 0)) {
     *err = "create_cell_type: need n >= 4, T >= 4, dt > 0, density > 0 and non-null arrays";
+    return NPFEM_ERR_INVALID_ARG;
+  }
+  if (!(c_alpha >= 0) || !(c_beta >= 0) || std::isinf(c_alpha) || std::isinf(c_beta)) {
+    *err = "create_cell_type: damping c_alpha and c_beta must be finite and >= 0";
     return NPFEM_ERR_INVALID_ARG;
   }
   if (n > 65535) {
@@ -346,6 +351,8 @@ int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double
   H.n = n;
   H.T = T;
   H.dt = dt;
+  H.c_alpha = c_alpha;
+  H.c_beta = c_beta;
   H.w_area = w_area;
   H.w_vol = w_vol;
   H.tris.assign(tris, tris + 3 * T);
@@ -480,9 +487,11 @@ int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double
     }
   }
 
-  // ---- assemble A (sparse, symmetric)
+  // ---- assemble A (sparse, symmetric): (1/dt^2 + c_alpha/dt) M + (1 + c_beta/dt) L,
+  // the elastic part L scaled by ls (1 without damping)
   std::map<std::pair<int, int>, double> Aij;
-  for (int i = 0; i < n; ++i) Aij[{i, i}] += H.mass[i] / (dt * dt);
+  const double ls = 1.0 + c_beta / dt;
+  for (int i = 0; i < n; ++i) Aij[{i, i}] += H.mass[i] * (1.0 / (dt * dt) + c_alpha / dt);
   for (int t = 0; t < T; ++t) {
     // G = Dm^-T S, S = [[-1,1,0],[-1,0,1]];  Dm^-1 = [[d00, d01], [0, d11]]
     double d00 = H.Dinv[3 * t], d01 = H.Dinv[3 * t + 1], d11 = H.Dinv[3 * t + 2];
@@ -490,14 +499,14 @@ int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) {
         double s = G[0][a] * G[0][b] + G[1][a] * G[1][b];
-        Aij[{tris[3 * t + a], tris[3 * t + b]}] += H.w_tri[t] * s;
+        Aij[{tris[3 * t + a], tris[3 * t + b]}] += ls * (H.w_tri[t] * s);
       }
   }
   for (int e = 0; e < E; ++e)
     for (int a = 0; a < 4; ++a)
       for (int b = 0; b < 4; ++b)
         Aij[{H.hinges[4 * e + a], H.hinges[4 * e + b]}] +=
-            H.w_hinge[e] * H.c_hinge[4 * e + a] * H.c_hinge[4 * e + b];
+            ls * (H.w_hinge[e] * H.c_hinge[4 * e + a] * H.c_hinge[4 * e + b]);
   Graph g(n);
   for (auto& kv : Aij)
     if (kv.first.first != kv.first.second) g[kv.first.first].push_back(kv.first.second);

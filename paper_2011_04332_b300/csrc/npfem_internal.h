@@ -32,6 +32,7 @@ struct HostType {
   std::vector<double> hinge_unit;  // [E] 3/(A_A+A_B): w_hinge per unit bending weight
   std::vector<double> mass;      // [n]
   double A0 = 0, V0 = 0, w_area = 0, w_vol = 0, dt = 0, total_mass = 0;
+  double c_alpha = 0, c_beta = 0;  // Rayleigh damping
   // gradient gather: per vertex, corner codes (t*3+slot >= 0) and hinge codes
   // (-(h*4+k)-1 < 0) with the hinge coefficient
   std::vector<int32_t> inc_ptr;  // [n+1]
@@ -76,7 +77,7 @@ void pack_sweep(int n, const std::vector<SweepOp>& ops, bool relabel, int W, std
 // Build the host type.  Returns 0 or a negative NPFEM_ERR_* code with a message.
 int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double w_strain,
                     double w_bend, double w_area, double w_vol, double density, double dt,
-                    HostType* out, std::string* err);
+                    double c_alpha, double c_beta, HostType* out, std::string* err);
 
 // ------------------------------------------------------------------ device view
 template <typename S>
@@ -113,6 +114,7 @@ struct DevTypeView {
   const uint32_t* cta_bwd_rc[kCtaPacks];
   const double* cta_bwd_val[kCtaPacks];
   double A0, V0, w_area, w_vol, dt;
+  double damp_m, damp_l;    // Rayleigh damping over dt: c_alpha/dt (mass part), c_beta/dt (elastic part)
 };
 
 }  // namespace npfem

@@ -199,6 +199,57 @@ struct EvalOut {
   bool degenerate;
 };
 
+// Rayleigh damping terms of the objective, out of line so that the iteration kernels'
+// register allocation does not carry them when damping is off.  Each returns its lane's
+// share of the damping energy.  Elastic part: per triangle (c_beta/dt) w_t |G_t U|^2 / 2
+// with its corner gradients, per hinge (c_beta/dt) w_e |sum_j c_j U_j|^2 / 2 into the
+// hinge buffer (the gather applies the c_j).
+template <typename S>
+__device__ __noinline__ double damping_elastic(const int32_t* tris, const S* Dinv, const S* w_tri,
+                                               const int32_t* hinges, const S* c_hinge, const S* w_hinge, int T,
+                                               int E, S dl, const S* U, S* corner, S* hbuf, int lane) {
+  const S half = (S)0.5;
+  double e = 0.0;
+  for (int t = lane; t < T; t += 32) {
+    const int i0 = __ldg(&tris[3 * t]), i1 = __ldg(&tris[3 * t + 1]), i2 = __ldg(&tris[3 * t + 2]);
+    const V3<S> u0 = ld3(U, i0);
+    const V3<S> u1 = ld3(U, i1) - u0, u2 = ld3(U, i2) - u0;
+    const S d00 = __ldg(&Dinv[3 * t]), d01 = __ldg(&Dinv[3 * t + 1]), d11 = __ldg(&Dinv[3 * t + 2]);
+    const S wd = dl * __ldg(&w_tri[t]);
+    const V3<S> F0 = d00 * u1, F1 = d01 * u1 + d11 * u2;
+    e += (double)(half * wd * (dot(F0, F0) + dot(F1, F1)));
+    const V3<S> P0 = wd * F0, P1 = wd * F1;
+    const V3<S> g1 = d00 * P0 + d01 * P1, g2 = d11 * P1;
+    st3(corner, 3 * t + 0, ld3(corner, 3 * t + 0) - (g1 + g2));
+    st3(corner, 3 * t + 1, ld3(corner, 3 * t + 1) + g1);
+    st3(corner, 3 * t + 2, ld3(corner, 3 * t + 2) + g2);
+  }
+  for (int h = lane; h < E; h += 32) {
+    const int i = __ldg(&hinges[4 * h]), j = __ldg(&hinges[4 * h + 1]);
+    const int ka = __ldg(&hinges[4 * h + 2]), kb = __ldg(&hinges[4 * h + 3]);
+    const S c1 = __ldg(&c_hinge[4 * h + 1]), c2 = __ldg(&c_hinge[4 * h + 2]), c3 = __ldg(&c_hinge[4 * h + 3]);
+    const V3<S> ui = ld3(U, i);
+    const V3<S> KU = c1 * (ld3(U, j) - ui) + c2 * (ld3(U, ka) - ui) + c3 * (ld3(U, kb) - ui);
+    const S wd = dl * __ldg(&w_hinge[h]);
+    e += (double)(half * wd * dot(KU, KU));
+    st3(hbuf, h, ld3(hbuf, h) + wd * KU);
+  }
+  return e;
+}
+
+// Mass part: (c_alpha/dt) m_v |U_v|^2 / 2 per vertex, its gradient added to G.
+template <typename S>
+__device__ __noinline__ double damping_mass(const S* mass, int n, S dm, const S* U, S* G, int lane) {
+  double e = 0.0;
+  for (int v = lane; v < n; v += 32) {
+    const V3<S> u = ld3(U, v);
+    const S md = dm * __ldg(&mass[v]);
+    e += 0.5 * (double)md * (double)dot(u, u);
+    st3(G, v, ld3(G, v) + md * u);
+  }
+  return e;
+}
+
 // f(X+U) and its gradient into Gout.  W = y - x_n.  The strain projection maps the
 // triangle deformation gradient F = [e1 e2] Dm^-1 to R = F (F^T F)^(-1/2) via the
 // closed-form 2x2 SPD square root (C + sqrt(det C) I)/sqrt(tr C + 2 sqrt(det C)).
@@ -298,6 +349,11 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const StepParams& P,
     e_el.add(half * we * dot(r, r));
     st3(w.hbuf, h, we * r);
   }
+  // Rayleigh damping, elastic part: (c_beta/dt)/2 U^T L U with U = x - x_n, element by
+  // element into the same corner and hinge buffers (each owned by the lane that wrote it)
+  if (ty.damp_l != 0.0)
+    e_el.add((S)damping_elastic<S>(ty.tris, ty.Dinv, ty.w_tri, ty.hinges, ty.c_hinge, ty.w_hinge, T, E,
+                                   (S)ty.damp_l, U, w.corner, w.hbuf, lane));
   __syncwarp();
 
   NPFEM_PHASE_BEGIN(t_gather)
@@ -320,6 +376,8 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const StepParams& P,
     }
     st3(Gout, v, g);
   }
+  // Rayleigh damping, mass part: (c_alpha/dt)/2 sum_v m_v |U_v|^2 (same vertex per lane)
+  if (ty.damp_m != 0.0) e_el.add((S)damping_mass<S>(ty.mass, n, (S)ty.damp_m, U, Gout, lane));
   NPFEM_PHASE_END(t_gather, kPhGather, P, lane)
   EvalOut o;
   o.energy = e_el.total() + e_area + e_vol;

@@ -38,7 +38,7 @@ class _Mesh(C.Structure):
 
 class _Material(C.Structure):
     _fields_ = [("w_strain", C.c_double), ("w_bend", C.c_double), ("w_area", C.c_double),
-                ("w_vol", C.c_double), ("density", C.c_double)]
+                ("w_vol", C.c_double), ("density", C.c_double), ("c_alpha", C.c_double), ("c_beta", C.c_double)]
 
 
 class _Opts(C.Structure):
@@ -130,14 +130,16 @@ def analyze_cell_type(verts: np.ndarray, tris: np.ndarray, material: Sequence[fl
     tr = np.ascontiguousarray(tris, dtype=np.int32)
     m = _Mesh(xyz.shape[0], tr.shape[0], xyz.ctypes.data_as(C.POINTER(C.c_double)),
               tr.ctypes.data_as(C.POINTER(C.c_int32)))
-    mat = _Material(*[float(a) for a in material])
+    vals = [float(a) for a in material]
+    mat = _Material(*(vals + [0.0] * (7 - len(vals))))
     inf = _TypeInfo()
     _check(lib.npfem_cell_type_analyze(C.byref(m), C.byref(mat), float(dt), C.byref(inf)))
     return {k: getattr(inf, k) for k, _ in _TypeInfo._fields_}
 
 
 class CellType:
-    """A prefactored cell type: npfem_create_cell_type(mesh, material, dt)."""
+    """A prefactored cell type: npfem_create_cell_type(mesh, material, dt); material is
+    (w_strain, w_bend, w_area, w_vol, density[, c_alpha, c_beta]) (damping 0 if absent)."""
 
     def __init__(self, verts: np.ndarray, tris: np.ndarray, material: Sequence[float], dt: float):
         lib = load_library()
@@ -146,7 +148,8 @@ class CellType:
         m = _Mesh(self._xyz.shape[0], self._tris.shape[0],
                   self._xyz.ctypes.data_as(C.POINTER(C.c_double)),
                   self._tris.ctypes.data_as(C.POINTER(C.c_int32)))
-        mat = _Material(*[float(a) for a in material])
+        vals = [float(a) for a in material]
+        mat = _Material(*(vals + [0.0] * (7 - len(vals))))
         h = C.c_void_p()
         _check(lib.npfem_create_cell_type(C.byref(m), C.byref(mat), float(dt), C.byref(h)))
         self.handle = h
