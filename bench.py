@@ -33,6 +33,15 @@ METRIC = "RBC-equivalent cell-steps/sec on 1 B300 at stated residual"
 UNIT = "RBC-equivalent cell-steps/s"
 
 
+# Rayleigh damping (c_alpha 1/us, c_beta us) given to every cell type (--damping)
+DAMPING = (0.0, 0.0)
+
+
+def _mat(spec):
+    """Material tuple of a cell-type spec, with the benchmark's damping appended."""
+    return spec.material.as_tuple() + DAMPING
+
+
 # ------------------------------------------------------------------ workloads
 # collision parameters (search radius um, contact thickness um, weight nN/um) per workload
 COLLISIONS = {"pack4096": (0.5, 0.05, 60.0)}
@@ -115,7 +124,7 @@ def oracle_baseline(b, sample_cells: int, workers: int, tol: float = 0.0, collis
         # the sampled cells' contact detection (over the whole batch) is part of their step
         from oracle import npfem_oracle as O
         radius, delta, weight = collisions
-        ots = [O.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
+        ots = [O.CellType(t.mesh.verts, t.mesh.tris, _mat(t), b.dt) for t in b.types]
         verts = [i for c in sel for i in range(int(b.offsets[c]), int(b.offsets[c + 1]))]
         t0 = time.perf_counter()
         con = O.detect_contacts(ots, b.type_of_cell, b.offsets, b.x, radius, vertices=verts)
@@ -131,7 +140,7 @@ def oracle_baseline(b, sample_cells: int, workers: int, tol: float = 0.0, collis
         chunks = [cells[i::workers] for i in range(workers)]
         for ch in chunks:
             if ch:
-                jobs.append((ty.mesh.verts, ty.mesh.tris, ty.material.as_tuple(), b.dt,
+                jobs.append((ty.mesh.verts, ty.mesh.tris, _mat(ty), b.dt,
                              [(*b.cell_state(c), b.iters[c], contacts.get(c)) for c in ch], tol))
     ctx = mp.get_context("spawn")
     env_backup = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
@@ -247,7 +256,7 @@ def run_ours(args, rank, world, local_rank):
 
     prec = native.FP32FORM if args.precision == "fp32form" else native.FP64
     tdt = torch.float32 if prec == native.FP32FORM else torch.float64
-    types = [native.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
+    types = [native.CellType(t.mesh.verts, t.mesh.tris, _mat(t), b.dt) for t in b.types]
     infos = [t.info() for t in types]
     batch = native.Batch(types, b.type_of_cell, prec)
     coll = COLLISIONS.get(args.workload)
@@ -284,7 +293,7 @@ def run_ours(args, rank, world, local_rank):
         xin, vin, fin = (t.double().cpu().numpy() for t in (x0, v0, f))
         scon = None
         if coll is not None:
-            allt = [O.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
+            allt = [O.CellType(t.mesh.verts, t.mesh.tris, _mat(t), b.dt) for t in b.types]
             scon = O.detect_contacts(allt, b.type_of_cell, b.offsets, xin, coll[0],
                                      vertices=[i for c in sample for i in range(int(b.offsets[c]), int(b.offsets[c + 1]))])
         xg = xs.double().cpu().numpy()
@@ -293,7 +302,7 @@ def run_ours(args, rank, world, local_rank):
             t = int(b.type_of_cell[c])
             if t not in ot:
                 ty = b.types[t]
-                ot[t] = O.CellType(ty.mesh.verts, ty.mesh.tris, ty.material.as_tuple(), b.dt)
+                ot[t] = O.CellType(ty.mesh.verts, ty.mesh.tris, _mat(ty), b.dt)
             s = b.cell_slice(c)
             con = None if scon is None else (*O.cell_contacts(scon, s.start, s.stop), coll[1], coll[2])
             r = O.step(ot[t].rest, ot[t].solver, xin[:, s].T, vin[:, s].T, fin[:, s].T, int(b.iters[c]), tol=tol,
@@ -462,6 +471,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32+f64" if prec == native.FP32FORM else "f64", "data": "synthetic",
         "config": {"workload": desc, "cells": b.ncells, "rbc_equivalents_per_step": rbc_eq_per_rank,
                    "precision": args.precision, "l2": "flushed between steps (256 MB write, untimed)",
+                   "damping": ({"c_alpha_per_us": DAMPING[0], "c_beta_us": DAMPING[1]} if any(DAMPING) else None),
                    "launch": "one CUDA graph per step" if graph is not None else "direct npfem_step call",
                    "mode": "split kernels (k_begin, then k_solve + k_iter per iteration and cell type)",
                    "split_shapes": {str(t): list(batch.get_split_launch(t)[0]) for t in sorted(set(int(q) for q in b.type_of_cell))},
@@ -623,9 +633,13 @@ def main():
     ap.add_argument("--tol", type=float, default=0.0,
                     help="converged-residual mode: per-cell stop at |g|/|g0| < tol (0: fixed iteration counts)")
     ap.add_argument("--budget", type=int, default=16, help="with --tol: iteration budget per cell")
+    ap.add_argument("--damping", default="0,0",
+                    help="Rayleigh damping c_alpha,c_beta (1/us, us) for every cell type")
     ap.add_argument("--groups", type=int, default=0,
                     help="with --no-tune: phase-offset chains per cell type (0: library default)")
     args = ap.parse_args()
+    global DAMPING
+    DAMPING = tuple(float(q) for q in args.damping.split(","))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
