@@ -652,11 +652,56 @@ class CellType:
 
     def __init__(self, verts, tris, material, dt, w_scale=None):
         """material: (w_strain, w_bend, w_area, w_vol, density[, c_alpha, c_beta])."""
+        self.material = tuple(material)
         w_strain, w_bend, w_area, w_vol, density = material[:5]
         c_alpha, c_beta = (tuple(material[5:7]) + (0.0, 0.0))[:2]
         self.rest = rest_state(verts, tris, w_strain, w_bend, w_area, w_vol, density, dt, c_alpha, c_beta)
         self.solver = GlobalSolver(pd_matrix(self.rest, w_scale))
         self.w_scale = w_scale
+
+
+def implicit_adjoint(ct: CellType, x_n: np.ndarray, v_n: np.ndarray, f_ext: np.ndarray, x_star: np.ndarray,
+                     gx_next: np.ndarray, gv_next: np.ndarray):
+    """Reverse-mode derivative of a loss L(x*, v*) through the converged minimiser x* of
+    one step's objective (the solver run to convergence, Implementation and architecture
+    section), by the implicit-function theorem instead of the unrolled iteration.
+
+    With grad f(x*; y, w) = 0, H = grad^2 f(x*) and v* = (x* - x_n)/dt:
+      H lam = dL/dx* + dL/dv* / dt,
+      dL/dy = (M/dt^2) lam   (d grad f / dy = -M/dt^2),
+      dL/dx_n = dL/dy - dL/dv*/dt,  dL/dv_n = dt dL/dy,  dL/df = (dt^2/m) dL/dy = lam,
+      dL/dw_q = -lam . d(grad f)/dw_q  for the material weights (strain, bend, area, vol).
+    H and d(grad f)/dw come from complex-step differentiation of the analytic gradient
+    (exact to rounding); lam from a dense solve.  Arrays [n,3]; returns gx, gv, gf, gw[4]."""
+    rs = ct.rest
+    dt = rs.dt
+    n = rs.n
+    ctr = np.real(x_n).mean(axis=0)
+    xs = x_star - ctr
+    y = (x_n - ctr) + dt * v_n + dt * dt * f_ext / rs.mass[:, None]
+    ws0 = np.ones(4) if ct.w_scale is None else np.asarray(ct.w_scale, dtype=np.float64)
+    h = 1e-30
+    H = np.zeros((3 * n, 3 * n))
+    for k in range(3 * n):
+        e = np.zeros(3 * n, dtype=complex)
+        e[k] = 1j * h
+        g = objective(rs, xs + e.reshape(n, 3), y, ws0)[1]
+        H[:, k] = np.imag(g).ravel() / h
+    H = 0.5 * (H + H.T)
+    b = (gx_next + gv_next / dt).ravel()
+    lam = np.linalg.solve(H, b).reshape(n, 3)
+    dLdy = rs.mass[:, None] / dt ** 2 * lam
+    gx = dLdy - gv_next / dt
+    gv = dt * dLdy
+    gf = lam.copy()
+    gw = np.zeros(4)
+    w_mat = np.asarray(ct.material[:4], dtype=np.float64)
+    for q in range(4):
+        ws = ws0.astype(complex)
+        ws[q] += 1j * h
+        dg = np.imag(objective(rs, xs, y, ws)[1]) / h
+        gw[q] = -np.sum(lam * dg) / (w_mat[q] * ws0[q])
+    return gx, gv, gf, gw
 
 
 def batch_step(types: List[CellType], type_of_cell, offsets, x, v, f, iters,
