@@ -70,6 +70,7 @@ typedef int npfem_status;
 #define NPFEM_CELL_NONFINITE 4        /* NaN/Inf in the result */
 #define NPFEM_CELL_ITER_LIMIT 8       /* iteration count above the supported bound (adjoint: 16;
                                          split step: opts->max_iters); the cell stopped there */
+#define NPFEM_CELL_CG_NOT_CONVERGED 16 /* implicit adjoint: CG stopped before its tolerance */
 
 typedef enum { NPFEM_FP64 = 0, NPFEM_FP32FORM = 1 } npfem_precision;
 
@@ -189,6 +190,32 @@ npfem_status npfem_step_adjoint(npfem_batch* batch, const void* x, const void* v
                                 const int32_t* iters, const npfem_solver_opts* opts,
                                 const double* gx_next, const double* gv_next, double* gx, double* gv,
                                 double* gf, double* gw, int32_t* status_out, void* stream);
+
+/* Gradients through the CONVERGED step (FP64 batches): the solver run to convergence
+ * (Implementation and architecture section) differentiated by the implicit-function
+ * theorem instead of through the unrolled iteration.  The forward step is run here,
+ * with the batch's mode, on internal copies of x and v (iters, opts as in npfem_step;
+ * opts->tol > 0 and a generous budget make it converge); then, with x* its result,
+ * H = grad^2 f(x*) and v* = (x* - x_n)/dt, each cell solves
+ *   H lam = gx_next + gv_next / dt
+ * by conjugate gradients preconditioned with the prefactored matrix A^-1, and returns
+ *   gx = (M/dt^2) lam - gv_next/dt,  gv = (M/dt) lam,  gf = lam,
+ *   gw[cell][q] = -lam . d(grad f)/d(w_q) for (w_strain, w_bend, w_area, w_vol).
+ * The gradients are exact for the minimiser; for an unconverged x* they are those of
+ * the minimiser's linearisation at x*.
+ *   cg_tol       stop when |residual| <= cg_tol |gx_next + gv_next/dt| (finite, > 0)
+ *   cg_max_iters at most this many CG iterations per cell (>= 1)
+ *   status_out   out [ncells] or NULL: the forward step's flags, with 16 ORed in where CG
+ *                stopped before cg_tol (budget used, or H not positive along a direction).
+ * Arrays as in npfem_step_adjoint.  The first call allocates two [3][N_total] FP64 copies
+ * and the adjoint workspace.  Asynchronous on `stream`.  Errors: INVALID_ARG (null
+ * pointer, FP32-form batch, bad cg_tol / cg_max_iters, collisions on, a damped type),
+ * CUDA, OOM. */
+npfem_status npfem_step_adjoint_implicit(npfem_batch* batch, const void* x, const void* v, const void* f_ext,
+                                         const int32_t* iters, const npfem_solver_opts* opts,
+                                         const double* gx_next, const double* gv_next, double* gx, double* gv,
+                                         double* gf, double* gw, double cg_tol, int32_t cg_max_iters,
+                                         int32_t* status_out, void* stream);
 
 /* Launch shape of the cells of one type (the autotuner's knobs): warps per CTA
  * (1..4; one warp advances one cell), CTAs per SM (1..16), whether each warp's FP64

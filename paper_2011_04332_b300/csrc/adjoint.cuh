@@ -467,4 +467,127 @@ __global__ void __launch_bounds__(128) npfem_adjoint_kernel(DevTypeView<double> 
   }
 }
 
+// ------------------------------------------------------------------ implicit adjoint
+// Gradients through the converged minimiser x* of the step objective (the solver run to
+// convergence, Implementation and architecture section) by the implicit-function
+// theorem: grad f(x*; y, w) = 0, so with H = grad^2 f(x*)
+//   H lam = dL/dx* + dL/dv*/dt   (v* = (x* - x_n)/dt),
+//   dL/dy = (M/dt^2) lam,  dL/dx_n = dL/dy - dL/dv*/dt,  dL/dv_n = dt dL/dy,
+//   dL/df = lam,  dL/dw_q = -lam . d(grad f)/dw_q.
+// lam comes from conjugate gradients on H (Hessian-vector products), preconditioned by
+// the prefactored projective-dynamics matrix A^-1; the forward step that produced x* is
+// the caller's (npfem_step on copies of the inputs).
+struct ImplicitParams {
+  const double* x_n;      // [3][Nt] the step's input positions
+  const double* x_star;   // [3][Nt] the converged positions
+  const double* gx_next;  // [3][Nt] dL/dx*
+  const double* gv_next;  // [3][Nt] dL/dv* or null
+  double* gx;             // [3][Nt] out
+  double* gv;
+  double* gf;
+  double* gw;             // [ncells][4] out
+  char* scratch;          // 6 [3n] FP64 vectors per warp slot
+  size_t slot_bytes;
+  double cg_tol;          // stop when |r| <= cg_tol |b|
+  int cg_max;
+  int32_t* status_out;    // [ncells] or null: bit 16 ORed in when CG did not converge
+};
+
+constexpr int kImplicitVectors = 6;
+constexpr int kStatusCgNotConverged = 16;
+
+__global__ void __launch_bounds__(128) npfem_adjoint_implicit_kernel(DevTypeView<double> ty, StepParams P,
+                                                                      ImplicitParams A) {
+  extern __shared__ double smem_z[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
+  double* zs = P.z_in_smem ? smem_z + (size_t)wib * (P.solve_per_coord ? 1 : 3) * (ty.n + 1) : nullptr;
+  CellWs<double> w = carve<double>(P.scratch + (size_t)slot * P.slot_bytes, ty.n, ty.T, ty.E, zs);
+  const int n = ty.n, len = 3 * n;
+  double* lam = reinterpret_cast<double*>(A.scratch + (size_t)slot * A.slot_bytes);
+  double* r = lam + len;
+  double* z = r + len;
+  double* pv = z + len;
+  double* hp = pv + len;
+  double* U = hp + len;
+  const int64_t Nt = P.n_total;
+  const double dt = ty.dt;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = atomicAdd(P.queue_counter, 1);
+    item = __shfl_sync(kFull, item, 0);
+    if (item >= P.ncells_list) break;
+    const int cell = P.cell_list[item];
+    const int64_t off = P.offsets[cell];
+    const double ax = A.x_n[off], ay = A.x_n[Nt + off], az = A.x_n[2 * Nt + off];
+    Acc<double> cx, cy, cz, bb;
+    for (int k = lane; k < n; k += 32) {
+      const double anc[3] = {ax, ay, az};
+      for (int c = 0; c < 3; ++c) {
+        const double xn = A.x_n[c * Nt + off + k];
+        w.X[3 * k + c] = xn - anc[c];
+        U[3 * k + c] = A.x_star[c * Nt + off + k] - xn;
+        const double gvv = A.gv_next ? A.gv_next[c * Nt + off + k] : 0.0;
+        const double b = A.gx_next[c * Nt + off + k] + gvv / dt;
+        r[3 * k + c] = b;
+        lam[3 * k + c] = 0.0;
+        bb.add_prod(b, b);
+      }
+      cx.add(w.X[3 * k]);
+      cy.add(w.X[3 * k + 1]);
+      cz.add(w.X[3 * k + 2]);
+    }
+    const V3<double> cvol{cx.total() / n, cy.total() / n, cz.total() / n};
+    const double bn = sqrt(bb.total());
+    __syncwarp();
+    bool converged = bn == 0.0;
+    double wd[4];
+    if (!converged) {
+      global_solve<double>(ty, w.z, P.z_in_smem != 0, r, z, lane, P.solve_per_coord != 0);
+      for (int e = lane; e < len; e += 32) pv[e] = z[e];
+      __syncwarp();
+      double rz = vdot64<double>(r, z, len, lane);
+      for (int it = 0; it < A.cg_max; ++it) {
+        hessian_vector(ty, w, U, pv, hp, cvol, wd, lane);
+        const double php = vdot64<double>(pv, hp, len, lane);
+        if (!(php > 0.0)) break;  // not positive definite along p: stop, report
+        const double a = rz / php;
+        vaxpy(lam, a, pv, len, lane);
+        vaxpy(r, -a, hp, len, lane);
+        __syncwarp();
+        const double rn = sqrt(vdot64<double>(r, r, len, lane));
+        if (rn <= A.cg_tol * bn) {
+          converged = true;
+          break;
+        }
+        global_solve<double>(ty, w.z, P.z_in_smem != 0, r, z, lane, P.solve_per_coord != 0);
+        const double rz1 = vdot64<double>(r, z, len, lane);
+        const double beta = rz1 / rz;
+        rz = rz1;
+        for (int e = lane; e < len; e += 32) pv[e] = z[e] + beta * pv[e];
+        __syncwarp();
+      }
+    }
+    // weight derivatives: wd[q] = lam . d(grad f)/d(w_q)
+    hessian_vector(ty, w, U, lam, hp, cvol, wd, lane);
+    for (int vtx = lane; vtx < n; vtx += 32) {
+      const double mi = __ldg(&ty.mass[vtx]);
+      for (int c = 0; c < 3; ++c) {
+        const double l = lam[3 * vtx + c];
+        const double dldy = mi / (dt * dt) * l;
+        const double gvv = A.gv_next ? A.gv_next[c * Nt + off + vtx] : 0.0;
+        A.gx[c * Nt + off + vtx] = dldy - gvv / dt;
+        A.gv[c * Nt + off + vtx] = dt * dldy;
+        A.gf[c * Nt + off + vtx] = l;
+      }
+    }
+    if (lane == 0) {
+      for (int q = 0; q < 4; ++q) A.gw[(size_t)cell * 4 + q] = -wd[q];
+      if (A.status_out && !converged) A.status_out[cell] |= kStatusCgNotConverged;
+    }
+    __syncwarp();
+  }
+}
+
 }  // namespace npfem

@@ -118,6 +118,8 @@ struct npfem_batch {
   double* d_res = nullptr;
   int32_t* d_status = nullptr;
   int32_t* d_done = nullptr;
+  double* d_xstar = nullptr;  // implicit adjoint: the forward step's positions and velocities
+  double* d_vstar = nullptr;
   // collisions (npfem_batch_set_collisions): parameters and detection buffers
   bool coll = false;
   bool coll_alloc = false;
@@ -879,6 +881,26 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
   return NPFEM_OK;
 }
 
+// The adjoint workspace of every type (first adjoint call): per warp slot of the fused
+// launch, the unrolled adjoint's tape and vectors (the implicit adjoint uses six of them).
+static npfem_status ensure_adjoint_workspace(npfem_batch* b) {
+  for (TypeLaunch& L : b->launches) {
+    if (L.adj_scratch) continue;
+    const HostType& H = b->types[L.type_index]->host;
+    size_t v3 = (size_t)3 * H.n;
+    size_t nvec = 3 * (size_t)(kMaxAdjIters + 1) + 4 * (size_t)kMaxAdjIters + 2 * (size_t)(kHistory + 1) + 6;
+    nvec = std::max<size_t>(nvec, kImplicitVectors);
+    size_t bytes = ((sizeof(double) * (nvec * v3 + 3 * kMaxAdjIters) + sizeof(int) * kMaxAdjIters) + 255) &
+                   ~(size_t)255;
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes * (size_t)L.blocks * L.warps_per_block);
+    if (e != cudaSuccess) return fail(NPFEM_ERR_OOM, std::string("adjoint workspace: ") + cudaGetErrorString(e));
+    L.adj_scratch = static_cast<char*>(p);
+    L.adj_slot = bytes;
+  }
+  return NPFEM_OK;
+}
+
 npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, const void* f_ext,
                                 const int32_t* iters, const npfem_solver_opts* opts, const double* gx_next,
                                 const double* gv_next, double* gx, double* gv, double* gf, double* gw,
@@ -898,18 +920,8 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     if (t->host.c_alpha != 0.0 || t->host.c_beta != 0.0)
       return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: a cell type has damping (damping is not differentiated)");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  for (TypeLaunch& L : b->launches) {
-    if (L.adj_scratch) continue;
-    const HostType& H = b->types[L.type_index]->host;
-    size_t v3 = (size_t)3 * H.n;
-    size_t nvec = 3 * (size_t)(kMaxAdjIters + 1) + 4 * (size_t)kMaxAdjIters + 2 * (size_t)(kHistory + 1) + 6;
-    size_t bytes = ((sizeof(double) * (nvec * v3 + 3 * kMaxAdjIters) + sizeof(int) * kMaxAdjIters) + 255) &
-                   ~(size_t)255;
-    void* p = nullptr;
-    NPFEM_CUDA_TRY(cudaMalloc(&p, bytes * (size_t)L.blocks * L.warps_per_block));
-    L.adj_scratch = static_cast<char*>(p);
-    L.adj_slot = bytes;
-  }
+  npfem_status arc = ensure_adjoint_workspace(b);
+  if (arc != NPFEM_OK) return arc;
   NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kMaxChains * kSplitCounters, st));
   for (size_t li = 0; li < b->launches.size(); ++li) {
     const TypeLaunch& L = b->launches[li];
@@ -947,6 +959,77 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     A.w_mat[3] = H.w_vol;
     npfem_adjoint_kernel<<<L.blocks, 32 * L.warps_per_block, L.smem_bytes, st>>>(
         t->v64, P, A, static_cast<const double*>(x), static_cast<const double*>(v), static_cast<const double*>(f_ext));
+    NPFEM_CUDA_TRY(cudaGetLastError());
+  }
+  return NPFEM_OK;
+}
+
+npfem_status npfem_step_adjoint_implicit(npfem_batch* b, const void* x, const void* v, const void* f_ext,
+                                         const int32_t* iters, const npfem_solver_opts* opts, const double* gx_next,
+                                         const double* gv_next, double* gx, double* gv, double* gf, double* gw,
+                                         double cg_tol, int32_t cg_max_iters, int32_t* status_out, void* stream) {
+  if (!b || !opts) return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint_implicit: null batch or opts");
+  if (b->prec != NPFEM_FP64) return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint_implicit: needs an FP64 batch");
+  if (b->ncells == 0) return NPFEM_OK;
+  if (!x || !v || !f_ext || !gx_next || !gx || !gv || !gf || !gw)
+    return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint_implicit: null array");
+  if (!(cg_tol > 0.0) || std::isinf(cg_tol) || cg_max_iters < 1)
+    return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint_implicit: need finite cg_tol > 0 and cg_max_iters >= 1");
+  if (b->coll)
+    return fail(NPFEM_ERR_INVALID_ARG,
+                "step_adjoint_implicit: collisions are enabled (contacts are not differentiated)");
+  for (const npfem_cell_type* t : b->types)
+    if (t->host.c_alpha != 0.0 || t->host.c_beta != 0.0)
+      return fail(NPFEM_ERR_INVALID_ARG,
+                  "step_adjoint_implicit: a cell type has damping (damping is not differentiated)");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = sizeof(double) * 3 * (size_t)b->n_total;
+  if (!b->d_xstar) {
+    void* p;
+    NPFEM_CUDA_TRY(b->mem.alloc(bytes, &p));
+    b->d_xstar = static_cast<double*>(p);
+    NPFEM_CUDA_TRY(b->mem.alloc(bytes, &p));
+    b->d_vstar = static_cast<double*>(p);
+  }
+  npfem_status arc = ensure_adjoint_workspace(b);
+  if (arc != NPFEM_OK) return arc;
+  // forward: the step on copies of x and v (x* is its final iterate)
+  NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_xstar, x, bytes, cudaMemcpyDeviceToDevice, st));
+  NPFEM_CUDA_TRY(cudaMemcpyAsync(b->d_vstar, v, bytes, cudaMemcpyDeviceToDevice, st));
+  npfem_solver_opts o = *opts;
+  o.alpha_log = nullptr;
+  o.alpha_log_len = 0;
+  npfem_status rc = npfem_step(b, b->d_xstar, b->d_vstar, f_ext, iters, &o, nullptr, status_out, stream);
+  if (rc != NPFEM_OK) return rc;
+  NPFEM_CUDA_TRY(cudaMemsetAsync(b->d_counters, 0, sizeof(int) * b->types.size() * kMaxChains * kSplitCounters, st));
+  for (const TypeLaunch& L : b->launches) {
+    const npfem_cell_type* t = b->types[L.type_index];
+    StepParams P{};
+    P.ncells_list = L.ncells;
+    P.cell_list = L.cell_list;
+    P.offsets = b->d_offsets;
+    P.n_total = b->n_total;
+    P.queue_counter = L.counter;
+    P.scratch = L.scratch;
+    P.slot_bytes = L.slot_bytes;
+    P.z_in_smem = L.z_in_smem;
+    P.solve_per_coord = L.solve_per_coord;
+    P.phase_cycles = b->d_phase;
+    ImplicitParams A{};
+    A.x_n = static_cast<const double*>(x);
+    A.x_star = b->d_xstar;
+    A.gx_next = gx_next;
+    A.gv_next = gv_next;
+    A.gx = gx;
+    A.gv = gv;
+    A.gf = gf;
+    A.gw = gw;
+    A.scratch = L.adj_scratch;
+    A.slot_bytes = L.adj_slot;
+    A.cg_tol = cg_tol;
+    A.cg_max = cg_max_iters;
+    A.status_out = status_out;
+    npfem_adjoint_implicit_kernel<<<L.blocks, 32 * L.warps_per_block, L.smem_bytes, st>>>(t->v64, P, A);
     NPFEM_CUDA_TRY(cudaGetLastError());
   }
   return NPFEM_OK;

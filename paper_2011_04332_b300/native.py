@@ -96,6 +96,8 @@ def load_library() -> C.CDLL:
         "npfem_batch_set_collisions": [vp, C.POINTER(_CollisionParams)],
         "npfem_batch_contacts": [vp, vp, vp, vp, vp],
         "npfem_batch_contact_time": [vp, C.POINTER(C.c_double)],
+        "npfem_step_adjoint_implicit": [vp, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp, vp, vp, vp, C.c_double,
+                                        C.c_int32, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -236,6 +238,24 @@ class Batch:
         _check(_lib.npfem_step_adjoint(self.handle, _ptr(x), _ptr(v), _ptr(f), _ptr(iters), C.byref(opts),
                                        _ptr(gx_next), _ptr(gv_next), _ptr(gx), _ptr(gv), _ptr(gf), _ptr(gw),
                                        _ptr(status), C.c_void_p(stream)))
+
+    def step_adjoint_implicit(self, x, v, f, gx_next, gv_next, gx, gv, gf, gw, iters=None, iters_default: int = 5,
+                              tol: float = 0.0, max_iters: int = 0, cg_tol: float = 1e-12, cg_max_iters: int = 200,
+                              status=None, stream=None):
+        """npfem_step_adjoint_implicit on device tensors (FP64 batches): gradients through
+        the converged step (forward step with iters/tol as in step, then CG on the Hessian)."""
+        if iters is not None and max_iters == 0:
+            max_iters = self._iter_bound(iters)
+        opts = _Opts(int(iters_default), 0, None, int(max_iters), float(tol), None)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        elif not isinstance(stream, int):
+            stream = stream.cuda_stream
+        _check(_lib.npfem_step_adjoint_implicit(self.handle, _ptr(x), _ptr(v), _ptr(f), _ptr(iters), C.byref(opts),
+                                                _ptr(gx_next), _ptr(gv_next), _ptr(gx), _ptr(gv), _ptr(gf),
+                                                _ptr(gw), float(cg_tol), int(cg_max_iters), _ptr(status),
+                                                C.c_void_p(stream)))
 
     def set_launch(self, type_index: int, warps_per_block: int, blocks_per_sm: int, solve_in_shared: bool,
                    solve_per_coord: bool = False):
