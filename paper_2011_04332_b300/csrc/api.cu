@@ -764,6 +764,7 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
     e = cudaFuncSetAttribute(npfem_step_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(npfem_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_adjoint_implicit_kernel, smem_optin);
   if (e == cudaSuccess)
     e = set_solve_smem_attr<double>(smem_optin);
   if (e == cudaSuccess)
