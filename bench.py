@@ -538,7 +538,48 @@ def measure_adjoint(dev, nsteps: int = 40, ckpt_every: int = 20, ncells: int = 2
             "ms_per_adjoint_step": t_bwd / nsteps,
             "ms_per_forward_step": t_fwd / nsteps,
             "backward_includes": "segment recomputation (one extra forward step per step) + adjoint steps",
-            "loss": float(loss.detach()), "grad_w": [float(g) for g in w.grad[0].tolist()]}
+            "loss": float(loss.detach()), "grad_w": [float(g) for g in w.grad[0].tolist()],
+            "implicit": measure_adjoint_implicit(dev, b)}
+
+
+def measure_adjoint_implicit(dev, b, reps: int = 5, fwd_tol: float = 1e-10, budget: int = 100,
+                             cg_tol: float = 1e-10):
+    """Implicit-function adjoint on the same cells: one call = the forward step run to
+    |g|/|g0| < fwd_tol (fused kernel, budget iterations) + CG on the Hessian per cell."""
+    import torch
+    from paper_2011_04332_b300 import native
+    t = b.types[0]
+    ct = native.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt)
+    batch = native.Batch([ct], b.type_of_cell, native.FP64)
+    batch.set_mode(False)
+    x, v, f = (torch.tensor(a, device=dev) for a in (b.x, b.v, b.f))
+    gxn = torch.tensor(np.random.default_rng(1004).standard_normal(b.x.shape), device=dev)
+    gx, gv, gf = (torch.zeros_like(x) for _ in range(3))
+    gw = torch.zeros((b.ncells, 4), dtype=torch.float64, device=dev)
+    st = torch.zeros(b.ncells, dtype=torch.int32, device=dev)
+    it = torch.full((b.ncells,), budget, dtype=torch.int32, device=dev)
+    dn = torch.zeros(b.ncells, dtype=torch.int32, device=dev)
+
+    def call():
+        batch.step_adjoint_implicit(x, v, f, gxn, None, gx, gv, gf, gw, iters=it, tol=fwd_tol, cg_tol=cg_tol,
+                                    cg_max_iters=500, status=st)
+    call()
+    torch.cuda.synchronize()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    xs, vs = x.clone(), v.clone()
+    e0.record()
+    batch.step(xs, vs, f, iters=it, tol=fwd_tol, iters_done=dn)
+    e1.record()
+    for _ in range(reps):
+        call()
+    e2.record()
+    torch.cuda.synchronize()
+    ms_fwd, ms_call = e0.elapsed_time(e1), e1.elapsed_time(e2) / reps
+    return {"workload": f"{b.ncells} RBC (642 vertices) FP64, forward to |g|/|g0| < {fwd_tol:g} "
+                        f"(budget {budget}), CG to {cg_tol:g}",
+            "adjoint_cell_steps_per_s": b.ncells / (ms_call / 1e3), "ms_per_call": ms_call,
+            "ms_forward_alone": ms_fwd, "forward_iterations_mean": float(dn.double().mean()),
+            "cg_status_bits_set": int(((st & 16) != 0).sum())}
 
 
 # Sources that define what the step kernels execute: the device code and the host
