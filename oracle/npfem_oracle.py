@@ -315,10 +315,11 @@ def internal_energy_and_gradient(rs: RestState, x: np.ndarray, w_scale=None):
     return parts, g
 
 
-def objective(rs: RestState, x: np.ndarray, y: np.ndarray, w_scale=None, contact=None, damp=None):
+def objective(rs: RestState, x: np.ndarray, y: np.ndarray, w_scale=None, contact=None, damp=None, walls=None):
     """Implicit-Euler variational objective of one step (Eq. (2) discretised):
     f(x) = (x-y)^T M (x-y) / (2 dt^2) + E_int(x) [+ E_contact(x)] [+ E_damp(x)], and its
     gradient.  contact: (idx, nrm, crel, delta, weight) as in contact_energy_and_gradient.
+    walls: (lo, hi, delta, weight) in the coordinates of x, as in wall_energy_and_gradient.
     damp: (x_n, C) with the step's start x_n and C = damping_matrix: the dissipation term
     E_damp = (x - x_n)^T C (x - x_n) / (2 dt) per coordinate joins; the stationarity
     condition is then implicit Euler for M a + C v + grad E = f."""
@@ -337,6 +338,10 @@ def objective(rs: RestState, x: np.ndarray, y: np.ndarray, w_scale=None, contact
         ec, gc = contact_energy_and_gradient(x, *contact)
         parts.contact = ec
         g = g + gc
+    if walls is not None:
+        ew, gw = wall_energy_and_gradient(x, *walls)
+        parts.contact = parts.contact + ew
+        g = g + gw
     return parts, g
 
 
@@ -446,6 +451,19 @@ def cell_contacts(contacts: Dict[str, np.ndarray], o0: int, o1: int):
             nrm.append(contacts["normal"][i, k])
             off.append(contacts["offset"][i, k])
     return (np.array(idx, dtype=np.int64), np.array(nrm).reshape(-1, 3), np.array(off))
+
+
+def wall_energy_and_gradient(x: np.ndarray, lo: np.ndarray, hi: np.ndarray, delta: float, weight: float):
+    """Box walls (cell-wall contact of the collision reading): the faces of the box
+    [lo, hi] act on every vertex with the contacts' one-sided penalty,
+    E = sum_v sum_d (w/2) [max(0, delta - (x_vd - lo_d))^2 + max(0, delta - (hi_d - x_vd))^2],
+    with lo, hi in the coordinates of x.  Returns E and the gradient [n,3]."""
+    pl = delta - (x - lo[None, :])
+    pl = np.where(np.real(pl) > 0.0, pl, 0.0)
+    ph = delta - (hi[None, :] - x)
+    ph = np.where(np.real(ph) > 0.0, ph, 0.0)
+    E = 0.5 * weight * (np.sum(pl * pl) + np.sum(ph * ph))
+    return E, weight * (ph - pl)
 
 
 def contact_energy_and_gradient(x: np.ndarray, idx: np.ndarray, nrm: np.ndarray, crel: np.ndarray,
@@ -560,7 +578,7 @@ def two_loop(g: np.ndarray, S: List[np.ndarray], Y: List[np.ndarray],
 
 
 def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
-         f_ext: np.ndarray, iters: int, w_scale=None, tol: float = 0.0, contact=None) -> StepResult:
+         f_ext: np.ndarray, iters: int, w_scale=None, tol: float = 0.0, contact=None, walls=None) -> StepResult:
     """One implicit time step of one cell by quasi-Newton projective dynamics.
 
     y = x_n + dt v_n + dt^2 M^-1 f_ext;  x^(0) = y;  history cleared.
@@ -575,6 +593,8 @@ def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
     centroid of x_n (the objective is translation invariant), adding it back at the end.
     contact: (idx, nrm, c, delta, weight) with absolute plane offsets c (see
     detect_contacts / cell_contacts): the contact penalty joins the objective.
+    walls: (lo, hi, delta, weight), box corners in absolute coordinates: the wall penalty
+    of wall_energy_and_gradient joins the objective.
     With Rayleigh damping in the rest state (c_alpha, c_beta), the dissipation term of
     `objective` joins with x_n the step's start, and the solver's matrix (pd_matrix)
     carries C/dt.
@@ -587,8 +607,11 @@ def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
     if contact is not None:
         idx, nrm, c_abs, delta, weight = contact
         contact = (idx, nrm, c_abs - nrm @ ctr, delta, weight)
+    if walls is not None:
+        lo, hi, wdelta, wweight = walls
+        walls = (np.asarray(lo, dtype=np.float64) - ctr, np.asarray(hi, dtype=np.float64) - ctr, wdelta, wweight)
     damp = (xn, damping_matrix(rs, w_scale)) if (rs.c_alpha != 0.0 or rs.c_beta != 0.0) else None
-    parts, g = objective(rs, x, y, w_scale, contact, damp)
+    parts, g = objective(rs, x, y, w_scale, contact, damp, walls)
     fx = parts.total
     g0n = float(np.sqrt(np.sum(np.real(g) ** 2)))
     S: List[np.ndarray] = []
@@ -607,7 +630,7 @@ def step(rs: RestState, solver: GlobalSolver, x_n: np.ndarray, v_n: np.ndarray,
         alpha = 1.0
         for h in range(MAX_HALVINGS + 1):
             xt = x + alpha * d
-            pt, gt = objective(rs, xt, y, w_scale, contact, damp)
+            pt, gt = objective(rs, xt, y, w_scale, contact, damp, walls)
             trials += 1
             ft = pt.total
             armijo = np.real(ft) <= np.real(fx + ARMIJO_C1 * alpha * gd)
@@ -706,12 +729,14 @@ def implicit_adjoint(ct: CellType, x_n: np.ndarray, v_n: np.ndarray, f_ext: np.n
 
 def batch_step(types: List[CellType], type_of_cell, offsets, x, v, f, iters,
                cells: Optional[List[int]] = None, tol: float = 0.0,
-               collisions: Optional[tuple] = None) -> Dict[str, np.ndarray]:
+               collisions: Optional[tuple] = None, box: Optional[tuple] = None) -> Dict[str, np.ndarray]:
     """One step for a batch in SoA [3, N_total] layout; returns new x, v (for the
     selected cells only; other columns are copied through) plus per-cell residuals,
     statuses, accepted step lengths, gradient norms and iterations done (tol: as in
     `step`).  collisions = (radius, delta, weight): contacts detected on x (for the
-    selected cells' vertices) join each cell's objective; they are returned too."""
+    selected cells' vertices) join each cell's objective; they are returned too.
+    box = (lo, hi) with collisions: the box's walls act on every vertex with the same
+    delta and weight."""
     xo, vo = x.copy(), v.copy()
     contacts = None
     if collisions is not None:
@@ -730,7 +755,10 @@ def batch_step(types: List[CellType], type_of_cell, offsets, x, v, f, iters,
         con = None
         if contacts is not None:
             con = (*cell_contacts(contacts, s.start, s.stop), delta, weight)
-        r = step(ct.rest, ct.solver, x[:, s].T, v[:, s].T, f[:, s].T, int(iters[c]), ct.w_scale, tol, con)
+        wl = None
+        if contacts is not None and box is not None:
+            wl = (box[0], box[1], delta, weight)
+        r = step(ct.rest, ct.solver, x[:, s].T, v[:, s].T, f[:, s].T, int(iters[c]), ct.w_scale, tol, con, wl)
         xo[:, s] = r.x.T
         vo[:, s] = r.v.T
         res[c] = r.residual

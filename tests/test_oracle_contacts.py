@@ -199,3 +199,54 @@ def test_overlapping_cells_separate():
         counts.append(inside())
     assert counts[0] > 0
     assert all(c1 <= c0 for c0, c1 in zip(counts, counts[1:])) and counts[-1] < counts[0]
+
+
+def test_wall_gradient_matches_central_differences():
+    rng = np.random.default_rng(13)
+    x = rng.uniform(-1.0, 1.0, (30, 3))
+    lo, hi = np.array([-0.9, -0.8, -1.0]), np.array([0.85, 0.9, 0.7])
+    E, g = O.wall_energy_and_gradient(x, lo, hi, 0.2, 9.0)
+    assert E > 0
+    h = 1e-6
+    for v in range(30):
+        for d in range(3):
+            xp, xm = x.copy(), x.copy()
+            xp[v, d] += h
+            xm[v, d] -= h
+            fd = (O.wall_energy_and_gradient(xp, lo, hi, 0.2, 9.0)[0]
+                  - O.wall_energy_and_gradient(xm, lo, hi, 0.2, 9.0)[0]) / (2 * h)
+            assert g[v, d] == pytest.approx(fd, rel=1e-7, abs=1e-9)
+
+
+def test_one_wall_contact_delivers_its_impulse():
+    """A rest cell with one vertex a distance p beyond the lower x wall and every other
+    vertex farther than delta inside: the first PD iterate's mass-weighted displacement is
+    dt^2 w (delta + p) along +x (as for one cell contact)."""
+    m = I.rbc_mesh(2)
+    ct = _type(m)
+    x = m.verts.copy()
+    order = np.argsort(x[:, 0])
+    p, delta, w = 0.05, 0.02, 25.0
+    lo = np.array([x[order[0], 0] + p, -100.0, -100.0])
+    hi = np.array([100.0, 100.0, 100.0])
+    assert x[order[1], 0] > lo[0] + delta
+    r = O.step(ct.rest, ct.solver, x, np.zeros_like(x), np.zeros_like(x), 1, walls=(lo, hi, delta, w))
+    impulse = np.sum(ct.rest.mass[:, None] * (r.x - x), axis=0)
+    assert np.allclose(impulse, DT * DT * w * (delta + p) * np.array([1.0, 0.0, 0.0]), rtol=1e-12, atol=1e-15)
+
+
+def test_cell_thrown_at_a_wall_turns_back():
+    """A cell moving at 2 um/us towards the upper x wall: within a few steps its velocity
+    turns negative and no vertex gets more than 0.3 um beyond the wall."""
+    m = I.icosphere(2)
+    ct = _type(m)
+    x = m.verts.copy()
+    v = np.tile([[2.0, 0.0, 0.0]], (m.n, 1))
+    lo, hi = np.array([-5.0, -5.0, -5.0]), np.array([1.5, 5.0, 5.0])
+    worst = 0.0
+    for _ in range(20):
+        r = O.step(ct.rest, ct.solver, x, v, np.zeros_like(x), 8, walls=(lo, hi, 0.05, 200.0))
+        x, v = r.x, r.v
+        worst = max(worst, float(np.max(x[:, 0] - hi[0])))
+    assert np.mean(v[:, 0]) < 0
+    assert worst < 0.3
