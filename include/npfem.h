@@ -306,6 +306,11 @@ typedef struct {
   double radius; /* um: match search radius (also the detection grid's cell edge) */
   double delta;  /* um: contact thickness, >= 0 */
   double weight; /* nN/um: collision weight, >= 0 */
+  int32_t walls; /* != 0: the faces of the box [box_lo, box_hi] act on every vertex of the
+                    current iterate with (weight/2) max(0, delta - gap)^2 per face, gap the
+                    distance inside the box along that face's axis (cell-wall contact) */
+  double box_lo[3]; /* um, with walls: box corners, box_lo < box_hi on every axis */
+  double box_hi[3];
 } npfem_collision_params;
 
 /* Enable collisions for every later npfem_step / npfem_step_host of the batch (params

@@ -422,13 +422,16 @@ static npfem_status detect_contacts(npfem_batch* b, const void* x, cudaStream_t 
   return detect_contacts_t<float>(b, static_cast<const float*>(x), st);
 }
 
-// The step kernels' view of the contacts of the current step (null when collisions are off).
-static void set_contact_params(const npfem_batch* b, StepParams& P) {
+// The step kernels' view of the contacts of the current step (null when collisions are off)
+// and of the box walls; x is the state being stepped (the cells' anchors are read from it).
+static void set_contact_params(const npfem_batch* b, StepParams& P, const void* x) {
   if (!b->coll) return;
   P.contact_count = b->cp.ccount;
   P.contact_plane = b->cp.cplane;
   P.contact_delta = b->coll_p.delta;
   P.contact_weight = b->coll_p.weight;
+  P.box = b->coll_p.walls ? b->cp.box : nullptr;
+  P.x_state = x;
 }
 
 static constexpr int kTimingSlots = 1 + 2 * kSplitMaxIters;
@@ -544,7 +547,7 @@ static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_e
   P.alpha_log = opts->alpha_log;
   P.alpha_log_len = opts->alpha_log_len;
   P.phase_cycles = b->d_phase;
-  set_contact_params(b, P);
+  set_contact_params(b, P, x);
   auto launch = [&](size_t c, int kind, int it, int slot) -> npfem_status {
     const Chain& C = chains[c];
     const TypeLaunch& L = b->launches[C.li];
@@ -867,7 +870,7 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
     P.z_in_smem = L.z_in_smem;
     P.solve_per_coord = L.solve_per_coord;
     P.phase_cycles = b->d_phase;
-    set_contact_params(b, P);
+    set_contact_params(b, P, x);
     dim3 grid(L.blocks), block(32 * L.warps_per_block);
     if (b->prec == NPFEM_FP64)
       npfem_step_kernel<double><<<grid, block, L.smem_bytes, st>>>(t->v64, P, static_cast<double*>(x),
@@ -1375,6 +1378,10 @@ npfem_status npfem_batch_set_collisions(npfem_batch* b, const npfem_collision_pa
   if (!(p->radius > 0.0) || std::isinf(p->radius) || !(p->delta >= 0.0) || std::isinf(p->delta) ||
       !(p->weight >= 0.0) || std::isinf(p->weight))
     return fail(NPFEM_ERR_INVALID_ARG, "batch_set_collisions: need finite radius > 0, delta >= 0, weight >= 0");
+  if (p->walls)
+    for (int d = 0; d < 3; ++d)
+      if (!(p->box_lo[d] < p->box_hi[d]) || std::isinf(p->box_lo[d]) || std::isinf(p->box_hi[d]))
+        return fail(NPFEM_ERR_INVALID_ARG, "batch_set_collisions: walls need a finite box with box_lo < box_hi");
   if (b->n_total >= ((int64_t)1 << 30))
     return fail(NPFEM_ERR_UNSUPPORTED, "batch_set_collisions: more than 2^30 vertices");
   size_t nsmem = 0;  // the normals kernel keeps a cell's triangle normals in shared memory
@@ -1413,6 +1420,8 @@ npfem_status npfem_batch_set_collisions(npfem_batch* b, const npfem_collision_pa
     C.sortpos = static_cast<float4*>(q);
     NPFEM_CUDA_TRY(take(256, &q));
     C.maxabs = static_cast<int32_t*>(q);
+    NPFEM_CUDA_TRY(take(sizeof(double) * 6, &q));
+    C.box = static_cast<double*>(q);
     NPFEM_CUDA_TRY(take(sizeof(double) * 3 * N, &q));
     C.nrm = static_cast<double*>(q);
     NPFEM_CUDA_TRY(take(sizeof(int32_t) * N, &q));
@@ -1431,6 +1440,10 @@ npfem_status npfem_batch_set_collisions(npfem_batch* b, const npfem_collision_pa
   }
   b->coll_p = *p;
   b->coll = true;
+  if (b->coll_alloc && p->walls) {
+    const double box[6] = {p->box_lo[0], p->box_lo[1], p->box_lo[2], p->box_hi[0], p->box_hi[1], p->box_hi[2]};
+    NPFEM_CUDA_TRY(cudaMemcpy(b->cp.box, box, sizeof(box), cudaMemcpyHostToDevice));
+  }
   return NPFEM_OK;
 }
 

@@ -47,6 +47,7 @@ struct ContactParams {
   int32_t* sorted;           // [N] vertex ids in bucket order
   float4* sortpos;           // [N] position (float) + cell id, bucket order
   int32_t* maxabs;           // [1] largest |coordinate| of the step's input (float bits)
+  double* box;               // [6] wall box lo, hi (collisions with walls)
   double* nrm;               // [N][3] unit vertex normals
   int32_t* ccount;           // [N] matches per vertex (0..2)
   int32_t* cvertex;          // [N][2] matched vertex (-1: unused)

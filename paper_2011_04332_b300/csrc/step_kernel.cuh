@@ -42,6 +42,8 @@ struct StepParams {
   const int32_t* contact_count;  // [N_total] contact planes per vertex (0..2), or null: no collisions
   const double* contact_plane;   // [N_total][2][4] unit normal, offset relative to the cell's anchor
   double contact_delta, contact_weight;  // penalty (w/2) max(0, delta - gap)^2 per plane
+  const double* box;           // with collisions and walls: [6] box lo, hi (absolute); else null
+  const void* x_state;         // the state being stepped (S*): each cell's anchor is its first vertex
   double* alpha_log;           // [ncells][alpha_log_len] or null
   int alpha_log_len;
   int* queue_counter;          // work-queue head (zeroed before the launch)
@@ -198,6 +200,50 @@ struct EvalOut {
   double energy;
   bool degenerate;
 };
+
+// Box walls (cell-wall contact): each face of the box [lo, hi] acts on every vertex of the
+// current iterate with (w/2) max(0, delta - gap)^2, gap the distance inside the box along
+// the face's axis; positions relative to the cell's anchor (the first vertex of the stepped
+// state, as in the step).  Adds to the gradient; returns the lane's share of the energy.
+template <typename S>
+__device__ __noinline__ double wall_pass(const S* xs, int64_t off, int64_t Nt, double dl, double wc,
+                                         const double* box, const S* X, const S* U, S* G, int n, int lane) {
+  double lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) {
+    const double a = (double)xs[d * Nt + off];
+    lo[d] = box[d] - a;
+    hi[d] = box[3 + d] - a;
+  }
+  double e = 0.0;
+  for (int v = lane; v < n; v += 32) {
+    const V3<S> p = ld3(X, v) + ld3(U, v);
+    const double q[3] = {(double)p.x, (double)p.y, (double)p.z};
+    double f[3] = {0.0, 0.0, 0.0};
+    bool any = false;
+    for (int d = 0; d < 3; ++d) {
+      const double pl = dl - (q[d] - lo[d]);
+      if (pl > 0.0) {
+        e += 0.5 * wc * pl * pl;
+        f[d] -= wc * pl;
+        any = true;
+      }
+      const double ph = dl - (hi[d] - q[d]);
+      if (ph > 0.0) {
+        e += 0.5 * wc * ph * ph;
+        f[d] += wc * ph;
+        any = true;
+      }
+    }
+    if (any) {
+      V3<S> g = ld3(G, v);
+      g.x += (S)f[0];
+      g.y += (S)f[1];
+      g.z += (S)f[2];
+      st3(G, v, g);
+    }
+  }
+  return e;
+}
 
 // Rayleigh damping terms of the objective, out of line so that the iteration kernels'
 // register allocation does not carry them when damping is off.  Each returns its lane's
@@ -407,6 +453,10 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const StepParams& P,
       st3(Gout, v, g);
     }
     o.energy += warp_sum_d(e_ct);
+    // box walls (cell-wall contact), out of line: a step without walls carries none of it
+    if (P.box)
+      o.energy += warp_sum_d(wall_pass<S>(static_cast<const S*>(P.x_state), off, P.n_total, P.contact_delta,
+                                          P.contact_weight, P.box, X, U, Gout, n, lane));
   }
   o.degenerate = __any_sync(kFull, degen);
   __syncwarp();

@@ -47,7 +47,8 @@ class _Opts(C.Structure):
 
 
 class _CollisionParams(C.Structure):
-    _fields_ = [("radius", C.c_double), ("delta", C.c_double), ("weight", C.c_double)]
+    _fields_ = [("radius", C.c_double), ("delta", C.c_double), ("weight", C.c_double), ("walls", C.c_int32),
+                ("box_lo", C.c_double * 3), ("box_hi", C.c_double * 3)]
 
 
 class _TypeInfo(C.Structure):
@@ -329,14 +330,21 @@ class Batch:
         _check(_lib.npfem_batch_get_split_launch(self.handle, int(type_index), out))
         return tuple(int(v) for v in out[:7]), bool(out[7])
 
-    def set_collisions(self, radius: Optional[float] = None, delta: float = 0.0, weight: float = 0.0) -> None:
+    def set_collisions(self, radius: Optional[float] = None, delta: float = 0.0, weight: float = 0.0,
+                       box=None) -> None:
         """npfem_batch_set_collisions: contacts (search radius, thickness delta, weight w)
-        detected at the start of every later step; radius=None disables them."""
+        detected at the start of every later step, and with box = (lo[3], hi[3]) the box's
+        walls acting on every vertex; radius=None disables them."""
         if radius is None:
             _check(_lib.npfem_batch_set_collisions(self.handle, None))
             self.collisions_on = False
         else:
             p = _CollisionParams(float(radius), float(delta), float(weight))
+            if box is not None:
+                p.walls = 1
+                for d in range(3):
+                    p.box_lo[d] = float(box[0][d])
+                    p.box_hi[d] = float(box[1][d])
             _check(_lib.npfem_batch_set_collisions(self.handle, C.byref(p)))
             self.collisions_on = True
 

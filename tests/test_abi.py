@@ -115,7 +115,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     if cc is None:
         pytest.skip("no C compiler")
     structs = {"npfem_mesh": native._Mesh, "npfem_material": native._Material,
-               "npfem_solver_opts": native._Opts, "npfem_type_info": native._TypeInfo}
+               "npfem_solver_opts": native._Opts, "npfem_type_info": native._TypeInfo,
+               "npfem_collision_params": native._CollisionParams}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "npfem.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')

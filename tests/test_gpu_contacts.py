@@ -302,3 +302,45 @@ def test_contact_detection_timing():
     assert batch.contact_time() > 0.0
     for k in ("x", "v", "residual", "count", "vertex", "plane"):
         assert np.array_equal(plain[k], timed[k]), k
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_walls_parity(prec):
+    """Small packing batch with the box walls of a cube that cuts into the cells: contacts
+    plus wall penalties against the oracle, two steps."""
+    nat = _native()
+    p = nat.FP64 if prec == "fp64" else nat.FP32FORM
+    b = _small_packing(seed=6)
+    lo = b.x.min(axis=1) + 0.4
+    hi = b.x.max(axis=1) - 0.4
+    _, batch = _setup(b, p, collisions=False)
+    batch.set_collisions(RADIUS, DELTA, WEIGHT, box=(lo, hi))
+    ots = [O.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
+    x, v, f = _inputs(b, p)
+    for s in range(2):
+        got = _step(batch, p, x, v, f, b.iters)
+        ref = O.batch_step(ots, b.type_of_cell, b.offsets, x, v, f, b.iters, collisions=(RADIUS, DELTA, WEIGHT),
+                           box=(lo, hi))
+        _check_contacts(b, got, ref["contacts"], x)
+        _check_state(b, p, got, ref, range(b.ncells), ots)
+        x, v = ref["x"], ref["v"]
+        if p == nat.FP32FORM:
+            x, v = (a.astype(np.float32).astype(np.float64) for a in (x, v))
+
+
+def test_packing_in_a_box_stays_inside():
+    """64 RBCs packed at 35 % volume fraction in a box whose walls sit 1 um outside the
+    initial cells: after 30 steps no vertex is more than 0.2 um beyond a wall."""
+    nat = _native()
+    b = I.packing_batch(64, 0, hematocrit=0.35, seed=12)
+    lo, hi = b.x.min(axis=1) - 1.0, b.x.max(axis=1) + 1.0
+    _, batch = _setup(b, nat.FP32FORM, collisions=False)
+    batch.set_collisions(0.5, 0.05, 60.0, box=(lo, hi))
+    x, v, f = _inputs(b, nat.FP32FORM)
+    worst = 0.0
+    for s in range(30):
+        got = _step(batch, nat.FP32FORM, x, v, f, b.iters)
+        x, v = got["x"], got["v"]
+        worst = max(worst, float(np.max(x - hi[:, None])), float(np.max(lo[:, None] - x)))
+        assert np.all(np.isfinite(x))
+    assert worst < 0.2, worst
