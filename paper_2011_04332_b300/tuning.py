@@ -40,9 +40,21 @@ def _flush_l2(device) -> None:
 
 
 def _time_step(batch: native.Batch, x, v, f, iters, reps: int, warm: bool = True, tol: float = 0.0) -> float:
+    """Best of `reps` timings of one step replayed as a CUDA graph (as the benchmark runs
+    it: no host launch overhead between the chains' kernels), L2 flushed before each."""
     xs, vs = x.clone(), v.clone()
+    batch.step(xs, vs, f, iters=iters, tol=tol)      # uncaptured first (workspace, events)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(x.device)
+    side.wait_stream(torch.cuda.current_stream(x.device))
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            batch.step(xs, vs, f, iters=iters, tol=tol)
+    torch.cuda.current_stream(x.device).wait_stream(side)
+    torch.cuda.synchronize()
     if warm:
-        batch.step(xs, vs, f, iters=iters, tol=tol)      # warm-up (first touch of the workspace)
+        graph.replay()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     best = float("inf")
     for _ in range(reps):
@@ -50,10 +62,11 @@ def _time_step(batch: native.Batch, x, v, f, iters, reps: int, warm: bool = True
         vs.copy_(v)
         _flush_l2(x.device)
         e0.record()
-        batch.step(xs, vs, f, iters=iters, tol=tol)
+        graph.replay()
         e1.record()
         torch.cuda.synchronize()
         best = min(best, e0.elapsed_time(e1))
+    del graph
     return best
 
 
@@ -136,11 +149,12 @@ def split_iter_candidates():
 
 
 def autotune_split(batch: native.Batch, x, v, f, iters=None, reps: int = 2, solve_only: bool = False,
-                   tol: float = 0.0) -> Dict[int, dict]:
+                   tol: float = 0.0, confirm: int = 5) -> Dict[int, dict]:
     """Coordinate search of the split-mode shapes per cell type (first the solve kernel's
     shape, then the iteration kernels'), then one group count for all types, timing
-    whole steps (best of `reps`; the group counts and the final comparison best of 3).
-    The result is kept only if it beats the starting configuration."""
+    whole steps (best of `reps`; the group counts best of 3).  The result is kept only if,
+    timed alternately with the starting configuration `confirm` times each, its median
+    is at least 1 % lower."""
     batch.set_mode(True)
     types = sorted({int(t) for t in batch.type_of_cell})
     start = {t: (list(batch.get_split_launch(t)[0]), batch.get_groups(t)) for t in types}
@@ -184,12 +198,33 @@ def autotune_split(batch: native.Batch, x, v, f, iters=None, reps: int = 2, solv
             best_g, best_ms = g, ms
     for t in types:
         batch.set_groups(t, best_g)
-    if best_ms > start_ms:        # keep the starting configuration
+    chosen = {t: (list(batch.get_split_launch(t)[0]), batch.get_groups(t)) for t in types}
+
+    def apply(cfg):
         for t in types:
-            batch.set_split_launch(t, start[t][0])
-            batch.set_groups(t, start[t][1])
+            batch.set_split_launch(t, cfg[t][0])
+            batch.set_groups(t, cfg[t][1])
+
+    # The winner of many noisy comparisons is biased towards a lucky timing: confirm it
+    # against the starting configuration, timed alternately, by the median of 5 each.
+    keep = False
+    if chosen != start and best_ms <= start_ms:
+        tc, ts = [], []
+        for _ in range(confirm):
+            apply(chosen)
+            tc.append(_time_step(batch, x, v, f, iters, 1, warm=True, tol=tol))
+            apply(start)
+            ts.append(_time_step(batch, x, v, f, iters, 1, warm=True, tol=tol))
+        mc, ms_ = sorted(tc)[confirm // 2], sorted(ts)[confirm // 2]
+        keep = mc < 0.99 * ms_
+        best_ms = mc if keep else ms_
+    if not keep:                  # keep the starting configuration
+        apply(start)
+        for t in types:
             out[t] = {"split_shape": tuple(start[t][0])}
-        best_g, best_ms = start[types[0]][1], start_ms
+        best_ms = min(best_ms, start_ms)
+    else:
+        apply(chosen)
     for t in types:
         out[t]["groups"] = batch.get_groups(t)
         out[t]["ms"] = best_ms
