@@ -44,7 +44,15 @@ def _mat(spec):
 
 # ------------------------------------------------------------------ workloads
 # collision parameters (search radius um, contact thickness um, weight nN/um) per workload
-COLLISIONS = {"pack4096": (0.5, 0.05, 60.0)}
+# (and whether the packing box's walls act: a box 1 um outside the initial cells)
+COLLISIONS = {"pack4096": (0.5, 0.05, 60.0, False), "packbox4096": (0.5, 0.05, 60.0, True)}
+
+
+def _box(b, coll):
+    """The wall box of a collision workload (lo[3], hi[3]), or None."""
+    if coll is None or not coll[3]:
+        return None
+    return (b.x.min(axis=1) - 1.0, b.x.max(axis=1) + 1.0)
 
 
 def make_workload(name: str, rank: int = 0):
@@ -66,12 +74,13 @@ def make_workload(name: str, rank: int = 0):
     elif name == "homog2562":
         b = I.homogeneous_rbc_batch(ncells=1184, seed=1001 + 100 * rank, subdiv=4)
         desc = "homogeneous 1184 RBC (2562 vertices, Evans-Fung), 5 iterations"
-    elif name == "pack4096":
+    elif name in ("pack4096", "packbox4096"):
         b = I.packing_batch(4096, 0, hematocrit=0.35, seed=1006 + 100 * rank)
-        r, d, w = COLLISIONS[name]
+        r, d, w, walls = COLLISIONS[name]
         desc = ("cell packing: 4096 RBC (642 vertices) at rest with random positions and orientations in a "
                 f"cube at 35 % volume fraction (overlapping), 5 iterations, collisions radius {r} um, "
-                f"delta {d} um, weight {w} nN/um, contact detection inside every step")
+                f"delta {d} um, weight {w} nN/um, contact detection inside every step"
+                + ("; box walls 1 um outside the initial cells" if walls else ""))
     elif name == "small":
         b = I.homogeneous_rbc_batch(ncells=64, seed=1001 + 100 * rank)
         desc = "64 RBC (642 vertices), 5 iterations"
@@ -97,8 +106,8 @@ def _oracle_worker(args):
     mesh_v, mesh_t, mat, dt, cells, tol = args
     ct = O.CellType(mesh_v, mesh_t, mat, dt)
     t0 = time.perf_counter()
-    for (x, v, f, it, con) in cells:
-        O.step(ct.rest, ct.solver, x, v, f, int(it), tol=tol, contact=con)
+    for (x, v, f, it, con, wl) in cells:
+        O.step(ct.rest, ct.solver, x, v, f, int(it), tol=tol, contact=con, walls=wl)
     return time.perf_counter() - t0, len(cells)
 
 
@@ -123,7 +132,7 @@ def oracle_baseline(b, sample_cells: int, workers: int, tol: float = 0.0, collis
     if collisions is not None:
         # the sampled cells' contact detection (over the whole batch) is part of their step
         from oracle import npfem_oracle as O
-        radius, delta, weight = collisions
+        radius, delta, weight = collisions[:3]
         ots = [O.CellType(t.mesh.verts, t.mesh.tris, _mat(t), b.dt) for t in b.types]
         verts = [i for c in sel for i in range(int(b.offsets[c]), int(b.offsets[c + 1]))]
         t0 = time.perf_counter()
@@ -131,6 +140,8 @@ def oracle_baseline(b, sample_cells: int, workers: int, tol: float = 0.0, collis
         for c in sel:
             contacts[c] = (*O.cell_contacts(con, int(b.offsets[c]), int(b.offsets[c + 1])), delta, weight)
         t_detect = time.perf_counter() - t0
+    box = _box(b, collisions)
+    walls = None if box is None else (box[0], box[1], collisions[1], collisions[2])
     by_type = {}
     for c in sel:
         by_type.setdefault(int(b.type_of_cell[c]), []).append(c)
@@ -141,7 +152,7 @@ def oracle_baseline(b, sample_cells: int, workers: int, tol: float = 0.0, collis
         for ch in chunks:
             if ch:
                 jobs.append((ty.mesh.verts, ty.mesh.tris, _mat(ty), b.dt,
-                             [(*b.cell_state(c), b.iters[c], contacts.get(c)) for c in ch], tol))
+                             [(*b.cell_state(c), b.iters[c], contacts.get(c), walls) for c in ch], tol))
     ctx = mp.get_context("spawn")
     env_backup = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
     for k in env_backup:
@@ -261,7 +272,7 @@ def run_ours(args, rank, world, local_rank):
     batch = native.Batch(types, b.type_of_cell, prec)
     coll = COLLISIONS.get(args.workload)
     if coll is not None:
-        batch.set_collisions(*coll)
+        batch.set_collisions(coll[0], coll[1], coll[2], box=_box(b, coll))
     x0 = torch.tensor(b.x, dtype=tdt, device=dev)
     v0 = torch.tensor(b.v, dtype=tdt, device=dev)
     f = torch.tensor(b.f, dtype=tdt, device=dev)
@@ -305,8 +316,10 @@ def run_ours(args, rank, world, local_rank):
                 ot[t] = O.CellType(ty.mesh.verts, ty.mesh.tris, _mat(ty), b.dt)
             s = b.cell_slice(c)
             con = None if scon is None else (*O.cell_contacts(scon, s.start, s.stop), coll[1], coll[2])
+            bx = _box(b, coll)
+            wl = None if bx is None else (bx[0], bx[1], coll[1], coll[2])
             r = O.step(ot[t].rest, ot[t].solver, xin[:, s].T, vin[:, s].T, fin[:, s].T, int(b.iters[c]), tol=tol,
-                       contact=con)
+                       contact=con, walls=wl)
             rad = np.max(np.linalg.norm(r.x - r.x.mean(axis=0), axis=1))
             errs.append(float(np.max(np.abs(xg[:, s].T - r.x)) / rad))
             counts.append((int(done_gpu[c]), len(r.alphas)))
@@ -478,6 +491,7 @@ def run_ours(args, rank, world, local_rank):
                    "groups": {str(t): batch.get_groups(t) for t in sorted(set(int(q) for q in b.type_of_cell))},
                    "autotune": tuned,
                    "collisions": ({"radius_um": coll[0], "delta_um": coll[1], "weight_nN_per_um": coll[2],
+                                   "walls": bool(coll[3]),
                                    "detection": "normals, spatial hash, scan, scatter, query kernels inside the step",
                                    "detection_ms_per_step": detect_ms / args.steps}
                                   if coll is not None else None),
@@ -659,7 +673,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="homog4096", choices=["homog4096", "hetero10k", "stress20k", "homog1776", "homog2562",
-                                                            "pack4096", "small"])
+                                                            "pack4096", "packbox4096", "small"])
     ap.add_argument("--precision", default="fp32form", choices=["fp32form", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=128)
