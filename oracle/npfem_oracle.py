@@ -692,10 +692,13 @@ def implicit_adjoint(ct: CellType, x_n: np.ndarray, v_n: np.ndarray, f_ext: np.n
     With grad f(x*; y, w) = 0, H = grad^2 f(x*) and v* = (x* - x_n)/dt:
       H lam = dL/dx* + dL/dv* / dt,
       dL/dy = (M/dt^2) lam   (d grad f / dy = -M/dt^2),
-      dL/dx_n = dL/dy - dL/dv*/dt,  dL/dv_n = dt dL/dy,  dL/df = (dt^2/m) dL/dy = lam,
+      dL/dx_n = dL/dy - dL/dv*/dt (+ C lam / dt with Rayleigh damping),
+      dL/dv_n = dt dL/dy,  dL/df = (dt^2/m) dL/dy = lam,
       dL/dw_q = -lam . d(grad f)/dw_q  for the material weights (strain, bend, area, vol).
     H and d(grad f)/dw come from complex-step differentiation of the analytic gradient
-    (exact to rounding); lam from a dense solve.  Arrays [n,3]; returns gx, gv, gf, gw[4]."""
+    (exact to rounding); lam from a dense solve.  With Rayleigh damping the dissipation
+    term is part of f (its matrix C = c_alpha M + c_beta L(w) depends on the weights).
+    Arrays [n,3]; returns gx, gv, gf, gw[4]."""
     rs = ct.rest
     dt = rs.dt
     n = rs.n
@@ -703,18 +706,27 @@ def implicit_adjoint(ct: CellType, x_n: np.ndarray, v_n: np.ndarray, f_ext: np.n
     xs = x_star - ctr
     y = (x_n - ctr) + dt * v_n + dt * dt * f_ext / rs.mass[:, None]
     ws0 = np.ones(4) if ct.w_scale is None else np.asarray(ct.w_scale, dtype=np.float64)
+    damped = rs.c_alpha != 0.0 or rs.c_beta != 0.0
+    xn = x_n - ctr
+
+    def damp(ws):     # the step's Rayleigh dissipation term (its matrix depends on the weights)
+        return (xn, damping_matrix(rs, ws)) if damped else None
+
     h = 1e-30
     H = np.zeros((3 * n, 3 * n))
+    d0 = damp(ws0)
     for k in range(3 * n):
         e = np.zeros(3 * n, dtype=complex)
         e[k] = 1j * h
-        g = objective(rs, xs + e.reshape(n, 3), y, ws0)[1]
+        g = objective(rs, xs + e.reshape(n, 3), y, ws0, None, d0)[1]
         H[:, k] = np.imag(g).ravel() / h
     H = 0.5 * (H + H.T)
     b = (gx_next + gv_next / dt).ravel()
     lam = np.linalg.solve(H, b).reshape(n, 3)
     dLdy = rs.mass[:, None] / dt ** 2 * lam
     gx = dLdy - gv_next / dt
+    if damped:    # the dissipation term depends on x_n directly: d grad f / d x_n gains -C/dt
+        gx = gx + (d0[1] @ lam) / dt
     gv = dt * dLdy
     gf = lam.copy()
     gw = np.zeros(4)
@@ -722,7 +734,7 @@ def implicit_adjoint(ct: CellType, x_n: np.ndarray, v_n: np.ndarray, f_ext: np.n
     for q in range(4):
         ws = ws0.astype(complex)
         ws[q] += 1j * h
-        dg = np.imag(objective(rs, xs, y, ws)[1]) / h
+        dg = np.imag(objective(rs, xs, y, ws, None, damp(ws))[1]) / h
         gw[q] = -np.sum(lam * dg) / (w_mat[q] * ws0[q])
     return gx, gv, gf, gw
 

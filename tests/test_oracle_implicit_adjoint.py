@@ -1,6 +1,7 @@
 """Pin of the oracle's implicit-function adjoint: the gradient of L = gx . x* + gv . v*
 through the converged minimiser of a step equals central differences of a step run to
-convergence, for every input kind (positions, velocities, forces, material weights)."""
+convergence, for every input kind (positions, velocities, forces, material weights), with
+and without Rayleigh damping (whose dissipation term depends on x_n directly)."""
 import numpy as np
 import pytest
 
@@ -8,7 +9,7 @@ from oracle import npfem_oracle as O
 from paper_2011_04332_b300 import inputs as I
 
 DT = 0.1
-MAT = (1.0, 0.05, 10.0, 10.0, 1.1)
+MAT0 = (1.0, 0.05, 10.0, 10.0, 1.1)
 
 
 def _converged(mat, x, v, f, mesh):
@@ -18,8 +19,10 @@ def _converged(mat, x, v, f, mesh):
     return ct, r
 
 
-@pytest.mark.parametrize("mesh_fn", [I.icosahedron, lambda: I.rbc_mesh(1)])
-def test_implicit_adjoint_matches_central_differences(mesh_fn):
+@pytest.mark.parametrize("mesh_fn,damping", [(I.icosahedron, ()), (lambda: I.rbc_mesh(1), ()),
+                                             (lambda: I.rbc_mesh(1), (0.5, 1.0))])
+def test_implicit_adjoint_matches_central_differences(mesh_fn, damping):
+    MAT = MAT0 + damping
     m = mesh_fn()
     rng = np.random.default_rng(41)
     x = m.verts * np.array([1.1, 0.95, 1.0]) + 0.02 * rng.standard_normal(m.verts.shape) + 3.0
@@ -30,7 +33,8 @@ def test_implicit_adjoint_matches_central_differences(mesh_fn):
     ct, r = _converged(MAT, x, v, f, m)
     gx, gv, gf, gw = O.implicit_adjoint(ct, x, v, f, r.x, gx_next, gv_next)
 
-    def loss(mat=MAT, x=x, v=v, f=f):
+    def loss(mat=None, x=x, v=v, f=f):
+        mat = MAT if mat is None else mat
         _, rr = _converged(mat, x, v, f, m)
         return float(np.sum(gx_next * rr.x) + np.sum(gv_next * rr.v))
 
