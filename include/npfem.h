@@ -185,7 +185,8 @@ npfem_status npfem_step(npfem_batch* batch, void* x, void* v, const void* f_ext,
  * slot for a 642-vertex type).  Asynchronous on `stream`.
  * opts->tol must be 0 (the adjoint differentiates fixed iteration counts); opts->iters_done
  * is ignored.
- * Errors: INVALID_ARG (null pointer, FP32-form batch, tol != 0), CUDA, OOM. */
+ * Errors: INVALID_ARG (null pointer, FP32-form batch, tol != 0, collisions on, a type with
+ * Rayleigh damping: use npfem_step_adjoint_implicit), CUDA, OOM. */
 npfem_status npfem_step_adjoint(npfem_batch* batch, const void* x, const void* v, const void* f_ext,
                                 const int32_t* iters, const npfem_solver_opts* opts,
                                 const double* gx_next, const double* gv_next, double* gx, double* gv,
@@ -207,10 +208,12 @@ npfem_status npfem_step_adjoint(npfem_batch* batch, const void* x, const void* v
  *   cg_max_iters at most this many CG iterations per cell (>= 1)
  *   status_out   out [ncells] or NULL: the forward step's flags, with 16 ORed in where CG
  *                stopped before cg_tol (budget used, or H not positive along a direction).
+ * With Rayleigh damping (c_alpha, c_beta of a type) the dissipation term is part of f: it
+ * enters H and the weight derivatives, and since it depends on x_n directly,
+ * gx gains C lam / dt.
  * Arrays as in npfem_step_adjoint.  The first call allocates two [3][N_total] FP64 copies
  * and the adjoint workspace.  Asynchronous on `stream`.  Errors: INVALID_ARG (null
- * pointer, FP32-form batch, bad cg_tol / cg_max_iters, collisions on, a damped type),
- * CUDA, OOM. */
+ * pointer, FP32-form batch, bad cg_tol / cg_max_iters, collisions on), CUDA, OOM. */
 npfem_status npfem_step_adjoint_implicit(npfem_batch* batch, const void* x, const void* v, const void* f_ext,
                                          const int32_t* iters, const npfem_solver_opts* opts,
                                          const double* gx_next, const double* gv_next, double* gx, double* gv,

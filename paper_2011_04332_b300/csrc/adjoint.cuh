@@ -84,8 +84,11 @@ __device__ __forceinline__ void vzero(double* y, int len, int lane) {
   for (int i = lane; i < len; i += 32) y[i] = 0.0;
 }
 
-// Hessian-vector product out = grad^2 f(x) Vv at x = x_n + U (inertia included), and
-// wd[q] = Vv . d(grad f)/d(w_q) for the four material weights.
+__device__ void matrix_weight_forms(const DevTypeView<double>& ty, const double* a, const double* b, double* fs,
+                                    double* fb, int lane);
+
+// Hessian-vector product out = grad^2 f(x) Vv at x = x_n + U (inertia and Rayleigh damping
+// included), and wd[q] = Vv . d(grad f)/d(w_q) for the four material weights.
 __device__ void hessian_vector(const DevTypeView<double>& ty, const CellWs<double>& w, const double* U,
                                const double* Vv, double* out, V3<double> cvol, double wd[4], int lane) {
   const int n = ty.n, T = ty.T, E = ty.E;
@@ -196,6 +199,10 @@ __device__ void hessian_vector(const DevTypeView<double>& ty, const CellWs<doubl
     wb_sum.add(ue * dot(dK, K - p));
     st3(w.hbuf, h, hvec);
   }
+  // Rayleigh damping: the quadratic (c_beta/dt) L and (c_alpha/dt) M terms, constant Hessians
+  if (ty.damp_l != 0.0)
+    damping_elastic<double>(ty.tris, ty.Dinv, ty.w_tri, ty.hinges, ty.c_hinge, ty.w_hinge, T, E, ty.damp_l, Vv,
+                            w.corner, w.hbuf, lane);
   __syncwarp();
   const double idt2 = 1.0 / (ty.dt * ty.dt);
   for (int vtx = lane; vtx < n; vtx += 32) {
@@ -210,8 +217,16 @@ __device__ void hessian_vector(const DevTypeView<double>& ty, const CellWs<doubl
     }
     st3(out, vtx, g);
   }
+  if (ty.damp_m != 0.0) damping_mass<double>(ty.mass, n, ty.damp_m, Vv, out, lane);
   wd[0] = ws_sum.total();
   wd[1] = wb_sum.total();
+  if (ty.damp_l != 0.0) {
+    // d/dw of (c_beta/dt) L(w) U: the elastic matrix's weight forms between Vv and U
+    double fs, fb;
+    matrix_weight_forms(ty, Vv, U, &fs, &fb, lane);
+    wd[0] += ty.damp_l * fs;
+    wd[1] += ty.damp_l * fb;
+  }
   __syncwarp();
 }
 
@@ -467,13 +482,42 @@ __global__ void __launch_bounds__(128) npfem_adjoint_kernel(DevTypeView<double> 
   }
 }
 
+// out = C a / dt = (c_alpha/dt) M a + (c_beta/dt) L a (Rayleigh damping), through the
+// element buffers and the gradient gather of the step.
+__device__ void apply_rayleigh(const DevTypeView<double>& ty, const CellWs<double>& w, const double* a,
+                               double* out, int lane) {
+  const int n = ty.n;
+  for (int i = lane; i < 9 * ty.T; i += 32) w.corner[i] = 0.0;
+  for (int i = lane; i < 3 * ty.E; i += 32) w.hbuf[i] = 0.0;
+  __syncwarp();
+  if (ty.damp_l != 0.0)
+    damping_elastic<double>(ty.tris, ty.Dinv, ty.w_tri, ty.hinges, ty.c_hinge, ty.w_hinge, ty.T, ty.E, ty.damp_l,
+                            a, w.corner, w.hbuf, lane);
+  __syncwarp();
+  for (int vtx = lane; vtx < n; vtx += 32) {
+    V3<double> g = (ty.damp_m * __ldg(&ty.mass[vtx])) * ld3(a, vtx);
+    const int e0 = __ldg(&ty.inc_ptr[vtx]), e1 = __ldg(&ty.inc_ptr[vtx + 1]);
+    for (int e = e0; e < e1; ++e) {
+      const int code = __ldg(&ty.inc_code[e]);
+      if (code >= 0)
+        g = g + ld3(w.corner, code);
+      else
+        g = g + __ldg(&ty.inc_coef[e]) * ld3(w.hbuf, (-code - 1) >> 2);
+    }
+    st3(out, vtx, g);
+  }
+  __syncwarp();
+}
+
 // ------------------------------------------------------------------ implicit adjoint
 // Gradients through the converged minimiser x* of the step objective (the solver run to
 // convergence, Implementation and architecture section) by the implicit-function
 // theorem: grad f(x*; y, w) = 0, so with H = grad^2 f(x*)
 //   H lam = dL/dx* + dL/dv*/dt   (v* = (x* - x_n)/dt),
 //   dL/dy = (M/dt^2) lam,  dL/dx_n = dL/dy - dL/dv*/dt,  dL/dv_n = dt dL/dy,
-//   dL/df = lam,  dL/dw_q = -lam . d(grad f)/dw_q.
+//   dL/df = lam,  dL/dw_q = -lam . d(grad f)/dw_q,
+// and with Rayleigh damping, whose dissipation term depends on x_n directly, dL/dx_n gains
+// C lam / dt (the Hessian and the weight terms include the damping already).
 // lam comes from conjugate gradients on H (Hessian-vector products), preconditioned by
 // the prefactored projective-dynamics matrix A^-1; the forward step that produced x* is
 // the caller's (npfem_step on copies of the inputs).
@@ -571,13 +615,15 @@ __global__ void __launch_bounds__(128) npfem_adjoint_implicit_kernel(DevTypeView
     }
     // weight derivatives: wd[q] = lam . d(grad f)/d(w_q)
     hessian_vector(ty, w, U, lam, hp, cvol, wd, lane);
+    const bool damped = ty.damp_m != 0.0 || ty.damp_l != 0.0;
+    if (damped) apply_rayleigh(ty, w, lam, z, lane);  // z <- C lam / dt
     for (int vtx = lane; vtx < n; vtx += 32) {
       const double mi = __ldg(&ty.mass[vtx]);
       for (int c = 0; c < 3; ++c) {
         const double l = lam[3 * vtx + c];
         const double dldy = mi / (dt * dt) * l;
         const double gvv = A.gv_next ? A.gv_next[c * Nt + off + vtx] : 0.0;
-        A.gx[c * Nt + off + vtx] = dldy - gvv / dt;
+        A.gx[c * Nt + off + vtx] = dldy - gvv / dt + (damped ? z[3 * vtx + c] : 0.0);
         A.gv[c * Nt + off + vtx] = dt * dldy;
         A.gf[c * Nt + off + vtx] = l;
       }

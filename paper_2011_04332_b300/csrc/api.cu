@@ -942,7 +942,10 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: collisions are enabled (contacts are not differentiated)");
   for (const npfem_cell_type* t : b->types)
     if (t->host.c_alpha != 0.0 || t->host.c_beta != 0.0)
-      return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: a cell type has damping (damping is not differentiated)");
+      return fail(NPFEM_ERR_INVALID_ARG,
+                  "step_adjoint: a cell type has damping (the unrolled adjoint does not differentiate it; "
+                  "npfem_step_adjoint_implicit does)");
+
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   npfem_status arc = ensure_adjoint_workspace(b);
   if (arc != NPFEM_OK) return arc;
@@ -1002,10 +1005,7 @@ npfem_status npfem_step_adjoint_implicit(npfem_batch* b, const void* x, const vo
   if (b->coll)
     return fail(NPFEM_ERR_INVALID_ARG,
                 "step_adjoint_implicit: collisions are enabled (contacts are not differentiated)");
-  for (const npfem_cell_type* t : b->types)
-    if (t->host.c_alpha != 0.0 || t->host.c_beta != 0.0)
-      return fail(NPFEM_ERR_INVALID_ARG,
-                  "step_adjoint_implicit: a cell type has damping (damping is not differentiated)");
+
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = sizeof(double) * 3 * (size_t)b->n_total;
   if (!b->d_xstar) {

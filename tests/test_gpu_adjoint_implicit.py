@@ -18,9 +18,14 @@ def _native():
     return native
 
 
-def _batch(b):
+def _materials(b, damping):
+    return [t.material.as_tuple() + tuple(damping) for t in b.types]
+
+
+def _batch(b, damping=()):
     nat = _native()
-    types = [nat.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
+    mats = _materials(b, damping)
+    types = [nat.CellType(t.mesh.verts, t.mesh.tris, mats[k], b.dt) for k, t in enumerate(b.types)]
     batch = nat.Batch(types, b.type_of_cell, nat.FP64)
     batch.set_mode(False)
     return types, batch
@@ -50,11 +55,14 @@ def _forward(batch, b, x, v, f):
     return X.cpu().numpy(), V.cpu().numpy(), res.cpu().numpy()
 
 
-def test_implicit_adjoint_matches_oracle():
-    """Small mixed batch (42-vertex RBC and platelet, 162-vertex RBC): every gradient
-    against the oracle's implicit adjoint at its own converged state."""
+@pytest.mark.parametrize("damping", [(), (0.5, 1.0)])
+def test_implicit_adjoint_matches_oracle(damping):
+    """Small mixed batch (42-vertex RBC and platelet, 162-vertex RBC), without and with
+    Rayleigh damping: every gradient against the oracle's implicit adjoint at its own
+    converged state."""
     b = I.small_mixed_batch()
-    _, batch = _batch(b)
+    _, batch = _batch(b, damping)
+    mats = _materials(b, damping)
     rng = np.random.default_rng(51)
     gxn = rng.standard_normal(b.x.shape)
     gvn = 0.1 * rng.standard_normal(b.x.shape)
@@ -63,7 +71,7 @@ def test_implicit_adjoint_matches_oracle():
     for c in range(b.ncells):
         s = b.cell_slice(c)
         t = b.types[int(b.type_of_cell[c])]
-        ct = O.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt)
+        ct = O.CellType(t.mesh.verts, t.mesh.tris, mats[int(b.type_of_cell[c])], b.dt)
         xc, vc, fc = b.cell_state(c)
         r = O.step(ct.rest, ct.solver, xc, vc, fc, 400, tol=1e-13)
         assert r.residual < 1e-11
