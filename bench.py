@@ -598,7 +598,9 @@ def measure_adjoint_implicit(dev, b, reps: int = 5, fwd_tol: float = 1e-10, budg
 
 # Sources that define what the step kernels execute: the device code and the host
 # packer that lays out the factor they stream (launch plumbing is excluded).
-KERNEL_SOURCES = ("npfem_internal.h", "step_kernel.cuh", "split_kernels.cuh", "adjoint.cuh", "host_setup.cpp",
+# The sources a step's kernels are compiled from; the adjoint kernels (adjoint.cuh) take
+# no part in a step, so an edit there leaves the captured solve traffic valid.
+KERNEL_SOURCES = ("npfem_internal.h", "step_kernel.cuh", "split_kernels.cuh", "host_setup.cpp",
                   "contact_kernels.cuh")
 
 
