@@ -184,9 +184,9 @@ npfem_status npfem_step(npfem_batch* batch, void* x, void* v, const void* f_ext,
  * The first call on a batch allocates its adjoint workspace (about 2 MB per warp
  * slot for a 642-vertex type).  Asynchronous on `stream`.
  * opts->tol must be 0 (the adjoint differentiates fixed iteration counts); opts->iters_done
- * is ignored.
- * Errors: INVALID_ARG (null pointer, FP32-form batch, tol != 0, collisions on, a type with
- * Rayleigh damping: use npfem_step_adjoint_implicit), CUDA, OOM. */
+ * is ignored.  With Rayleigh damping the dissipation term of every iterate's gradient
+ * depends on x_n directly, and the matrix weight terms carry the (1 + c_beta/dt) factor.
+ * Errors: INVALID_ARG (null pointer, FP32-form batch, tol != 0, collisions on), CUDA, OOM. */
 npfem_status npfem_step_adjoint(npfem_batch* batch, const void* x, const void* v, const void* f_ext,
                                 const int32_t* iters, const npfem_solver_opts* opts,
                                 const double* gx_next, const double* gv_next, double* gx, double* gv,

@@ -86,6 +86,8 @@ __device__ __forceinline__ void vzero(double* y, int len, int lane) {
 
 __device__ void matrix_weight_forms(const DevTypeView<double>& ty, const double* a, const double* b, double* fs,
                                     double* fb, int lane);
+__device__ void apply_rayleigh(const DevTypeView<double>& ty, const CellWs<double>& w, const double* a,
+                               double* out, int lane);
 
 // Hessian-vector product out = grad^2 f(x) Vv at x = x_n + U (inertia and Rayleigh damping
 // included), and wd[q] = Vv . d(grad f)/d(w_q) for the four material weights.
@@ -404,13 +406,14 @@ __device__ void reverse_cell(const DevTypeView<double>& ty, const StepParams& P,
       vaxpy(aw.RB, bb * aw.rho[i], yi, len, lane);
       __syncwarp();
     }
-    // r_0 = A^-1 q_h: dL/dq_h = A^-1 dL/dr_0; dL/dw via dA/dw
+    // r_0 = A^-1 q_h: dL/dq_h = A^-1 dL/dr_0; dL/dw via dA/dw (A carries the elastic part
+    // L as (1 + c_beta/dt) L under Rayleigh damping)
     global_solve<double>(ty, w.z, P.z_in_smem != 0, aw.RB, aw.QB, lane, P.solve_per_coord != 0);
     {
       double fs, fb;
       matrix_weight_forms(ty, aw.QB, aw.Rs, &fs, &fb, lane);
-      wacc[0] -= fs;
-      wacc[1] -= fb;
+      wacc[0] -= (1.0 + ty.damp_l) * fs;
+      wacc[1] -= (1.0 + ty.damp_l) * fb;
     }
     for (int t = h - 1; t >= 0; --t) {
       const int i = plist[t];
@@ -439,6 +442,18 @@ __device__ void reverse_cell(const DevTypeView<double>& ty, const StepParams& P,
   // g_0 = grad f(x_0)
   hessian_vector(ty, w, tU, aw.gbar, aw.HV, cvol, wd, lane);
   for (int q = 0; q < 4; ++q) wacc[q] += wd[q];
+  // Rayleigh damping: every g_k holds C (x_k - x_n) / dt, so dL/dx_n gains
+  // -C/dt times the sum of all gradient adjoints (into RB, summed in DB)
+  const bool damped = ty.damp_m != 0.0 || ty.damp_l != 0.0;
+  if (damped) {
+    for (int e = lane; e < len; e += 32) {
+      double sg = 0.0;
+      for (int k = 0; k <= K; ++k) sg += aw.gbar[(size_t)k * len + e];
+      aw.DB[e] = sg;
+    }
+    __syncwarp();
+    apply_rayleigh(ty, w, aw.DB, aw.RB, lane);
+  }
   // x_0 = y; y = x_n + dt v_n + dt^2 M^-1 f;  v_{n+1} = (x_K - x_n)/dt
   for (int vtx = lane; vtx < n; vtx += 32) {
     const double mi = __ldg(&ty.mass[vtx]);
@@ -446,7 +461,7 @@ __device__ void reverse_cell(const DevTypeView<double>& ty, const StepParams& P,
       const int e = 3 * vtx + c;
       const double yb = aw.YB[e] - mi / (dt * dt) * aw.gbar[e] + aw.XB[e] + aw.HV[e];
       const double gvv = A.gv_next ? A.gv_next[c * Nt + off + vtx] : 0.0;
-      A.gx[c * Nt + off + vtx] = yb - gvv / dt;
+      A.gx[c * Nt + off + vtx] = yb - gvv / dt - (damped ? aw.RB[e] : 0.0);
       A.gv[c * Nt + off + vtx] = dt * yb;
       A.gf[c * Nt + off + vtx] = dt * dt / mi * yb;
     }

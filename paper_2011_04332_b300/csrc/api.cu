@@ -940,11 +940,6 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: tol must be 0 (fixed iteration counts)");
   if (b->coll)
     return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: collisions are enabled (contacts are not differentiated)");
-  for (const npfem_cell_type* t : b->types)
-    if (t->host.c_alpha != 0.0 || t->host.c_beta != 0.0)
-      return fail(NPFEM_ERR_INVALID_ARG,
-                  "step_adjoint: a cell type has damping (the unrolled adjoint does not differentiate it; "
-                  "npfem_step_adjoint_implicit does)");
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   npfem_status arc = ensure_adjoint_workspace(b);

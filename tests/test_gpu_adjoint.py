@@ -22,9 +22,10 @@ def _native():
     return native
 
 
-def gpu_adjoint(b, lam_x, lam_v, iters=None):
+def gpu_adjoint(b, lam_x, lam_v, iters=None, damping=()):
     nat = _native()
-    types = [nat.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt) for t in b.types]
+    types = [nat.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple() + tuple(damping), b.dt)
+             for t in b.types]
     batch = nat.Batch(types, b.type_of_cell, nat.FP64)
     dev = torch.device("cuda:0")
     T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
@@ -40,15 +41,16 @@ def gpu_adjoint(b, lam_x, lam_v, iters=None):
     return (gx.cpu().numpy(), gv.cpu().numpy(), gf.cpu().numpy(), gw.cpu().numpy())
 
 
-def oracle_jvp(b, dx, dv, df, dws):
-    """Complex-step J.delta of (x_{n+1}, v_{n+1}); dws[type] perturbs the weight scale."""
+def oracle_jvp(b, dx, dv, df, dws, damping=()):
+    """Complex-step J.delta of (x_{n+1}, v_{n+1}); dws[type] perturbs the weight scale;
+    damping = (c_alpha, c_beta) joins every type's material."""
     out_x = np.zeros_like(b.x)
     out_v = np.zeros_like(b.x)
     for c in range(b.ncells):
         t = int(b.type_of_cell[c])
         spec = b.types[t]
         ws = np.ones(4, complex) + 1j * H_CS * dws[t]
-        ct = O.CellType(spec.mesh.verts, spec.mesh.tris, spec.material.as_tuple(), b.dt, ws)
+        ct = O.CellType(spec.mesh.verts, spec.mesh.tris, spec.material.as_tuple() + tuple(damping), b.dt, ws)
         s = b.cell_slice(c)
         x = b.x[:, s].T + 1j * H_CS * dx[:, s].T
         v = b.v[:, s].T + 1j * H_CS * dv[:, s].T
@@ -59,8 +61,10 @@ def oracle_jvp(b, dx, dv, df, dws):
     return out_x, out_v
 
 
-@pytest.mark.parametrize("seed", [3, 4])
-def test_adjoint_dot_product_against_oracle_forward_mode(seed):
+@pytest.mark.parametrize("seed,damping", [(3, ()), (4, ()), (5, (0.5, 1.0))])
+def test_adjoint_dot_product_against_oracle_forward_mode(seed, damping):
+    """Without and with Rayleigh damping (whose dissipation term makes every iterate's
+    gradient depend on x_n directly)."""
     b = I.small_mixed_batch(seed=seed, iters=(3, 6))
     rng = np.random.default_rng(seed)
     lam_x = rng.standard_normal(b.x.shape)
@@ -69,9 +73,9 @@ def test_adjoint_dot_product_against_oracle_forward_mode(seed):
     dv = rng.standard_normal(b.x.shape) * 1e-2
     df = rng.standard_normal(b.x.shape) * 1e-3
     dws = rng.standard_normal((len(b.types), 4))
-    jx, jv = oracle_jvp(b, dx, dv, df, dws)
+    jx, jv = oracle_jvp(b, dx, dv, df, dws, damping)
     lhs = np.sum(lam_x * jx) + np.sum(lam_v * jv)
-    gx, gv, gf, gw = gpu_adjoint(b, lam_x, lam_v)
+    gx, gv, gf, gw = gpu_adjoint(b, lam_x, lam_v, damping=damping)
     rhs = np.sum(gx * dx) + np.sum(gv * dv) + np.sum(gf * df)
     for c in range(b.ncells):
         t = int(b.type_of_cell[c])
@@ -82,7 +86,7 @@ def test_adjoint_dot_product_against_oracle_forward_mode(seed):
     for blk in range(4):
         d = [np.zeros_like(dx), np.zeros_like(dv), np.zeros_like(df), np.zeros_like(dws)]
         d[blk] = [dx, dv, df, dws][blk]
-        jx, jv = oracle_jvp(b, *d)
+        jx, jv = oracle_jvp(b, *d, damping=damping)
         l2 = np.sum(lam_x * jx) + np.sum(lam_v * jv)
         r2 = np.sum(gx * d[0]) + np.sum(gv * d[1]) + np.sum(gf * d[2])
         for c in range(b.ncells):

@@ -123,3 +123,46 @@ def test_damping_dissipates_mechanical_energy():
             e = np.array(energies)
             assert np.all(e[1:] <= e[:-1] * (1 + 1e-9)), e
     assert ends[1] < ends[0]
+
+
+def test_damped_complex_step_derivative_matches_central_differences():
+    """The oracle's forward-mode derivative of the damped step (complex step through the
+    whole fixed-iteration step) agrees with central differences of the real step, for
+    perturbations of x_n (which the dissipation term sees directly), v_n, f and the weight
+    scales (which also scale the c_beta part of C and of the solver's matrix)."""
+    mat = (1.0, 0.05, 10.0, 10.0, 1.1, 0.5, 1.0)
+    m = I.rbc_mesh(1)
+    rng = np.random.default_rng(31)
+    x = m.verts * np.array([1.1, 0.95, 1.0]) + 0.02 * rng.standard_normal(m.verts.shape) + 3.0
+    v = 0.1 * rng.standard_normal(x.shape)
+    f = 0.2 * rng.standard_normal(x.shape)
+    ct = _type(m, mat)
+    iters, h, e = 5, 1e-30, 1e-6
+
+    def step(xx, vv, ff, ws=None, c=ct):
+        return O.step(c.rest, c.solver, xx, vv, ff, iters, ws)
+
+    for name in ("x", "v", "f"):
+        d = rng.standard_normal(x.shape)
+        arg = {"x": x, "v": v, "f": f}
+        cplx = {k: a.astype(complex) for k, a in arg.items()}
+        cplx[name] = arg[name] + 1j * h * d
+        r = step(cplx["x"], cplx["v"], cplx["f"])
+        cs = np.imag(r.x) / h
+        hi = dict(arg)
+        lo = dict(arg)
+        hi[name] = arg[name] + e * d
+        lo[name] = arg[name] - e * d
+        fd = (step(hi["x"], hi["v"], hi["f"]).x - step(lo["x"], lo["v"], lo["f"]).x) / (2 * e)
+        assert np.max(np.abs(cs - fd)) <= 1e-6 * np.max(np.abs(cs)), name
+    for q in range(4):
+        ws = np.ones(4, complex)
+        ws[q] += 1j * h
+        ctc = O.CellType(m.verts, m.tris, mat, DT, ws)
+        csw = np.imag(step(x.astype(complex), v.astype(complex), f.astype(complex), ws, ctc).x) / h
+        wp, wm = np.ones(4), np.ones(4)
+        wp[q] += e
+        wm[q] -= e
+        cp, cm = (O.CellType(m.verts, m.tris, mat, DT, w) for w in (wp, wm))
+        fdw = (step(x, v, f, wp, cp).x - step(x, v, f, wm, cm).x) / (2 * e)
+        assert np.max(np.abs(csw - fdw)) <= 1e-5 * np.max(np.abs(csw)), q
