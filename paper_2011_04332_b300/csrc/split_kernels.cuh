@@ -68,21 +68,119 @@ __device__ __forceinline__ CellWs<S> split_ws(char* base, const DevTypeView<S>& 
   return carve<S>(base + kStateBytes, ty.n, ty.T, ty.E, nullptr);
 }
 
-// First half of the two-loop recursion: Q = g, newest -> oldest pairs.
+// Fused streaming passes of the two-loop recursion.  Each lane takes the elements lane,
+// lane + 32, ... in increasing order (the order of a separate pass), four at a time with
+// every load of the four issued before the first store, so the loads of a pass stay in
+// flight together although the pass writes one of the vectors it reads.
+template <typename S>
+__device__ __forceinline__ S update_dot(S* q, S c, const S* u, const S* t, int len, int lane) {
+  // q += c u; returns this lane's partial sum of t . q over the updated values
+  S acc = 0;
+  int e = lane;
+  for (; e + 96 < len; e += 128) {
+    S qv[4], uv[4], tv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      qv[j] = q[e + 32 * j];
+      uv[j] = u[e + 32 * j];
+      tv[j] = t[e + 32 * j];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const S qn = qv[j] + c * uv[j];
+      q[e + 32 * j] = qn;
+      acc += tv[j] * qn;
+    }
+  }
+  for (; e < len; e += 32) {
+    const S qn = q[e] + c * u[e];
+    q[e] = qn;
+    acc += t[e] * qn;
+  }
+  return acc;
+}
+
+template <typename S>
+__device__ __forceinline__ S copy_dot(S* q, const S* g, const S* t, int len, int lane) {
+  // q = g; returns this lane's partial sum of t . g
+  S acc = 0;
+  int e = lane;
+  for (; e + 96 < len; e += 128) {
+    S gv[4], tv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      gv[j] = g[e + 32 * j];
+      tv[j] = t[e + 32 * j];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      q[e + 32 * j] = gv[j];
+      acc += tv[j] * gv[j];
+    }
+  }
+  for (; e < len; e += 32) {
+    const S gq = g[e];
+    q[e] = gq;
+    acc += t[e] * gq;
+  }
+  return acc;
+}
+
+template <typename S>
+__device__ __forceinline__ void update_negate(const S* q, S c, const S* u, const S* g, S* d, Acc<S>& agd, int len,
+                                              int lane) {
+  // d = -(q + c u); agd accumulates g . d
+  int e = lane;
+  for (; e + 96 < len; e += 128) {
+    S qv[4], uv[4], gv[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      qv[j] = q[e + 32 * j];
+      uv[j] = u[e + 32 * j];
+      gv[j] = g[e + 32 * j];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const S dv = -(qv[j] + c * uv[j]);
+      d[e + 32 * j] = dv;
+      agd.add_prod(gv[j], dv);
+    }
+  }
+  for (; e < len; e += 32) {
+    const S dv = -(q[e] + c * u[e]);
+    d[e] = dv;
+    agd.add_prod(g[e], dv);
+  }
+}
+
+// First half of the two-loop recursion: Q = g, newest -> oldest pairs.  Each pass applies
+// one pair's update and accumulates the next pair's s . Q from the updated values it holds
+// in registers, so Q is read once per pair (the products and each lane's summation order
+// are those of separate dot and update passes).
 template <typename S>
 __device__ __forceinline__ void two_loop_first(const CellWs<S>& w, CellState<S>* st, const S* G, int len,
                                                int lane) {
-  for (int i = lane; i < len; i += 32) w.Q[i] = G[i];
-  __syncwarp();
-  for (int q = 0; q < st->hcount; ++q) {
-    int i = (st->hhead - 1 - q + kHistory) % kHistory;
-    const S* si = w.hs + (size_t)i * len;
-    const S* yi = w.hy + (size_t)i * len;
-    S a = st->rho[i] * vdot<S>(si, w.Q, len, lane);
-    if (lane == 0) st->aco[i] = a;
-    for (int e = lane; e < len; e += 32) w.Q[e] -= a * yi[e];
+  const int hc = st->hcount, hh = st->hhead;
+  if (hc == 0) {
+    for (int e = lane; e < len; e += 32) w.Q[e] = G[e];
     __syncwarp();
+    return;
   }
+  int i = (hh - 1 + kHistory) % kHistory;
+  S acc = copy_dot<S>(w.Q, G, w.hs + (size_t)i * len, len, lane);
+  for (int q = 0; q < hc; ++q) {
+    const S a = st->rho[i] * warp_sum<S>(acc);
+    if (lane == 0) st->aco[i] = a;
+    const S* yi = w.hy + (size_t)i * len;
+    if (q + 1 < hc) {
+      const int inext = (hh - 1 - (q + 1) + kHistory) % kHistory;
+      acc = update_dot<S>(w.Q, -a, yi, w.hs + (size_t)inext * len, len, lane);
+      i = inext;
+    } else {
+      for (int e = lane; e < len; e += 32) w.Q[e] -= a * yi[e];
+    }
+  }
+  __syncwarp();
 }
 
 // K7: residual, x_{n+1} = anchor + X + U, v_{n+1} = U / dt, status.
@@ -211,8 +309,10 @@ __global__ void __launch_bounds__(128, IterOccupancy<S>::min_blocks) npfem_k_beg
       continue;
     }
     if (lane == 0) P.act_out[atomicAdd(P.act_count_out, 1)] = item;
+    // the history is empty here, so the first half of the two-loop recursion is Q = g
     NPFEM_PHASE_BEGIN(t_loop1)
-    two_loop_first<S>(w, st, w.G, len, lane);
+    for (int e = lane; e < len; e += 32) w.Q[e] = w.G[e];
+    __syncwarp();
     NPFEM_PHASE_END(t_loop1, kPhTwoLoop, P, lane)
   }
 }
@@ -410,18 +510,41 @@ __global__ void __launch_bounds__(128, IterOccupancy<S>::min_blocks) npfem_k_ite
     const double fx = st->fx;
     int hcount = st->hcount, hhead = st->hhead;
     NPFEM_PHASE_BEGIN(t_loop2)
-    for (int q = hcount - 1; q >= 0; --q) {
-      int i = (hhead - 1 - q + kHistory) % kHistory;
-      const S* si = w.hs + (size_t)i * len;
-      const S* yi = w.hy + (size_t)i * len;
-      S b = st->rho[i] * vdot<S>(yi, w.Q, len, lane);
-      S c = st->aco[i] - b;
-      for (int e = lane; e < len; e += 32) w.Q[e] += c * si[e];
-      __syncwarp();
+    // Second half, oldest -> newest pairs, fused like the first: each pass applies one
+    // pair's update and accumulates the next pair's y . Q; the last pass writes D = -Q
+    // and accumulates g . D (Q's final value is not kept: the fallback below and the next
+    // first half overwrite it).
+    double gd;
+    {
+      Acc<S> agd;
+      if (hcount == 0) {
+        for (int e = lane; e < len; e += 32) {
+          const S d = -w.Q[e];
+          w.D[e] = d;
+          agd.add_prod(G[e], d);
+        }
+      } else {
+        int i = (hhead - hcount + kHistory) % kHistory;
+        S acc = 0;
+        {
+          const S* yi = w.hy + (size_t)i * len;
+          for (int e = lane; e < len; e += 32) acc += yi[e] * w.Q[e];
+        }
+        for (int q = hcount - 1; q >= 0; --q) {
+          const S b = st->rho[i] * warp_sum<S>(acc);
+          const S c = st->aco[i] - b;
+          const S* si = w.hs + (size_t)i * len;
+          if (q > 0) {
+            const int inext = (hhead - 1 - (q - 1) + kHistory) % kHistory;
+            acc = update_dot<S>(w.Q, c, si, w.hy + (size_t)inext * len, len, lane);
+            i = inext;
+          } else {
+            update_negate<S>(w.Q, c, si, G, w.D, agd, len, lane);
+          }
+        }
+      }
+      gd = agd.total();
     }
-    for (int e = lane; e < len; e += 32) w.D[e] = -w.Q[e];
-    __syncwarp();
-    double gd = vdot64<S>(G, w.D, len, lane);
     NPFEM_PHASE_END(t_loop2, kPhTwoLoop, P, lane)
     if (!(gd < 0.0)) {  // not a descent direction: drop history, plain PD step
       hcount = 0;
