@@ -150,6 +150,38 @@ def test_history_is_bounded_and_curvature_checked():
     assert np.allclose(O.two_loop(y, [s], [y], gs), s)
 
 
+def test_two_loop_equals_dense_bfgs_inverse_update():
+    """With several pairs the two-loop recursion is the BFGS inverse-Hessian update
+    H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T applied oldest -> newest from
+    H0 = A^-1 (per coordinate), written out densely over the 3n components; the newest
+    pair also satisfies the secant condition H y = s exactly."""
+    rng = np.random.default_rng(7)
+    n = 9
+    B = rng.standard_normal((n, n))
+    A = B @ B.T + n * np.eye(n)
+    gs = O.GlobalSolver(A)
+    S, Y = [], []
+    for _ in range(4):
+        s = rng.standard_normal((n, 3))
+        y = rng.standard_normal((n, 3)) + 3 * s
+        assert np.sum(s * y) > 0
+        S.append(s)
+        Y.append(y)
+    H = np.kron(np.linalg.inv(A), np.eye(3))      # flat index 3 i + c of an (n, 3) array
+    I3n = np.eye(3 * n)
+    for s, y in zip(S, Y):
+        sf, yf = s.ravel(), y.ravel()
+        rho = 1.0 / (sf @ yf)
+        V = I3n - rho * np.outer(yf, sf)
+        H = V.T @ H @ V + rho * np.outer(sf, sf)
+    g = rng.standard_normal((n, 3))
+    r = O.two_loop(g, S, Y, gs)
+    assert np.allclose(r.ravel(), H @ g.ravel(), rtol=1e-12, atol=1e-12 * np.max(np.abs(r)))
+    assert np.allclose(O.two_loop(Y[-1], S, Y, gs), S[-1], rtol=1e-12, atol=1e-12)
+    # the order matters: the reversed history is a different operator
+    assert not np.allclose(O.two_loop(g, S[::-1], Y[::-1], gs), r, rtol=1e-6)
+
+
 def test_complex_step_derivative_matches_central_differences():
     """The oracle's forward-mode derivative (complex step through the whole step,
     forces and weight scales) agrees with central differences of the real step."""
