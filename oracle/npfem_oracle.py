@@ -22,6 +22,11 @@ What it computes, and where each piece comes from
   parameters, Calpha and Cbeta (Setting up new materials section), read here as
   Rayleigh damping C = Calpha M + Cbeta L (L the elastic part of the PD matrix) in
   implicit Euler: a dissipation term in the objective and C/dt in the matrix.
+* Strain limits (optional): the membrane-strain constraint set of a triangle is the set
+  of deformation gradients whose singular values lie in [s_min, s_max] (ShapeOp-style
+  strain limiting, the solver's origin named in the Implementation and architecture
+  section; per-material parameters, Setting up new materials section); the default
+  [1, 1] is the set of rotations.
 * Collisions (optional): contact detection at the start of a step and a penalty
   per contact in the step objective; the paper names collision detection and
   collision forces (Performance figure, "Other"), a collision weight (Collision at
@@ -115,6 +120,8 @@ class RestState:
     dt: float
     c_alpha: float = 0.0    # Rayleigh damping: C = c_alpha M + c_beta L (1/us, us)
     c_beta: float = 0.0
+    s_min: float = 1.0      # strain limits: singular values of F clamped to [s_min, s_max]
+    s_max: float = 1.0
 
 
 def _cot(a: np.ndarray, b: np.ndarray) -> np.ndarray:
@@ -124,7 +131,7 @@ def _cot(a: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 def rest_state(X: np.ndarray, tris: np.ndarray, w_strain: float, w_bend: float,
                w_area: float, w_vol: float, density: float, dt: float,
-               c_alpha: float = 0.0, c_beta: float = 0.0) -> RestState:
+               c_alpha: float = 0.0, c_beta: float = 0.0, s_min: float = 1.0, s_max: float = 1.0) -> RestState:
     """Rest-shape constants of a cell type (mass-lumped linear FE, Introduction).
 
     * Each triangle gets a local orthonormal frame (u along the first edge, w in
@@ -134,6 +141,8 @@ def rest_state(X: np.ndarray, tris: np.ndarray, w_strain: float, w_bend: float,
     * Lumped masses: the cell mass density*V0 is spread by the area share of
       each vertex (a third of the incident rest triangle areas).
     """
+    if not (0.0 < s_min <= 1.0 <= s_max < np.inf):
+        raise ValueError("strain limits must satisfy 0 < s_min <= 1 <= s_max (the rest shape is in the set)")
     X = np.asarray(X, dtype=np.float64)
     tris = np.asarray(tris, dtype=np.int64)
     n = X.shape[0]
@@ -178,7 +187,8 @@ def rest_state(X: np.ndarray, tris: np.ndarray, w_strain: float, w_bend: float,
         np.add.at(vert_area, tris[:, k], area / 3.0)
     mass = density * V0 * vert_area / A0
     return RestState(n, tris, H, Dm_inv, area, w_strain * area, c, kappa0, K0, w_h,
-                     A0, V0, mass, float(w_area), float(w_vol), float(dt), float(c_alpha), float(c_beta))
+                     A0, V0, mass, float(w_area), float(w_vol), float(dt), float(c_alpha), float(c_beta),
+                     float(s_min), float(s_max))
 
 
 def _norm_rows(a: np.ndarray) -> np.ndarray:
@@ -215,6 +225,49 @@ def polar_project(F: np.ndarray) -> (np.ndarray, np.ndarray):
     R = np.einsum("tij,tjk->tik", F, Sinv)
     R[bad] = F[bad]
     return R, bad
+
+
+def clamped_project(F: np.ndarray, s_min: float, s_max: float) -> (np.ndarray, np.ndarray):
+    """Closest 3x2 matrix to F whose singular values lie in [s_min, s_max], for a batch
+    F [T,3,2]: U clamp(Sigma) V^T (strain-limit reading of the membrane-strain
+    constraint set, Setting up new materials section; [1, 1] gives the rotations).
+
+    With C = F^T F = V Sigma^2 V^T the projection is F V diag(k_i) V^T, k_i =
+    clamp(sigma_i)/sigma_i, and V diag(k1, k2) V^T = k2 I + (k1 - k2)/(l1 - l2) (C - l2 I)
+    with l1 >= l2 the eigenvalues of C (the spectral projector of the 2x2 C in closed
+    form); equal eigenvalues give k1 = k2 and the matrix k2 I.  Clamping decisions use
+    real parts (complex-step inputs).  Returns (P, degenerate_mask); degenerate elements
+    (det C <= 1e-30) get P = F, as in polar_project."""
+    C = np.einsum("tki,tkj->tij", F, F)
+    det = C[:, 0, 0] * C[:, 1, 1] - C[:, 0, 1] * C[:, 1, 0]
+    bad = np.real(det) <= DEGENERATE_DET
+    h = 0.5 * (C[:, 0, 0] + C[:, 1, 1])
+    q = 0.5 * (C[:, 0, 0] - C[:, 1, 1])
+    disc = np.sqrt(q * q + C[:, 0, 1] * C[:, 1, 0])
+    l1 = h + disc
+    l2 = np.where(bad, 1.0, h - disc)
+    sig1, sig2 = np.sqrt(l1), np.sqrt(l2)
+
+    def k_of(sig):
+        r = np.real(sig)
+        return np.where(r > s_max, s_max / sig, np.where(r < s_min, s_min / sig, np.ones_like(sig)))
+
+    k1, k2 = k_of(sig1), k_of(sig2)
+    split = np.real(disc) > 0.0
+    coef = np.where(split, (k1 - k2) / np.where(split, 2.0 * disc, 1.0), 0.0)   # l1 - l2 = 2 disc exactly
+    eye = np.eye(2)[None]
+    M = k2[:, None, None] * eye + coef[:, None, None] * (C - l2[:, None, None] * eye)
+    P = np.einsum("tij,tjk->tik", F, M)
+    P[bad] = F[bad]
+    return P, bad
+
+
+def strain_project(F: np.ndarray, s_min: float = 1.0, s_max: float = 1.0) -> (np.ndarray, np.ndarray):
+    """Projection of each F onto the membrane-strain constraint set: the rotations
+    (polar_project) for the default limits [1, 1], else clamped_project."""
+    if s_min == 1.0 and s_max == 1.0:
+        return polar_project(F)
+    return clamped_project(F, s_min, s_max)
 
 
 def deformation_gradient(rs: RestState, x: np.ndarray) -> np.ndarray:
@@ -262,7 +315,8 @@ class EnergyParts:
 def internal_energy_and_gradient(rs: RestState, x: np.ndarray, w_scale=None):
     """Elastic energy sum_t E_t + sum_e E_e + E_A + E_V and its gradient [n,3].
 
-    E_t = w_t/2 |F - R(F)|^2,  grad_F = w_t (F - R)   (projection onto rotations)
+    E_t = w_t/2 |F - R(F)|^2,  grad_F = w_t (F - R)   (R: projection onto the strain
+          constraint set, the rotations unless the rest state carries strain limits)
     E_e = w_e/2 |K - p(K)|^2,  grad_xj = c_j w_e (K - p)
     E_A = w_A/2 (A - A0)^2 / A0,  E_V = w_V/2 (V - V0)^2 / V0
     `w_scale` optionally multiplies (w_strain, w_bend, w_area, w_vol).
@@ -273,7 +327,7 @@ def internal_energy_and_gradient(rs: RestState, x: np.ndarray, w_scale=None):
     t = rs.tris
     # --- membrane strain, per triangle
     F = deformation_gradient(rs, x)
-    R, bad = polar_project(F)
+    R, bad = strain_project(F, rs.s_min, rs.s_max)
     wt = rs.w_tri * ws[0]
     Dlt = F - R
     e_strain = 0.5 * np.sum(wt * np.einsum("tij,tij->t", Dlt, Dlt))
@@ -674,11 +728,13 @@ class CellType:
     """Rest state + factored global matrix of one cell type."""
 
     def __init__(self, verts, tris, material, dt, w_scale=None):
-        """material: (w_strain, w_bend, w_area, w_vol, density[, c_alpha, c_beta])."""
+        """material: (w_strain, w_bend, w_area, w_vol, density[, c_alpha, c_beta[, s_min, s_max]])."""
         self.material = tuple(material)
         w_strain, w_bend, w_area, w_vol, density = material[:5]
         c_alpha, c_beta = (tuple(material[5:7]) + (0.0, 0.0))[:2]
-        self.rest = rest_state(verts, tris, w_strain, w_bend, w_area, w_vol, density, dt, c_alpha, c_beta)
+        s_min, s_max = (tuple(material[7:9]) + (1.0, 1.0))[:2]
+        self.rest = rest_state(verts, tris, w_strain, w_bend, w_area, w_vol, density, dt, c_alpha, c_beta,
+                               s_min, s_max)
         self.solver = GlobalSolver(pd_matrix(self.rest, w_scale))
         self.w_scale = w_scale
 
