@@ -99,6 +99,15 @@ typedef struct {
    * (1/dt^2 + c_alpha/dt) M + (1 + c_beta/dt) L.  Both 0: no damping. */
   double c_alpha;  /* 1/us, >= 0 */
   double c_beta;   /* us, >= 0 */
+  /* Strain limits: the membrane-strain constraint set of a triangle is the set of
+   * deformation gradients whose singular values lie in [s_min, s_max] (ShapeOp-style
+   * strain limiting; the solver's origin, Implementation and architecture section), so
+   * R(F) = U clamp(Sigma, s_min, s_max) V^T for F = U Sigma V^T.  Both 0 (or both 1):
+   * the rotations, R = F (F^T F)^(-1/2).  Otherwise 0 < s_min <= 1 <= s_max, finite
+   * (the rest shape lies in the set); else INVALID_ARG.  The adjoints do not
+   * differentiate limited types (INVALID_ARG). */
+  double s_min;
+  double s_max;
 } npfem_material;
 
 typedef struct {
@@ -186,7 +195,8 @@ npfem_status npfem_step(npfem_batch* batch, void* x, void* v, const void* f_ext,
  * opts->tol must be 0 (the adjoint differentiates fixed iteration counts); opts->iters_done
  * is ignored.  With Rayleigh damping the dissipation term of every iterate's gradient
  * depends on x_n directly, and the matrix weight terms carry the (1 + c_beta/dt) factor.
- * Errors: INVALID_ARG (null pointer, FP32-form batch, tol != 0, collisions on), CUDA, OOM. */
+ * Errors: INVALID_ARG (null pointer, FP32-form batch, tol != 0, collisions on, a type with
+ * strain limits), CUDA, OOM. */
 npfem_status npfem_step_adjoint(npfem_batch* batch, const void* x, const void* v, const void* f_ext,
                                 const int32_t* iters, const npfem_solver_opts* opts,
                                 const double* gx_next, const double* gv_next, double* gx, double* gv,
@@ -213,7 +223,8 @@ npfem_status npfem_step_adjoint(npfem_batch* batch, const void* x, const void* v
  * gx gains C lam / dt.
  * Arrays as in npfem_step_adjoint.  The first call allocates two [3][N_total] FP64 copies
  * and the adjoint workspace.  Asynchronous on `stream`.  Errors: INVALID_ARG (null
- * pointer, FP32-form batch, bad cg_tol / cg_max_iters, collisions on), CUDA, OOM. */
+ * pointer, FP32-form batch, bad cg_tol / cg_max_iters, collisions on, a type with strain
+ * limits), CUDA, OOM. */
 npfem_status npfem_step_adjoint_implicit(npfem_batch* batch, const void* x, const void* v, const void* f_ext,
                                          const int32_t* iters, const npfem_solver_opts* opts,
                                          const double* gx_next, const double* gv_next, double* gx, double* gv,

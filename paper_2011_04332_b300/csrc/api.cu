@@ -171,6 +171,9 @@ static void fill_view(npfem_cell_type* t, DevTypeView<S>* v, const S* Dinv, cons
   v->dt = H.dt;
   v->damp_m = H.c_alpha / H.dt;
   v->damp_l = H.c_beta / H.dt;
+  v->s_min = H.s_min;
+  v->s_max = H.s_max;
+  v->limited = (H.s_min != 1.0 || H.s_max != 1.0) ? 1 : 0;
 }
 
 template <typename S>
@@ -345,7 +348,10 @@ static npfem_status launch_split(npfem_batch* b, const npfem_cell_type* t, const
     P.act_out = act0;
     P.act_count_out = act_count;
     int grid = std::max(1, std::min<int>(b->sms * L.it_bps, (G.gn + L.it_wpb - 1) / L.it_wpb));
-    npfem_k_begin<S><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, max_iters, x, v, f);
+    if (view.limited)
+      npfem_k_begin<S, true><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, max_iters, x, v, f);
+    else
+      npfem_k_begin<S, false><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, max_iters, x, v, f);
   } else if (kind == 1) {
     P.queue_counter = G.counter + 1 + 2 * it;
     P.act_in = (it & 1) ? act1 : act0;
@@ -375,7 +381,10 @@ static npfem_status launch_split(npfem_batch* b, const npfem_cell_type* t, const
     P.act_out = (it & 1) ? act0 : act1;
     P.act_count_out = act_count + it + 1;
     int grid = std::max(1, std::min<int>(b->sms * L.it_bps, (G.gn + L.it_wpb - 1) / L.it_wpb));
-    npfem_k_iter<S><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, x, v);
+    if (view.limited)
+      npfem_k_iter<S, true><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, x, v);
+    else
+      npfem_k_iter<S, false><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, x, v);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(NPFEM_ERR_CUDA, std::string("split step launch: ") + cudaGetErrorString(e));
@@ -627,10 +636,26 @@ npfem_status npfem_last_error_string(char* buf, size_t len) {
   return NPFEM_OK;
 }
 
+// Strain limits of a material: both 0 means the rotations [1, 1]; otherwise
+// 0 < s_min <= 1 <= s_max < inf.
+static bool strain_limits(const npfem_material* mat, double* lo, double* hi) {
+  if (mat->s_min == 0.0 && mat->s_max == 0.0) {
+    *lo = *hi = 1.0;
+    return true;
+  }
+  *lo = mat->s_min;
+  *hi = mat->s_max;
+  return *lo > 0.0 && *lo <= 1.0 && *hi >= 1.0 && std::isfinite(*hi);
+}
+
 npfem_status npfem_create_cell_type(const npfem_mesh* mesh, const npfem_material* mat, double dt,
                                     npfem_cell_type** out) {
   if (!mesh || !mat || !out) return fail(NPFEM_ERR_INVALID_ARG, "create_cell_type: null argument");
   *out = nullptr;
+  double s_lo, s_hi;
+  if (!strain_limits(mat, &s_lo, &s_hi))
+    return fail(NPFEM_ERR_INVALID_ARG, "create_cell_type: strain limits must be 0 < s_min <= 1 <= s_max (finite), "
+                                       "or both 0");
   auto* t = new (std::nothrow) npfem_cell_type();
   if (!t) return fail(NPFEM_ERR_OOM, "create_cell_type: host allocation failed");
   std::string err;
@@ -640,6 +665,8 @@ npfem_status npfem_create_cell_type(const npfem_mesh* mesh, const npfem_material
     delete t;
     return fail(rc, err);
   }
+  t->host.s_min = s_lo;
+  t->host.s_max = s_hi;
   cudaError_t e = cudaGetDevice(&t->device);
   const HostType& H = t->host;
   const int32_t *tris, *hinges, *inc_ptr, *inc_code, *perm, *fcol, *bcol;
@@ -724,6 +751,10 @@ npfem_status npfem_cell_type_info(const npfem_cell_type* t, npfem_type_info* inf
 npfem_status npfem_cell_type_analyze(const npfem_mesh* mesh, const npfem_material* mat, double dt,
                                      npfem_type_info* info) {
   if (!mesh || !mat || !info) return fail(NPFEM_ERR_INVALID_ARG, "cell_type_analyze: null argument");
+  double s_lo, s_hi;
+  if (!strain_limits(mat, &s_lo, &s_hi))
+    return fail(NPFEM_ERR_INVALID_ARG, "cell_type_analyze: strain limits must be 0 < s_min <= 1 <= s_max (finite), "
+                                       "or both 0");
   HostType H;
   std::string err;
   int rc = build_host_type(mesh->n_verts, mesh->n_tris, mesh->rest_xyz, mesh->tris, mat->w_strain, mat->w_bend,
@@ -940,6 +971,9 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: tol must be 0 (fixed iteration counts)");
   if (b->coll)
     return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: collisions are enabled (contacts are not differentiated)");
+  for (const npfem_cell_type* t : b->types)
+    if (t->host.s_min != 1.0 || t->host.s_max != 1.0)
+      return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: a cell type has strain limits (not differentiated)");
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   npfem_status arc = ensure_adjoint_workspace(b);
@@ -1000,6 +1034,9 @@ npfem_status npfem_step_adjoint_implicit(npfem_batch* b, const void* x, const vo
   if (b->coll)
     return fail(NPFEM_ERR_INVALID_ARG,
                 "step_adjoint_implicit: collisions are enabled (contacts are not differentiated)");
+  for (const npfem_cell_type* t : b->types)
+    if (t->host.s_min != 1.0 || t->host.s_max != 1.0)
+      return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint_implicit: a cell type has strain limits (not differentiated)");
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = sizeof(double) * 3 * (size_t)b->n_total;

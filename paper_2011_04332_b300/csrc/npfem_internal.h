@@ -33,6 +33,7 @@ struct HostType {
   std::vector<double> mass;      // [n]
   double A0 = 0, V0 = 0, w_area = 0, w_vol = 0, dt = 0, total_mass = 0;
   double c_alpha = 0, c_beta = 0;  // Rayleigh damping
+  double s_min = 1, s_max = 1;     // strain limits (singular values of F clamped to them)
   // gradient gather: per vertex, corner codes (t*3+slot >= 0) and hinge codes
   // (-(h*4+k)-1 < 0) with the hinge coefficient
   std::vector<int32_t> inc_ptr;  // [n+1]
@@ -115,6 +116,8 @@ struct DevTypeView {
   const double* cta_bwd_val[kCtaPacks];
   double A0, V0, w_area, w_vol, dt;
   double damp_m, damp_l;    // Rayleigh damping over dt: c_alpha/dt (mass part), c_beta/dt (elastic part)
+  double s_min, s_max;      // strain limits; limited = 0 for the rotations [1, 1]
+  int limited;
 };
 
 }  // namespace npfem

@@ -235,7 +235,7 @@ __device__ void split_finalize(const DevTypeView<S>& ty, const StepParams& P, co
   __syncwarp();
 }
 
-template <typename S>
+template <typename S, bool kLim>
 __global__ void __launch_bounds__(128, IterOccupancy<S>::min_blocks) npfem_k_begin(DevTypeView<S> ty, StepParams P, int max_iters, S* x,
                                                      S* v, const S* f) {
   const int lane = threadIdx.x & 31;
@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(128, IterOccupancy<S>::min_blocks) npfem_k_beg
     __syncwarp();
     NPFEM_PHASE_END(t_predict, kPhPredict, P, lane)
     NPFEM_PHASE_BEGIN(t_obj0)
-    EvalOut ev = eval_objective<S>(ty, P, w, w.U, w.G, cvol, cell, lane);
+    EvalOut ev = eval_objective<S, kLim ? 1 : 0>(ty, P, w, w.U, w.G, cvol, cell, lane);
     NPFEM_PHASE_END(t_obj0, kPhObjective, P, lane)
     const double g0n = sqrt(vdot64<S>(w.G, w.G, len, lane));
     if (lane == 0) {
@@ -487,7 +487,7 @@ __global__ void __launch_bounds__(32 * W) npfem_k_solve_cta(DevTypeView<S> ty, S
   }
 }
 
-template <typename S>
+template <typename S, bool kLim>
 __global__ void __launch_bounds__(128, IterOccupancy<S>::min_blocks) npfem_k_iter(DevTypeView<S> ty, StepParams P, S* x, S* v) {
   const int lane = threadIdx.x & 31;
   const int n = ty.n, len = 3 * n;
@@ -562,7 +562,7 @@ __global__ void __launch_bounds__(128, IterOccupancy<S>::min_blocks) npfem_k_ite
       for (int e = lane; e < len; e += 32) UT[e] = U[e] + sa * w.D[e];
       __syncwarp();
       NPFEM_PHASE_BEGIN(t_obj)
-      EvalOut et = eval_objective<S>(ty, P, w, UT, GT, cvol, cell, lane);
+      EvalOut et = eval_objective<S, kLim ? 1 : 0>(ty, P, w, UT, GT, cvol, cell, lane);
       NPFEM_PHASE_END(t_obj, kPhObjective, P, lane)
       ft = et.energy;
       degen = et.degenerate;  // the trial that ends the search is the accepted one

@@ -296,14 +296,57 @@ __device__ __noinline__ double damping_mass(const S* mass, int n, S dm, const S*
   return e;
 }
 
+// Strain limits: projection of F = [F0 F1] (3x2) onto the matrices whose singular values
+// lie in [s_min, s_max], R = F M with M = k2 I + (k1 - k2)/(l1 - l2) (C - l2 I), where
+// l1 >= l2 are the eigenvalues of C = F^T F and k_i = clamp(sqrt(l_i))/sqrt(l_i) (the
+// spectral projector of the 2x2 C in closed form; l1 - l2 = 2 disc exactly, equal
+// eigenvalues give k1 = k2 and M = k2 I).  M is evaluated in FP64 in both forms, per
+// triangle in a pass of its own that stores (m00, m01, m11) in the first three slots of
+// the triangle's corner record; the strain pass, run by the same lane over the same
+// triangles, reads them before it overwrites the record.  The pass runs at the top of the
+// objective, where few values are live, so that types without limits keep the register
+// allocation of the polar projection (a call inside the objective, or the FP64 projector
+// inside the strain loop, would raise the spills of the iteration kernel).
+template <typename S>
+__device__ __forceinline__ void strain_limit_pass(const DevTypeView<S>& ty, const S* X, const S* U, S* corner,
+                                               int lane) {
+  const double s_min = ty.s_min, s_max = ty.s_max;
+  for (int t = lane; t < ty.T; t += 32) {
+    int i0 = __ldg(&ty.tris[3 * t]), i1 = __ldg(&ty.tris[3 * t + 1]), i2 = __ldg(&ty.tris[3 * t + 2]);
+    V3<S> e1 = edge(X, U, i0, i1), e2 = edge(X, U, i0, i2);
+    const S d00 = __ldg(&ty.Dinv[3 * t]), d01 = __ldg(&ty.Dinv[3 * t + 1]), d11 = __ldg(&ty.Dinv[3 * t + 2]);
+    V3<S> F0 = d00 * e1;
+    V3<S> F1 = d01 * e1 + d11 * e2;
+    const double a0 = F0.x, a1 = F0.y, a2 = F0.z, b0 = F1.x, b1 = F1.y, b2 = F1.z;
+    const double c00 = a0 * a0 + a1 * a1 + a2 * a2;
+    const double c01 = a0 * b0 + a1 * b1 + a2 * b2;
+    const double c11 = b0 * b0 + b1 * b1 + b2 * b2;
+    const double h = 0.5 * (c00 + c11), q = 0.5 * (c00 - c11);
+    const double disc = sqrt(q * q + c01 * c01);
+    const double l1 = h + disc, l2 = h - disc;
+    const double s1 = sqrt(l1), s2 = sqrt(l2);
+    const double k1 = fmin(fmax(s1, s_min), s_max) / s1;
+    const double k2 = fmin(fmax(s2, s_min), s_max) / s2;
+    const double coef = disc > 0.0 ? (k1 - k2) / (2.0 * disc) : 0.0;
+    corner[9 * t] = (S)(k2 + coef * (c00 - l2));
+    corner[9 * t + 1] = (S)(coef * c01);
+    corner[9 * t + 2] = (S)(k2 + coef * (c11 - l2));
+  }
+}
+
 // f(X+U) and its gradient into Gout.  W = y - x_n.  The strain projection maps the
 // triangle deformation gradient F = [e1 e2] Dm^-1 to R = F (F^T F)^(-1/2) via the
 // closed-form 2x2 SPD square root (C + sqrt(det C) I)/sqrt(tr C + 2 sqrt(det C)).
-template <typename S>
+// kLim: 0 compiles the rotations only, 1 the strain-limited projection only, 2 chooses by
+// the type at run time (the split kernels are instantiated per case, so a batch without
+// limits runs code with no trace of them).
+template <typename S, int kLim = 2>
 __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const StepParams& P, const CellWs<S>& w, const S* U,
                                   S* Gout, V3<S> cvol, int cell, int lane) {
   const int n = ty.n, T = ty.T, E = ty.E;
   const S* X = w.X;
+  const bool limited = kLim == 1 || (kLim == 2 && ty.limited);
+  if (limited) strain_limit_pass<S>(ty, X, U, w.corner, lane);
   NPFEM_PHASE_BEGIN(t_area)
   // pass A: global area and volume (FP64 reductions)
   Acc<S> a_sum, v_sum;
@@ -339,13 +382,20 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const StepParams& P,
     S det = c00 * c11 - c01 * c01;
     V3<S> P0{0, 0, 0}, P1{0, 0, 0};
     if ((double)det > kDegenerateDet) {
-      S s = sqrt(det);
-      S tau = sqrt(c00 + c11 + (S)2 * s);
-      S s00 = (c00 + s) / tau, s01 = c01 / tau, s11 = (c11 + s) / tau;
-      S idet = (S)1 / (s00 * s11 - s01 * s01);
-      // R = F S^-1, S^-1 = [[s11, -s01], [-s01, s00]] / det S
-      V3<S> R0 = idet * (s11 * F0 - s01 * F1);
-      V3<S> R1 = idet * (s00 * F1 - s01 * F0);
+      V3<S> R0, R1;
+      if (limited) {
+        const S m00 = w.corner[9 * t], m01 = w.corner[9 * t + 1], m11 = w.corner[9 * t + 2];
+        R0 = m00 * F0 + m01 * F1;
+        R1 = m01 * F0 + m11 * F1;
+      } else {
+        S s = sqrt(det);
+        S tau = sqrt(c00 + c11 + (S)2 * s);
+        S s00 = (c00 + s) / tau, s01 = c01 / tau, s11 = (c11 + s) / tau;
+        S idet = (S)1 / (s00 * s11 - s01 * s01);
+        // R = F S^-1, S^-1 = [[s11, -s01], [-s01, s00]] / det S
+        R0 = idet * (s11 * F0 - s01 * F1);
+        R1 = idet * (s00 * F1 - s01 * F0);
+      }
       V3<S> D0 = F0 - R0, D1 = F1 - R1;
       e_el.add(half * wt * (dot(D0, D0) + dot(D1, D1)));
       P0 = wt * D0;

@@ -38,7 +38,8 @@ class _Mesh(C.Structure):
 
 class _Material(C.Structure):
     _fields_ = [("w_strain", C.c_double), ("w_bend", C.c_double), ("w_area", C.c_double),
-                ("w_vol", C.c_double), ("density", C.c_double), ("c_alpha", C.c_double), ("c_beta", C.c_double)]
+                ("w_vol", C.c_double), ("density", C.c_double), ("c_alpha", C.c_double), ("c_beta", C.c_double),
+                ("s_min", C.c_double), ("s_max", C.c_double)]
 
 
 class _Opts(C.Structure):
@@ -134,7 +135,7 @@ def analyze_cell_type(verts: np.ndarray, tris: np.ndarray, material: Sequence[fl
     m = _Mesh(xyz.shape[0], tr.shape[0], xyz.ctypes.data_as(C.POINTER(C.c_double)),
               tr.ctypes.data_as(C.POINTER(C.c_int32)))
     vals = [float(a) for a in material]
-    mat = _Material(*(vals + [0.0] * (7 - len(vals))))
+    mat = _Material(*(vals + [0.0] * (9 - len(vals))))
     inf = _TypeInfo()
     _check(lib.npfem_cell_type_analyze(C.byref(m), C.byref(mat), float(dt), C.byref(inf)))
     return {k: getattr(inf, k) for k, _ in _TypeInfo._fields_}
@@ -142,7 +143,8 @@ def analyze_cell_type(verts: np.ndarray, tris: np.ndarray, material: Sequence[fl
 
 class CellType:
     """A prefactored cell type: npfem_create_cell_type(mesh, material, dt); material is
-    (w_strain, w_bend, w_area, w_vol, density[, c_alpha, c_beta]) (damping 0 if absent)."""
+    (w_strain, w_bend, w_area, w_vol, density[, c_alpha, c_beta[, s_min, s_max]])
+    (damping 0 and no strain limits if absent)."""
 
     def __init__(self, verts: np.ndarray, tris: np.ndarray, material: Sequence[float], dt: float):
         lib = load_library()
@@ -152,7 +154,7 @@ class CellType:
                   self._xyz.ctypes.data_as(C.POINTER(C.c_double)),
                   self._tris.ctypes.data_as(C.POINTER(C.c_int32)))
         vals = [float(a) for a in material]
-        mat = _Material(*(vals + [0.0] * (7 - len(vals))))
+        mat = _Material(*(vals + [0.0] * (9 - len(vals))))
         h = C.c_void_p()
         _check(lib.npfem_create_cell_type(C.byref(m), C.byref(mat), float(dt), C.byref(h)))
         self.handle = h
