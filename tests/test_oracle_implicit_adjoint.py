@@ -1,7 +1,8 @@
 """Pin of the oracle's implicit-function adjoint: the gradient of L = gx . x* + gv . v*
 through the converged minimiser of a step equals central differences of a step run to
 convergence, for every input kind (positions, velocities, forces, material weights), with
-and without Rayleigh damping (whose dissipation term depends on x_n directly)."""
+and without Rayleigh damping (whose dissipation term depends on x_n directly), and with
+strain limits (whose projection is clamped on both sides of the deformation)."""
 import numpy as np
 import pytest
 
@@ -19,9 +20,14 @@ def _converged(mat, x, v, f, mesh):
     return ct, r
 
 
-@pytest.mark.parametrize("mesh_fn,damping", [(I.icosahedron, ()), (lambda: I.rbc_mesh(1), ()),
-                                             (lambda: I.rbc_mesh(1), (0.5, 1.0))])
-def test_implicit_adjoint_matches_central_differences(mesh_fn, damping):
+# wrel: relative step of the weight differences.  With strain limits the energy is flat
+# inside the limits, so the converged state's own rounding, divided by a 1e-6 step of the
+# small bending weight, is ~2e-5 of the derivative; a 1e-4 step (no singular value lies
+# within 4e-4 of a limit, so none crosses one) leaves truncation error ~1e-9.
+@pytest.mark.parametrize("mesh_fn,damping,wrel", [(I.icosahedron, (), 1e-6), (lambda: I.rbc_mesh(1), (), 1e-6),
+                                                  (lambda: I.rbc_mesh(1), (0.5, 1.0), 1e-6),
+                                                  (lambda: I.rbc_mesh(1), (0.0, 0.0, 0.97, 1.03), 1e-4)])
+def test_implicit_adjoint_matches_central_differences(mesh_fn, damping, wrel):
     MAT = MAT0 + damping
     m = mesh_fn()
     rng = np.random.default_rng(41)
@@ -49,7 +55,7 @@ def test_implicit_adjoint_matches_central_differences(mesh_fn, damping):
             assert grad[i, d] == pytest.approx(fd, rel=1e-5, abs=1e-7), (name, i, d)
     for q in range(4):
         mp, mm = list(MAT), list(MAT)
-        hq = 1e-6 * MAT[q]
+        hq = wrel * MAT[q]
         mp[q] += hq
         mm[q] -= hq
         fd = (loss(mat=tuple(mp)) - loss(mat=tuple(mm))) / (2 * hq)
