@@ -94,6 +94,20 @@ def test_invalid_arguments_are_rejected(lib):
     _expect(-1, lambda: native.analyze_cell_type(m.verts, m.tris, (1, .05, 10, 10, 0.0), 0.1))
 
 
+def test_strain_limits_are_checked_on_the_host(lib):
+    """Both 0 (or both 1) select the rotations; otherwise 0 < s_min <= 1 <= s_max, finite
+    (the rest shape must lie in the constraint set)."""
+    m = I.icosahedron()
+    base = I.RBC_MATERIAL.as_tuple() + (0.0, 0.0)
+    for ok in ((0.0, 0.0), (1.0, 1.0), (0.9, 1.1), (1.0, 1.5), (0.5, 1.0)):
+        native.analyze_cell_type(m.verts, m.tris, base + ok, 0.1)
+    for bad in ((1.1, 1.2), (0.8, 0.9), (0.0, 1.1), (-0.1, 1.1), (0.9, float("inf")), (float("nan"), 1.1),
+                (1.2, 1.1)):
+        with pytest.raises(native.NpfemError, match="strain limits") as ei:
+            native.analyze_cell_type(m.verts, m.tris, base + bad, 0.1)
+        assert ei.value.code == -1, bad
+
+
 def test_non_spd_material_is_rejected(lib):
     m = I.rbc_mesh(2)
     _expect(-3, lambda: native.analyze_cell_type(m.verts, m.tris, (-50.0, 0.05, 10, 10, 1.1), 10.0))
