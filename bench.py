@@ -35,11 +35,15 @@ UNIT = "RBC-equivalent cell-steps/s"
 
 # Rayleigh damping (c_alpha 1/us, c_beta us) given to every cell type (--damping)
 DAMPING = (0.0, 0.0)
+# strain limits (s_min, s_max) given to every cell type (--strain-limits); (0, 0): none
+STRAIN_LIMITS = (0.0, 0.0)
 
 
 def _mat(spec):
-    """Material tuple of a cell-type spec, with the benchmark's damping appended."""
-    return spec.material.as_tuple() + DAMPING
+    """Material tuple of a cell-type spec, with the benchmark's damping and strain limits
+    appended (the limits only when set)."""
+    m = spec.material.as_tuple() + DAMPING
+    return m + STRAIN_LIMITS if any(STRAIN_LIMITS) else m
 
 
 # ------------------------------------------------------------------ workloads
@@ -485,6 +489,8 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": desc, "cells": b.ncells, "rbc_equivalents_per_step": rbc_eq_per_rank,
                    "precision": args.precision, "l2": "flushed between steps (256 MB write, untimed)",
                    "damping": ({"c_alpha_per_us": DAMPING[0], "c_beta_us": DAMPING[1]} if any(DAMPING) else None),
+                   "strain_limits": ({"s_min": STRAIN_LIMITS[0], "s_max": STRAIN_LIMITS[1]}
+                                     if any(STRAIN_LIMITS) else None),
                    "launch": "one CUDA graph per step" if graph is not None else "direct npfem_step call",
                    "mode": "split kernels (k_begin, then k_solve + k_iter per iteration and cell type)",
                    "split_shapes": {str(t): list(batch.get_split_launch(t)[0]) for t in sorted(set(int(q) for q in b.type_of_cell))},
@@ -664,7 +670,10 @@ def run_reference(args, rank, world):
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": desc, "precision": "fp64 (CPU oracle)"},
+            "config": {"workload": desc, "precision": "fp64 (CPU oracle)",
+                       "damping": ({"c_alpha_per_us": DAMPING[0], "c_beta_us": DAMPING[1]} if any(DAMPING) else None),
+                       "strain_limits": ({"s_min": STRAIN_LIMITS[0], "s_max": STRAIN_LIMITS[1]}
+                                         if any(STRAIN_LIMITS) else None)},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sdesc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
@@ -692,11 +701,14 @@ def main():
     ap.add_argument("--budget", type=int, default=16, help="with --tol: iteration budget per cell")
     ap.add_argument("--damping", default="0,0",
                     help="Rayleigh damping c_alpha,c_beta (1/us, us) for every cell type")
+    ap.add_argument("--strain-limits", default="0,0",
+                    help="strain limits s_min,s_max for every cell type (0,0: the rotations)")
     ap.add_argument("--groups", type=int, default=0,
                     help="with --no-tune: phase-offset chains per cell type (0: library default)")
     args = ap.parse_args()
-    global DAMPING
+    global DAMPING, STRAIN_LIMITS
     DAMPING = tuple(float(q) for q in args.damping.split(","))
+    STRAIN_LIMITS = tuple(float(q) for q in args.strain_limits.split(","))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
