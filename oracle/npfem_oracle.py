@@ -245,7 +245,10 @@ def clamped_project(F: np.ndarray, s_min: float, s_max: float) -> (np.ndarray, n
     q = 0.5 * (C[:, 0, 0] - C[:, 1, 1])
     disc = np.sqrt(q * q + C[:, 0, 1] * C[:, 1, 0])
     l1 = h + disc
-    l2 = np.where(bad, 1.0, h - disc)
+    # the smaller eigenvalue as det C / l1 with det C = |F0 x F1|^2 (Lagrange identity):
+    # h - disc and C00 C11 - C01^2 both cancel for thin triangles
+    fx = np.cross(F[:, :, 0], F[:, :, 1])
+    l2 = np.where(bad, 1.0, np.sum(fx * fx, axis=1) / np.where(bad, 1.0, l1))
     sig1, sig2 = np.sqrt(l1), np.sqrt(l2)
 
     def k_of(sig):

@@ -323,10 +323,14 @@ __device__ __forceinline__ void strain_limit_pass(const DevTypeView<S>& ty, cons
     const double c11 = b0 * b0 + b1 * b1 + b2 * b2;
     const double h = 0.5 * (c00 + c11), q = 0.5 * (c00 - c11);
     const double disc = sqrt(q * q + c01 * c01);
-    const double l1 = h + disc, l2 = h - disc;
-    const double s1 = sqrt(l1), s2 = sqrt(l2);
-    const double k1 = fmin(fmax(s1, s_min), s_max) / s1;
-    const double k2 = fmin(fmax(s2, s_min), s_max) / s2;
+    // smaller eigenvalue as det C / l1, det C = |F0 x F1|^2 (Lagrange identity): h - disc
+    // and c00 c11 - c01^2 both cancel for thin triangles; l2 = 0 (collinear F) gives M = I
+    const double x0 = a1 * b2 - a2 * b1, x1 = a2 * b0 - a0 * b2, x2 = a0 * b1 - a1 * b0;
+    const double l1 = h + disc, l2 = (x0 * x0 + x1 * x1 + x2 * x2) / l1;
+    const bool ok = l2 > 0.0;
+    const double s1 = sqrt(l1), s2 = ok ? sqrt(l2) : 1.0;
+    const double k1 = ok ? fmin(fmax(s1, s_min), s_max) / s1 : 1.0;
+    const double k2 = ok ? fmin(fmax(s2, s_min), s_max) / s2 : 1.0;
     const double coef = disc > 0.0 ? (k1 - k2) / (2.0 * disc) : 0.0;
     corner[9 * t] = (S)(k2 + coef * (c00 - l2));
     corner[9 * t + 1] = (S)(coef * c01);

@@ -126,3 +126,21 @@ def test_complex_step_derivative_of_step_matches_central_differences():
     cs = np.imag(O.step(ct.rest, ct.solver, x + 1j * h * d, v.astype(complex), f.astype(complex), 4).x) / h
     fd = (O.step(ct.rest, ct.solver, x + e * d, v, f, 4).x - O.step(ct.rest, ct.solver, x - e * d, v, f, 4).x) / (2 * e)
     assert np.max(np.abs(cs - fd)) <= 1e-5 * np.max(np.abs(cs))
+
+
+def test_thin_triangles_project_accurately():
+    """Nearly collapsed triangles (singular values (1.3, s2), s2 down to 1e-7, not flagged
+    degenerate): the projection stays finite and agrees with the SVD to the closed
+    form's own conditioning, about eps * s_min / s2 (the smaller eigenvalue det C / l1
+    with det C = |F0 x F1|^2 has no cancellation; h - disc lost every digit of it here)."""
+    rng = np.random.default_rng(71)
+    lo, hi = 0.9, 1.1
+    for s2 in (1e-3, 1e-4, 1e-5, 1e-6, 1e-7):
+        Q, _ = np.linalg.qr(rng.standard_normal((3, 2)))
+        th = rng.uniform(0, 2 * np.pi)
+        V = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+        F = (Q @ np.diag([1.3, s2]) @ V.T)[None]
+        P, bad = O.clamped_project(F, lo, hi)
+        assert not bad.any() and np.all(np.isfinite(P))
+        bound = 16 * np.finfo(float).eps * lo / s2 + 1e-14
+        assert np.max(np.abs(P - _svd_project(F, lo, hi))) <= bound, s2
