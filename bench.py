@@ -4,11 +4,13 @@
 A step is one npfem_step over the whole batch: every cell runs the full quasi-Newton
 solve (prediction, local projections, global FP64 solves, L-BFGS, line search,
 write-back).  Metric: RBC-equivalent cell-steps per second, one RBC-equivalent being
-(n_vertices/642)*(iterations/5).  Default workload: 4096 placed 642-vertex RBCs,
-5 iterations, FP32 form (FP32 local work, FP64 factor/solves/reductions).
+(n_vertices/642)*(iterations/5).  Default workload: the heterogeneous 10^4-cell batch
+(4500 642-vertex RBCs, 4500 2562-vertex RBCs, 1000 162-vertex platelets, 3..8 iterations
+per cell), FP32 form (FP32 local work, FP64 factor/solves/reductions), followed by a
+short pass of the same batch in the plain FP64 form for the FP32-form speed-up.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload homog4096|hetero10k]
-                  [--precision fp32form|fp64] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload hetero10k|homog4096|...]
+                  [--precision fp32form|fp64] [--impl ours|reference] [--tune]
 
 `--impl reference` times the CPU FP64 oracle (the only other implementation of the
 method) on a bounded sample of the same workload.  Under torchrun every rank steps its
@@ -182,6 +184,59 @@ def oracle_baseline(b, sample_cells: int, workers: int, tol: float = 0.0, collis
     return rbc_eq / busy, workers, desc
 
 
+# ------------------------------------------------------------------ parity sample
+def sample_cells(b, per_type: int = 3):
+    """The cells the parity check compares with the oracle: for every cell type the
+    first, middle and last cell of that type in batch order (all, if it has fewer)."""
+    out = []
+    for t in sorted({int(q) for q in b.type_of_cell}):
+        idx = np.flatnonzero(b.type_of_cell == t)
+        pos = np.unique(np.linspace(0, len(idx) - 1, per_type).round().astype(int))
+        out += [int(idx[i]) for i in pos]
+    return sorted(out)
+
+
+def oracle_parity(b, x0, v0, f, xs, cells, bar, tol, coll, done_gpu, ocache):
+    """Per-cell relative position error (max |x - x_oracle| over the cell radius) of the
+    GPU step xs taken from (x0, v0, f) against the oracle's step of the same inputs, for
+    the sampled cells; reported per cell type.  FP32-form runs give the oracle the
+    FP32-rounded inputs (x0, v0, f as stored)."""
+    from oracle import npfem_oracle as O
+    xin, vin, fin = (t.double().cpu().numpy() for t in (x0, v0, f))
+    scon = None
+    if coll is not None:
+        allt = [O.CellType(t.mesh.verts, t.mesh.tris, _mat(t), b.dt) for t in b.types]
+        scon = O.detect_contacts(allt, b.type_of_cell, b.offsets, xin, coll[0],
+                                 vertices=[i for c in cells for i in range(int(b.offsets[c]), int(b.offsets[c + 1]))])
+    bx = _box(b, coll)
+    wl = None if bx is None else (bx[0], bx[1], coll[1], coll[2])
+    xg = xs.double().cpu().numpy()
+    per_type, counts = {}, []
+    for c in cells:
+        t = int(b.type_of_cell[c])
+        if t not in ocache:
+            ty = b.types[t]
+            ocache[t] = O.CellType(ty.mesh.verts, ty.mesh.tris, _mat(ty), b.dt)
+        s = b.cell_slice(c)
+        con = None if scon is None else (*O.cell_contacts(scon, s.start, s.stop), coll[1], coll[2])
+        r = O.step(ocache[t].rest, ocache[t].solver, xin[:, s].T, vin[:, s].T, fin[:, s].T, int(b.iters[c]), tol=tol,
+                   contact=con, walls=wl)
+        rad = np.max(np.linalg.norm(r.x - r.x.mean(axis=0), axis=1))
+        e = float(np.max(np.abs(xg[:, s].T - r.x)) / rad)
+        key = f"{t}:{b.types[t].mesh.n}v"
+        per_type[key] = max(per_type.get(key, 0.0), e)
+        if done_gpu is not None:
+            counts.append((int(done_gpu[c]), len(r.alphas)))
+    worst = max(per_type.values())
+    out = {"cells": cells, "per_type_max_rel_position_error": per_type, "max_rel_position_error": worst,
+           "bar": bar, "pass": bool(worst <= bar),
+           "definition": "max over the cell's vertices of |x - x_oracle|_inf / cell radius, one step from the "
+                         "same inputs; per cell type the max over its sampled cells (first, middle, last)"}
+    if done_gpu is not None:
+        out["iterations_gpu_oracle"] = counts
+    return out
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -295,48 +350,22 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 126 MB L2
     stream = torch.cuda.current_stream(dev)
 
-    # sampled parity against the oracle on the first step (rank 0)
+    # sampled parity against the oracle on the first step (rank 0): every cell type
+    sample = sample_cells(b)
     err = None
+    ocache = {}
     if rank == 0 and not args.no_check:
-        from oracle import npfem_oracle as O
         xs, vs_ = x0.clone(), v0.clone()
         batch.step(xs, vs_, f, iters=iters, residual=res, status=st, tol=tol, iters_done=done)
         torch.cuda.synchronize()
-        done_gpu = done.cpu().numpy() if done is not None else b.iters
-        sample = [0, b.ncells // 3, (2 * b.ncells) // 3, b.ncells - 1]
-        ot = {}
-        xin, vin, fin = (t.double().cpu().numpy() for t in (x0, v0, f))
-        scon = None
-        if coll is not None:
-            allt = [O.CellType(t.mesh.verts, t.mesh.tris, _mat(t), b.dt) for t in b.types]
-            scon = O.detect_contacts(allt, b.type_of_cell, b.offsets, xin, coll[0],
-                                     vertices=[i for c in sample for i in range(int(b.offsets[c]), int(b.offsets[c + 1]))])
-        xg = xs.double().cpu().numpy()
-        errs, counts = [], []
-        for c in sample:
-            t = int(b.type_of_cell[c])
-            if t not in ot:
-                ty = b.types[t]
-                ot[t] = O.CellType(ty.mesh.verts, ty.mesh.tris, _mat(ty), b.dt)
-            s = b.cell_slice(c)
-            con = None if scon is None else (*O.cell_contacts(scon, s.start, s.stop), coll[1], coll[2])
-            bx = _box(b, coll)
-            wl = None if bx is None else (bx[0], bx[1], coll[1], coll[2])
-            r = O.step(ot[t].rest, ot[t].solver, xin[:, s].T, vin[:, s].T, fin[:, s].T, int(b.iters[c]), tol=tol,
-                       contact=con, walls=wl)
-            rad = np.max(np.linalg.norm(r.x - r.x.mean(axis=0), axis=1))
-            errs.append(float(np.max(np.abs(xg[:, s].T - r.x)) / rad))
-            counts.append((int(done_gpu[c]), len(r.alphas)))
-        err = {"cells": sample, "max_rel_position_error": max(errs),
-               "bar": 1e-5 if prec == native.FP32FORM else 1e-10}
-        if tol > 0:
-            err["iterations_gpu_oracle"] = counts
+        err = oracle_parity(b, x0, v0, f, xs, sample, 1e-5 if prec == native.FP32FORM else 1e-10, tol, coll,
+                            done.cpu().numpy() if done is not None else None, ocache)
 
     tuned = None
-    if args.no_tune and args.groups > 0:
+    if not args.tune and args.groups > 0:
         for t in sorted({int(q) for q in b.type_of_cell}):
             batch.set_groups(t, args.groups)
-    if not args.no_tune:
+    if args.tune:
         # launch-shape autotuning on copies of the state (outside the timed region)
         from paper_2011_04332_b300 import tuning
         t0 = time.perf_counter()
@@ -376,18 +405,24 @@ def run_ours(args, rank, world, local_rank):
     ktime = {t: {k: [0.0, 0] for k in native.Batch.KERNELS} for t in present}
     kspan = {k: 0.0 for k in native.Batch.KERNELS}      # union of concurrent launches, all types
     detect_ms = 0.0                                      # contact detection (collisions on)
+    t_wall = 0.0                                         # host time of the timed replays only
     with ClockSampler(local_rank) as clk:
-        t_wall0 = time.perf_counter()
         for k in range(args.steps):
             flush.zero_()
-            ev[k][0].record(stream)
             if fpool is not None and k % 10 == 0:
                 f.copy_(fpool[(k // 10) % len(fpool)])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ev[k][0].record(stream)
             one_step()
             ev[k][1].record(stream)
+            ev[k][1].synchronize()
+            t_wall += time.perf_counter() - t0
+            # outside the timed interval: iterations each cell ran, and the per-kernel
+            # durations of this step (events on the kernels' own streams, re-recorded by
+            # every replay, so they are read before the next one)
             if done_sum is not None:
-                done_sum += done     # iterations each cell ran (after the end event: untimed)
-            # per-kernel durations of this step (events on the kernels' own streams)
+                done_sum += done
             for t in present:
                 for name, (kms, kn) in batch.kernel_times(t).items():
                     ktime[t][name][0] += kms
@@ -397,7 +432,6 @@ def run_ours(args, rank, world, local_rank):
             if coll is not None:
                 detect_ms += batch.contact_time()
         torch.cuda.synchronize()
-        t_wall = time.perf_counter() - t_wall0
     if world > 1:
         torch.distributed.barrier()
     ms = [a.elapsed_time(bq) for a, bq in ev]
@@ -447,6 +481,18 @@ def run_ours(args, rank, world, local_rank):
                 "kernel_share_of_step": solve_span / ms_per_step if ms_per_step else None,
                 "step_frac": flops_per_step / (ms_per_step / 1e3) / 1e12 / fp64_peak if fp64_peak else None}
 
+    # HBM: the method's algorithmic I/O (read x, v, f and write x, v: 15 scalars per vertex
+    # and step) over the step time, against the measured copy bandwidth
+    ssz_ = 4 if prec == native.FP32FORM else 8
+    io_bytes = 15.0 * ssz_ * b.n_total
+    hbm_peak, hbm_src = measured_hbm_peak()
+    hbm = {"algorithmic_bytes_per_step": io_bytes, "achieved_gbs": io_bytes / (ms_per_step / 1e3) / 1e9,
+           "peak_gbs": hbm_peak, "peak_source": hbm_src,
+           "frac": io_bytes / (ms_per_step / 1e3) / 1e9 / hbm_peak if hbm_peak else None,
+           "note": "the step's algorithmic HBM traffic; per-type constants stay L2-resident, and the per-cell "
+                   "workspace traffic of the iteration kernels is not algorithmic (see the kernels' DRAM bytes in "
+                   "the ncu summaries)"}
+
     # end-to-end through the C ABI with host (pinned) buffers
     e2e = None
     if rank == 0 and not args.no_e2e:
@@ -468,6 +514,8 @@ def run_ours(args, rank, world, local_rank):
                             tol=tol, iters_done=nd)
         times = []
         for _ in range(args.steps):
+            flush.zero_()                       # L2 flushed between steps, as in the device-timed leg
+            torch.cuda.synchronize()
             t0 = time.perf_counter()
             batch.step_host(nx, nv_, nf, iters=ni, residual=nr, status=ns, stream=stream.cuda_stream,
                             tol=tol, iters_done=nd)
@@ -476,7 +524,16 @@ def run_ours(args, rank, world, local_rank):
         d2h = 2 * 3 * b.n_total * ssz + 12 * b.ncells + (4 * b.ncells if nd is not None else 0)
         e2e = {"value": rbc_eq_per_rank / statistics.mean(times), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "api": "npfem_step_host (pinned host buffers, copies + step + copies, synchronous)"}
+               "api": "npfem_step_host (pinned host buffers, copies + step + copies, synchronous)",
+               "l2": "flushed before each step (untimed)"}
+
+    # the same batch in the plain FP64 form: its throughput and its parity at the FP64 bar,
+    # for the FP32-form speed-up at stated accuracy
+    fp64 = None
+    if rank == 0 and prec == native.FP32FORM and not args.no_fp64:
+        fp64 = fp64_pass(args, b, types, iters, tol, coll, sample, ocache, dev, flush, rbc_eq_per_rank)
+        if fp64.get("value"):
+            fp64["speedup_fp32form_over_fp64"] = value / fp64["value"]
 
     adjoint = None
     if rank == 0 and not args.no_adjoint:
@@ -512,9 +569,11 @@ def run_ours(args, rank, world, local_rank):
         "status_nonzero_cells": int(np.count_nonzero(status)),
         "parity_sample": err,
         "roofline": roofline,
+        "hbm": hbm,
         "fp32_peak_tflops": fp32_peak,
         "cpu_baseline": cpu,
         "e2e": e2e,
+        "fp64_form": fp64,
         "adjoint": adjoint,
         "kernels": kernels,
         "gpu_launches": args.steps * (sum(min(batch.get_groups(t), int(np.sum(b.type_of_cell == t)))
@@ -524,6 +583,60 @@ def run_ours(args, rank, world, local_rank):
         "wall_s_timed_region": t_wall,
     }
     return out
+
+
+def fp64_pass(args, b, types, iters, tol, coll, sample, ocache, dev, flush, units):
+    """The workload's batch in the plain FP64 form (FP64 everywhere): parity of its first
+    step against the oracle on the sampled cells at the FP64 bar, then `args.fp64_steps`
+    CUDA-graph replays timed with events (L2 flushed between them, library default
+    shapes)."""
+    import torch
+    from paper_2011_04332_b300 import native
+    batch = native.Batch(types, b.type_of_cell, native.FP64)
+    if coll is not None:
+        batch.set_collisions(coll[0], coll[1], coll[2], box=_box(b, coll))
+    x0 = torch.tensor(b.x, dtype=torch.float64, device=dev)
+    v0 = torch.tensor(b.v, dtype=torch.float64, device=dev)
+    f = torch.tensor(b.f, dtype=torch.float64, device=dev)
+    it = iters.clone()
+    res = torch.zeros(b.ncells, dtype=torch.float64, device=dev)
+    st = torch.zeros(b.ncells, dtype=torch.int32, device=dev)
+    done = torch.zeros(b.ncells, dtype=torch.int32, device=dev) if tol > 0 else None
+    x, v = x0.clone(), v0.clone()
+    batch.step(x, v, f, iters=it, residual=res, status=st, tol=tol, iters_done=done)
+    torch.cuda.synchronize()
+    err = None
+    if not args.no_check:
+        err = oracle_parity(b, x0, v0, f, x, sample, 1e-10, tol, coll,
+                            done.cpu().numpy() if done is not None else None, ocache)
+    stream = torch.cuda.current_stream(dev)
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side):
+            batch.step(x, v, f, iters=it, residual=res, status=st, tol=tol, iters_done=done)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    for _ in range(2):
+        graph.replay()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.fp64_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    mean = statistics.mean(ms)
+    del graph
+    return {"value": units / (mean / 1e3), "unit": UNIT, "ms_per_step": mean, "steps": args.fp64_steps,
+            "warmup": 2, "parity_sample": err,
+            "residual": {"median": float(res.median()), "max": float(res.max())},
+            "how": "same batch and inputs in the plain FP64 form (FP64 local work, two-loop and solves), "
+                   "one CUDA graph per step, L2 flushed between steps, library default launch shapes"}
 
 
 def measure_adjoint(dev, nsteps: int = 40, ckpt_every: int = 20, ncells: int = 256):
@@ -638,6 +751,15 @@ def measured_traffic(workload: str, precision: str):
     return ent["dram_bytes_per_cell_solve"], ent["how"]
 
 
+def measured_hbm_peak():
+    """Copy bandwidth measured on the B300s (MEASURED_PEAKS.json), else the
+    profiling recipe's fallback figure."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"]), "measured (copy)"
+    except (OSError, ValueError, KeyError):
+        return 6400.0, "fallback"
+
+
 def probe_peaks():
     import ctypes
     from paper_2011_04332_b300 import build as B
@@ -683,7 +805,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="homog4096", choices=["homog4096", "hetero10k", "stress20k", "homog1776", "homog2562",
+    ap.add_argument("--workload", default="hetero10k", choices=["homog4096", "hetero10k", "stress20k", "homog1776", "homog2562",
                                                             "pack4096", "packbox4096", "small"])
     ap.add_argument("--precision", default="fp32form", choices=["fp32form", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -694,8 +816,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain-FP64 pass of an FP32-form run")
+    ap.add_argument("--fp64-steps", type=int, default=5, help="timed steps of the plain-FP64 pass")
     ap.add_argument("--no-graph", action="store_true")
-    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--tune", action="store_true",
+                    help="autotune the split launch shapes and groups first (default: the library's per-size-class "
+                         "defaults, which measured as fast as the tuner's choice on the 10^4-cell batch)")
+    ap.add_argument("--no-tune", action="store_true", help="(the default; kept for older command lines)")
     ap.add_argument("--tol", type=float, default=0.0,
                     help="converged-residual mode: per-cell stop at |g|/|g0| < tol (0: fixed iteration counts)")
     ap.add_argument("--budget", type=int, default=16, help="with --tol: iteration budget per cell")
@@ -704,7 +831,7 @@ def main():
     ap.add_argument("--strain-limits", default="0,0",
                     help="strain limits s_min,s_max for every cell type (0,0: the rotations)")
     ap.add_argument("--groups", type=int, default=0,
-                    help="with --no-tune: phase-offset chains per cell type (0: library default)")
+                    help="without --tune: phase-offset chains per cell type (0: library default)")
     args = ap.parse_args()
     global DAMPING, STRAIN_LIMITS
     DAMPING = tuple(float(q) for q in args.damping.split(","))
