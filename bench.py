@@ -87,6 +87,9 @@ def make_workload(name: str, rank: int = 0):
                 f"cube at 35 % volume fraction (overlapping), 5 iterations, collisions radius {r} um, "
                 f"delta {d} um, weight {w} nN/um, contact detection inside every step"
                 + ("; box walls 1 um outside the initial cells" if walls else ""))
+    elif name == "plt1776":
+        b = I.placed_cells([I.CellTypeSpec(I.platelet_mesh(2), I.PLT_MATERIAL)], [0] * 1776, 1007 + 100 * rank, 5)
+        desc = "homogeneous 1776 platelets (162 vertices, oblate ellipsoid), 5 iterations"
     elif name == "small":
         b = I.homogeneous_rbc_batch(ncells=64, seed=1001 + 100 * rank)
         desc = "64 RBC (642 vertices), 5 iterations"
@@ -639,7 +642,7 @@ def fp64_pass(args, b, types, iters, tol, coll, sample, ocache, dev, flush, unit
                    "one CUDA graph per step, L2 flushed between steps, library default launch shapes"}
 
 
-def measure_adjoint(dev, nsteps: int = 40, ckpt_every: int = 20, ncells: int = 256):
+def measure_adjoint(dev, nsteps: int = 200, ckpt_every: int = 20, ncells: int = 256):
     """Adjoint throughput on the calibration workload: ncells placed 642-vertex RBCs,
     FP64, loss = squared distance of axial/transverse diameters to seeded targets after
     an nsteps rollout with checkpoints every ckpt_every steps (forward + backward)."""
@@ -670,7 +673,8 @@ def measure_adjoint(dev, nsteps: int = 40, ckpt_every: int = 20, ncells: int = 2
             "adjoint_cell_steps_per_s": ncells * nsteps / (t_bwd / 1e3),
             "ms_per_adjoint_step": t_bwd / nsteps,
             "ms_per_forward_step": t_fwd / nsteps,
-            "backward_includes": "segment recomputation (one extra forward step per step) + adjoint steps",
+            "backward_includes": "npfem_rollout_adjoint: a checkpointed forward rollout, segment recomputation "
+                                 "and the step adjoints (the library recomputes the forward from (x0, v0))",
             "loss": float(loss.detach()), "grad_w": [float(g) for g in w.grad[0].tolist()],
             "implicit": measure_adjoint_implicit(dev, b)}
 
@@ -805,7 +809,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="hetero10k", choices=["homog4096", "hetero10k", "stress20k", "homog1776", "homog2562",
+    ap.add_argument("--workload", default="hetero10k", choices=["homog4096", "hetero10k", "stress20k", "homog1776", "homog2562", "plt1776",
                                                             "pack4096", "packbox4096", "small"])
     ap.add_argument("--precision", default="fp32form", choices=["fp32form", "fp64"])
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

@@ -104,8 +104,9 @@ typedef struct {
    * strain limiting; the solver's origin, Implementation and architecture section), so
    * R(F) = U clamp(Sigma, s_min, s_max) V^T for F = U Sigma V^T.  Both 0 (or both 1):
    * the rotations, R = F (F^T F)^(-1/2).  Otherwise 0 < s_min <= 1 <= s_max, finite
-   * (the rest shape lies in the set); else INVALID_ARG.  The adjoints do not
-   * differentiate limited types (INVALID_ARG). */
+   * (the rest shape lies in the set); else INVALID_ARG.  The adjoints differentiate
+   * the clamped projection (by regime: both singular values inside the limits, both
+   * clamped to one limit, or one on each side). */
   double s_min;
   double s_max;
 } npfem_material;
@@ -195,12 +196,38 @@ npfem_status npfem_step(npfem_batch* batch, void* x, void* v, const void* f_ext,
  * opts->tol must be 0 (the adjoint differentiates fixed iteration counts); opts->iters_done
  * is ignored.  With Rayleigh damping the dissipation term of every iterate's gradient
  * depends on x_n directly, and the matrix weight terms carry the (1 + c_beta/dt) factor.
- * Errors: INVALID_ARG (null pointer, FP32-form batch, tol != 0, collisions on, a type with
- * strain limits), CUDA, OOM. */
+ * Errors: INVALID_ARG (null pointer, FP32-form batch, tol != 0, collisions on), CUDA, OOM. */
 npfem_status npfem_step_adjoint(npfem_batch* batch, const void* x, const void* v, const void* f_ext,
                                 const int32_t* iters, const npfem_solver_opts* opts,
                                 const double* gx_next, const double* gv_next, double* gx, double* gv,
                                 double* gf, double* gw, int32_t* status_out, void* stream);
+
+/* Reverse mode of a whole rollout of `nsteps` steps with constant external forces (FP64
+ * batches): the membrane-calibration use of the adjoint (Setting up new materials
+ * section: a material's per-element weights; the derivative is that of the unrolled
+ * quasi-Newton iteration of npfem_step, Implementation and architecture section).
+ * Starting from (x0, v0), the library runs the forward rollout, keeping (x, v) before
+ * every ckpt_every-th step, then sweeps the segments backwards: each segment's states
+ * are recomputed from its checkpoint and the step adjoints (npfem_step_adjoint) run in
+ * reverse.  Memory grows with nsteps/ckpt_every + ckpt_every states, not nsteps.
+ *   x0, v0, f_ext   in  [3][N_total] double: initial state and the forces of every step.
+ *   iters, opts     as in npfem_step_adjoint (fixed counts, at most 16, tol 0).
+ *   nsteps >= 1, ckpt_every >= 1.
+ *   gx_end          in  [3][N_total] dL/dx_N;  gv_end in [3][N_total] dL/dv_N or NULL (zero).
+ *   gx0, gv0, gf    out [3][N_total] dL/dx0, dL/dv0, dL/df_ext (the sum over all steps).
+ *   gweights        out [ntypes][4] dL/d(w_strain, w_bend, w_area, w_vol) of each cell type
+ *                   (summed over its cells and all steps in a fixed order: reproducible).
+ *   status_out      out [ncells] or NULL: the OR of every forward step's and every step
+ *                   adjoint's NPFEM_CELL_* bits.
+ * The library owns the workspace (checkpoints, segment states, gradient buffers; about
+ * (2 nsteps/ckpt_every + 2 ckpt_every + 7) x 24 N_total bytes), allocated on the first
+ * call and grown when a later call needs more.  Asynchronous on `stream`.  Errors:
+ * INVALID_ARG (null pointer, FP32-form batch, nsteps or ckpt_every < 1, tol != 0,
+ * collisions on), CUDA, OOM. */
+npfem_status npfem_rollout_adjoint(npfem_batch* batch, const double* x0, const double* v0, const double* f_ext,
+                                   const int32_t* iters, const npfem_solver_opts* opts, int32_t nsteps,
+                                   int32_t ckpt_every, const double* gx_end, const double* gv_end, double* gx0,
+                                   double* gv0, double* gf, double* gweights, int32_t* status_out, void* stream);
 
 /* Gradients through the CONVERGED step (FP64 batches): the solver run to convergence
  * (Implementation and architecture section) differentiated by the implicit-function
@@ -223,8 +250,7 @@ npfem_status npfem_step_adjoint(npfem_batch* batch, const void* x, const void* v
  * gx gains C lam / dt.
  * Arrays as in npfem_step_adjoint.  The first call allocates two [3][N_total] FP64 copies
  * and the adjoint workspace.  Asynchronous on `stream`.  Errors: INVALID_ARG (null
- * pointer, FP32-form batch, bad cg_tol / cg_max_iters, collisions on, a type with strain
- * limits), CUDA, OOM. */
+ * pointer, FP32-form batch, bad cg_tol / cg_max_iters, collisions on), CUDA, OOM. */
 npfem_status npfem_step_adjoint_implicit(npfem_batch* batch, const void* x, const void* v, const void* f_ext,
                                          const int32_t* iters, const npfem_solver_opts* opts,
                                          const double* gx_next, const double* gv_next, double* gx, double* gv,
@@ -378,6 +404,8 @@ npfem_status npfem_step_host(npfem_batch* batch, void* x, void* v, const void* f
  * in the array (otherwise NPFEM_ERR_UNSUPPORTED with the sizes in the message).
  * The first call on a device looks up the array's device address and sets the
  * kernels' shared-memory limit; make that first call before any stream capture.
+ * Both are kept for the life of the process: after cudaDeviceReset on a device,
+ * further calls on it are unsupported.
  * Every call reuses the same array (the work-queue counter is cleared on each call),
  * so calls whose GPU work overlaps (two streams, or two threads) race and must be
  * serialised by the caller.  Asynchronous on `stream`. */

@@ -7,9 +7,11 @@ must equal the materials the batch's cell types were built with: the factorised 
 matrix depends on them, so new weight values need new cell types (see
 `Calibration.rebuild`).
 
-Rollouts keep a checkpoint of (x, v) every `ckpt_every` steps; the backward pass
-recomputes each segment forward from its checkpoint and runs the per-step adjoints in
-reverse, so memory grows with nsteps/ckpt_every + ckpt_every states instead of nsteps.
+Rollouts differentiate through the library's rollout adjoint (npfem_rollout_adjoint):
+it keeps a checkpoint of (x, v) every `ckpt_every` steps, recomputes each segment forward
+from its checkpoint and runs the per-step adjoints in reverse, so memory grows with
+nsteps/ckpt_every + ckpt_every states instead of nsteps.  The forward pass here only
+steps and keeps (x0, v0).
 """
 from __future__ import annotations
 
@@ -61,45 +63,22 @@ class RolloutFunction(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x0, v0, f, weights, batch, type_of_cell, iters, nsteps, ckpt_every):
         x, v = x0.detach().clone(), v0.detach().clone()
-        ckpts = []
-        for s in range(nsteps):
-            if s % ckpt_every == 0:
-                ckpts.append((x.clone(), v.clone()))
+        for _ in range(nsteps):
             batch.step(x, v, f.detach(), iters=iters)
-        ctx.ckpts = ckpts
-        ctx.save_for_backward(f.detach(), type_of_cell, iters)
+        ctx.save_for_backward(x0.detach(), v0.detach(), f.detach(), iters)
         ctx.batch, ctx.nsteps, ctx.ckpt_every, ctx.ntypes = batch, nsteps, ckpt_every, weights.shape[0]
         return x, v
 
     @staticmethod
     def backward(ctx, gxn, gvn):
-        f, toc, iters = ctx.saved_tensors
-        b, N, K = ctx.batch, ctx.nsteps, ctx.ckpt_every
-        x_like = ctx.ckpts[0][0]
-        gx = torch.zeros_like(x_like) if gxn is None else gxn.contiguous().clone()
-        gv = torch.zeros_like(x_like) if gvn is None else gvn.contiguous().clone()
-        gf_tot = torch.zeros_like(x_like)
-        gw_tot = torch.zeros((ctx.ntypes, 4), dtype=torch.float64, device=x_like.device)
-        ngx, ngv, ngf = torch.empty_like(gx), torch.empty_like(gx), torch.empty_like(gx)
-        gw = torch.empty((b.ncells, 4), dtype=torch.float64, device=x_like.device)
-        for seg in range(len(ctx.ckpts) - 1, -1, -1):
-            s0 = seg * K
-            s1 = min(N, s0 + K)
-            x, v = ctx.ckpts[seg][0].clone(), ctx.ckpts[seg][1].clone()
-            states = []
-            for s in range(s0, s1):
-                states.append((x.clone(), v.clone()))
-                if s + 1 < s1:
-                    b.step(x, v, f, iters=iters)
-            for s in range(s1 - 1, s0 - 1, -1):
-                xs, vs = states[s - s0]
-                b.step_adjoint(xs, vs, f, gx, gv, ngx, ngv, ngf, gw, iters=iters)
-                gx, ngx = ngx, gx
-                gv, ngv = ngv, gv
-                gf_tot += ngf
-                gw_tot += _type_sum(b, gw, toc, ctx.ntypes)
-        ctx.ckpts = None
-        return gx, gv, gf_tot, gw_tot, None, None, None, None, None
+        x0, v0, f, iters = ctx.saved_tensors
+        b = ctx.batch
+        gxn = torch.zeros_like(x0) if gxn is None else gxn.contiguous()
+        gvn = None if gvn is None else gvn.contiguous()
+        gx, gv, gf = torch.empty_like(x0), torch.empty_like(x0), torch.empty_like(x0)
+        gw = torch.empty((ctx.ntypes, 4), dtype=torch.float64, device=x0.device)
+        b.rollout_adjoint(x0, v0, f, gxn, gvn, gx, gv, gf, gw, ctx.nsteps, ctx.ckpt_every, iters=iters)
+        return gx, gv, gf, gw, None, None, None, None, None
 
 
 def rollout(batch: native.Batch, x0, v0, f, weights, type_of_cell, iters, nsteps: int, ckpt_every: int):

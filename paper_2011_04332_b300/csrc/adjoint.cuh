@@ -89,8 +89,58 @@ __device__ void matrix_weight_forms(const DevTypeView<double>& ty, const double*
 __device__ void apply_rayleigh(const DevTypeView<double>& ty, const CellWs<double>& w, const double* a,
                                double* out, int lane);
 
+// Strain limits: the projection P = U clamp(Sigma, lo, hi) V^T of F = [F0 F1] and its
+// directional derivative dP along dF, given the polar factor R = F (F^T F)^-1/2 and its
+// derivative dR.  By regime of the two singular values: both inside the limits, P = F and
+// dP = dF; both clamped to the same limit L, P = L R and dP = L dR (well conditioned for
+// any eigenvalue gap); otherwise (one on each side, so the eigenvalues l1 > l2 of
+// C = F^T F are apart) the spectral form P = F M, M = k2 I + c (C - l2 I),
+// c = (k1 - k2)/(l1 - l2), k_i = clamp(s_i)/s_i, differentiated with
+// dl1 = tr(Pi1 dC), Pi1 = (C - l2 I)/(l1 - l2), dl2 = tr(dC) - dl1, dk_i = -L/(2 s_i^3) dl_i
+// for a clamped s_i (0 inside), dc = (dk1 - dk2)/(l1 - l2) - (k1 - k2)(dl1 - dl2)/(l1 - l2)^2,
+// dM = dk2 I + dc (C - l2 I) + c (dC - dl2 I), dP = dF M + F dM.  Regimes and
+// eigenvalues as in the step's limit pass (l2 = |F0 x F1|^2 / l1, l1 - l2 = 2 disc).
+__device__ __noinline__ void limited_projection_jvp(V3<double> F0, V3<double> F1, V3<double> dF0, V3<double> dF1,
+                                                    V3<double> R0, V3<double> R1, V3<double> dR0,
+                                                    V3<double> dR1, double lo, double hi, V3<double>* P0,
+                                                    V3<double>* P1, V3<double>* dP0, V3<double>* dP1) {
+  const double c00 = dot(F0, F0), c01 = dot(F0, F1), c11 = dot(F1, F1);
+  const double h = 0.5 * (c00 + c11), q = 0.5 * (c00 - c11);
+  const double disc = sqrt(q * q + c01 * c01);
+  const V3<double> fx = cross(F0, F1);
+  const double l1 = h + disc, l2 = dot(fx, fx) / l1;
+  const double s1 = sqrt(l1), s2 = sqrt(l2);
+  const int r1 = s1 > hi ? 1 : (s1 < lo ? -1 : 0), r2 = s2 > hi ? 1 : (s2 < lo ? -1 : 0);
+  if (r1 == 0 && r2 == 0) {
+    *P0 = F0, *P1 = F1, *dP0 = dF0, *dP1 = dF1;
+    return;
+  }
+  if (r1 == r2) {
+    const double L = r1 > 0 ? hi : lo;
+    *P0 = L * R0, *P1 = L * R1, *dP0 = L * dR0, *dP1 = L * dR1;
+    return;
+  }
+  const double g00 = 2.0 * dot(F0, dF0), g01 = dot(F0, dF1) + dot(dF0, F1), g11 = 2.0 * dot(F1, dF1);
+  const double gap = 2.0 * disc;
+  const double dl1 = ((c00 - l2) * g00 + 2.0 * c01 * g01 + (c11 - l2) * g11) / gap;
+  const double dl2 = g00 + g11 - dl1;
+  const double L1 = r1 > 0 ? hi : lo, L2 = r2 > 0 ? hi : lo;
+  const double k1 = r1 ? L1 / s1 : 1.0, k2 = r2 ? L2 / s2 : 1.0;
+  const double dk1 = r1 ? -L1 / (2.0 * s1 * l1) * dl1 : 0.0, dk2 = r2 ? -L2 / (2.0 * s2 * l2) * dl2 : 0.0;
+  const double c = (k1 - k2) / gap;
+  const double dc = (dk1 - dk2) / gap - (k1 - k2) * (dl1 - dl2) / (gap * gap);
+  const double m00 = k2 + c * (c00 - l2), m01 = c * c01, m11 = k2 + c * (c11 - l2);
+  const double dm00 = dk2 + dc * (c00 - l2) + c * (g00 - dl2), dm01 = dc * c01 + c * g01,
+               dm11 = dk2 + dc * (c11 - l2) + c * (g11 - dl2);
+  *P0 = m00 * F0 + m01 * F1;
+  *P1 = m01 * F0 + m11 * F1;
+  *dP0 = (m00 * dF0 + m01 * dF1) + (dm00 * F0 + dm01 * F1);
+  *dP1 = (m01 * dF0 + m11 * dF1) + (dm01 * F0 + dm11 * F1);
+}
+
 // Hessian-vector product out = grad^2 f(x) Vv at x = x_n + U (inertia and Rayleigh damping
-// included), and wd[q] = Vv . d(grad f)/d(w_q) for the four material weights.
+// included), and wd[q] = Vv . d(grad f)/d(w_q) for the four material weights.  With strain
+// limits the strain term differentiates the clamped projection (limited_projection_jvp).
 __device__ void hessian_vector(const DevTypeView<double>& ty, const CellWs<double>& w, const double* U,
                                const double* Vv, double* out, V3<double> cvol, double wd[4], int lane) {
   const int n = ty.n, T = ty.T, E = ty.E;
@@ -147,6 +197,8 @@ __device__ void hessian_vector(const DevTypeView<double>& ty, const CellWs<doubl
       double n10 = h01 * i00 + h11 * i01, n11 = h01 * i01 + h11 * i11;
       V3<double> dR0 = (i00 * dF0 + i01 * dF1) - (n00 * R0 + n10 * R1);
       V3<double> dR1 = (i01 * dF0 + i11 * dF1) - (n01 * R0 + n11 * R1);
+      if (ty.limited)
+        limited_projection_jvp(F0, F1, dF0, dF1, R0, R1, dR0, dR1, ty.s_min, ty.s_max, &R0, &R1, &dR0, &dR1);
       P0 = wt * (dF0 - dR0);
       P1 = wt * (dF1 - dR1);
       ws_sum.add(at * (dot(dF0, F0 - R0) + dot(dF1, F1 - R1)));

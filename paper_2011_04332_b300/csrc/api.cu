@@ -101,6 +101,7 @@ struct npfem_batch {
     for (cudaEvent_t e : det_ev)
       if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : stag_events) cudaEventDestroy(e);
+    if (roll) cudaFree(roll);
     for (TypeLaunch& L : launches) {
       if (L.scratch) cudaFree(L.scratch);
       if (L.adj_scratch) cudaFree(L.adj_scratch);
@@ -130,6 +131,10 @@ struct npfem_batch {
   cudaEvent_t det_ev[2] = {nullptr, nullptr};  // around the detection kernels (kernel timing on)
   std::vector<cudaEvent_t> stag_events;         // staggered group starts (one per chain)
   bool det_timed = false;                      // the last step recorded det_ev
+  // rollout adjoint (npfem_rollout_adjoint): checkpoints, segment states and gradient
+  // buffers in one allocation, grown on demand
+  char* roll = nullptr;
+  size_t roll_bytes = 0;
 };
 
 template <typename S>
@@ -177,7 +182,7 @@ static void fill_view(npfem_cell_type* t, DevTypeView<S>* v, const S* Dinv, cons
 }
 
 template <typename S>
-static cudaError_t upload_precision(npfem_cell_type* t, DevTypeView<S>* view, const int32_t* tris,
+static cudaError_t upload_precision(npfem_cell_type* t, DevTypeView<S>* view, const int32_t* tris, const int32_t* tri4,
                                     const int32_t* hinges, const int32_t* inc_ptr, const int32_t* inc_code,
                                     const int32_t* perm, const double* dinv, const int32_t* fcol,
                                     const uint32_t* frow, const double* fval, const int32_t* bcol,
@@ -199,6 +204,17 @@ static cudaError_t upload_precision(npfem_cell_type* t, DevTypeView<S>* view, co
   if ((e = t->mem.upload(convert<S>(H.hinge_unit), &hunit)) != cudaSuccess) return e;
   view->tri_area = tarea;
   view->hinge_unit = hunit;
+  std::vector<double> trc(4 * (size_t)H.T);
+  for (int q = 0; q < H.T; ++q) {
+    trc[4 * q] = H.Dinv[3 * q];
+    trc[4 * q + 1] = H.Dinv[3 * q + 1];
+    trc[4 * q + 2] = H.Dinv[3 * q + 2];
+    trc[4 * q + 3] = H.w_tri[q];
+  }
+  const S* trc_d;
+  if ((e = t->mem.upload(convert<S>(trc), &trc_d)) != cudaSuccess) return e;
+  view->trc = trc_d;
+  view->tri4 = tri4;
   fill_view<S>(t, view, Dinv, w_tri, c_hinge, K0, w_hinge, mass, im, coef, tris, hinges, inc_ptr, inc_code, perm,
                dinv, fcol, frow, fval, bcol, brow, bval);
   return cudaSuccess;
@@ -288,8 +304,8 @@ static void default_split_shape(TypeLaunch& L, int n, npfem_precision prec) {
   L.sv_cells = 1;
   if (n <= 256) {         // platelet-sized: 14 solve warps/SM, one vector per warp
     L.sv_wpb = 2, L.sv_bps = 7, L.sv_smem = 1;
-  } else if (n <= 1024) {  // 642-vertex RBC: CTAs of 2 warps per cell, 10 per SM
-    L.sv_wpb = 2, L.sv_bps = 10, L.sv_smem = 2;
+  } else if (n <= 1024) {  // 642-vertex RBC: CTAs of 2 warps per cell, 13 per SM (72 registers)
+    L.sv_wpb = 2, L.sv_bps = 13, L.sv_smem = 2;
   } else {                 // 2562-vertex RBC: CTAs of 6 warps per cell, 3 per SM
     L.sv_wpb = 6, L.sv_bps = 3, L.sv_smem = 2;
   }
@@ -669,12 +685,16 @@ npfem_status npfem_create_cell_type(const npfem_mesh* mesh, const npfem_material
   t->host.s_max = s_hi;
   cudaError_t e = cudaGetDevice(&t->device);
   const HostType& H = t->host;
-  const int32_t *tris, *hinges, *inc_ptr, *inc_code, *perm, *fcol, *bcol;
+  const int32_t *tris, *tri4, *hinges, *inc_ptr, *inc_code, *perm, *fcol, *bcol;
+  std::vector<int32_t> tri4_h(4 * (size_t)H.T, 0);
+  for (int q = 0; q < H.T; ++q)
+    for (int k = 0; k < 3; ++k) tri4_h[4 * q + k] = H.tris[3 * q + k];
   const uint32_t *frow, *brow;
   const double *dinv, *fval, *bval;
 #define UP(vec, ptr)                                      \
   if (e == cudaSuccess) e = t->mem.upload(vec, &ptr);
   UP(H.tris, tris);
+  UP(tri4_h, tri4);
   UP(H.hinges, hinges);
   UP(H.inc_ptr, inc_ptr);
   UP(H.inc_code, inc_code);
@@ -700,10 +720,10 @@ npfem_status npfem_create_cell_type(const npfem_mesh* mesh, const npfem_material
     if (e == cudaSuccess) e = t->mem.upload(P.bwd_val, &cbv[i]);
   }
   if (e == cudaSuccess)
-    e = upload_precision<double>(t, &t->v64, tris, hinges, inc_ptr, inc_code, perm, dinv, fcol, frow, fval, bcol,
+    e = upload_precision<double>(t, &t->v64, tris, tri4, hinges, inc_ptr, inc_code, perm, dinv, fcol, frow, fval, bcol,
                                  brow, bval);
   if (e == cudaSuccess)
-    e = upload_precision<float>(t, &t->v32, tris, hinges, inc_ptr, inc_code, perm, dinv, fcol, frow, fval, bcol,
+    e = upload_precision<float>(t, &t->v32, tris, tri4, hinges, inc_ptr, inc_code, perm, dinv, fcol, frow, fval, bcol,
                                 brow, bval);
   if (e == cudaSuccess) {
     for (int i = 0; i < kCtaPacks; ++i) {
@@ -971,9 +991,6 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: tol must be 0 (fixed iteration counts)");
   if (b->coll)
     return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: collisions are enabled (contacts are not differentiated)");
-  for (const npfem_cell_type* t : b->types)
-    if (t->host.s_min != 1.0 || t->host.s_max != 1.0)
-      return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint: a cell type has strain limits (not differentiated)");
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   npfem_status arc = ensure_adjoint_workspace(b);
@@ -1020,6 +1037,151 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
   return NPFEM_OK;
 }
 
+}  // extern "C"
+
+// Rollout adjoint helpers: y += x; a |= c; out4 += sum over the listed cells of gw[c][0..3]
+// in a fixed order (one CTA per cell type, strided per-thread sums, then a tree in shared
+// memory), so the per-type weight gradients are bit-for-bit reproducible.
+__global__ void npfem_k_add(double* __restrict__ y, const double* __restrict__ x, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += x[i];
+}
+__global__ void npfem_k_or(int32_t* __restrict__ a, const int32_t* __restrict__ c, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] |= c[i];
+}
+constexpr int kTypeSumThreads = 256;
+__global__ void __launch_bounds__(kTypeSumThreads) npfem_k_type_sum(const double* __restrict__ gw,
+                                                                     const int32_t* __restrict__ cells, int ncells,
+                                                                     double* __restrict__ out4) {
+  __shared__ double red[4][kTypeSumThreads];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int i = threadIdx.x; i < ncells; i += kTypeSumThreads)
+    for (int q = 0; q < 4; ++q) acc[q] += gw[4 * (size_t)cells[i] + q];
+  for (int q = 0; q < 4; ++q) red[q][threadIdx.x] = acc[q];
+  __syncthreads();
+  for (int w = kTypeSumThreads / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+      for (int q = 0; q < 4; ++q) red[q][threadIdx.x] += red[q][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) out4[threadIdx.x] += red[threadIdx.x][0];
+}
+
+static int grid_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 148 * 16)); }
+
+extern "C" {
+
+npfem_status npfem_rollout_adjoint(npfem_batch* b, const double* x0, const double* v0, const double* f_ext,
+                                   const int32_t* iters, const npfem_solver_opts* opts, int32_t nsteps,
+                                   int32_t ckpt_every, const double* gx_end, const double* gv_end, double* gx0,
+                                   double* gv0, double* gf, double* gweights, int32_t* status_out, void* stream) {
+  if (!b || !opts) return fail(NPFEM_ERR_INVALID_ARG, "rollout_adjoint: null batch or opts");
+  if (b->prec != NPFEM_FP64) return fail(NPFEM_ERR_INVALID_ARG, "rollout_adjoint: needs an FP64 batch");
+  if (nsteps < 1 || ckpt_every < 1)
+    return fail(NPFEM_ERR_INVALID_ARG, "rollout_adjoint: nsteps and ckpt_every must be >= 1");
+  if (!gweights) return fail(NPFEM_ERR_INVALID_ARG, "rollout_adjoint: null gweights");
+  if (opts->tol != 0.0)
+    return fail(NPFEM_ERR_INVALID_ARG, "rollout_adjoint: tol must be 0 (fixed iteration counts)");
+  if (b->coll)
+    return fail(NPFEM_ERR_INVALID_ARG, "rollout_adjoint: collisions are enabled (contacts are not differentiated)");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t ntypes = b->types.size();
+  NPFEM_CUDA_TRY(cudaMemsetAsync(gweights, 0, sizeof(double) * 4 * ntypes, st));
+  if (b->ncells == 0) return NPFEM_OK;
+  if (!x0 || !v0 || !f_ext || !gx_end || !gx0 || !gv0 || !gf)
+    return fail(NPFEM_ERR_INVALID_ARG, "rollout_adjoint: null array");
+  if (opts->iters < 0 || opts->iters > kMaxAdjIters)
+    return fail(NPFEM_ERR_INVALID_ARG, "rollout_adjoint: iteration count must be in [0, 16]");
+  // workspace: ncp checkpoints and K segment states of (x, v), the running state, two
+  // (gx, gv) pairs, one step's gf, per-cell gw and statuses
+  const int K = ckpt_every, ncp = (nsteps + K - 1) / K;
+  const size_t nv = (size_t)3 * b->n_total, vb = sizeof(double) * nv;
+  const size_t need = vb * (2 * (size_t)ncp + 2 * (size_t)K + 2 + 4 + 1) + sizeof(double) * 4 * (size_t)b->ncells +
+                      sizeof(int32_t) * (size_t)b->ncells + 256;
+  if (need > b->roll_bytes) {
+    if (b->roll) {
+      NPFEM_CUDA_TRY(cudaStreamSynchronize(st));
+      cudaFree(b->roll);
+      b->roll = nullptr;
+      b->roll_bytes = 0;
+    }
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, need);
+    if (e != cudaSuccess) return fail(NPFEM_ERR_OOM, std::string("rollout_adjoint: workspace: ") + cudaGetErrorString(e));
+    b->roll = static_cast<char*>(p);
+    b->roll_bytes = need;
+  }
+  double* base = reinterpret_cast<double*>(b->roll);
+  double* ck = base;                                  // [ncp][2][3N]
+  double* seg = ck + 2 * (size_t)ncp * nv;            // [K][2][3N]
+  double* xw = seg + 2 * (size_t)K * nv;              // running x, v
+  double* vw = xw + nv;
+  double* g[4] = {vw + nv, vw + 2 * nv, vw + 3 * nv, vw + 4 * nv};  // (gx, gv) pairs a and b
+  double* gfs = vw + 5 * nv;
+  double* gwc = gfs + nv;                             // [ncells][4]
+  int32_t* sts = reinterpret_cast<int32_t*>(gwc + 4 * (size_t)b->ncells);
+  const int32_t* ssrc = status_out ? sts : nullptr;
+  if (status_out) NPFEM_CUDA_TRY(cudaMemsetAsync(status_out, 0, sizeof(int32_t) * b->ncells, st));
+  npfem_solver_opts fo = *opts;
+  fo.alpha_log = nullptr;
+  fo.alpha_log_len = 0;
+  fo.iters_done = nullptr;
+  auto step_fwd = [&](double* x, double* v) -> npfem_status {
+    npfem_status rc = npfem_step(b, x, v, f_ext, iters, &fo, nullptr, status_out ? sts : nullptr, stream);
+    if (rc == NPFEM_OK && status_out) npfem_k_or<<<grid_for(b->ncells), 256, 0, st>>>(status_out, ssrc, b->ncells);
+    return rc;
+  };
+  // forward: checkpoint (x, v) before steps 0, K, 2K, ...
+  NPFEM_CUDA_TRY(cudaMemcpyAsync(xw, x0, vb, cudaMemcpyDeviceToDevice, st));
+  NPFEM_CUDA_TRY(cudaMemcpyAsync(vw, v0, vb, cudaMemcpyDeviceToDevice, st));
+  for (int s = 0; s < nsteps; ++s) {
+    if (s % K == 0) {
+      NPFEM_CUDA_TRY(cudaMemcpyAsync(ck + 2 * (size_t)(s / K) * nv, xw, vb, cudaMemcpyDeviceToDevice, st));
+      NPFEM_CUDA_TRY(cudaMemcpyAsync(ck + (2 * (size_t)(s / K) + 1) * nv, vw, vb, cudaMemcpyDeviceToDevice, st));
+    }
+    npfem_status rc = step_fwd(xw, vw);
+    if (rc != NPFEM_OK) return rc;
+  }
+  // reverse: per segment, recompute its states from the checkpoint, then the step adjoints
+  NPFEM_CUDA_TRY(cudaMemcpyAsync(g[0], gx_end, vb, cudaMemcpyDeviceToDevice, st));
+  if (gv_end)
+    NPFEM_CUDA_TRY(cudaMemcpyAsync(g[1], gv_end, vb, cudaMemcpyDeviceToDevice, st));
+  else
+    NPFEM_CUDA_TRY(cudaMemsetAsync(g[1], 0, vb, st));
+  NPFEM_CUDA_TRY(cudaMemsetAsync(gf, 0, vb, st));
+  int cur = 0;  // (g[2 cur], g[2 cur + 1]) holds dL/d(x_s, v_s) of the step being reversed
+  for (int sg = ncp - 1; sg >= 0; --sg) {
+    const int s0 = sg * K, s1 = std::min(nsteps, s0 + K);
+    NPFEM_CUDA_TRY(cudaMemcpyAsync(xw, ck + 2 * (size_t)sg * nv, vb, cudaMemcpyDeviceToDevice, st));
+    NPFEM_CUDA_TRY(cudaMemcpyAsync(vw, ck + (2 * (size_t)sg + 1) * nv, vb, cudaMemcpyDeviceToDevice, st));
+    for (int s = s0; s < s1; ++s) {
+      NPFEM_CUDA_TRY(cudaMemcpyAsync(seg + 2 * (size_t)(s - s0) * nv, xw, vb, cudaMemcpyDeviceToDevice, st));
+      NPFEM_CUDA_TRY(cudaMemcpyAsync(seg + (2 * (size_t)(s - s0) + 1) * nv, vw, vb, cudaMemcpyDeviceToDevice, st));
+      if (s + 1 < s1) {
+        npfem_status rc = npfem_step(b, xw, vw, f_ext, iters, &fo, nullptr, nullptr, stream);
+        if (rc != NPFEM_OK) return rc;
+      }
+    }
+    for (int s = s1 - 1; s >= s0; --s) {
+      const double* xs = seg + 2 * (size_t)(s - s0) * nv;
+      const double* vs = xs + nv;
+      npfem_status rc = npfem_step_adjoint(b, xs, vs, f_ext, iters, opts, g[2 * cur], g[2 * cur + 1],
+                                           g[2 * (1 - cur)], g[2 * (1 - cur) + 1], gfs, gwc, ssrc ? sts : nullptr,
+                                           stream);
+      if (rc != NPFEM_OK) return rc;
+      cur = 1 - cur;
+      npfem_k_add<<<grid_for((int64_t)nv), 256, 0, st>>>(gf, gfs, (int64_t)nv);
+      for (const TypeLaunch& L : b->launches)
+        npfem_k_type_sum<<<1, kTypeSumThreads, 0, st>>>(gwc, L.cell_list, L.ncells, gweights + 4 * L.type_index);
+      if (status_out) npfem_k_or<<<grid_for(b->ncells), 256, 0, st>>>(status_out, ssrc, b->ncells);
+      NPFEM_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  NPFEM_CUDA_TRY(cudaMemcpyAsync(gx0, g[2 * cur], vb, cudaMemcpyDeviceToDevice, st));
+  NPFEM_CUDA_TRY(cudaMemcpyAsync(gv0, g[2 * cur + 1], vb, cudaMemcpyDeviceToDevice, st));
+  return NPFEM_OK;
+}
+
 npfem_status npfem_step_adjoint_implicit(npfem_batch* b, const void* x, const void* v, const void* f_ext,
                                          const int32_t* iters, const npfem_solver_opts* opts, const double* gx_next,
                                          const double* gv_next, double* gx, double* gv, double* gf, double* gw,
@@ -1034,9 +1196,6 @@ npfem_status npfem_step_adjoint_implicit(npfem_batch* b, const void* x, const vo
   if (b->coll)
     return fail(NPFEM_ERR_INVALID_ARG,
                 "step_adjoint_implicit: collisions are enabled (contacts are not differentiated)");
-  for (const npfem_cell_type* t : b->types)
-    if (t->host.s_min != 1.0 || t->host.s_max != 1.0)
-      return fail(NPFEM_ERR_INVALID_ARG, "step_adjoint_implicit: a cell type has strain limits (not differentiated)");
 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = sizeof(double) * 3 * (size_t)b->n_total;

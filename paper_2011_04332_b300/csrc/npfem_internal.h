@@ -87,6 +87,8 @@ struct DevTypeView {
   int nchunks_fwd, nchunks_bwd;
   int cta_nlev_fwd[kCtaPacks], cta_nlev_bwd[kCtaPacks];   // levels of the CTA packings
   const int32_t* tris;      // [T][3]
+  const int32_t* tri4;      // [T][4] (i0, i1, i2, 0): one 16-byte load per triangle
+  const S* trc;             // [T][4] (d00, d01, d11, w_tri): one vector load per triangle
   const S* Dinv;            // [T][3]
   const S* w_tri;           // [T]
   const int32_t* hinges;    // [E][4]

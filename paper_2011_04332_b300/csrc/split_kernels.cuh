@@ -374,14 +374,17 @@ __global__ void __launch_bounds__(128) npfem_k_solve(DevTypeView<S> ty, StepPara
 // but cooperative): warp w applies sub-chunk w of every level to the shared vector
 // zs ([n+1][3] doubles in shared memory), with a barrier of the CTA before every level
 // that touches a row written since the last barrier; the levels in between commute.
+// Levels of the factor stream a warp of the CTA-cooperative sweep keeps in flight.
+constexpr int kCtaPrefetch = 6;
+
 template <int W>
 __device__ __forceinline__ void cta_sweep(int nlev, const int32_t* __restrict__ meta, const uint32_t* __restrict__ rc,
                                           const double* __restrict__ val, uint32_t zs, int n, int warp, int lane) {
-  int mb[kPrefetch];
-  uint32_t eb[kPrefetch];
-  double vb[kPrefetch];
+  int mb[kCtaPrefetch];
+  uint32_t eb[kCtaPrefetch];
+  double vb[kCtaPrefetch];
 #pragma unroll
-  for (int k = 0; k < kPrefetch; ++k) {
+  for (int k = 0; k < kCtaPrefetch; ++k) {
     if (k < nlev) {
       const size_t sc = (size_t)k * W + warp;
       mb[k] = __ldg(meta + sc);
@@ -393,15 +396,15 @@ __device__ __forceinline__ void cta_sweep(int nlev, const int32_t* __restrict__ 
       vb[k] = 0.0;
     }
   }
-  for (int base = 0; base < nlev; base += kPrefetch) {
+  for (int base = 0; base < nlev; base += kCtaPrefetch) {
 #pragma unroll
-    for (int k = 0; k < kPrefetch; ++k) {
+    for (int k = 0; k < kCtaPrefetch; ++k) {
       const int lv = base + k;
       if (lv < nlev) {
         const int m = mb[k];
         const uint32_t e = eb[k];
         const double l = vb[k];
-        const int nx = lv + kPrefetch;
+        const int nx = lv + kCtaPrefetch;
         if (nx < nlev) {
           const size_t sc = (size_t)nx * W + warp;
           mb[k] = __ldg(meta + sc);
@@ -437,8 +440,20 @@ struct CtaPack {
   static_assert(W == kCtaWarps[value], "no level packing for this CTA width");
 };
 
+// Resident CTAs per SM the CTA-cooperative solve is compiled for (a register budget of
+// 65536 / (32 W x min_blocks) per thread).  The 2-warp CTA of the 642-vertex type holds
+// a 15.4 KB vector, so shared memory admits 13 per SM, and 72 registers let registers
+// admit as many (at 96 registers only 10 fit); the wider CTAs keep the residency their
+// shared memory allows for the larger types (6 warps: three 61.5 KB vectors of a
+// 2562-vertex cell).
+template <int W>
+struct SolveCtaOccupancy {
+  static constexpr int min_blocks = W == 2 ? 13 : (W == 4 ? 5 : (W == 6 ? 3 : 2));
+};
+
 template <typename S, int W>
-__global__ void __launch_bounds__(32 * W) npfem_k_solve_cta(DevTypeView<S> ty, StepParams P) {
+__global__ void __launch_bounds__(32 * W, SolveCtaOccupancy<W>::min_blocks) npfem_k_solve_cta(DevTypeView<S> ty,
+                                                                                            StepParams P) {
   constexpr int pk = CtaPack<W>::value;
   extern __shared__ double smem_z[];
   __shared__ int s_item;

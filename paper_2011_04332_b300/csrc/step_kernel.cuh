@@ -130,6 +130,34 @@ __device__ __forceinline__ void st3(S* p, int i, V3<S> v) {
   p[3 * i + 1] = v.y;
   p[3 * i + 2] = v.z;
 }
+// Four consecutive entries of a per-element table with 4 entries per element (16-byte
+// aligned rows: one vector load for floats and ints, two for doubles).
+struct Q4f {
+  float x, y, z, w;
+};
+struct Q4d {
+  double x, y, z, w;
+};
+template <typename S>
+struct Q4Of;
+template <>
+struct Q4Of<float> {
+  using type = Q4f;
+};
+template <>
+struct Q4Of<double> {
+  using type = Q4d;
+};
+__device__ __forceinline__ Q4f ldg4(const float* p) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  return {a.x, a.y, a.z, a.w};
+}
+__device__ __forceinline__ Q4d ldg4(const double* p) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p)), b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  return {a.x, a.y, b.x, b.y};
+}
+__device__ __forceinline__ int4 ldg4(const int32_t* p) { return __ldg(reinterpret_cast<const int4*>(p)); }
+
 template <typename S>
 __device__ __forceinline__ V3<S> operator+(V3<S> a, V3<S> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
 template <typename S>
@@ -196,6 +224,9 @@ __device__ __forceinline__ CellWs<S> carve(char* base, int n, int T, int E, doub
 }
 
 // ------------------------------------------------------------------ K2
+// Incidence entries of a vertex loaded together by the gradient gather (pass D).
+constexpr int kGatherBatch = 6;
+
 struct EvalOut {
   double energy;
   bool degenerate;
@@ -355,7 +386,8 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const StepParams& P,
   // pass A: global area and volume (FP64 reductions)
   Acc<S> a_sum, v_sum;
   for (int t = lane; t < T; t += 32) {
-    int i0 = __ldg(&ty.tris[3 * t]), i1 = __ldg(&ty.tris[3 * t + 1]), i2 = __ldg(&ty.tris[3 * t + 2]);
+    const int4 tv = ldg4(ty.tri4 + 4 * t);
+    const int i0 = tv.x, i1 = tv.y, i2 = tv.z;
     V3<S> e1 = edge(X, U, i0, i1), e2 = edge(X, U, i0, i2);
     V3<S> N = cross(e1, e2);
     a_sum.add(sqrt(dot(N, N)));
@@ -376,10 +408,12 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const StepParams& P,
   Acc<S> e_el;
   bool degen = false;
   for (int t = lane; t < T; t += 32) {
-    int i0 = __ldg(&ty.tris[3 * t]), i1 = __ldg(&ty.tris[3 * t + 1]), i2 = __ldg(&ty.tris[3 * t + 2]);
+    const int4 tv = ldg4(ty.tri4 + 4 * t);
+    const typename Q4Of<S>::type tc = ldg4(ty.trc + 4 * t);
+    const int i0 = tv.x, i1 = tv.y, i2 = tv.z;
     V3<S> e1 = edge(X, U, i0, i1), e2 = edge(X, U, i0, i2);
-    const S d00 = __ldg(&ty.Dinv[3 * t]), d01 = __ldg(&ty.Dinv[3 * t + 1]), d11 = __ldg(&ty.Dinv[3 * t + 2]);
-    const S wt = __ldg(&ty.w_tri[t]);
+    const S d00 = tc.x, d01 = tc.y, d11 = tc.z;
+    const S wt = tc.w;
     V3<S> F0 = d00 * e1;
     V3<S> F1 = d01 * e1 + d11 * e2;
     S c00 = dot(F0, F0), c01 = dot(F0, F1), c11 = dot(F1, F1);
@@ -433,9 +467,10 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const StepParams& P,
 
   // pass C: hinges (bending projection onto |K| = |K0|)
   for (int h = lane; h < E; h += 32) {
-    int i = __ldg(&ty.hinges[4 * h]), j = __ldg(&ty.hinges[4 * h + 1]);
-    int ka = __ldg(&ty.hinges[4 * h + 2]), kb = __ldg(&ty.hinges[4 * h + 3]);
-    const S c1 = __ldg(&ty.c_hinge[4 * h + 1]), c2 = __ldg(&ty.c_hinge[4 * h + 2]), c3 = __ldg(&ty.c_hinge[4 * h + 3]);
+    const int4 hv = ldg4(ty.hinges + 4 * h);
+    const int i = hv.x, j = hv.y, ka = hv.z, kb = hv.w;
+    const typename Q4Of<S>::type cv = ldg4(ty.c_hinge + 4 * h);
+    const S c1 = cv.y, c2 = cv.z, c3 = cv.w;
     V3<S> K = c1 * edge(X, U, i, j) + c2 * edge(X, U, i, ka) + c3 * edge(X, U, i, kb);
     S kn = sqrt(dot(K, K));
     V3<S> p;
@@ -465,14 +500,28 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const StepParams& P,
     e_el.add(half * m * idt2 * dot(du, du));
     V3<S> g = (m * idt2) * du;
     const int e0 = __ldg(&ty.inc_ptr[v]), e1 = __ldg(&ty.inc_ptr[v + 1]);
-    for (int e = e0; e < e1; ++e) {
-      int code = __ldg(&ty.inc_code[e]);
-      if (code >= 0) {
-        g = g + ld3(w.corner, code);
-      } else {
-        int h = (-code - 1) >> 2;
-        g = g + __ldg(&ty.inc_coef[e]) * ld3(w.hbuf, h);
+    // The vertex's entries (its corners, then its hinge entries) kGatherBatch at a time:
+    // every code of a batch, then every record it names, is loaded before the first add,
+    // so a lane has a batch of independent loads in flight instead of one round trip per
+    // entry.  The adds keep the entry order; a corner adds 1 * record, which rounds like
+    // the plain add.  Records are addressed from the corner array, which the hinge
+    // buffer follows (hbuf = corner + 9T).
+    for (int e = e0; e < e1; e += kGatherBatch) {
+      int off[kGatherBatch];
+      S cf[kGatherBatch];
+#pragma unroll
+      for (int k = 0; k < kGatherBatch; ++k) {
+        const int ek = e + k < e1 ? e + k : e1 - 1;
+        const int code = __ldg(&ty.inc_code[ek]);
+        off[k] = code >= 0 ? 3 * code : 9 * T + 3 * ((-code - 1) >> 2);
+        cf[k] = code >= 0 ? (S)1 : __ldg(&ty.inc_coef[ek]);
       }
+      V3<S> rec[kGatherBatch];
+#pragma unroll
+      for (int k = 0; k < kGatherBatch; ++k) rec[k] = {w.corner[off[k]], w.corner[off[k] + 1], w.corner[off[k] + 2]};
+#pragma unroll
+      for (int k = 0; k < kGatherBatch; ++k)
+        if (e + k < e1) g = g + cf[k] * rec[k];
     }
     st3(Gout, v, g);
   }

@@ -98,6 +98,8 @@ def load_library() -> C.CDLL:
         "npfem_batch_set_collisions": [vp, C.POINTER(_CollisionParams)],
         "npfem_batch_contacts": [vp, vp, vp, vp, vp],
         "npfem_batch_contact_time": [vp, C.POINTER(C.c_double)],
+        "npfem_rollout_adjoint": [vp, vp, vp, vp, vp, C.POINTER(_Opts), C.c_int32, C.c_int32, vp, vp, vp, vp, vp,
+                                  vp, vp, vp],
         "npfem_step_adjoint_implicit": [vp, vp, vp, vp, vp, C.POINTER(_Opts), vp, vp, vp, vp, vp, vp, C.c_double,
                                         C.c_int32, vp, vp],
     }
@@ -125,6 +127,65 @@ def _ptr(t) -> Optional[int]:
         return t.ctypes.data
     assert t.is_contiguous()
     return t.data_ptr()
+
+
+def _state_dtype(precision: int):
+    import torch
+    return torch.float64 if precision == FP64 else torch.float32
+
+
+def _check_dev(name: str, t, dtype, shape, optional: bool = False, at_least: bool = False):
+    """Raise ValueError unless t is a contiguous CUDA tensor of this dtype and shape (the
+    library reads and writes it through a raw pointer: a wrong size or type would make
+    the kernels access memory outside it).  at_least: the leading dimension may be
+    larger (per-cell outputs, of which the library writes the first ncells rows)."""
+    if t is None:
+        if optional:
+            return
+        raise ValueError(f"{name}: required")
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name}: expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise ValueError(f"{name}: dtype {t.dtype}, expected {dtype}")
+    shp, want = tuple(t.shape), tuple(shape)
+    ok = shp == want or (at_least and len(shp) == len(want) and shp[0] >= want[0] and shp[1:] == want[1:])
+    if not ok:
+        raise ValueError(f"{name}: shape {shp}, expected {'at least ' if at_least else ''}{want}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: not contiguous")
+
+
+def _check_host(name: str, a, dtype, shape, optional: bool = False):
+    """The host-buffer counterpart of _check_dev for numpy arrays."""
+    if a is None:
+        if optional:
+            return
+        raise ValueError(f"{name}: required")
+    if not isinstance(a, np.ndarray):
+        raise ValueError(f"{name}: expected a numpy array")
+    if a.dtype != np.dtype(dtype):
+        raise ValueError(f"{name}: dtype {a.dtype}, expected {np.dtype(dtype)}")
+    if tuple(a.shape) != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(a.shape)}, expected {tuple(shape)}")
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{name}: not C-contiguous")
+
+
+def _check_step_args(ncells: int, n_total: int, precision: int, x, v, f, iters, residual, status, iters_done,
+                     alpha_log):
+    import torch
+    sd = _state_dtype(precision)
+    for name, t in (("x", x), ("v", v), ("f", f)):
+        _check_dev(name, t, sd, (3, n_total))
+    _check_dev("iters", iters, torch.int32, (ncells,), optional=True, at_least=True)
+    _check_dev("residual", residual, torch.float64, (ncells,), optional=True, at_least=True)
+    _check_dev("status", status, torch.int32, (ncells,), optional=True, at_least=True)
+    _check_dev("iters_done", iters_done, torch.int32, (ncells,), optional=True, at_least=True)
+    if alpha_log is not None:
+        if alpha_log.dim() != 2:
+            raise ValueError("alpha_log: expected [ncells, length]")
+        _check_dev("alpha_log", alpha_log, torch.float64, (ncells, alpha_log.shape[1]), at_least=True)
 
 
 def analyze_cell_type(verts: np.ndarray, tris: np.ndarray, material: Sequence[float], dt: float) -> dict:
@@ -175,7 +236,12 @@ def step_noalloc(cell_type: "CellType", precision: int, ncells: int, x, v, f, it
                  iters_default: int = 5, residual=None, status=None, alpha_log=None, stream=None,
                  tol: float = 0.0, iters_done=None):
     """npfem_step_noalloc: step `ncells` back-to-back cells of one type without any
-    device allocation (static library workspace); device tensors as for Batch.step."""
+    device allocation (static library workspace); device tensors as for Batch.step,
+    x, v, f of shape [3, ncells * n] (back-to-back cells of the type)."""
+    if int(ncells) >= 0:
+        n = int(cell_type.info()["n_verts"])
+        _check_step_args(int(ncells), int(ncells) * n, precision, x, v, f, iters, residual, status, iters_done,
+                         alpha_log)
     opts = _Opts(int(iters_default), 0 if alpha_log is None else int(alpha_log.shape[-1]), _ptr(alpha_log),
                  0, float(tol), _ptr(iters_done))
     if stream is None:
@@ -216,6 +282,8 @@ class Batch:
         With an iters tensor, pass max_iters (>= every count) to use the split kernels.
         tol > 0: converged-residual mode (iteration counts become budgets); iters_done: an
         int32 device tensor [ncells] that receives the iterations each cell ran."""
+        _check_step_args(self.ncells, self.n_total, self.precision, x, v, f, iters, residual, status, iters_done,
+                         alpha_log)
         if iters is not None and max_iters == 0:
             max_iters = self._iter_bound(iters)
         opts = _Opts(int(iters_default), 0 if alpha_log is None else int(alpha_log.shape[-1]),
@@ -232,6 +300,7 @@ class Batch:
                      status=None, stream=None, tol: float = 0.0):
         """npfem_step_adjoint on device tensors (FP64 batches): reverse mode of one step
         (fixed iteration counts: the library rejects tol != 0)."""
+        self._check_adjoint_args(x, v, f, gx_next, gv_next, gx, gv, gf, gw, iters, status)
         opts = _Opts(int(iters_default), 0, None, 0, float(tol), None)
         if stream is None:
             import torch
@@ -242,11 +311,36 @@ class Batch:
                                        _ptr(gx_next), _ptr(gv_next), _ptr(gx), _ptr(gv), _ptr(gf), _ptr(gw),
                                        _ptr(status), C.c_void_p(stream)))
 
+    def rollout_adjoint(self, x0, v0, f, gx_end, gv_end, gx0, gv0, gf, gweights, nsteps: int, ckpt_every: int,
+                        iters=None, iters_default: int = 5, status=None, stream=None):
+        """npfem_rollout_adjoint on device tensors (FP64 batches): reverse mode of an
+        nsteps rollout from (x0, v0) with constant forces f, checkpointed every ckpt_every
+        steps inside the library; gweights [ntypes, 4] receives the per-type weight
+        gradients."""
+        import torch
+        shp = (3, self.n_total)
+        for name, t in (("x0", x0), ("v0", v0), ("f", f), ("gx_end", gx_end), ("gx0", gx0), ("gv0", gv0), ("gf", gf)):
+            _check_dev(name, t, torch.float64, shp)
+        _check_dev("gv_end", gv_end, torch.float64, shp, optional=True)
+        _check_dev("gweights", gweights, torch.float64, (len(self.types), 4))
+        _check_dev("iters", iters, torch.int32, (self.ncells,), optional=True, at_least=True)
+        _check_dev("status", status, torch.int32, (self.ncells,), optional=True, at_least=True)
+        max_iters = self._iter_bound(iters) if iters is not None else 0
+        opts = _Opts(int(iters_default), 0, None, int(max_iters), 0.0, None)
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        elif not isinstance(stream, int):
+            stream = stream.cuda_stream
+        _check(_lib.npfem_rollout_adjoint(self.handle, _ptr(x0), _ptr(v0), _ptr(f), _ptr(iters), C.byref(opts),
+                                          int(nsteps), int(ckpt_every), _ptr(gx_end), _ptr(gv_end), _ptr(gx0),
+                                          _ptr(gv0), _ptr(gf), _ptr(gweights), _ptr(status), C.c_void_p(stream)))
+
     def step_adjoint_implicit(self, x, v, f, gx_next, gv_next, gx, gv, gf, gw, iters=None, iters_default: int = 5,
                               tol: float = 0.0, max_iters: int = 0, cg_tol: float = 1e-12, cg_max_iters: int = 200,
                               status=None, stream=None):
         """npfem_step_adjoint_implicit on device tensors (FP64 batches): gradients through
         the converged step (forward step with iters/tol as in step, then CG on the Hessian)."""
+        self._check_adjoint_args(x, v, f, gx_next, gv_next, gx, gv, gf, gw, iters, status)
         if iters is not None and max_iters == 0:
             max_iters = self._iter_bound(iters)
         opts = _Opts(int(iters_default), 0, None, int(max_iters), float(tol), None)
@@ -259,6 +353,17 @@ class Batch:
                                                 _ptr(gx_next), _ptr(gv_next), _ptr(gx), _ptr(gv), _ptr(gf),
                                                 _ptr(gw), float(cg_tol), int(cg_max_iters), _ptr(status),
                                                 C.c_void_p(stream)))
+
+    def _check_adjoint_args(self, x, v, f, gx_next, gv_next, gx, gv, gf, gw, iters, status):
+        import torch
+        shp = (3, self.n_total)
+        for name, t in (("x", x), ("v", v), ("f", f), ("gx", gx), ("gv", gv), ("gf", gf)):
+            _check_dev(name, t, torch.float64, shp)
+        _check_dev("gx_next", gx_next, torch.float64, shp, optional=True)
+        _check_dev("gv_next", gv_next, torch.float64, shp, optional=True)
+        _check_dev("gw", gw, torch.float64, (self.ncells, 4), at_least=True)
+        _check_dev("iters", iters, torch.int32, (self.ncells,), optional=True, at_least=True)
+        _check_dev("status", status, torch.int32, (self.ncells,), optional=True, at_least=True)
 
     def set_launch(self, type_index: int, warps_per_block: int, blocks_per_sm: int, solve_in_shared: bool,
                    solve_per_coord: bool = False):
@@ -353,6 +458,10 @@ class Batch:
     def contacts(self, count=None, vertex=None, plane=None, stream=None) -> None:
         """npfem_batch_contacts: the last step's contacts into device tensors
         (int32 [N], int32 [N, 2], float64 [N, 2, 4]; each may be None)."""
+        import torch
+        _check_dev("count", count, torch.int32, (self.n_total,), optional=True)
+        _check_dev("vertex", vertex, torch.int32, (self.n_total, 2), optional=True)
+        _check_dev("plane", plane, torch.float64, (self.n_total, 2, 4), optional=True)
         if stream is None:
             import torch
             stream = torch.cuda.current_stream().cuda_stream
@@ -370,6 +479,13 @@ class Batch:
                   residual=None, status=None, stream: int = 0, tol: float = 0.0, iters_done=None):
         """npfem_step_host on host arrays (copies in, steps, copies out; synchronous);
         iters_done: a host int32 array [ncells] or None."""
+        sd = np.float64 if self.precision == FP64 else np.float32
+        for name, a in (("x", x), ("v", v), ("f", f)):
+            _check_host(name, a, sd, (3, self.n_total))
+        _check_host("iters", iters, np.int32, (self.ncells,), optional=True)
+        _check_host("residual", residual, np.float64, (self.ncells,), optional=True)
+        _check_host("status", status, np.int32, (self.ncells,), optional=True)
+        _check_host("iters_done", iters_done, np.int32, (self.ncells,), optional=True)
         opts = _Opts(int(iters_default), 0, None, int(np.max(iters)) if iters is not None and len(iters) else 0,
                      float(tol), _ptr(iters_done))
         _check(_lib.npfem_step_host(self.handle, _ptr(x), _ptr(v), _ptr(f), _ptr(iters), C.byref(opts),

@@ -102,9 +102,10 @@ SplitShape = Tuple[int, int, int, int, int, int, int]
 
 # Largest resident warps per SM of the solve kernel for 1..4 cells per warp (register
 # use of the four instantiations on sm_103a: 64, 80, 96, 126 registers per thread), and
-# of the CTA-cooperative solve kernel (96 registers).
+# largest resident CTAs per SM of the CTA-cooperative solve kernel per CTA width (2, 4, 6,
+# 8 warps compiled for 72, 95, 96, 128 registers per thread).
 SOLVE_MAX_WARPS = {1: 32, 2: 24, 3: 20, 4: 16}
-CTA_MAX_WARPS = 20
+CTA_MAX_CTAS = {2: 13, 4: 5, 6: 3, 8: 2}
 
 
 def split_solve_candidates(n_verts: int, smem_per_sm: int = 228 * 1024, smem_per_cta: int = 227 * 1024):
@@ -118,7 +119,7 @@ def split_solve_candidates(n_verts: int, smem_per_sm: int = 228 * 1024, smem_per
     zb = 24 * (n_verts + 1)
     if zb <= smem_per_cta:
         for wpb in (2, 4, 6, 8):
-            top = min(16, smem_per_sm // (zb + 1024), CTA_MAX_WARPS // wpb)
+            top = min(16, smem_per_sm // (zb + 1024), CTA_MAX_CTAS[wpb])
             # every CTA count from half the resident maximum up: the count sets how the
             # cells divide into waves, which matters as much as the occupancy
             for bps in range(max(1, top // 2), top + 1):

@@ -147,3 +147,23 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert got[(cname, "sizeof")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_binding_checks_tensors_before_passing_pointers():
+    """The Python binding refuses host tensors, wrong dtypes and wrong shapes before any
+    pointer reaches the library (checked here on CPU tensors, without a GPU)."""
+    torch = pytest.importorskip("torch")
+    from paper_2011_04332_b300 import native
+    x = torch.zeros(3, 24, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA"):
+        native._check_step_args(2, 24, native.FP64, x, x, x, None, None, None, None, None)
+    with pytest.raises(ValueError, match="required"):
+        native._check_step_args(2, 24, native.FP64, None, x, x, None, None, None, None, None)
+    a = np.zeros((3, 24), np.float32)
+    with pytest.raises(ValueError, match="dtype"):
+        native._check_host("x", a, np.float64, (3, 24))
+    with pytest.raises(ValueError, match="shape"):
+        native._check_host("x", a, np.float32, (3, 25))
+    with pytest.raises(ValueError, match="contiguous"):
+        native._check_host("x", np.zeros((24, 3), np.float32).T, np.float32, (3, 24))
+    native._check_host("status", np.zeros(5, np.int32), np.int32, (5,))

@@ -20,7 +20,7 @@ def test_split_solve_candidates_fit(n):
             zb = 24 * (n + 1)
             assert cells == 1 and per_coord == 0 and wpb in (2, 4, 6, 8)
             assert zb <= SMEM_CTA and bps * (zb + 1024) <= SMEM_SM
-            assert warps <= T.CTA_MAX_WARPS
+            assert bps <= T.CTA_MAX_CTAS[wpb]
         elif place == 1:                       # per-warp vectors in shared memory
             zb = (8 if per_coord else 24) * (n + 1)
             cta = wpb * cells * zb

@@ -32,9 +32,12 @@ def _rel_err(b, x, xref, radius_from=None):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_noalloc_matches_batched_step_twice(prec):
+@pytest.mark.parametrize("subdiv,ncells", [(3, 37), (4, 9)])
+def test_noalloc_matches_batched_step_twice(prec, subdiv, ncells):
+    """642-vertex cells keep their solve vectors in shared memory; 2562-vertex cells do
+    not fit four of them there and keep them in the static workspace."""
     from paper_2011_04332_b300 import native
-    b = I.homogeneous_rbc_batch(ncells=37, seed=77, velocity_sigma=0.02)
+    b = I.homogeneous_rbc_batch(ncells=ncells, seed=77, velocity_sigma=0.02, subdiv=subdiv)
     n = b.types[0].mesh.n
     assert np.array_equal(b.offsets, np.arange(b.ncells + 1) * n)   # back-to-back layout
     p = native.FP64 if prec == "fp64" else native.FP32FORM
@@ -67,10 +70,26 @@ def test_noalloc_matches_batched_step_twice(prec):
 
 
 def test_noalloc_rejects_too_many_cells():
+    """The library refuses a call beyond its static cell limit before any launch; the
+    state tensors are sized for the call, so nothing could go out of bounds even if it
+    did not."""
     from paper_2011_04332_b300 import native
     m = I.icosahedron()
     ct = native.CellType(m.verts, m.tris, I.RBC_MATERIAL.as_tuple(), 0.1)
-    dummy = torch.zeros(3, 12, dtype=torch.float64, device="cuda:0")
+    ncells = 65537
+    x = torch.zeros(3, ncells * m.n, dtype=torch.float64, device="cuda:0")
     with pytest.raises(native.NpfemError) as ei:
-        native.step_noalloc(ct, native.FP64, 65537, dummy, dummy.clone(), dummy.clone())
+        native.step_noalloc(ct, native.FP64, ncells, x, x.clone(), x.clone())
     assert ei.value.code == -6 and "65536" in str(ei.value)
+
+
+def test_noalloc_wrapper_rejects_mismatched_tensors():
+    """The binding checks sizes against ncells before passing pointers to the library."""
+    from paper_2011_04332_b300 import native
+    m = I.icosahedron()
+    ct = native.CellType(m.verts, m.tris, I.RBC_MATERIAL.as_tuple(), 0.1)
+    x = torch.zeros(3, 4 * m.n, dtype=torch.float64, device="cuda:0")
+    with pytest.raises(ValueError):
+        native.step_noalloc(ct, native.FP64, 5, x, x.clone(), x.clone())          # 4 cells of state, 5 asked
+    with pytest.raises(ValueError):
+        native.step_noalloc(ct, native.FP32FORM, 4, x, x.clone(), x.clone())     # FP64 tensors, FP32 call
