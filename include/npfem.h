@@ -288,7 +288,9 @@ npfem_status npfem_batch_get_launch(const npfem_batch* batch, int32_t type_index
  * 1: shared memory, one per warp, 2: shared memory, one per CTA whose warps sweep the
  * cell together through a level packing of the factor), per-coordinate solve, cells per warp (1..4)
  * of the solve kernel: a warp sweeps that many cells of the type together through the
- * shared factor};
+ * shared factor (placement 2: cells per CTA, 1, or 2 with 2 or 4 warps per CTA: each
+ * factor entry updates both cells' vectors, with each cell's updates in the one-cell
+ * order)};
  * NPFEM_ERR_INVALID_ARG outside those ranges, NPFEM_ERR_UNSUPPORTED when a CTA's solve
  * vectors exceed shared memory.  npfem_batch_get_split_launch returns those seven values
  * plus the mode in shape[7] (host array of 8). */
@@ -302,6 +304,27 @@ npfem_status npfem_batch_set_mode(npfem_batch* batch, int32_t mode);
  * NPFEM_ERR_INVALID_ARG for groups outside 1..4 or a type without cells in the batch. */
 npfem_status npfem_batch_set_groups(npfem_batch* batch, int32_t type_index, int32_t groups);
 npfem_status npfem_batch_get_groups(const npfem_batch* batch, int32_t type_index, int32_t* groups);
+
+/* Split mode: iteration kernels of type type_index (the prediction with the first
+ * objective evaluation, and the rest of each iteration around the FP64 solve).
+ * warps >= 1 (default in the FP32 form: 2 for up to 256 vertices, 4 up to 1024, else 8; in the FP64
+ * form 0, whose objective is bound by the FP64 pipe rather than by gathers): one CTA of that
+ * many warps per cell, the cell's start positions, trial displacement and gradient in
+ * shared memory during each objective evaluation (9n values: 23 KB for a 642-vertex FP32
+ * cell), triangles and hinges visited by colour classes whose elements share no vertex
+ * (Implementation and architecture section: the per-element local step with the gradient
+ * assembled per vertex), CTA-wide sums.  warps = 0: one warp per cell with per-element
+ * records in the workspace and a per-vertex gather.  The width sets the order of a cell's
+ * sums: results of different widths agree to rounding; for a given width they do not
+ * depend on any other launch setting.  NPFEM_ERR_INVALID_ARG for warps outside 0..16 or a
+ * type without cells in the batch; NPFEM_ERR_UNSUPPORTED when the shared-memory arrays
+ * exceed a CTA or the type needs more than 64 colour classes (the setting is then left as
+ * it was; a new batch falls back to warps = 0 in those cases).  npfem_batch_get_iter_width
+ * returns the width and, when ctas_per_sm is not null, the CTAs per SM that are resident
+ * at that width (0 with warps = 0). */
+npfem_status npfem_batch_set_iter_width(npfem_batch* batch, int32_t type_index, int32_t warps);
+npfem_status npfem_batch_get_iter_width(const npfem_batch* batch, int32_t type_index, int32_t* warps,
+                                        int32_t* ctas_per_sm);
 npfem_status npfem_batch_set_split_launch(npfem_batch* batch, int32_t type_index, const int32_t* shape);
 npfem_status npfem_batch_get_split_launch(const npfem_batch* batch, int32_t type_index, int32_t* shape);
 

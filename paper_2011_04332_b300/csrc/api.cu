@@ -14,6 +14,7 @@
 #include "step_kernel.cuh"
 #include "adjoint.cuh"
 #include "split_kernels.cuh"
+#include "iter_cta.cuh"
 #include "contact_kernels.cuh"
 
 using namespace npfem;
@@ -57,6 +58,9 @@ struct TypeLaunch {
   char* cell_scratch;        // owned: cell_slot bytes per cell (first split step)
   size_t cell_slot;
   int it_wpb, it_bps, sv_wpb, sv_bps, sv_smem, sv_percoord, sv_cells;
+  // CTA iteration kernels (one cell per CTA, X, U and G in shared memory): warps per cell
+  // (0: the one-warp-per-cell kernels) and the CTAs per SM that are resident at that width
+  int itc_w = 0, itc_bps = 0;
   int* active = nullptr;  // split mode: [2][ncells] lists of iterating cells (inside cell_scratch)
   int groups = 1;         // split mode: cells split into this many groups with phase-offset chains
   std::vector<int32_t> host_list;  // the type's cells (batch indices, increasing)
@@ -282,18 +286,20 @@ static cudaError_t set_solve_smem_attr(int bytes) {
   cudaError_t e = cudaSuccess;
   for (int c = 1; c <= 4 && e == cudaSuccess; ++c)
     for (int pl = 1; pl <= 2 && e == cudaSuccess; ++pl) e = allow_dynamic_smem(solve_kernel<S>(c, pl), bytes);
-  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[0]>, bytes);
-  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[1]>, bytes);
-  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[2]>, bytes);
-  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[3]>, bytes);
+  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[0], 1>, bytes);
+  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[1], 1>, bytes);
+  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[2], 1>, bytes);
+  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[3], 1>, bytes);
+  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[0], 2>, bytes);
+  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_solve_cta<S, kCtaWarps[1], 2>, bytes);
   return e;
 }
 
 // Dynamic shared memory of a solve-kernel CTA: per warp, `cells` solve vectors of
-// [n+1][3] doubles (or [n+1] per coordinate); placement 2 (the CTA's warps sweep one
-// cell together): one vector of [n+1][3] doubles.
+// [n+1][3] doubles (or [n+1] per coordinate); placement 2 (the CTA's warps sweep its
+// cells together): `cells` vectors of [n+1][3] doubles.
 static size_t split_solve_smem(int n, int wpb, int per_coord, int cells, int placement = 1) {
-  if (placement == 2) return sizeof(double) * 3 * ((size_t)n + 1);
+  if (placement == 2) return sizeof(double) * 3 * ((size_t)n + 1) * (size_t)cells;
   return sizeof(double) * (per_coord ? 1 : 3) * ((size_t)n + 1) * (size_t)wpb * (size_t)cells;
 }
 
@@ -321,6 +327,52 @@ static void default_split_shape(TypeLaunch& L, int n, npfem_precision prec) {
     L.sv_smem = 0;
     L.sv_wpb = 2, L.sv_bps = 8;
   }
+}
+
+// Width of the CTA iteration kernels for an n-vertex type (warps per cell), measured on
+// B300 in the FP32 form: 2 warps for platelet-sized cells, 4 for 642 vertices, 8 for 2562
+// (the mixed 10^4-cell step: 79.6 ms at 8 warps against 83.2 at 16).  The FP64 form keeps
+// the one-warp kernels (0): its objective is bound by the FP64 pipe, not by the gathers
+// the shared-memory kernels remove, and the one-warp kernels measured faster (4096-cell
+// step 34.5 against 39.5 ms).  The width sets the order of a cell's CTA-wide sums, so it
+// is fixed per type unless the caller sets it (npfem_batch_set_iter_width).
+static int default_iter_width(int n, npfem_precision prec) {
+  if (prec == NPFEM_FP64) return 0;
+  return n <= 256 ? 2 : (n <= 1024 ? 4 : 8);
+}
+
+// Uses the CTA iteration kernels with w warps per cell for the type (w = 0: the warp
+// kernels), if the type is coloured and its shared-memory arrays fit a CTA; records the
+// resident CTAs per SM at that width.  Returns false if the kernels cannot run the type
+// at that width.
+static bool set_iter_cta(npfem_batch* b, TypeLaunch& L, int w) {
+  L.itc_w = 0;
+  L.itc_bps = 0;
+  if (w == 0) return true;
+  const HostType& H = b->types[L.type_index]->host;
+  if (H.tri_cptr.empty() || H.hinge_cptr.empty()) return false;
+  const bool f64 = b->prec == NPFEM_FP64;
+  const size_t smem = f64 ? iter_cta_smem_bytes<double>(H.n) : iter_cta_smem_bytes<float>(H.n);
+  if (smem + sizeof(CtaShared) + 1024 > (size_t)b->smem_optin) return false;  // static shared memory, rounded up
+  int nb = 0;
+  cudaError_t e = f64 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, npfem_k_iter_cta<double, false>, 32 * w, smem)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, npfem_k_iter_cta<float, false>, 32 * w, smem);
+  if (e != cudaSuccess || nb < 1) {
+    cudaGetLastError();
+    return false;
+  }
+  L.itc_w = w;
+  L.itc_bps = nb;
+  return true;
+}
+
+template <typename S>
+static cudaError_t set_iter_cta_smem_attr(int bytes) {
+  cudaError_t e = allow_dynamic_smem(npfem_k_begin_cta<S, false>, bytes);
+  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_begin_cta<S, true>, bytes);
+  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_iter_cta<S, false>, bytes);
+  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_k_iter_cta<S, true>, bytes);
+  return e;
 }
 
 static npfem_status ensure_cell_scratch(npfem_batch* b, TypeLaunch& L) {
@@ -359,12 +411,18 @@ static npfem_status launch_split(npfem_batch* b, const npfem_cell_type* t, const
   int* act_count = G.counter + kActiveCountOff;
   int* act0 = L.active + G.g0;                // list of even iterations (item indices of the group)
   int* act1 = L.active + L.ncells + G.g0;     // list of odd iterations
+  const size_t itc_smem = iter_cta_smem_bytes<S>(view.n);
+  const int itc_grid = std::max(1, std::min<int>(b->sms * L.itc_bps, G.gn));
   if (kind == 0) {
     P.queue_counter = G.counter;
     P.act_out = act0;
     P.act_count_out = act_count;
     int grid = std::max(1, std::min<int>(b->sms * L.it_bps, (G.gn + L.it_wpb - 1) / L.it_wpb));
-    if (view.limited)
+    if (L.itc_w > 0 && view.limited)
+      npfem_k_begin_cta<S, true><<<itc_grid, 32 * L.itc_w, itc_smem, st>>>(view, P, max_iters, x, v, f);
+    else if (L.itc_w > 0)
+      npfem_k_begin_cta<S, false><<<itc_grid, 32 * L.itc_w, itc_smem, st>>>(view, P, max_iters, x, v, f);
+    else if (view.limited)
       npfem_k_begin<S, true><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, max_iters, x, v, f);
     else
       npfem_k_begin<S, false><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, max_iters, x, v, f);
@@ -376,14 +434,21 @@ static npfem_status launch_split(npfem_batch* b, const npfem_cell_type* t, const
     P.solve_per_coord = L.sv_percoord;
     P.solve_cells = std::max(1, std::min(4, L.sv_cells));
     const HostType& H = t->host;
-    if (L.sv_smem == 2) {  // CTA-cooperative: one cell per CTA of sv_wpb warps
+    if (L.sv_smem == 2 && L.sv_cells == 2) {  // CTA-cooperative, two cells per CTA of sv_wpb warps
+      const size_t smem = split_solve_smem(H.n, L.sv_wpb, 0, 2, 2);
+      const int grid = std::max(1, std::min<int>(b->sms * L.sv_bps, (G.gn + 1) / 2));
+      if (L.sv_wpb == kCtaWarps[0])
+        npfem_k_solve_cta<S, kCtaWarps[0], 2><<<grid, 32 * kCtaWarps[0], smem, st>>>(view, P);
+      else
+        npfem_k_solve_cta<S, kCtaWarps[1], 2><<<grid, 32 * kCtaWarps[1], smem, st>>>(view, P);
+    } else if (L.sv_smem == 2) {  // CTA-cooperative: one cell per CTA of sv_wpb warps
       const size_t smem = split_solve_smem(H.n, L.sv_wpb, 0, 1, 2);
       const int grid = std::max(1, std::min<int>(b->sms * L.sv_bps, G.gn));
       switch (L.sv_wpb) {
-        case kCtaWarps[0]: npfem_k_solve_cta<S, kCtaWarps[0]><<<grid, 32 * kCtaWarps[0], smem, st>>>(view, P); break;
-        case kCtaWarps[1]: npfem_k_solve_cta<S, kCtaWarps[1]><<<grid, 32 * kCtaWarps[1], smem, st>>>(view, P); break;
-        case kCtaWarps[2]: npfem_k_solve_cta<S, kCtaWarps[2]><<<grid, 32 * kCtaWarps[2], smem, st>>>(view, P); break;
-        default: npfem_k_solve_cta<S, kCtaWarps[3]><<<grid, 32 * kCtaWarps[3], smem, st>>>(view, P); break;
+        case kCtaWarps[0]: npfem_k_solve_cta<S, kCtaWarps[0], 1><<<grid, 32 * kCtaWarps[0], smem, st>>>(view, P); break;
+        case kCtaWarps[1]: npfem_k_solve_cta<S, kCtaWarps[1], 1><<<grid, 32 * kCtaWarps[1], smem, st>>>(view, P); break;
+        case kCtaWarps[2]: npfem_k_solve_cta<S, kCtaWarps[2], 1><<<grid, 32 * kCtaWarps[2], smem, st>>>(view, P); break;
+        default: npfem_k_solve_cta<S, kCtaWarps[3], 1><<<grid, 32 * kCtaWarps[3], smem, st>>>(view, P); break;
       }
     } else {
       size_t smem = L.sv_smem ? split_solve_smem(H.n, L.sv_wpb, L.sv_percoord, P.solve_cells) : 0;
@@ -397,7 +462,11 @@ static npfem_status launch_split(npfem_batch* b, const npfem_cell_type* t, const
     P.act_out = (it & 1) ? act0 : act1;
     P.act_count_out = act_count + it + 1;
     int grid = std::max(1, std::min<int>(b->sms * L.it_bps, (G.gn + L.it_wpb - 1) / L.it_wpb));
-    if (view.limited)
+    if (L.itc_w > 0 && view.limited)
+      npfem_k_iter_cta<S, true><<<itc_grid, 32 * L.itc_w, itc_smem, st>>>(view, P, x, v);
+    else if (L.itc_w > 0)
+      npfem_k_iter_cta<S, false><<<itc_grid, 32 * L.itc_w, itc_smem, st>>>(view, P, x, v);
+    else if (view.limited)
       npfem_k_iter<S, true><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, x, v);
     else
       npfem_k_iter<S, false><<<grid, 32 * L.it_wpb, 0, st>>>(view, P, x, v);
@@ -685,7 +754,7 @@ npfem_status npfem_create_cell_type(const npfem_mesh* mesh, const npfem_material
   t->host.s_max = s_hi;
   cudaError_t e = cudaGetDevice(&t->device);
   const HostType& H = t->host;
-  const int32_t *tris, *tri4, *hinges, *inc_ptr, *inc_code, *perm, *fcol, *bcol;
+  const int32_t *tris, *tri4, *hinges, *inc_ptr, *inc_code, *perm, *fcol, *bcol, *tcp, *hcp;
   std::vector<int32_t> tri4_h(4 * (size_t)H.T, 0);
   for (int q = 0; q < H.T; ++q)
     for (int k = 0; k < 3; ++k) tri4_h[4 * q + k] = H.tris[3 * q + k];
@@ -706,6 +775,8 @@ npfem_status npfem_create_cell_type(const npfem_mesh* mesh, const npfem_material
   UP(H.bwd_meta, bcol);
   UP(H.bwd_rc, brow);
   UP(H.bwd_val, bval);
+  UP(H.tri_cptr, tcp);
+  UP(H.hinge_cptr, hcp);
 #undef UP
   const int32_t *cfm[kCtaPacks], *cbm[kCtaPacks];
   const uint32_t *cfr[kCtaPacks], *cbr[kCtaPacks];
@@ -726,6 +797,12 @@ npfem_status npfem_create_cell_type(const npfem_mesh* mesh, const npfem_material
     e = upload_precision<float>(t, &t->v32, tris, tri4, hinges, inc_ptr, inc_code, perm, dinv, fcol, frow, fval, bcol,
                                 brow, bval);
   if (e == cudaSuccess) {
+    const int ntc = H.tri_cptr.empty() ? 0 : (int)H.tri_cptr.size() - 1;
+    const int nhc = H.hinge_cptr.empty() ? 0 : (int)H.hinge_cptr.size() - 1;
+    t->v64.ntc = t->v32.ntc = ntc;
+    t->v64.nhc = t->v32.nhc = nhc;
+    t->v64.tri_cptr = t->v32.tri_cptr = tcp;
+    t->v64.hinge_cptr = t->v32.hinge_cptr = hcp;
     for (int i = 0; i < kCtaPacks; ++i) {
       const HostType::LevelPack& P = H.cta[i];
       const int nf = (int)P.fwd_meta.size() / P.W, nb = (int)P.bwd_meta.size() / P.W;
@@ -843,6 +920,8 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
     e = set_solve_smem_attr<double>(smem_optin);
   if (e == cudaSuccess)
     e = set_solve_smem_attr<float>(smem_optin);
+  if (e == cudaSuccess) e = set_iter_cta_smem_attr<double>(smem_optin);
+  if (e == cudaSuccess) e = set_iter_cta_smem_attr<float>(smem_optin);
   if (e != cudaSuccess) return cleanup(NPFEM_ERR_CUDA, std::string("batch_create: ") + cudaGetErrorString(e));
   const size_t ssize = prec == NPFEM_FP64 ? sizeof(double) : sizeof(float);
   for (int ti = 0; ti < ntypes; ++ti) {
@@ -865,6 +944,7 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
     const size_t zbytes = sizeof(double) * 3 * ((size_t)H.n + 1);
     const int zs = zbytes * 4 <= 72 * 1024 ? 1 : 0;
     default_split_shape(L, H.n, prec);
+    set_iter_cta(b, L, default_iter_width(H.n, prec));  // else the warp kernels
     npfem_status rc = configure_launch(b, L, 4, 3, zs, 0);
     if (rc != NPFEM_OK) {
       for (TypeLaunch& P : b->launches) {
@@ -1293,10 +1373,11 @@ npfem_status npfem_batch_set_split_launch(npfem_batch* b, int32_t type_index, co
         return fail(NPFEM_ERR_INVALID_ARG,
                     "batch_set_split_launch: warps/CTA in 1..4 (solve placement 2: 2, 4, 6 or 8), CTAs/SM in 1..16, "
                     "cells per solve warp in 1..4, placement in 0..2");
-      if (shape[4] == 2 && (!cta_width || shape[5] != 0 || shape[6] != 1))
+      if (shape[4] == 2 && (!cta_width || shape[5] != 0 || shape[6] < 1 || shape[6] > 2 ||
+                            (shape[6] == 2 && shape[2] != kCtaWarps[0] && shape[2] != kCtaWarps[1])))
         return fail(NPFEM_ERR_INVALID_ARG,
-                    "batch_set_split_launch: a CTA-cooperative solve takes 2, 4, 6 or 8 warps per CTA, one cell, "
-                    "interleaved coordinates");
+                    "batch_set_split_launch: a CTA-cooperative solve takes 2, 4, 6 or 8 warps per CTA and one cell "
+                    "(or 2 or 4 warps and two cells), interleaved coordinates");
       size_t smem = shape[4] ? split_solve_smem(H.n, shape[2], shape[5], shape[6], shape[4]) : 0;
       if (shape[4] == 2) smem += 16;  // the CTA kernel's static shared memory (rounded up)
       if (smem > (size_t)b->smem_optin)
@@ -1445,6 +1526,36 @@ npfem_status npfem_batch_get_groups(const npfem_batch* b, int32_t type_index, in
       return NPFEM_OK;
     }
   return fail(NPFEM_ERR_INVALID_ARG, "batch_get_groups: no cells of that type in the batch");
+}
+
+npfem_status npfem_batch_set_iter_width(npfem_batch* b, int32_t type_index, int32_t warps) {
+  if (!b || warps < 0 || warps > kIterCtaMaxWarps)
+    return fail(NPFEM_ERR_INVALID_ARG, "batch_set_iter_width: warps in 0..16");
+  for (TypeLaunch& L : b->launches)
+    if (L.type_index == type_index) {
+      const int keep_w = L.itc_w, keep_b = L.itc_bps;
+      if (!set_iter_cta(b, L, warps)) {
+        L.itc_w = keep_w;
+        L.itc_bps = keep_b;
+        return fail(NPFEM_ERR_UNSUPPORTED,
+                    "batch_set_iter_width: the type's shared-memory arrays exceed a CTA, or its elements are not "
+                    "coloured");
+      }
+      return NPFEM_OK;
+    }
+  return fail(NPFEM_ERR_INVALID_ARG, "batch_set_iter_width: no cells of that type in the batch");
+}
+
+npfem_status npfem_batch_get_iter_width(const npfem_batch* b, int32_t type_index, int32_t* warps,
+                                        int32_t* ctas_per_sm) {
+  if (!b || !warps) return fail(NPFEM_ERR_INVALID_ARG, "batch_get_iter_width: null argument");
+  for (const TypeLaunch& L : b->launches)
+    if (L.type_index == type_index) {
+      *warps = L.itc_w;
+      if (ctas_per_sm) *ctas_per_sm = L.itc_bps;
+      return NPFEM_OK;
+    }
+  return fail(NPFEM_ERR_INVALID_ARG, "batch_get_iter_width: no cells of that type in the batch");
 }
 
 npfem_status npfem_step_host(npfem_batch* b, void* x, void* v, const void* f_ext, const int32_t* iters,

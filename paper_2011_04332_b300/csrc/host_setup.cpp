@@ -35,6 +35,46 @@ inline double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 inline double norm(V3 a) { return std::sqrt(dot(a, a)); }
 inline double cotangent(V3 a, V3 b) { return dot(a, b) / norm(cross(a, b)); }
 
+// ---------------------------------------------------------------- element colours
+// Colour elements of k vertices each so that no two elements of a colour share a vertex,
+// and store them colour by colour (stable within a colour): the CTA iteration kernels add
+// one colour's gradient contributions to the shared-memory gradient at a time, without
+// conflicts and in a fixed order.  Greedy: each element takes, among the colours none of
+// its vertices has yet, the one holding the fewest elements (a new colour only when every
+// existing one is taken), which keeps the classes of a near-regular mesh equally full.
+// Returns false (and leaves the elements as they were) if more than kMaxColours colours
+// would be needed.
+bool colour_elements(int n, int k, std::vector<int32_t>* elems, std::vector<int32_t>* cptr) {
+  const int m = (int)elems->size() / k;
+  std::vector<uint64_t> used(n, 0);
+  std::vector<int> colour(m);
+  std::vector<int> count;
+  for (int e = 0; e < m; ++e) {
+    uint64_t taken = 0;
+    for (int j = 0; j < k; ++j) taken |= used[(*elems)[(size_t)k * e + j]];
+    int best = -1;
+    for (int c = 0; c < (int)count.size(); ++c)
+      if (!((taken >> c) & 1u) && (best < 0 || count[c] < count[best])) best = c;
+    if (best < 0) {
+      if ((int)count.size() == kMaxColours) return false;
+      best = (int)count.size();
+      count.push_back(0);
+    }
+    colour[e] = best;
+    ++count[best];
+    for (int j = 0; j < k; ++j) used[(*elems)[(size_t)k * e + j]] |= uint64_t(1) << best;
+  }
+  cptr->assign(count.size() + 1, 0);
+  for (size_t c = 0; c < count.size(); ++c) (*cptr)[c + 1] = (*cptr)[c] + count[c];
+  std::vector<int32_t> next(cptr->begin(), cptr->end() - 1), out(elems->size());
+  for (int e = 0; e < m; ++e) {
+    const int p = next[colour[e]]++;
+    for (int j = 0; j < k; ++j) out[(size_t)k * p + j] = (*elems)[(size_t)k * e + j];
+  }
+  elems->swap(out);
+  return true;
+}
+
 // ---------------------------------------------------------------- orderings
 using Graph = std::vector<std::vector<int>>;
 
@@ -396,6 +436,13 @@ int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double
     *err = "create_cell_type: mesh is not a closed manifold";
     return NPFEM_ERR_BAD_MESH;
   }
+  // ---- elements in colour order (each triangle keeps its vertex order, hence its
+  // orientation); every per-element table below follows this order
+  if (!colour_elements(n, 3, &H.tris, &H.tri_cptr) || !colour_elements(n, 4, &H.hinges, &H.hinge_cptr)) {
+    H.tri_cptr.clear();
+    H.hinge_cptr.clear();
+  }
+  tris = H.tris.data();
 
   // ---- per-triangle rest frame: Dm = [[|e1|, e2.u], [0, e2.w]], F = [e1 e2] Dm^-1
   H.Dinv.resize(3 * T);

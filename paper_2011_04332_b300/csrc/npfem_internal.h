@@ -16,6 +16,7 @@ constexpr double kDegenerateNorm = 1e-30;
 constexpr int kChunk = 32;               // entries per triangular-solve chunk (one per lane)
 constexpr int kCtaPacks = 4;             // level packings for CTA-cooperative sweeps
 constexpr int kCtaWarps[kCtaPacks] = {2, 4, 6, 8};
+constexpr int kMaxColours = 64;          // colour classes of triangles or of hinges
 
 // Host-side result of the per-type setup (all FP64; the device upload makes FP32
 // copies of the element constants for the FP32-form kernels).
@@ -26,6 +27,10 @@ struct HostType {
   std::vector<double> w_tri;     // [T]
   std::vector<double> area;      // [T] rest areas
   std::vector<int32_t> hinges;   // [E][4] (i, j, kA, kB)
+  // Elements are stored colour by colour: no two triangles (hinges) of one colour share a
+  // vertex; colour c holds [cptr[c], cptr[c+1]).  Empty when more than kMaxColours
+  // colours would be needed (the CTA iteration kernels are then not used for the type).
+  std::vector<int32_t> tri_cptr, hinge_cptr;
   std::vector<double> c_hinge;   // [E][4]
   std::vector<double> K0;        // [E][4] (K0x, K0y, K0z, |K0|)
   std::vector<double> w_hinge;   // [E]
@@ -120,6 +125,9 @@ struct DevTypeView {
   double damp_m, damp_l;    // Rayleigh damping over dt: c_alpha/dt (mass part), c_beta/dt (elastic part)
   double s_min, s_max;      // strain limits; limited = 0 for the rotations [1, 1]
   int limited;
+  int ntc, nhc;             // colour classes of the triangles and hinges (0: not coloured)
+  const int32_t* tri_cptr;  // [ntc+1] first triangle of each colour
+  const int32_t* hinge_cptr;  // [nhc+1] first hinge of each colour
 };
 
 }  // namespace npfem

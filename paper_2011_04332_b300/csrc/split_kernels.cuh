@@ -68,31 +68,32 @@ __device__ __forceinline__ CellWs<S> split_ws(char* base, const DevTypeView<S>& 
   return carve<S>(base + kStateBytes, ty.n, ty.T, ty.E, nullptr);
 }
 
-// Fused streaming passes of the two-loop recursion.  Each lane takes the elements lane,
-// lane + 32, ... in increasing order (the order of a separate pass), four at a time with
-// every load of the four issued before the first store, so the loads of a pass stay in
-// flight together although the pass writes one of the vectors it reads.
+// Fused streaming passes of the two-loop recursion.  Each lane (thread) takes the
+// elements lane, lane + stride, ... in increasing order (the order of a separate pass;
+// stride 32 for a warp, the CTA size for a CTA), four at a time with every load of the
+// four issued before the first store, so the loads of a pass stay in flight together
+// although the pass writes one of the vectors it reads.
 template <typename S>
-__device__ __forceinline__ S update_dot(S* q, S c, const S* u, const S* t, int len, int lane) {
+__device__ __forceinline__ S update_dot(S* q, S c, const S* u, const S* t, int len, int lane, int stride = 32) {
   // q += c u; returns this lane's partial sum of t . q over the updated values
   S acc = 0;
   int e = lane;
-  for (; e + 96 < len; e += 128) {
+  for (; e + 3 * stride < len; e += 4 * stride) {
     S qv[4], uv[4], tv[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      qv[j] = q[e + 32 * j];
-      uv[j] = u[e + 32 * j];
-      tv[j] = t[e + 32 * j];
+      qv[j] = q[e + stride * j];
+      uv[j] = u[e + stride * j];
+      tv[j] = t[e + stride * j];
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const S qn = qv[j] + c * uv[j];
-      q[e + 32 * j] = qn;
+      q[e + stride * j] = qn;
       acc += tv[j] * qn;
     }
   }
-  for (; e < len; e += 32) {
+  for (; e < len; e += stride) {
     const S qn = q[e] + c * u[e];
     q[e] = qn;
     acc += t[e] * qn;
@@ -101,24 +102,24 @@ __device__ __forceinline__ S update_dot(S* q, S c, const S* u, const S* t, int l
 }
 
 template <typename S>
-__device__ __forceinline__ S copy_dot(S* q, const S* g, const S* t, int len, int lane) {
+__device__ __forceinline__ S copy_dot(S* q, const S* g, const S* t, int len, int lane, int stride = 32) {
   // q = g; returns this lane's partial sum of t . g
   S acc = 0;
   int e = lane;
-  for (; e + 96 < len; e += 128) {
+  for (; e + 3 * stride < len; e += 4 * stride) {
     S gv[4], tv[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      gv[j] = g[e + 32 * j];
-      tv[j] = t[e + 32 * j];
+      gv[j] = g[e + stride * j];
+      tv[j] = t[e + stride * j];
     }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      q[e + 32 * j] = gv[j];
+      q[e + stride * j] = gv[j];
       acc += tv[j] * gv[j];
     }
   }
-  for (; e < len; e += 32) {
+  for (; e < len; e += stride) {
     const S gq = g[e];
     q[e] = gq;
     acc += t[e] * gq;
@@ -371,15 +372,18 @@ __global__ void __launch_bounds__(128) npfem_k_solve(DevTypeView<S> ty, StepPara
 }
 
 // One sweep of a CTA of W warps over a level packing (Eqs. (7)-(8), as in chunk_sweep_n
-// but cooperative): warp w applies sub-chunk w of every level to the shared vector
-// zs ([n+1][3] doubles in shared memory), with a barrier of the CTA before every level
-// that touches a row written since the last barrier; the levels in between commute.
+// but cooperative): warp w applies sub-chunk w of every level to the shared vectors of
+// the CTA's kCells cells ([n+1][3] doubles each, zstride bytes apart, the first at zs),
+// with a barrier of the CTA before every level that touches a row written since the last
+// barrier; the levels in between commute.  Each factor entry loaded updates every cell,
+// and each cell sees its updates in the order of the one-cell sweep.
 // Levels of the factor stream a warp of the CTA-cooperative sweep keeps in flight.
 constexpr int kCtaPrefetch = 6;
 
-template <int W>
+template <int W, int kCells>
 __device__ __forceinline__ void cta_sweep(int nlev, const int32_t* __restrict__ meta, const uint32_t* __restrict__ rc,
-                                          const double* __restrict__ val, uint32_t zs, int n, int warp, int lane) {
+                                          const double* __restrict__ val, uint32_t zs, uint32_t zstride, int n,
+                                          int warp, int lane) {
   int mb[kCtaPrefetch];
   uint32_t eb[kCtaPrefetch];
   double vb[kCtaPrefetch];
@@ -414,13 +418,25 @@ __device__ __forceinline__ void cta_sweep(int nlev, const int32_t* __restrict__ 
         if (m & 1) __syncthreads();
         if (!(m & 2)) {
           const int r = (int)(e & 0xffffu), j = (int)(e >> 16);
-          const uint32_t aj = zs + 24u * (uint32_t)j, ar = zs + 24u * (uint32_t)r;
-          const double x0 = lds_f64(aj), x1 = lds_f64(aj + 8), x2 = lds_f64(aj + 16);
-          const double z0 = fma(-l, x0, lds_f64(ar)), z1 = fma(-l, x1, lds_f64(ar + 8)),
-                       z2 = fma(-l, x2, lds_f64(ar + 16));
-          sts_f64(ar, z0);
-          sts_f64(ar + 8, z1);
-          sts_f64(ar + 16, z2);
+          double xj[kCells][3], zr[kCells][3];
+#pragma unroll
+          for (int c = 0; c < kCells; ++c) {
+            const uint32_t aj = zs + c * zstride + 24u * (uint32_t)j;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) xj[c][d] = lds_f64(aj + 8 * d);
+          }
+#pragma unroll
+          for (int c = 0; c < kCells; ++c) {
+            const uint32_t ar = zs + c * zstride + 24u * (uint32_t)r;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) zr[c][d] = fma(-l, xj[c][d], lds_f64(ar + 8 * d));
+          }
+#pragma unroll
+          for (int c = 0; c < kCells; ++c) {
+            const uint32_t ar = zs + c * zstride + 24u * (uint32_t)r;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) sts_f64(ar + 8 * d, zr[c][d]);
+          }
         }
       }
     }
@@ -428,11 +444,6 @@ __device__ __forceinline__ void cta_sweep(int nlev, const int32_t* __restrict__ 
   __syncthreads();
 }
 
-// Q <- A^-1 Q for every cell still iterating (cells in batch order, ended ones
-// skipped), one cell per CTA of W warps at a time:
-// for cells whose FP64 solve vector ([n+1][3], 24(n+1) bytes) is too large to keep
-// one per warp in shared memory.  The CTA's warps share the vector and sweep the
-// W-warp level packing of the factor together.
 // Index of the level packing for a CTA of W warps.
 template <int W>
 struct CtaPack {
@@ -441,61 +452,105 @@ struct CtaPack {
 };
 
 // Resident CTAs per SM the CTA-cooperative solve is compiled for (a register budget of
-// 65536 / (32 W x min_blocks) per thread).  The 2-warp CTA of the 642-vertex type holds
-// a 15.4 KB vector, so shared memory admits 13 per SM, and 72 registers let registers
-// admit as many (at 96 registers only 10 fit); the wider CTAs keep the residency their
-// shared memory allows for the larger types (6 warps: three 61.5 KB vectors of a
-// 2562-vertex cell).
-template <int W>
+// 65536 / (32 W x min_blocks) per thread).  One cell per CTA: the 2-warp CTA of the
+// 642-vertex type holds a 15.4 KB vector, so shared memory admits 13 per SM, and 72
+// registers let registers admit as many (at 96 registers only 10 fit); the wider CTAs
+// keep the residency their shared memory allows for the larger types (6 warps: three
+// 61.5 KB vectors of a 2562-vertex cell).  Two cells per CTA: shared memory admits 7
+// 2-warp CTAs of the 642-vertex type (2 x 15.4 KB each).
+template <int W, int kCells>
 struct SolveCtaOccupancy {
-  static constexpr int min_blocks = W == 2 ? 13 : (W == 4 ? 5 : (W == 6 ? 3 : 2));
+  static constexpr int min_blocks =
+      kCells == 1 ? (W == 2 ? 13 : (W == 4 ? 5 : (W == 6 ? 3 : 2))) : (W == 2 ? 7 : (W == 4 ? 4 : 1));
 };
 
-template <typename S, int W>
-__global__ void __launch_bounds__(32 * W, SolveCtaOccupancy<W>::min_blocks) npfem_k_solve_cta(DevTypeView<S> ty,
-                                                                                            StepParams P) {
+// Q <- A^-1 Q, one CTA of W warps per kCells cells at a time, for cells whose FP64 solve
+// vectors ([n+1][3], 24(n+1) bytes each) are too large to keep one per warp in shared
+// memory: the CTA's warps share the vectors and sweep the W-warp level packing of the
+// factor together (Eqs. (7)-(8): permute, unit-lower forward sweep, D^-1, unit-upper
+// backward sweep).  One cell per CTA: cells in batch order, ended ones skipped.  Two
+// cells per CTA: pairs of the compacted list of cells still iterating (a last odd cell
+// alone); each cell's arithmetic is that of the one-cell kernel.
+template <typename S, int W, int kCells>
+__global__ void __launch_bounds__(32 * W, (SolveCtaOccupancy<W, kCells>::min_blocks)) npfem_k_solve_cta(
+    DevTypeView<S> ty, StepParams P) {
   constexpr int pk = CtaPack<W>::value;
   extern __shared__ double smem_z[];
   __shared__ int s_item;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = ty.n;
   const uint32_t zs = (uint32_t)__cvta_generic_to_shared(smem_z);
+  const size_t zlen = 3 * ((size_t)n + 1);
+  const uint32_t zstride = (uint32_t)(sizeof(double) * zlen);
+  const int total = kCells == 1 ? P.ncells_list : *P.act_count_in;
   for (;;) {
-    if (tid == 0) s_item = atomicAdd(P.queue_counter, 1);
+    if (tid == 0) s_item = atomicAdd(P.queue_counter, kCells);
     __syncthreads();
     const int item = s_item;
     __syncthreads();
-    if (item >= P.ncells_list) break;
-    char* base = P.scratch + (size_t)item * P.slot_bytes;
-    {
+    if (item >= total) break;
+    S* Q[kCells];
+    int cnt = 1;
+    if (kCells == 1) {
+      char* base = P.scratch + (size_t)item * P.slot_bytes;
       const CellState<S>* cs = reinterpret_cast<const CellState<S>*>(base);
       if (cs->k >= cs->iters) continue;  // same header for the whole CTA: a uniform branch
+      Q[0] = split_ws<S>(base, ty).Q;
+    } else {
+      cnt = total - item < kCells ? total - item : kCells;
+#pragma unroll
+      for (int c = 0; c < kCells; ++c)
+        Q[c] = split_ws<S>(P.scratch + (size_t)P.act_in[c < cnt ? item + c : item] * P.slot_bytes, ty).Q;
     }
-    CellWs<S> w = split_ws<S>(base, ty);
     NPFEM_PHASE_BEGIN(t_solve)
     for (int r = tid; r < n; r += 32 * W) {
       const int v = __ldg(&ty.perm[r]);
-      const S q0 = w.Q[3 * v], q1 = w.Q[3 * v + 1], q2 = w.Q[3 * v + 2];
-      smem_z[3 * r] = (double)q0;
-      smem_z[3 * r + 1] = (double)q1;
-      smem_z[3 * r + 2] = (double)q2;
+#pragma unroll
+      for (int c = 0; c < kCells; ++c) {
+        if (c < cnt) {
+          const S q0 = Q[c][3 * v], q1 = Q[c][3 * v + 1], q2 = Q[c][3 * v + 2];
+          smem_z[c * zlen + 3 * r] = (double)q0;
+          smem_z[c * zlen + 3 * r + 1] = (double)q1;
+          smem_z[c * zlen + 3 * r + 2] = (double)q2;
+        }
+      }
     }
-    if (tid < 3) smem_z[3 * n + tid] = 0.0;
+    if (tid < 3)
+#pragma unroll
+      for (int c = 0; c < kCells; ++c) smem_z[c * zlen + 3 * n + tid] = 0.0;
     __syncthreads();
-    cta_sweep<W>(ty.cta_nlev_fwd[pk], ty.cta_fwd_meta[pk], ty.cta_fwd_rc[pk], ty.cta_fwd_val[pk], zs, n, warp, lane);
+    if (cnt == kCells)
+      cta_sweep<W, kCells>(ty.cta_nlev_fwd[pk], ty.cta_fwd_meta[pk], ty.cta_fwd_rc[pk], ty.cta_fwd_val[pk], zs,
+                           zstride, n, warp, lane);
+    else
+      cta_sweep<W, 1>(ty.cta_nlev_fwd[pk], ty.cta_fwd_meta[pk], ty.cta_fwd_rc[pk], ty.cta_fwd_val[pk], zs, zstride,
+                      n, warp, lane);
     for (int r = tid; r < n; r += 32 * W) {
       const double d = __ldg(&ty.dinv[r]);
-      smem_z[3 * r] *= d;
-      smem_z[3 * r + 1] *= d;
-      smem_z[3 * r + 2] *= d;
+#pragma unroll
+      for (int c = 0; c < kCells; ++c) {
+        smem_z[c * zlen + 3 * r] *= d;
+        smem_z[c * zlen + 3 * r + 1] *= d;
+        smem_z[c * zlen + 3 * r + 2] *= d;
+      }
     }
     __syncthreads();
-    cta_sweep<W>(ty.cta_nlev_bwd[pk], ty.cta_bwd_meta[pk], ty.cta_bwd_rc[pk], ty.cta_bwd_val[pk], zs, n, warp, lane);
+    if (cnt == kCells)
+      cta_sweep<W, kCells>(ty.cta_nlev_bwd[pk], ty.cta_bwd_meta[pk], ty.cta_bwd_rc[pk], ty.cta_bwd_val[pk], zs,
+                           zstride, n, warp, lane);
+    else
+      cta_sweep<W, 1>(ty.cta_nlev_bwd[pk], ty.cta_bwd_meta[pk], ty.cta_bwd_rc[pk], ty.cta_bwd_val[pk], zs, zstride,
+                      n, warp, lane);
     for (int r = tid; r < n; r += 32 * W) {
       const int v = __ldg(&ty.perm[r]);
-      w.Q[3 * v] = (S)smem_z[3 * r];
-      w.Q[3 * v + 1] = (S)smem_z[3 * r + 1];
-      w.Q[3 * v + 2] = (S)smem_z[3 * r + 2];
+#pragma unroll
+      for (int c = 0; c < kCells; ++c) {
+        if (c < cnt) {
+          Q[c][3 * v] = (S)smem_z[c * zlen + 3 * r];
+          Q[c][3 * v + 1] = (S)smem_z[c * zlen + 3 * r + 1];
+          Q[c][3 * v + 2] = (S)smem_z[c * zlen + 3 * r + 2];
+        }
+      }
     }
     NPFEM_PHASE_END(t_solve, kPhSolve, P, warp == 0 ? lane : 1)
     __syncthreads();

@@ -96,6 +96,7 @@ struct Acc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double x) { s += x; }
   __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+  __device__ __forceinline__ double part() const { return s; }
   __device__ __forceinline__ double total() const { return warp_sum_d(s); }
 };
 template <>
@@ -113,7 +114,8 @@ struct Acc<float> {
     add(p);
     lo += e;
   }
-  __device__ __forceinline__ double total() const { return warp_sum_d((double)hi + (double)lo); }
+  __device__ __forceinline__ double part() const { return (double)hi + (double)lo; }  // this lane's sum
+  __device__ __forceinline__ double total() const { return warp_sum_d(part()); }
 };
 
 template <typename S>
@@ -238,7 +240,8 @@ struct EvalOut {
 // state, as in the step).  Adds to the gradient; returns the lane's share of the energy.
 template <typename S>
 __device__ __noinline__ double wall_pass(const S* xs, int64_t off, int64_t Nt, double dl, double wc,
-                                         const double* box, const S* X, const S* U, S* G, int n, int lane) {
+                                         const double* box, const S* X, const S* U, S* G, int n, int lane,
+                                         int stride = 32) {
   double lo[3], hi[3];
   for (int d = 0; d < 3; ++d) {
     const double a = (double)xs[d * Nt + off];
@@ -246,7 +249,7 @@ __device__ __noinline__ double wall_pass(const S* xs, int64_t off, int64_t Nt, d
     hi[d] = box[3 + d] - a;
   }
   double e = 0.0;
-  for (int v = lane; v < n; v += 32) {
+  for (int v = lane; v < n; v += stride) {
     const V3<S> p = ld3(X, v) + ld3(U, v);
     const double q[3] = {(double)p.x, (double)p.y, (double)p.z};
     double f[3] = {0.0, 0.0, 0.0};
@@ -316,9 +319,10 @@ __device__ __noinline__ double damping_elastic(const int32_t* tris, const S* Din
 
 // Mass part: (c_alpha/dt) m_v |U_v|^2 / 2 per vertex, its gradient added to G.
 template <typename S>
-__device__ __noinline__ double damping_mass(const S* mass, int n, S dm, const S* U, S* G, int lane) {
+__device__ __noinline__ double damping_mass(const S* mass, int n, S dm, const S* U, S* G, int lane,
+                                            int stride = 32) {
   double e = 0.0;
-  for (int v = lane; v < n; v += 32) {
+  for (int v = lane; v < n; v += stride) {
     const V3<S> u = ld3(U, v);
     const S md = dm * __ldg(&mass[v]);
     e += 0.5 * (double)md * (double)dot(u, u);
@@ -340,9 +344,9 @@ __device__ __noinline__ double damping_mass(const S* mass, int n, S dm, const S*
 // inside the strain loop, would raise the spills of the iteration kernel).
 template <typename S>
 __device__ __forceinline__ void strain_limit_pass(const DevTypeView<S>& ty, const S* X, const S* U, S* corner,
-                                               int lane) {
+                                               int lane, int stride = 32) {
   const double s_min = ty.s_min, s_max = ty.s_max;
-  for (int t = lane; t < ty.T; t += 32) {
+  for (int t = lane; t < ty.T; t += stride) {
     int i0 = __ldg(&ty.tris[3 * t]), i1 = __ldg(&ty.tris[3 * t + 1]), i2 = __ldg(&ty.tris[3 * t + 2]);
     V3<S> e1 = edge(X, U, i0, i1), e2 = edge(X, U, i0, i2);
     const S d00 = __ldg(&ty.Dinv[3 * t]), d01 = __ldg(&ty.Dinv[3 * t + 1]), d11 = __ldg(&ty.Dinv[3 * t + 2]);
@@ -367,6 +371,91 @@ __device__ __forceinline__ void strain_limit_pass(const DevTypeView<S>& ty, cons
     corner[9 * t + 1] = (S)(coef * c01);
     corner[9 * t + 2] = (S)(k2 + coef * (c11 - l2));
   }
+}
+
+// Strain, area and volume terms of one triangle: e1, e2 its edges from corner 0, q0 corner 0
+// relative to the volume centre cvol, tc = (d00, d01, d11, w_t), kA and kV the area and
+// volume penalty slopes.  Adds the strain energy w_t/2 |F - R|^2 to e_el, sets degen for a
+// degenerate F^T F, and returns the gradients at the three corners.  mrec: the triangle's
+// strain-limit matrix (m00, m01, m11), R = F M, for a limited type; null: R = F (F^T F)^-1/2
+// by the closed-form 2x2 SPD square root (C + sqrt(det C) I)/sqrt(tr C + 2 sqrt(det C)).
+template <typename S>
+__device__ __forceinline__ void triangle_terms(V3<S> e1, V3<S> e2, V3<S> q0, const typename Q4Of<S>::type& tc,
+                                               const S* mrec, S kA, S kV, Acc<S>& e_el, bool& degen, V3<S>& g0,
+                                               V3<S>& g1, V3<S>& g2) {
+  const S half = (S)0.5, sixth = (S)(1.0 / 6.0);
+  const S d00 = tc.x, d01 = tc.y, d11 = tc.z;
+  const S wt = tc.w;
+  V3<S> F0 = d00 * e1;
+  V3<S> F1 = d01 * e1 + d11 * e2;
+  S c00 = dot(F0, F0), c01 = dot(F0, F1), c11 = dot(F1, F1);
+  S det = c00 * c11 - c01 * c01;
+  V3<S> P0{0, 0, 0}, P1{0, 0, 0};
+  if ((double)det > kDegenerateDet) {
+    V3<S> R0, R1;
+    if (mrec) {
+      const S m00 = mrec[0], m01 = mrec[1], m11 = mrec[2];
+      R0 = m00 * F0 + m01 * F1;
+      R1 = m01 * F0 + m11 * F1;
+    } else {
+      S s = sqrt(det);
+      S tau = sqrt(c00 + c11 + (S)2 * s);
+      S s00 = (c00 + s) / tau, s01 = c01 / tau, s11 = (c11 + s) / tau;
+      S idet = (S)1 / (s00 * s11 - s01 * s01);
+      // R = F S^-1, S^-1 = [[s11, -s01], [-s01, s00]] / det S
+      R0 = idet * (s11 * F0 - s01 * F1);
+      R1 = idet * (s00 * F1 - s01 * F0);
+    }
+    V3<S> D0 = F0 - R0, D1 = F1 - R1;
+    e_el.add(half * wt * (dot(D0, D0) + dot(D1, D1)));
+    P0 = wt * D0;
+    P1 = wt * D1;
+  } else {
+    degen = true;
+  }
+  // strain: dE/de1 = P0 d00 + P1 d01, dE/de2 = P1 d11
+  g1 = d00 * P0 + d01 * P1;
+  g2 = d11 * P1;
+  g0 = (S)-1 * (g1 + g2);
+  // area: dA_t/dx_k = n/2 x (x_{k+2} - x_{k+1})
+  V3<S> N = cross(e1, e2);
+  S nn = sqrt(dot(N, N));
+  if (nn > (S)0) {
+    V3<S> nh = ((S)1 / nn) * N;
+    g0 = g0 + (kA * half) * cross(nh, e2 - e1);
+    g1 = g1 + (kA * half) * cross(nh, (S)-1 * e2);
+    g2 = g2 + (kA * half) * cross(nh, e1);
+  }
+  // volume: dV_t/dq0 = q1 x q2 / 6 (cyclic), q = x - cvol
+  V3<S> q1 = q0 + e1, q2 = q0 + e2;
+  g0 = g0 + (kV * sixth) * cross(q1, q2);
+  g1 = g1 + (kV * sixth) * cross(q2, q0);
+  g2 = g2 + (kV * sixth) * cross(q0, q1);
+}
+
+// Hinge vector K = sum_j c_j x_j = c1 (x_j - x_i) + c2 (x_kA - x_i) + c3 (x_kB - x_i) of the
+// hinge (i, j, kA, kB) with coefficients cv = (c0, c1, c2, c3).
+template <typename S>
+__device__ __forceinline__ V3<S> hinge_vector(const S* X, const S* U, int4 hv,
+                                              const typename Q4Of<S>::type& cv) {
+  return cv.y * edge(X, U, hv.x, hv.y) + cv.z * edge(X, U, hv.x, hv.z) + cv.w * edge(X, U, hv.x, hv.w);
+}
+
+// Bending term of one hinge: the projection p of K onto |K| = |K0| (K0row = (K0x, K0y,
+// K0z, |K0|); p = K0 when |K| vanishes), w_e/2 |K - p|^2 added to e_el.  Returns w_e (K - p),
+// whose product with c_j is the gradient at the hinge's vertex j.
+template <typename S>
+__device__ __forceinline__ V3<S> hinge_terms(V3<S> K, const S* K0row, S we, Acc<S>& e_el) {
+  S kn = sqrt(dot(K, K));
+  V3<S> p;
+  if ((double)kn < kDegenerateNorm) {
+    p = {__ldg(&K0row[0]), __ldg(&K0row[1]), __ldg(&K0row[2])};
+  } else {
+    p = (__ldg(&K0row[3]) / kn) * K;
+  }
+  V3<S> r = K - p;
+  e_el.add((S)0.5 * we * dot(r, r));
+  return we * r;
 }
 
 // f(X+U) and its gradient into Gout.  W = y - x_n.  The strain projection maps the
@@ -401,7 +490,7 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const StepParams& P,
   const double e_vol = 0.5 * ty.w_vol * dV * dV / ty.V0;
   const S kA = (S)(ty.w_area * dA / ty.A0);
   const S kV = (S)(ty.w_vol * dV / ty.V0);
-  const S half = (S)0.5, sixth = (S)(1.0 / 6.0);
+  const S half = (S)0.5;
 
   NPFEM_PHASE_END(t_area, kPhAreaVolume, P, lane)
   // pass B: triangles (strain projection + area/volume corner gradients)
@@ -411,55 +500,10 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const StepParams& P,
     const int4 tv = ldg4(ty.tri4 + 4 * t);
     const typename Q4Of<S>::type tc = ldg4(ty.trc + 4 * t);
     const int i0 = tv.x, i1 = tv.y, i2 = tv.z;
-    V3<S> e1 = edge(X, U, i0, i1), e2 = edge(X, U, i0, i2);
-    const S d00 = tc.x, d01 = tc.y, d11 = tc.z;
-    const S wt = tc.w;
-    V3<S> F0 = d00 * e1;
-    V3<S> F1 = d01 * e1 + d11 * e2;
-    S c00 = dot(F0, F0), c01 = dot(F0, F1), c11 = dot(F1, F1);
-    S det = c00 * c11 - c01 * c01;
-    V3<S> P0{0, 0, 0}, P1{0, 0, 0};
-    if ((double)det > kDegenerateDet) {
-      V3<S> R0, R1;
-      if (limited) {
-        const S m00 = w.corner[9 * t], m01 = w.corner[9 * t + 1], m11 = w.corner[9 * t + 2];
-        R0 = m00 * F0 + m01 * F1;
-        R1 = m01 * F0 + m11 * F1;
-      } else {
-        S s = sqrt(det);
-        S tau = sqrt(c00 + c11 + (S)2 * s);
-        S s00 = (c00 + s) / tau, s01 = c01 / tau, s11 = (c11 + s) / tau;
-        S idet = (S)1 / (s00 * s11 - s01 * s01);
-        // R = F S^-1, S^-1 = [[s11, -s01], [-s01, s00]] / det S
-        R0 = idet * (s11 * F0 - s01 * F1);
-        R1 = idet * (s00 * F1 - s01 * F0);
-      }
-      V3<S> D0 = F0 - R0, D1 = F1 - R1;
-      e_el.add(half * wt * (dot(D0, D0) + dot(D1, D1)));
-      P0 = wt * D0;
-      P1 = wt * D1;
-    } else {
-      degen = true;
-    }
-    // strain: dE/de1 = P0 d00 + P1 d01, dE/de2 = P1 d11
-    V3<S> g1 = d00 * P0 + d01 * P1;
-    V3<S> g2 = d11 * P1;
-    V3<S> g0 = (S)-1 * (g1 + g2);
-    // area: dA_t/dx_k = n/2 x (x_{k+2} - x_{k+1})
-    V3<S> N = cross(e1, e2);
-    S nn = sqrt(dot(N, N));
-    if (nn > (S)0) {
-      V3<S> nh = ((S)1 / nn) * N;
-      g0 = g0 + (kA * half) * cross(nh, e2 - e1);
-      g1 = g1 + (kA * half) * cross(nh, (S)-1 * e2);
-      g2 = g2 + (kA * half) * cross(nh, e1);
-    }
-    // volume: dV_t/dq0 = q1 x q2 / 6 (cyclic), q = x - cvol
-    V3<S> q0 = (ld3(X, i0) + ld3(U, i0)) - cvol;
-    V3<S> q1 = q0 + e1, q2 = q0 + e2;
-    g0 = g0 + (kV * sixth) * cross(q1, q2);
-    g1 = g1 + (kV * sixth) * cross(q2, q0);
-    g2 = g2 + (kV * sixth) * cross(q0, q1);
+    const V3<S> e1 = edge(X, U, i0, i1), e2 = edge(X, U, i0, i2);
+    const V3<S> q0 = (ld3(X, i0) + ld3(U, i0)) - cvol;
+    V3<S> g0, g1, g2;
+    triangle_terms<S>(e1, e2, q0, tc, limited ? w.corner + 9 * t : nullptr, kA, kV, e_el, degen, g0, g1, g2);
     st3(w.corner, 3 * t + 0, g0);
     st3(w.corner, 3 * t + 1, g1);
     st3(w.corner, 3 * t + 2, g2);
@@ -468,21 +512,9 @@ __device__ EvalOut eval_objective(const DevTypeView<S>& ty, const StepParams& P,
   // pass C: hinges (bending projection onto |K| = |K0|)
   for (int h = lane; h < E; h += 32) {
     const int4 hv = ldg4(ty.hinges + 4 * h);
-    const int i = hv.x, j = hv.y, ka = hv.z, kb = hv.w;
     const typename Q4Of<S>::type cv = ldg4(ty.c_hinge + 4 * h);
-    const S c1 = cv.y, c2 = cv.z, c3 = cv.w;
-    V3<S> K = c1 * edge(X, U, i, j) + c2 * edge(X, U, i, ka) + c3 * edge(X, U, i, kb);
-    S kn = sqrt(dot(K, K));
-    V3<S> p;
-    if ((double)kn < kDegenerateNorm) {
-      p = {__ldg(&ty.K0[4 * h]), __ldg(&ty.K0[4 * h + 1]), __ldg(&ty.K0[4 * h + 2])};
-    } else {
-      p = (__ldg(&ty.K0[4 * h + 3]) / kn) * K;
-    }
-    V3<S> r = K - p;
-    const S we = __ldg(&ty.w_hinge[h]);
-    e_el.add(half * we * dot(r, r));
-    st3(w.hbuf, h, we * r);
+    const V3<S> K = hinge_vector<S>(X, U, hv, cv);
+    st3(w.hbuf, h, hinge_terms<S>(K, ty.K0 + 4 * h, __ldg(&ty.w_hinge[h]), e_el));
   }
   // Rayleigh damping, elastic part: (c_beta/dt)/2 U^T L U with U = x - x_n, element by
   // element into the same corner and hinge buffers (each owned by the lane that wrote it)

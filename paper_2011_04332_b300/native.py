@@ -8,7 +8,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
-from typing import Optional, Sequence
+from typing import Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -88,6 +88,8 @@ def load_library() -> C.CDLL:
         "npfem_batch_set_groups": [vp, C.c_int32, C.c_int32],
         "npfem_batch_kernel_spans": [vp, C.c_int32, C.POINTER(C.c_double)],
         "npfem_batch_get_groups": [vp, C.c_int32, C.POINTER(C.c_int32)],
+        "npfem_batch_set_iter_width": [vp, C.c_int32, C.c_int32],
+        "npfem_batch_get_iter_width": [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
         "npfem_batch_kernel_times": [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int32)],
         "npfem_batch_set_mode": [vp, C.c_int32],
         "npfem_batch_set_split_launch": [vp, C.c_int32, C.POINTER(C.c_int32)],
@@ -401,6 +403,17 @@ class Batch:
         out = C.c_int32()
         _check(_lib.npfem_batch_get_groups(self.handle, int(type_index), C.byref(out)))
         return int(out.value)
+
+    def set_iter_width(self, type_index: int, warps: int) -> None:
+        """npfem_batch_set_iter_width: warps per cell of the CTA iteration kernels (0: one warp
+        per cell with the per-vertex gather)."""
+        _check(_lib.npfem_batch_set_iter_width(self.handle, int(type_index), int(warps)))
+
+    def get_iter_width(self, type_index: int) -> Tuple[int, int]:
+        """npfem_batch_get_iter_width: (warps per cell, resident CTAs per SM)."""
+        w, b = C.c_int32(), C.c_int32()
+        _check(_lib.npfem_batch_get_iter_width(self.handle, int(type_index), C.byref(w), C.byref(b)))
+        return int(w.value), int(b.value)
 
     def set_kernel_timing(self, enable: bool = True) -> None:
         """npfem_batch_set_kernel_timing: CUDA events around every split-mode launch."""

@@ -103,9 +103,11 @@ SplitShape = Tuple[int, int, int, int, int, int, int]
 # Largest resident warps per SM of the solve kernel for 1..4 cells per warp (register
 # use of the four instantiations on sm_103a: 64, 80, 96, 126 registers per thread), and
 # largest resident CTAs per SM of the CTA-cooperative solve kernel per CTA width (2, 4, 6,
-# 8 warps compiled for 72, 95, 96, 128 registers per thread).
+# 8 warps compiled for 72, 95, 96, 128 registers per thread); for two cells per CTA below.
 SOLVE_MAX_WARPS = {1: 32, 2: 24, 3: 20, 4: 16}
 CTA_MAX_CTAS = {2: 13, 4: 5, 6: 3, 8: 2}
+# two cells per CTA: 90 and 96 registers per thread for 2 and 4 warps
+CTA2_MAX_CTAS = {2: 11, 4: 5}
 
 
 def split_solve_candidates(n_verts: int, smem_per_sm: int = 228 * 1024, smem_per_cta: int = 227 * 1024):
@@ -125,6 +127,12 @@ def split_solve_candidates(n_verts: int, smem_per_sm: int = 228 * 1024, smem_per
             for bps in range(max(1, top // 2), top + 1):
                 if wpb * bps >= 4:
                     out.append((wpb, bps, 2, 0, 1))
+        # two cells per CTA (2 or 4 warps): each factor entry serves both cells
+        for wpb in (2, 4):
+            top = min(16, smem_per_sm // (2 * zb + 1024), CTA2_MAX_CTAS[wpb])
+            for bps in range(max(1, top // 2), top + 1):
+                if wpb * bps >= 4 and 2 * zb <= smem_per_cta:
+                    out.append((wpb, bps, 2, 0, 2))
     for cells in (1, 2, 3, 4):
         wmax = SOLVE_MAX_WARPS[cells]
         for wpb in (1, 2, 4):
@@ -178,7 +186,9 @@ def autotune_split(batch: native.Batch, x, v, f, iters=None, reps: int = 2, solv
             if ms < best_ms:
                 best_ms, cur = ms, shape
         batch.set_split_launch(t, cur)
-        if not solve_only:
+        # the CTA iteration kernels take one cell per CTA at the type's fixed width (which
+        # sets the order of a cell's sums): the warp kernels' shapes do not apply to them
+        if not solve_only and batch.get_iter_width(t)[0] == 0:
             for cand in split_iter_candidates():
                 shape = list(cand) + cur[2:]
                 if shape == cur:

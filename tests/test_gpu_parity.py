@@ -70,11 +70,14 @@ def cell_errors(b, x, xref, radius_from=None):
     return np.array(errs)
 
 
-def compare(b, precision, cells=None, steps=1, iters=None, check_alpha=True, bar=None, shapes=None):
+def compare(b, precision, cells=None, steps=1, iters=None, check_alpha=True, bar=None, shapes=None, width=None):
     nat = _native()
     r = Runner(b, precision)
     for t, shape in (shapes or {}).items():
         r.batch.set_split_launch(t, shape)
+    if width is not None:
+        for t in range(len(b.types)):
+            r.batch.set_iter_width(t, width)
     ots = oracle_types(b)
     x, v, f = b.x.copy(), b.v.copy(), b.f.copy()
     if precision == nat.FP32FORM:
@@ -451,17 +454,18 @@ def test_multi_cell_solve_is_identical(prec, cells):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-@pytest.mark.parametrize("warps", [2, 4, 6, 8])
-def test_cta_cooperative_solve(prec, warps):
-    """Placement 2: the 2 or 4 warps of a CTA sweep one cell's shared solve vector
-    through the level packing of the factor, for every type of a mixed batch (162, 642
-    and 2562 vertices, 3..8 iterations): parity with the oracle at the usual bars over
-    two steps, and agreement with the one-warp solve to rounding (the level packing
-    applies the same updates in another order)."""
+@pytest.mark.parametrize("warps,cells", [(2, 1), (4, 1), (6, 1), (8, 1), (2, 2), (4, 2)])
+def test_cta_cooperative_solve(prec, warps, cells):
+    """Placement 2: the warps of a CTA sweep one cell's (or two cells') shared solve
+    vectors through the level packing of the factor, for every type of a mixed batch
+    (162, 642 and 2562 vertices, 3..8 iterations, so the lists of cells still iterating
+    have odd lengths): parity with the oracle at the usual bars over two steps, agreement
+    with the one-warp solve to rounding (the level packing applies the same updates in
+    another order), and two cells per CTA give the one-cell CTA's results bit for bit."""
     nat = _native()
     b = I.heterogeneous_batch(n_rbc3=6, n_rbc4=4, n_plt=5, seed=1007)
     p = nat.FP64 if prec == "fp64" else nat.FP32FORM
-    shapes = {t: (2, 4, warps, 2, 2, 0, 1) for t in range(len(b.types))}
+    shapes = {t: (2, 4, warps, 2, 2, 0, cells) for t in range(len(b.types))}
     compare(b, p, steps=2, shapes=shapes)
     r = Runner(b, p)
     for t in range(len(b.types)):            # one cell per warp, vectors in shared memory
@@ -472,14 +476,22 @@ def test_cta_cooperative_solve(prec, warps):
         assert r.batch.get_split_launch(t)[0] == shape
     cta = r.step(b.x, b.v, b.f, iters=b.iters)
     _assert_modes_agree(one, cta, prec, b)
+    if cells == 2:
+        for t in range(len(b.types)):
+            r.batch.set_split_launch(t, (2, 4, warps, 2, 2, 0, 1))
+        single = r.step(b.x, b.v, b.f, iters=b.iters)
+        for a, c in zip(single, cta):
+            assert np.array_equal(a, c)
 
 
 def test_cta_cooperative_shape_validation():
-    """Placement 2 takes 2 or 4 warps per CTA, one cell, interleaved coordinates."""
+    """Placement 2 takes 2, 4, 6 or 8 warps per CTA and one cell, or 2 or 4 warps and
+    two cells, interleaved coordinates."""
     nat = _native()
     b = I.heterogeneous_batch(n_rbc3=2, n_rbc4=1, n_plt=1, seed=1008)
     r = Runner(b, nat.FP64)
-    for bad in [(2, 4, 3, 2, 2, 0, 1), (2, 4, 2, 2, 2, 1, 1), (2, 4, 4, 2, 2, 0, 2), (2, 4, 2, 2, 3, 0, 1), (2, 4, 5, 2, 2, 0, 1), (2, 4, 6, 2, 1, 0, 1)]:
+    for bad in [(2, 4, 3, 2, 2, 0, 1), (2, 4, 2, 2, 2, 1, 1), (2, 4, 4, 2, 2, 0, 3), (2, 4, 6, 2, 2, 0, 2),
+                (2, 4, 2, 2, 3, 0, 1), (2, 4, 5, 2, 2, 0, 1), (2, 4, 6, 2, 1, 0, 1)]:
         with pytest.raises(nat.NpfemError):
             r.batch.set_split_launch(0, bad)
 
@@ -524,3 +536,42 @@ def test_groups_leave_results_unchanged(prec):
     for bad in (0, 5):
         with pytest.raises(nat.NpfemError):
             r.batch.set_groups(0, bad)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_iteration_kernel_widths(prec):
+    """Split-mode iteration kernels with one CTA per cell (positions, trial displacement and
+    gradient in shared memory, elements by colour class) at widths 1 to 16 warps, and the
+    one-warp-per-cell kernels (width 0): every width matches the oracle at the usual bars
+    over two steps with ragged iteration counts (zero and one included), the widths agree
+    with each other to rounding (the width sets the order of a cell's sums), and a width
+    keeps its bits under other iteration launch shapes."""
+    nat = _native()
+    b = I.heterogeneous_batch(n_rbc3=5, n_rbc4=2, n_plt=4, seed=1011)
+    it = b.iters.copy()
+    it[0] = 0
+    it[2] = 1
+    p = nat.FP64 if prec == "fp64" else nat.FP32FORM
+    r = Runner(b, p)
+    defaults = [r.batch.get_iter_width(t)[0] for t in range(len(b.types))]
+    assert defaults == ([0] * len(b.types) if prec == "fp64" else [4, 8, 2])
+    ref = r.step(b.x, b.v, b.f, iters=it)
+    for w in (0, 1, 2, 4, 8, 16):
+        for t in range(len(b.types)):
+            r.batch.set_iter_width(t, w)
+            assert r.batch.get_iter_width(t)[0] == w
+            assert (r.batch.get_iter_width(t)[1] > 0) == (w > 0)
+        out = r.step(b.x, b.v, b.f, iters=it)
+        _assert_modes_agree(ref, out, prec, b)
+        shapes = {t: (2, 8) + tuple(r.batch.get_split_launch(t)[0][2:]) for t in range(len(b.types))}
+        compare(b, p, steps=2, iters=it, width=w)
+        for t, sh in shapes.items():
+            r.batch.set_split_launch(t, (4, 3) + sh[2:])
+        again = r.step(b.x, b.v, b.f, iters=it)
+        for a, c in zip(out, again):
+            assert np.array_equal(a, c), w
+        for t, sh in shapes.items():
+            r.batch.set_split_launch(t, sh)
+    for bad in (-1, 17):
+        with pytest.raises(nat.NpfemError):
+            r.batch.set_iter_width(0, bad)

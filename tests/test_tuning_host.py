@@ -16,11 +16,11 @@ def test_split_solve_candidates_fit(n):
     for wpb, bps, place, per_coord, cells in cands:
         warps = wpb * bps
         assert warps >= 4 and bps <= 16, (wpb, bps)
-        if place == 2:                         # one interleaved vector per CTA
-            zb = 24 * (n + 1)
-            assert cells == 1 and per_coord == 0 and wpb in (2, 4, 6, 8)
+        if place == 2:                         # one interleaved vector per cell of the CTA
+            zb = 24 * (n + 1) * cells
+            assert cells in (1, 2) and per_coord == 0 and wpb in ((2, 4, 6, 8) if cells == 1 else (2, 4))
             assert zb <= SMEM_CTA and bps * (zb + 1024) <= SMEM_SM
-            assert bps <= T.CTA_MAX_CTAS[wpb]
+            assert bps <= (T.CTA_MAX_CTAS if cells == 1 else T.CTA2_MAX_CTAS)[wpb]
         elif place == 1:                       # per-warp vectors in shared memory
             zb = (8 if per_coord else 24) * (n + 1)
             cta = wpb * cells * zb
