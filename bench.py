@@ -468,9 +468,12 @@ def run_ours(args, rank, world, local_rank):
     solve_launches = sum(ktime[t]["k_solve"][1] for t in present) / args.steps
     solve_span = kspan["k_solve"] / args.steps
     achieved = flops_per_step / (solve_span / 1e3) / 1e12 if solve_span > 0 else None
-    traffic_cell, traffic_how = measured_traffic(args.workload, args.precision)
-    cell_solves = float(np.sum(its))
-    traffic = traffic_cell * cell_solves / solve_launches if traffic_cell and solve_launches else None
+    # DRAM bytes of an average solve launch: per cell size, the captured bytes per
+    # cell-solve times the cell-solves of a step, over the step's solve launches
+    traffic_cell, traffic_how = measured_traffic(nv, args.precision)
+    traffic = None
+    if traffic_cell and solve_launches:
+        traffic = float(sum(traffic_cell[int(n)] * i for n, i in zip(nv, its))) / solve_launches
     roofline = {"bound": "alu", "pipe": "fp64", "kernel": "npfem_k_solve", "achieved": achieved, "peak": fp64_peak,
                 "unit": "TFLOP/s", "frac": achieved / fp64_peak if fp64_peak and achieved else None, "traffic": traffic,
                 "traffic_note": traffic_how,
@@ -495,6 +498,28 @@ def run_ours(args, rank, world, local_rank):
            "note": "the step's algorithmic HBM traffic; per-type constants stay L2-resident, and the per-cell "
                    "workspace traffic of the iteration kernels is not algorithmic (see the kernels' DRAM bytes in "
                    "the ncu summaries)"}
+    # the whole step's DRAM traffic and FP32 / FP64 flops from the per-kernel ncu records,
+    # over the measured step time: HBM bandwidth and the two pipes' fractions
+    recs, recs_how = kernel_records(nv, args.precision)
+    pipes = None
+    if recs:
+        cnt = step_counters(recs, nv, its)
+        sec = ms_per_step / 1e3
+        hbm["dram_bytes_per_step"] = cnt["dram_bytes"]
+        hbm["measured_gbs"] = cnt["dram_bytes"] / sec / 1e9
+        hbm["measured_frac"] = hbm["measured_gbs"] / hbm_peak if hbm_peak else None
+        hbm["measured_how"] = ("DRAM bytes per cell, cell-solve and cell-iteration of k_begin, k_solve and k_iter "
+                               "(ncu, profiles/traffic.json) times the step's cells and iterations, over the "
+                               "CUDA-event step time")
+        pipes = {"fp32_flops_per_step": cnt["fp32_flops"], "fp64_flops_per_step": cnt["fp64_flops"],
+                 "fp32_tflops": cnt["fp32_flops"] / sec / 1e12, "fp64_tflops": cnt["fp64_flops"] / sec / 1e12,
+                 "fp32_frac": cnt["fp32_flops"] / sec / 1e12 / fp32_peak if fp32_peak else None,
+                 "fp64_frac": cnt["fp64_flops"] / sec / 1e12 / fp64_peak if fp64_peak else None,
+                 "peaks": "FP32 and FP64 FMA rates measured live by the probe",
+                 "how": "executed FP32 / FP64 add, multiply (1 flop) and fused multiply-add (2 flops) thread "
+                        "instructions of every kernel of the step (ncu, profiles/traffic.json: " + recs_how + ")"}
+    else:
+        hbm["measured_how"] = recs_how
 
     # end-to-end through the C ABI with host (pinned) buffers
     e2e = None
@@ -573,6 +598,7 @@ def run_ours(args, rank, world, local_rank):
         "parity_sample": err,
         "roofline": roofline,
         "hbm": hbm,
+        "pipes": pipes,
         "fp32_peak_tflops": fp32_peak,
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -723,7 +749,7 @@ def measure_adjoint_implicit(dev, b, reps: int = 5, fwd_tol: float = 1e-10, budg
 # packer that lays out the factor they stream (launch plumbing is excluded).
 # The sources a step's kernels are compiled from; the adjoint kernels (adjoint.cuh) take
 # no part in a step, so an edit there leaves the captured solve traffic valid.
-KERNEL_SOURCES = ("npfem_internal.h", "step_kernel.cuh", "split_kernels.cuh", "host_setup.cpp",
+KERNEL_SOURCES = ("npfem_internal.h", "step_kernel.cuh", "split_kernels.cuh", "iter_cta.cuh", "host_setup.cpp",
                   "contact_kernels.cuh")
 
 
@@ -738,10 +764,10 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def measured_traffic(workload: str, precision: str):
-    """DRAM bytes per cell-solve of the solve kernel from profiles/traffic.json, only if
-    it was captured for the current kernel sources and this cell size and precision;
-    else None."""
+def measured_traffic(sizes, precision: str):
+    """DRAM bytes per cell-solve of the solve kernel for each cell size (vertices) from
+    profiles/traffic.json, only if captured for the current kernel sources, this
+    precision and every size; else None and the reason."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         rec = json.load(open(p))
@@ -749,10 +775,47 @@ def measured_traffic(workload: str, precision: str):
         return None, "no traffic record"
     if rec.get("kernel_src_sha256") != kernel_source_hash():
         return None, "kernel changed since the ncu capture"
-    ent = rec.get("entries", {}).get(f"{workload}/{precision}")
-    if not ent:
-        return None, "no capture for this workload"
-    return ent["dram_bytes_per_cell_solve"], ent["how"]
+    out, how = {}, []
+    for n in sorted(set(int(s) for s in sizes)):
+        ent = rec.get("entries", {}).get(f"n{n}/{precision}")
+        if not ent:
+            return None, f"no capture for {n}-vertex cells"
+        out[n] = ent["dram_bytes_per_cell_solve"]
+        how.append(f"{n} vertices: {ent['how']}")
+    return out, "; ".join(how)
+
+
+def kernel_records(sizes, precision: str):
+    """Per-kernel DRAM bytes and FP32 / FP64 flops of the step's kernels for each cell
+    size, from profiles/traffic.json ("kernels": ncu counters of every launch of one step
+    of a homogeneous batch, divided by the cells (k_begin), cell-solves (k_solve) or
+    cell-iterations (k_iter) of the launch), only if captured for the current kernel
+    sources, this precision and every size; else None and the reason."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(p))
+    except (OSError, ValueError):
+        return None, "no traffic record"
+    if rec.get("kernel_src_sha256") != kernel_source_hash():
+        return None, "kernel changed since the ncu capture"
+    out = {}
+    for n in sorted(set(int(s) for s in sizes)):
+        ent = rec.get("kernels", {}).get(f"n{n}/{precision}")
+        if not ent:
+            return None, f"no kernel record for {n}-vertex cells"
+        out[n] = ent
+    return out, rec.get("kernels_how", "")
+
+
+def step_counters(recs, nv, its):
+    """DRAM bytes, FP32 flops and FP64 flops of one step from the per-unit kernel records:
+    per cell k_begin once, k_solve and k_iter once per iteration."""
+    tot = {"dram_bytes": 0.0, "fp32_flops": 0.0, "fp64_flops": 0.0}
+    for n, i in zip(nv, its):
+        r = recs[int(n)]
+        for key in tot:
+            tot[key] += r["k_begin"][key] + i * (r["k_solve"][key] + r["k_iter"][key])
+    return tot
 
 
 def measured_hbm_peak():

@@ -307,7 +307,7 @@ npfem_status npfem_batch_get_groups(const npfem_batch* batch, int32_t type_index
 
 /* Split mode: iteration kernels of type type_index (the prediction with the first
  * objective evaluation, and the rest of each iteration around the FP64 solve).
- * warps >= 1 (default in the FP32 form: 2 for up to 256 vertices, 4 up to 1024, else 8; in the FP64
+ * warps in 1, 2, 4, 8, 16 (default in the FP32 form: 2 for up to 256 vertices, 4 up to 1024, else 8; in the FP64
  * form 0, whose objective is bound by the FP64 pipe rather than by gathers): one CTA of that
  * many warps per cell, the cell's start positions, trial displacement and gradient in
  * shared memory during each objective evaluation (9n values: 23 KB for a 642-vertex FP32
@@ -316,8 +316,8 @@ npfem_status npfem_batch_get_groups(const npfem_batch* batch, int32_t type_index
  * assembled per vertex), CTA-wide sums.  warps = 0: one warp per cell with per-element
  * records in the workspace and a per-vertex gather.  The width sets the order of a cell's
  * sums: results of different widths agree to rounding; for a given width they do not
- * depend on any other launch setting.  NPFEM_ERR_INVALID_ARG for warps outside 0..16 or a
- * type without cells in the batch; NPFEM_ERR_UNSUPPORTED when the shared-memory arrays
+ * depend on any other launch setting.  NPFEM_ERR_INVALID_ARG for warps not among 0, 1, 2,
+ * 4, 8, 16 or a type without cells in the batch; NPFEM_ERR_UNSUPPORTED when the shared-memory arrays
  * exceed a CTA or the type needs more than 64 colour classes (the setting is then left as
  * it was; a new batch falls back to warps = 0 in those cases).  npfem_batch_get_iter_width
  * returns the width and, when ctas_per_sm is not null, the CTAs per SM that are resident
@@ -425,10 +425,10 @@ npfem_status npfem_step_host(npfem_batch* batch, void* x, void* v, const void* f
  * device array reserved on every GPU that loads the library, held until exit.
  * Limits: ncells <= 65536, and the type's per-warp workspace must fit four warps
  * in the array (otherwise NPFEM_ERR_UNSUPPORTED with the sizes in the message).
- * The first call on a device looks up the array's device address and sets the
- * kernels' shared-memory limit; make that first call before any stream capture.
- * Both are kept for the life of the process: after cudaDeviceReset on a device,
- * further calls on it are unsupported.
+ * Every call looks up the array's device address in the current device's context and
+ * sets the kernels' shared-memory limit (neither allocates nor is cached, so calls after
+ * a cudaDeviceReset work); the first call on a device also loads the library's kernels
+ * there, so make that first call before any stream capture.
  * Every call reuses the same array (the work-queue counter is cleared on each call),
  * so calls whose GPU work overlaps (two streams, or two threads) race and must be
  * serialised by the caller.  Asynchronous on `stream`. */

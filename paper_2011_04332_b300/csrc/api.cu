@@ -312,8 +312,8 @@ static void default_split_shape(TypeLaunch& L, int n, npfem_precision prec) {
     L.sv_wpb = 2, L.sv_bps = 7, L.sv_smem = 1;
   } else if (n <= 1024) {  // 642-vertex RBC: CTAs of 2 warps per cell, 13 per SM (72 registers)
     L.sv_wpb = 2, L.sv_bps = 13, L.sv_smem = 2;
-  } else {                 // 2562-vertex RBC: CTAs of 6 warps per cell, 3 per SM
-    L.sv_wpb = 6, L.sv_bps = 3, L.sv_smem = 2;
+  } else {                 // 2562-vertex RBC: CTAs of 8 warps per cell, 3 per SM (80 registers)
+    L.sv_wpb = 8, L.sv_bps = 3, L.sv_smem = 2;
   }
   // iteration kernels: 32 warps per SM in the FP32 form (64 registers), 16 in FP64
   L.it_wpb = 2, L.it_bps = prec == NPFEM_FP64 ? 8 : 16;
@@ -411,8 +411,10 @@ static npfem_status launch_split(npfem_batch* b, const npfem_cell_type* t, const
   int* act_count = G.counter + kActiveCountOff;
   int* act0 = L.active + G.g0;                // list of even iterations (item indices of the group)
   int* act1 = L.active + L.ncells + G.g0;     // list of odd iterations
+  // CTA iteration kernels: the resident CTAs per SM, capped by the iteration shape's CTAs
+  // per SM (fewer leave room on each SM for the solve kernels of other chains)
   const size_t itc_smem = iter_cta_smem_bytes<S>(view.n);
-  const int itc_grid = std::max(1, std::min<int>(b->sms * L.itc_bps, G.gn));
+  const int itc_grid = std::max(1, std::min<int>(b->sms * std::min(L.itc_bps, L.it_bps), G.gn));
   if (kind == 0) {
     P.queue_counter = G.counter;
     P.act_out = act0;
@@ -1529,8 +1531,8 @@ npfem_status npfem_batch_get_groups(const npfem_batch* b, int32_t type_index, in
 }
 
 npfem_status npfem_batch_set_iter_width(npfem_batch* b, int32_t type_index, int32_t warps) {
-  if (!b || warps < 0 || warps > kIterCtaMaxWarps)
-    return fail(NPFEM_ERR_INVALID_ARG, "batch_set_iter_width: warps in 0..16");
+  if (!b || warps < 0 || warps > kIterCtaMaxWarps || (warps & (warps - 1)) != 0)
+    return fail(NPFEM_ERR_INVALID_ARG, "batch_set_iter_width: warps in 0, 1, 2, 4, 8, 16");
   for (TypeLaunch& L : b->launches)
     if (L.type_index == type_index) {
       const int keep_w = L.itc_w, keep_b = L.itc_bps;

@@ -38,25 +38,64 @@ struct CtaShared {
   int item;
 };
 
-// Sums over the CTA of K per-thread FP64 values; every thread receives the totals.  Lanes
-// combine by shuffles, then the warp totals are added in warp order.  All threads of the
-// CTA must make the same sequence of calls (par alternates the buffers).
+// Sums over the CTA of K <= 4 per-thread FP64 values; every thread receives the totals.
+// The FP64 pipe is the scarce unit (a warp-wide FP64 add occupies it for 64 cycles
+// whatever the active lanes), so the lanes reduce-scatter: at the first log2(K4) shuffle
+// steps (K4 = K rounded up to a power of two) each lane keeps half of the values it still
+// carries, so every later step is a single add for all values at once; lane l ends with
+// value l mod K4 summed over the warp.  The warp totals go to shared memory, and after
+// the barrier lane k*nw + q of every warp loads value k of warp q and a butterfly over the
+// nw lanes of each value adds them (nw a power of two, 32 / nw values per round).  Every
+// lane of every warp performs the same additions on the same operands, so all threads
+// receive identical totals.  Call discipline: all threads of the CTA make the same
+// sequence of calls (par alternates the buffers).
 template <int K>
 __device__ __forceinline__ void cta_sum(double (&v)[K], CtaShared& sh, int& par) {
+  static_assert(K >= 1 && K <= 4, "cta_sum takes 1 to 4 values");
+  constexpr int K4 = K == 1 ? 1 : (K == 2 ? 2 : 4);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double w[K4];
 #pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = warp_sum_d(v[k]);
+  for (int k = 0; k < K4; ++k) w[k] = k < K ? v[k] : 0.0;
+  // reduce-scatter over the lane bits 4, 3 (K4 = 4) or 4 (K4 = 2): after it, a lane's
+  // w[0] holds the partial sum of value (lane >> (5 - log2 K4)) over the lanes that share
+  // its remaining bits
+  if (K4 >= 2) {
+    const bool hi = lane & 16;
+#pragma unroll
+    for (int k = 0; k < K4 / 2; ++k) {
+      const double send = hi ? w[k] : w[k + K4 / 2];
+      const double keep = hi ? w[k + K4 / 2] : w[k];
+      w[k] = keep + __shfl_xor_sync(kFull, send, 16);
+    }
+  }
+  if (K4 == 4) {
+    const bool hi = lane & 8;
+    const double send = hi ? w[0] : w[1];
+    const double keep = hi ? w[1] : w[0];
+    w[0] = keep + __shfl_xor_sync(kFull, send, 8);
+  }
+  double x = w[0];
+#pragma unroll
+  for (int o = (K4 == 4 ? 4 : (K4 == 2 ? 8 : 16)); o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  // lane l now holds value (l >> 3) (K4 = 4), (l >> 4) (K4 = 2) or the only value
   double* r = sh.red[par];
   par ^= 1;
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < K; ++k) r[warp * K + k] = v[k];
+  const int vid = K4 == 4 ? lane >> 3 : (K4 == 2 ? lane >> 4 : 0);
+  if ((lane & (32 / K4 - 1)) == 0 && vid < K) r[vid * nw + warp] = x;
   __syncthreads();
+  // 32 / nw values per round (nw a power of two): lane j*nw + q loads value kb + j of warp
+  // q, and a butterfly over the nw lanes of each value adds the warps' totals
+  const int per_round = 32 / nw;
+  for (int kb = 0; kb < K; kb += per_round) {
+    const int j = lane / nw, k0 = kb + j;
+    double y = (j < per_round && k0 < K) ? r[k0 * nw + (lane % nw)] : 0.0;
+    for (int o = nw >> 1; o > 0; o >>= 1) y += __shfl_xor_sync(kFull, y, o);
 #pragma unroll
-  for (int k = 0; k < K; ++k) {
-    double s = 0.0;
-    for (int q = 0; q < nw; ++q) s += r[q * K + k];
-    v[k] = s;
+    for (int k = 0; k < K; ++k) {
+      const double t = __shfl_sync(kFull, y, ((k - kb) & 31) * nw & 31);
+      if (k >= kb && k < kb + per_round) v[k] = t;
+    }
   }
 }
 
@@ -64,6 +103,22 @@ __device__ __forceinline__ double cta_sum1(double x, CtaShared& sh, int& par) {
   double v[1] = {x};
   cta_sum<1>(v, sh, par);
   return v[0];
+}
+
+// Sum over the CTA in the working precision S, for the dot products of the two-loop
+// recursion (FP32 in the FP32 form, like the warp kernels' warp sums): lanes by shuffles,
+// then the warp totals in warp order.  Same call discipline as cta_sum.
+template <typename S>
+__device__ __forceinline__ S cta_sum_s(S x, CtaShared& sh, int& par) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  x = warp_sum<S>(x);
+  double* r = sh.red[par];
+  par ^= 1;
+  if (lane == 0) r[warp] = (double)x;  // exact: S is float or double
+  __syncthreads();
+  S s = 0;
+  for (int q = 0; q < nw; ++q) s += (S)r[q];
+  return s;
 }
 
 // Last pass of the second half of the two-loop recursion fused with the line search's
@@ -268,14 +323,15 @@ __device__ CtaEval cta_objective(const DevTypeView<S>& ty, const StepParams& P, 
     if (D) agtd.add_prod(g, D[e]);
     agg.add_prod(g, g);
   }
-  double r[4] = {e_el.part() + e_ct, agtd.part(), agg.part(), degen ? 1.0 : 0.0};
-  cta_sum<4>(r, sh, par);
+  double r[3] = {e_el.part() + e_ct, agtd.part(), agg.part()};
+  const bool any_degen = __syncthreads_or(degen);
+  cta_sum<3>(r, sh, par);
   NPFEM_PHASE_END(t_acc, kPhGather, P, tid)
   CtaEval o;
   o.energy = r[0] + e_area + e_vol;
   o.gtd = r[1];
   o.gg = r[2];
-  o.degenerate = r[3] > 0.0;
+  o.degenerate = any_degen;
   return o;
 }
 
@@ -292,7 +348,7 @@ __device__ __forceinline__ void cta_two_loop_first(const CellWs<S>& w, CellState
   int i = (hh - 1 + kHistory) % kHistory;
   S acc = copy_dot<S>(w.Q, G, w.hs + (size_t)i * len, len, tid, nt);
   for (int q = 0; q < hc; ++q) {
-    const S a = st->rho[i] * (S)cta_sum1((double)acc, sh, par);
+    const S a = st->rho[i] * cta_sum_s<S>(acc, sh, par);
     if (tid == 0) st->aco[i] = a;
     const S* yi = w.hy + (size_t)i * len;
     if (q + 1 < hc) {
@@ -512,7 +568,7 @@ __global__ void __launch_bounds__(32 * kIterCtaMaxWarps, IterCtaOccupancy<S>::mi
           for (int e = tid; e < len; e += nt) acc += yi[e] * w.Q[e];
         }
         for (int q = hcount - 1; q >= 0; --q) {
-          const S b = st->rho[i] * (S)cta_sum1((double)acc, sh, par);
+          const S b = st->rho[i] * cta_sum_s<S>(acc, sh, par);
           const S c = st->aco[i] - b;
           const S* si = w.hs + (size_t)i * len;
           if (q > 0) {

@@ -37,7 +37,6 @@ constexpr size_t kSmemLimit = 72 * 1024;
 static __device__ __align__(256) unsigned char g_npfem_static_scratch[kStaticBytes];
 
 std::mutex g_setup_mutex;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
 
 // Cells 0..ncells-1, cell i owning vertices [i*n, (i+1)*n).
 __global__ void fill_contiguous_layout(int64_t* offsets, int32_t* cells, int ncells, int n) {
@@ -47,14 +46,12 @@ __global__ void fill_contiguous_layout(int64_t* offsets, int32_t* cells, int nce
   }
 }
 
-// Once per device, with that device current: the device address of the static array
+// On every call, with the call's device current: the device address of the static array
 // (its host-side name is only a stand-in) and the shared-memory opt-in of the kernels.
-npfem_status setup_device(int dev, unsigned char** base, std::string* err) {
+// Neither allocates, and neither is cached, so a call after a device reset (a new primary
+// context) finds the array and the kernel attribute of that context.
+npfem_status setup_device(unsigned char** base, std::string* err) {
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (g_scratch_addr[dev]) {
-    *base = g_scratch_addr[dev];
-    return NPFEM_OK;
-  }
   void* p = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&p, g_npfem_static_scratch);
   if (e != cudaSuccess) {
@@ -69,8 +66,7 @@ npfem_status setup_device(int dev, unsigned char** base, std::string* err) {
     *err = std::string("step_noalloc: cudaFuncSetAttribute failed: ") + cudaGetErrorString(e);
     return NPFEM_ERR_CUDA;
   }
-  g_scratch_addr[dev] = static_cast<unsigned char*>(p);
-  *base = g_scratch_addr[dev];
+  *base = static_cast<unsigned char*>(p);
   return NPFEM_OK;
 }
 
@@ -114,7 +110,7 @@ extern "C" npfem_status npfem_step_noalloc(const npfem_cell_type* type, npfem_pr
   if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
     return npfem_internal_fail(NPFEM_ERR_CUDA, "step_noalloc: no usable current device");
   unsigned char* base = nullptr;
-  npfem_status rc = setup_device(dev, &base, &err);
+  npfem_status rc = setup_device(&base, &err);
   if (rc != NPFEM_OK) return npfem_internal_fail(rc, err);
   int sms = 148;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -455,13 +455,13 @@ struct CtaPack {
 // 65536 / (32 W x min_blocks) per thread).  One cell per CTA: the 2-warp CTA of the
 // 642-vertex type holds a 15.4 KB vector, so shared memory admits 13 per SM, and 72
 // registers let registers admit as many (at 96 registers only 10 fit); the wider CTAs
-// keep the residency their shared memory allows for the larger types (6 warps: three
+// keep the residency their shared memory allows for the larger types (6 or 8 warps: three
 // 61.5 KB vectors of a 2562-vertex cell).  Two cells per CTA: shared memory admits 7
 // 2-warp CTAs of the 642-vertex type (2 x 15.4 KB each).
 template <int W, int kCells>
 struct SolveCtaOccupancy {
   static constexpr int min_blocks =
-      kCells == 1 ? (W == 2 ? 13 : (W == 4 ? 5 : (W == 6 ? 3 : 2))) : (W == 2 ? 7 : (W == 4 ? 4 : 1));
+      kCells == 1 ? (W == 2 ? 13 : (W == 4 ? 5 : 3)) : (W == 2 ? 7 : (W == 4 ? 4 : 1));
 };
 
 // Q <- A^-1 Q, one CTA of W warps per kCells cells at a time, for cells whose FP64 solve

@@ -391,7 +391,9 @@ __device__ __forceinline__ void triangle_terms(V3<S> e1, V3<S> e2, V3<S> q0, con
   S c00 = dot(F0, F0), c01 = dot(F0, F1), c11 = dot(F1, F1);
   S det = c00 * c11 - c01 * c01;
   V3<S> P0{0, 0, 0}, P1{0, 0, 0};
-  if ((double)det > kDegenerateDet) {
+  // the threshold in the element's own precision: an FP64 compare per element would load
+  // the FP32 form's FP64 pipe, which the solves need (1e-30 is a normal FP32 number)
+  if (det > (S)kDegenerateDet) {
     V3<S> R0, R1;
     if (mrec) {
       const S m00 = mrec[0], m01 = mrec[1], m11 = mrec[2];
@@ -448,7 +450,7 @@ template <typename S>
 __device__ __forceinline__ V3<S> hinge_terms(V3<S> K, const S* K0row, S we, Acc<S>& e_el) {
   S kn = sqrt(dot(K, K));
   V3<S> p;
-  if ((double)kn < kDegenerateNorm) {
+  if (kn < (S)kDegenerateNorm) {
     p = {__ldg(&K0row[0]), __ldg(&K0row[1]), __ldg(&K0row[2])};
   } else {
     p = (__ldg(&K0row[3]) / kn) * K;

@@ -103,9 +103,9 @@ SplitShape = Tuple[int, int, int, int, int, int, int]
 # Largest resident warps per SM of the solve kernel for 1..4 cells per warp (register
 # use of the four instantiations on sm_103a: 64, 80, 96, 126 registers per thread), and
 # largest resident CTAs per SM of the CTA-cooperative solve kernel per CTA width (2, 4, 6,
-# 8 warps compiled for 72, 95, 96, 128 registers per thread); for two cells per CTA below.
+# 8 warps compiled for 72, 95, 96, 80 registers per thread); for two cells per CTA below.
 SOLVE_MAX_WARPS = {1: 32, 2: 24, 3: 20, 4: 16}
-CTA_MAX_CTAS = {2: 13, 4: 5, 6: 3, 8: 2}
+CTA_MAX_CTAS = {2: 13, 4: 5, 6: 3, 8: 3}
 # two cells per CTA: 90 and 96 registers per thread for 2 and 4 warps
 CTA2_MAX_CTAS = {2: 11, 4: 5}
 

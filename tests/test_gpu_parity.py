@@ -572,6 +572,6 @@ def test_iteration_kernel_widths(prec):
             assert np.array_equal(a, c), w
         for t, sh in shapes.items():
             r.batch.set_split_launch(t, sh)
-    for bad in (-1, 17):
+    for bad in (-1, 3, 6, 17, 32):
         with pytest.raises(nat.NpfemError):
             r.batch.set_iter_width(0, bad)
