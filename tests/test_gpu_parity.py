@@ -157,6 +157,20 @@ def test_stress_mix_sampled_cells():
     compare(b, nat.FP32FORM, cells=cells)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_mixed_10k_batch_sampled_cells(prec):
+    """The mixed 10^4-cell batch of the benchmark (4500 642-vertex RBCs, 4500 2562-vertex
+    RBCs and 1000 platelets in a seeded random order, 3..8 iterations per cell) in its
+    default launch configuration (concurrent chains per type, CTA iteration kernels in
+    the FP32 form): 5 sampled cells of every type against the oracle, positions,
+    velocities, statuses, residuals and (FP64) the accepted step lengths."""
+    nat = _native()
+    b = I.heterogeneous_batch(4500, 4500, 1000, seed=1002)
+    rng = np.random.default_rng(13)
+    cells = sorted(int(c) for t in range(3) for c in rng.choice(np.flatnonzero(b.type_of_cell == t), 5, replace=False))
+    compare(b, nat.FP64 if prec == "fp64" else nat.FP32FORM, cells=cells)
+
+
 def test_heterogeneous_types_and_iterations():
     nat = _native()
     b = I.heterogeneous_batch(n_rbc3=6, n_rbc4=3, n_plt=5, seed=1002)
