@@ -303,6 +303,14 @@ npfem_status npfem_batch_set_mode(npfem_batch* batch, int32_t mode);
  * the batch, 2 from 2048, else 1.  Results do not depend on the grouping.
  * NPFEM_ERR_INVALID_ARG for groups outside 1..4 or a type without cells in the batch. */
 npfem_status npfem_batch_set_groups(npfem_batch* batch, int32_t type_index, int32_t groups);
+
+/* Split mode with several chains (cell types or groups): enable != 0 launches every
+ * chain's FP64 solves on a stream of their own at the highest stream priority, the rest
+ * of the chain at the lowest, ordered by events (so pending solve CTAs take SM slots
+ * first as they free up).  Default on; enable = 0 keeps each chain on one stream.
+ * Results do not change.  The streams are created on the next uncaptured step.
+ * Synchronises the device. */
+npfem_status npfem_batch_set_solve_streams(npfem_batch* batch, int32_t enable);
 npfem_status npfem_batch_get_groups(const npfem_batch* batch, int32_t type_index, int32_t* groups);
 
 /* Split mode: iteration kernels of type type_index (the prediction with the first
@@ -328,11 +336,15 @@ npfem_status npfem_batch_get_iter_width(const npfem_batch* batch, int32_t type_i
 npfem_status npfem_batch_set_split_launch(npfem_batch* batch, int32_t type_index, const int32_t* shape);
 npfem_status npfem_batch_get_split_launch(const npfem_batch* batch, int32_t type_index, int32_t* shape);
 
-/* Per-phase telemetry of the batch's steps since creation or the last reset: SM
- * clock cycles summed over all warps, in the order prediction, objective evaluation,
- * two-loop recursion, global FP64 solve, history update, write-back, and (contained
- * in the objective) the area/volume pass and the gradient gather.  Synchronises the
- * device.  cycles: host array of 8; reset != 0 zeroes the counters after reading. */
+/* Per-phase telemetry of the batch's steps since creation or the last reset, counted
+ * only while npfem_batch_set_phase_counting(batch, 1) is in effect (off by default: the
+ * kernels then skip the per-phase atomics): SM clock cycles summed over all warps (the
+ * CTA iteration kernels: over CTAs), in the order prediction, objective evaluation,
+ * two-loop recursion, global FP64 solve, history update, write-back, and (contained in
+ * the objective) the area/volume pass and the gradient assembly (gather, or the colour
+ * passes of the CTA kernels).  npfem_batch_phase_cycles synchronises the device;
+ * cycles: host array of 8; reset != 0 zeroes the counters after reading. */
+npfem_status npfem_batch_set_phase_counting(npfem_batch* batch, int32_t enable);
 npfem_status npfem_batch_phase_cycles(npfem_batch* batch, uint64_t* cycles, int32_t reset);
 
 /* Per-kernel timing of split-mode steps with CUDA events recorded on the stream each

@@ -78,6 +78,7 @@ struct npfem_batch {
   std::vector<TypeLaunch> launches;
   int* d_counters = nullptr;
   unsigned long long* d_phase = nullptr;  // [kPhases] per-phase cycle counters
+  bool phase_counting = false;            // kernels add to d_phase only when set
   int sms = 148, smem_optin = 0;
   int mode = 1;  // 0: fused persistent kernel, 1: split kernels (k_begin, k_solve, k_iter)
   // split mode with several cell types: one internal stream per type, forked from and
@@ -85,6 +86,12 @@ struct npfem_batch {
   std::vector<cudaStream_t> type_streams;
   std::vector<cudaEvent_t> type_events;
   cudaEvent_t fork_event = nullptr;
+  // solve_streams: the chains' solve launches on streams of their own at the highest
+  // priority (the rest of a chain at the lowest), ordered with the chain by two events per
+  // chain (to_solve[c]: the chain's work before a solve; from_solve[c]: the solve)
+  bool solve_streams_on = true;  // measured: mixed 10^4 batch -1.9 %, 20 000-cell mix -5.4 % per step
+  std::vector<cudaStream_t> solve_streams;
+  std::vector<cudaEvent_t> to_solve, from_solve;
   // optional per-launch kernel timing in split mode: a (start, end) event pair around
   // every launch, per chain (type launch x group) and launch slot (0: k_begin, 1 + 2i:
   // k_solve of iteration i, 2 + 2i: k_iter of iteration i), re-recorded by every step
@@ -101,6 +108,9 @@ struct npfem_batch {
     if (d2h_stream) cudaStreamDestroy(d2h_stream);
     for (cudaStream_t s : type_streams) cudaStreamDestroy(s);
     for (cudaEvent_t e : type_events) cudaEventDestroy(e);
+    for (cudaStream_t s : solve_streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : to_solve) cudaEventDestroy(e);
+    for (cudaEvent_t e : from_solve) cudaEventDestroy(e);
     if (fork_event) cudaEventDestroy(fork_event);
     for (cudaEvent_t e : det_ev)
       if (e) cudaEventDestroy(e);
@@ -603,7 +613,7 @@ static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_e
     NPFEM_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
     if (!b->fork_event) NPFEM_CUDA_TRY(cudaEventCreateWithFlags(&b->fork_event, cudaEventDisableTiming));
     for (size_t c = 0; c < nc; ++c) {
-      const int want = chains[c].li == heavy ? greatest : least;
+      const int want = b->solve_streams_on ? least : (chains[c].li == heavy ? greatest : least);
       if (c < b->type_streams.size()) {
         int have = 0;
         NPFEM_CUDA_TRY(cudaStreamGetPriority(b->type_streams[c], &have));
@@ -623,7 +633,21 @@ static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_e
         b->type_events.push_back(e2);
       }
     }
+    while (b->solve_streams_on && b->solve_streams.size() < nc) {
+      if (cs != cudaStreamCaptureStatusNone)
+        return fail(NPFEM_ERR_INVALID_ARG,
+                    "split step: first step of this batch configuration under stream capture; run it once uncaptured");
+      cudaStream_t s2;
+      cudaEvent_t e1, e2;
+      NPFEM_CUDA_TRY(cudaStreamCreateWithPriority(&s2, cudaStreamNonBlocking, greatest));
+      NPFEM_CUDA_TRY(cudaEventCreateWithFlags(&e1, cudaEventDisableTiming));
+      NPFEM_CUDA_TRY(cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+      b->solve_streams.push_back(s2);
+      b->to_solve.push_back(e1);
+      b->from_solve.push_back(e2);
+    }
   }
+  const bool split_solve = fork && b->solve_streams_on;
   if (b->ktiming && b->k_last_slots.size() < nc) {
     return fail(NPFEM_ERR_INVALID_ARG, "split step: kernel timing was enabled for fewer chains; enable it again");
   }
@@ -644,13 +668,18 @@ static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_e
   P.iters_done = opts->iters_done;
   P.alpha_log = opts->alpha_log;
   P.alpha_log_len = opts->alpha_log_len;
-  P.phase_cycles = b->d_phase;
+  P.phase_cycles = b->phase_counting ? b->d_phase : nullptr;
   set_contact_params(b, P, x);
   auto launch = [&](size_t c, int kind, int it, int slot) -> npfem_status {
     const Chain& C = chains[c];
     const TypeLaunch& L = b->launches[C.li];
     const npfem_cell_type* t = b->types[L.type_index];
     cudaStream_t cs = fork ? b->type_streams[c] : st;
+    if (split_solve && kind == 1) {  // the solve on the chain's solve stream, after the chain's work
+      NPFEM_CUDA_TRY(cudaEventRecord(b->to_solve[c], cs));
+      cs = b->solve_streams[c];
+      NPFEM_CUDA_TRY(cudaStreamWaitEvent(cs, b->to_solve[c], 0));
+    }
     cudaEvent_t* ke = b->ktiming ? &b->kev[(c * kTimingSlots + slot) * 2] : nullptr;
     if (ke) NPFEM_CUDA_TRY(record_timing_event(ke[0], cs));
     npfem_status rc;
@@ -662,6 +691,10 @@ static npfem_status step_split(npfem_batch* b, void* x, void* v, const void* f_e
                                static_cast<const float*>(f_ext), t->v32, cs);
     if (rc != NPFEM_OK) return rc;
     if (ke) NPFEM_CUDA_TRY(record_timing_event(ke[1], cs));
+    if (split_solve && kind == 1) {  // the rest of the chain after the solve
+      NPFEM_CUDA_TRY(cudaEventRecord(b->from_solve[c], cs));
+      NPFEM_CUDA_TRY(cudaStreamWaitEvent(b->type_streams[c], b->from_solve[c], 0));
+    }
     return NPFEM_OK;
   };
   // Staggered groups (one cell type): group g starts when group g-1's k_begin is done, so
@@ -1022,7 +1055,7 @@ npfem_status npfem_step(npfem_batch* b, void* x, void* v, const void* f_ext, con
     P.slot_bytes = L.slot_bytes;
     P.z_in_smem = L.z_in_smem;
     P.solve_per_coord = L.solve_per_coord;
-    P.phase_cycles = b->d_phase;
+    P.phase_cycles = b->phase_counting ? b->d_phase : nullptr;
     set_contact_params(b, P, x);
     dim3 grid(L.blocks), block(32 * L.warps_per_block);
     if (b->prec == NPFEM_FP64)
@@ -1097,7 +1130,7 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     P.slot_bytes = L.slot_bytes;
     P.z_in_smem = L.z_in_smem;
     P.solve_per_coord = L.solve_per_coord;
-    P.phase_cycles = b->d_phase;
+    P.phase_cycles = b->phase_counting ? b->d_phase : nullptr;
     AdjParams A;
     A.gx_next = gx_next;
     A.gv_next = gv_next;
@@ -1311,7 +1344,7 @@ npfem_status npfem_step_adjoint_implicit(npfem_batch* b, const void* x, const vo
     P.slot_bytes = L.slot_bytes;
     P.z_in_smem = L.z_in_smem;
     P.solve_per_coord = L.solve_per_coord;
-    P.phase_cycles = b->d_phase;
+    P.phase_cycles = b->phase_counting ? b->d_phase : nullptr;
     ImplicitParams A{};
     A.x_n = static_cast<const double*>(x);
     A.x_star = b->d_xstar;
@@ -1411,6 +1444,12 @@ npfem_status npfem_batch_get_split_launch(const npfem_batch* b, int32_t type_ind
       return NPFEM_OK;
     }
   return fail(NPFEM_ERR_INVALID_ARG, "batch_get_split_launch: no cells of that type in the batch");
+}
+
+npfem_status npfem_batch_set_phase_counting(npfem_batch* b, int32_t enable) {
+  if (!b) return fail(NPFEM_ERR_INVALID_ARG, "batch_set_phase_counting: null batch");
+  b->phase_counting = enable != 0;
+  return NPFEM_OK;
 }
 
 npfem_status npfem_batch_phase_cycles(npfem_batch* b, uint64_t* cycles, int32_t reset) {
@@ -1528,6 +1567,13 @@ npfem_status npfem_batch_get_groups(const npfem_batch* b, int32_t type_index, in
       return NPFEM_OK;
     }
   return fail(NPFEM_ERR_INVALID_ARG, "batch_get_groups: no cells of that type in the batch");
+}
+
+npfem_status npfem_batch_set_solve_streams(npfem_batch* b, int32_t enable) {
+  if (!b) return fail(NPFEM_ERR_INVALID_ARG, "batch_set_solve_streams: null batch");
+  NPFEM_CUDA_TRY(cudaDeviceSynchronize());
+  b->solve_streams_on = enable != 0;
+  return NPFEM_OK;
 }
 
 npfem_status npfem_batch_set_iter_width(npfem_batch* b, int32_t type_index, int32_t warps) {

@@ -59,13 +59,14 @@ struct StepParams {
   unsigned long long* phase_cycles;  // [kPhases] per-phase SM cycles summed over warps
 };
 
-// Per-phase cycle telemetry: each warp adds the SM clock cycles it spent in a phase
-// to a batch-owned counter (one relaxed 64-bit atomic by lane 0 per phase instance).
+// Per-phase cycle telemetry (when the batch counts phases, P.phase_cycles non-null): each
+// warp (CTA) adds the SM clock cycles it spent in a phase to a batch-owned counter (one
+// relaxed 64-bit atomic by lane (thread) 0 per phase instance).
 enum Phase { kPhPredict = 0, kPhObjective, kPhTwoLoop, kPhSolve, kPhHistory, kPhWrite, kPhAreaVolume, kPhGather,
              kPhases = 8 };
 #define NPFEM_PHASE_BEGIN(var) const long long var = clock64();
 #define NPFEM_PHASE_END(var, ph, P, lane) \
-  if ((lane) == 0) atomicAdd(&(P).phase_cycles[ph], (unsigned long long)(clock64() - (var)));
+  if ((lane) == 0 && (P).phase_cycles) atomicAdd(&(P).phase_cycles[ph], (unsigned long long)(clock64() - (var)));
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll

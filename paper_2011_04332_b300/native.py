@@ -89,6 +89,8 @@ def load_library() -> C.CDLL:
         "npfem_batch_kernel_spans": [vp, C.c_int32, C.POINTER(C.c_double)],
         "npfem_batch_get_groups": [vp, C.c_int32, C.POINTER(C.c_int32)],
         "npfem_batch_set_iter_width": [vp, C.c_int32, C.c_int32],
+        "npfem_batch_set_phase_counting": [vp, C.c_int32],
+        "npfem_batch_set_solve_streams": [vp, C.c_int32],
         "npfem_batch_get_iter_width": [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
         "npfem_batch_kernel_times": [vp, C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_int32)],
         "npfem_batch_set_mode": [vp, C.c_int32],
@@ -380,6 +382,14 @@ class Batch:
                 "solve_per_coord": bool(out[3]), "grid": out[4]}
 
     PHASES = ("predict", "objective", "two_loop", "solve", "history", "write", "area_volume", "gather")
+
+    def set_solve_streams(self, enable: bool = True) -> None:
+        """npfem_batch_set_solve_streams: solves of every chain on high-priority streams."""
+        _check(_lib.npfem_batch_set_solve_streams(self.handle, int(enable)))
+
+    def set_phase_counting(self, enable: bool = True) -> None:
+        """npfem_batch_set_phase_counting: per-phase cycle counters on (off by default)."""
+        _check(_lib.npfem_batch_set_phase_counting(self.handle, int(enable)))
 
     def phase_cycles(self, reset: bool = False) -> dict:
         """npfem_batch_phase_cycles: SM cycles per phase summed over warps (synchronises)."""

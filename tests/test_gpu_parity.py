@@ -268,13 +268,24 @@ def test_rollout_tracks_oracle():
     assert cell_errors(b, x, xo).max() < 1e-8
 
 
-def test_phase_cycle_telemetry():
-    """Per-phase cycle counters accumulate over steps and reset on request."""
+@pytest.mark.parametrize("width", [None, 0])
+def test_phase_cycle_telemetry(width):
+    """Per-phase cycle counters are off by default (a step adds nothing), and once
+    switched on accumulate over steps and reset on request; for the CTA iteration
+    kernels (default width) and the one-warp kernels (width 0), with bit-identical
+    states whether counting or not."""
     nat = _native()
     b = I.homogeneous_rbc_batch(ncells=8, seed=11)
     r = Runner(b, nat.FP32FORM)
+    if width is not None:
+        r.batch.set_iter_width(0, width)
     r.batch.phase_cycles(reset=True)
-    r.step(b.x, b.v, b.f)
+    plain = r.step(b.x, b.v, b.f)
+    assert all(v == 0 for v in r.batch.phase_cycles().values())
+    r.batch.set_phase_counting(True)
+    counted = r.step(b.x, b.v, b.f)
+    for a, c_ in zip(plain, counted):
+        assert np.array_equal(a, c_)
     c = r.batch.phase_cycles(reset=True)
     assert c["solve"] > 0 and c["objective"] > 0 and c["two_loop"] > 0 and c["write"] > 0
     assert c["gather"] < c["objective"] and c["area_volume"] < c["objective"]
@@ -514,8 +525,8 @@ def test_cta_cooperative_shape_validation():
 def test_groups_leave_results_unchanged(prec):
     """Cells of a type split into 2..4 phase-offset chains (their solves take turns, their
     iteration kernels overlap the other groups' solves) give the one-group results bit
-    for bit, directly and replayed from a captured CUDA graph; groups outside 1..4 are
-    rejected."""
+    for bit, with the solves on high-priority streams of their own or not, directly and
+    replayed from a captured CUDA graph; groups outside 1..4 are rejected."""
     nat = _native()
     b = I.heterogeneous_batch(n_rbc3=9, n_rbc4=3, n_plt=7, seed=1009)
     p = nat.FP64 if prec == "fp64" else nat.FP32FORM
@@ -526,6 +537,12 @@ def test_groups_leave_results_unchanged(prec):
             r.batch.set_groups(t, groups)
             assert r.batch.get_groups(t) == groups
         out = r.step(b.x, b.v, b.f, iters=b.iters)
+        for a, c in zip(ref, out):
+            assert np.array_equal(a, c)
+        # the chains' solves on streams of their own (default) or on the chains' streams
+        r.batch.set_solve_streams(False)
+        out = r.step(b.x, b.v, b.f, iters=b.iters)
+        r.batch.set_solve_streams(True)
         for a, c in zip(ref, out):
             assert np.array_equal(a, c)
     dev = torch.device("cuda:0")
