@@ -307,7 +307,8 @@ npfem_status npfem_batch_set_groups(npfem_batch* batch, int32_t type_index, int3
 /* Split mode with several chains (cell types or groups): enable != 0 launches every
  * chain's FP64 solves on a stream of their own at the highest stream priority, the rest
  * of the chain at the lowest, ordered by events (so pending solve CTAs take SM slots
- * first as they free up).  Default on; enable = 0 keeps each chain on one stream.
+ * first as they free up).  Default on in the FP32 form, off in FP64 (whose iteration
+ * kernels need the FP64 pipe as much); enable = 0 keeps each chain on one stream.
  * Results do not change.  The streams are created on the next uncaptured step.
  * Synchronises the device. */
 npfem_status npfem_batch_set_solve_streams(npfem_batch* batch, int32_t enable);

@@ -89,7 +89,9 @@ struct npfem_batch {
   // solve_streams: the chains' solve launches on streams of their own at the highest
   // priority (the rest of a chain at the lowest), ordered with the chain by two events per
   // chain (to_solve[c]: the chain's work before a solve; from_solve[c]: the solve)
-  bool solve_streams_on = true;  // measured: mixed 10^4 batch -1.9 %, 20 000-cell mix -5.4 % per step
+  // solve streams: on in the FP32 form (mixed 10^4 batch -1.9 %, 20 000-cell mix -5.4 % per
+  // step), off in the FP64 form, whose iteration kernels are FP64 bound too (+11 %)
+  bool solve_streams_on = true;
   std::vector<cudaStream_t> solve_streams;
   std::vector<cudaEvent_t> to_solve, from_solve;
   // optional per-launch kernel timing in split mode: a (start, end) event pair around
@@ -920,6 +922,7 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
   b->type_of_cell.assign(type_of_cell, type_of_cell + ncells);
   b->ncells = ncells;
   b->prec = prec;
+  b->solve_streams_on = prec != NPFEM_FP64;
   b->offsets.assign(ncells + 1, 0);
   for (int c = 0; c < ncells; ++c) b->offsets[c + 1] = b->offsets[c] + types[type_of_cell[c]]->host.n;
   b->n_total = b->offsets[ncells];
