@@ -335,28 +335,39 @@ __device__ CtaEval cta_objective(const DevTypeView<S>& ty, const StepParams& P, 
   return o;
 }
 
-// First half of the two-loop recursion by the CTA: Q = G, newest -> oldest pairs (the
-// pass structure of two_loop_first, with CTA-wide dot products).
+// First half of the two-loop recursion by the CTA: Q = g, newest -> oldest pairs (the
+// pass structure of two_loop_first, with CTA-wide dot products), run in place on the shared
+// gradient Gs (not needed afterwards): the vector stays on chip through the passes and the
+// last pass writes Q to the workspace for the solve.  Every thread updates only its own
+// elements (e = tid + k nt in every pass), so the passes need no barrier of their own.
+// newest_dot: when non-null, this thread's partial sum of s . g for the newest pair,
+// already accumulated (in the same order) by the history update that wrote the pair.
 template <typename S>
-__device__ __forceinline__ void cta_two_loop_first(const CellWs<S>& w, CellState<S>* st, int hc, int hh, const S* G,
-                                                   int len, CtaShared& sh, int& par) {
+__device__ __forceinline__ void cta_two_loop_first(const CellWs<S>& w, CellState<S>* st, int hc, int hh, S* Gs,
+                                                   int len, CtaShared& sh, int& par, const S* newest_dot) {
   const int tid = threadIdx.x, nt = blockDim.x;
   if (hc == 0) {
-    for (int e = tid; e < len; e += nt) w.Q[e] = G[e];
+    for (int e = tid; e < len; e += nt) w.Q[e] = Gs[e];
     return;
   }
   int i = (hh - 1 + kHistory) % kHistory;
-  S acc = copy_dot<S>(w.Q, G, w.hs + (size_t)i * len, len, tid, nt);
+  S acc = 0;
+  if (newest_dot) {
+    acc = *newest_dot;
+  } else {
+    const S* si = w.hs + (size_t)i * len;
+    for (int e = tid; e < len; e += nt) acc += si[e] * Gs[e];
+  }
   for (int q = 0; q < hc; ++q) {
     const S a = st->rho[i] * cta_sum_s<S>(acc, sh, par);
     if (tid == 0) st->aco[i] = a;
     const S* yi = w.hy + (size_t)i * len;
     if (q + 1 < hc) {
       const int inext = (hh - 1 - (q + 1) + kHistory) % kHistory;
-      acc = update_dot<S>(w.Q, -a, yi, w.hs + (size_t)inext * len, len, tid, nt);
+      acc = update_dot<S>(Gs, -a, yi, w.hs + (size_t)inext * len, len, tid, nt);
       i = inext;
     } else {
-      for (int e = tid; e < len; e += nt) w.Q[e] -= a * yi[e];
+      for (int e = tid; e < len; e += nt) w.Q[e] = Gs[e] - a * yi[e];
     }
   }
 }
@@ -561,11 +572,17 @@ __global__ void __launch_bounds__(32 * kIterCtaMaxWarps, IterCtaOccupancy<S>::mi
           Us[e] = ut;
         }
       } else {
+        // r = A^-1 q from the solve is staged in the shared Gs (free until the line search)
+        // by the first pass, and the passes update it there
         int i = (hhead - hcount + kHistory) % kHistory;
         S acc = 0;
         {
           const S* yi = w.hy + (size_t)i * len;
-          for (int e = tid; e < len; e += nt) acc += yi[e] * w.Q[e];
+          for (int e = tid; e < len; e += nt) {
+            const S qe = w.Q[e];
+            Gs[e] = qe;
+            acc += yi[e] * qe;
+          }
         }
         for (int q = hcount - 1; q >= 0; --q) {
           const S b = st->rho[i] * cta_sum_s<S>(acc, sh, par);
@@ -573,10 +590,10 @@ __global__ void __launch_bounds__(32 * kIterCtaMaxWarps, IterCtaOccupancy<S>::mi
           const S* si = w.hs + (size_t)i * len;
           if (q > 0) {
             const int inext = (hhead - 1 - (q - 1) + kHistory) % kHistory;
-            acc = update_dot<S>(w.Q, c, si, w.hy + (size_t)inext * len, len, tid, nt);
+            acc = update_dot<S>(Gs, c, si, w.hy + (size_t)inext * len, len, tid, nt);
             i = inext;
           } else {
-            cta_negate_trial<S>(w.Q, c, si, G, U, w.D, UT, Us, agd, len, tid, nt);
+            cta_negate_trial<S>(Gs, c, si, G, U, w.D, UT, Us, agd, len, tid, nt);
           }
         }
       }
@@ -632,19 +649,22 @@ __global__ void __launch_bounds__(32 * kIterCtaMaxWarps, IterCtaOccupancy<S>::mi
     NPFEM_PHASE_BEGIN(t_hist)
     S new_rho = (S)0;
     bool keep = false;
+    S sg = 0;  // this thread's part of s . g, the first dot of the next first half if the pair is kept
     if (k < iters - 1 && !stop) {
       // the accepted trial is in Us and Gs: s = UT - U, y = GT - G
       S* si = w.hs + (size_t)hhead * len;
       S* yi = w.hy + (size_t)hhead * len;
       Acc<S> asy, ass, ayy;
       for (int e = tid; e < len; e += nt) {
+        const S g = Gs[e];
         const S s = Us[e] - U[e];
-        const S y = Gs[e] - G[e];
+        const S y = g - G[e];
         si[e] = s;
         yi[e] = y;
         asy.add_prod(s, y);
         ass.add_prod(s, s);
         ayy.add_prod(y, y);
+        sg += s * g;
       }
       double r3[3] = {asy.part(), ass.part(), ayy.part()};
       cta_sum<3>(r3, sh, par);
@@ -675,7 +695,7 @@ __global__ void __launch_bounds__(32 * kIterCtaMaxWarps, IterCtaOccupancy<S>::mi
     if (k + 1 < iters && !stop) {
       if (tid == 0) P.act_out[atomicAdd(P.act_count_out, 1)] = item;
       NPFEM_PHASE_BEGIN(t_loop1)
-      cta_two_loop_first<S>(w, st, hcount, hhead, Gs, len, sh, par);
+      cta_two_loop_first<S>(w, st, hcount, hhead, Gs, len, sh, par, keep ? &sg : nullptr);
       NPFEM_PHASE_END(t_loop1, kPhTwoLoop, P, tid)
     } else {
       cta_finalize<S>(ty, P, st, Xs, Us, gg, cell, k + 1, x, v);
