@@ -347,12 +347,33 @@ template <typename S>
 __device__ __forceinline__ void strain_limit_pass(const DevTypeView<S>& ty, const S* X, const S* U, S* corner,
                                                int lane, int stride = 32) {
   const double s_min = ty.s_min, s_max = ty.s_max;
+  // margin of the inside test below, far above the rounding of its working precision
+  const S lo2 = (S)(s_min * s_min * (1.0 + (sizeof(S) == 4 ? 1e-4 : 1e-12)));
+  const S hi2 = (S)(s_max * s_max * (1.0 - (sizeof(S) == 4 ? 1e-4 : 1e-12)));
   for (int t = lane; t < ty.T; t += stride) {
     int i0 = __ldg(&ty.tris[3 * t]), i1 = __ldg(&ty.tris[3 * t + 1]), i2 = __ldg(&ty.tris[3 * t + 2]);
     V3<S> e1 = edge(X, U, i0, i1), e2 = edge(X, U, i0, i2);
     const S d00 = __ldg(&ty.Dinv[3 * t]), d01 = __ldg(&ty.Dinv[3 * t + 1]), d11 = __ldg(&ty.Dinv[3 * t + 2]);
     V3<S> F0 = d00 * e1;
     V3<S> F1 = d01 * e1 + d11 * e2;
+    {
+      // Both squared singular values clearly inside [s_min^2, s_max^2]: the clamp changes
+      // nothing, k1 = k2 = 1 and the projector below yields M = I exactly, so it is skipped.
+      // The test runs in the working precision (for the FP32 form an FP32 test instead of
+      // an FP64 eigen-decomposition per triangle); near a limit, or for a degenerate F
+      // (NaN or infinite quotient), the FP64 projector decides.
+      const S c00s = dot(F0, F0), c01s = dot(F0, F1), c11s = dot(F1, F1);
+      const S hs = (S)0.5 * (c00s + c11s), qs = (S)0.5 * (c00s - c11s);
+      const S l1s = hs + sqrt(qs * qs + c01s * c01s);
+      const V3<S> xs = cross(F0, F1);
+      const S l2s = dot(xs, xs) / l1s;
+      if (l2s > lo2 && l1s < hi2) {
+        corner[9 * t] = (S)1;
+        corner[9 * t + 1] = (S)0;
+        corner[9 * t + 2] = (S)1;
+        continue;
+      }
+    }
     const double a0 = F0.x, a1 = F0.y, a2 = F0.z, b0 = F1.x, b1 = F1.y, b2 = F1.z;
     const double c00 = a0 * a0 + a1 * a1 + a2 * a2;
     const double c01 = a0 * b0 + a1 * b1 + a2 * b2;
