@@ -135,6 +135,10 @@ typedef struct {
   int64_t nnz_factor;      /* off-diagonal nonzeros of the unit lower factor */
   int64_t solve_chunks;    /* 32-entry chunks per triangular solve */
   double rest_area, rest_volume, total_mass;
+  /* colour classes of the triangles and of the hinges (no two elements of a class share a
+   * vertex; the CTA iteration kernels visit them class by class), 0 when the mesh needs
+   * more than 64 (the type then runs the one-warp iteration kernels) */
+  int32_t tri_colours, hinge_colours;
 } npfem_type_info;
 
 /* Build a cell type once: rest geometry, lumped masses, the global matrix A and

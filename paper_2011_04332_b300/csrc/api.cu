@@ -879,6 +879,8 @@ npfem_status npfem_cell_type_info(const npfem_cell_type* t, npfem_type_info* inf
   info->rest_area = H.A0;
   info->rest_volume = H.V0;
   info->total_mass = H.total_mass;
+  info->tri_colours = H.tri_cptr.empty() ? 0 : (int32_t)H.tri_cptr.size() - 1;
+  info->hinge_colours = H.hinge_cptr.empty() ? 0 : (int32_t)H.hinge_cptr.size() - 1;
   return NPFEM_OK;
 }
 
@@ -902,6 +904,8 @@ npfem_status npfem_cell_type_analyze(const npfem_mesh* mesh, const npfem_materia
   info->rest_area = H.A0;
   info->rest_volume = H.V0;
   info->total_mass = H.total_mass;
+  info->tri_colours = H.tri_cptr.empty() ? 0 : (int32_t)H.tri_cptr.size() - 1;
+  info->hinge_colours = H.hinge_cptr.empty() ? 0 : (int32_t)H.hinge_cptr.size() - 1;
   return NPFEM_OK;
 }
 

@@ -71,6 +71,16 @@ bool colour_elements(int n, int k, std::vector<int32_t>* elems, std::vector<int3
     const int p = next[colour[e]]++;
     for (int j = 0; j < k; ++j) out[(size_t)k * p + j] = (*elems)[(size_t)k * e + j];
   }
+  // the invariant the CTA kernels rely on, checked as built: within a class, every vertex
+  // occurs at most once
+  std::vector<int> seen(n, -1);
+  for (size_t c = 0; c + 1 < cptr->size(); ++c)
+    for (int e = (*cptr)[c]; e < (*cptr)[c + 1]; ++e)
+      for (int j = 0; j < k; ++j) {
+        const int v = out[(size_t)k * e + j];
+        if (seen[v] == (int)c) return false;
+        seen[v] = (int)c;
+      }
   elems->swap(out);
   return true;
 }

@@ -81,6 +81,18 @@ def icosahedron() -> Mesh:
     return _orient_outward(Mesh(v, t, "icosahedron"))
 
 
+def bipyramid(m: int, radius: float = 2.0, height: float = 1.0) -> Mesh:
+    """Closed bipyramid over an m-gon: m equator vertices and two poles, each pole in m
+    triangles (a mesh whose vertex valence exceeds any small number of colour classes)."""
+    th = 2.0 * np.pi * np.arange(m) / m
+    v = np.concatenate([np.stack([radius * np.cos(th), radius * np.sin(th), np.zeros(m)], axis=1),
+                        [[0.0, 0.0, height], [0.0, 0.0, -height]]])
+    i = np.arange(m)
+    north = np.stack([i, (i + 1) % m, np.full(m, m)], axis=1)
+    south = np.stack([(i + 1) % m, i, np.full(m, m + 1)], axis=1)
+    return _orient_outward(Mesh(v, np.concatenate([north, south]).astype(np.int32), f"bipyramid{m}"))
+
+
 def _orient_outward(m: Mesh) -> Mesh:
     """Flip every face whose normal points towards the centroid (convex base solids only)."""
     v, t = m.verts, m.tris.copy()

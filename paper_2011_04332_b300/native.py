@@ -55,7 +55,8 @@ class _CollisionParams(C.Structure):
 class _TypeInfo(C.Structure):
     _fields_ = [("n_verts", C.c_int32), ("n_tris", C.c_int32), ("n_hinges", C.c_int32),
                 ("nnz_factor", C.c_int64), ("solve_chunks", C.c_int64),
-                ("rest_area", C.c_double), ("rest_volume", C.c_double), ("total_mass", C.c_double)]
+                ("rest_area", C.c_double), ("rest_volume", C.c_double), ("total_mass", C.c_double),
+                ("tri_colours", C.c_int32), ("hinge_colours", C.c_int32)]
 
 
 _lib = None

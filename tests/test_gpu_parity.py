@@ -171,6 +171,22 @@ def test_mixed_10k_batch_sampled_cells(prec):
     compare(b, nat.FP64 if prec == "fp64" else nat.FP32FORM, cells=cells)
 
 
+def test_uncoloured_type_runs_the_warp_kernels():
+    """A type whose mesh would need more than 64 colour classes (a 70-gon bipyramid, 70
+    triangles at each pole) has no CTA iteration kernels: its width is 0, setting one is
+    refused, and its cells (FP32 form, beside a coloured RBC type on the CTA kernels) match
+    the oracle."""
+    nat = _native()
+    types = [I.CellTypeSpec(I.bipyramid(70), I.RBC_MATERIAL), I.CellTypeSpec(I.rbc_mesh(2), I.RBC_MATERIAL)]
+    b = I.placed_cells(types, [0, 1, 0, 1, 0], 1012, 4)
+    r = Runner(b, nat.FP32FORM)
+    assert r.batch.get_iter_width(0) == (0, 0) and r.batch.get_iter_width(1)[0] == 4
+    with pytest.raises(nat.NpfemError):
+        r.batch.set_iter_width(0, 4)
+    compare(b, nat.FP32FORM, steps=2)
+    compare(b, nat.FP64)
+
+
 def test_heterogeneous_types_and_iterations():
     nat = _native()
     b = I.heterogeneous_batch(n_rbc3=6, n_rbc4=3, n_plt=5, seed=1002)
