@@ -180,7 +180,7 @@ def test_uncoloured_type_runs_the_warp_kernels():
     types = [I.CellTypeSpec(I.bipyramid(70), I.RBC_MATERIAL), I.CellTypeSpec(I.rbc_mesh(2), I.RBC_MATERIAL)]
     b = I.placed_cells(types, [0, 1, 0, 1, 0], 1012, 4)
     r = Runner(b, nat.FP32FORM)
-    assert r.batch.get_iter_width(0) == (0, 0) and r.batch.get_iter_width(1)[0] == 4
+    assert r.batch.get_iter_width(0) == (0, 0) and r.batch.get_iter_width(1)[0] == 2   # 162 vertices
     with pytest.raises(nat.NpfemError):
         r.batch.set_iter_width(0, 4)
     compare(b, nat.FP32FORM, steps=2)
