@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <map>
 #include <numeric>
+#include <functional>
 #include <set>
 #include <utility>
 
@@ -216,6 +217,191 @@ std::vector<V3> cut_directions() {
     v = {v.x / l, v.y / l, v.z / l};
   }
   return d;
+}
+
+// Smallest vertex separator along the cut edges of a two-sided split: a minimum vertex
+// cover of the bipartite graph of cut edges.  By König's theorem, with a maximum matching
+// M and Z the vertices reachable from unmatched lower-side vertices by alternating paths,
+// the cover is (lower \ Z) ∪ (upper ∩ Z).  side[v]: 0 lower, 1 upper, 2 outside this
+// subproblem; `pos` is scratch of size n, all -1 on entry and on return.
+std::vector<int> cut_cover(const Graph& g, const std::vector<char>& side, const std::vector<int>& idx,
+                           std::vector<int>& pos) {
+  std::vector<int> A, B;
+  for (int v : idx) {
+    bool cut = false;
+    for (int u : g[v])
+      if (side[u] == 1 - side[v]) {
+        cut = true;
+        break;
+      }
+    if (cut) {
+      std::vector<int>& s = side[v] == 0 ? A : B;
+      pos[v] = (int)s.size();
+      s.push_back(v);
+    }
+  }
+  std::vector<int> aptr(A.size() + 1, 0), adj;
+  for (size_t a = 0; a < A.size(); ++a) {
+    for (int u : g[A[a]])
+      if (side[u] == 1) adj.push_back(pos[u]);
+    aptr[a + 1] = (int)adj.size();
+  }
+  std::vector<int> mate_a(A.size(), -1), mate_b(B.size(), -1);
+  std::vector<char> seen;
+  // Kuhn's augmenting-path search from lower vertex a.
+  std::function<bool(int)> augment = [&](int a) -> bool {
+    for (int q = aptr[a]; q < aptr[a + 1]; ++q) {
+      const int b = adj[q];
+      if (seen[b]) continue;
+      seen[b] = 1;
+      if (mate_b[b] < 0 || augment(mate_b[b])) {
+        mate_a[a] = b;
+        mate_b[b] = a;
+        return true;
+      }
+    }
+    return false;
+  };
+  for (size_t a = 0; a < A.size(); ++a) {
+    seen.assign(B.size(), 0);
+    augment((int)a);
+  }
+  std::vector<char> za(A.size(), 0), zb(B.size(), 0);
+  std::vector<int> stack;
+  for (size_t a = 0; a < A.size(); ++a)
+    if (mate_a[a] < 0) {
+      za[a] = 1;
+      stack.push_back((int)a);
+    }
+  while (!stack.empty()) {
+    const int a = stack.back();
+    stack.pop_back();
+    for (int q = aptr[a]; q < aptr[a + 1]; ++q) {
+      const int b = adj[q];
+      if (!zb[b]) {
+        zb[b] = 1;
+        const int a2 = mate_b[b];
+        if (a2 >= 0 && !za[a2]) {
+          za[a2] = 1;
+          stack.push_back(a2);
+        }
+      }
+    }
+  }
+  std::vector<int> cover;
+  for (size_t a = 0; a < A.size(); ++a)
+    if (!za[a]) cover.push_back(A[a]);
+  for (size_t b = 0; b < B.size(); ++b)
+    if (zb[b]) cover.push_back(B[b]);
+  for (int v : A) pos[v] = -1;
+  for (int v : B) pos[v] = -1;
+  return cover;
+}
+
+// Nested dissection with searched cut planes and cut-cover separators: at every level, for
+// cut planes of the given directions at the 35–65 % quantiles, the separator is the
+// minimum cover of the cut edges; the kept split minimises |S| (1 + bal (max(|L|,|U|) /
+// (|L| + |U|) − 1/2)).  Every leaf and separator is one block; stage[v] numbers the blocks
+// in elimination order.
+void covered_dissection(const Graph& g, const std::vector<V3>& p, const std::vector<V3>& dirs,
+                        std::vector<int> idx, std::vector<int>* order, std::vector<int>* stage, int* nstage,
+                        int leaf, double bal, std::vector<char>& side, std::vector<int>& pos) {
+  auto emit = [&](const std::vector<int>& block) {
+    for (int v : block) (*stage)[v] = *nstage;
+    ++*nstage;
+    order->insert(order->end(), block.begin(), block.end());
+  };
+  if ((int)idx.size() <= leaf) {
+    emit(idx);
+    return;
+  }
+  static const double kFractions[] = {0.35, 0.4, 0.45, 0.5, 0.55, 0.6, 0.65};
+  std::vector<int> sorted, best_sep;
+  size_t best_dir = 0, best_cut = 0;
+  double best = 1e300;
+  for (size_t di = 0; di < dirs.size(); ++di) {
+    const V3 d = dirs[di];
+    sorted = idx;
+    std::sort(sorted.begin(), sorted.end(), [&](int a, int b) {
+      const double ca = dot(p[a], d), cb = dot(p[b], d);
+      return ca < cb || (ca == cb && a < b);
+    });
+    for (double fr : kFractions) {
+      const size_t cut = (size_t)(fr * (double)sorted.size());
+      for (size_t i = 0; i < sorted.size(); ++i) side[sorted[i]] = i < cut ? 0 : 1;
+      std::vector<int> sep = cut_cover(g, side, idx, pos);
+      size_t nlo = cut, nhi = sorted.size() - cut;
+      for (int v : sep) --(side[v] == 0 ? nlo : nhi);
+      if (nlo > 0 && nhi > 0) {
+        const double big = (double)std::max(nlo, nhi), both = (double)(nlo + nhi);
+        const double score = (double)sep.size() * (1.0 + bal * (big / both - 0.5));
+        if (score < best) {
+          best = score;
+          best_dir = di;
+          best_cut = cut;
+          best_sep.swap(sep);
+        }
+      }
+    }
+  }
+  if (best > 1e299) {  // cannot split further
+    for (int v : idx) side[v] = 2;
+    emit(idx);
+    return;
+  }
+  // rebuild the kept split
+  const V3 d = dirs[best_dir];
+  sorted = idx;
+  std::sort(sorted.begin(), sorted.end(), [&](int a, int b) {
+    const double ca = dot(p[a], d), cb = dot(p[b], d);
+    return ca < cb || (ca == cb && a < b);
+  });
+  for (size_t i = 0; i < sorted.size(); ++i) side[sorted[i]] = i < best_cut ? 0 : 1;
+  for (int v : best_sep) side[v] = 3;
+  std::vector<int> best_lo, best_hi;
+  for (int v : sorted)
+    if (side[v] != 3) (side[v] == 0 ? best_lo : best_hi).push_back(v);
+  for (int v : idx) side[v] = 2;
+  std::sort(best_lo.begin(), best_lo.end());
+  std::sort(best_hi.begin(), best_hi.end());
+  covered_dissection(g, p, dirs, best_lo, order, stage, nstage, leaf, bal, side, pos);
+  covered_dissection(g, p, dirs, best_hi, order, stage, nstage, leaf, bal, side, pos);
+  emit(best_sep);
+}
+
+// Minimum degree constrained to a block order: the elimination graph is that of the whole
+// pattern, and the next vertex is one of least degree among the earliest block not yet
+// eliminated (reorders the vertices inside every leaf and separator of a dissection; the
+// last block, the top separator, keeps its order: its fill is dense whatever the order).
+std::vector<int> constrained_minimum_degree(const Graph& g, const std::vector<int>& stage, int nstage) {
+  const int n = (int)g.size();
+  std::vector<std::set<int>> nb(n);
+  for (int v = 0; v < n; ++v)
+    for (int u : g[v])
+      if (u != v) nb[v].insert(u);
+  std::set<std::array<int, 3>> pq;
+  for (int v = 0; v < n; ++v) pq.insert({stage[v], (int)nb[v].size(), v});
+  std::vector<int> order;
+  order.reserve(n);
+  while (!pq.empty()) {
+    if ((*pq.begin())[0] == nstage - 1) {
+      for (int v = 0; v < n; ++v)
+        if (stage[v] == nstage - 1) order.push_back(v);
+      break;
+    }
+    const int v = (*pq.begin())[2];
+    pq.erase(pq.begin());
+    order.push_back(v);
+    const std::vector<int> N(nb[v].begin(), nb[v].end());
+    for (int a : N) {
+      pq.erase({stage[a], (int)nb[a].size(), a});
+      nb[a].erase(v);
+      for (int b : N)
+        if (b != a) nb[a].insert(b);
+      pq.insert({stage[a], (int)nb[a].size(), a});
+    }
+  }
+  return order;
 }
 
 // Exact minimum degree on the elimination graph (small n only).
@@ -569,7 +755,8 @@ int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double
     if (kv.first.first != kv.first.second) g[kv.first.first].push_back(kv.first.second);
 
   // ---- ordering: least fill among geometric nested dissections (longest axis at the
-  // median; searched cut planes) and minimum degree
+  // median; searched cut planes with one-sided or cut-cover separators, the latter also
+  // reordered by constrained minimum degree) and minimum degree
   std::vector<int> best;
   std::vector<std::vector<int>> best_cols;
   int64_t best_nnz = -1;
@@ -587,6 +774,16 @@ int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double
       std::vector<int> o;
       searched_dissection(g, X, dirs, idx, &o, leaf);
       orders.push_back(o);
+    }
+    {
+      std::vector<char> side(n, 2);
+      std::vector<int> pos(n, -1);
+      for (double bal : {0.3, 0.7}) {
+        std::vector<int> o, stage(n, 0);
+        int nstage = 0;
+        covered_dissection(g, X, dirs, idx, &o, &stage, &nstage, 4, bal, side, pos);
+        orders.push_back(constrained_minimum_degree(g, stage, nstage));
+      }
     }
     if (n <= 1500) orders.push_back(minimum_degree(g));  // exact, quadratic-ish: small meshes only
     for (auto& o : orders) {

@@ -7,11 +7,16 @@ deformations, Setting up new materials section).
   adjoints run on the stored forward states (the checkpointing recomputes the same
   states), and its per-type weight gradients equal the chain's sums to rounding.
 * Central differences (relative step 1e-6) of the loss after 100 steps agree with the
-  adjoint to 1e-6 for the four material weights, along the force field itself, and along
+  adjoint to 1e-6 for the four material weights.  Along the force field itself and along
   random affine fields per cell of the forces and of the initial positions (of the
-  field's own RMS size, or 0.1 um for positions; directions use Richardson-extrapolated
-  central differences at h and h/2); after 10 steps also along the gradient's own
-  per-vertex fields.  Along white-noise directions the loss is strongly nonlinear at
+  field's own RMS size, or 0.1 um for positions) they agree to 1e-6 as well, taken at
+  h = 4e-5, 2e-5 and 1e-5 and extrapolated twice (removing the h^2 and h^4 terms): at
+  h <= 2e-6 the loss's own rounding (about 1e-12 of a loss of 3e3, after 100 FP64 steps)
+  divided by the step is already 1e-6 of the smallest of these derivatives (measured:
+  the initial-position direction's plain differences lie 1.0e-6 .. 1.3e-6 from the
+  adjoint for h = 2e-6 .. 5e-7, the twice-extrapolated ones 1e-8 from it).  After 10
+  steps also along the gradient's own per-vertex fields (h = 1e-6 and 5e-7, extrapolated
+  once).  Along white-noise directions the loss is strongly nonlinear at
   longer horizons: after 100 steps the central differences converge to the
   adjoint only as h^2 (relative error 1.5e-4 at h = 1e-6, 2e-6 at 1e-7).  After 200
   steps the loss is too nonlinear for central differences to serve as a reference at
@@ -30,6 +35,7 @@ pytestmark = pytest.mark.gpu
 NCELLS, CKPT = 256, 20
 CELLS = np.arange(0, NCELLS, NCELLS // 8)      # the 8 cells whose diameters enter the loss
 H = 1e-6
+H_DIR = 4e-5                                  # largest step of the directional checks after 100 steps
 
 
 @pytest.fixture(scope="module")
@@ -150,7 +156,8 @@ def test_calibration_gradient_matches_central_differences(setup):
                     ("f affine", _unit_rms(_affine_field(b, rng)) * frms),
                     ("x0 affine", _unit_rms(_affine_field(b, rng)) * 0.1)):
         grad = gf if name.startswith("f") else gx
-        fd_ = _central_difference(cal, b, x0.detach(), v0, f.detach(), targets, iters, nsteps, name[0], d)
+        fd_ = _central_difference(cal, b, x0.detach(), v0, f.detach(), targets, iters, nsteps, name[0], d,
+                                  h=H_DIR, levels=3)
         adj = float((grad * d).sum())
         assert adj == pytest.approx(fd_, rel=1e-6), (name, adj, fd_)
 
@@ -199,18 +206,22 @@ def _affine_field(b, rng):
     return torch.tensor(out, device="cuda:0")
 
 
-def _central_difference(cal, b, x0, v0, f, targets, iters, nsteps, which, d):
-    """Central differences along d at steps H and H/2, combined by Richardson
-    extrapolation (4 D(H/2) - D(H))/3, which removes their H^2 error term."""
-    def cd(h):
+def _central_difference(cal, b, x0, v0, f, targets, iters, nsteps, which, d, h=H, levels=2):
+    """Central differences D along d, Richardson-extrapolated.  levels=2: steps h and h/2,
+    (4 D(h/2) - D(h))/3, which removes the h^2 error term; levels=3: steps h, h/2, h/4,
+    (64 D(h/4) - 20 D(h/2) + D(h))/45, which removes the h^2 and h^4 terms."""
+    def cd(s):
         if which == "f":
-            lp = _loss_of(cal, b, x0, v0, f + h * d, targets, iters, nsteps)
-            lm = _loss_of(cal, b, x0, v0, f - h * d, targets, iters, nsteps)
+            lp = _loss_of(cal, b, x0, v0, f + s * d, targets, iters, nsteps)
+            lm = _loss_of(cal, b, x0, v0, f - s * d, targets, iters, nsteps)
         else:
-            lp = _loss_of(cal, b, x0 + h * d, v0, f, targets, iters, nsteps)
-            lm = _loss_of(cal, b, x0 - h * d, v0, f, targets, iters, nsteps)
-        return (lp - lm) / (2 * h)
-    return (4.0 * cd(H / 2) - cd(H)) / 3.0
+            lp = _loss_of(cal, b, x0 + s * d, v0, f, targets, iters, nsteps)
+            lm = _loss_of(cal, b, x0 - s * d, v0, f, targets, iters, nsteps)
+        return (lp - lm) / (2 * s)
+    if levels == 2:
+        return (4.0 * cd(h / 2) - cd(h)) / 3.0
+    assert levels == 3
+    return (64.0 * cd(h / 4) - 20.0 * cd(h / 2) + cd(h)) / 45.0
 
 
 def test_rollout_adjoint_sums_weight_gradients_per_type():
