@@ -190,6 +190,11 @@ static void fill_view(npfem_cell_type* t, DevTypeView<S>* v, const S* Dinv, cons
   v->w_area = H.w_area;
   v->w_vol = H.w_vol;
   v->dt = H.dt;
+  v->inv_A0 = 1.0 / H.A0;
+  v->inv_V0 = 1.0 / H.V0;
+  v->idt2 = 1.0 / (H.dt * H.dt);
+  v->inv_dt = 1.0 / H.dt;
+  v->inv_n = 1.0 / H.n;
   v->damp_m = H.c_alpha / H.dt;
   v->damp_l = H.c_beta / H.dt;
   v->s_min = H.s_min;

@@ -32,11 +32,30 @@ struct IterCtaOccupancy<float> {
 
 // Shared scratch of a CTA: double-buffered per-warp partial sums (one barrier per
 // reduction: a buffer is written again only two reductions later, when every thread has
-// passed the barrier of the reduction in between) and the work-queue item.
+// passed the barrier of the reduction in between), in FP64 and in FP32 (the FP32 form's
+// two-loop dot products), the work-queue item, and the scalars that one warp derives
+// from a reduction for the whole CTA (published by a later barrier: the area and volume
+// terms of an evaluation, the curvature test of a history pair).
 struct CtaShared {
   double red[2][kIterCtaMaxWarps * 4];
+  float redf[2][kIterCtaMaxWarps];
+  double e_av;     // area + volume energy of the evaluation
+  double kA, kV;   // their gradient coefficients
+  int keep;        // the new history pair passed the curvature test
   int item;
 };
+
+// The working-precision partial-sum buffer of cta_sum_s.
+template <typename S>
+__device__ __forceinline__ S* sum_buffer(CtaShared& sh, int par);
+template <>
+__device__ __forceinline__ float* sum_buffer<float>(CtaShared& sh, int par) {
+  return sh.redf[par];
+}
+template <>
+__device__ __forceinline__ double* sum_buffer<double>(CtaShared& sh, int par) {
+  return sh.red[par];
+}
 
 // Sums over the CTA of K <= 4 per-thread FP64 values; every thread receives the totals.
 // The FP64 pipe is the scarce unit (a warp-wide FP64 add occupies it for 64 cycles
@@ -107,17 +126,18 @@ __device__ __forceinline__ double cta_sum1(double x, CtaShared& sh, int& par) {
 
 // Sum over the CTA in the working precision S, for the dot products of the two-loop
 // recursion (FP32 in the FP32 form, like the warp kernels' warp sums): lanes by shuffles,
-// then the warp totals in warp order.  Same call discipline as cta_sum.
+// then the warp totals in warp order, kept in S (no conversion through FP64).  Same call
+// discipline as cta_sum (the FP32 buffers alternate with the same parity).
 template <typename S>
 __device__ __forceinline__ S cta_sum_s(S x, CtaShared& sh, int& par) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   x = warp_sum<S>(x);
-  double* r = sh.red[par];
+  S* r = sum_buffer<S>(sh, par);
   par ^= 1;
-  if (lane == 0) r[warp] = (double)x;  // exact: S is float or double
+  if (lane == 0) r[warp] = x;
   __syncthreads();
   S s = 0;
-  for (int q = 0; q < nw; ++q) s += (S)r[q];
+  for (int q = 0; q < nw; ++q) s += r[q];
   return s;
 }
 
@@ -236,17 +256,23 @@ __device__ CtaEval cta_objective(const DevTypeView<S>& ty, const StepParams& P, 
   }
   double av[2] = {a_sum.part(), v_sum.part()};
   cta_sum<2>(av, sh, par);  // also publishes the strain-limit matrices of the pass above
-  const double A = 0.5 * av[0];
-  const double V = av[1] / 6.0;
-  const double dA = A - ty.A0, dV = V - ty.V0;
-  const double e_area = 0.5 * ty.w_area * dA * dA / ty.A0;
-  const double e_vol = 0.5 * ty.w_vol * dV * dV / ty.V0;
-  const S kA = (S)(ty.w_area * dA / ty.A0);
-  const S kV = (S)(ty.w_vol * dV / ty.V0);
+  // The area and volume terms are scalar FP64 work on the totals; every FP64 warp
+  // instruction occupies the FP64 pipe for the whole warp, so one warp derives them and
+  // the barrier after the inertia pass publishes them.
+  if (tid < 32) {
+    const double A = 0.5 * av[0];
+    const double V = av[1] * (1.0 / 6.0);
+    const double dA = A - ty.A0, dV = V - ty.V0;
+    if (tid == 0) {
+      sh.e_av = 0.5 * ty.w_area * dA * dA * ty.inv_A0 + 0.5 * ty.w_vol * dV * dV * ty.inv_V0;
+      sh.kA = ty.w_area * dA * ty.inv_A0;
+      sh.kV = ty.w_vol * dV * ty.inv_V0;
+    }
+  }
   NPFEM_PHASE_END(t_area, kPhAreaVolume, P, tid)
 
   NPFEM_PHASE_BEGIN(t_acc)
-  const S half = (S)0.5, idt2 = (S)(1.0 / (ty.dt * ty.dt));
+  const S half = (S)0.5, idt2 = (S)ty.idt2;
   Acc<S> e_el;
   for (int v = tid; v < n; v += nt) {
     const V3<S> du = ld3(Us, v) - ld3(w.W, v);
@@ -256,7 +282,8 @@ __device__ CtaEval cta_objective(const DevTypeView<S>& ty, const StepParams& P, 
   }
   // damping's mass part visits the same vertices per thread: no barrier in between
   if (ty.damp_m != 0.0) e_el.add((S)damping_mass<S>(ty.mass, n, (S)ty.damp_m, Us, Gs, tid, nt));
-  __syncthreads();
+  __syncthreads();  // also publishes the area and volume terms
+  const S kA = (S)sh.kA, kV = (S)sh.kV;
   bool degen = false;
   for (int c = 0; c < ty.ntc; ++c) {
     const int lo = __ldg(&ty.tri_cptr[c]), hi = __ldg(&ty.tri_cptr[c + 1]);
@@ -328,7 +355,7 @@ __device__ CtaEval cta_objective(const DevTypeView<S>& ty, const StepParams& P, 
   cta_sum<3>(r, sh, par);
   NPFEM_PHASE_END(t_acc, kPhGather, P, tid)
   CtaEval o;
-  o.energy = r[0] + e_area + e_vol;
+  o.energy = r[0] + sh.e_av;
   o.gtd = r[1];
   o.gg = r[2];
   o.degenerate = any_degen;
@@ -372,6 +399,19 @@ __device__ __forceinline__ void cta_two_loop_first(const CellWs<S>& w, CellState
   }
 }
 
+// a + (X + U) rounded once to S: exactly in FP64 for S = double; for S = float by a
+// compensated FP32 sum (the rounding errors of X + U and of a + (X + U), each recovered
+// exactly by Knuth's TwoSum, added back at the end), which equals the FP64 sum rounded to
+// FP32 but for rare double-rounding ties and leaves the FP64 pipe to the solves.
+__device__ __forceinline__ double anchored_sum(double a, double X, double U) { return a + (X + U); }
+__device__ __forceinline__ float anchored_sum(float a, float X, float U) {
+  const float s = X + U, bs = s - X;
+  const float e1 = (X - (s - bs)) + (U - bs);
+  const float t = a + s, bt = t - a;
+  const float e2 = (a - (t - bt)) + (s - bt);
+  return t + (e1 + e2);
+}
+
 // K7 by the CTA: x_{n+1} = anchor + X + U, v_{n+1} = U / dt, residual |g| / |g0|, status.
 template <typename S>
 __device__ void cta_finalize(const DevTypeView<S>& ty, const StepParams& P, CellState<S>* st, const S* Xs,
@@ -380,19 +420,19 @@ __device__ void cta_finalize(const DevTypeView<S>& ty, const StepParams& P, Cell
   const int64_t off = P.offsets[cell], Nt = P.n_total;
   NPFEM_PHASE_BEGIN(t_write)
   const S ax = x[off], ay = x[Nt + off], az = x[2 * Nt + off];
-  const S idt = (S)(1.0 / ty.dt);
+  const S idt = (S)ty.inv_dt;
   bool bad = false;
   for (int k = tid; k < n; k += nt) {
-    const double nx = (double)ax + ((double)Xs[3 * k] + (double)Us[3 * k]);
-    const double ny = (double)ay + ((double)Xs[3 * k + 1] + (double)Us[3 * k + 1]);
-    const double nz = (double)az + ((double)Xs[3 * k + 2] + (double)Us[3 * k + 2]);
+    const S nx = anchored_sum(ax, Xs[3 * k], Us[3 * k]);
+    const S ny = anchored_sum(ay, Xs[3 * k + 1], Us[3 * k + 1]);
+    const S nz = anchored_sum(az, Xs[3 * k + 2], Us[3 * k + 2]);
     const S vx = Us[3 * k] * idt, vy = Us[3 * k + 1] * idt, vz = Us[3 * k + 2] * idt;
-    bad = bad || !isfinite(nx) || !isfinite(ny) || !isfinite(nz) || !isfinite((double)vx) ||
-          !isfinite((double)vy) || !isfinite((double)vz);
+    bad = bad || !isfinite(nx) || !isfinite(ny) || !isfinite(nz) || !isfinite(vx) || !isfinite(vy) ||
+          !isfinite(vz);
     if (k != 0) {
-      x[off + k] = (S)nx;
-      x[Nt + off + k] = (S)ny;
-      x[2 * Nt + off + k] = (S)nz;
+      x[off + k] = nx;
+      x[Nt + off + k] = ny;
+      x[2 * Nt + off + k] = nz;
     }
     v[off + k] = vx;
     v[Nt + off + k] = vy;
@@ -401,9 +441,9 @@ __device__ void cta_finalize(const DevTypeView<S>& ty, const StepParams& P, Cell
   // vertex 0 is the anchor: every thread read it above, so it is written after the barrier
   bad = __syncthreads_or(bad);
   if (tid == 0) {
-    x[off] = (S)((double)ax + ((double)Xs[0] + (double)Us[0]));
-    x[Nt + off] = (S)((double)ay + ((double)Xs[1] + (double)Us[1]));
-    x[2 * Nt + off] = (S)((double)az + ((double)Xs[2] + (double)Us[2]));
+    x[off] = anchored_sum(ax, Xs[0], Us[0]);
+    x[Nt + off] = anchored_sum(ay, Xs[1], Us[1]);
+    x[2 * Nt + off] = anchored_sum(az, Xs[2], Us[2]);
     int status = st->status;
     if (st->degen) status |= 2;
     if (bad) status |= 4;
@@ -486,7 +526,8 @@ __global__ void __launch_bounds__(32 * kIterCtaMaxWarps, IterCtaOccupancy<S>::mi
     }
     double cs[3] = {cx.part(), cy.part(), cz.part()};
     cta_sum<3>(cs, sh, par);  // also completes Xs and Us for the objective
-    const V3<S> cvol{(S)(cs[0] / n), (S)(cs[1] / n), (S)(cs[2] / n)};
+    const double inv_n = ty.inv_n;
+    const V3<S> cvol{(S)(cs[0] * inv_n), (S)(cs[1] * inv_n), (S)(cs[2] * inv_n)};
     NPFEM_PHASE_END(t_predict, kPhPredict, P, tid)
     NPFEM_PHASE_BEGIN(t_obj0)
     const CtaEval ev = cta_objective<S, kLim ? 1 : 0>(ty, P, w, Xs, Us, Gs, w.G, nullptr, cvol, cell, sh, par);
@@ -668,7 +709,9 @@ __global__ void __launch_bounds__(32 * kIterCtaMaxWarps, IterCtaOccupancy<S>::mi
       }
       double r3[3] = {asy.part(), ass.part(), ayy.part()};
       cta_sum<3>(r3, sh, par);
-      if (r3[0] > kCurvatureEps * sqrt(r3[1]) * sqrt(r3[2])) {
+      // the curvature test and 1 / (s . y): scalar FP64 work, by thread 0 alone (the
+      // barrier below publishes the decision)
+      if (tid == 0 && r3[0] > kCurvatureEps * sqrt(r3[1]) * sqrt(r3[2])) {
         keep = true;
         new_rho = (S)(1.0 / r3[0]);
       }
@@ -676,21 +719,25 @@ __global__ void __launch_bounds__(32 * kIterCtaMaxWarps, IterCtaOccupancy<S>::mi
     NPFEM_PHASE_END(t_hist, kPhHistory, P, tid)
     if (P.alpha_log && k < P.alpha_log_len && tid == 0) P.alpha_log[(size_t)cell * P.alpha_log_len + k] = alpha;
     const int slot = hhead;
-    if (keep) {
-      hhead = (hhead + 1) % kHistory;
-      hcount = hcount < kHistory ? hcount + 1 : kHistory;
-    }
     if (tid == 0) {
+      sh.keep = keep;
+      const int hh = keep ? (hhead + 1) % kHistory : hhead;
+      const int hc = keep ? (hcount < kHistory ? hcount + 1 : kHistory) : hcount;
       if (keep) st->rho[slot] = new_rho;
-      st->hcount = hcount;
-      st->hhead = hhead;
+      st->hcount = hc;
+      st->hhead = hh;
       st->fx = ft;
       st->cur = cur ^ 1;
       st->k = k + 1;
       st->status |= status;
       if (degen) st->degen = 1;
     }
-    __syncthreads();  // the header (rho of the new pair) before the first half reads it
+    __syncthreads();  // the header (rho of the new pair) and the decision before the first half reads them
+    keep = sh.keep != 0;
+    if (keep) {
+      hhead = (hhead + 1) % kHistory;
+      hcount = hcount < kHistory ? hcount + 1 : kHistory;
+    }
     // the accepted trial (UT, GT) is the new current iterate
     if (k + 1 < iters && !stop) {
       if (tid == 0) P.act_out[atomicAdd(P.act_count_out, 1)] = item;

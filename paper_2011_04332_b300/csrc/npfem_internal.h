@@ -122,6 +122,7 @@ struct DevTypeView {
   const uint32_t* cta_bwd_rc[kCtaPacks];
   const double* cta_bwd_val[kCtaPacks];
   double A0, V0, w_area, w_vol, dt;
+  double inv_A0, inv_V0, idt2, inv_dt, inv_n;  // 1 / A0, 1 / V0, 1 / dt^2, 1 / dt, 1 / n
   double damp_m, damp_l;    // Rayleigh damping over dt: c_alpha/dt (mass part), c_beta/dt (elastic part)
   double s_min, s_max;      // strain limits; limited = 0 for the rotations [1, 1]
   int limited;
