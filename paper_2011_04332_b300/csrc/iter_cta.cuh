@@ -141,6 +141,18 @@ __device__ __forceinline__ S cta_sum_s(S x, CtaShared& sh, int& par) {
   return s;
 }
 
+// Requests a global vector of len elements into L2 (one prefetch per 128-byte line,
+// spread over the CTA's threads; the line of the last element too, for vectors that do
+// not start on a line) ahead of the pass that reads it.  The two-loop passes are latency
+// bound — each waits for its loads, then for its CTA-wide reduction — so the next pass's
+// vectors come from DRAM while the current pass runs.
+template <typename S>
+__device__ __forceinline__ void prefetch_l2(const S* p, int len, int tid, int nt) {
+  constexpr int kLine = 128 / (int)sizeof(S);
+  for (int e = tid * kLine; e < len; e += nt * kLine) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + e));
+  if (tid == 0 && len > 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(p + len - 1));
+}
+
 // Last pass of the second half of the two-loop recursion fused with the line search's
 // first trial (step 1): d = -(q + c u), UT = Us = U + d; agd accumulates g . d.  Four
 // elements per thread in flight, as in update_dot.
@@ -378,6 +390,7 @@ __device__ __forceinline__ void cta_two_loop_first(const CellWs<S>& w, CellState
     return;
   }
   int i = (hh - 1 + kHistory) % kHistory;
+  if (hc > 1) prefetch_l2(w.hs + (size_t)((hh - 2 + kHistory) % kHistory) * len, len, tid, nt);
   S acc = 0;
   if (newest_dot) {
     acc = *newest_dot;
@@ -386,6 +399,11 @@ __device__ __forceinline__ void cta_two_loop_first(const CellWs<S>& w, CellState
     for (int e = tid; e < len; e += nt) acc += si[e] * Gs[e];
   }
   for (int q = 0; q < hc; ++q) {
+    // the pass of pair q (newest first) reads y_q and s_{q+1}; fetch the next pass's
+    if (q + 1 < hc) {
+      prefetch_l2(w.hy + (size_t)((hh - 1 - (q + 1) + kHistory) % kHistory) * len, len, tid, nt);
+      if (q + 2 < hc) prefetch_l2(w.hs + (size_t)((hh - 1 - (q + 2) + kHistory) % kHistory) * len, len, tid, nt);
+    }
     const S a = st->rho[i] * cta_sum_s<S>(acc, sh, par);
     if (tid == 0) st->aco[i] = a;
     const S* yi = w.hy + (size_t)i * len;
@@ -615,8 +633,22 @@ __global__ void __launch_bounds__(32 * kIterCtaMaxWarps, IterCtaOccupancy<S>::mi
       } else {
         // r = A^-1 q from the solve is staged in the shared Gs (free until the line search)
         // by the first pass, and the passes update it there
-        int i = (hhead - hcount + kHistory) % kHistory;
+        // pair k (oldest first) is slot (hhead - hcount + k) mod m; the pass of pair k reads
+        // s_k and y_{k+1} (the last pass s_k, g and U), and fetches the next pass's vectors
+        auto slot = [&](int k) { return (hhead - hcount + k + kHistory) % kHistory; };
+        auto prefetch_pass = [&](int k) {
+          if (k >= hcount) return;
+          prefetch_l2(w.hs + (size_t)slot(k) * len, len, tid, nt);
+          if (k + 1 < hcount) {
+            prefetch_l2(w.hy + (size_t)slot(k + 1) * len, len, tid, nt);
+          } else {
+            prefetch_l2(G, len, tid, nt);
+            prefetch_l2(U, len, tid, nt);
+          }
+        };
+        int i = slot(0);
         S acc = 0;
+        prefetch_pass(0);
         {
           const S* yi = w.hy + (size_t)i * len;
           for (int e = tid; e < len; e += nt) {
@@ -626,6 +658,8 @@ __global__ void __launch_bounds__(32 * kIterCtaMaxWarps, IterCtaOccupancy<S>::mi
           }
         }
         for (int q = hcount - 1; q >= 0; --q) {
+          const int k = hcount - 1 - q;
+          prefetch_pass(k + 1);
           const S b = st->rho[i] * cta_sum_s<S>(acc, sh, par);
           const S c = st->aco[i] - b;
           const S* si = w.hs + (size_t)i * len;
