@@ -355,7 +355,7 @@ static void default_split_shape(TypeLaunch& L, int n, npfem_precision prec) {
 // is fixed per type unless the caller sets it (npfem_batch_set_iter_width).
 static int default_iter_width(int n, npfem_precision prec) {
   if (prec == NPFEM_FP64) return 0;
-  return n <= 256 ? 2 : (n <= 1024 ? 4 : 8);
+  return default_cta_warps(n);
 }
 
 // Uses the CTA iteration kernels with w warps per cell for the type (w = 0: the warp

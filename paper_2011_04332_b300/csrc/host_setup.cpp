@@ -40,22 +40,44 @@ inline double cotangent(V3 a, V3 b) { return dot(a, b) / norm(cross(a, b)); }
 // Colour elements of k vertices each so that no two elements of a colour share a vertex,
 // and store them colour by colour (stable within a colour): the CTA iteration kernels add
 // one colour's gradient contributions to the shared-memory gradient at a time, without
-// conflicts and in a fixed order.  Greedy: each element takes, among the colours none of
-// its vertices has yet, the one holding the fewest elements (a new colour only when every
-// existing one is taken), which keeps the classes of a near-regular mesh equally full.
+// conflicts and in a fixed order, with a barrier after each colour.  A CTA of nt threads
+// takes ceil(size / nt) passes over a colour, so the colouring minimises the passes
+// sum_c ceil(|c| / nt) and then the colours:
+//  1. DSatur (Brélaz 1979): the uncoloured element whose neighbours (elements sharing a
+//     vertex with it) show the most distinct colours goes next (ties: more neighbours,
+//     then the lower index), into the least-filled colour none of them has (a new colour
+//     only when every existing one is taken);
+//  2. balancing: an element moves from a colour whose last pass is partly filled to one
+//     whose last pass has room and that no neighbour has, when that takes a pass away
+//     and adds none — first out of the colours that spill over into an extra pass (the
+//     emptiest last pass first), then out of the smallest colours until they are empty.
 // Returns false (and leaves the elements as they were) if more than kMaxColours colours
 // would be needed.
-bool colour_elements(int n, int k, std::vector<int32_t>* elems, std::vector<int32_t>* cptr) {
+bool colour_elements(int n, int k, int nt, std::vector<int32_t>* elems, std::vector<int32_t>* cptr) {
   const int m = (int)elems->size() / k;
-  std::vector<uint64_t> used(n, 0);
-  std::vector<int> colour(m);
-  std::vector<int> count;
+  // neighbours: elements sharing a vertex
+  std::vector<std::vector<int>> inc(n);
+  for (int e = 0; e < m; ++e)
+    for (int j = 0; j < k; ++j) inc[(*elems)[(size_t)k * e + j]].push_back(e);
+  std::vector<std::vector<int>> nb(m);
   for (int e = 0; e < m; ++e) {
-    uint64_t taken = 0;
-    for (int j = 0; j < k; ++j) taken |= used[(*elems)[(size_t)k * e + j]];
+    for (int j = 0; j < k; ++j)
+      for (int f : inc[(*elems)[(size_t)k * e + j]])
+        if (f != e) nb[e].push_back(f);
+    std::sort(nb[e].begin(), nb[e].end());
+    nb[e].erase(std::unique(nb[e].begin(), nb[e].end()), nb[e].end());
+  }
+  // 1. DSatur
+  std::vector<int> colour(m, -1), count;
+  std::vector<uint64_t> seen(m, 0);  // colours among the coloured neighbours
+  std::set<std::array<int, 3>> queue;  // (-saturation, -degree, e): first is next
+  for (int e = 0; e < m; ++e) queue.insert({0, -(int)nb[e].size(), e});
+  while (!queue.empty()) {
+    const int e = (*queue.begin())[2];
+    queue.erase(queue.begin());
     int best = -1;
     for (int c = 0; c < (int)count.size(); ++c)
-      if (!((taken >> c) & 1u) && (best < 0 || count[c] < count[best])) best = c;
+      if (!((seen[e] >> c) & 1u) && (best < 0 || count[c] < count[best])) best = c;
     if (best < 0) {
       if ((int)count.size() == kMaxColours) return false;
       best = (int)count.size();
@@ -63,24 +85,82 @@ bool colour_elements(int n, int k, std::vector<int32_t>* elems, std::vector<int3
     }
     colour[e] = best;
     ++count[best];
-    for (int j = 0; j < k; ++j) used[(*elems)[(size_t)k * e + j]] |= uint64_t(1) << best;
+    for (int f : nb[e]) {
+      if (colour[f] >= 0 || ((seen[f] >> best) & 1u)) continue;
+      queue.erase({-__builtin_popcountll(seen[f]), -(int)nb[f].size(), f});
+      seen[f] |= uint64_t(1) << best;
+      queue.insert({-__builtin_popcountll(seen[f]), -(int)nb[f].size(), f});
+    }
   }
-  cptr->assign(count.size() + 1, 0);
-  for (size_t c = 0; c < count.size(); ++c) (*cptr)[c + 1] = (*cptr)[c] + count[c];
+  // 2. balancing
+  const int nc = (int)count.size();
+  auto passes = [&](int size) { return (size + nt - 1) / nt; };
+  auto room = [&](int c) { return passes(count[c] + 1) == passes(count[c]) && count[c] > 0; };
+  auto move_one = [&](int from) {  // one element of `from` to the fullest colour with room
+    for (int e = 0; e < m; ++e) {
+      if (colour[e] != from) continue;
+      uint64_t taken = 0;
+      for (int f : nb[e]) taken |= uint64_t(1) << colour[f];
+      int to = -1;
+      for (int c = 0; c < nc; ++c)
+        if (c != from && !((taken >> c) & 1u) && room(c) && (to < 0 || count[c] % nt > count[to] % nt)) to = c;
+      if (to >= 0) {
+        colour[e] = to;
+        --count[from];
+        ++count[to];
+        return true;
+      }
+    }
+    return false;
+  };
+  std::vector<char> stuck(nc, 0);
+  for (;;) {  // colours spilling into an extra pass, emptiest last pass first
+    int c = -1;
+    for (int d = 0; d < nc; ++d)
+      if (!stuck[d] && count[d] > nt && count[d] % nt != 0 && (c < 0 || count[d] % nt < count[c] % nt)) c = d;
+    if (c < 0) break;
+    const int target = count[c] - count[c] % nt;
+    while (count[c] > target && move_one(c)) {
+    }
+    if (count[c] > target) stuck[c] = 1;
+  }
+  std::fill(stuck.begin(), stuck.end(), 0);
+  for (;;) {  // the smallest colours, emptied if they can be
+    int c = -1;
+    for (int d = 0; d < nc; ++d)
+      if (!stuck[d] && count[d] > 0 && count[d] < nt && (c < 0 || count[d] < count[c])) c = d;
+    if (c < 0) break;
+    const std::vector<int> save = colour, save_count = count;
+    while (count[c] > 0 && move_one(c)) {
+    }
+    if (count[c] > 0) {  // partly emptied: no pass saved, undo
+      colour = save;
+      count = save_count;
+      stuck[c] = 1;
+    }
+  }
+  // renumber the non-empty colours in order, and lay the elements out colour by colour
+  std::vector<int> renum(nc, -1);
+  int used = 0;
+  for (int c = 0; c < nc; ++c)
+    if (count[c] > 0) renum[c] = used++;
+  cptr->assign(used + 1, 0);
+  for (int e = 0; e < m; ++e) ++(*cptr)[renum[colour[e]] + 1];
+  for (int c = 0; c < used; ++c) (*cptr)[c + 1] += (*cptr)[c];
   std::vector<int32_t> next(cptr->begin(), cptr->end() - 1), out(elems->size());
   for (int e = 0; e < m; ++e) {
-    const int p = next[colour[e]]++;
+    const int p = next[renum[colour[e]]]++;
     for (int j = 0; j < k; ++j) out[(size_t)k * p + j] = (*elems)[(size_t)k * e + j];
   }
   // the invariant the CTA kernels rely on, checked as built: within a class, every vertex
   // occurs at most once
-  std::vector<int> seen(n, -1);
+  std::vector<int> vseen(n, -1);
   for (size_t c = 0; c + 1 < cptr->size(); ++c)
     for (int e = (*cptr)[c]; e < (*cptr)[c + 1]; ++e)
       for (int j = 0; j < k; ++j) {
         const int v = out[(size_t)k * e + j];
-        if (seen[v] == (int)c) return false;
-        seen[v] = (int)c;
+        if (vseen[v] == (int)c) return false;
+        vseen[v] = (int)c;
       }
   elems->swap(out);
   return true;
@@ -634,7 +714,8 @@ int build_host_type(int n, int T, const double* xyz, const int32_t* tris, double
   }
   // ---- elements in colour order (each triangle keeps its vertex order, hence its
   // orientation); every per-element table below follows this order
-  if (!colour_elements(n, 3, &H.tris, &H.tri_cptr) || !colour_elements(n, 4, &H.hinges, &H.hinge_cptr)) {
+  const int nt = 32 * default_cta_warps(n);
+  if (!colour_elements(n, 3, nt, &H.tris, &H.tri_cptr) || !colour_elements(n, 4, nt, &H.hinges, &H.hinge_cptr)) {
     H.tri_cptr.clear();
     H.hinge_cptr.clear();
   }

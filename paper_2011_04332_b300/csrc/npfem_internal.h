@@ -17,6 +17,9 @@ constexpr int kChunk = 32;               // entries per triangular-solve chunk (
 constexpr int kCtaPacks = 4;             // level packings for CTA-cooperative sweeps
 constexpr int kCtaWarps[kCtaPacks] = {2, 4, 6, 8};
 constexpr int kMaxColours = 64;          // colour classes of triangles or of hinges
+// Warps per cell of the FP32 form's default CTA iteration kernels for an n-vertex type
+// (its colour classes are balanced for that CTA size).
+inline int default_cta_warps(int n) { return n <= 256 ? 2 : (n <= 1024 ? 4 : 8); }
 
 // Host-side result of the per-type setup (all FP64; the device upload makes FP32
 // copies of the element constants for the FP32-form kernels).
