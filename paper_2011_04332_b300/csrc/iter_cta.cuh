@@ -285,6 +285,31 @@ __device__ CtaEval cta_objective(const DevTypeView<S>& ty, const StepParams& P, 
 
   NPFEM_PHASE_BEGIN(t_acc)
   const S half = (S)0.5, idt2 = (S)ty.idt2;
+  // The table rows of a thread's first element in the next colour class are loaded before
+  // the barrier that ends the current class (or the inertia pass), so their L2 round trip
+  // overlaps the wait; they are live only across the barrier, not through the element
+  // arithmetic.
+  int4 tv_next = make_int4(0, 0, 0, 0), hv_next = make_int4(0, 0, 0, 0);
+  typename Q4Of<S>::type tc_next{}, cv_next{};
+  S k0n_next = 0, wh_next = 0;
+  auto load_tri = [&](int lo, int hi) {
+    if (lo + tid < hi) {
+      tv_next = ldg4(ty.tri4 + 4 * (lo + tid));
+      tc_next = ldg4(ty.trc + 4 * (lo + tid));
+    }
+  };
+  auto load_hinge = [&](int lo, int hi) {
+    if (lo + tid < hi) {
+      hv_next = ldg4(ty.hinges + 4 * (lo + tid));
+      cv_next = ldg4(ty.c_hinge + 4 * (lo + tid));
+      k0n_next = __ldg(&ty.K0[4 * (lo + tid) + 3]);
+      wh_next = __ldg(&ty.w_hinge[lo + tid]);
+    }
+  };
+  if (ty.ntc > 0)
+    load_tri(__ldg(&ty.tri_cptr[0]), __ldg(&ty.tri_cptr[1]));
+  else if (ty.nhc > 0)
+    load_hinge(__ldg(&ty.hinge_cptr[0]), __ldg(&ty.hinge_cptr[1]));
   Acc<S> e_el;
   for (int v = tid; v < n; v += nt) {
     const V3<S> du = ld3(Us, v) - ld3(w.W, v);
@@ -297,33 +322,54 @@ __device__ CtaEval cta_objective(const DevTypeView<S>& ty, const StepParams& P, 
   __syncthreads();  // also publishes the area and volume terms
   const S kA = (S)sh.kA, kV = (S)sh.kV;
   bool degen = false;
+  auto triangle = [&](int t, const int4& tv, const typename Q4Of<S>::type& tc) {
+    const int i0 = tv.x, i1 = tv.y, i2 = tv.z;
+    const V3<S> e1 = edge(Xs, Us, i0, i1), e2 = edge(Xs, Us, i0, i2);
+    const V3<S> q0 = (ld3(Xs, i0) + ld3(Us, i0)) - cvol;
+    V3<S> g0, g1, g2;
+    triangle_terms<S>(e1, e2, q0, tc, limited ? w.corner + 9 * t : nullptr, kA, kV, e_el, degen, g0, g1, g2);
+    st3(Gs, i0, ld3(Gs, i0) + g0);
+    st3(Gs, i1, ld3(Gs, i1) + g1);
+    st3(Gs, i2, ld3(Gs, i2) + g2);
+  };
   for (int c = 0; c < ty.ntc; ++c) {
     const int lo = __ldg(&ty.tri_cptr[c]), hi = __ldg(&ty.tri_cptr[c + 1]);
-    for (int t = lo + tid; t < hi; t += nt) {
-      const int4 tv = ldg4(ty.tri4 + 4 * t);
-      const typename Q4Of<S>::type tc = ldg4(ty.trc + 4 * t);
-      const int i0 = tv.x, i1 = tv.y, i2 = tv.z;
-      const V3<S> e1 = edge(Xs, Us, i0, i1), e2 = edge(Xs, Us, i0, i2);
-      const V3<S> q0 = (ld3(Xs, i0) + ld3(Us, i0)) - cvol;
-      V3<S> g0, g1, g2;
-      triangle_terms<S>(e1, e2, q0, tc, limited ? w.corner + 9 * t : nullptr, kA, kV, e_el, degen, g0, g1, g2);
-      st3(Gs, i0, ld3(Gs, i0) + g0);
-      st3(Gs, i1, ld3(Gs, i1) + g1);
-      st3(Gs, i2, ld3(Gs, i2) + g2);
+    if (lo + tid < hi) {
+      triangle(lo + tid, tv_next, tc_next);
+      for (int t = lo + tid + nt; t < hi; t += nt) triangle(t, ldg4(ty.tri4 + 4 * t), ldg4(ty.trc + 4 * t));
     }
+    if (c + 1 < ty.ntc)
+      load_tri(hi, __ldg(&ty.tri_cptr[c + 2]));
+    else if (ty.nhc > 0)
+      load_hinge(__ldg(&ty.hinge_cptr[0]), __ldg(&ty.hinge_cptr[1]));
     __syncthreads();
   }
+  auto hinge = [&](int h, const int4& hv, const typename Q4Of<S>::type& cv, S k0n, S wh) {
+    const V3<S> K = hinge_vector<S>(Xs, Us, hv, cv);
+    // the bending term of hinge_terms, with |K0| and w_e given
+    const S kn = sqrt(dot(K, K));
+    V3<S> p;
+    if (kn < (S)kDegenerateNorm) {
+      p = {__ldg(&ty.K0[4 * h]), __ldg(&ty.K0[4 * h + 1]), __ldg(&ty.K0[4 * h + 2])};
+    } else {
+      p = (k0n / kn) * K;
+    }
+    const V3<S> d = K - p;
+    e_el.add((S)0.5 * wh * dot(d, d));
+    const V3<S> r = wh * d;
+    st3(Gs, hv.x, ld3(Gs, hv.x) + cv.x * r);
+    st3(Gs, hv.y, ld3(Gs, hv.y) + cv.y * r);
+    st3(Gs, hv.z, ld3(Gs, hv.z) + cv.z * r);
+    st3(Gs, hv.w, ld3(Gs, hv.w) + cv.w * r);
+  };
   for (int c = 0; c < ty.nhc; ++c) {
     const int lo = __ldg(&ty.hinge_cptr[c]), hi = __ldg(&ty.hinge_cptr[c + 1]);
-    for (int h = lo + tid; h < hi; h += nt) {
-      const int4 hv = ldg4(ty.hinges + 4 * h);
-      const typename Q4Of<S>::type cv = ldg4(ty.c_hinge + 4 * h);
-      const V3<S> r = hinge_terms<S>(hinge_vector<S>(Xs, Us, hv, cv), ty.K0 + 4 * h, __ldg(&ty.w_hinge[h]), e_el);
-      st3(Gs, hv.x, ld3(Gs, hv.x) + cv.x * r);
-      st3(Gs, hv.y, ld3(Gs, hv.y) + cv.y * r);
-      st3(Gs, hv.z, ld3(Gs, hv.z) + cv.z * r);
-      st3(Gs, hv.w, ld3(Gs, hv.w) + cv.w * r);
+    if (lo + tid < hi) {
+      hinge(lo + tid, hv_next, cv_next, k0n_next, wh_next);
+      for (int h = lo + tid + nt; h < hi; h += nt)
+        hinge(h, ldg4(ty.hinges + 4 * h), ldg4(ty.c_hinge + 4 * h), __ldg(&ty.K0[4 * h + 3]), __ldg(&ty.w_hinge[h]));
     }
+    if (c + 1 < ty.nhc) load_hinge(hi, __ldg(&ty.hinge_cptr[c + 2]));
     __syncthreads();
   }
   if (ty.damp_l != 0.0) e_el.add((S)damping_elastic_cta<S>(ty, (S)ty.damp_l, Us, Gs, tid, nt));
