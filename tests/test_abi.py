@@ -58,8 +58,9 @@ def _max_elements_at_a_vertex(n, elems):
 def test_element_colour_classes(lib):
     """Triangles and hinges come in vertex-disjoint colour classes (verified as built);
     a valid class count is at least the largest number of elements at one vertex, and the
-    greedy colouring stays within a few classes of that bound on the workload meshes.  A
-    mesh that would need more than 64 classes reports 0 (its type runs the one-warp
+    DSatur colouring stays within a few classes of that bound on the workload meshes (it
+    finds 9-10 triangle classes against a bound of 6, 16-17 hinge classes against 10-12).
+    A mesh that would need more than 64 classes reports 0 (its type runs the one-warp
     iteration kernels)."""
     from oracle import npfem_oracle as O
     for m in (I.platelet_mesh(2), I.rbc_mesh(2), I.rbc_mesh(3), I.rbc_mesh(4)):
@@ -67,8 +68,8 @@ def test_element_colour_classes(lib):
         n = m.verts.shape[0]
         hinges = O.rest_state(m.verts, m.tris, *I.RBC_MATERIAL.as_tuple(), I.DT_DEFAULT).hinges
         lo_t, lo_h = _max_elements_at_a_vertex(n, m.tris), _max_elements_at_a_vertex(n, hinges)
-        assert lo_t <= info["tri_colours"] <= lo_t + 8, (m.name, info["tri_colours"], lo_t)
-        assert lo_h <= info["hinge_colours"] <= 2 * lo_h + 4, (m.name, info["hinge_colours"], lo_h)
+        assert lo_t <= info["tri_colours"] <= lo_t + 5, (m.name, info["tri_colours"], lo_t)
+        assert lo_h <= info["hinge_colours"] <= lo_h + 7, (m.name, info["hinge_colours"], lo_h)
     m = I.bipyramid(70)
     info = native.analyze_cell_type(m.verts, m.tris, I.RBC_MATERIAL.as_tuple(), I.DT_DEFAULT)
     assert info["tri_colours"] == 0 and info["hinge_colours"] == 0
