@@ -1157,7 +1157,10 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     A.w_mat[1] = 0;
     A.w_mat[2] = H.w_area;
     A.w_mat[3] = H.w_vol;
-    npfem_adjoint_kernel<<<L.blocks, 32 * L.warps_per_block, L.smem_bytes, st>>>(
+    // one warp per CTA over the launch's warp slots (the same slots and per-warp shared
+    // memory as the fused step): the adjoint is FP64 bound at a warp per cell, so its few
+    // warps are spread over every SM rather than packed four to an SM
+    npfem_adjoint_kernel<<<L.blocks * L.warps_per_block, 32, L.smem_bytes / L.warps_per_block, st>>>(
         t->v64, P, A, static_cast<const double*>(x), static_cast<const double*>(v), static_cast<const double*>(f_ext));
     NPFEM_CUDA_TRY(cudaGetLastError());
   }
@@ -1371,7 +1374,8 @@ npfem_status npfem_step_adjoint_implicit(npfem_batch* b, const void* x, const vo
     A.cg_tol = cg_tol;
     A.cg_max = cg_max_iters;
     A.status_out = status_out;
-    npfem_adjoint_implicit_kernel<<<L.blocks, 32 * L.warps_per_block, L.smem_bytes, st>>>(t->v64, P, A);
+    npfem_adjoint_implicit_kernel<<<L.blocks * L.warps_per_block, 32, L.smem_bytes / L.warps_per_block, st>>>(
+        t->v64, P, A);  // one warp per CTA, as the unrolled adjoint
     NPFEM_CUDA_TRY(cudaGetLastError());
   }
   return NPFEM_OK;
