@@ -1,4 +1,5 @@
-// Reverse mode of one npFEM step (K8), FP64, one warp per cell.
+// Reverse mode of one npFEM step (K8), FP64: a CTA per cell for the unrolled iteration,
+// a warp per cell for the implicit-function adjoint.
 //
 // The forward step is the quasi-Newton projective-dynamics iteration of the paper's
 // solid solver (Liu et al. 2017, named in the Implementation and architecture
@@ -16,6 +17,7 @@
 // with S = (F^T F)^1/2, dR = dF S^-1 - R dS S^-1 where S dS + dS S = dC solves in
 // closed form for 2x2 SPD S as dS = (dC + det(S) S^-1 dC S^-1) / (2 tr(S)).
 #pragma once
+#include "iter_cta.cuh"
 #include "step_kernel.cuh"
 
 namespace npfem {
@@ -84,10 +86,81 @@ __device__ __forceinline__ void vzero(double* y, int len, int lane) {
   for (int i = lane; i < len; i += 32) y[i] = 0.0;
 }
 
+// The threads that work on one cell: a warp (the implicit adjoint) or a CTA (the unrolled
+// adjoint's reverse sweep).  Element loops stride by size() from rank(); sync() orders the
+// team's memory accesses; sums<K>() turn per-thread FP64 partials into totals every member
+// receives (all members make the same sequence of calls); leader() writes per-cell
+// scalars; solver() marks the warp that runs the warp-level FP64 solve (lane() its lane).
+struct WarpTeam {
+  int lane_;
+  __device__ int rank() const { return lane_; }
+  __device__ int size() const { return 32; }
+  __device__ int lane() const { return lane_; }
+  __device__ bool leader() const { return lane_ == 0; }
+  __device__ bool solver() const { return true; }
+  __device__ void sync() const { __syncwarp(); }
+  template <int K>
+  __device__ void sums(double (&v)[K]) const {
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = warp_sum_d(v[k]);
+  }
+};
+struct CtaTeam {
+  CtaShared* sh;
+  int* par;
+  __device__ int rank() const { return threadIdx.x; }
+  __device__ int size() const { return blockDim.x; }
+  __device__ int lane() const { return threadIdx.x & 31; }
+  __device__ bool leader() const { return threadIdx.x == 0; }
+  __device__ bool solver() const { return threadIdx.x < 32; }
+  __device__ void sync() const { __syncthreads(); }
+  template <int K>
+  __device__ void sums(double (&v)[K]) const {
+    cta_sum<K>(v, *sh, *par);
+  }
+};
+
+template <class Tm>
+__device__ __forceinline__ double team_sum(const Tm& T, double x) {
+  double v[1] = {x};
+  T.sums(v);
+  return v[0];
+}
+template <class Tm>
+__device__ __forceinline__ void tvaxpy(const Tm& T, double* y, double a, const double* x, int len) {
+  for (int i = T.rank(); i < len; i += T.size()) y[i] = fma(a, x[i], y[i]);
+}
+template <class Tm>
+__device__ __forceinline__ void tvzero(const Tm& T, double* y, int len) {
+  for (int i = T.rank(); i < len; i += T.size()) y[i] = 0.0;
+}
+// a . b: plain products (as vdot) or through the FP64 accumulator (as vdot64)
+template <class Tm>
+__device__ __forceinline__ double tdot(const Tm& T, const double* a, const double* b, int len) {
+  double s = 0;
+  for (int i = T.rank(); i < len; i += T.size()) s += a[i] * b[i];
+  return team_sum(T, s);
+}
+template <class Tm>
+__device__ __forceinline__ double tdot64(const Tm& T, const double* a, const double* b, int len) {
+  Acc<double> s;
+  for (int i = T.rank(); i < len; i += T.size()) s.add_prod(a[i], b[i]);
+  return team_sum(T, s.part());
+}
+// The warp-level solve Q <- A^-1 Q run by the team's solver warp, visible to the team after.
+template <class Tm>
+__device__ __forceinline__ void team_solve(const Tm& T, const DevTypeView<double>& ty, const CellWs<double>& w,
+                                           const StepParams& P, const double* in, double* out) {
+  if (T.solver()) global_solve<double>(ty, w.z, P.z_in_smem != 0, in, out, T.lane(), P.solve_per_coord != 0);
+  T.sync();
+}
+
+template <class Tm>
 __device__ void matrix_weight_forms(const DevTypeView<double>& ty, const double* a, const double* b, double* fs,
-                                    double* fb, int lane);
+                                    double* fb, const Tm& T);
+template <class Tm>
 __device__ void apply_rayleigh(const DevTypeView<double>& ty, const CellWs<double>& w, const double* a,
-                               double* out, int lane);
+                               double* out, const Tm& T);
 
 // Strain limits: the projection P = U clamp(Sigma, lo, hi) V^T of F = [F0 F1] and its
 // directional derivative dP along dF, given the polar factor R = F (F^T F)^-1/2 and its
@@ -141,12 +214,13 @@ __device__ __noinline__ void limited_projection_jvp(V3<double> F0, V3<double> F1
 // Hessian-vector product out = grad^2 f(x) Vv at x = x_n + U (inertia and Rayleigh damping
 // included), and wd[q] = Vv . d(grad f)/d(w_q) for the four material weights.  With strain
 // limits the strain term differentiates the clamped projection (limited_projection_jvp).
+template <class Tm>
 __device__ void hessian_vector(const DevTypeView<double>& ty, const CellWs<double>& w, const double* U,
-                               const double* Vv, double* out, V3<double> cvol, double wd[4], int lane) {
+                               const double* Vv, double* out, V3<double> cvol, double wd[4], const Tm& Tm_) {
   const int n = ty.n, T = ty.T, E = ty.E;
   const double* X = w.X;
   Acc<double> a_sum, v_sum, da_sum, dv_sum, ws_sum, wb_sum;
-  for (int t = lane; t < T; t += 32) {
+  for (int t = Tm_.rank(); t < T; t += Tm_.size()) {
     int i0 = __ldg(&ty.tris[3 * t]), i1 = __ldg(&ty.tris[3 * t + 1]), i2 = __ldg(&ty.tris[3 * t + 2]);
     V3<double> e1 = edge(X, U, i0, i1), e2 = edge(X, U, i0, i2);
     V3<double> v0 = ld3(Vv, i0), de1 = ld3(Vv, i1) - v0, de2 = ld3(Vv, i2) - v0;
@@ -158,14 +232,16 @@ __device__ void hessian_vector(const DevTypeView<double>& ty, const CellWs<doubl
     v_sum.add(dot(q0, N));
     dv_sum.add(dot(v0, N) + dot(q0, dN));
   }
-  const double A = 0.5 * a_sum.total(), V = v_sum.total() / 6.0;
-  const double dAv = 0.5 * da_sum.total(), dVv = dv_sum.total() / 6.0;
+  double sv[4] = {a_sum.part(), v_sum.part(), da_sum.part(), dv_sum.part()};
+  Tm_.sums(sv);
+  const double A = 0.5 * sv[0], V = sv[1] / 6.0;
+  const double dAv = 0.5 * sv[2], dVv = sv[3] / 6.0;
   const double kA = ty.w_area * (A - ty.A0) / ty.A0, kV = ty.w_vol * (V - ty.V0) / ty.V0;
   const double cA = ty.w_area / ty.A0 * dAv, cV = ty.w_vol / ty.V0 * dVv;
   wd[2] = (A - ty.A0) / ty.A0 * dAv;
   wd[3] = (V - ty.V0) / ty.V0 * dVv;
 
-  for (int t = lane; t < T; t += 32) {
+  for (int t = Tm_.rank(); t < T; t += Tm_.size()) {
     int i0 = __ldg(&ty.tris[3 * t]), i1 = __ldg(&ty.tris[3 * t + 1]), i2 = __ldg(&ty.tris[3 * t + 2]);
     V3<double> e1 = edge(X, U, i0, i1), e2 = edge(X, U, i0, i2);
     V3<double> vv0 = ld3(Vv, i0), vv1 = ld3(Vv, i1), vv2 = ld3(Vv, i2);
@@ -230,7 +306,7 @@ __device__ void hessian_vector(const DevTypeView<double>& ty, const CellWs<doubl
     st3(w.corner, 3 * t + 1, g1);
     st3(w.corner, 3 * t + 2, g2);
   }
-  for (int h = lane; h < E; h += 32) {
+  for (int h = Tm_.rank(); h < E; h += Tm_.size()) {
     int i = __ldg(&ty.hinges[4 * h]), j = __ldg(&ty.hinges[4 * h + 1]);
     int ka = __ldg(&ty.hinges[4 * h + 2]), kb = __ldg(&ty.hinges[4 * h + 3]);
     const double c1 = __ldg(&ty.c_hinge[4 * h + 1]), c2 = __ldg(&ty.c_hinge[4 * h + 2]), c3 = __ldg(&ty.c_hinge[4 * h + 3]);
@@ -254,12 +330,16 @@ __device__ void hessian_vector(const DevTypeView<double>& ty, const CellWs<doubl
     st3(w.hbuf, h, hvec);
   }
   // Rayleigh damping: the quadratic (c_beta/dt) L and (c_alpha/dt) M terms, constant Hessians
-  if (ty.damp_l != 0.0)
-    damping_elastic<double>(ty.tris, ty.Dinv, ty.w_tri, ty.hinges, ty.c_hinge, ty.w_hinge, T, E, ty.damp_l, Vv,
-                            w.corner, w.hbuf, lane);
-  __syncwarp();
+  if (ty.damp_l != 0.0) {
+    // the warp-level elastic damping terms, added to every element's record by the solver warp
+    Tm_.sync();
+    if (Tm_.solver())
+      damping_elastic<double>(ty.tris, ty.Dinv, ty.w_tri, ty.hinges, ty.c_hinge, ty.w_hinge, T, E, ty.damp_l, Vv,
+                              w.corner, w.hbuf, Tm_.lane());
+  }
+  Tm_.sync();
   const double idt2 = 1.0 / (ty.dt * ty.dt);
-  for (int vtx = lane; vtx < n; vtx += 32) {
+  for (int vtx = Tm_.rank(); vtx < n; vtx += Tm_.size()) {
     V3<double> g = (__ldg(&ty.mass[vtx]) * idt2) * ld3(Vv, vtx);
     const int e0 = __ldg(&ty.inc_ptr[vtx]), e1 = __ldg(&ty.inc_ptr[vtx + 1]);
     for (int e = e0; e < e1; ++e) {
@@ -271,24 +351,27 @@ __device__ void hessian_vector(const DevTypeView<double>& ty, const CellWs<doubl
     }
     st3(out, vtx, g);
   }
-  if (ty.damp_m != 0.0) damping_mass<double>(ty.mass, n, ty.damp_m, Vv, out, lane);
-  wd[0] = ws_sum.total();
-  wd[1] = wb_sum.total();
+  if (ty.damp_m != 0.0) damping_mass<double>(ty.mass, n, ty.damp_m, Vv, out, Tm_.rank(), Tm_.size());
+  double sw[2] = {ws_sum.part(), wb_sum.part()};
+  Tm_.sums(sw);
+  wd[0] = sw[0];
+  wd[1] = sw[1];
   if (ty.damp_l != 0.0) {
     // d/dw of (c_beta/dt) L(w) U: the elastic matrix's weight forms between Vv and U
     double fs, fb;
-    matrix_weight_forms(ty, Vv, U, &fs, &fb, lane);
+    matrix_weight_forms(ty, Vv, U, &fs, &fb, Tm_);
     wd[0] += ty.damp_l * fs;
     wd[1] += ty.damp_l * fb;
   }
-  __syncwarp();
+  Tm_.sync();
 }
 
 // Quadratic forms a^T (dA/dw_strain) b and a^T (dA/dw_bend) b of the global matrix.
+template <class Tm>
 __device__ void matrix_weight_forms(const DevTypeView<double>& ty, const double* a, const double* b, double* fs,
-                                    double* fb, int lane) {
+                                    double* fb, const Tm& Tm_) {
   Acc<double> ss, sb;
-  for (int t = lane; t < ty.T; t += 32) {
+  for (int t = Tm_.rank(); t < ty.T; t += Tm_.size()) {
     int i0 = __ldg(&ty.tris[3 * t]), i1 = __ldg(&ty.tris[3 * t + 1]), i2 = __ldg(&ty.tris[3 * t + 2]);
     const double d00 = __ldg(&ty.Dinv[3 * t]), d01 = __ldg(&ty.Dinv[3 * t + 1]), d11 = __ldg(&ty.Dinv[3 * t + 2]);
     V3<double> a0 = ld3(a, i0), ae1 = ld3(a, i1) - a0, ae2 = ld3(a, i2) - a0;
@@ -297,7 +380,7 @@ __device__ void matrix_weight_forms(const DevTypeView<double>& ty, const double*
     V3<double> bF0 = d00 * be1, bF1 = d01 * be1 + d11 * be2;
     ss.add(__ldg(&ty.tri_area[t]) * (dot(aF0, bF0) + dot(aF1, bF1)));
   }
-  for (int h = lane; h < ty.E; h += 32) {
+  for (int h = Tm_.rank(); h < ty.E; h += Tm_.size()) {
     int i = __ldg(&ty.hinges[4 * h]), j = __ldg(&ty.hinges[4 * h + 1]);
     int ka = __ldg(&ty.hinges[4 * h + 2]), kb = __ldg(&ty.hinges[4 * h + 3]);
     const double c1 = __ldg(&ty.c_hinge[4 * h + 1]), c2 = __ldg(&ty.c_hinge[4 * h + 2]), c3 = __ldg(&ty.c_hinge[4 * h + 3]);
@@ -306,25 +389,30 @@ __device__ void matrix_weight_forms(const DevTypeView<double>& ty, const double*
     V3<double> Kb = c1 * (ld3(b, j) - bi) + c2 * (ld3(b, ka) - bi) + c3 * (ld3(b, kb) - bi);
     sb.add(__ldg(&ty.hinge_unit[h]) * dot(Ka, Kb));
   }
-  *fs = ss.total();
-  *fb = sb.total();
+  double v[2] = {ss.part(), sb.part()};
+  Tm_.sums(v);
+  *fs = v[0];
+  *fb = v[1];
 }
 
-// Reverse sweep of one cell after process_cell<double, true> filled the tape.
+// Reverse sweep of one cell after process_cell<double, true> filled the tape, by a team.
+template <class Tm>
 __device__ void reverse_cell(const DevTypeView<double>& ty, const StepParams& P, const AdjParams& A,
-                             const CellWs<double>& w, const AdjWs& aw, int cell, int iters, int lane) {
+                             const CellWs<double>& w, const AdjWs& aw, int cell, int iters, const Tm& T) {
   const int n = ty.n, len = 3 * n;
   const int64_t off = P.offsets[cell], Nt = P.n_total;
   const double dt = ty.dt;
   const double* tU = aw.tape.U;
   const double* tG = aw.tape.G;
   Acc<double> cxa, cya, cza;
-  for (int k = lane; k < n; k += 32) {
+  for (int k = T.rank(); k < n; k += T.size()) {
     cxa.add(w.X[3 * k]);
     cya.add(w.X[3 * k + 1]);
     cza.add(w.X[3 * k + 2]);
   }
-  V3<double> cvol{cxa.total() / n, cya.total() / n, cza.total() / n};
+  double cs[3] = {cxa.part(), cya.part(), cza.part()};
+  T.sums(cs);
+  V3<double> cvol{cs[0] / n, cs[1] / n, cs[2] / n};
   double wacc[4] = {0, 0, 0, 0};
   const int K = iters;
   // pairs kept by the forward pass (identical arithmetic to the forward history update)
@@ -332,30 +420,30 @@ __device__ void reverse_cell(const DevTypeView<double>& ty, const StepParams& P,
     double* sj = aw.sP + (size_t)j * len;
     double* yj = aw.yP + (size_t)j * len;
     Acc<double> asy;
-    for (int e = lane; e < len; e += 32) {
+    for (int e = T.rank(); e < len; e += T.size()) {
       double s = tU[(size_t)(j + 1) * len + e] - tU[(size_t)j * len + e];
       double y = tG[(size_t)(j + 1) * len + e] - tG[(size_t)j * len + e];
       sj[e] = s;
       yj[e] = y;
       asy.add_prod(s, y);
     }
-    double sy = asy.total();
-    if (lane == 0) aw.rho[j] = 1.0 / sy;
+    double sy = team_sum(T, asy.part());
+    if (T.leader()) aw.rho[j] = 1.0 / sy;
   }
-  for (int k = 0; k <= K; ++k) vzero(aw.gbar + (size_t)k * len, len, lane);
+  for (int k = 0; k <= K; ++k) tvzero(T, aw.gbar + (size_t)k * len, len);
   for (int j = 0; j < K; ++j) {
-    vzero(aw.sbar + (size_t)j * len, len, lane);
-    vzero(aw.ybar + (size_t)j * len, len, lane);
+    tvzero(T, aw.sbar + (size_t)j * len, len);
+    tvzero(T, aw.ybar + (size_t)j * len, len);
   }
-  vzero(aw.YB, len, lane);
+  tvzero(T, aw.YB, len);
   // dL/dx_K = dL/dx_{n+1} + dL/dv_{n+1} / dt
-  for (int k = lane; k < n; k += 32)
+  for (int k = T.rank(); k < n; k += T.size())
     for (int c = 0; c < 3; ++c) {
       double gxv = A.gx_next[c * Nt + off + k];
       double gvv = A.gv_next ? A.gv_next[c * Nt + off + k] : 0.0;
       aw.XB[3 * k + c] = gxv + gvv / dt;
     }
-  __syncwarp();
+  T.sync();
   double wd[4];
   for (int k = K - 1; k >= 0; --k) {
     const int fl = aw.tape.flags[k];
@@ -367,28 +455,28 @@ __device__ void reverse_cell(const DevTypeView<double>& ty, const StepParams& P,
     if (fl & kTapeKept) {
       const double* sb = aw.sbar + (size_t)k * len;
       const double* yb = aw.ybar + (size_t)k * len;
-      for (int e = lane; e < len; e += 32) {
+      for (int e = T.rank(); e < len; e += T.size()) {
         aw.XB[e] += sb[e];
         gb1[e] += yb[e];
         gbk[e] -= yb[e];
       }
-      __syncwarp();
+      T.sync();
     }
     // (2) g_{k+1} = grad f(x_{k+1}): dL/dx_{k+1} += H gbar_{k+1}; dL/dy -= M/dt^2 gbar; weights
-    hessian_vector(ty, w, xk1, gb1, aw.HV, cvol, wd, lane);
+    hessian_vector(ty, w, xk1, gb1, aw.HV, cvol, wd, T);
     for (int q = 0; q < 4; ++q) wacc[q] += wd[q];
-    for (int vtx = lane; vtx < n; vtx += 32) {
+    for (int vtx = T.rank(); vtx < n; vtx += T.size()) {
       const double mi = __ldg(&ty.mass[vtx]) / (dt * dt);
       for (int c = 0; c < 3; ++c) {
         aw.XB[3 * vtx + c] += aw.HV[3 * vtx + c];
         aw.YB[3 * vtx + c] -= mi * gb1[3 * vtx + c];
       }
     }
-    __syncwarp();
+    T.sync();
     // (3) x_{k+1} = x_k + alpha d_k: dL/dd_k = alpha dL/dx_{k+1}; dL/dx_k = dL/dx_{k+1} - sbar_k
-    for (int e = lane; e < len; e += 32) aw.DB[e] = alpha * aw.XB[e];
-    if (fl & kTapeKept) vaxpy(aw.XB, -1.0, aw.sbar + (size_t)k * len, len, lane);
-    __syncwarp();
+    for (int e = T.rank(); e < len; e += T.size()) aw.DB[e] = alpha * aw.XB[e];
+    if (fl & kTapeKept) tvaxpy(T, aw.XB, -1.0, aw.sbar + (size_t)k * len, len);
+    T.sync();
     // (4) d_k = -H_k g_k: active pairs at iteration k (newest first)
     int plist[kHistory];
     int h = 0;
@@ -412,58 +500,58 @@ __device__ void reverse_cell(const DevTypeView<double>& ty, const StepParams& P,
     // forward recompute of the two-loop with intermediates: Qs[t] before pair plist[t]
     double acoef[kHistory], bcoef[kHistory], abar[kHistory];
     const double* gk = tG + (size_t)k * len;
-    copy_vec<double>(aw.Qs, gk, len, lane);
-    __syncwarp();
+    for (int e = T.rank(); e < len; e += T.size()) aw.Qs[e] = gk[e];
+    T.sync();
     for (int t = 0; t < h; ++t) {
       const int i = plist[t];
       const double* si = aw.sP + (size_t)i * len;
       const double* yi = aw.yP + (size_t)i * len;
       double* qt = aw.Qs + (size_t)t * len;
       double* qn = aw.Qs + (size_t)(t + 1) * len;
-      acoef[t] = aw.rho[i] * vdot<double>(si, qt, len, lane);
-      for (int e = lane; e < len; e += 32) qn[e] = qt[e] - acoef[t] * yi[e];
-      __syncwarp();
+      acoef[t] = aw.rho[i] * tdot(T, si, qt, len);
+      for (int e = T.rank(); e < len; e += T.size()) qn[e] = qt[e] - acoef[t] * yi[e];
+      T.sync();
       abar[t] = 0.0;
     }
-    global_solve<double>(ty, w.z, P.z_in_smem != 0, aw.Qs + (size_t)h * len, aw.Rs, lane, P.solve_per_coord != 0);
+    team_solve(T, ty, w, P, aw.Qs + (size_t)h * len, aw.Rs);
     for (int u = 0; u < h; ++u) {
       const int t = h - 1 - u, i = plist[t];
       const double* si = aw.sP + (size_t)i * len;
       const double* yi = aw.yP + (size_t)i * len;
       const double* ru = aw.Rs + (size_t)u * len;
       double* rn = aw.Rs + (size_t)(u + 1) * len;
-      bcoef[u] = aw.rho[i] * vdot<double>(yi, ru, len, lane);
+      bcoef[u] = aw.rho[i] * tdot(T, yi, ru, len);
       const double c = acoef[t] - bcoef[u];
-      for (int e = lane; e < len; e += 32) rn[e] = ru[e] + c * si[e];
-      __syncwarp();
+      for (int e = T.rank(); e < len; e += T.size()) rn[e] = ru[e] + c * si[e];
+      T.sync();
     }
     // reverse: dL/dr_h = -dL/dd_k
-    for (int e = lane; e < len; e += 32) aw.RB[e] = -aw.DB[e];
+    for (int e = T.rank(); e < len; e += T.size()) aw.RB[e] = -aw.DB[e];
     for (int q = 0; q < h; ++q)
-      if (lane == 0) aw.rhobar[plist[q]] = 0.0;
-    __syncwarp();
+      if (T.leader()) aw.rhobar[plist[q]] = 0.0;
+    T.sync();
     for (int u = h - 1; u >= 0; --u) {
       const int t = h - 1 - u, i = plist[t];
       const double* si = aw.sP + (size_t)i * len;
       const double* yi = aw.yP + (size_t)i * len;
       const double* ru = aw.Rs + (size_t)u * len;
       const double c = acoef[t] - bcoef[u];
-      const double cb = vdot64<double>(aw.RB, si, len, lane);
-      vaxpy(aw.sbar + (size_t)i * len, c, aw.RB, len, lane);
+      const double cb = tdot64(T, aw.RB, si, len);
+      const double yr = tdot64(T, yi, ru, len);
+      tvaxpy(T, aw.sbar + (size_t)i * len, c, aw.RB, len);
       abar[t] += cb;
       const double bb = -cb;
-      const double yr = vdot64<double>(yi, ru, len, lane);
-      if (lane == 0) aw.rhobar[i] += bb * yr;
-      vaxpy(aw.ybar + (size_t)i * len, bb * aw.rho[i], ru, len, lane);
-      vaxpy(aw.RB, bb * aw.rho[i], yi, len, lane);
-      __syncwarp();
+      if (T.leader()) aw.rhobar[i] += bb * yr;
+      tvaxpy(T, aw.ybar + (size_t)i * len, bb * aw.rho[i], ru, len);
+      tvaxpy(T, aw.RB, bb * aw.rho[i], yi, len);
+      T.sync();
     }
     // r_0 = A^-1 q_h: dL/dq_h = A^-1 dL/dr_0; dL/dw via dA/dw (A carries the elastic part
     // L as (1 + c_beta/dt) L under Rayleigh damping)
-    global_solve<double>(ty, w.z, P.z_in_smem != 0, aw.RB, aw.QB, lane, P.solve_per_coord != 0);
+    team_solve(T, ty, w, P, aw.RB, aw.QB);
     {
       double fs, fb;
-      matrix_weight_forms(ty, aw.QB, aw.Rs, &fs, &fb, lane);
+      matrix_weight_forms(ty, aw.QB, aw.Rs, &fs, &fb, T);
       wacc[0] -= (1.0 + ty.damp_l) * fs;
       wacc[1] -= (1.0 + ty.damp_l) * fb;
     }
@@ -472,42 +560,42 @@ __device__ void reverse_cell(const DevTypeView<double>& ty, const StepParams& P,
       const double* si = aw.sP + (size_t)i * len;
       const double* yi = aw.yP + (size_t)i * len;
       const double* qt = aw.Qs + (size_t)t * len;
-      abar[t] -= vdot64<double>(yi, aw.QB, len, lane);
-      vaxpy(aw.ybar + (size_t)i * len, -acoef[t], aw.QB, len, lane);
-      const double sq = vdot64<double>(si, qt, len, lane);
-      if (lane == 0) aw.rhobar[i] += abar[t] * sq;
-      vaxpy(aw.sbar + (size_t)i * len, abar[t] * aw.rho[i], qt, len, lane);
-      vaxpy(aw.QB, abar[t] * aw.rho[i], si, len, lane);
-      __syncwarp();
+      abar[t] -= tdot64(T, yi, aw.QB, len);
+      const double sq = tdot64(T, si, qt, len);
+      tvaxpy(T, aw.ybar + (size_t)i * len, -acoef[t], aw.QB, len);
+      if (T.leader()) aw.rhobar[i] += abar[t] * sq;
+      tvaxpy(T, aw.sbar + (size_t)i * len, abar[t] * aw.rho[i], qt, len);
+      tvaxpy(T, aw.QB, abar[t] * aw.rho[i], si, len);
+      T.sync();
     }
-    vaxpy(gbk, 1.0, aw.QB, len, lane);
-    __syncwarp();
+    tvaxpy(T, gbk, 1.0, aw.QB, len);
+    T.sync();
     // rho_i = 1/(y_i . s_i)
     for (int t = 0; t < h; ++t) {
       const int i = plist[t];
       const double r2 = aw.rho[i] * aw.rho[i] * aw.rhobar[i];
-      vaxpy(aw.ybar + (size_t)i * len, -r2, aw.sP + (size_t)i * len, len, lane);
-      vaxpy(aw.sbar + (size_t)i * len, -r2, aw.yP + (size_t)i * len, len, lane);
+      tvaxpy(T, aw.ybar + (size_t)i * len, -r2, aw.sP + (size_t)i * len, len);
+      tvaxpy(T, aw.sbar + (size_t)i * len, -r2, aw.yP + (size_t)i * len, len);
     }
-    __syncwarp();
+    T.sync();
   }
   // g_0 = grad f(x_0)
-  hessian_vector(ty, w, tU, aw.gbar, aw.HV, cvol, wd, lane);
+  hessian_vector(ty, w, tU, aw.gbar, aw.HV, cvol, wd, T);
   for (int q = 0; q < 4; ++q) wacc[q] += wd[q];
   // Rayleigh damping: every g_k holds C (x_k - x_n) / dt, so dL/dx_n gains
   // -C/dt times the sum of all gradient adjoints (into RB, summed in DB)
   const bool damped = ty.damp_m != 0.0 || ty.damp_l != 0.0;
   if (damped) {
-    for (int e = lane; e < len; e += 32) {
+    for (int e = T.rank(); e < len; e += T.size()) {
       double sg = 0.0;
       for (int k = 0; k <= K; ++k) sg += aw.gbar[(size_t)k * len + e];
       aw.DB[e] = sg;
     }
-    __syncwarp();
-    apply_rayleigh(ty, w, aw.DB, aw.RB, lane);
+    T.sync();
+    apply_rayleigh(ty, w, aw.DB, aw.RB, T);
   }
   // x_0 = y; y = x_n + dt v_n + dt^2 M^-1 f;  v_{n+1} = (x_K - x_n)/dt
-  for (int vtx = lane; vtx < n; vtx += 32) {
+  for (int vtx = T.rank(); vtx < n; vtx += T.size()) {
     const double mi = __ldg(&ty.mass[vtx]);
     for (int c = 0; c < 3; ++c) {
       const int e = 3 * vtx + c;
@@ -518,50 +606,64 @@ __device__ void reverse_cell(const DevTypeView<double>& ty, const StepParams& P,
       A.gf[c * Nt + off + vtx] = dt * dt / mi * yb;
     }
   }
-  if (lane == 0)
+  if (T.leader())
     for (int q = 0; q < 4; ++q) A.gw[(size_t)cell * 4 + q] = wacc[q];
-  __syncwarp();
+  T.sync();
 }
 
-__global__ void __launch_bounds__(128) npfem_adjoint_kernel(DevTypeView<double> ty, StepParams P, AdjParams A,
-                                                             const double* x, const double* v, const double* f) {
+// The unrolled adjoint, one CTA of kAdjWarps warps per cell (work queue over the cells).
+// Warp 0 recomputes the forward step with the tape (the warp-level fused step, whose
+// iterates are the FP64 split step's bit for bit) and runs the warp-level FP64 solves;
+// the reverse sweep's vector passes, Hessian-vector products and sums use the whole CTA
+// (a warp per cell kept the FP64 pipe about 20 % busy: each warp waits on its memory).
+// Each CTA uses one workspace slot and one solve vector in shared memory.
+constexpr int kAdjWarps = 4;
+__global__ void __launch_bounds__(32 * kAdjWarps) npfem_adjoint_kernel(DevTypeView<double> ty, StepParams P,
+                                                                       AdjParams A, const double* x,
+                                                                       const double* v, const double* f) {
   extern __shared__ double smem_z[];
+  __shared__ CtaShared sh;
+  int par = 0;
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const int slot = blockIdx.x * (blockDim.x >> 5) + wib;
-  double* zs = P.z_in_smem ? smem_z + (size_t)wib * (P.solve_per_coord ? 1 : 3) * (ty.n + 1) : nullptr;
+  const int slot = blockIdx.x;
+  double* zs = P.z_in_smem ? smem_z : nullptr;
   CellWs<double> w = carve<double>(P.scratch + (size_t)slot * P.slot_bytes, ty.n, ty.T, ty.E, zs);
   AdjWs aw = carve_adj(A.scratch + (size_t)slot * A.slot_bytes, ty.n);
+  const CtaTeam team{&sh, &par};
   for (;;) {
-    int item = 0;
-    if (lane == 0) item = atomicAdd(P.queue_counter, 1);
-    item = __shfl_sync(kFull, item, 0);
+    if (threadIdx.x == 0) sh.item = atomicAdd(P.queue_counter, 1);
+    __syncthreads();
+    const int item = sh.item;
+    __syncthreads();
     if (item >= P.ncells_list) break;
     const int cell = P.cell_list[item];
     const int iters = P.iters ? P.iters[cell] : P.iters_default;
-    if (iters < 0 || iters > kMaxAdjIters) {
-      if (lane == 0 && P.status_out) P.status_out[cell] = 8;
+    if (iters < 0 || iters > kMaxAdjIters) {  // the same for the whole CTA
+      if (threadIdx.x == 0 && P.status_out) P.status_out[cell] = 8;
       continue;
     }
-    process_cell<double, true>(ty, P, w, cell, const_cast<double*>(x), const_cast<double*>(v), f, lane, &aw.tape);
-    reverse_cell(ty, P, A, w, aw, cell, iters, lane);
-    if (lane == 0 && P.status_out) P.status_out[cell] = 0;
+    if (threadIdx.x < 32)
+      process_cell<double, true>(ty, P, w, cell, const_cast<double*>(x), const_cast<double*>(v), f, lane, &aw.tape);
+    __syncthreads();
+    reverse_cell(ty, P, A, w, aw, cell, iters, team);
+    if (threadIdx.x == 0 && P.status_out) P.status_out[cell] = 0;
   }
 }
 
 // out = C a / dt = (c_alpha/dt) M a + (c_beta/dt) L a (Rayleigh damping), through the
 // element buffers and the gradient gather of the step.
+template <class Tm>
 __device__ void apply_rayleigh(const DevTypeView<double>& ty, const CellWs<double>& w, const double* a,
-                               double* out, int lane) {
+                               double* out, const Tm& T) {
   const int n = ty.n;
-  for (int i = lane; i < 9 * ty.T; i += 32) w.corner[i] = 0.0;
-  for (int i = lane; i < 3 * ty.E; i += 32) w.hbuf[i] = 0.0;
-  __syncwarp();
-  if (ty.damp_l != 0.0)
+  for (int i = T.rank(); i < 9 * ty.T; i += T.size()) w.corner[i] = 0.0;
+  for (int i = T.rank(); i < 3 * ty.E; i += T.size()) w.hbuf[i] = 0.0;
+  T.sync();
+  if (ty.damp_l != 0.0 && T.solver())
     damping_elastic<double>(ty.tris, ty.Dinv, ty.w_tri, ty.hinges, ty.c_hinge, ty.w_hinge, ty.T, ty.E, ty.damp_l,
-                            a, w.corner, w.hbuf, lane);
-  __syncwarp();
-  for (int vtx = lane; vtx < n; vtx += 32) {
+                            a, w.corner, w.hbuf, T.lane());
+  T.sync();
+  for (int vtx = T.rank(); vtx < n; vtx += T.size()) {
     V3<double> g = (ty.damp_m * __ldg(&ty.mass[vtx])) * ld3(a, vtx);
     const int e0 = __ldg(&ty.inc_ptr[vtx]), e1 = __ldg(&ty.inc_ptr[vtx + 1]);
     for (int e = e0; e < e1; ++e) {
@@ -573,7 +675,7 @@ __device__ void apply_rayleigh(const DevTypeView<double>& ty, const CellWs<doubl
     }
     st3(out, vtx, g);
   }
-  __syncwarp();
+  T.sync();
 }
 
 // ------------------------------------------------------------------ implicit adjoint
@@ -660,7 +762,7 @@ __global__ void __launch_bounds__(128) npfem_adjoint_implicit_kernel(DevTypeView
       __syncwarp();
       double rz = vdot64<double>(r, z, len, lane);
       for (int it = 0; it < A.cg_max; ++it) {
-        hessian_vector(ty, w, U, pv, hp, cvol, wd, lane);
+        hessian_vector(ty, w, U, pv, hp, cvol, wd, WarpTeam{lane});
         const double php = vdot64<double>(pv, hp, len, lane);
         if (!(php > 0.0)) break;  // not positive definite along p: stop, report
         const double a = rz / php;
@@ -681,9 +783,9 @@ __global__ void __launch_bounds__(128) npfem_adjoint_implicit_kernel(DevTypeView
       }
     }
     // weight derivatives: wd[q] = lam . d(grad f)/d(w_q)
-    hessian_vector(ty, w, U, lam, hp, cvol, wd, lane);
+    hessian_vector(ty, w, U, lam, hp, cvol, wd, WarpTeam{lane});
     const bool damped = ty.damp_m != 0.0 || ty.damp_l != 0.0;
-    if (damped) apply_rayleigh(ty, w, lam, z, lane);  // z <- C lam / dt
+    if (damped) apply_rayleigh(ty, w, lam, z, WarpTeam{lane});  // z <- C lam / dt
     for (int vtx = lane; vtx < n; vtx += 32) {
       const double mi = __ldg(&ty.mass[vtx]);
       for (int c = 0; c < 3; ++c) {

@@ -960,8 +960,7 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
   e = cudaFuncSetAttribute(npfem_step_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(npfem_step_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(npfem_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+  if (e == cudaSuccess) e = allow_dynamic_smem(npfem_adjoint_kernel, smem_optin);
   if (e == cudaSuccess) e = allow_dynamic_smem(npfem_adjoint_implicit_kernel, smem_optin);
   if (e == cudaSuccess)
     e = set_solve_smem_attr<double>(smem_optin);
@@ -1157,10 +1156,10 @@ npfem_status npfem_step_adjoint(npfem_batch* b, const void* x, const void* v, co
     A.w_mat[1] = 0;
     A.w_mat[2] = H.w_area;
     A.w_mat[3] = H.w_vol;
-    // one warp per CTA over the launch's warp slots (the same slots and per-warp shared
-    // memory as the fused step): the adjoint is FP64 bound at a warp per cell, so its few
-    // warps are spread over every SM rather than packed four to an SM
-    npfem_adjoint_kernel<<<L.blocks * L.warps_per_block, 32, L.smem_bytes / L.warps_per_block, st>>>(
+    // one CTA of kAdjWarps warps per cell, over the launch's warp slots (one slot and one
+    // solve vector in shared memory per CTA)
+    const int adj_blocks = std::max(1, std::min(L.blocks * L.warps_per_block, L.ncells));
+    npfem_adjoint_kernel<<<adj_blocks, 32 * kAdjWarps, L.smem_bytes / L.warps_per_block, st>>>(
         t->v64, P, A, static_cast<const double*>(x), static_cast<const double*>(v), static_cast<const double*>(f_ext));
     NPFEM_CUDA_TRY(cudaGetLastError());
   }
