@@ -266,7 +266,9 @@ npfem_status npfem_step_adjoint_implicit(npfem_batch* batch, const void* x, cons
  * solve vector lives in shared memory (1) or in the workspace (0), and whether the
  * three coordinates share each triangular sweep (solve_per_coord = 0, vector of
  * 24*(n+1) bytes) or are swept one after another (1, vector of 8*(n+1) bytes).
- * Results do not depend on the shape.  Reallocates that type's workspace; synchronises
+ * The adjoints use the shape's warp slots and solve placement too: the unrolled adjoint
+ * runs a CTA of four warps per cell over them (one slot each), the implicit adjoint one
+ * warp per cell.  Results do not depend on the shape.  Reallocates that type's workspace; synchronises
  * the device.  Default: 4 warps, 3 CTAs/SM, shared memory when four interleaved
  * vectors fit in 72 KB.  Errors: INVALID_ARG, UNSUPPORTED (vectors exceed shared
  * memory), OOM.  npfem_batch_get_launch fills shape[5] = {warps per CTA, CTAs per SM,
