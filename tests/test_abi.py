@@ -76,6 +76,17 @@ def test_element_colour_classes(lib):
     assert info["n_tris"] == 140
 
 
+def test_ordering_fill_on_the_workload_meshes(lib):
+    """The fill-reducing ordering (least fill among plane-cut nested dissections with
+    one-sided and cut-cover separators, the latter reordered by constrained minimum
+    degree, and exact minimum degree up to 1500 vertices) keeps nnz(L) of the workload
+    meshes at the values it reaches: the FP64 solve's work is 12 nnz(L) + 3n per
+    cell-solve, so a regression here is a slower step."""
+    for m, bound in ((I.platelet_mesh(2), 4226), (I.rbc_mesh(3), 27615), (I.rbc_mesh(4), 161174)):
+        info = native.analyze_cell_type(m.verts, m.tris, I.RBC_MATERIAL.as_tuple(), I.DT_DEFAULT)
+        assert info["nnz_factor"] <= bound, (m.name, info["nnz_factor"], bound)
+
+
 def test_analyze_matches_oracle_rest_quantities(lib):
     from oracle import npfem_oracle as O
     for m in (I.tetrahedron(), I.icosahedron(), I.platelet_mesh(1), I.rbc_mesh(2)):
