@@ -16,6 +16,7 @@
 #include <map>
 #include <numeric>
 #include <functional>
+#include <iterator>
 #include <set>
 #include <utility>
 
@@ -455,13 +456,16 @@ void covered_dissection(const Graph& g, const std::vector<V3>& p, const std::vec
 // last block, the top separator, keeps its order: its fill is dense whatever the order).
 std::vector<int> constrained_minimum_degree(const Graph& g, const std::vector<int>& stage, int nstage) {
   const int n = (int)g.size();
-  std::vector<std::set<int>> nb(n);
-  for (int v = 0; v < n; ++v)
+  std::vector<std::vector<int>> nb(n);  // sorted neighbour lists of the elimination graph
+  for (int v = 0; v < n; ++v) {
     for (int u : g[v])
-      if (u != v) nb[v].insert(u);
+      if (u != v) nb[v].push_back(u);
+    std::sort(nb[v].begin(), nb[v].end());
+    nb[v].erase(std::unique(nb[v].begin(), nb[v].end()), nb[v].end());
+  }
   std::set<std::array<int, 3>> pq;
   for (int v = 0; v < n; ++v) pq.insert({stage[v], (int)nb[v].size(), v});
-  std::vector<int> order;
+  std::vector<int> order, merged;
   order.reserve(n);
   while (!pq.empty()) {
     if ((*pq.begin())[0] == nstage - 1) {
@@ -472,12 +476,14 @@ std::vector<int> constrained_minimum_degree(const Graph& g, const std::vector<in
     const int v = (*pq.begin())[2];
     pq.erase(pq.begin());
     order.push_back(v);
-    const std::vector<int> N(nb[v].begin(), nb[v].end());
-    for (int a : N) {
+    const std::vector<int> N = nb[v];
+    for (int a : N) {  // eliminating v joins its neighbours into a clique
       pq.erase({stage[a], (int)nb[a].size(), a});
-      nb[a].erase(v);
-      for (int b : N)
-        if (b != a) nb[a].insert(b);
+      merged.clear();
+      std::set_union(nb[a].begin(), nb[a].end(), N.begin(), N.end(), std::back_inserter(merged));
+      merged.erase(std::remove_if(merged.begin(), merged.end(), [&](int x) { return x == a || x == v; }),
+                   merged.end());
+      nb[a].swap(merged);
       pq.insert({stage[a], (int)nb[a].size(), a});
     }
   }
