@@ -265,7 +265,8 @@ npfem_status npfem_step_adjoint_implicit(npfem_batch* batch, const void* x, cons
  * (1..4; one warp advances one cell), CTAs per SM (1..16), whether each warp's FP64
  * solve vector lives in shared memory (1) or in the workspace (0), and whether the
  * three coordinates share each triangular sweep (solve_per_coord = 0, vector of
- * 24*(n+1) bytes) or are swept one after another (1, vector of 8*(n+1) bytes).
+ * 24*(n+1) bytes) or are swept one after another (1, vector of 8*(n+1) bytes; applies
+ * to a vector in shared memory only: one in the workspace is always swept whole).
  * The adjoints use the shape's warp slots and solve placement too: the unrolled adjoint
  * runs a CTA of four warps per cell over them (one slot each), the implicit adjoint one
  * warp per cell.  Results do not depend on the shape.  Reallocates that type's workspace; synchronises

@@ -249,13 +249,17 @@ static npfem_status configure_launch(npfem_batch* b, TypeLaunch& L, int wpb, int
   const HostType& H = b->types[L.type_index]->host;
   if (wpb < 1 || wpb > 4 || bps < 1 || bps > 16) return fail(NPFEM_ERR_INVALID_ARG, "launch: warps/CTA in 1..4, CTAs/SM in 1..16");
   const size_t ssize = b->prec == NPFEM_FP64 ? sizeof(double) : sizeof(float);
+  // the per-coordinate sweep only narrows a vector kept in shared memory; a vector in the
+  // workspace is always the full [n+1][3] one (the solve sweeps it with the three
+  // coordinates together)
   const size_t zbytes = sizeof(double) * (per_coord ? 1 : 3) * ((size_t)H.n + 1);
+  const size_t zbytes_ws = sizeof(double) * 3 * ((size_t)H.n + 1);
   const size_t smem = zsmem ? zbytes * wpb : 0;
   if (smem > (size_t)b->smem_optin) return fail(NPFEM_ERR_UNSUPPORTED, "launch: solve vectors exceed shared memory");
   size_t v = (size_t)3 * H.n;
   size_t bytes = ssize * ((8 + 2 * kHistory) * v + 9 * (size_t)H.T + 3 * (size_t)H.E);
   bytes = (bytes + 255) & ~(size_t)255;
-  if (!zsmem) bytes += zbytes;
+  if (!zsmem) bytes += zbytes_ws;
   bytes = (bytes + 255) & ~(size_t)255;
   const int blocks = std::max(1, std::min<int>(b->sms * bps, (L.ncells + wpb - 1) / wpb));
   void* scr = nullptr;

@@ -95,6 +95,44 @@ def test_adjoint_dot_product_against_oracle_forward_mode(seed, damping):
         assert r2 == pytest.approx(l2, rel=1e-8, abs=1e-12 * abs(lhs)), f"block {blk}"
 
 
+def test_adjoint_launch_shapes_agree():
+    """The unrolled adjoint (a CTA of four warps per cell over the launch's warp slots)
+    gives the same bits whatever the launch shape: the solve vector in shared memory or in
+    the workspace (the path of types whose vectors do not fit, such as 2562 vertices), the
+    three coordinates swept together or one after another, and 1 to 4 warp slots per CTA
+    of the step (other slot counts and CTA grids).  Damped, so every term is exercised."""
+    nat = _native()
+    b = I.small_mixed_batch(seed=11, iters=(2, 5))
+    damping = (0.5, 1.0)
+    types = [nat.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple() + damping, b.dt) for t in b.types]
+    batch = nat.Batch(types, b.type_of_cell, nat.FP64)
+    dev = torch.device("cuda:0")
+    T = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+    rng = np.random.default_rng(11)
+    x, v, f = T(b.x), T(b.v), T(b.f)
+    gxn, gvn = T(rng.standard_normal(b.x.shape)), T(rng.standard_normal(b.x.shape) * 1e-2)
+    it = torch.tensor(b.iters, device=dev)
+
+    def run():
+        gx, gv, gf = torch.zeros_like(x), torch.zeros_like(x), torch.zeros_like(x)
+        gw = torch.zeros((b.ncells, 4), dtype=torch.float64, device=dev)
+        st = torch.full((b.ncells,), -1, dtype=torch.int32, device=dev)
+        batch.step_adjoint(x, v, f, gxn, gvn, gx, gv, gf, gw, iters=it, status=st)
+        torch.cuda.synchronize()
+        assert int(st.max()) == 0 and int(st.min()) == 0
+        return [a.cpu().numpy() for a in (gx, gv, gf, gw)]
+
+    ref = run()
+    assert all(np.isfinite(a).all() for a in ref) and np.abs(ref[3]).max() > 0
+    for wpb, bps, shared, per_coord in ((4, 3, False, False), (4, 3, True, True), (1, 8, True, False),
+                                        (2, 2, False, True)):
+        for t in range(len(types)):
+            batch.set_launch(t, wpb, bps, shared, per_coord)
+        out = run()
+        for a, c in zip(ref, out):
+            assert np.array_equal(a, c), (wpb, bps, shared, per_coord)
+
+
 def test_adjoint_matches_central_differences_rbc642():
     """Eight placed 642-vertex RBCs (the calibration workload's cells), FP64: the adjoint
     of L = lambda.v_{n+1} w.r.t. forces and the four weights against central differences
