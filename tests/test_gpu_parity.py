@@ -333,6 +333,28 @@ def test_launch_shapes_give_identical_results():
     assert np.array_equal(x2, x0)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fused_mode_launch_shapes_give_identical_results(prec):
+    """The fused persistent kernel (mode 0) under the launch shapes of
+    npfem_batch_set_launch, the per-coordinate choice with the solve vector in the
+    workspace included (which then sweeps the whole vector): identical states."""
+    nat = _native()
+    b = I.heterogeneous_batch(n_rbc3=5, n_rbc4=2, n_plt=5, seed=1013)
+    r = Runner(b, nat.FP64 if prec == "fp64" else nat.FP32FORM)
+    r.batch.set_mode(False)
+    ref = r.step(b.x, b.v, b.f, iters=b.iters)
+    for shape in ((4, 3, False, False), (2, 2, False, True), (1, 8, True, False), (3, 1, True, True)):
+        for t in range(len(b.types)):
+            n = b.types[t].mesh.n
+            if shape[2] and shape[0] * (8 if shape[3] else 24) * (n + 1) > 72 * 1024:
+                continue  # vectors that do not fit shared memory at this width
+            r.batch.set_launch(t, *shape)
+        out = r.step(b.x, b.v, b.f, iters=b.iters)
+        for a, c in zip(ref, out):
+            assert np.array_equal(a, c), shape
+    r.batch.set_mode(True)
+
+
 def test_cuda_graph_replay_equals_direct_steps():
     """npfem_step is capturable: a captured step replayed twice gives the same state as
     two direct calls."""
