@@ -338,7 +338,8 @@ static void default_split_shape(TypeLaunch& L, int n, npfem_precision prec) {
   }
   // iteration kernels: 32 warps per SM in the FP32 form (64 registers), 16 in FP64
   L.it_wpb = 2, L.it_bps = prec == NPFEM_FP64 ? 8 : 16;
-  // large types run as several concurrent chains that fill each other's wave tails
+  // large types run as several concurrent chains that fill each other's wave tails (a
+  // batch of one type: see npfem_batch_create)
   L.groups = L.ncells >= 4096 ? 4 : (L.ncells >= 2048 ? 2 : 1);
   // fewer CTAs per SM where the SM cannot hold that many shared vectors; workspace
   // vectors where it cannot hold one
@@ -1007,6 +1008,14 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
       return fail(rc, msg);
     }
     b->launches.push_back(L);
+  }
+  // A batch of one cell type has no other type's chains to overlap with: its groups are
+  // its only concurrency, so it splits from 512 cells on (4 groups from 1024).  With
+  // several types each type keeps the rule of default_split_shape (more groups measured
+  // slower there: their chains already overlap).
+  if (b->launches.size() == 1) {
+    TypeLaunch& L = b->launches[0];
+    L.groups = L.ncells >= 1024 ? 4 : (L.ncells >= 512 ? 2 : 1);
   }
   *out = b;
   return NPFEM_OK;
