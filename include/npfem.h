@@ -307,8 +307,9 @@ npfem_status npfem_batch_set_mode(npfem_batch* batch, int32_t mode);
  * each with its own chain of kernels on its own stream, running concurrently: the
  * chains fill each other's wave tails and one group's FP32 iteration kernel overlaps
  * another group's FP64 solve.  Default: 4 groups for types with at least 4096 cells in
- * the batch, 2 from 2048, else 1; in a batch of one cell type (no other type's chains
- * to overlap with) 4 from 1024 cells, 2 from 512.  Results do not depend on the grouping.
+ * the batch, 2 from 2048, else 1; in an FP32-form batch of one cell type (no other
+ * type's chains to overlap with) 4 from 1024 cells, 2 from 512.  Results do not depend on
+ * the grouping.
  * NPFEM_ERR_INVALID_ARG for groups outside 1..4 or a type without cells in the batch. */
 npfem_status npfem_batch_set_groups(npfem_batch* batch, int32_t type_index, int32_t groups);
 

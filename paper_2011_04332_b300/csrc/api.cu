@@ -1009,11 +1009,13 @@ npfem_status npfem_batch_create(const npfem_cell_type* const* types, int32_t nty
     }
     b->launches.push_back(L);
   }
-  // A batch of one cell type has no other type's chains to overlap with: its groups are
-  // its only concurrency, so it splits from 512 cells on (4 groups from 1024).  With
-  // several types each type keeps the rule of default_split_shape (more groups measured
-  // slower there: their chains already overlap).
-  if (b->launches.size() == 1) {
+  // A batch of one cell type has no other type's chains to overlap with: in the FP32
+  // form its groups are its only concurrency, so it splits from 512 cells on (4 groups
+  // from 1024).  With several types each type keeps the rule of default_split_shape (more
+  // groups measured slower there: their chains already overlap), and so does the FP64
+  // form, whose iteration kernels compete with the solves for the FP64 pipe (1024 cells:
+  // 4 groups measured 16 % slower than 1).
+  if (b->launches.size() == 1 && prec != NPFEM_FP64) {
     TypeLaunch& L = b->launches[0];
     L.groups = L.ncells >= 1024 ? 4 : (L.ncells >= 512 ? 2 : 1);
   }
