@@ -485,6 +485,12 @@ def run_ours(args, rank, world, local_rank):
                                 "across concurrent chains, so the time is the union of their intervals, %.3f ms per "
                                 "step" % (round(solve_launches), solve_ms_total, solve_span)),
                 "kernel_share_of_step": solve_span / ms_per_step if ms_per_step else None,
+                # the same flops over the summed durations of the solve launches (average launch
+                # duration x launches): each launch shares the GPU with the other chains' kernels
+                # while it runs, so this reads lower than the union-of-intervals figure
+                "achieved_per_launch": (flops_per_step / (solve_ms_total / 1e3) / 1e12) if solve_ms_total > 0 else None,
+                "frac_per_launch": (flops_per_step / (solve_ms_total / 1e3) / 1e12 / fp64_peak)
+                if solve_ms_total > 0 and fp64_peak else None,
                 "step_frac": flops_per_step / (ms_per_step / 1e3) / 1e12 / fp64_peak if fp64_peak else None}
 
     # HBM: the method's algorithmic I/O (read x, v, f and write x, v: 15 scalars per vertex
