@@ -51,7 +51,8 @@ inline double cotangent(V3 a, V3 b) { return dot(a, b) / norm(cross(a, b)); }
 //  2. balancing: an element moves from a colour whose last pass is partly filled to one
 //     whose last pass has room and that no neighbour has, when that takes a pass away
 //     and adds none — first out of the colours that spill over into an extra pass (the
-//     emptiest last pass first), then out of the smallest colours until they are empty.
+//     emptiest last pass first), then out of the smallest colours until they are empty;
+//  3. within each colour, an order for the shared-memory banks (below).
 // Returns false (and leaves the elements as they were) if more than kMaxColours colours
 // would be needed.
 bool colour_elements(int n, int k, int nt, std::vector<int32_t>* elems, std::vector<int32_t>* cptr) {
@@ -152,6 +153,104 @@ bool colour_elements(int n, int k, int nt, std::vector<int32_t>* elems, std::vec
   for (int e = 0; e < m; ++e) {
     const int p = next[renum[colour[e]]]++;
     for (int j = 0; j < k; ++j) out[(size_t)k * p + j] = (*elems)[(size_t)k * e + j];
+  }
+  // 3. shared-memory banks: a warp of the CTA kernels takes 32 consecutive elements of a
+  // class, and its loads of the elements' j-th vertices (x_v at word 3v of the shared
+  // arrays, bank 3v mod 32) are conflict-free when those vertices differ mod 32.  Within
+  // each class, elements are dealt to warps greedily, each slot taking the element (and,
+  // for triangles, the cyclic rotation of its vertices, which keeps its orientation) that
+  // adds the fewest repeats of a residue at any vertex position.
+  {
+    std::vector<int32_t> dealt(out.size());
+    std::vector<int> pool;
+    for (size_t c = 0; c + 1 < cptr->size(); ++c) {
+      const int lo = (*cptr)[c], hi = (*cptr)[c + 1];
+      pool.clear();
+      for (int e = lo; e < hi; ++e) pool.push_back(e);
+      int slot = lo;
+      while (!pool.empty()) {
+        int cnt[4][32] = {};
+        for (int w = 0; w < 32 && !pool.empty(); ++w, ++slot) {
+          int best = -1, best_rot = 0, best_cost = 1 << 30;
+          for (int q = 0; q < (int)pool.size(); ++q) {
+            const int32_t* el = &out[(size_t)k * pool[q]];
+            for (int r = 0; r < (k == 3 ? 3 : 1); ++r) {
+              int cost = 0;
+              for (int j = 0; j < k; ++j) cost += cnt[j][el[(j + r) % k] & 31];
+              if (cost < best_cost) {
+                best_cost = cost;
+                best = q;
+                best_rot = r;
+              }
+            }
+            if (best_cost == 0) break;
+          }
+          const int32_t* el = &out[(size_t)k * pool[best]];
+          for (int j = 0; j < k; ++j) {
+            const int32_t vj = el[(j + best_rot) % k];
+            dealt[(size_t)k * slot + j] = vj;
+            ++cnt[j][vj & 31];
+          }
+          pool.erase(pool.begin() + best);
+        }
+      }
+      // then pairwise exchanges between the class's warps (with re-rotation of
+      // triangles) while they lower the number of same-residue pairs in some warp
+      const int nwarps = (hi - lo + 31) / 32;
+      if (nwarps < 2) continue;
+      std::vector<std::array<std::array<int, 32>, 4>> hist(nwarps);
+      for (auto& hw : hist)
+        for (auto& hp : hw) hp.fill(0);
+      for (int e = lo; e < hi; ++e)
+        for (int j = 0; j < k; ++j) ++hist[(e - lo) / 32][j][dealt[(size_t)k * e + j] & 31];
+      for (int sweep = 0; sweep < 4; ++sweep) {
+        bool improved = false;
+        for (int a = lo; a < hi; ++a)
+          for (int b = a + 1; b < hi; ++b) {
+            const int wa = (a - lo) / 32, wb = (b - lo) / 32;
+            if (wa == wb) continue;
+            int32_t* ea = &dealt[(size_t)k * a];
+            int32_t* eb = &dealt[(size_t)k * b];
+            // gain of moving b's vertices into warp a (rotation rb) and a's into warp b (ra)
+            int delta_best = 0, rab = 0, rbb = 0;
+            for (int ra = 0; ra < (k == 3 ? 3 : 1); ++ra)
+              for (int rb = 0; rb < (k == 3 ? 3 : 1); ++rb) {
+                int delta = 0;
+                for (int j = 0; j < k; ++j) {
+                  const int xa = ea[j] & 31, xb = eb[j] & 31;            // current residues
+                  const int na = ea[(j + ra) % k] & 31, nb = eb[(j + rb) % k] & 31;  // new
+                  // warp a loses xa, gains nb; warp b loses xb, gains na (pair counts)
+                  int ca = hist[wa][j][xa] - 1, cb = hist[wb][j][xb] - 1;
+                  delta -= ca + cb;
+                  delta += (nb == xa ? ca : hist[wa][j][nb]) + (na == xb ? cb : hist[wb][j][na]);
+                }
+                if (delta < delta_best) {
+                  delta_best = delta;
+                  rab = ra;
+                  rbb = rb;
+                }
+              }
+            if (delta_best < 0) {
+              int32_t na[4], nb[4];
+              for (int j = 0; j < k; ++j) {
+                na[j] = ea[(j + rab) % k];
+                nb[j] = eb[(j + rbb) % k];
+              }
+              for (int j = 0; j < k; ++j) {
+                --hist[wa][j][ea[j] & 31];
+                --hist[wb][j][eb[j] & 31];
+                ea[j] = nb[j];
+                eb[j] = na[j];
+                ++hist[wa][j][ea[j] & 31];
+                ++hist[wb][j][eb[j] & 31];
+              }
+              improved = true;
+            }
+          }
+        if (!improved) break;
+      }
+    }
+    out.swap(dealt);
   }
   // the invariant the CTA kernels rely on, checked as built: within a class, every vertex
   // occurs at most once
