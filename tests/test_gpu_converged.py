@@ -7,12 +7,15 @@ bits); such cells are "ambiguous": their count may differ by one, and each side'
 must still be valid (residual below tol when it stopped early).  Every other cell must
 stop at the oracle's count and match it within the fixed-count bars.
 
-FP32 form: the kernel evaluates the gradient in FP32, whose norm carries a noise floor
-that is not small against tol |g0| at tol = 1e-3, so the count is a decision taken in
-the kernel's precision.  Given the count the state is unique: each cell must match the
-oracle's fixed-count step of the same count within the FP32 bar, and the decision must
-be valid in FP64 terms within a factor of two (the oracle's ratio at the stopping
-iterate below 2 tol, every earlier ratio above tol / 2).
+FP32 form: the kernel evaluates the gradient in FP32.  Near the minimiser the strain
+term's F - R is a small difference of O(1) matrices, so the FP32 gradient norm carries a
+noise floor of about 1e-3 |g0| (measured: a cell whose FP64 ratios were 1.7e-3, 1.3e-4,
+2.0e-5 at iterations 3, 4, 5 kept an FP32 ratio above 1e-3 until iteration 6), and the
+count is a decision taken in the kernel's precision.  Given the count the state is
+unique: each cell must match the oracle's fixed-count step of the same count within the
+FP32 bar, and a cell that stopped early must have an FP64 ratio below 2 tol there.  Where
+tol lies above the noise floor (1e-2) the decision must also not come late: every
+earlier FP64 ratio above tol / 2; at tol = 1e-3 the FP32 form cannot resolve that.
 """
 import numpy as np
 import pytest
@@ -27,6 +30,8 @@ FP64_BAR = 1e-10
 FP32_BAR = 1e-5
 # relative closeness of |g_k|/|g_0| to tol below which the FP64 stopping decision may differ
 FP64_MARGIN = 1e-8
+# the FP32 form's gradient-norm ratio resolves tolerances from this one up
+FP32_RESOLVED_TOL = 1e-2
 
 
 def _native():
@@ -92,7 +97,8 @@ def _check_fp32_against_oracle(b, got, ots, x, v, f, budget, tol, cells):
         if k < int(budget[c]):
             assert got["residual"][c] < tol, (c, got["residual"][c])
             assert r[k] < 2 * tol, (c, k, r)
-        assert np.all(r[1:k] > tol / 2), (c, k, r)
+        if tol >= FP32_RESOLVED_TOL:
+            assert np.all(r[1:k] > tol / 2), (c, k, r)
         s = b.cell_slice(c)
         rad = _radius(ref["x"][:, s])
         assert np.max(np.abs(got["x"][:, s] - ref["x"][:, s])) / rad <= FP32_BAR, c
