@@ -145,16 +145,18 @@ def test_full_size_batch_sampled_cells(prec):
     compare(b, nat.FP64 if prec == "fp64" else nat.FP32FORM, cells=cells)
 
 
-def test_stress_mix_sampled_cells():
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_stress_mix_sampled_cells(prec):
     """The 20000-cell serving-shaped mix (70 % 642-vertex RBC, 10 % 2562-vertex RBC, 20 %
-    platelets) in the FP32 form with the default launch shapes: 32 sampled cells against the
-    oracle, for the first step and for a step under a re-drawn force field."""
+    platelets) with the default launch shapes: 32 sampled cells against the oracle, for the
+    first step and for a step under a re-drawn force field."""
     nat = _native()
+    precision = nat.FP64 if prec == "fp64" else nat.FP32FORM
     b = I.stress_mix_batch()
     cells = sorted(np.random.default_rng(11).choice(b.ncells, size=32, replace=False).tolist())
-    compare(b, nat.FP32FORM, cells=cells)
+    compare(b, precision, cells=cells)
     b.f = I.redrawn_forces(b, b.x, 1005, 1)
-    compare(b, nat.FP32FORM, cells=cells)
+    compare(b, precision, cells=cells)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -169,6 +171,40 @@ def test_mixed_10k_batch_sampled_cells(prec):
     rng = np.random.default_rng(13)
     cells = sorted(int(c) for t in range(3) for c in rng.choice(np.flatnonzero(b.type_of_cell == t), 5, replace=False))
     compare(b, nat.FP64 if prec == "fp64" else nat.FP32FORM, cells=cells)
+
+
+# FP64 form: rounding of the per-cell sums (6.8e-15 measured on B300 over 10^4 and 2*10^4
+# cells).  FP32 form: the gradient's FP32 rounding leaves its vertex sum off zero by about
+# 6e-8 of |g| times sqrt(n), and the velocities are stored in FP32 (1.3e-6 measured).
+MOMENTUM_BAR = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+@pytest.mark.parametrize("workload", ["mixed10k", "stress20k"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_full_size_momentum_balance_every_cell(workload, prec):
+    """Every cell of the full-size mixed workloads in the default launch configuration, not a
+    sample: over one step each cell's momentum sum_i m_i v_i changes by dt sum_i f_i, the
+    balance the step keeps at any iteration count (pinned on the oracle's step).  Error per
+    cell = max over components of the imbalance / sum_i m_i |v_i^{n+1}|_inf; masses from the
+    oracle's rest state of each type."""
+    nat = _native()
+    b = (I.heterogeneous_batch(4500, 4500, 1000, seed=1002) if workload == "mixed10k"
+         else I.stress_mix_batch())
+    precision = nat.FP64 if prec == "fp64" else nat.FP32FORM
+    x, v, f = b.x, b.v, b.f
+    if prec == "fp32":
+        x, v, f = (a.astype(np.float32).astype(np.float64) for a in (x, v, f))
+    _, vg, _, st, _ = Runner(b, precision).step(x, v, f, iters=b.iters)
+    assert np.all(st == O.STATUS_OK)
+    masses = [O.CellType(t.mesh.verts, t.mesh.tris, t.material.as_tuple(), b.dt).rest.mass for t in b.types]
+    m = np.concatenate([masses[t] for t in b.type_of_cell])
+    starts = np.asarray(b.offsets[:-1], dtype=np.int64)
+    p_new = np.add.reduceat(m * vg, starts, axis=1)
+    p_expect = np.add.reduceat(m * v, starts, axis=1) + b.dt * np.add.reduceat(f, starts, axis=1)
+    scale = np.add.reduceat(m * np.max(np.abs(vg), axis=0), starts)
+    err = np.max(np.abs(p_new - p_expect), axis=0) / scale
+    print(f"{workload} {prec}: max momentum imbalance {err.max():.3e} over {b.ncells} cells")
+    assert err.max() <= MOMENTUM_BAR[prec]
 
 
 def test_uncoloured_type_runs_the_warp_kernels():

@@ -59,6 +59,29 @@ def test_objective_decreases_every_iteration():
         x, v = r.x, r.v
 
 
+def test_linear_momentum_balance_at_any_iteration_count():
+    """sum_i m_i v_i^{n+1} = sum_i m_i v_i^n + dt sum_i f_i after any number of iterations.
+    Implicit Euler with translation-invariant energies balances momentum at its minimiser;
+    the iteration keeps the balance at every iterate because it starts at the inertial
+    prediction y (sum_i m_i (x_i - y_i) = 0) and A 1 = m/dt^2 makes every L-BFGS direction
+    momentum-free (sum_i m_i d_i = dt^2 sum_i g_i = 0 by induction over the history).  A wrong
+    mass in the inertial term or in A, or a dropped dt^2 f/m in y, breaks it."""
+    for mesh, mat in ((I.rbc_mesh(2), MAT), (I.platelet_mesh(1), I.PLT_MATERIAL.as_tuple())):
+        ct = _type(mesh, mat)
+        m = ct.rest.mass[:, None]
+        rng = np.random.default_rng(41)
+        x = mesh.verts @ I.random_rotation(rng).T + rng.uniform(-50, 50, 3)
+        v = 0.05 * rng.standard_normal(x.shape)
+        f = 0.02 * rng.standard_normal(x.shape)
+        for iters in (0, 1, 2, 5, 9):
+            r = O.step(ct.rest, ct.solver, x, v, f, iters)
+            p_expect = (m * v).sum(axis=0) + DT * f.sum(axis=0)
+            p_got = (m * r.v).sum(axis=0)
+            scale = (m * np.abs(r.v)).sum()
+            assert np.max(np.abs(p_got - p_expect)) <= 1e-13 * scale, (iters, p_got - p_expect)
+            assert np.max(np.abs(DT * f.sum(axis=0))) > 1e-3 * scale   # the forces' impulse counts
+
+
 def test_one_iteration_equals_projective_dynamics_step():
     """With no area/volume energy and one iteration, quasi-Newton PD reduces to one
     local/global PD step: x1 = A^-1 (M y/dt^2 + sum_t w_t G_t^T p_t + sum_e w_e c_e p_e)."""
