@@ -84,6 +84,30 @@ def test_detection_matches_kdtree_search():
     assert total > 50          # the configuration really overlaps
 
 
+def test_equal_distances_go_to_the_smaller_cell():
+    """A vertex of cell 0 on the plane x = 0, with cell 2 the mirror image of cell 1 in that
+    plane: its nearest vertices in cells 1 and 2 are at exactly equal distances, and the
+    tie goes to the smaller cell index (slot 0 = cell 1, slot 1 = cell 2)."""
+    m = I.icosphere(1)
+    x0 = m.verts.copy()
+    x1 = m.verts + np.array([1.5, 0.0, 0.0])
+    x2 = x1 * np.array([-1.0, 1.0, 1.0])
+    z = [np.zeros_like(x0)] * 3
+    b = I._assemble([I.CellTypeSpec(m, I.RBC_MATERIAL)], [0, 0, 0], [x0, x1, x2], z, z, [1] * 3, DT, 0)
+    ots = [_type(t.mesh) for t in b.types]
+    con = O.detect_contacts(ots, b.type_of_cell, b.offsets, b.x, 1.0)
+    on_plane = np.flatnonzero(x0[:, 0] == 0.0)
+    assert len(on_plane) > 0
+    ties = 0
+    for i in on_plane:
+        if con["count"][i] == 2:
+            j1, j2 = con["vertex"][i]
+            assert list(con["cell"][i]) == [1, 2]
+            assert j2 - b.offsets[2] == j1 - b.offsets[1]      # mirror images of one vertex
+            ties += 1
+    assert ties > 0
+
+
 def test_detection_is_translation_invariant():
     b = _overlapping_spheres(seed=8)
     ots = [_type(t.mesh) for t in b.types]

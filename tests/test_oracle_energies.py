@@ -35,6 +35,22 @@ def test_regular_tetrahedron_area_volume():
     assert np.allclose(rs.mass, MAT[4] * rs.V0 / 4.0, rtol=1e-14)
 
 
+def test_cell_collapsed_to_a_point():
+    """Every vertex at one point: each triangle is degenerate (F = 0, no strain energy, and
+    counted), each hinge has K = 0 exactly and falls back to p = K0, so the bending energy
+    is sum_e (w_e/2)|K0_e|^2; A = V = 0 leaves (w_A/2) A0 and (w_V/2) V0."""
+    m = I.rbc_mesh(2)
+    rs = _rest(m)
+    x = np.tile(np.array([[1.5, -2.0, 0.7]]), (m.n, 1))
+    parts, _ = O.internal_energy_and_gradient(rs, x)
+    assert parts.strain == 0.0
+    assert parts.degenerate == m.ntris
+    assert parts.bend == pytest.approx(0.5 * np.sum(rs.w_hinge * np.sum(rs.K0 * rs.K0, axis=1)), rel=1e-14)
+    assert parts.bend > 0.0
+    assert parts.area == pytest.approx(0.5 * MAT[2] * rs.A0, rel=1e-14)
+    assert parts.volume == pytest.approx(0.5 * MAT[3] * rs.V0, rel=1e-14)
+
+
 def test_icosphere_counts_and_sphere_limits():
     for s in range(4):
         m = I.icosphere(s)

@@ -54,7 +54,7 @@ def test_objective_decreases_every_iteration():
     for s in range(3):
         r = O.step(ct.rest, ct.solver, x, v, f, 8)
         e = np.array(r.energies)
-        assert np.all(e[1:] <= e[:-1] + O.ENERGY_GUARD_EPS * np.abs(e[:-1]))
+        assert np.all(e[1:] <= e[:-1] + 1e-6 * np.abs(e[:-1]))   # the energy guard: 1e-6 relative
         assert r.grad_norms[-1] < r.grad_norms[0]
         x, v = r.x, r.v
 
@@ -80,6 +80,91 @@ def test_linear_momentum_balance_at_any_iteration_count():
             scale = (m * np.abs(r.v)).sum()
             assert np.max(np.abs(p_got - p_expect)) <= 1e-13 * scale, (iters, p_got - p_expect)
             assert np.max(np.abs(DT * f.sum(axis=0))) > 1e-3 * scale   # the forces' impulse counts
+
+
+def _rough_start(dt, noise, seed=3):
+    """A 162-vertex RBC with positions scattered by `noise` um about its rest shape: far
+    from the minimiser, so that the line search has to shorten steps."""
+    m = I.rbc_mesh(2)
+    ct = _type(m, dt=dt)
+    x = m.verts + noise * np.random.default_rng(seed).standard_normal(m.verts.shape)
+    return ct, x
+
+
+@pytest.mark.parametrize("dt,noise", [(0.1, 1.0), (10.0, 0.3), (1000.0, 1.0)])
+def test_line_search_halves_and_never_raises_the_objective(dt, noise):
+    """Backtracking from alpha = 1 by halving: every accepted step length is a power of two
+    (and some are below 1 from these rough starts), and no accepted iterate raises the
+    objective by more than the energy guard (1e-6 relative)."""
+    ct, x = _rough_start(dt, noise)
+    r = O.step(ct.rest, ct.solver, x, np.zeros_like(x), np.zeros_like(x), 8)
+    a = np.array(r.alphas)
+    assert np.array_equal(a, 2.0 ** np.round(np.log2(a)))
+    assert a.min() < 1.0
+    e = np.array(r.energies)
+    assert np.all(e[1:] <= e[:-1] + 1e-6 * np.abs(e[:-1]))
+
+
+def test_history_holds_the_five_newest_pairs(monkeypatch):
+    """The two-loop recursion of iteration k sees min(k, 5) pairs (history 5), the newest
+    last (its y the difference of the last two gradients)."""
+    ct, x = _rough_start(0.1, 0.3)
+    seen = []
+    real = O.two_loop
+
+    def spy(g, S, Y, solver):
+        seen.append(([s.copy() for s in S], [y.copy() for y in Y], g.copy()))
+        return real(g, S, Y, solver)
+
+    monkeypatch.setattr(O, "two_loop", spy)
+    iters = 9
+    r = O.step(ct.rest, ct.solver, x, np.zeros_like(x), np.zeros_like(x), iters)
+    assert len(seen) == iters
+    assert [len(S) for S, _, _ in seen] == [min(k, 5) for k in range(iters)]
+    # the newest pair's y is the difference of the gradients the last two recursions saw
+    for k in range(1, iters):
+        S, Y, g = seen[k]
+        assert np.array_equal(Y[-1], g - seen[k - 1][2])
+
+
+@pytest.mark.parametrize("kappa,alpha", [(1.998, 1.0), (2.002, 0.5)])
+def test_sufficient_decrease_on_a_one_contact_quadratic(kappa, alpha):
+    """With no elastic energy and one penetrating contact on vertex i, the objective is the
+    quadratic a u^2/2 + w (pen - u)^2/2 along the contact normal (a = m_i/dt^2), while the
+    PD matrix holds only a: the first direction is u = w pen / a, and the full step keeps the
+    fraction 1 - kappa/2 of its predicted decrease, kappa = (a + w)/a.  The weak sufficient
+    decrease of the line search takes it at kappa = 1.998 (fraction 1e-3) and halves it at
+    kappa = 2.002 (fraction -1e-3; at alpha = 1/2 the fraction is 1 - kappa/4): one
+    iteration moves vertex i by alpha w pen / a along the normal and no other vertex."""
+    m = I.icosphere(1)
+    ct = _type(m, (0.0, 0.0, 0.0, 0.0, 1.1))
+    i = 5
+    a = ct.rest.mass[i] / DT ** 2
+    n = np.array([0.6, 0.0, 0.8])
+    x = m.verts + np.array([3.0, -1.0, 2.0])
+    delta, depth = 0.01, 0.05
+    c = n @ x[i] + depth                     # gap n.x_i - c = -depth: penetrating
+    w = (kappa - 1.0) * a
+    r = O.step(ct.rest, ct.solver, x, np.zeros_like(x), np.zeros_like(x), 1,
+               contact=(np.array([i]), n[None, :], np.array([c]), delta, w))
+    assert r.alphas == [alpha]
+    assert r.x[i] - x[i] == pytest.approx(alpha * w * (delta + depth) / a * n, rel=1e-12, abs=1e-15)
+    assert np.array_equal(np.delete(r.x, i, axis=0), np.delete(x, i, axis=0))
+
+
+def test_collapsed_strain_only_cell_is_flagged_and_stays():
+    """A strain-only cell collapsed to a point, at rest: every triangle is degenerate and
+    contributes nothing, so the gradient is exactly zero; the step leaves the state where it
+    is, flags the degenerate elements in its status, and reports residual 0 (|g0| = 0)."""
+    m = I.rbc_mesh(1)
+    ct = _type(m, (1.0, 0.0, 0.0, 0.0, 1.1))
+    x = np.tile(np.array([[2.0, -1.0, 0.5]]), (m.n, 1))
+    r = O.step(ct.rest, ct.solver, x, np.zeros_like(x), np.zeros_like(x), 3)
+    assert np.array_equal(r.x, x)
+    assert np.array_equal(r.v, np.zeros_like(x))
+    assert r.status == O.STATUS_DEGENERATE
+    assert r.residual == 0.0
+    assert r.grad_norms == [0.0] * 4
 
 
 def test_one_iteration_equals_projective_dynamics_step():
