@@ -207,6 +207,46 @@ def test_full_size_momentum_balance_every_cell(workload, prec):
     assert err.max() <= MOMENTUM_BAR[prec]
 
 
+@pytest.mark.parametrize("width", [None, 0])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_collapsed_cells_are_flagged_and_stay(prec, width):
+    """A strain-only type (bending, area and volume weights 0) with two of its three cells
+    collapsed to a point: every triangle of those is degenerate and the gradient exactly
+    zero, so they keep their state exactly, report residual 0 and only the degenerate
+    status, as the oracle's step does; the ordinary cell between them matches the oracle.
+    CTA iteration kernels (default width) and the one-warp kernels (width 0)."""
+    nat = _native()
+    mesh = I.rbc_mesh(2)
+    spec = I.CellTypeSpec(mesh, I.Material(1.0, 0.0, 0.0, 0.0, 1.1))
+    p0, p2 = np.array([2.0, -1.0, 0.5]), np.array([-4.0, 8.0, 0.25])      # exact in FP32
+    xs = [np.tile(p0, (mesh.n, 1)), mesh.verts + np.array([20.0, 0.0, 0.0]), np.tile(p2, (mesh.n, 1))]
+    z = [np.zeros_like(xs[0])] * 3
+    f = [np.zeros_like(xs[0]), I.stretch_forces(mesh.verts, rng=np.random.default_rng(3)), np.zeros_like(xs[0])]
+    b = I._assemble([spec], [0, 0, 0], xs, z, f, [4, 4, 4], I.DT_DEFAULT, 0)
+    precision = nat.FP64 if prec == "fp64" else nat.FP32FORM
+    x, v, fv = b.x, b.v, b.f
+    if prec == "fp32":
+        x, v, fv = (a.astype(np.float32).astype(np.float64) for a in (x, v, fv))
+    r = Runner(b, precision)
+    if width is not None:
+        r.batch.set_iter_width(0, width)
+    xg, vg, res, st, _ = r.step(x, v, fv, iters=b.iters)
+    ref = O.batch_step(oracle_types(b), b.type_of_cell, b.offsets, x, v, fv, b.iters)
+    for c in (0, 2):
+        s_ = b.cell_slice(c)
+        assert ref["status"][c] == O.STATUS_DEGENERATE and ref["residual"][c] == 0.0
+        assert st[c] == nat.CELL_DEGENERATE
+        assert res[c] == 0.0
+        assert np.array_equal(xg[:, s_], x[:, s_])
+        assert np.array_equal(vg[:, s_], np.zeros_like(vg[:, s_]))
+    assert st[1] == ref["status"][1] == O.STATUS_OK
+    bar = FP64_BAR if prec == "fp64" else FP32_BAR
+    s1 = b.cell_slice(1)                      # (the collapsed cells have no radius to divide by)
+    xr = ref["x"][:, s1]
+    rad = np.max(np.linalg.norm(xr - xr.mean(axis=1, keepdims=True), axis=0))
+    assert np.max(np.abs(xg[:, s1] - xr)) / rad <= bar
+
+
 def test_uncoloured_type_runs_the_warp_kernels():
     """A type whose mesh would need more than 64 colour classes (a 70-gon bipyramid, 70
     triangles at each pole) has no CTA iteration kernels: its width is 0, setting one is
