@@ -171,7 +171,8 @@ npfem_status npfem_batch_layout(const npfem_batch* batch, int64_t* n_total, int6
  *         NPFEM_FP64, float for NPFEM_FP32FORM; overwritten with x_{n+1}, v_{n+1}.
  *   f_ext in [3][N_total] external forces (nN), same type as x.
  *   iters in [ncells] int32 per-cell iteration counts (>= 0), or NULL to use opts->iters.
- *   residual_out out [ncells] |grad f(x_final)| / |grad f(x_0)| (FP64), or NULL.
+ *   residual_out out [ncells] |grad f(x_final)| / |grad f(x_0)| (FP64; 0 when grad f(x_0)
+ *                is exactly zero), or NULL.
  *   status_out   out [ncells] NPFEM_CELL_* bit flags, or NULL.
  * With opts->tol > 0 a cell that meets the tolerance stops early and its remaining
  * iterations are skipped (split mode keeps launching up to the budget over the
