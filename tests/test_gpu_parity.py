@@ -247,6 +247,18 @@ def test_collapsed_cells_are_flagged_and_stay(prec, width):
     assert np.max(np.abs(xg[:, s1] - xr)) / rad <= bar
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_largest_size_class_parity(prec):
+    """Two placed 10242-vertex RBCs (icosphere subdivision 5; factor nnz 0.86 M), one step
+    against the oracle: the largest cells the tests step (type setup grows to about a minute
+    at 40962 vertices).  Their solve vectors exceed shared memory (workspace placement) and
+    their iteration arrays exceed a CTA's shared memory (one-warp iteration kernels)."""
+    nat = _native()
+    b = I.homogeneous_rbc_batch(ncells=2, seed=1001, subdiv=5)
+    assert b.types[0].mesh.n == 10242
+    compare(b, nat.FP64 if prec == "fp64" else nat.FP32FORM)
+
+
 def test_uncoloured_type_runs_the_warp_kernels():
     """A type whose mesh would need more than 64 colour classes (a 70-gon bipyramid, 70
     triangles at each pole) has no CTA iteration kernels: its width is 0, setting one is
