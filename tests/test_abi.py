@@ -130,6 +130,15 @@ def test_invalid_arguments_are_rejected(lib):
     _expect(-1, lambda: native.analyze_cell_type(m.verts, m.tris, (1, .05, 10, 10, 0.0), 0.1))
 
 
+def test_vertex_limit_is_enforced(lib):
+    """Types are limited to 65535 vertices (the packed solve tables hold 16-bit row
+    indices): one more is refused as unsupported before any mesh work."""
+    m = I.icosahedron()
+    v = np.zeros((65536, 3))
+    v[:12] = m.verts
+    _expect(-6, lambda: native.analyze_cell_type(v, m.tris, I.RBC_MATERIAL.as_tuple(), 0.1))
+
+
 def test_strain_limits_are_checked_on_the_host(lib):
     """Both 0 (or both 1) select the rotations; otherwise 0 < s_min <= 1 <= s_max, finite
     (the rest shape must lie in the constraint set)."""
