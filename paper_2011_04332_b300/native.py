@@ -21,6 +21,8 @@ FP32FORM = 1
 CELL_LINESEARCH_FAIL = 1
 CELL_DEGENERATE = 2
 CELL_NONFINITE = 4
+CELL_ITER_LIMIT = 8
+CELL_CG_NOT_CONVERGED = 16
 
 ERRORS = {-1: "INVALID_ARG", -2: "BAD_MESH", -3: "NOT_SPD", -4: "CUDA", -5: "OOM", -6: "UNSUPPORTED"}
 

@@ -130,6 +130,16 @@ def test_invalid_arguments_are_rejected(lib):
     _expect(-1, lambda: native.analyze_cell_type(m.verts, m.tris, (1, .05, 10, 10, 0.0), 0.1))
 
 
+def test_binding_status_bits_match_the_header():
+    """The binding's NPFEM_CELL_* values are the header's."""
+    hdr = open(os.path.join(ROOT, "include", "npfem.h")).read()
+    bits = {k: int(v) for k, v in re.findall(r"#define NPFEM_CELL_(\w+) (\d+)", hdr)}
+    assert len(bits) == 6
+    for k, v in bits.items():
+        if k != "OK":
+            assert getattr(native, "CELL_" + k) == v, k
+
+
 def test_vertex_limit_is_enforced(lib):
     """Types are limited to 65535 vertices (the packed solve tables hold 16-bit row
     indices): one more is refused as unsupported before any mesh work."""

@@ -38,7 +38,7 @@ class Runner:
         assert np.array_equal(self.batch.offsets, b.offsets)
         self.dtype = torch.float64 if precision == nat.FP64 else torch.float32
 
-    def step(self, x, v, f, iters=None, alpha_len=8, iters_default=5):
+    def step(self, x, v, f, iters=None, alpha_len=8, iters_default=5, max_iters=0):
         dev = torch.device("cuda:0")
         X = torch.tensor(x, dtype=self.dtype, device=dev).contiguous()
         Vt = torch.tensor(v, dtype=self.dtype, device=dev).contiguous()
@@ -48,7 +48,8 @@ class Runner:
         res = torch.full((max(nc, 1),), -1.0, dtype=torch.float64, device=dev)
         st = torch.full((max(nc, 1),), -1, dtype=torch.int32, device=dev)
         al = torch.zeros((max(nc, 1), alpha_len), dtype=torch.float64, device=dev)
-        self.batch.step(X, Vt, F, iters=it, iters_default=iters_default, residual=res, status=st, alpha_log=al)
+        self.batch.step(X, Vt, F, iters=it, iters_default=iters_default, residual=res, status=st, alpha_log=al,
+                        max_iters=max_iters)
         torch.cuda.synchronize()
         return (X.double().cpu().numpy(), Vt.double().cpu().numpy(), res.cpu().numpy()[:nc],
                 st.cpu().numpy()[:nc], al.cpu().numpy()[:nc])
@@ -257,6 +258,40 @@ def test_largest_size_class_parity(prec):
     b = I.homogeneous_rbc_batch(ncells=2, seed=1001, subdiv=5)
     assert b.types[0].mesh.n == 10242
     compare(b, nat.FP64 if prec == "fp64" else nat.FP32FORM)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_counts_beyond_the_split_bound_run_fused(prec):
+    """Per-cell counts above the split kernels' bound of 32 iterations (40 and 33, beside
+    ordinary counts) send the step to the fused kernel; every cell matches the oracle."""
+    nat = _native()
+    b = I.small_mixed_batch()
+    it = b.iters.copy()
+    it[0], it[4] = 40, 33
+    compare(b, nat.FP64 if prec == "fp64" else nat.FP32FORM, iters=it)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_counts_above_max_iters_stop_there_with_the_limit_status(prec):
+    """Split mode with a caller-given max_iters of 3: cells whose count is above it run 3
+    iterations and report NPFEM_CELL_ITER_LIMIT alone; they equal the oracle's 3-iteration
+    step, and the other cells their own counts' steps."""
+    nat = _native()
+    b = I.small_mixed_batch()
+    it = b.iters.copy()
+    it[1], it[2], it[5] = 6, 3, 1
+    precision = nat.FP64 if prec == "fp64" else nat.FP32FORM
+    x, v, f = b.x, b.v, b.f
+    if prec == "fp32":
+        x, v, f = (a.astype(np.float32).astype(np.float64) for a in (x, v, f))
+    xg, vg, res, st, _ = Runner(b, precision).step(x, v, f, iters=it, max_iters=3)
+    capped = np.minimum(it, 3)
+    ref = O.batch_step(oracle_types(b), b.type_of_cell, b.offsets, x, v, f, capped)
+    assert np.array_equal(st, np.where(it > 3, nat.CELL_ITER_LIMIT, O.STATUS_OK))
+    assert np.all(ref["status"] == O.STATUS_OK)
+    bar = FP64_BAR if prec == "fp64" else FP32_BAR
+    assert cell_errors(b, xg, ref["x"]).max() <= bar
+    assert cell_errors(b, vg * b.dt, ref["v"] * b.dt, radius_from=ref["x"]).max() <= bar
 
 
 def test_uncoloured_type_runs_the_warp_kernels():
